@@ -1,0 +1,734 @@
+/*
+ * apic_oracle.c -- plain, slow FP64 CPU oracle for the APIC / explicit MPM step of
+ * Jiang, Schroeder & Teran, "An angular momentum conserving Affine-Particle-In-Cell
+ * method" (arXiv:1603.06188).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the checker the CUDA path is compared
+ * against.  Only the test suite, the smoke check and the benchmark's CPU-baseline leg
+ * may load it.  It shares no code, header, table or constant with the CUDA library.
+ *
+ * Everything is written as the paper states it: dense grid arrays, loops over every
+ * particle and every node of its stencil, no blocking, fusion or reordering.
+ *
+ * Conventions
+ *   - d = dim (2 or 3).  Vectors are d doubles, matrices d*d doubles row-major
+ *     (M[a*d+b] = M_ab).
+ *   - Grid node i = (i0,i1[,i2]) sits at x_i = origin + i*dx, 0 <= i_a < res[a].
+ *     Linear node index: i0 + res0*(i1 + res1*i2).
+ *   - w_ip = N((x_p - x_i)/dx) as a tensor product of 1-D cardinal B-splines
+ *     (Sec. 3.5); grad w_ip is the gradient with respect to x_p, which is what
+ *     makes sum_i x_i (grad w_ip)^T = I (Sec. 3.5).
+ *   - Integrator family parameter lambda (Sec. 3.3); forces are evaluated for the
+ *     explicit member lambda = 0 only (F^{n+lambda} = F^n).
+ *
+ * Readings of the paper taken here (each is listed with its reason in the design notes):
+ *   - force sign: f_i = -sum_p V_p P(F_p^n) (F_p^n)^T grad w_ip, i.e. f = -dPhi/dx~
+ *     (the printed force equation of Sec. 3.3 drops the minus sign);
+ *   - kernel N: quadratic / cubic cardinal B-splines (never written out in the paper);
+ *   - stencil base: floor(x/dx - 1/2) (quadratic), floor(x/dx) - 1 (cubic);
+ *   - constitutive model: fixed-corotated, P = 2 mu (F - R) + lam (J - 1) J F^{-T};
+ *   - gravity and sticky walls are not in the paper; they are applied in the grid
+ *     update after the force, gravity only where m_i > 0.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int dim;            /* 2 or 3 */
+    int order;          /* 2 = quadratic, 3 = cubic B-spline */
+    int transfer;       /* 0 = APIC, 1 = PIC (C_p = 0, no B on the way back) */
+    int res[3];         /* grid nodes per axis */
+    double dx;
+    double origin[3];
+    double dt;
+    double gravity[3];
+    int boundary;       /* 0 = none, 1 = sticky walls */
+    int wall;           /* wall thickness in nodes */
+    int model;          /* 0 = none (transfer only), 1 = fixed-corotated */
+    double mu, lam;     /* Lame parameters */
+    double lambda_t;    /* integrator family parameter lambda of Sec. 3.3 */
+} or_cfg;
+
+/* ------------------------------------------------------------------ */
+/* Sec. 3.5: 1-D cardinal B-splines and their derivatives.            */
+/* ------------------------------------------------------------------ */
+double or_N(int order, double t)
+{
+    double a = fabs(t);
+    if (order == 2) {
+        if (a < 0.5) return 0.75 - a * a;
+        if (a < 1.5) return 0.5 * (1.5 - a) * (1.5 - a);
+        return 0.0;
+    }
+    if (order == 3) {
+        if (a < 1.0) return 0.5 * a * a * a - a * a + 2.0 / 3.0;
+        if (a < 2.0) return (2.0 - a) * (2.0 - a) * (2.0 - a) / 6.0;
+        return 0.0;
+    }
+    return 0.0;
+}
+
+double or_dN(int order, double t)
+{
+    double a = fabs(t), s = (t < 0.0) ? -1.0 : 1.0;
+    if (order == 2) {
+        if (a < 0.5) return -2.0 * t;
+        if (a < 1.5) return -s * (1.5 - a);
+        return 0.0;
+    }
+    if (order == 3) {
+        if (a < 1.0) return s * (1.5 * a * a - 2.0 * a);
+        if (a < 2.0) return -s * 0.5 * (2.0 - a) * (2.0 - a);
+        return 0.0;
+    }
+    return 0.0;
+}
+
+static int stencil_width(const or_cfg* c) { return c->order + 1; }
+static int stencil_count(const or_cfg* c)
+{
+    int K = stencil_width(c), n = 1;
+    for (int a = 0; a < c->dim; ++a) n *= K;
+    return n;
+}
+static int64_t node_count(const or_cfg* c)
+{
+    int64_t n = 1;
+    for (int a = 0; a < c->dim; ++a) n *= c->res[a];
+    return n;
+}
+static int64_t node_index(const or_cfg* c, const int* i)
+{
+    int64_t idx = 0;
+    for (int a = c->dim - 1; a >= 0; --a) idx = idx * c->res[a] + i[a];
+    return idx;
+}
+
+/*
+ * Stencil of one particle (Sec. 3.5): base node, the (order+1)^d weights w_ip and
+ * gradients grad w_ip.  Stencil node j has per-axis offset a_k = (j / K^k) % K from
+ * the base.  Returns 0, or -1 if any stencil node falls outside the grid.
+ */
+int or_stencil(const or_cfg* c, const double* xp, int* base, double* w, double* dw)
+{
+    const int d = c->dim, K = stencil_width(c);
+    double w1[3][4], d1[3][4];
+    int rc = 0;
+    for (int a = 0; a < d; ++a) {
+        double u = (xp[a] - c->origin[a]) / c->dx;
+        base[a] = (c->order == 2) ? (int)floor(u - 0.5) : (int)floor(u) - 1;
+        if (base[a] < 0 || base[a] + c->order > c->res[a] - 1) rc = -1;
+        for (int k = 0; k < K; ++k) {
+            double t = u - (double)(base[a] + k);
+            w1[a][k] = or_N(c->order, t);
+            d1[a][k] = or_dN(c->order, t) / c->dx;
+        }
+    }
+    const int ns = stencil_count(c);
+    for (int j = 0; j < ns; ++j) {
+        int off[3] = {0, 0, 0}, r = j;
+        for (int a = 0; a < d; ++a) { off[a] = r % K; r /= K; }
+        double ww = 1.0;
+        for (int a = 0; a < d; ++a) ww *= w1[a][off[a]];
+        w[j] = ww;
+        for (int g = 0; g < d; ++g) {
+            double gg = 1.0;
+            for (int a = 0; a < d; ++a) gg *= (a == g) ? d1[a][off[a]] : w1[a][off[a]];
+            dw[j * d + g] = gg;
+        }
+    }
+    return rc;
+}
+
+/* Brute force: w_ip and grad w_ip for EVERY node of the grid (definition in Sec. 3.5). */
+void or_weights_all(const or_cfg* c, const double* xp, double* w_all, double* dw_all)
+{
+    const int d = c->dim;
+    const int64_t nn = node_count(c);
+    for (int64_t idx = 0; idx < nn; ++idx) {
+        int i[3] = {0, 0, 0};
+        int64_t r = idx;
+        for (int a = 0; a < d; ++a) { i[a] = (int)(r % c->res[a]); r /= c->res[a]; }
+        double t[3];
+        for (int a = 0; a < d; ++a) t[a] = (xp[a] - (c->origin[a] + i[a] * c->dx)) / c->dx;
+        double ww = 1.0;
+        for (int a = 0; a < d; ++a) ww *= or_N(c->order, t[a]);
+        w_all[idx] = ww;
+        for (int g = 0; g < d; ++g) {
+            double gg = 1.0;
+            for (int a = 0; a < d; ++a)
+                gg *= (a == g) ? or_dN(c->order, t[a]) / c->dx : or_N(c->order, t[a]);
+            dw_all[idx * d + g] = gg;
+        }
+    }
+}
+
+static void stencil_node(const or_cfg* c, const int* base, int j, int* i, double* xi)
+{
+    const int K = stencil_width(c);
+    int r = j;
+    for (int a = 0; a < c->dim; ++a) {
+        i[a] = base[a] + r % K;
+        r /= K;
+        xi[a] = c->origin[a] + i[a] * c->dx;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Small dense linear algebra (d = 2 or 3).                            */
+/* ------------------------------------------------------------------ */
+static double det_d(int d, const double* A)
+{
+    if (d == 2) return A[0] * A[3] - A[1] * A[2];
+    return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+           A[2] * (A[3] * A[7] - A[4] * A[6]);
+}
+
+/* cofactor matrix: cof(A) = det(A) A^{-T} */
+static void cofactor_d(int d, const double* A, double* C)
+{
+    if (d == 2) {
+        C[0] = A[3]; C[1] = -A[2]; C[2] = -A[1]; C[3] = A[0];
+        return;
+    }
+    C[0] = A[4] * A[8] - A[5] * A[7];
+    C[1] = A[5] * A[6] - A[3] * A[8];
+    C[2] = A[3] * A[7] - A[4] * A[6];
+    C[3] = A[2] * A[7] - A[1] * A[8];
+    C[4] = A[0] * A[8] - A[2] * A[6];
+    C[5] = A[1] * A[6] - A[0] * A[7];
+    C[6] = A[1] * A[5] - A[2] * A[4];
+    C[7] = A[2] * A[3] - A[0] * A[5];
+    C[8] = A[0] * A[4] - A[1] * A[3];
+}
+
+static void inverse_d(int d, const double* A, double* Ai)
+{
+    double C[9];
+    cofactor_d(d, A, C);
+    double det = det_d(d, A);
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) Ai[a * d + b] = C[b * d + a] / det;
+}
+
+static void matmul_d(int d, const double* A, const double* B, double* C)
+{
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) {
+            double s = 0.0;
+            for (int k = 0; k < d; ++k) s += A[a * d + k] * B[k * d + b];
+            C[a * d + b] = s;
+        }
+}
+
+/*
+ * Singular value decomposition F = U diag(sigma) V^T by one-sided (Hestenes) Jacobi:
+ * plane rotations applied to the columns of F until they are mutually orthogonal.
+ * Returned with det U = det V = +1; when det F < 0 the smallest singular value is
+ * made negative.  Columns of U belonging to zero singular values are completed to an
+ * orthonormal basis.
+ */
+void or_svd(int d, const double* F, double* U, double* sigma, double* V)
+{
+    double A[9];
+    memcpy(A, F, sizeof(double) * d * d);
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) V[a * d + b] = (a == b) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < d - 1; ++p)
+            for (int q = p + 1; q < d; ++q) {
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int i = 0; i < d; ++i) {
+                    al += A[i * d + p] * A[i * d + p];
+                    be += A[i * d + q] * A[i * d + q];
+                    ga += A[i * d + p] * A[i * d + q];
+                }
+                if (ga == 0.0) continue;
+                double rel = fabs(ga) / sqrt(al * be);
+                if (rel > off) off = rel;
+                if (rel < 1e-17) continue;
+                double zeta = (be - al) / (2.0 * ga);
+                double t = ((zeta >= 0.0) ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+                for (int i = 0; i < d; ++i) {
+                    double ap = A[i * d + p], aq = A[i * d + q];
+                    A[i * d + p] = cs * ap - sn * aq;
+                    A[i * d + q] = sn * ap + cs * aq;
+                    double vp = V[i * d + p], vq = V[i * d + q];
+                    V[i * d + p] = cs * vp - sn * vq;
+                    V[i * d + q] = sn * vp + cs * vq;
+                }
+            }
+        if (off < 1e-15) break;
+    }
+    /* column norms are the singular values; sort descending (permuting U and V alike) */
+    double s[3];
+    for (int j = 0; j < d; ++j) {
+        double nrm = 0.0;
+        for (int i = 0; i < d; ++i) nrm += A[i * d + j] * A[i * d + j];
+        s[j] = sqrt(nrm);
+    }
+    for (int a = 0; a < d; ++a)
+        for (int b = a + 1; b < d; ++b)
+            if (s[b] > s[a]) {
+                double tmp = s[a]; s[a] = s[b]; s[b] = tmp;
+                for (int i = 0; i < d; ++i) {
+                    tmp = A[i * d + a]; A[i * d + a] = A[i * d + b]; A[i * d + b] = tmp;
+                    tmp = V[i * d + a]; V[i * d + a] = V[i * d + b]; V[i * d + b] = tmp;
+                }
+            }
+    double smax = s[0] > 0.0 ? s[0] : 1.0;
+    int have[3] = {0, 0, 0};
+    for (int j = 0; j < d; ++j) {
+        if (s[j] > 1e-14 * smax) {
+            for (int i = 0; i < d; ++i) U[i * d + j] = A[i * d + j] / s[j];
+            have[j] = 1;
+        }
+    }
+    /* complete missing columns of U (rank-deficient F) */
+    for (int j = 0; j < d; ++j) {
+        if (have[j]) continue;
+        if (d == 2) {
+            int o = 1 - j;
+            if (have[o]) { U[0 * 2 + j] = -U[1 * 2 + o]; U[1 * 2 + j] = U[0 * 2 + o]; }
+            else { U[0 * 2 + j] = (j == 0); U[1 * 2 + j] = (j == 1); }
+        } else {
+            /* Gram-Schmidt against the columns already present, starting from the axes */
+            for (int e = 0; e < 3; ++e) {
+                double cnd[3] = {0, 0, 0};
+                cnd[e] = 1.0;
+                for (int k = 0; k < 3; ++k) {
+                    if (!have[k]) continue;
+                    double dot = 0.0;
+                    for (int i = 0; i < 3; ++i) dot += cnd[i] * U[i * 3 + k];
+                    for (int i = 0; i < 3; ++i) cnd[i] -= dot * U[i * 3 + k];
+                }
+                double nrm = sqrt(cnd[0] * cnd[0] + cnd[1] * cnd[1] + cnd[2] * cnd[2]);
+                if (nrm > 0.5) {
+                    for (int i = 0; i < 3; ++i) U[i * 3 + j] = cnd[i] / nrm;
+                    break;
+                }
+            }
+        }
+        have[j] = 1;
+    }
+    /* make V a rotation (flip a column of U and V together), then U */
+    if (det_d(d, V) < 0.0) {
+        for (int i = 0; i < d; ++i) { V[i * d + d - 1] = -V[i * d + d - 1]; U[i * d + d - 1] = -U[i * d + d - 1]; }
+    }
+    if (det_d(d, U) < 0.0) {
+        for (int i = 0; i < d; ++i) U[i * d + d - 1] = -U[i * d + d - 1];
+        s[d - 1] = -s[d - 1];
+    }
+    for (int j = 0; j < d; ++j) sigma[j] = s[j];
+}
+
+/* Rotation part of the polar decomposition, R = U V^T with det R = +1. */
+void or_polar(int d, const double* F, double* R)
+{
+    double U[9], s[3], V[9];
+    or_svd(d, F, U, s, V);
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) {
+            double acc = 0.0;
+            for (int k = 0; k < d; ++k) acc += U[a * d + k] * V[b * d + k];
+            R[a * d + b] = acc;
+        }
+}
+
+/*
+ * Fixed-corotated energy density and first Piola-Kirchhoff stress (Sec. 3.1 defines
+ * P = dPsi/dF; the paper says the particular model does not matter, Sec. 3.3):
+ *   Psi = mu |F - R|_F^2 + lam/2 (J - 1)^2,   P = 2 mu (F - R) + lam (J - 1) J F^{-T}.
+ */
+double or_psi_fcr(int d, double mu, double lam, const double* F)
+{
+    double R[9];
+    or_polar(d, F, R);
+    double s = 0.0;
+    for (int k = 0; k < d * d; ++k) s += (F[k] - R[k]) * (F[k] - R[k]);
+    double J = det_d(d, F);
+    return mu * s + 0.5 * lam * (J - 1.0) * (J - 1.0);
+}
+
+void or_stress_fcr(int d, double mu, double lam, const double* F, double* P)
+{
+    double R[9], C[9];
+    or_polar(d, F, R);
+    cofactor_d(d, F, C);
+    double J = det_d(d, F);
+    for (int k = 0; k < d * d; ++k) P[k] = 2.0 * mu * (F[k] - R[k]) + lam * (J - 1.0) * C[k];
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 3.2: transfer to grid.                                         */
+/* ------------------------------------------------------------------ */
+/*
+ * m_i = sum_p m_p w_ip
+ * D_p = sum_i w_ip (x_i - x_p)(x_i - x_p)^T          (computed by summation)
+ * m_i v_i = sum_p w_ip m_p (v_p + B_p D_p^{-1} (x_i - x_p))   (APIC)
+ * m_i v_i = sum_p w_ip m_p v_p                                (PIC, Sec. 1 eq. 1)
+ * f_i = -sum_p V_p P(F_p) F_p^T grad w_ip   (Sec. 3.3, lambda = 0, sign reading above)
+ * Grid arrays are accumulated into (callers zero them first).  Returns the number of
+ * particles whose stencil left the grid (those are skipped).
+ */
+int64_t or_p2g(const or_cfg* c, int64_t n, const double* x, const double* v, const double* B,
+               const double* F, const double* mass, const double* vol, double* gm, double* gmv,
+               double* gf)
+{
+    const int d = c->dim, ns = stencil_count(c);
+    int64_t bad = 0;
+    double w[64], dw[192];
+    for (int64_t p = 0; p < n; ++p) {
+        const double* xp = x + p * d;
+        int base[3];
+        if (or_stencil(c, xp, base, w, dw) != 0) { ++bad; continue; }
+        double D[9] = {0}, Dinv[9], Cp[9] = {0};
+        for (int j = 0; j < ns; ++j) {
+            int i[3]; double xi[3], r[3];
+            stencil_node(c, base, j, i, xi);
+            for (int a = 0; a < d; ++a) r[a] = xi[a] - xp[a];
+            for (int a = 0; a < d; ++a)
+                for (int b = 0; b < d; ++b) D[a * d + b] += w[j] * r[a] * r[b];
+        }
+        if (c->transfer == 0) {
+            inverse_d(d, D, Dinv);
+            matmul_d(d, B + p * d * d, Dinv, Cp);
+        }
+        double tau[9] = {0};
+        if (c->model == 1) {
+            double P[9];
+            or_stress_fcr(d, c->mu, c->lam, F + p * d * d, P);
+            /* tau = V_p P F^T */
+            const double* Fp = F + p * d * d;
+            for (int a = 0; a < d; ++a)
+                for (int b = 0; b < d; ++b) {
+                    double s = 0.0;
+                    for (int k = 0; k < d; ++k) s += P[a * d + k] * Fp[b * d + k];
+                    tau[a * d + b] = vol[p] * s;
+                }
+        }
+        for (int j = 0; j < ns; ++j) {
+            int i[3]; double xi[3], r[3];
+            stencil_node(c, base, j, i, xi);
+            for (int a = 0; a < d; ++a) r[a] = xi[a] - xp[a];
+            int64_t ni = node_index(c, i);
+            gm[ni] += w[j] * mass[p];
+            for (int a = 0; a < d; ++a) {
+                double vel = v[p * d + a];
+                for (int b = 0; b < d; ++b) vel += Cp[a * d + b] * r[b];
+                gmv[ni * d + a] += w[j] * mass[p] * vel;
+                if (c->model == 1) {
+                    double s = 0.0;
+                    for (int b = 0; b < d; ++b) s += tau[a * d + b] * dw[j * d + b];
+                    gf[ni * d + a] -= s;
+                }
+            }
+        }
+    }
+    return bad;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 3.3: grid evolution, explicit member lambda = 0.               */
+/* ------------------------------------------------------------------ */
+/*
+ * v_i = (m v)_i / m_i,  v~_i = v_i + dt f_i / m_i (+ dt g, sticky walls; not in paper).
+ * Nodes with m_i = 0 get v_i = v~_i = 0.
+ */
+void or_grid_update(const or_cfg* c, const double* gm, const double* gmv, const double* gf,
+                    double* gv, double* gvt)
+{
+    const int d = c->dim;
+    const int64_t nn = node_count(c);
+    for (int64_t idx = 0; idx < nn; ++idx) {
+        int i[3] = {0, 0, 0};
+        int64_t r = idx;
+        for (int a = 0; a < d; ++a) { i[a] = (int)(r % c->res[a]); r /= c->res[a]; }
+        if (gm[idx] <= 0.0) {
+            for (int a = 0; a < d; ++a) { gv[idx * d + a] = 0.0; gvt[idx * d + a] = 0.0; }
+            continue;
+        }
+        int wall = 0;
+        if (c->boundary == 1)
+            for (int a = 0; a < d; ++a)
+                if (i[a] < c->wall || i[a] >= c->res[a] - c->wall) wall = 1;
+        for (int a = 0; a < d; ++a) {
+            double vi = gmv[idx * d + a] / gm[idx];
+            double vt = vi + c->dt * gf[idx * d + a] / gm[idx] + c->dt * c->gravity[a];
+            gv[idx * d + a] = vi;
+            gvt[idx * d + a] = wall ? 0.0 : vt;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 3.4: transfer to particles, general form.                      */
+/* ------------------------------------------------------------------ */
+/*
+ * x~_i = x_i + dt (lambda v_i + (1 - lambda) v~_i)
+ * v_p^{n+1} = sum_i w_ip v~_i
+ * x_p^{n+1} = sum_i w_ip x~_i
+ * B_p^{n+1} = 1/2 sum_i w_ip ( v~_i (x_i - x_p + x~_i - x_p^{n+1})^T
+ *                              + (x_i - x_p - x~_i + x_p^{n+1}) v~_i^T )   (APIC)
+ * B_p^{n+1} = 0                                                            (PIC)
+ * F_p^{n+1} = (I + sum_i (x~_i - x_i) (grad w_ip)^T) F_p^n
+ * x, F updated in place; v, B written.  Returns the number of skipped particles.
+ */
+int64_t or_g2p(const or_cfg* c, int64_t n, double* x, double* v, double* B, double* F,
+               const double* gv, const double* gvt)
+{
+    const int d = c->dim, ns = stencil_count(c);
+    const double lt = c->lambda_t;
+    int64_t bad = 0;
+    double w[64], dw[192];
+    for (int64_t p = 0; p < n; ++p) {
+        double* xp = x + p * d;
+        int base[3];
+        if (or_stencil(c, xp, base, w, dw) != 0) { ++bad; continue; }
+        double xn[3] = {0, 0, 0}, vn[3] = {0, 0, 0}, G[9] = {0};
+        for (int j = 0; j < ns; ++j) {
+            int i[3]; double xi[3];
+            stencil_node(c, base, j, i, xi);
+            int64_t ni = node_index(c, i);
+            for (int a = 0; a < d; ++a) {
+                double xt = xi[a] + c->dt * (lt * gv[ni * d + a] + (1.0 - lt) * gvt[ni * d + a]);
+                xn[a] += w[j] * xt;
+                vn[a] += w[j] * gvt[ni * d + a];
+                for (int b = 0; b < d; ++b) G[a * d + b] += (xt - xi[a]) * dw[j * d + b];
+            }
+        }
+        double Bn[9] = {0};
+        if (c->transfer == 0) {
+            for (int j = 0; j < ns; ++j) {
+                int i[3]; double xi[3], xt[3], vt[3];
+                stencil_node(c, base, j, i, xi);
+                int64_t ni = node_index(c, i);
+                for (int a = 0; a < d; ++a) {
+                    vt[a] = gvt[ni * d + a];
+                    xt[a] = xi[a] + c->dt * (lt * gv[ni * d + a] + (1.0 - lt) * vt[a]);
+                }
+                for (int a = 0; a < d; ++a)
+                    for (int b = 0; b < d; ++b) {
+                        double t1 = vt[a] * (xi[b] - xp[b] + xt[b] - xn[b]);
+                        double t2 = (xi[a] - xp[a] - xt[a] + xn[a]) * vt[b];
+                        Bn[a * d + b] += 0.5 * w[j] * (t1 + t2);
+                    }
+            }
+        }
+        double Fo[9], M[9];
+        memcpy(Fo, F + p * d * d, sizeof(double) * d * d);
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) M[a * d + b] = (a == b ? 1.0 : 0.0) + G[a * d + b];
+        matmul_d(d, M, Fo, F + p * d * d);
+        for (int a = 0; a < d; ++a) { xp[a] = xn[a]; v[p * d + a] = vn[a]; }
+        memcpy(B + p * d * d, Bn, sizeof(double) * d * d);
+    }
+    return bad;
+}
+
+/*
+ * The lambda = 0 form the general transfer reduces to (Sec. 5.7):
+ *   v_p = sum_i w_ip v~_i,  B_p = sum_i w_ip v~_i (x_i - x_p)^T,
+ *   x_p^{n+1} = x_p + dt v_p^{n+1},  F_p^{n+1} = (I + dt sum_i v~_i (grad w_ip)^T) F_p.
+ */
+int64_t or_g2p_lambda0(const or_cfg* c, int64_t n, double* x, double* v, double* B, double* F,
+                       const double* gvt)
+{
+    const int d = c->dim, ns = stencil_count(c);
+    int64_t bad = 0;
+    double w[64], dw[192];
+    for (int64_t p = 0; p < n; ++p) {
+        double* xp = x + p * d;
+        int base[3];
+        if (or_stencil(c, xp, base, w, dw) != 0) { ++bad; continue; }
+        double vn[3] = {0, 0, 0}, Bn[9] = {0}, G[9] = {0};
+        for (int j = 0; j < ns; ++j) {
+            int i[3]; double xi[3];
+            stencil_node(c, base, j, i, xi);
+            int64_t ni = node_index(c, i);
+            for (int a = 0; a < d; ++a) {
+                double vt = gvt[ni * d + a];
+                vn[a] += w[j] * vt;
+                for (int b = 0; b < d; ++b) {
+                    if (c->transfer == 0) Bn[a * d + b] += w[j] * vt * (xi[b] - xp[b]);
+                    G[a * d + b] += vt * dw[j * d + b];
+                }
+            }
+        }
+        double Fo[9], M[9];
+        memcpy(Fo, F + p * d * d, sizeof(double) * d * d);
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) M[a * d + b] = (a == b ? 1.0 : 0.0) + c->dt * G[a * d + b];
+        matmul_d(d, M, Fo, F + p * d * d);
+        for (int a = 0; a < d; ++a) { v[p * d + a] = vn[a]; xp[a] += c->dt * vn[a]; }
+        memcpy(B + p * d * d, Bn, sizeof(double) * d * d);
+    }
+    return bad;
+}
+
+/* ------------------------------------------------------------------ */
+/* Potential energy Phi(x~) = sum_p V_p Psi(F^_p(x~)) (Sec. 3.3), for the  */
+/* finite-difference check of the force.  dxg holds x~_i - x_i per node. */
+/* ------------------------------------------------------------------ */
+double or_potential(const or_cfg* c, int64_t n, const double* x, const double* F,
+                    const double* vol, const double* dxg)
+{
+    const int d = c->dim, ns = stencil_count(c);
+    double w[64], dw[192], phi = 0.0;
+    for (int64_t p = 0; p < n; ++p) {
+        int base[3];
+        if (or_stencil(c, x + p * d, base, w, dw) != 0) continue;
+        double M[9], Fh[9];
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) M[a * d + b] = (a == b) ? 1.0 : 0.0;
+        for (int j = 0; j < ns; ++j) {
+            int i[3]; double xi[3];
+            stencil_node(c, base, j, i, xi);
+            int64_t ni = node_index(c, i);
+            for (int a = 0; a < d; ++a)
+                for (int b = 0; b < d; ++b) M[a * d + b] += dxg[ni * d + a] * dw[j * d + b];
+        }
+        matmul_d(d, M, F + p * d * d, Fh);
+        phi += vol[p] * or_psi_fcr(d, c->mu, c->lam, Fh);
+    }
+    return phi;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 3.1 / 5.3: total linear and angular momentum.                  */
+/* ------------------------------------------------------------------ */
+/*
+ * Particles: p = sum m_p v_p;  l = sum x_p x m_p v_p + m_p (B_p)^T : eps
+ * ((B^T):eps = (B_21 - B_12, B_02 - B_20, B_10 - B_01); in 2-D only the z entry).
+ * In 2-D, l[0] holds the scalar z component and l[1] = l[2] = 0.
+ */
+void or_momentum_particles(const or_cfg* c, int64_t n, const double* x, const double* v,
+                           const double* B, const double* mass, double* p, double* l)
+{
+    const int d = c->dim;
+    for (int a = 0; a < 3; ++a) { p[a] = 0.0; l[a] = 0.0; }
+    for (int64_t q = 0; q < n; ++q) {
+        const double* xp = x + q * d;
+        const double* vp = v + q * d;
+        const double* Bp = B + q * d * d;
+        double m = mass[q];
+        for (int a = 0; a < d; ++a) p[a] += m * vp[a];
+        if (d == 2) {
+            l[0] += m * (xp[0] * vp[1] - xp[1] * vp[0]);
+            if (c->transfer == 0) l[0] += m * (Bp[2] - Bp[1]);
+        } else {
+            l[0] += m * (xp[1] * vp[2] - xp[2] * vp[1]);
+            l[1] += m * (xp[2] * vp[0] - xp[0] * vp[2]);
+            l[2] += m * (xp[0] * vp[1] - xp[1] * vp[0]);
+            if (c->transfer == 0) {
+                l[0] += m * (Bp[7] - Bp[5]);
+                l[1] += m * (Bp[2] - Bp[6]);
+                l[2] += m * (Bp[3] - Bp[1]);
+            }
+        }
+    }
+}
+
+/* Grid: p = sum_i (m v)_i,  l = sum_i x_i x (m v)_i (Sec. 5.1 / 5.3). */
+void or_momentum_grid(const or_cfg* c, const double* gmv, double* p, double* l)
+{
+    const int d = c->dim;
+    const int64_t nn = node_count(c);
+    for (int a = 0; a < 3; ++a) { p[a] = 0.0; l[a] = 0.0; }
+    for (int64_t idx = 0; idx < nn; ++idx) {
+        int i[3] = {0, 0, 0};
+        int64_t r = idx;
+        double xi[3];
+        for (int a = 0; a < d; ++a) {
+            i[a] = (int)(r % c->res[a]); r /= c->res[a];
+            xi[a] = c->origin[a] + i[a] * c->dx;
+        }
+        const double* q = gmv + idx * d;
+        for (int a = 0; a < d; ++a) p[a] += q[a];
+        if (d == 2) {
+            l[0] += xi[0] * q[1] - xi[1] * q[0];
+        } else {
+            l[0] += xi[1] * q[2] - xi[2] * q[1];
+            l[1] += xi[2] * q[0] - xi[0] * q[2];
+            l[2] += xi[0] * q[1] - xi[1] * q[0];
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Cell keys and the stable sort by key.                                */
+/* ------------------------------------------------------------------ */
+/*
+ * Key of a particle given as integer cell index plus offset in [0,1) per axis:
+ * the stencil base node b (quadratic: cell - 1 if offset < 1/2 else cell;
+ * cubic: cell - 1), then block = b / E (E = block edge, a power of two),
+ * in-block cell = b mod E, key = linear(block) << (d log2 E) | linear(in-block),
+ * both linearised with axis 0 fastest.  Blocks per axis = ceil(res / E).
+ */
+void or_keys(const or_cfg* c, int block_edge, int64_t n, const int32_t* cell, const double* off,
+             uint32_t* keys)
+{
+    const int d = c->dim;
+    int lg = 0;
+    while ((1 << lg) < block_edge) ++lg;
+    for (int64_t p = 0; p < n; ++p) {
+        uint32_t blk = 0, in = 0, mult_b = 1, mult_i = 1;
+        for (int a = 0; a < d; ++a) {
+            int b = cell[p * d + a] - 1;
+            if (c->order == 2 && off[p * d + a] >= 0.5) b = cell[p * d + a];
+            int nb = (c->res[a] + block_edge - 1) / block_edge;
+            blk += (uint32_t)(b / block_edge) * mult_b;
+            in += (uint32_t)(b % block_edge) * mult_i;
+            mult_b *= (uint32_t)nb;
+            mult_i *= (uint32_t)block_edge;
+        }
+        keys[p] = (blk << (d * lg)) | in;
+    }
+}
+
+typedef struct { uint32_t key; int64_t idx; } key_idx;
+static int cmp_key_idx(const void* a, const void* b)
+{
+    const key_idx* x = (const key_idx*)a;
+    const key_idx* y = (const key_idx*)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    if (x->idx != y->idx) return x->idx < y->idx ? -1 : 1;
+    return 0;
+}
+
+/* Stable sort: order by (key, original index); perm[k] = index of the k-th particle. */
+void or_stable_sort(int64_t n, const uint32_t* keys, int64_t* perm)
+{
+    key_idx* t = (key_idx*)malloc(sizeof(key_idx) * (n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) { t[i].key = keys[i]; t[i].idx = i; }
+    qsort(t, (size_t)n, sizeof(key_idx), cmp_key_idx);
+    for (int64_t i = 0; i < n; ++i) perm[i] = t[i].idx;
+    free(t);
+}
+
+/* ------------------------------------------------------------------ */
+/* One whole explicit step: P2G, grid update, G2P (general form).       */
+/* ------------------------------------------------------------------ */
+int64_t or_step(const or_cfg* c, int64_t n, double* x, double* v, double* B, double* F,
+                const double* mass, const double* vol)
+{
+    const int d = c->dim;
+    const int64_t nn = node_count(c);
+    double* gm = (double*)calloc((size_t)nn, sizeof(double));
+    double* gmv = (double*)calloc((size_t)nn * d, sizeof(double));
+    double* gf = (double*)calloc((size_t)nn * d, sizeof(double));
+    double* gv = (double*)calloc((size_t)nn * d, sizeof(double));
+    double* gvt = (double*)calloc((size_t)nn * d, sizeof(double));
+    int64_t bad = -1;
+    if (gm && gmv && gf && gv && gvt) {
+        bad = or_p2g(c, n, x, v, B, F, mass, vol, gm, gmv, gf);
+        or_grid_update(c, gm, gmv, gf, gv, gvt);
+        bad += or_g2p(c, n, x, v, B, F, gv, gvt);
+    }
+    free(gm); free(gmv); free(gf); free(gv); free(gvt);
+    return bad;
+}
