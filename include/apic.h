@@ -1,0 +1,166 @@
+/*
+ * apic.h -- C ABI of the GB300 (sm_103a) APIC / explicit MPM hot path.
+ *
+ * Method: Jiang, Schroeder & Teran, "An angular momentum conserving Affine-Particle-In-
+ * Cell method" (arXiv:1603.06188).  One step is the particle-to-grid transfer of mass and
+ * affine momentum (Sec. 3.2) with the elastic force (Sec. 3.3), the explicit grid update
+ * (Sec. 3.3, lambda = 0) and the grid-to-particle transfer of v_p, B_p with advection of
+ * x_p and F_p (Sec. 3.4, in the lambda = 0 form of Sec. 5.7).
+ *
+ * General rules
+ *   - Every call returns an apic_status and never aborts.  apic_last_error() gives a
+ *     human-readable reason for the last failure of a simulation.
+ *   - The library allocates no device memory: the caller passes one device workspace of
+ *     apic_workspace_size() bytes to apic_create() and keeps it alive until
+ *     apic_destroy().  Host-side bookkeeping (a small struct) is malloc'ed.
+ *   - All kernels are launched on the stream given to apic_create() (a cudaStream_t
+ *     passed as void*; NULL = the legacy default stream).  Calls are asynchronous except
+ *     those documented as synchronising.
+ *   - Device-side checks (a particle whose stencil leaves the grid, a timed-out wait) are
+ *     latched in an error word that synchronising calls read; they then return
+ *     APIC_ERR_NUMERIC / APIC_ERR_TIMEOUT.
+ *   - Positions cross the boundary as FP64 absolute coordinates.  Inside, a particle's
+ *     position is an integer cell index plus an offset in [0,1) (FP32 for precision 32),
+ *     so weights keep full precision on large grids.
+ *   - Particles are reordered internally every step (sorted by cell key); downloads
+ *     return them in upload order.
+ *   - Row-major matrices: B[a*d+b] = B_ab = sum_i w_ip v~_ia (x_i - x_p)_b (Sec. 3.4),
+ *     F[a*d+b] = F_ab.
+ *   - Grid nodes sit at x_i = origin + i*dx, 0 <= i_a < res[a].  Dense grid arrays
+ *     exchanged with the caller use node index i0 + res0*(i1 + res1*i2).
+ */
+#ifndef APIC_H
+#define APIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct apic_sim apic_sim;
+
+typedef enum {
+    APIC_OK = 0,
+    APIC_ERR_ARG = 1,          /* invalid argument or call order */
+    APIC_ERR_OOM = 2,          /* workspace too small or particle capacity exceeded */
+    APIC_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    APIC_ERR_TIMEOUT = 4,      /* a bounded device-side wait ran out */
+    APIC_ERR_NUMERIC = 5,      /* a particle's stencil left the grid (it was clamped) */
+    APIC_ERR_UNSUPPORTED = 6   /* configuration the library does not implement */
+} apic_status;
+
+enum { APIC_TRANSFER_APIC = 0, APIC_TRANSFER_PIC = 1 };
+enum { APIC_BOUNDARY_NONE = 0, APIC_BOUNDARY_STICKY = 1 };
+enum { APIC_MODEL_NONE = 0, APIC_MODEL_FIXED_COROTATED = 1 };
+enum { APIC_WHERE_PARTICLES = 0, APIC_WHERE_GRID = 1 };
+enum { APIC_GRID_MOMENTUM = 0, APIC_GRID_VELOCITY = 1 };
+
+typedef struct {
+    int dim;                 /* 2 or 3 */
+    int order;               /* 2 = quadratic, 3 = cubic B-spline (Sec. 3.5); 1 (multilinear)
+                                is rejected with APIC_ERR_UNSUPPORTED: the B_p transfer is
+                                unstable for it (Sec. 5.9) */
+    int precision;           /* 32 or 64: arithmetic type of particle and grid state */
+    int transfer;            /* APIC_TRANSFER_APIC, or APIC_TRANSFER_PIC (C_p = 0, Sec. 5.6) */
+    int res[3];              /* grid nodes per axis (res[2] ignored in 2-D); <= 1024 in 3-D */
+    double dx;               /* grid spacing */
+    double origin[3];        /* position of node 0 */
+    double dt;               /* time step */
+    double gravity[3];       /* added to v~ of nodes with mass (not in the paper) */
+    int boundary;            /* APIC_BOUNDARY_NONE or _STICKY: v~ = 0 on nodes within `wall`
+                                nodes of a face (not in the paper) */
+    int wall;                /* wall thickness in nodes */
+    int model;               /* APIC_MODEL_NONE (transfer only) or _FIXED_COROTATED */
+    double E, nu;            /* Young's modulus, Poisson's ratio */
+    double particle_mass;    /* m_p, the same for every particle of a simulation */
+    double particle_volume;  /* V_p (reference volume), the same for every particle */
+    int tile_particles;      /* particles per P2G / G2P tile (power of two, 64..4096);
+                                0 = default */
+} apic_config;
+
+/* Bytes of device workspace a simulation with this config and capacity needs.
+ * Errors: APIC_ERR_ARG (NULL pointer, bad config), APIC_ERR_UNSUPPORTED. */
+apic_status apic_workspace_size(const apic_config* cfg, int64_t max_particles, size_t* bytes);
+
+/* Create a simulation.  `workspace` is a device pointer (256-byte aligned) to at least
+ * apic_workspace_size() bytes, owned by the caller, used exclusively by this simulation
+ * until apic_destroy().  `stream` is a cudaStream_t (or NULL).  Zeroes the grid on the
+ * stream.  Errors: APIC_ERR_ARG, APIC_ERR_UNSUPPORTED, APIC_ERR_OOM (workspace too small). */
+apic_status apic_create(const apic_config* cfg, int64_t max_particles, void* workspace,
+                        size_t workspace_bytes, void* stream, apic_sim** out);
+
+/* Release the host-side state.  Synchronises the stream.  The workspace is the caller's. */
+apic_status apic_destroy(apic_sim* sim);
+
+/* Load n particles (n <= max_particles) from FP64 arrays: x (n*d), v (n*d), B (n*d*d),
+ * F (n*d*d).  v, B may be NULL (zero); F may be NULL (identity).  `on_device` = 1 if the
+ * pointers are device memory, 0 for host memory.  The data are copied; the library keeps
+ * no pointer.  Synchronising when on_device = 0.
+ * Errors: APIC_ERR_ARG, APIC_ERR_OOM (n > capacity), APIC_ERR_CUDA. */
+apic_status apic_upload(apic_sim* sim, int64_t n, const double* x, const double* v,
+                        const double* B, const double* F, int on_device);
+
+/* Copy the particle state back in upload order (any pointer may be NULL to skip that
+ * field).  Synchronising.  Errors: APIC_ERR_ARG, APIC_ERR_CUDA, and a latched device error. */
+apic_status apic_download(apic_sim* sim, double* x, double* v, double* B, double* F, int on_device);
+
+/* Positions in their internal form, upload order: integer cell (n*d int32) and offset in
+ * [0,1) widened exactly to FP64 (n*d).  Synchronising, host pointers. */
+apic_status apic_download_positions(apic_sim* sim, int32_t* cell, double* offset);
+
+/* Sec. 3.2 (+ Sec. 3.3 force): cell keys, stable radix sort by key, tile list, and the
+ * scatter m_i = sum_p w_ip m_p, (m v)_i = sum_p w_ip m_p (v_p + B_p D_p^{-1} (x_i - x_p)),
+ * with dt f_i = -dt sum_p V_p P(F_p) F_p^T grad w_ip added into the momentum when a
+ * constitutive model is set.  D_p = (dx^2/4) I (quadratic) / (dx^2/3) I (cubic), the
+ * constants Sec. 5.6 prints for B-splines.  Asynchronous. */
+apic_status apic_p2g(apic_sim* sim);
+
+/* Sec. 3.3, lambda = 0: v~_i = ((m v)_i + dt f_i) / m_i + dt g, sticky walls, v~ = 0 where
+ * m_i = 0.  Clears the accumulation grid for the next step.  Asynchronous. */
+apic_status apic_grid_update(apic_sim* sim);
+
+/* Sec. 3.4 with Sec. 5.7 (lambda = 0): v_p = sum_i w_ip v~_i, B_p = sum_i w_ip v~_i
+ * (x_i - x_p)^T (zero for PIC), F_p <- (I + dt sum_i v~_i grad w_ip^T) F_p,
+ * x_p <- x_p + dt v_p.  Writes the particles in sorted order and their next cell keys.
+ * Asynchronous. */
+apic_status apic_g2p(apic_sim* sim);
+
+/* n whole steps (apic_p2g, apic_grid_update, apic_g2p).  Asynchronous. */
+apic_status apic_step(apic_sim* sim, int n);
+
+/* Total linear momentum p and angular momentum l about the world origin, accumulated in
+ * FP64 (Sec. 3.1; Sec. 5.3 for the particle form l = sum x_p x m_p v_p + m_p B_p^T : eps).
+ * where = APIC_WHERE_PARTICLES, or APIC_WHERE_GRID: after apic_p2g, sum (m v)_i (which
+ * includes dt f_i) and sum x_i x (m v)_i; after apic_grid_update, sum m_i v~_i and
+ * sum x_i x m_i v~_i.  In 2-D, l[0] is the z component.  Synchronising, host pointers. */
+apic_status apic_momentum(apic_sim* sim, int where, double p[3], double l[3]);
+
+/* Dense copy of the grid (host pointers, res-box node order): which =
+ * APIC_GRID_MOMENTUM after apic_p2g: m (nodes) and (m v)_i + dt f_i (nodes*d);
+ * APIC_GRID_VELOCITY after apic_grid_update: m and v~.  Synchronising. */
+apic_status apic_grid_download(apic_sim* sim, int which, double* m, double* mv);
+
+/* The last sort (host pointers, n entries each): sorted keys, and perm[k] = internal
+ * index, at sort time, of the k-th sorted particle (right after apic_upload the internal
+ * order is the upload order).  Synchronising. */
+apic_status apic_keys_download(apic_sim* sim, uint32_t* keys, uint32_t* perm);
+
+/* Active node blocks (4^d nodes each) of the grid after apic_p2g: out[b] = 1 if block b
+ * (linear index, axis 0 fastest, ceil(res/4) blocks per axis) takes part in the grid
+ * update, else 0.  n_blocks must equal the block count.  Synchronising, host pointer. */
+apic_status apic_grid_occupancy(apic_sim* sim, uint8_t* out, int64_t n_blocks);
+
+/* Counters: [0] particles, [1] blocks of the grid, [2] tiles of the last sort,
+ * [3] FP64 fallbacks of the 3x3 polar decomposition since creation.  Synchronising. */
+apic_status apic_stats(apic_sim* sim, int64_t out[4]);
+
+/* Reason for the last failing call on this simulation ("" if none). */
+const char* apic_last_error(apic_sim* sim);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APIC_H */

@@ -1,0 +1,302 @@
+"""Thin ctypes binding of the C ABI in include/apic.h (argument marshalling only).
+
+Module-level functions carry the C entry points' names; :class:`Sim` bundles them with a
+torch-allocated device workspace (PyTorch provides device memory and the stream; every
+step of the method runs in libapic.so's kernels).  Loading fails loudly when the library
+has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+APIC_OK, APIC_ERR_ARG, APIC_ERR_OOM, APIC_ERR_CUDA, APIC_ERR_TIMEOUT, APIC_ERR_NUMERIC, APIC_ERR_UNSUPPORTED = range(7)
+TRANSFER = {"apic": 0, "pic": 1}
+BOUNDARY = {"none": 0, "sticky": 1}
+MODEL = {"none": 0, "fcr": 1, "fixed_corotated": 1}
+WHERE_PARTICLES, WHERE_GRID = 0, 1
+GRID_MOMENTUM, GRID_VELOCITY = 0, 1
+STATUS_NAMES = {0: "APIC_OK", 1: "APIC_ERR_ARG", 2: "APIC_ERR_OOM", 3: "APIC_ERR_CUDA", 4: "APIC_ERR_TIMEOUT",
+                5: "APIC_ERR_NUMERIC", 6: "APIC_ERR_UNSUPPORTED"}
+
+
+class ApicError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(C.Structure):
+    """Mirror of ``apic_config``."""
+
+    _fields_ = [
+        ("dim", C.c_int), ("order", C.c_int), ("precision", C.c_int), ("transfer", C.c_int),
+        ("res", C.c_int * 3), ("dx", C.c_double), ("origin", C.c_double * 3),
+        ("dt", C.c_double), ("gravity", C.c_double * 3),
+        ("boundary", C.c_int), ("wall", C.c_int), ("model", C.c_int),
+        ("E", C.c_double), ("nu", C.c_double),
+        ("particle_mass", C.c_double), ("particle_volume", C.c_double),
+        ("tile_particles", C.c_int),
+    ]
+
+
+def make_config(dim=3, order=2, precision=32, transfer="apic", res=(64, 64, 64), dx=1 / 64, origin=(0, 0, 0),
+                dt=0.0, gravity=(0, 0, 0), boundary="none", wall=0, model="none", E=0.0, nu=0.0,
+                particle_mass=1.0, particle_volume=1.0, tile_particles=0) -> Config:
+    c = Config()
+    c.dim, c.order, c.precision = dim, order, precision
+    c.transfer = TRANSFER[transfer] if isinstance(transfer, str) else transfer
+    r = list(res) + [1] * (3 - len(res))
+    c.res = (C.c_int * 3)(*r)
+    c.dx = dx
+    c.origin = (C.c_double * 3)(*(list(origin) + [0.0] * (3 - len(origin))))
+    c.dt = dt
+    c.gravity = (C.c_double * 3)(*(list(gravity) + [0.0] * (3 - len(gravity))))
+    c.boundary = BOUNDARY[boundary] if isinstance(boundary, str) else boundary
+    c.wall = wall
+    c.model = MODEL[model] if isinstance(model, str) else model
+    c.E, c.nu = E, nu
+    c.particle_mass, c.particle_volume = particle_mass, particle_volume
+    c.tile_particles = tile_particles
+    return c
+
+
+_lib = None
+SIGNATURES = {
+    "apic_workspace_size": (C.c_int, [C.POINTER(Config), C.c_int64, C.POINTER(C.c_size_t)]),
+    "apic_create": (C.c_int, [C.POINTER(Config), C.c_int64, C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "apic_destroy": (C.c_int, [C.c_void_p]),
+    "apic_upload": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "apic_download": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "apic_download_positions": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "apic_p2g": (C.c_int, [C.c_void_p]),
+    "apic_grid_update": (C.c_int, [C.c_void_p]),
+    "apic_g2p": (C.c_int, [C.c_void_p]),
+    "apic_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "apic_momentum": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "apic_grid_download": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "apic_keys_download": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "apic_grid_occupancy": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "apic_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "apic_last_error": (C.c_char_p, [C.c_void_p]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libapic.so (optionally building it first).  Raises if it is not there."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"libapic.so is not built ({path}); run __graft_entry__.build() or "
+                               "python -m paper_1603_06188_gb300.build")
+        _build.build()
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st: int, sim=None):
+    if st != APIC_OK:
+        msg = load().apic_last_error(sim).decode() if sim else ""
+        raise ApicError(st, msg)
+
+
+def _ptr(a) -> C.c_void_p | None:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(a.data_ptr())
+
+
+# ----------------------------------------------------------------------- C entry points
+def apic_workspace_size(cfg: Config, max_particles: int) -> int:
+    out = C.c_size_t(0)
+    _check(load().apic_workspace_size(C.byref(cfg), max_particles, C.byref(out)))
+    return out.value
+
+
+def apic_create(cfg: Config, max_particles: int, workspace_ptr: int, workspace_bytes: int, stream_ptr: int):
+    h = C.c_void_p()
+    _check(load().apic_create(C.byref(cfg), max_particles, C.c_void_p(workspace_ptr), workspace_bytes,
+                              C.c_void_p(stream_ptr), C.byref(h)))
+    return h
+
+
+def apic_destroy(sim):
+    _check(load().apic_destroy(sim))
+
+
+def apic_upload(sim, n, x, v=None, B=None, F=None, on_device=0):
+    _check(load().apic_upload(sim, n, _ptr(x), _ptr(v), _ptr(B), _ptr(F), on_device), sim)
+
+
+def apic_download(sim, x=None, v=None, B=None, F=None, on_device=0):
+    _check(load().apic_download(sim, _ptr(x), _ptr(v), _ptr(B), _ptr(F), on_device), sim)
+
+
+def apic_download_positions(sim, cell, offset):
+    _check(load().apic_download_positions(sim, _ptr(cell), _ptr(offset)), sim)
+
+
+def apic_p2g(sim):
+    _check(load().apic_p2g(sim), sim)
+
+
+def apic_grid_update(sim):
+    _check(load().apic_grid_update(sim), sim)
+
+
+def apic_g2p(sim):
+    _check(load().apic_g2p(sim), sim)
+
+
+def apic_step(sim, n: int):
+    _check(load().apic_step(sim, n), sim)
+
+
+def apic_momentum(sim, where: int):
+    p = np.zeros(3)
+    l = np.zeros(3)
+    _check(load().apic_momentum(sim, where, _ptr(p), _ptr(l)), sim)
+    return p, l
+
+
+def apic_grid_download(sim, which: int, m, mv):
+    _check(load().apic_grid_download(sim, which, _ptr(m), _ptr(mv)), sim)
+
+
+def apic_keys_download(sim, keys, perm):
+    _check(load().apic_keys_download(sim, _ptr(keys), _ptr(perm)), sim)
+
+
+def apic_grid_occupancy(sim, out, n_blocks: int):
+    _check(load().apic_grid_occupancy(sim, _ptr(out), n_blocks), sim)
+
+
+def apic_stats(sim):
+    out = np.zeros(4, dtype=np.int64)
+    _check(load().apic_stats(sim, _ptr(out)), sim)
+    return out
+
+
+def apic_last_error(sim) -> str:
+    return load().apic_last_error(sim).decode()
+
+
+# ----------------------------------------------------------------------- convenience
+class Sim:
+    """One simulation: config + torch-owned device workspace + the library handle."""
+
+    def __init__(self, cfg: Config, max_particles: int, device=None, stream=None):
+        import torch
+
+        self.cfg = cfg
+        self.dim = cfg.dim
+        self.capacity = max_particles
+        self.device = torch.device(device or "cuda")
+        nbytes = apic_workspace_size(cfg, max_particles)
+        # torch's caching allocator returns 512-byte aligned blocks
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        self.handle = apic_create(cfg, max_particles, self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
+        self.n = 0
+
+    @property
+    def res(self):
+        return tuple(self.cfg.res[a] for a in range(self.dim))
+
+    @property
+    def n_nodes(self) -> int:
+        return int(np.prod(self.res))
+
+    @property
+    def n_blocks(self) -> int:
+        return int(np.prod([(r + 3) // 4 for r in self.res]))
+
+    def upload(self, x, v=None, B=None, F=None):
+        """Host numpy arrays (float64) or CUDA float64 tensors."""
+        d = self.dim
+        n = len(x)
+        self.n = n          # the library holds n particles even when it reports a range error
+        if isinstance(x, np.ndarray):
+            arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(n, -1) for a in (x, v, B, F)]
+            apic_upload(self.handle, n, *arrs, on_device=0)
+        else:
+            arrs = [None if a is None else a.contiguous() for a in (x, v, B, F)]
+            apic_upload(self.handle, n, *arrs, on_device=1)
+            self._keep = arrs
+
+    def download(self):
+        d, n = self.dim, self.n
+        x = np.zeros((n, d)); v = np.zeros((n, d)); B = np.zeros((n, d, d)); F = np.zeros((n, d, d))
+        apic_download(self.handle, x, v, B, F, on_device=0)
+        return x, v, B, F
+
+    def download_positions(self):
+        cell = np.zeros((self.n, self.dim), dtype=np.int32)
+        off = np.zeros((self.n, self.dim))
+        apic_download_positions(self.handle, cell, off)
+        return cell, off
+
+    def p2g(self):
+        apic_p2g(self.handle)
+
+    def grid_update(self):
+        apic_grid_update(self.handle)
+
+    def g2p(self):
+        apic_g2p(self.handle)
+
+    def step(self, n: int = 1):
+        apic_step(self.handle, n)
+
+    def momentum(self, where: str = "particles"):
+        return apic_momentum(self.handle, WHERE_PARTICLES if where == "particles" else WHERE_GRID)
+
+    def grid(self, which: str = "momentum"):
+        m = np.zeros(self.n_nodes)
+        mv = np.zeros((self.n_nodes, self.dim))
+        apic_grid_download(self.handle, GRID_MOMENTUM if which == "momentum" else GRID_VELOCITY, m, mv)
+        return m, mv
+
+    def keys(self):
+        k = np.zeros(self.n, dtype=np.uint32)
+        p = np.zeros(self.n, dtype=np.uint32)
+        apic_keys_download(self.handle, k, p)
+        return k, p
+
+    def occupancy(self):
+        out = np.zeros(self.n_blocks, dtype=np.uint8)
+        apic_grid_occupancy(self.handle, out, self.n_blocks)
+        return out
+
+    def stats(self) -> dict:
+        s = apic_stats(self.handle)
+        return {"particles": int(s[0]), "blocks": int(s[1]), "tiles": int(s[2]), "polar_fp64_fallbacks": int(s[3])}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            apic_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,90 @@
+// apic_internal.h -- declarations shared by the library's translation units (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#define APIC_BLOCK_EDGE 4
+#define APIC_ERRBIT_RANGE 1u     // a particle's stencil left the grid (clamped)
+#define APIC_ERRBIT_TIMEOUT 2u   // a bounded mbarrier wait ran out
+#define APIC_ERRBIT_CAPACITY 4u  // tile list overflow
+
+namespace apic {
+
+// Type-erased description of one simulation's device buffers, handed to the launchers.
+struct Buffers {
+    // particle state: two copies (ping-pong), 7 arrays each, element size per precision
+    void* st[2][7];
+    uint32_t* knext;             // keys of the current particle order (input of the sort)
+    uint32_t* kA; uint32_t* kB;  // radix ping-pong keys
+    uint32_t* vA; uint32_t* vB;  // radix ping-pong values (particle indices)
+    uint32_t* radix_counts;      // 256 * radix tiles
+    uint32_t* scan_part;         // partial sums of the device scan
+    uint32_t* tiles;             // tile start offsets (+ end sentinel)
+    uint32_t* chunk_cnt;         // per-chunk tile counts (scanned in place)
+    uint32_t* ntiles;            // device counter: number of tiles
+    void* acc;                   // accumulation grid (4 lanes per node)
+    void* vel;                   // velocity grid (4 lanes per node)
+    uint32_t* flags;             // active node blocks
+    double* mom_part;            // per-CTA momentum partials
+    double* mom_out;             // 6 doubles
+    uint32_t* err;               // latched error bits
+    uint32_t* fallbacks;         // FP64 polar fallbacks
+    double* staging;             // FP64 staging for upload / download
+    size_t staging_doubles;
+};
+
+struct HostCfg {
+    int dim, order, precision, transfer;
+    int res[3];
+    int nb[3];
+    double dx, origin[3], dt, gravity[3];
+    int boundary, wall, model;
+    double mu, lam, mass, vol;
+    int tile;                    // particles per tile (power of two)
+    int key_bits;
+    int nblocks;
+    int64_t capacity;
+};
+
+// sort / tiles (apic_sort.cu)
+int radix_tiles(int64_t n);
+size_t scan_partials_needed(int64_t n);
+// sorts knext (values = identity) into (*keys_out, *vals_out); returns the CUDA error
+cudaError_t radix_sort(const Buffers& b, int64_t n, int key_bits, cudaStream_t s,
+                       uint32_t** keys_out, uint32_t** vals_out);
+cudaError_t build_tiles(const Buffers& b, const uint32_t* skeys, int64_t n, int dim, int tile,
+                        int64_t max_tiles, cudaStream_t s);
+cudaError_t exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* part,
+                           uint32_t* total, cudaStream_t s);
+
+// transfer kernels (apic_transfer_f32.cu / apic_transfer_f64.cu): one set per real type
+struct Launch {
+    int sms;          // multiprocessors
+    int p2g_grid;     // persistent grid sizes
+    int g2p_grid;
+    int mom_parts;    // CTAs of the momentum reduction
+};
+
+#define APIC_DECLARE_PRECISION(SFX)                                                                          \
+    cudaError_t keys_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, cudaStream_t s);           \
+    cudaError_t p2g_##SFX(const HostCfg& c, const Buffers& b, int cur, const uint32_t* skeys,                 \
+                          const uint32_t* perm, int64_t n, const Launch& L, cudaStream_t s);                   \
+    cudaError_t grid_update_##SFX(const HostCfg& c, const Buffers& b, const Launch& L, cudaStream_t s);       \
+    cudaError_t g2p_##SFX(const HostCfg& c, const Buffers& b, int cur, const uint32_t* skeys,                 \
+                          const uint32_t* perm, int64_t n, const Launch& L, cudaStream_t s);                   \
+    cudaError_t upload_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const double* x,         \
+                             const double* v, const double* B, const double* F, cudaStream_t s);              \
+    cudaError_t download_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, double* x, double* v,  \
+                               double* B, double* F, int32_t* cell, double* off, cudaStream_t s);              \
+    cudaError_t momentum_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, int where,             \
+                               int grid_phase, const Launch& L, cudaStream_t s);                               \
+    cudaError_t grid_dense_##SFX(const HostCfg& c, const Buffers& b, int which, double* m, double* mv,        \
+                                 cudaStream_t s);                                                               \
+    cudaError_t occupancy_##SFX(const HostCfg& c, int* p2g_per_sm, int* g2p_per_sm);
+
+APIC_DECLARE_PRECISION(f32)
+APIC_DECLARE_PRECISION(f64)
+
+}  // namespace apic

@@ -1,0 +1,299 @@
+// apic_sort.cu -- stable LSD radix sort of particle cell keys, a device-wide exclusive
+// scan, and the tile list that P2G / G2P walk.  The sort is what lets P2G accumulate a
+// grid block's particles in shared memory (the key is the particle's stencil-base block
+// followed by the base node inside the block), so its order is part of the contract:
+// stable, ties kept in current index order.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "apic_internal.h"
+
+namespace apic {
+
+namespace {
+
+constexpr int RT = 256;              // radix threads per CTA
+constexpr int RI = 8;                // keys per thread
+constexpr int RTILE = RT * RI;       // keys per radix tile
+constexpr int RW = RT / 32;          // warps per CTA
+constexpr int SCH = 4096;            // elements per scan chunk (256 threads x 16)
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Per-tile digit histogram.  Warp w of tile t owns keys [t*RTILE + w*256, +256), walked in
+// rounds of 32 (the same order the scatter uses).  Same-digit lanes are merged with
+// match.any so the shared-memory counter sees one add per distinct digit.
+__global__ void __launch_bounds__(RT) k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                                                   int ntiles, uint32_t* __restrict__ counts)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * RTILE + w * (RI * 32);
+#pragma unroll
+    for (int r = 0; r < RI; ++r) {
+        const int64_t idx = base + r * 32 + lane;
+        const bool valid = idx < n;
+        const unsigned d = valid ? (keys[idx] >> shift) & 255u : 256u;
+        const unsigned peers = __match_any_sync(FULL, d);
+        if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter: rank = (global start of this digit in this tile) + (same digit in earlier
+// warps of the tile) + (same digit earlier in this warp).
+__global__ void __launch_bounds__(RT) k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                      uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
+                                                      int shift, int ntiles, const uint32_t* __restrict__ offsets)
+{
+    __shared__ uint32_t wc[RW][256];
+    __shared__ uint32_t goff[256];
+    for (int i = threadIdx.x; i < RW * 256; i += RT) (&wc[0][0])[i] = 0;
+    goff[threadIdx.x] = offsets[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * RTILE + w * (RI * 32);
+    uint32_t key[RI], val[RI], lr[RI];
+    unsigned dig[RI];
+#pragma unroll
+    for (int r = 0; r < RI; ++r) {
+        const int64_t idx = base + r * 32 + lane;
+        const bool valid = idx < n;
+        key[r] = valid ? kin[idx] : 0u;
+        val[r] = valid ? (vin ? vin[idx] : (uint32_t)idx) : 0u;
+        const unsigned d = valid ? (key[r] >> shift) & 255u : 256u;
+        dig[r] = d;
+        const unsigned peers = __match_any_sync(FULL, d);
+        const unsigned before = (unsigned)__popc(peers & lanemask_lt());
+        const uint32_t cnt = valid ? wc[w][d] : 0u;
+        __syncwarp();
+        lr[r] = cnt + before;
+        if (valid && lane == __ffs(peers) - 1) wc[w][d] = cnt + (uint32_t)__popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        uint32_t run = 0;
+        for (int ww = 0; ww < RW; ++ww) {
+            const uint32_t c = wc[ww][threadIdx.x];
+            wc[ww][threadIdx.x] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RI; ++r) {
+        const int64_t idx = base + r * 32 + lane;
+        if (idx < n) {
+            const unsigned d = dig[r];
+            const uint32_t pos = goff[d] + wc[w][d] + lr[r];
+            kout[pos] = key[r];
+            vout[pos] = val[r];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- exclusive scan
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// exclusive scan of one value per thread over a 256-thread CTA; returns the CTA total
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t& excl)
+{
+    __shared__ uint32_t ws[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t inc = warp_incl_scan(v, lane);
+    if (lane == 31) ws[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = lane < 8 ? ws[lane] : 0u;
+        t = warp_incl_scan(t, lane);
+        if (lane < 8) ws[lane] = t;
+    }
+    __syncthreads();
+    excl = inc - v + (w > 0 ? ws[w - 1] : 0u);
+    const uint32_t total = ws[7];
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t* __restrict__ in, int64_t n, uint32_t* __restrict__ part)
+{
+    const int64_t base = (int64_t)blockIdx.x * SCH + threadIdx.x * 16;
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        if (base + i < n) s += in[base + i];
+    uint32_t ex;
+    const uint32_t tot = block_excl_scan(s, ex);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(256) k_scan_top(uint32_t* __restrict__ part, int64_t np, uint32_t* __restrict__ total)
+{
+    uint32_t carry = 0;
+    for (int64_t b = 0; b < np; b += 256) {
+        const int64_t i = b + threadIdx.x;
+        const uint32_t v = i < np ? part[i] : 0u;
+        uint32_t ex;
+        const uint32_t tot = block_excl_scan(v, ex);
+        if (i < np) part[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void __launch_bounds__(256) k_scan_down(const uint32_t* in, uint32_t* out, int64_t n,
+                                                   const uint32_t* __restrict__ part)
+{
+    const int64_t base = (int64_t)blockIdx.x * SCH + threadIdx.x * 16;
+    uint32_t v[16];
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        v[i] = (base + i < n) ? in[base + i] : 0u;
+        s += v[i];
+    }
+    uint32_t ex;
+    block_excl_scan(s, ex);
+    uint32_t run = part[blockIdx.x] + ex;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+}
+
+// ---------------------------------------------------------------- tiles
+// A tile is a maximal run of sorted particles with the same node block inside one aligned
+// chunk of `tile` particles; a new tile starts at every chunk start and every block change.
+__device__ __forceinline__ bool is_head(const uint32_t* skeys, int64_t k, int64_t chunk_start, int sh)
+{
+    return k == chunk_start || (skeys[k] >> sh) != (skeys[k - 1] >> sh);
+}
+
+__global__ void __launch_bounds__(256) k_tile_count(const uint32_t* __restrict__ skeys, int64_t n, int sh, int tile,
+                                                    uint32_t* __restrict__ cnt)
+{
+    const int64_t cs = (int64_t)blockIdx.x * tile;
+    const int per = tile / 256;
+    const int64_t k0 = cs + (int64_t)threadIdx.x * per;
+    uint32_t c = 0;
+    for (int i = 0; i < per; ++i) {
+        const int64_t k = k0 + i;
+        if (k < n && is_head(skeys, k, cs, sh)) ++c;
+    }
+    uint32_t ex;
+    const uint32_t tot = block_excl_scan(c, ex);
+    if (threadIdx.x == 0) cnt[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(256) k_tile_write(const uint32_t* __restrict__ skeys, int64_t n, int sh, int tile,
+                                                    const uint32_t* __restrict__ off, const uint32_t* __restrict__ ntiles,
+                                                    int64_t max_tiles, uint32_t* __restrict__ tiles, int nchunks,
+                                                    uint32_t* __restrict__ err)
+{
+    const int64_t cs = (int64_t)blockIdx.x * tile;
+    const int per = tile / 256;
+    const int64_t k0 = cs + (int64_t)threadIdx.x * per;
+    uint32_t c = 0;
+    for (int i = 0; i < per; ++i) {
+        const int64_t k = k0 + i;
+        if (k < n && is_head(skeys, k, cs, sh)) ++c;
+    }
+    uint32_t ex;
+    const uint32_t tot = block_excl_scan(c, ex);
+    uint32_t pos = off[blockIdx.x] + ex;
+    for (int i = 0; i < per; ++i) {
+        const int64_t k = k0 + i;
+        if (k < n && is_head(skeys, k, cs, sh)) {
+            if ((int64_t)pos < max_tiles) tiles[pos] = (uint32_t)k;
+            ++pos;
+        }
+    }
+    if (blockIdx.x == nchunks - 1 && threadIdx.x == 0) {
+        const uint32_t nt = *ntiles;
+        if ((int64_t)nt < max_tiles) tiles[nt] = (uint32_t)n;
+        else atomicOr(err, APIC_ERRBIT_CAPACITY);
+        (void)tot;
+    }
+}
+
+}  // namespace
+
+int radix_tiles(int64_t n) { return (int)((n + RTILE - 1) / RTILE); }
+
+size_t scan_partials_needed(int64_t n)
+{
+    const int64_t m = 256 * (int64_t)radix_tiles(n) + 1;
+    const int64_t mm = m > n ? m : n;
+    return (size_t)((mm + SCH - 1) / SCH + 1);
+}
+
+cudaError_t exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* part, uint32_t* total,
+                           cudaStream_t s)
+{
+    if (n <= 0) {
+        if (total) return cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
+        return cudaSuccess;
+    }
+    const int64_t np = (n + SCH - 1) / SCH;
+    k_scan_reduce<<<(unsigned)np, 256, 0, s>>>(in, n, part);
+    k_scan_top<<<1, 256, 0, s>>>(part, np, total);
+    k_scan_down<<<(unsigned)np, 256, 0, s>>>(in, out, n, part);
+    return cudaGetLastError();
+}
+
+cudaError_t radix_sort(const Buffers& b, int64_t n, int key_bits, cudaStream_t s, uint32_t** keys_out,
+                       uint32_t** vals_out)
+{
+    const int nt = radix_tiles(n);
+    const int passes = (key_bits + 7) / 8;
+    const uint32_t* kin = b.knext;
+    const uint32_t* vin = nullptr;
+    uint32_t* kb[2] = {b.kA, b.kB};
+    uint32_t* vb[2] = {b.vA, b.vB};
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        k_radix_hist<<<nt, RT, 0, s>>>(kin, n, shift, nt, b.radix_counts);
+        cudaError_t e = exclusive_scan(b.radix_counts, b.radix_counts, 256 * (int64_t)nt, b.scan_part, nullptr, s);
+        if (e != cudaSuccess) return e;
+        k_radix_scatter<<<nt, RT, 0, s>>>(kin, vin, kb[p & 1], vb[p & 1], n, shift, nt, b.radix_counts);
+        kin = kb[p & 1];
+        vin = vb[p & 1];
+    }
+    *keys_out = const_cast<uint32_t*>(kin);
+    *vals_out = const_cast<uint32_t*>(vin);
+    return cudaGetLastError();
+}
+
+cudaError_t build_tiles(const Buffers& b, const uint32_t* skeys, int64_t n, int dim, int tile, int64_t max_tiles,
+                        cudaStream_t s)
+{
+    const int64_t nchunks = (n + tile - 1) / tile;
+    const int sh = 2 * dim;
+    k_tile_count<<<(unsigned)nchunks, 256, 0, s>>>(skeys, n, sh, tile, b.chunk_cnt);
+    cudaError_t e = exclusive_scan(b.chunk_cnt, b.chunk_cnt, nchunks, b.scan_part, b.ntiles, s);
+    if (e != cudaSuccess) return e;
+    k_tile_write<<<(unsigned)nchunks, 256, 0, s>>>(skeys, n, sh, tile, b.chunk_cnt, b.ntiles, max_tiles, b.tiles,
+                                                   (int)nchunks, b.err);
+    return cudaGetLastError();
+}
+
+}  // namespace apic

@@ -1,0 +1,880 @@
+// apic_transfer.cuh -- the per-step kernels of the APIC / explicit MPM method
+// (arXiv:1603.06188), templated on dimension D, B-spline order and real type R:
+//   k_keys         cell keys of the current particle order
+//   k_p2g          Sec. 3.2 transfer to grid + Sec. 3.3 force, shared-memory tile per node block
+//   k_grid_update  Sec. 3.3 explicit (lambda = 0) grid update
+//   k_g2p          Sec. 3.4 transfer to particles (lambda = 0 form of Sec. 5.7), grid blocks
+//                  staged in shared memory by bulk asynchronous copies (TMA engine)
+//   k_mom_*        Sec. 3.1 / 5.3 total momentum, FP64 accumulation
+// plus upload / download / dense-grid conversion kernels.  Included by apic_transfer_f32.cu
+// and apic_transfer_f64.cu, which instantiate it for one real type each.
+#pragma once
+
+#include "apic_device.cuh"
+
+namespace apic {
+
+constexpr unsigned FULLMASK = 0xffffffffu;
+constexpr int TPB = 256;
+
+template <typename R> struct HostToDev {
+    static DevCfg<R> make(const HostCfg& h, int64_t n)
+    {
+        DevCfg<R> c;
+        for (int a = 0; a < 3; ++a) {
+            c.res[a] = h.res[a];
+            c.nb[a] = h.nb[a];
+            c.origin[a] = (R)h.origin[a];
+            c.gravity[a] = (R)h.gravity[a];
+        }
+        c.dx = (R)h.dx;
+        c.inv_dx = (R)(1.0 / h.dx);
+        c.dt = (R)h.dt;
+        c.boundary = h.boundary;
+        c.wall = h.wall;
+        c.model = h.model;
+        c.transfer = h.transfer;
+        c.mu = (R)h.mu;
+        c.lam = (R)h.lam;
+        c.mass = (R)h.mass;
+        c.vol = (R)h.vol;
+        const double kappa = h.order == 2 ? 0.25 : 1.0 / 3.0;
+        c.inv_kdx = (R)(1.0 / (kappa * h.dx));
+        c.n = (int)n;
+        c.nblocks = h.nblocks;
+        return c;
+    }
+};
+
+template <typename R> PState<R> state_of(const Buffers& b, int which)
+{
+    PState<R> s;
+    s.A = (V4<R>*)b.st[which][0];
+    s.V = (V4<R>*)b.st[which][1];
+    s.Ba = (V4<R>*)b.st[which][2];
+    s.Bb = (V4<R>*)b.st[which][3];
+    s.Fa = (V4<R>*)b.st[which][4];
+    s.Fb = (V4<R>*)b.st[which][5];
+    s.Fc = (V2<R>*)b.st[which][6];
+    return s;
+}
+
+// ---------------------------------------------------------------- stencil base + key
+// Per-axis base node (clamped into the grid; a clamp latches APIC_ERRBIT_RANGE), its
+// fractional position fx = u - base and the 1-D weights.
+template <int D, int ORDER, typename R>
+__device__ __forceinline__ bool particle_stencil(const R* o, const int* cell, const DevCfg<R>& c, int* base, R* fx,
+                                                 R (*w)[ORDER + 1], R (*dw)[ORDER + 1])
+{
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        axis_weights<ORDER, R>(o[a], cell[a], base[a], fx[a], w[a], dw[a]);
+        if (base[a] < 0 || base[a] + ORDER > c.res[a] - 1) {
+            ok = false;
+            base[a] = base[a] < 0 ? 0 : c.res[a] - 1 - ORDER;
+        }
+    }
+    return ok;
+}
+
+template <int D, int ORDER, typename R>
+__device__ __forceinline__ uint32_t key_of(const R* o, const int* cell, const DevCfg<R>& c, uint32_t* err)
+{
+    int base[D];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        int b = (ORDER == 2) ? (o[a] >= R(0.5) ? cell[a] : cell[a] - 1) : cell[a] - 1;
+        if (b < 0 || b + ORDER > c.res[a] - 1) {
+            ok = false;
+            b = b < 0 ? 0 : c.res[a] - 1 - ORDER;
+        }
+        base[a] = b;
+    }
+    if (!ok) set_err(err, APIC_ERRBIT_RANGE);
+    if (D == 3) {
+        const uint32_t blk = ((uint32_t)(base[2] >> 2) * c.nb[1] + (uint32_t)(base[1] >> 2)) * c.nb[0] + (uint32_t)(base[0] >> 2);
+        const uint32_t in = ((uint32_t)(base[2] & 3) << 4) | ((uint32_t)(base[1] & 3) << 2) | (uint32_t)(base[0] & 3);
+        return (blk << 6) | in;
+    }
+    const uint32_t blk = (uint32_t)(base[1] >> 2) * c.nb[0] + (uint32_t)(base[0] >> 2);
+    return (blk << 4) | ((uint32_t)(base[1] & 3) << 2) | (uint32_t)(base[0] & 3);
+}
+
+template <int D, typename R> __device__ __forceinline__ void block_coords(uint32_t blk, const DevCfg<R>& c, int* b)
+{
+    b[0] = (int)(blk % (uint32_t)c.nb[0]);
+    if (D == 3) {
+        b[1] = (int)((blk / (uint32_t)c.nb[0]) % (uint32_t)c.nb[1]);
+        b[2] = (int)(blk / ((uint32_t)c.nb[0] * (uint32_t)c.nb[1]));
+    } else {
+        b[1] = (int)(blk / (uint32_t)c.nb[0]);
+    }
+}
+
+template <int D, int ORDER, typename R>
+__global__ void __launch_bounds__(TPB) k_keys(PState<R> st, DevCfg<R> c, uint32_t* __restrict__ keys, uint32_t* err)
+{
+    const int k = blockIdx.x * TPB + threadIdx.x;
+    if (k >= c.n) return;
+    Particle<D, R> p;
+    load_xF<D, R>(st, k, p);
+    keys[k] = key_of<D, ORDER, R>(p.o, p.cell, c, err);
+}
+
+// ---------------------------------------------------------------- P2G (Sec. 3.2, 3.3)
+// One CTA walks tiles (a run of sorted particles of one node block).  Each particle's
+// contributions to its (ORDER+1)^D stencil nodes are first summed over the run of lanes
+// that share the same stencil base node (a segmented shuffle reduction; the sort makes
+// such lanes adjacent), then the run's head adds them into a shared-memory tile of
+// (4+ORDER)^D nodes; the tile is added to the global grid once.
+//   mass:     w m_p
+//   momentum: w m_p (v_p + B_p D_p^{-1} (x_i - x_p)) - dt V_p P F^T grad w
+template <int D, int ORDER, typename R>
+__global__ void __launch_bounds__(TPB) k_p2g(PState<R> st, const uint32_t* __restrict__ perm,
+                                             const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ tiles,
+                                             const uint32_t* __restrict__ ntiles_p, R* __restrict__ acc,
+                                             uint32_t* __restrict__ flags, DevCfg<R> c, uint32_t* err,
+                                             uint32_t* fallbacks)
+{
+    constexpr int K = ORDER + 1;
+    constexpr int TE = 4 + ORDER;
+    constexpr int TN = (D == 3) ? TE * TE * TE : TE * TE;
+    constexpr int NS = (D == 3) ? K * K * K : K * K;
+    constexpr int NV = D + 1;   // momentum lanes + mass
+    __shared__ R sm[NV][TN];
+    const int lane = threadIdx.x & 31;
+    const int ntiles = (int)*ntiles_p;
+    const R dt_dx = c.dt * c.inv_dx;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        for (int i = threadIdx.x; i < NV * TN; i += TPB) (&sm[0][0])[i] = R(0);
+        const uint32_t start = tiles[t], end = tiles[t + 1];
+        const uint32_t blk = skeys[start] >> (2 * D);
+        int bo[3] = {0, 0, 0};
+        block_coords<D, R>(blk, c, bo);
+#pragma unroll
+        for (int a = 0; a < D; ++a) bo[a] *= 4;
+        __syncthreads();
+        for (uint32_t k0 = start; k0 < end; k0 += TPB) {
+            const uint32_t k = k0 + threadIdx.x;
+            bool ok = k < end;
+            uint32_t key = ok ? skeys[k] : FULLMASK;
+            R w[D][K], dw[D][K], fx[D];
+            int lb[D];
+            R mv[D], mC[D * D], T[D * D];
+            const R m = c.mass;
+            if (ok) {
+                Particle<D, R> p;
+                const uint32_t q = perm[k];
+                load_xF<D, R>(st, q, p);
+                load_vB<D, R>(st, q, p);
+                int base[D];
+                if (!particle_stencil<D, ORDER, R>(p.o, p.cell, c, base, fx, w, dw)) set_err(err, APIC_ERRBIT_RANGE);
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    lb[a] = base[a] - bo[a];
+                    if (lb[a] < 0 || lb[a] > 3) ok = false;
+                }
+                if (!ok) set_err(err, APIC_ERRBIT_RANGE);
+#pragma unroll
+                for (int a = 0; a < D; ++a) mv[a] = m * p.v[a];
+                const R s = (c.transfer == 0) ? m * c.inv_kdx : R(0);
+#pragma unroll
+                for (int i = 0; i < D * D; ++i) mC[i] = s * p.B[i];
+                if (c.model == 1) {
+                    R tau[D * D];
+                    stress_tau<D, R>(p.F, c.mu, c.lam, c.vol, tau, fallbacks);
+#pragma unroll
+                    for (int i = 0; i < D * D; ++i) T[i] = dt_dx * tau[i];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < D * D; ++i) T[i] = R(0);
+                }
+            }
+            if (!ok) {
+                key = FULLMASK;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    lb[a] = 0;
+                    fx[a] = R(0);
+                    mv[a] = R(0);
+#pragma unroll
+                    for (int j = 0; j < K; ++j) { w[a][j] = R(0); dw[a][j] = R(0); }
+                }
+#pragma unroll
+                for (int i = 0; i < D * D; ++i) { mC[i] = R(0); T[i] = R(0); }
+            }
+            // segments of lanes with equal keys (= equal stencil base node)
+            const uint32_t prev = __shfl_up_sync(FULLMASK, key, 1);
+            const bool head = (lane == 0) || (key != prev);
+            const uint32_t H = __ballot_sync(FULLMASK, head);
+            const uint32_t after = (lane == 31) ? 0u : (H & (FULLMASK << (lane + 1)));
+            const int seg_end = after ? (__ffs(after) - 1) : 32;
+            int lbase = lb[0] + TE * lb[1];
+            if (D == 3) lbase += TE * TE * lb[2];
+#pragma unroll
+            for (int j = 0; j < NS; ++j) {
+                const int ia = j % K, ib = (j / K) % K, ic = j / (K * K);
+                R wv, g[D], r[D];
+                if (D == 3) {
+                    const R wab = w[0][ia] * w[1][ib];
+                    wv = wab * w[2][ic];
+                    g[0] = dw[0][ia] * w[1][ib] * w[2][ic];
+                    g[1] = w[0][ia] * dw[1][ib] * w[2][ic];
+                    g[2] = wab * dw[2][ic];
+                    r[2] = R(ic) - fx[2];
+                } else {
+                    wv = w[0][ia] * w[1][ib];
+                    g[0] = dw[0][ia] * w[1][ib];
+                    g[1] = w[0][ia] * dw[1][ib];
+                }
+                r[0] = R(ia) - fx[0];
+                r[1] = R(ib) - fx[1];
+                R val[NV];
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    R q = mv[a];
+                    R f = R(0);
+#pragma unroll
+                    for (int b = 0; b < D; ++b) {
+                        q += mC[a * D + b] * r[b];
+                        f += T[a * D + b] * g[b];
+                    }
+                    val[a] = wv * q - f;
+                }
+                val[D] = wv * m;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        const R other = __shfl_down_sync(FULLMASK, val[v], o);
+                        if (lane + o < seg_end) val[v] += other;
+                    }
+                }
+                if (head && ok) {
+                    const int li = lbase + ia + TE * ib + (D == 3 ? TE * TE * ic : 0);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) atomicAdd(&sm[v][li], val[v]);
+                }
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < TN; i += TPB) {
+            const R mm = sm[D][i];
+            if (mm == R(0)) continue;
+            int g[3];
+            g[0] = bo[0] + i % TE;
+            g[1] = bo[1] + (i / TE) % TE;
+            if (D == 3) g[2] = bo[2] + i / (TE * TE);
+            const uint32_t ni = node_index<D>(g, c.nb);
+            R* dst = acc + 4 * (size_t)ni;
+#pragma unroll
+            for (int a = 0; a < D; ++a) atomicAdd(dst + a, sm[a][i]);
+            atomicAdd(dst + 3, mm);
+        }
+        if (threadIdx.x < (1 << D)) {
+            int bb[3];
+            block_coords<D, R>(blk, c, bb);
+            bool in = true;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                bb[a] += (threadIdx.x >> a) & 1;
+                if (bb[a] >= c.nb[a]) in = false;
+            }
+            if (in) {
+                const uint32_t b2 = (D == 3) ? ((uint32_t)bb[2] * c.nb[1] + bb[1]) * c.nb[0] + bb[0]
+                                             : (uint32_t)bb[1] * c.nb[0] + bb[0];
+                flags[b2] = 1u;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- grid update (Sec. 3.3)
+// One warp per active node block: v~ = ((m v) + dt f) / m + dt g, sticky walls, v~ = 0 where
+// m = 0; writes (v~, m) to the velocity grid and clears the accumulation grid and flag.
+template <int D, typename R>
+__global__ void __launch_bounds__(TPB) k_grid_update(R* __restrict__ acc, R* __restrict__ vel,
+                                                     uint32_t* __restrict__ flags, DevCfg<R> c)
+{
+    constexpr int BN = (D == 3) ? 64 : 16;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * TPB + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * TPB) >> 5;
+    for (int b = gw; b < c.nblocks; b += nw) {
+        if (flags[b] == 0u) continue;
+        int bc[3] = {0, 0, 0};
+        block_coords<D, R>((uint32_t)b, c, bc);
+        for (int i = lane; i < BN; i += 32) {
+            const size_t node = (size_t)b * BN + i;
+            V4<R> a = *reinterpret_cast<const V4<R>*>(acc + 4 * node);
+            int g[3];
+            g[0] = bc[0] * 4 + (i & 3);
+            g[1] = bc[1] * 4 + ((i >> 2) & 3);
+            g[2] = (D == 3) ? bc[2] * 4 + (i >> 4) : 0;
+            const R m = a.w;
+            R v[3] = {R(0), R(0), R(0)};
+            if (m > R(0)) {
+                const R inv = R(1) / m;
+                v[0] = a.x * inv + c.dt * c.gravity[0];
+                v[1] = a.y * inv + c.dt * c.gravity[1];
+                if (D == 3) v[2] = a.z * inv + c.dt * c.gravity[2];
+                if (c.boundary == 1) {
+                    bool wall = false;
+#pragma unroll
+                    for (int d = 0; d < D; ++d)
+                        if (g[d] < c.wall || g[d] >= c.res[d] - c.wall) wall = true;
+                    if (wall) v[0] = v[1] = v[2] = R(0);
+                }
+            }
+            *reinterpret_cast<V4<R>*>(vel + 4 * node) = V4<R>{v[0], v[1], v[2], m};
+            *reinterpret_cast<V4<R>*>(acc + 4 * node) = V4<R>{R(0), R(0), R(0), R(0)};
+        }
+        __syncwarp();
+        if (lane == 0) flags[b] = 0u;
+    }
+}
+
+// ---------------------------------------------------------------- mbarrier + bulk copy
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+// bounded wait: gives up after `limit` polls (each poll may suspend the thread briefly)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned limit)
+{
+    for (unsigned i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// ---------------------------------------------------------------- G2P (Sec. 3.4, 5.7)
+// Per tile, the 2^D node blocks its particles' stencils can reach are brought into shared
+// memory with bulk asynchronous copies completing on an mbarrier; each particle then
+// gathers v_p = sum w v~, B_p = sum w v~ (x_i - x_p)^T, grad v = sum v~ grad w^T, updates
+// F_p <- (I + dt grad v) F_p and x_p <- x_p + dt v_p, and is written at its sorted slot
+// together with its next cell key.
+template <int D, int ORDER, typename R>
+__global__ void __launch_bounds__(TPB) k_g2p(PState<R> in, PState<R> out, const uint32_t* __restrict__ perm,
+                                             const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ tiles,
+                                             const uint32_t* __restrict__ ntiles_p, const R* __restrict__ vel,
+                                             uint32_t* __restrict__ knext, DevCfg<R> c, uint32_t* err)
+{
+    constexpr int K = ORDER + 1;
+    constexpr int BN = (D == 3) ? 64 : 16;
+    constexpr int NB = 1 << D;
+    constexpr int NS = (D == 3) ? K * K * K : K * K;
+    __shared__ __align__(128) R sv[NB][BN][4];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+    unsigned phase = 0;
+    const int ntiles = (int)*ntiles_p;
+    const R dt_dx = c.dt * c.inv_dx;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint32_t start = tiles[t], end = tiles[t + 1];
+        const uint32_t blk = skeys[start] >> (2 * D);
+        int bc[3] = {0, 0, 0};
+        block_coords<D, R>(blk, c, bc);
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            unsigned nblk = 0;
+            bool inb[NB];
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                inb[q] = true;
+#pragma unroll
+                for (int a = 0; a < D; ++a)
+                    if (bc[a] + ((q >> a) & 1) >= c.nb[a]) inb[q] = false;
+                nblk += inb[q] ? 1u : 0u;
+            }
+            const unsigned bytes = (unsigned)(BN * 4 * sizeof(R));
+            mbar_expect_tx(&mbar, nblk * bytes);
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                if (!inb[q]) continue;
+                int bb[3] = {bc[0] + (q & 1), bc[1] + ((q >> 1) & 1), (D == 3) ? bc[2] + ((q >> 2) & 1) : 0};
+                const uint32_t b2 = (D == 3) ? ((uint32_t)bb[2] * c.nb[1] + bb[1]) * c.nb[0] + bb[0]
+                                             : (uint32_t)bb[1] * c.nb[0] + bb[0];
+                bulk_copy_g2s(&sv[q][0][0], vel + (size_t)b2 * BN * 4, bytes, &mbar);
+            }
+            bool ok = mbar_wait_bounded(&mbar, phase, 1u << 22);
+            if (!ok) {
+                set_err(err, APIC_ERRBIT_TIMEOUT);
+                mbar_wait_bounded(&mbar, phase, 1u << 22);
+            }
+            s_ok = ok ? 1 : 0;
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        phase ^= 1u;
+        for (uint32_t k0 = start; k0 < end; k0 += TPB) {
+            const uint32_t k = k0 + threadIdx.x;
+            if (k >= end) continue;
+            Particle<D, R> p;
+            const uint32_t q = perm[k];
+            load_xF<D, R>(in, q, p);
+            int base[D], lb[D];
+            R w[D][K], dw[D][K], fx[D];
+            bool ok = particle_stencil<D, ORDER, R>(p.o, p.cell, c, base, fx, w, dw);
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                lb[a] = base[a] - 4 * bc[a];
+                if (lb[a] < 0 || lb[a] > 3) { ok = false; lb[a] = 0; }
+            }
+            if (!ok) set_err(err, APIC_ERRBIT_RANGE);
+            R vp[D], Bh[D * D], G[D * D];
+#pragma unroll
+            for (int a = 0; a < D; ++a) vp[a] = R(0);
+#pragma unroll
+            for (int i = 0; i < D * D; ++i) { Bh[i] = R(0); G[i] = R(0); }
+#pragma unroll
+            for (int j = 0; j < NS; ++j) {
+                const int ia = j % K, ib = (j / K) % K, ic = j / (K * K);
+                const int L0 = lb[0] + ia, L1 = lb[1] + ib, L2 = (D == 3) ? lb[2] + ic : 0;
+                const int qb = (L0 >> 2) | ((L1 >> 2) << 1) | ((L2 >> 2) << 2);
+                const int ni = (L0 & 3) | ((L1 & 3) << 2) | ((L2 & 3) << 4);
+                const R* nv = &sv[qb][ni][0];
+                R vt[D];
+#pragma unroll
+                for (int a = 0; a < D; ++a) vt[a] = nv[a];
+                R wv, g[D], r[D];
+                if (D == 3) {
+                    const R wab = w[0][ia] * w[1][ib];
+                    wv = wab * w[2][ic];
+                    g[0] = dw[0][ia] * w[1][ib] * w[2][ic];
+                    g[1] = w[0][ia] * dw[1][ib] * w[2][ic];
+                    g[2] = wab * dw[2][ic];
+                    r[2] = R(ic) - fx[2];
+                } else {
+                    wv = w[0][ia] * w[1][ib];
+                    g[0] = dw[0][ia] * w[1][ib];
+                    g[1] = w[0][ia] * dw[1][ib];
+                }
+                r[0] = R(ia) - fx[0];
+                r[1] = R(ib) - fx[1];
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const R wva = wv * vt[a];
+                    vp[a] += wva;
+#pragma unroll
+                    for (int b = 0; b < D; ++b) {
+                        Bh[a * D + b] += wva * r[b];
+                        G[a * D + b] += vt[a] * g[b];
+                    }
+                }
+            }
+            // F <- (I + dt grad v) F with grad v = G / dx
+            R Fn[D * D];
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int b = 0; b < D; ++b) {
+                    R s = p.F[a * D + b];
+#pragma unroll
+                    for (int kk = 0; kk < D; ++kk) s += dt_dx * G[a * D + kk] * p.F[kk * D + b];
+                    Fn[a * D + b] = s;
+                }
+#pragma unroll
+            for (int i = 0; i < D * D; ++i) {
+                p.F[i] = Fn[i];
+                p.B[i] = (c.transfer == 0) ? c.dx * Bh[i] : R(0);
+            }
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                p.v[a] = vp[a];
+                R o = p.o[a] + dt_dx * vp[a];
+                const R fl = floor(o);
+                o -= fl;
+                int cl = p.cell[a] + (int)fl;
+                if (o >= R(1)) { o -= R(1); cl += 1; }
+                if (cl < 0) { cl = 0; o = R(0); set_err(err, APIC_ERRBIT_RANGE); }
+                if (cl > c.res[a] - 1) { cl = c.res[a] - 1; o = R(0); set_err(err, APIC_ERRBIT_RANGE); }
+                p.o[a] = o;
+                p.cell[a] = cl;
+            }
+            store_all<D, R>(out, k, p);
+            knext[k] = key_of<D, ORDER, R>(p.o, p.cell, c, err);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- momentum (FP64)
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULLMASK, v, o);
+    return v;
+}
+
+// writes 6 partial sums (p, l) of this CTA to part[blockIdx.x*6 ...] in a fixed order
+__device__ __forceinline__ void block_sum6(double* a, double* part)
+{
+    __shared__ double s[6][TPB / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const double v = warp_sum_d(a[i]);
+        if (lane == 0) s[i][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double t = 0.0;
+        for (int ww = 0; ww < TPB / 32; ++ww) t += s[threadIdx.x][ww];
+        part[(size_t)blockIdx.x * 6 + threadIdx.x] = t;
+    }
+}
+
+template <int D, typename R>
+__global__ void __launch_bounds__(TPB) k_mom_particles(PState<R> st, DevCfg<R> c, double mass, double dx,
+                                                       double o0, double o1, double o2, double* part)
+{
+    double a[6] = {0, 0, 0, 0, 0, 0};
+    const double org[3] = {o0, o1, o2};
+    for (int k = blockIdx.x * TPB + threadIdx.x; k < c.n; k += gridDim.x * TPB) {
+        Particle<D, R> p;
+        load_xF<D, R>(st, k, p);
+        load_vB<D, R>(st, k, p);
+        double x[3] = {0, 0, 0}, v[3] = {0, 0, 0};
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            x[d] = org[d] + ((double)p.cell[d] + (double)p.o[d]) * dx;
+            v[d] = mass * (double)p.v[d];
+            a[d] += v[d];
+        }
+        if (D == 3) {
+            a[3] += x[1] * v[2] - x[2] * v[1];
+            a[4] += x[2] * v[0] - x[0] * v[2];
+            a[5] += x[0] * v[1] - x[1] * v[0];
+            if (c.transfer == 0) {
+                a[3] += mass * ((double)p.B[7] - (double)p.B[5]);
+                a[4] += mass * ((double)p.B[2] - (double)p.B[6]);
+                a[5] += mass * ((double)p.B[3] - (double)p.B[1]);
+            }
+        } else {
+            a[3] += x[0] * v[1] - x[1] * v[0];
+            if (c.transfer == 0) a[3] += mass * ((double)p.B[2] - (double)p.B[1]);
+        }
+    }
+    block_sum6(a, part);
+}
+
+// which = 0: accumulation grid (lanes 0..D-1 = momentum); 1: velocity grid (m v~)
+template <int D, typename R>
+__global__ void __launch_bounds__(TPB) k_mom_grid(const R* __restrict__ grid, int which, DevCfg<R> c, double dx,
+                                                  double o0, double o1, double o2, double* part)
+{
+    constexpr int BN = (D == 3) ? 64 : 16;
+    double a[6] = {0, 0, 0, 0, 0, 0};
+    const double org[3] = {o0, o1, o2};
+    const int64_t total = (int64_t)c.nblocks * BN;
+    for (int64_t node = (int64_t)blockIdx.x * TPB + threadIdx.x; node < total; node += (int64_t)gridDim.x * TPB) {
+        const int b = (int)(node / BN), i = (int)(node % BN);
+        int bc[3] = {0, 0, 0};
+        block_coords<D, R>((uint32_t)b, c, bc);
+        int g[3] = {bc[0] * 4 + (i & 3), bc[1] * 4 + ((i >> 2) & 3), (D == 3) ? bc[2] * 4 + (i >> 4) : 0};
+        const R* q = grid + 4 * node;
+        const double m = (double)q[3];
+        if (m == 0.0) continue;
+        double x[3] = {0, 0, 0}, mv[3] = {0, 0, 0};
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            x[d] = org[d] + (double)g[d] * dx;
+            mv[d] = which == 0 ? (double)q[d] : m * (double)q[d];
+            a[d] += mv[d];
+        }
+        if (D == 3) {
+            a[3] += x[1] * mv[2] - x[2] * mv[1];
+            a[4] += x[2] * mv[0] - x[0] * mv[2];
+            a[5] += x[0] * mv[1] - x[1] * mv[0];
+        } else {
+            a[3] += x[0] * mv[1] - x[1] * mv[0];
+        }
+    }
+    block_sum6(a, part);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(TPB) k_mom_final(const double* __restrict__ part, int np, double* __restrict__ out)
+{
+    __shared__ double s[6][TPB];
+    for (int i = 0; i < 6; ++i) {
+        double t = 0.0;
+        for (int b = threadIdx.x; b < np; b += TPB) t += part[(size_t)b * 6 + i];
+        s[i][threadIdx.x] = t;
+    }
+    __syncthreads();
+    for (int st = TPB / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st)
+            for (int i = 0; i < 6; ++i) s[i][threadIdx.x] += s[i][threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) out[threadIdx.x] = s[threadIdx.x][0];
+}
+
+// ---------------------------------------------------------------- upload / download
+template <int D, typename R>
+__global__ void __launch_bounds__(TPB) k_upload(PState<R> st, DevCfg<R> c, double dx, double o0, double o1, double o2,
+                                                const double* __restrict__ x, const double* __restrict__ v,
+                                                const double* __restrict__ B, const double* __restrict__ F,
+                                                uint32_t* err)
+{
+    const int k = blockIdx.x * TPB + threadIdx.x;
+    if (k >= c.n) return;
+    const double org[3] = {o0, o1, o2};
+    Particle<D, R> p;
+    p.id = (uint32_t)k;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const double u = (x[(size_t)k * D + a] - org[a]) / dx;
+        double cl = floor(u);
+        R o = (R)(u - cl);
+        if (o >= R(1)) { o = R(0); cl += 1.0; }
+        int ci = (int)cl;
+        if (!(cl >= 0.0) || cl > (double)(c.res[a] - 1)) {
+            set_err(err, APIC_ERRBIT_RANGE);
+            ci = cl < 0.0 ? 0 : c.res[a] - 1;
+            o = R(0);
+        }
+        p.o[a] = o;
+        p.cell[a] = ci;
+        p.v[a] = v ? (R)v[(size_t)k * D + a] : R(0);
+    }
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) {
+        p.B[i] = B ? (R)B[(size_t)k * D * D + i] : R(0);
+        p.F[i] = F ? (R)F[(size_t)k * D * D + i] : ((i % (D + 1)) == 0 ? R(1) : R(0));
+    }
+    store_all<D, R>(st, k, p);
+}
+
+template <int D, typename R>
+__global__ void __launch_bounds__(TPB) k_download(PState<R> st, DevCfg<R> c, double dx, double o0, double o1, double o2,
+                                                  double* __restrict__ x, double* __restrict__ v, double* __restrict__ B,
+                                                  double* __restrict__ F, int32_t* __restrict__ cell,
+                                                  double* __restrict__ off)
+{
+    const int k = blockIdx.x * TPB + threadIdx.x;
+    if (k >= c.n) return;
+    const double org[3] = {o0, o1, o2};
+    Particle<D, R> p;
+    load_xF<D, R>(st, k, p);
+    load_vB<D, R>(st, k, p);
+    const size_t id = p.id;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        if (x) x[id * D + a] = org[a] + ((double)p.cell[a] + (double)p.o[a]) * dx;
+        if (v) v[id * D + a] = (double)p.v[a];
+        if (cell) cell[id * D + a] = p.cell[a];
+        if (off) off[id * D + a] = (double)p.o[a];
+    }
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) {
+        if (B) B[id * D * D + i] = (double)p.B[i];
+        if (F) F[id * D * D + i] = (double)p.F[i];
+    }
+}
+
+template <int D, typename R>
+__global__ void __launch_bounds__(TPB) k_grid_dense(const R* __restrict__ grid, int which, DevCfg<R> c,
+                                                    double* __restrict__ m, double* __restrict__ mv)
+{
+    const int64_t nn = (int64_t)c.res[0] * c.res[1] * (D == 3 ? c.res[2] : 1);
+    for (int64_t idx = (int64_t)blockIdx.x * TPB + threadIdx.x; idx < nn; idx += (int64_t)gridDim.x * TPB) {
+        int g[3];
+        int64_t r = idx;
+        g[0] = (int)(r % c.res[0]); r /= c.res[0];
+        g[1] = (int)(r % c.res[1]); r /= c.res[1];
+        g[2] = (D == 3) ? (int)r : 0;
+        const uint32_t ni = node_index<D>(g, c.nb);
+        const R* q = grid + 4 * (size_t)ni;
+        m[idx] = (double)q[3];
+        for (int a = 0; a < D; ++a) mv[idx * D + a] = (double)q[a];
+        (void)which;
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+inline unsigned blocks_for(int64_t n) { return (unsigned)((n + TPB - 1) / TPB); }
+
+#define APIC_DISPATCH(c, KERNEL_CALL)                                                  \
+    do {                                                                               \
+        if ((c).dim == 3 && (c).order == 2) { constexpr int D = 3, O = 2; KERNEL_CALL; } \
+        else if ((c).dim == 3 && (c).order == 3) { constexpr int D = 3, O = 3; KERNEL_CALL; } \
+        else if ((c).dim == 2 && (c).order == 2) { constexpr int D = 2, O = 2; KERNEL_CALL; } \
+        else { constexpr int D = 2, O = 3; KERNEL_CALL; }                              \
+    } while (0)
+
+template <typename R> struct Impl {
+    static cudaError_t keys(const HostCfg& h, const Buffers& b, int cur, int64_t n, cudaStream_t s)
+    {
+        if (n == 0) return cudaSuccess;
+        DevCfg<R> c = HostToDev<R>::make(h, n);
+        PState<R> st = state_of<R>(b, cur);
+        APIC_DISPATCH(h, (k_keys<D, O, R><<<blocks_for(n), TPB, 0, s>>>(st, c, b.knext, b.err)));
+        return cudaGetLastError();
+    }
+    static cudaError_t p2g(const HostCfg& h, const Buffers& b, int cur, const uint32_t* sk, const uint32_t* perm,
+                           int64_t n, const Launch& L, cudaStream_t s)
+    {
+        if (n == 0) return cudaSuccess;
+        DevCfg<R> c = HostToDev<R>::make(h, n);
+        PState<R> st = state_of<R>(b, cur);
+        APIC_DISPATCH(h, (k_p2g<D, O, R><<<L.p2g_grid, TPB, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, (R*)b.acc,
+                                                                      b.flags, c, b.err, b.fallbacks)));
+        return cudaGetLastError();
+    }
+    static cudaError_t grid_update(const HostCfg& h, const Buffers& b, const Launch& L, cudaStream_t s)
+    {
+        DevCfg<R> c = HostToDev<R>::make(h, 0);
+        const int grid = L.sms * 8;
+        if (h.dim == 3) k_grid_update<3, R><<<grid, TPB, 0, s>>>((R*)b.acc, (R*)b.vel, b.flags, c);
+        else k_grid_update<2, R><<<grid, TPB, 0, s>>>((R*)b.acc, (R*)b.vel, b.flags, c);
+        return cudaGetLastError();
+    }
+    static cudaError_t g2p(const HostCfg& h, const Buffers& b, int cur, const uint32_t* sk, const uint32_t* perm,
+                           int64_t n, const Launch& L, cudaStream_t s)
+    {
+        if (n == 0) return cudaSuccess;
+        DevCfg<R> c = HostToDev<R>::make(h, n);
+        PState<R> in = state_of<R>(b, cur), out = state_of<R>(b, cur ^ 1);
+        APIC_DISPATCH(h, (k_g2p<D, O, R><<<L.g2p_grid, TPB, 0, s>>>(in, out, perm, sk, b.tiles, b.ntiles,
+                                                                      (const R*)b.vel, b.knext, c, b.err)));
+        return cudaGetLastError();
+    }
+    static cudaError_t upload(const HostCfg& h, const Buffers& b, int cur, int64_t n, const double* x,
+                              const double* v, const double* B, const double* F, cudaStream_t s)
+    {
+        if (n == 0) return cudaSuccess;
+        DevCfg<R> c = HostToDev<R>::make(h, n);
+        PState<R> st = state_of<R>(b, cur);
+        if (h.dim == 3)
+            k_upload<3, R><<<blocks_for(n), TPB, 0, s>>>(st, c, h.dx, h.origin[0], h.origin[1], h.origin[2], x, v, B, F, b.err);
+        else
+            k_upload<2, R><<<blocks_for(n), TPB, 0, s>>>(st, c, h.dx, h.origin[0], h.origin[1], h.origin[2], x, v, B, F, b.err);
+        return cudaGetLastError();
+    }
+    static cudaError_t download(const HostCfg& h, const Buffers& b, int cur, int64_t n, double* x, double* v,
+                                double* B, double* F, int32_t* cell, double* off, cudaStream_t s)
+    {
+        if (n == 0) return cudaSuccess;
+        DevCfg<R> c = HostToDev<R>::make(h, n);
+        PState<R> st = state_of<R>(b, cur);
+        if (h.dim == 3)
+            k_download<3, R><<<blocks_for(n), TPB, 0, s>>>(st, c, h.dx, h.origin[0], h.origin[1], h.origin[2], x, v, B, F, cell, off);
+        else
+            k_download<2, R><<<blocks_for(n), TPB, 0, s>>>(st, c, h.dx, h.origin[0], h.origin[1], h.origin[2], x, v, B, F, cell, off);
+        return cudaGetLastError();
+    }
+    static cudaError_t momentum(const HostCfg& h, const Buffers& b, int cur, int64_t n, int where, int grid_phase,
+                                const Launch& L, cudaStream_t s)
+    {
+        const int nparts = L.mom_parts;
+        DevCfg<R> c = HostToDev<R>::make(h, n);
+        if (where == 0) {
+            PState<R> st = state_of<R>(b, cur);
+            if (h.dim == 3)
+                k_mom_particles<3, R><<<nparts, TPB, 0, s>>>(st, c, h.mass, h.dx, h.origin[0], h.origin[1], h.origin[2], b.mom_part);
+            else
+                k_mom_particles<2, R><<<nparts, TPB, 0, s>>>(st, c, h.mass, h.dx, h.origin[0], h.origin[1], h.origin[2], b.mom_part);
+        } else {
+            const R* g = (const R*)(grid_phase == 0 ? b.acc : b.vel);
+            if (h.dim == 3)
+                k_mom_grid<3, R><<<nparts, TPB, 0, s>>>(g, grid_phase, c, h.dx, h.origin[0], h.origin[1], h.origin[2], b.mom_part);
+            else
+                k_mom_grid<2, R><<<nparts, TPB, 0, s>>>(g, grid_phase, c, h.dx, h.origin[0], h.origin[1], h.origin[2], b.mom_part);
+        }
+        k_mom_final<R><<<1, TPB, 0, s>>>(b.mom_part, nparts, b.mom_out);
+        return cudaGetLastError();
+    }
+    static cudaError_t grid_dense(const HostCfg& h, const Buffers& b, int which, double* m, double* mv, cudaStream_t s)
+    {
+        DevCfg<R> c = HostToDev<R>::make(h, 0);
+        const R* g = (const R*)(which == 0 ? b.acc : b.vel);
+        if (h.dim == 3) k_grid_dense<3, R><<<1024, TPB, 0, s>>>(g, which, c, m, mv);
+        else k_grid_dense<2, R><<<1024, TPB, 0, s>>>(g, which, c, m, mv);
+        return cudaGetLastError();
+    }
+    static cudaError_t occupancy(const HostCfg& h, int* p2g_per_sm, int* g2p_per_sm)
+    {
+        cudaError_t e = cudaSuccess;
+        APIC_DISPATCH(h, {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g<D, O, R>, TPB, 0);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(g2p_per_sm, k_g2p<D, O, R>, TPB, 0);
+        });
+        return e;
+    }
+};
+
+#define APIC_DEFINE_PRECISION(R, SFX)                                                                         \
+    cudaError_t keys_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, cudaStream_t s)             \
+    {                                                                                                           \
+        return Impl<R>::keys(c, b, cur, n, s);                                                                  \
+    }                                                                                                           \
+    cudaError_t p2g_##SFX(const HostCfg& c, const Buffers& b, int cur, const uint32_t* skeys,                  \
+                          const uint32_t* perm, int64_t n, const Launch& L, cudaStream_t s)                     \
+    {                                                                                                           \
+        return Impl<R>::p2g(c, b, cur, skeys, perm, n, L, s);                                                   \
+    }                                                                                                           \
+    cudaError_t grid_update_##SFX(const HostCfg& c, const Buffers& b, const Launch& L, cudaStream_t s)         \
+    {                                                                                                           \
+        return Impl<R>::grid_update(c, b, L, s);                                                                \
+    }                                                                                                           \
+    cudaError_t g2p_##SFX(const HostCfg& c, const Buffers& b, int cur, const uint32_t* skeys,                  \
+                          const uint32_t* perm, int64_t n, const Launch& L, cudaStream_t s)                     \
+    {                                                                                                           \
+        return Impl<R>::g2p(c, b, cur, skeys, perm, n, L, s);                                                   \
+    }                                                                                                           \
+    cudaError_t upload_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const double* x,          \
+                             const double* v, const double* B, const double* F, cudaStream_t s)                 \
+    {                                                                                                           \
+        return Impl<R>::upload(c, b, cur, n, x, v, B, F, s);                                                    \
+    }                                                                                                           \
+    cudaError_t download_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, double* x, double* v,   \
+                               double* B, double* F, int32_t* cell, double* off, cudaStream_t s)                \
+    {                                                                                                           \
+        return Impl<R>::download(c, b, cur, n, x, v, B, F, cell, off, s);                                       \
+    }                                                                                                           \
+    cudaError_t momentum_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, int where,              \
+                               int grid_phase, const Launch& L, cudaStream_t s)                                 \
+    {                                                                                                           \
+        return Impl<R>::momentum(c, b, cur, n, where, grid_phase, L, s);                                        \
+    }                                                                                                           \
+    cudaError_t grid_dense_##SFX(const HostCfg& c, const Buffers& b, int which, double* m, double* mv,         \
+                                 cudaStream_t s)                                                                \
+    {                                                                                                           \
+        return Impl<R>::grid_dense(c, b, which, m, mv, s);                                                      \
+    }                                                                                                           \
+    cudaError_t occupancy_##SFX(const HostCfg& c, int* p2g_per_sm, int* g2p_per_sm)                            \
+    {                                                                                                           \
+        return Impl<R>::occupancy(c, p2g_per_sm, g2p_per_sm);                                                   \
+    }
+
+}  // namespace apic

@@ -1,0 +1,6 @@
+// FP64 instantiation of the per-step kernels (particle and grid state in double).
+#include "apic_transfer.cuh"
+
+namespace apic {
+APIC_DEFINE_PRECISION(double, f64)
+}  // namespace apic

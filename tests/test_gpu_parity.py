@@ -1,0 +1,269 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, one transfer at a time, the
+oracle always fed the GPU's exact input state (FP32 values widened to FP64).
+
+Bars: cell keys, sort permutation and grid occupancy bit-exact; grid momentum, grid
+velocity, v_p, B_p, F_p and the displacement within 1e-5 normwise relative
+(||gpu - oracle||_inf / ||oracle||_inf) in FP32 and 1e-11 in FP64."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import configs, kappa, occupancy_rule, relerr, state_for
+from paper_1603_06188_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+TOL = {32: 1e-5, 64: 1e-11}
+
+
+@pytest.fixture(scope="module")
+def apic():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1603_06188_gb300 import apic as mod
+
+    mod.load(build_if_missing=True)
+    return mod
+
+
+def cube_scene(dim, res, ppc, seed=0, side=0.5):
+    if dim == 3:
+        return scenes.falling_cube_3d(res=res, side=side, ppc=ppc, seed=seed, omega=(0.5, -1.0, 2.0), v0=(0.3, 0.1, -0.2))
+    return scenes.rotating_disk_2d(res=res, radius=side / 2, ppc=ppc, seed=seed, omega=2.0)
+
+
+CASES = [
+    # dim, order, precision, res, ppc
+    (3, 2, 32, 32, 8),
+    (3, 3, 32, 32, 8),
+    (2, 2, 32, 64, 4),
+    (2, 3, 32, 64, 4),
+    (3, 2, 64, 24, 8),
+    (3, 3, 64, 24, 8),
+    (2, 2, 64, 64, 4),
+    (2, 3, 64, 64, 4),
+]
+
+
+def _ids(c):
+    return f"d{c[0]}_o{c[1]}_fp{c[2]}_r{c[3]}"
+
+
+def run_one_step(apic, dim, order, prec, res, ppc, model="fcr", transfer="apic", dt=2e-3, gravity=None,
+                 boundary="none", wall=0, tile=0, seed=0):
+    sc = cube_scene(dim, res, ppc, seed=seed)
+    x, v, B, F = state_for(sc, order, seed=seed)
+    g = gravity if gravity is not None else (0.0,) * dim
+    gc, oc, m, vol = configs(dim, order, (res,) * dim, sc.dx, precision=prec, transfer=transfer, dt=dt,
+                             gravity=g, boundary=boundary, wall=wall, model=model, tile=tile)
+    sim = apic.Sim(gc, len(x) + 7)
+    sim.upload(x, v, B, F)
+    x0, v0, B0, F0 = sim.download()          # the GPU's exact input state
+    cell0, off0 = sim.download_positions()
+    out = {"sim": sim, "sc": sc, "oc": oc, "m": m, "vol": vol, "in": (x0, v0, B0, F0), "cell": cell0, "off": off0}
+    sim.p2g()
+    out["keys"], out["perm"] = sim.keys()
+    out["occ"] = sim.occupancy()
+    out["grid_p2g"] = sim.grid("momentum")
+    out["mom_grid_p2g"] = sim.momentum("grid")
+    sim.grid_update()
+    out["grid_vel"] = sim.grid("velocity")
+    sim.g2p()
+    out["out"] = sim.download()
+    out["stats"] = sim.stats()
+    return out
+
+
+@pytest.mark.parametrize("case", CASES, ids=_ids)
+def test_keys_sort_occupancy_bit_exact(apic, case):
+    dim, order, prec, res, ppc = case
+    r = run_one_step(apic, dim, order, prec, res, ppc)
+    oc = r["oc"]
+    ref_keys = oracle.keys(oc, 4, r["cell"], r["off"])
+    ref_perm = oracle.stable_sort(ref_keys)
+    np.testing.assert_array_equal(r["keys"], ref_keys[ref_perm])
+    np.testing.assert_array_equal(r["perm"].astype(np.int64), ref_perm)
+    np.testing.assert_array_equal(r["occ"], occupancy_rule(ref_keys, dim, (res,) * dim))
+    assert r["stats"]["tiles"] >= 2
+
+
+@pytest.mark.parametrize("case", CASES, ids=_ids)
+def test_p2g_matches_oracle(apic, case):
+    dim, order, prec, res, ppc = case
+    r = run_one_step(apic, dim, order, prec, res, ppc)
+    x0, v0, B0, F0 = r["in"]
+    gm, gmv, gf, bad = oracle.p2g(r["oc"], x0, v0, B0, F0, r["m"], r["vol"])
+    assert bad == 0
+    m_gpu, p_gpu = r["grid_p2g"]
+    ref_p = gmv + r["oc"].dt * gf
+    assert relerr(m_gpu, gm) <= TOL[prec]
+    assert relerr(p_gpu, ref_p) <= TOL[prec]
+    # node occupancy by mass is the same set
+    np.testing.assert_array_equal(m_gpu > 0, gm > 0)
+
+
+@pytest.mark.parametrize("case", CASES, ids=_ids)
+def test_grid_update_matches_oracle(apic, case):
+    dim, order, prec, res, ppc = case
+    r = run_one_step(apic, dim, order, prec, res, ppc, gravity=(0.0, -9.8, 0.0)[:dim], boundary="sticky",
+                     wall=order + 1)
+    m_gpu, p_gpu = r["grid_p2g"]
+    _, vt_ref = oracle.grid_update(r["oc"], m_gpu, p_gpu, np.zeros_like(p_gpu))
+    m2, vt_gpu = r["grid_vel"]
+    np.testing.assert_array_equal(m2, m_gpu)
+    assert relerr(vt_gpu, vt_ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("case", CASES, ids=_ids)
+def test_g2p_matches_oracle(apic, case):
+    dim, order, prec, res, ppc = case
+    r = run_one_step(apic, dim, order, prec, res, ppc)
+    x0, v0, B0, F0 = r["in"]
+    _, vt = r["grid_vel"]
+    x1, v1, B1, F1, bad = oracle.g2p(r["oc"], x0, F0, vt, vt)
+    assert bad == 0
+    gx, gv, gB, gF = r["out"]
+    tol = TOL[prec]
+    assert relerr(gv, v1) <= tol
+    assert relerr(gB, B1) <= tol
+    assert relerr(gF, F1) <= tol
+    assert relerr(gF - F0, F1 - F0) <= 10 * tol
+    assert relerr(gx - x0, x1 - x0) <= tol
+
+
+@pytest.mark.parametrize("transfer", ["apic", "pic"])
+def test_transfer_modes_and_transfer_only(apic, transfer):
+    r = run_one_step(apic, 3, 2, 32, 32, 8, model="none", transfer=transfer)
+    x0, v0, B0, F0 = r["in"]
+    gm, gmv, gf, _ = oracle.p2g(r["oc"], x0, v0, B0, F0, r["m"], r["vol"])
+    m_gpu, p_gpu = r["grid_p2g"]
+    assert relerr(p_gpu, gmv) <= 1e-5
+    _, vt = r["grid_vel"]
+    x1, v1, B1, F1, _ = oracle.g2p(r["oc"], x0, F0, vt, vt)
+    gx, gv, gB, gF = r["out"]
+    assert relerr(gv, v1) <= 1e-5
+    if transfer == "pic":
+        assert np.all(gB == 0)
+    else:
+        assert relerr(gB, B1) <= 1e-5
+
+
+@pytest.mark.parametrize("tile", [256, 4096])
+def test_tile_sizes_agree(apic, tile):
+    r = run_one_step(apic, 3, 2, 32, 32, 8, tile=tile)
+    x0, v0, B0, F0 = r["in"]
+    gm, gmv, gf, _ = oracle.p2g(r["oc"], x0, v0, B0, F0, r["m"], r["vol"])
+    assert relerr(r["grid_p2g"][1], gmv + r["oc"].dt * gf) <= 1e-5
+
+
+def test_gpu_momentum_conservation_fp32(apic):
+    """Sec. 5.2 / 5.3 on the GPU: P2G and G2P keep p and l to FP32 rounding (forces on, no
+    gravity, no walls); the FP64 reductions see it."""
+    sc = scenes.falling_cube_3d(res=48, side=0.5, ppc=8, omega=(0.0, 0.0, 3.0), v0=(0.2, 0.0, 0.0), seed=3)
+    x, v, B, F = state_for(sc, 2, seed=3)
+    gc, oc, m, vol = configs(3, 2, (48,) * 3, sc.dx, dt=1e-3)
+    sim = apic.Sim(gc, len(x))
+    sim.upload(x, v, B, F)
+    p0, l0 = sim.momentum("particles")
+    sim.p2g()
+    pg, lg = sim.momentum("grid")
+    sim.grid_update()
+    sim.g2p()
+    p1, l1 = sim.momentum("particles")
+    sp = m * np.linalg.norm(v, axis=1).sum()
+    sl = m * (np.linalg.norm(x, axis=1) * np.linalg.norm(v, axis=1)).sum() + m * np.abs(B).sum()
+    assert np.abs(pg - p0).max() <= 1e-5 * sp
+    assert np.abs(lg - l0).max() <= 1e-5 * sl
+    assert np.abs(p1 - p0).max() <= 1e-5 * sp
+    assert np.abs(l1 - l0).max() <= 1e-5 * sl
+
+
+def test_gpu_fp64_disk_round_trips_conserve_to_1e12(apic):
+    """2-D FP64 rotating disk (64^2, dx = 1/64, 4 ppc, omega = 1, v0 = (0.1, 0)), transfer only,
+    100 P2G -> G2P round trips at dt = 1e-2: p and l conserved to 1e-12 relative, and the
+    trajectory matches the oracle's."""
+    sc = scenes.rotating_disk_2d(res=64, ppc=4, seed=0)
+    k = kappa(2) * sc.dx ** 2
+    B = sc.grad_v * k
+    gc, oc, m, vol = configs(2, 2, (64, 64), sc.dx, precision=64, dt=1e-2, model="none")
+    sim = apic.Sim(gc, sc.n)
+    sim.upload(sc.x, sc.v, B, None)
+    p0, l0 = sim.momentum("particles")
+    sim.step(100)
+    p1, l1 = sim.momentum("particles")
+    sp = np.linalg.norm(sc.v, axis=1).sum()
+    sl = (np.linalg.norm(sc.x, axis=1) * np.linalg.norm(sc.v, axis=1)).sum() + np.abs(B).sum()
+    assert np.abs(p1 - p0).max() <= 1e-12 * sp
+    assert np.abs(l1 - l0).max() <= 1e-12 * sl
+    gx, gv, gB, gF = sim.download()
+    ox, ov, oB, oF, bad = oracle.step(oc, sc.x, sc.v, B, np.broadcast_to(np.eye(2), (sc.n, 2, 2)), 1.0, vol, nsteps=100)
+    assert bad == 0
+    assert relerr(gv, ov) <= 1e-9
+    assert relerr(gx - sc.x, ox - sc.x) <= 1e-9
+
+
+def test_gpu_affine_round_trip(apic):
+    """Sec. 5.5 on the GPU at dt = 0: v_p = c + C x_p, B_p = C D_p are reproduced."""
+    sc = scenes.falling_cube_3d(res=32, side=0.5, ppc=8, seed=4)
+    rng = np.random.default_rng(4)
+    c = rng.normal(size=3)
+    Cm = rng.normal(size=(3, 3))
+    v = c + sc.x @ Cm.T
+    B = np.broadcast_to(Cm * kappa(2) * sc.dx ** 2, (sc.n, 3, 3)).copy()
+    gc, oc, m, vol = configs(3, 2, (32,) * 3, sc.dx, dt=0.0, model="none")
+    sim = apic.Sim(gc, sc.n)
+    sim.upload(sc.x, v, B)
+    sim.step(1)
+    gx, gv, gB, gF = sim.download()
+    assert relerr(gv, v) <= 2e-6
+    assert relerr(gB, B) <= 2e-5
+    assert np.abs(gx - sc.x).max() <= 1e-6 * sc.dx
+
+
+def test_gpu_single_particle_stability(apic):
+    """Sec. 5.4: one isolated particle keeps v_p and B_p and moves by dt v_p."""
+    rng = np.random.default_rng(5)
+    x = np.array([[0.43, 0.51, 0.57]])
+    v = rng.normal(size=(1, 3))
+    B = 1e-4 * rng.normal(size=(1, 3, 3))
+    gc, oc, m, vol = configs(3, 3, (32,) * 3, 1 / 32, dt=1e-3, model="none")
+    sim = apic.Sim(gc, 1)
+    sim.upload(x, v, B)
+    sim.step(3)
+    gx, gv, gB, gF = sim.download()
+    assert relerr(gv, v) <= 1e-6
+    assert relerr(gB, B) <= 1e-5
+    np.testing.assert_allclose(gx, x + 3e-3 * v, atol=1e-6 / 32)
+
+
+def test_empty_and_single_cell_edge_cases(apic):
+    gc, oc, m, vol = configs(3, 2, (16,) * 3, 1 / 16, dt=1e-3)
+    sim = apic.Sim(gc, 5000)
+    sim.upload(np.zeros((0, 3)))
+    sim.step(2)
+    p, l = sim.momentum("particles")
+    assert np.all(p == 0) and np.all(l == 0)
+    # every particle in one cell: a single long segment in P2G
+    rng = np.random.default_rng(6)
+    x = (8 + rng.random((5000, 3))) / 16
+    v = rng.normal(size=(5000, 3))
+    sim.upload(x, v)
+    x0, v0, B0, F0 = sim.download()
+    sim.p2g()
+    m_gpu, p_gpu = sim.grid("momentum")
+    gm, gmv, gf, _ = oracle.p2g(oc, x0, v0, B0, F0, m, vol)
+    assert relerr(m_gpu, gm) <= 1e-5
+    assert relerr(p_gpu, gmv + oc.dt * gf) <= 1e-5
+
+
+def test_out_of_grid_particle_is_reported(apic):
+    gc, oc, m, vol = configs(3, 2, (16,) * 3, 1 / 16, dt=1e-3)
+    sim = apic.Sim(gc, 10)
+    with pytest.raises(apic.ApicError) as e:
+        sim.upload(np.array([[0.5, 0.5, 0.5], [1.5, 0.5, 0.5]]))
+    assert e.value.status == apic.APIC_ERR_NUMERIC
+    # the clamp keeps the step memory-safe; the condition is reported again by the step
+    sim.step(1)
+    with pytest.raises(apic.ApicError):
+        sim.download()
