@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the APIC / explicit MPM step (particle-steps/s).
+
+Workloads (seeded synthetic inputs shaped like the paper's elastic-body scenes):
+  cube128   3-D explicit MPM + APIC, FP32, quadratic B-splines, 128^3 grid, dx = 1/128,
+            elastic cube of side 0.4 centred, 32 particles per cell (4.29M particles),
+            fixed-corotated E = 1e4, nu = 0.3, rho = 1, gravity -9.8, dt = 1e-4, sticky walls
+  spheres256  3-D, cubic B-splines, 256^3, two spheres r = 0.15 approaching at +-1, 32 ppc
+            (15.2M particles), E = 5e4, nu = 0.4, dt = 5e-6
+
+One "step" = the whole hot path: cell keys, radix sort, tile list, P2G (+force), grid
+update, G2P.  `value` is device-timed (CUDA events on the simulation's stream, inputs
+resident in HBM and larger than L2); `e2e` goes through the C ABI with pinned host buffers
+(upload + steps + per-step momentum read + download).  Under torchrun every rank runs its
+own replica (independent simulations; no collective on the data path), `value` is the
+sum over ranks divided by the slowest rank's time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload cube128] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "APIC particle-steps/s (P2G+grid+G2P) batched vs plain; p50/p99 latency"
+UNIT = "particle-steps/s"
+
+WORKLOADS = {
+    "cube128": dict(dim=3, order=2, res=128, ppc=32, E=1e4, nu=0.3, rho=1.0, gravity=(0.0, -9.8, 0.0), dt=1e-4,
+                    boundary="sticky", desc="3-D explicit MPM+APIC FP32 quadratic, 128^3, dx=1/128, elastic cube side 0.4, "
+                                            "32 ppc jittered, fixed-corotated E=1e4 nu=0.3 rho=1, gravity -9.8, dt=1e-4, sticky walls"),
+    "spheres256": dict(dim=3, order=3, res=256, ppc=32, E=5e4, nu=0.4, rho=1.0, gravity=(0.0, 0.0, 0.0), dt=5e-6,
+                       boundary="sticky", desc="3-D explicit MPM+APIC FP32 cubic, 256^3, two spheres r=0.15 at +-1, 32 ppc, "
+                                               "fixed-corotated E=5e4 nu=0.4 rho=1, dt=5e-6, sticky walls"),
+}
+
+# algorithmic bytes (FP32): per particle and per active grid node, for each single-kernel phase
+ALGO_BYTES = {
+    # P2G reads x (3 offsets + cell), v, B, F = 16 + 12 + 36 + 36 B; writes m and momentum per node
+    "p2g": (100, 16),
+    # grid update reads (m, momentum), writes (v~, m) and clears the accumulator
+    "grid_update": (0, 48),
+    # G2P reads x + F (52 B), writes x, v, B, F (100 B); reads v~ per node
+    "g2p": (152, 16),
+}
+KERNEL_OF_PHASE = {"p2g": "k_p2g", "grid_update": "k_grid_update", "g2p": "k_g2p"}
+
+
+def make_scene(w: dict, seed: int = 0):
+    from paper_1603_06188_gb300 import scenes
+
+    if w["res"] == 128:
+        return scenes.falling_cube_3d(res=128, side=0.4, ppc=w["ppc"], seed=seed)
+    return scenes.colliding_spheres_3d(res=256, radius=0.15, ppc=w["ppc"], speed=1.0, seed=seed)
+
+
+def initial_state(sc, order):
+    n = sc.n
+    kappa = 0.25 if order == 2 else 1.0 / 3.0
+    B = sc.grad_v * (kappa * sc.dx * sc.dx)
+    F = np.broadcast_to(np.eye(3), (n, 3, 3))
+    return sc.x, sc.v, B, F
+
+
+def lib_config(w, sc, precision=32):
+    from paper_1603_06188_gb300 import apic
+
+    vol = sc.dx ** 3 / w["ppc"]
+    return apic.make_config(dim=3, order=w["order"], precision=precision, res=(w["res"],) * 3, dx=sc.dx,
+                            dt=w["dt"], gravity=w["gravity"], boundary=w["boundary"], wall=w["order"] + 1,
+                            model="fcr", E=w["E"], nu=w["nu"], particle_mass=w["rho"] * vol, particle_volume=vol)
+
+
+def oracle_config(w, sc):
+    import oracle
+
+    return oracle.make_cfg(dim=3, order=w["order"], res=(w["res"],) * 3, dx=sc.dx, dt=w["dt"], gravity=w["gravity"],
+                           boundary=w["boundary"], wall=w["order"] + 1, model="fcr", E=w["E"], nu=w["nu"])
+
+
+def oracle_sample(sc, target: int):
+    """A spatially coherent slab of the scene with about `target` particles (lowest x)."""
+    if sc.n <= target:
+        return np.arange(sc.n)
+    cut = np.partition(sc.x[:, 0], target)[target]
+    return np.flatnonzero(sc.x[:, 0] < cut)
+
+
+def time_oracle(w, sc, target: int, steps: int, warmup: int = 0):
+    """Time the oracle (single-threaded FP64 C) on a slab sample; returns (value, seconds, n)."""
+    import oracle
+
+    idx = oracle_sample(sc, target)
+    x, v, B, F = initial_state(sc, w["order"])
+    x, v, B, F = x[idx], v[idx], B[idx], np.ascontiguousarray(F[idx])
+    vol = sc.dx ** 3 / w["ppc"]
+    m = w["rho"] * vol
+    oc = oracle_config(w, sc)
+    if warmup:
+        x, v, B, F, _ = oracle.step(oc, x, v, B, F, m, vol, nsteps=warmup)
+    t0 = time.perf_counter()
+    x, v, B, F, bad = oracle.step(oc, x, v, B, F, m, vol, nsteps=steps)
+    dt = time.perf_counter() - t0
+    return len(idx) * steps / dt, dt, len(idx)
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks / throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict | None:
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [t.strip() for t in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1603_06188_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernels."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        e = d.get(workload, {}).get(kernel)
+        if e and e.get("source_hash") == kernel_source_hash():
+            return float(e["dram_bytes_per_launch"])
+    except (ValueError, KeyError, TypeError):
+        return None
+    return None
+
+
+def dist_setup(n_gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+        pg = dist
+    return world, rank, local, pg
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    w = WORKLOADS[args.workload]
+    sc = make_scene(w)
+    target = args.ref_particles
+    value, secs, n = time_oracle(w, sc, target, args.steps, warmup=args.warmup)
+    sample = (f"slab of {n} of the {sc.n} particles (lowest x), full {w['res']}^3 grid, {args.steps} timed steps "
+              f"after {args.warmup} warm-up, FP64 single-threaded oracle")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "description": w["desc"], "particles": sc.n},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="cube128", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ppc", type=int, default=None)
+    ap.add_argument("--ref-particles", type=int, default=20000)
+    ap.add_argument("--cpu-sample", type=int, default=300000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local, dist = dist_setup(args.gpus)
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+
+    from paper_1603_06188_gb300 import apic, build
+
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    apic.load()
+    w = dict(WORKLOADS[args.workload])
+    if args.ppc:
+        w["ppc"] = args.ppc
+    sc = make_scene(w, seed=rank)
+    x, v, B, F = initial_state(sc, w["order"])
+    cfg = lib_config(w, sc)
+    sim = apic.Sim(cfg, sc.n)
+    sim.upload(x, v, B, F)
+    stream = sim.stream
+
+    # active node blocks after one P2G (for the grid part of the algorithmic bytes)
+    sim.p2g()
+    active_nodes = int(sim.occupancy().sum()) * 64
+    sim.grid_update()
+    sim.g2p()
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    p_before, l_before = sim.momentum("particles")
+    launches0 = sim.stats()["kernel_launches"]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    sim.profile(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev0.record(stream)
+    sim.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sim.profile(False)
+    phases = sim.profile_read()
+    ms = ev0.elapsed_time(ev1)
+    stats = sim.stats()
+    launches = stats["kernel_launches"] - launches0
+    p_after, l_after = sim.momentum("particles")
+    max_ms = ms
+    total_units = sc.n * args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        max_ms = float(t.item())
+        u = torch.tensor([float(total_units)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(u)
+        total_units = float(u.item())
+    value = total_units / (max_ms / 1e3)
+
+    # roofline of the dominant single-kernel phase
+    peak, peak_kind = peaks()
+    per_phase = {}
+    for name, (bp, bn) in ALGO_BYTES.items():
+        ph = phases[name]
+        if ph["launches"] == 0:
+            continue
+        t_launch = ph["ms"] / ph["launches"] * 1e-3
+        algo = bp * sc.n + bn * active_nodes
+        per_phase[name] = {"ms_per_launch": 1e3 * t_launch, "algorithmic_bytes": algo, "gbs": algo / t_launch / 1e9}
+    dom = max(per_phase, key=lambda k: per_phase[k]["ms_per_launch"])
+    traffic = recorded_traffic(KERNEL_OF_PHASE[dom], args.workload)
+    roof = {"bound": "hbm", "kernel": KERNEL_OF_PHASE[dom], "achieved": per_phase[dom]["gbs"], "peak": peak,
+            "unit": "GB/s", "frac": per_phase[dom]["gbs"] / peak, "traffic": traffic,
+            "peak_source": f"{peak_kind} hbm_gbs",
+            "algorithmic_bytes_per_launch": per_phase[dom]["algorithmic_bytes"]}
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        n = sc.n
+        pin = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+        hx, hv, hB, hF = pin((n, 3)), pin((n, 3)), pin((n, 3, 3)), pin((n, 3, 3))
+        hx[:], hv[:], hB[:], hF[:] = x, v, B, F
+        ox, ov, oB, oF = pin((n, 3)), pin((n, 3)), pin((n, 3, 3)), pin((n, 3, 3))
+        e_steps = max(1, min(args.steps, 100))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        apic.apic_upload(sim.handle, n, hx, hv, hB, hF, on_device=0)
+        for _ in range(e_steps):
+            sim.step(1)
+            sim.momentum("particles")
+        apic.apic_download(sim.handle, ox, ov, oB, oF, on_device=0)
+        torch.cuda.synchronize()
+        et = time.perf_counter() - t0
+        state_bytes = n * (3 + 3 + 9 + 9) * 8
+        e2e = {"value": n * e_steps / et * world, "unit": UNIT, "steps": e_steps,
+               "h2d_bytes_per_step": state_bytes / e_steps, "d2h_bytes_per_step": state_bytes / e_steps + 48}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        cv, csecs, cn = time_oracle(w, sc, args.cpu_sample, 2)
+        cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"2 steps of a slab of {cn} of the {sc.n} particles (lowest x) on the full grid, "
+                         f"{csecs:.1f} s, FP64 single-threaded"}
+
+    if rank == 0:
+        sp = np.abs(p_after - p_before).max()
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "description": w["desc"], "particles": sc.n, "ppc": w["ppc"],
+                       "grid": [w["res"]] * 3, "order": w["order"], "dt": w["dt"], "active_nodes": active_nodes,
+                       "l2": f"inputs larger than L2: particle state {sc.n * 100 / 1e6:.0f} MB per copy",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "phases_ms_per_step": {k: v_["ms"] / args.steps for k, v_ in phases.items()},
+            "per_kernel": per_phase,
+            "polar_fp64_fallbacks": stats["polar_fp64_fallbacks"],
+            "momentum_change_over_timed_steps": {"p": (p_after - p_before).tolist(), "l": (l_after - l_before).tolist(),
+                                                 "finite": bool(np.isfinite(p_after).all() and np.isfinite(l_after).all())},
+        }
+        print(json.dumps(out), flush=True)
+    sim.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -76,7 +76,7 @@ typedef struct {
     double E, nu;            /* Young's modulus, Poisson's ratio */
     double particle_mass;    /* m_p, the same for every particle of a simulation */
     double particle_volume;  /* V_p (reference volume), the same for every particle */
-    int tile_particles;      /* particles per P2G / G2P tile (power of two, 64..4096);
+    int tile_particles;      /* particles per P2G / G2P tile (power of two, 256..4096);
                                 0 = default */
 } apic_config;
 
@@ -153,8 +153,22 @@ apic_status apic_keys_download(apic_sim* sim, uint32_t* keys, uint32_t* perm);
 apic_status apic_grid_occupancy(apic_sim* sim, uint8_t* out, int64_t n_blocks);
 
 /* Counters: [0] particles, [1] blocks of the grid, [2] tiles of the last sort,
- * [3] FP64 fallbacks of the 3x3 polar decomposition since creation.  Synchronising. */
-apic_status apic_stats(apic_sim* sim, int64_t out[4]);
+ * [3] FP64 fallbacks of the 3x3 polar decomposition since creation, [4] kernels launched
+ * by this simulation since creation.  Synchronising. */
+apic_status apic_stats(apic_sim* sim, int64_t out[5]);
+
+/* Phases of a step, for apic_profile_read. */
+enum { APIC_PHASE_KEYS = 0, APIC_PHASE_SORT, APIC_PHASE_TILES, APIC_PHASE_P2G, APIC_PHASE_GRID,
+       APIC_PHASE_G2P, APIC_NPHASE };
+
+/* Start (enable = 1, clearing earlier records) or stop (0) per-phase timing: CUDA events
+ * recorded on the simulation's stream around each phase's kernels.  No device work
+ * changes.  Host-only bookkeeping; asynchronous. */
+apic_status apic_profile(apic_sim* sim, int enable);
+
+/* Accumulated device time (ms) and launch count per phase since apic_profile(sim, 1).
+ * Synchronising, host pointers of APIC_NPHASE entries. */
+apic_status apic_profile_read(apic_sim* sim, double ms[APIC_NPHASE], int64_t launches[APIC_NPHASE]);
 
 /* Reason for the last failing call on this simulation ("" if none). */
 const char* apic_last_error(apic_sim* sim);

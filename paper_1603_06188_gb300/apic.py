@@ -83,7 +83,10 @@ SIGNATURES = {
     "apic_grid_occupancy": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "apic_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
     "apic_last_error": (C.c_char_p, [C.c_void_p]),
+    "apic_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "apic_profile_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
 }
+PHASES = ["keys", "sort", "tiles", "p2g", "grid_update", "g2p"]
 
 
 def library_path() -> str:
@@ -190,13 +193,24 @@ def apic_grid_occupancy(sim, out, n_blocks: int):
 
 
 def apic_stats(sim):
-    out = np.zeros(4, dtype=np.int64)
+    out = np.zeros(5, dtype=np.int64)
     _check(load().apic_stats(sim, _ptr(out)), sim)
     return out
 
 
 def apic_last_error(sim) -> str:
     return load().apic_last_error(sim).decode()
+
+
+def apic_profile(sim, enable: int):
+    _check(load().apic_profile(sim, enable), sim)
+
+
+def apic_profile_read(sim):
+    ms = np.zeros(len(PHASES))
+    launches = np.zeros(len(PHASES), dtype=np.int64)
+    _check(load().apic_profile_read(sim, _ptr(ms), _ptr(launches)), sim)
+    return ms, launches
 
 
 # ----------------------------------------------------------------------- convenience
@@ -288,7 +302,15 @@ class Sim:
 
     def stats(self) -> dict:
         s = apic_stats(self.handle)
-        return {"particles": int(s[0]), "blocks": int(s[1]), "tiles": int(s[2]), "polar_fp64_fallbacks": int(s[3])}
+        return {"particles": int(s[0]), "blocks": int(s[1]), "tiles": int(s[2]), "polar_fp64_fallbacks": int(s[3]),
+                "kernel_launches": int(s[4])}
+
+    def profile(self, enable: bool = True):
+        apic_profile(self.handle, 1 if enable else 0)
+
+    def profile_read(self) -> dict:
+        ms, launches = apic_profile_read(self.handle)
+        return {name: {"ms": float(ms[i]), "launches": int(launches[i])} for i, name in enumerate(PHASES)}
 
     def close(self):
         if getattr(self, "handle", None):

@@ -9,6 +9,7 @@
 
 #include <new>
 #include <string>
+#include <vector>
 
 #include "apic.h"
 #include "apic_internal.h"
@@ -29,6 +30,13 @@ struct apic_sim {
     uint32_t* perm;
     int64_t max_tiles;
     std::string err;
+    int64_t launches;      // kernels launched since creation
+    // per-phase timing
+    bool prof_on;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used;
+    struct Rec { int phase; cudaEvent_t a, b; int64_t kernels; };
+    std::vector<Rec> recs;
 };
 
 namespace {
@@ -188,6 +196,39 @@ apic_status check_device(apic_sim* s)
     return fail(s, APIC_ERR_NUMERIC, "a particle's stencil left the grid; it was clamped to the boundary");
 }
 
+cudaEvent_t take_event(apic_sim* s)
+{
+    if (s->ev_used == s->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        s->ev_pool.push_back(e);
+    }
+    return s->ev_pool[s->ev_used++];
+}
+
+// records events around one phase when profiling is on; counts launched kernels always
+struct PhaseScope {
+    apic_sim* s;
+    int phase;
+    int64_t kernels;
+    cudaEvent_t a = nullptr;
+    PhaseScope(apic_sim* s_, int phase_, int64_t kernels_) : s(s_), phase(phase_), kernels(kernels_)
+    {
+        if (s->prof_on && (a = take_event(s)) != nullptr) cudaEventRecord(a, s->stream);
+    }
+    ~PhaseScope()
+    {
+        s->launches += kernels;
+        if (a) {
+            cudaEvent_t b = take_event(s);
+            if (b) {
+                cudaEventRecord(b, s->stream);
+                s->recs.push_back({phase, a, b, kernels});
+            }
+        }
+    }
+};
+
 #define DISPATCH(s, fn, ...) ((s)->c.precision == 32 ? fn##_f32(__VA_ARGS__) : fn##_f64(__VA_ARGS__))
 
 }  // namespace
@@ -227,6 +268,9 @@ apic_status apic_create(const apic_config* cfg, int64_t max_particles, void* wor
     s->phase = 0;
     s->skeys = s->perm = nullptr;
     s->max_tiles = L.max_tiles;
+    s->launches = 0;
+    s->prof_on = false;
+    s->ev_used = 0;
     char* base = (char*)workspace;
     for (int a = 0; a < 2; ++a)
         for (int i = 0; i < 7; ++i) s->b.st[a][i] = base + L.st[a][i];
@@ -282,6 +326,7 @@ apic_status apic_destroy(apic_sim* s)
 {
     if (!s) return APIC_ERR_ARG;
     cudaError_t e = cudaStreamSynchronize(s->stream);
+    for (cudaEvent_t ev : s->ev_pool) cudaEventDestroy(ev);
     delete s;
     return e == cudaSuccess ? APIC_OK : APIC_ERR_CUDA;
 }
@@ -372,10 +417,22 @@ apic_status apic_p2g(apic_sim* s)
         s->phase = 1;
         return APIC_OK;
     }
-    if (!s->keys_valid) CK(DISPATCH(s, keys, s->c, s->b, s->cur, n, s->stream), "keys kernel");
-    CK(radix_sort(s->b, n, s->c.key_bits, s->stream, &s->skeys, &s->perm), "radix sort");
-    CK(build_tiles(s->b, s->skeys, n, s->c.dim, s->c.tile, s->max_tiles, s->stream), "tile list");
-    CK(DISPATCH(s, p2g, s->c, s->b, s->cur, s->skeys, s->perm, n, s->L, s->stream), "p2g kernel");
+    if (!s->keys_valid) {
+        PhaseScope ps(s, APIC_PHASE_KEYS, 1);
+        CK(DISPATCH(s, keys, s->c, s->b, s->cur, n, s->stream), "keys kernel");
+    }
+    {
+        PhaseScope ps(s, APIC_PHASE_SORT, 5 * ((s->c.key_bits + 7) / 8));
+        CK(radix_sort(s->b, n, s->c.key_bits, s->stream, &s->skeys, &s->perm), "radix sort");
+    }
+    {
+        PhaseScope ps(s, APIC_PHASE_TILES, 5);
+        CK(build_tiles(s->b, s->skeys, n, s->c.dim, s->c.tile, s->max_tiles, s->stream), "tile list");
+    }
+    {
+        PhaseScope ps(s, APIC_PHASE_P2G, 1);
+        CK(DISPATCH(s, p2g, s->c, s->b, s->cur, s->skeys, s->perm, n, s->L, s->stream), "p2g kernel");
+    }
     s->phase = 1;
     return APIC_OK;
 }
@@ -385,7 +442,10 @@ apic_status apic_grid_update(apic_sim* s)
     if (!s) return APIC_ERR_ARG;
     if (s->phase != 1) return fail(s, APIC_ERR_ARG, "apic_grid_update must follow apic_p2g");
     CK(cudaSetDevice(s->device), "cudaSetDevice");
-    CK(DISPATCH(s, grid_update, s->c, s->b, s->L, s->stream), "grid update kernel");
+    {
+        PhaseScope ps(s, APIC_PHASE_GRID, 1);
+        CK(DISPATCH(s, grid_update, s->c, s->b, s->L, s->stream), "grid update kernel");
+    }
     s->phase = 2;
     return APIC_OK;
 }
@@ -396,7 +456,10 @@ apic_status apic_g2p(apic_sim* s)
     if (s->phase != 2) return fail(s, APIC_ERR_ARG, "apic_g2p must follow apic_grid_update");
     CK(cudaSetDevice(s->device), "cudaSetDevice");
     if (s->n > 0) {
-        CK(DISPATCH(s, g2p, s->c, s->b, s->cur, s->skeys, s->perm, s->n, s->L, s->stream), "g2p kernel");
+        {
+            PhaseScope ps(s, APIC_PHASE_G2P, 1);
+            CK(DISPATCH(s, g2p, s->c, s->b, s->cur, s->skeys, s->perm, s->n, s->L, s->stream), "g2p kernel");
+        }
         s->cur ^= 1;
         s->keys_valid = true;
     }
@@ -490,7 +553,7 @@ apic_status apic_grid_occupancy(apic_sim* s, uint8_t* out, int64_t n_blocks)
     return check_device(s);
 }
 
-apic_status apic_stats(apic_sim* s, int64_t out[4])
+apic_status apic_stats(apic_sim* s, int64_t out[5])
 {
     if (!s || !out) return APIC_ERR_ARG;
     CK(cudaSetDevice(s->device), "cudaSetDevice");
@@ -502,6 +565,36 @@ apic_status apic_stats(apic_sim* s, int64_t out[4])
     out[1] = s->c.nblocks;
     out[2] = nt;
     out[3] = fb;
+    out[4] = s->launches;
+    return APIC_OK;
+}
+
+apic_status apic_profile(apic_sim* s, int enable)
+{
+    if (!s) return APIC_ERR_ARG;
+    s->prof_on = enable != 0;
+    if (enable) {
+        s->recs.clear();
+        s->ev_used = 0;
+    }
+    return APIC_OK;
+}
+
+apic_status apic_profile_read(apic_sim* s, double ms[APIC_NPHASE], int64_t launches[APIC_NPHASE])
+{
+    if (!s || !ms || !launches) return APIC_ERR_ARG;
+    CK(cudaSetDevice(s->device), "cudaSetDevice");
+    CK(cudaStreamSynchronize(s->stream), "synchronize");
+    for (int i = 0; i < APIC_NPHASE; ++i) {
+        ms[i] = 0.0;
+        launches[i] = 0;
+    }
+    for (const auto& r : s->recs) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, r.a, r.b), "event elapsed time");
+        ms[r.phase] += t;
+        launches[r.phase] += r.kernels;
+    }
     return APIC_OK;
 }
 

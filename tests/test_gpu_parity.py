@@ -181,12 +181,13 @@ def test_gpu_momentum_conservation_fp32(apic):
 
 def test_gpu_fp64_disk_round_trips_conserve_to_1e12(apic):
     """2-D FP64 rotating disk (64^2, dx = 1/64, 4 ppc, omega = 1, v0 = (0.1, 0)), transfer only,
-    100 P2G -> G2P round trips at dt = 1e-2: p and l conserved to 1e-12 relative, and the
-    trajectory matches the oracle's."""
+    100 P2G -> G2P round trips at dt = 5e-3: p and l conserved to 1e-12 relative, and the
+    trajectory matches the oracle's.  (Without forces the particles move ballistically, so
+    at dt = 1e-2 the disk would leave the unit box before step 100.)"""
     sc = scenes.rotating_disk_2d(res=64, ppc=4, seed=0)
     k = kappa(2) * sc.dx ** 2
     B = sc.grad_v * k
-    gc, oc, m, vol = configs(2, 2, (64, 64), sc.dx, precision=64, dt=1e-2, model="none")
+    gc, oc, m, vol = configs(2, 2, (64, 64), sc.dx, precision=64, dt=5e-3, model="none")
     sim = apic.Sim(gc, sc.n)
     sim.upload(sc.x, sc.v, B, None)
     p0, l0 = sim.momentum("particles")
