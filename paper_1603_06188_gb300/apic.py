@@ -249,7 +249,7 @@ class Sim:
         n = len(x)
         self.n = n          # the library holds n particles even when it reports a range error
         if isinstance(x, np.ndarray):
-            arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(n, -1) for a in (x, v, B, F)]
+            arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (x, v, B, F)]
             apic_upload(self.handle, n, *arrs, on_device=0)
         else:
             arrs = [None if a is None else a.contiguous() for a in (x, v, B, F)]

@@ -217,8 +217,11 @@ def test_gpu_affine_round_trip(apic):
     sim.upload(sc.x, v, B)
     sim.step(1)
     gx, gv, gB, gF = sim.download()
-    assert relerr(gv, v) <= 2e-6
-    assert relerr(gB, B) <= 2e-5
+    # FP32 bound: the grid velocity carries an absolute rounding error ~eps |v|, and
+    # B = dx sum w v~ r^ is smaller than |v| dx by the factor |B| / (|v| dx)
+    eps = np.finfo(np.float32).eps
+    assert relerr(gv, v) <= 16 * eps
+    assert relerr(gB, B) <= 16 * eps * np.abs(v).max() * sc.dx / np.abs(B).max()
     assert np.abs(gx - sc.x).max() <= 1e-6 * sc.dx
 
 
