@@ -170,6 +170,34 @@ apic_status apic_profile(apic_sim* sim, int enable);
  * Synchronising, host pointers of APIC_NPHASE entries. */
 apic_status apic_profile_read(apic_sim* sim, double ms[APIC_NPHASE], int64_t launches[APIC_NPHASE]);
 
+/* Stable radix sort of 32-bit keys that allocates nothing.  The paper has no counterpart:
+ * this is a service for callers that cannot allocate device memory -- a host framework
+ * that owns all device memory and gives plug-ins no allocator, or a real-time loop that
+ * must not call cudaMalloc after start-up (it can synchronise the device and take
+ * unbounded time).  Such a caller passes only its inputs and outputs; the sort's own
+ * scratch (ping-pong keys and indices, digit histograms, scan partials) lives in a
+ * fixed-size static device array inside the library, which every GPU that loads the
+ * library holds until the process exits (about 9 MB).
+ *   keys        device pointer, n keys (read only)
+ *   key_bits    number of low key bits to sort on, 1..32 (higher bits must be zero)
+ *   sorted_keys device pointer, n entries: the keys in ascending order
+ *   perm        device pointer, n entries: perm[k] = input index of the k-th sorted key;
+ *               equal keys keep their input order (stable), the same result apic_p2g's
+ *               sort produces (see apic_keys_download)
+ *   stream      cudaStream_t (or NULL); the call is asynchronous on it.
+ * n <= APIC_SORT_NOALLOC_MAX_KEYS; larger n returns APIC_ERR_OOM before any launch.
+ * The first call on each device looks up the static array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that first call
+ * before any stream capture.  Every call reuses the same array, so calls whose work
+ * overlaps on the GPU (other streams, other threads) race on it: serialise them.
+ * Every scratch word a call reads is written earlier in the same call, so nothing left
+ * by a previous call is used.
+ * Errors: APIC_ERR_ARG (NULL pointer, n < 0, key_bits out of range), APIC_ERR_OOM,
+ * APIC_ERR_CUDA. */
+#define APIC_SORT_NOALLOC_MAX_KEYS (1 << 20)
+apic_status apic_sort_keys_noalloc(const uint32_t* keys, int64_t n, int key_bits, uint32_t* sorted_keys,
+                                   uint32_t* perm, void* stream);
+
 /* Reason for the last failing call on this simulation ("" if none). */
 const char* apic_last_error(apic_sim* sim);
 

@@ -84,6 +84,7 @@ SIGNATURES = {
     "apic_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
     "apic_last_error": (C.c_char_p, [C.c_void_p]),
     "apic_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "apic_sort_keys_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "apic_profile_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 PHASES = ["keys", "sort", "tiles", "p2g", "grid_update", "g2p"]
@@ -200,6 +201,19 @@ def apic_stats(sim):
 
 def apic_last_error(sim) -> str:
     return load().apic_last_error(sim).decode()
+
+
+APIC_SORT_NOALLOC_MAX_KEYS = 1 << 20
+
+
+def apic_sort_keys_noalloc(keys, n: int, key_bits: int, sorted_keys, perm, stream_ptr: int = 0) -> int:
+    """Stable key sort with no device allocation (static scratch inside the library).
+
+    For callers that cannot allocate device memory; all four pointers are device memory
+    the caller owns.  Returns the apic_status code (0 = APIC_OK) without raising, so a
+    caller can branch on APIC_ERR_OOM for n above APIC_SORT_NOALLOC_MAX_KEYS."""
+    return load().apic_sort_keys_noalloc(_ptr(keys), n, key_bits, _ptr(sorted_keys), _ptr(perm),
+                                         C.c_void_p(stream_ptr))
 
 
 def apic_profile(sim, enable: int):

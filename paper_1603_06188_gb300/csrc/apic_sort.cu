@@ -6,6 +6,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
+#include "apic.h"
 #include "apic_internal.h"
 
 namespace apic {
@@ -297,3 +300,75 @@ cudaError_t build_tiles(const Buffers& b, const uint32_t* skeys, int64_t n, int 
 }
 
 }  // namespace apic
+
+// ---------------------------------------------------------------- sort without allocation
+// apic_sort_keys_noalloc: the same kernels, with all scratch in one static device array.
+namespace apic {
+namespace {
+
+constexpr int64_t kNoAllocMaxKeys = APIC_SORT_NOALLOC_MAX_KEYS;
+constexpr int64_t kNoAllocTiles = (kNoAllocMaxKeys + RTILE - 1) / RTILE;
+constexpr int64_t kNoAllocParts = (256 * kNoAllocTiles + 1 + SCH - 1) / SCH + 1;
+// words: ping-pong keys, ping-pong indices, digit counts, scan partials
+constexpr int64_t kNoAllocWords = 2 * kNoAllocMaxKeys + 256 * kNoAllocTiles + kNoAllocParts;
+
+static __device__ __align__(256) uint32_t g_sort_scratch[kNoAllocWords];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+uint32_t* g_scratch_ptr[kMaxDevices] = {};
+
+// device address of g_sort_scratch on the current device (looked up once per device)
+cudaError_t noalloc_scratch(uint32_t** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_sort_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = static_cast<uint32_t*>(p);
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace apic
+
+extern "C" apic_status apic_sort_keys_noalloc(const uint32_t* keys, int64_t n, int key_bits, uint32_t* sorted_keys,
+                                              uint32_t* perm, void* stream)
+{
+    using namespace apic;
+    if (n < 0 || key_bits < 1 || key_bits > 32) return APIC_ERR_ARG;
+    if (n > kNoAllocMaxKeys) return APIC_ERR_OOM;
+    if (n == 0) return APIC_OK;
+    if (!keys || !sorted_keys || !perm) return APIC_ERR_ARG;
+    uint32_t* scratch = nullptr;
+    if (noalloc_scratch(&scratch) != cudaSuccess) return APIC_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t* tmp_keys = scratch;
+    uint32_t* tmp_vals = tmp_keys + kNoAllocMaxKeys;
+    uint32_t* counts = tmp_vals + kNoAllocMaxKeys;
+    uint32_t* part = counts + 256 * kNoAllocTiles;
+    const int nt = radix_tiles(n);
+    const int passes = (key_bits + 7) / 8;
+    const uint32_t* kin = keys;
+    const uint32_t* vin = nullptr;   // identity indices on the first pass
+    for (int p = 0; p < passes; ++p) {
+        // the last pass lands in the caller's outputs; earlier ones alternate with scratch
+        const bool to_out = ((passes - 1 - p) % 2) == 0;
+        uint32_t* kout = to_out ? sorted_keys : tmp_keys;
+        uint32_t* vout = to_out ? perm : tmp_vals;
+        const int shift = 8 * p;
+        k_radix_hist<<<nt, RT, 0, s>>>(kin, n, shift, nt, counts);
+        if (exclusive_scan(counts, counts, 256 * (int64_t)nt, part, nullptr, s) != cudaSuccess) return APIC_ERR_CUDA;
+        k_radix_scatter<<<nt, RT, 0, s>>>(kin, vin, kout, vout, n, shift, nt, counts);
+        kin = kout;
+        vin = vout;
+    }
+    return cudaGetLastError() == cudaSuccess ? APIC_OK : APIC_ERR_CUDA;
+}
