@@ -69,7 +69,7 @@ apic_status fill_cfg(const apic_config* in, int64_t max_particles, HostCfg* c, s
     const int maxres = in->dim == 3 ? 1024 : 32768;
     for (int a = 0; a < in->dim; ++a)
         if (in->res[a] < in->order + 2 || in->res[a] > maxres) { *why = "grid resolution out of range"; return APIC_ERR_ARG; }
-    int tile = in->tile_particles == 0 ? 1024 : in->tile_particles;
+    int tile = in->tile_particles == 0 ? 4096 : in->tile_particles;
     if (tile < 256 || tile > 4096 || (tile & (tile - 1))) { *why = "tile_particles must be a power of two in [256, 4096]"; return APIC_ERR_ARG; }
     memset(c, 0, sizeof(*c));
     c->dim = in->dim;
@@ -116,7 +116,7 @@ struct Carve {
 // offsets of every buffer inside the workspace (relative to its base)
 struct Layout {
     size_t st[2][7];
-    size_t knext, kA, kB, vA, vB, radix_counts, scan_part, tiles, chunk_cnt, ntiles;
+    size_t knext, kA, kB, vA, vB, radix_counts, scan_part, tiles, chunk_cnt, ntiles, tile_ctr;
     size_t acc, vel, flags, mom_part, mom_out, err, fallbacks, staging;
     size_t staging_doubles;
     int64_t max_tiles;
@@ -145,6 +145,7 @@ Layout layout_of(const HostCfg& c)
     L.tiles = cv.take((size_t)(L.max_tiles + 1) * 4);
     L.chunk_cnt = cv.take((size_t)(nchunks + 1) * 4);
     L.ntiles = cv.take(4);
+    L.tile_ctr = cv.take(8);
     const size_t bn = c.dim == 3 ? 64 : 16;
     L.acc = cv.take((size_t)c.nblocks * bn * 4 * R);
     L.vel = cv.take((size_t)c.nblocks * bn * 4 * R);
@@ -284,6 +285,7 @@ apic_status apic_create(const apic_config* cfg, int64_t max_particles, void* wor
     s->b.tiles = (uint32_t*)(base + L.tiles);
     s->b.chunk_cnt = (uint32_t*)(base + L.chunk_cnt);
     s->b.ntiles = (uint32_t*)(base + L.ntiles);
+    s->b.tile_ctr = (uint32_t*)(base + L.tile_ctr);
     s->b.acc = base + L.acc;
     s->b.vel = base + L.vel;
     s->b.flags = (uint32_t*)(base + L.flags);
@@ -304,6 +306,7 @@ apic_status apic_create(const apic_config* cfg, int64_t max_particles, void* wor
     }
     s->L.sms = sms;
     s->L.p2g_grid = sms * (p2g_per > 0 ? p2g_per : 1);
+    s->L.p2g_cells = !(c.dim == 3 && c.order == 3);
     s->L.g2p_grid = sms * (g2p_per > 0 ? g2p_per : 1);
     s->L.mom_parts = kMomParts;
     const size_t bn = c.dim == 3 ? 64 : 16;

@@ -24,6 +24,7 @@ struct Buffers {
     uint32_t* tiles;             // tile start offsets (+ end sentinel)
     uint32_t* chunk_cnt;         // per-chunk tile counts (scanned in place)
     uint32_t* ntiles;            // device counter: number of tiles
+    uint32_t* tile_ctr;          // 2 work counters (P2G, G2P), zeroed with each tile list
     void* acc;                   // accumulation grid (4 lanes per node)
     void* vel;                   // velocity grid (4 lanes per node)
     uint32_t* flags;             // active node blocks
@@ -65,6 +66,7 @@ struct Launch {
     int p2g_grid;     // persistent grid sizes
     int g2p_grid;
     int mom_parts;    // CTAs of the momentum reduction
+    int p2g_cells;    // 1 if the cell-parallel P2G kernel serves this (dim, order)
 };
 
 #define APIC_DECLARE_PRECISION(SFX)                                                                          \

@@ -210,8 +210,9 @@ __global__ void __launch_bounds__(256) k_tile_count(const uint32_t* __restrict__
 __global__ void __launch_bounds__(256) k_tile_write(const uint32_t* __restrict__ skeys, int64_t n, int sh, int tile,
                                                     const uint32_t* __restrict__ off, const uint32_t* __restrict__ ntiles,
                                                     int64_t max_tiles, uint32_t* __restrict__ tiles, int nchunks,
-                                                    uint32_t* __restrict__ err)
+                                                    uint32_t* __restrict__ err, uint32_t* __restrict__ tile_ctr)
 {
+    if (blockIdx.x == 0 && threadIdx.x < 2) tile_ctr[threadIdx.x] = 0u;
     const int64_t cs = (int64_t)blockIdx.x * tile;
     const int per = tile / 256;
     const int64_t k0 = cs + (int64_t)threadIdx.x * per;
@@ -295,7 +296,7 @@ cudaError_t build_tiles(const Buffers& b, const uint32_t* skeys, int64_t n, int 
     cudaError_t e = exclusive_scan(b.chunk_cnt, b.chunk_cnt, nchunks, b.scan_part, b.ntiles, s);
     if (e != cudaSuccess) return e;
     k_tile_write<<<(unsigned)nchunks, 256, 0, s>>>(skeys, n, sh, tile, b.chunk_cnt, b.ntiles, max_tiles, b.tiles,
-                                                   (int)nchunks, b.err);
+                                                   (int)nchunks, b.err, b.tile_ctr);
     return cudaGetLastError();
 }
 

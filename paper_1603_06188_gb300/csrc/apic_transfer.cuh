@@ -292,6 +292,217 @@ __global__ void __launch_bounds__(TPB) k_p2g(PState<R> st, const uint32_t* __res
     }
 }
 
+// ---------------------------------------------------------------- P2G, cell-parallel
+// Butterfly reduce-scatter of N register values over a group of lanes: at distance H the
+// lane with bit H set keeps the upper half of its values and receives its partner's upper
+// half, the other keeps the lower half; after log2(G) steps each lane holds the group's
+// full sums of about N/G of the values.  (off, cnt) track which original indices a lane's
+// first positions hold.
+template <typename R, int N, int H>
+__device__ __forceinline__ void bfly_step(R* cur, unsigned mask, bool upper)
+{
+    constexpr int HALF = (N + 1) / 2;
+#pragma unroll
+    for (int i = 0; i < HALF; ++i) {
+        const R lo = cur[i];
+        const R hi = (i + HALF < N) ? cur[i + HALF] : R(0);
+        const R send = upper ? lo : hi;
+        const R keep = upper ? hi : lo;
+        cur[i] = keep + __shfl_xor_sync(mask, send, H);
+    }
+}
+
+template <typename R, int N, int G> struct ReduceScatter {
+    static constexpr int FINAL = ReduceScatter<R, (N + 1) / 2, G / 2>::FINAL;
+    static __device__ __forceinline__ void run(R* cur, unsigned mask, int lig, int& off, int& cnt)
+    {
+        constexpr int H = G / 2;
+        constexpr int HALF = (N + 1) / 2;
+        const bool upper = (lig & H) != 0;
+        bfly_step<R, N, H>(cur, mask, upper);
+        if (upper) {
+            off += HALF;
+            cnt = cnt > HALF ? cnt - HALF : 0;
+        } else {
+            cnt = cnt < HALF ? cnt : HALF;
+        }
+        ReduceScatter<R, HALF, G / 2>::run(cur, mask, lig, off, cnt);
+    }
+};
+template <typename R, int N> struct ReduceScatter<R, N, 1> {
+    static constexpr int FINAL = N;
+    static __device__ __forceinline__ void run(R*, unsigned, int, int&, int&) {}
+};
+
+// One CTA takes tiles from a shared counter.  In a tile (sorted particles of one node
+// block) every in-block base cell's particles are a contiguous run; a group of G lanes
+// owns one cell at a time, each lane summing the full (ORDER+1)^D-node stencil of its
+// particles in registers (lanes stride the run by G, so a group's loads are contiguous).
+// The group's sums are combined by the butterfly reduce-scatter and added into the
+// shared-memory tile; the tile goes to the global grid once.  Contributions as in k_p2g.
+template <int D, int ORDER, typename R, int G>
+__global__ void __launch_bounds__(128, 2) k_p2g_cells(PState<R> st, const uint32_t* __restrict__ perm,
+                                                      const uint32_t* __restrict__ skeys,
+                                                      const uint32_t* __restrict__ tiles,
+                                                      const uint32_t* __restrict__ ntiles_p,
+                                                      uint32_t* __restrict__ tile_ctr, R* __restrict__ acc,
+                                                      uint32_t* __restrict__ flags, DevCfg<R> c, uint32_t* err,
+                                                      uint32_t* fallbacks)
+{
+    constexpr int NT = 128;
+    constexpr int K = ORDER + 1;
+    constexpr int TE = 4 + ORDER;
+    constexpr int TN = (D == 3) ? TE * TE * TE : TE * TE;
+    constexpr int NS = (D == 3) ? K * K * K : K * K;
+    constexpr int NV = D + 1;
+    constexpr int NVAL = NS * NV;
+    constexpr int NC = (D == 3) ? 64 : 16;      // base cells of a node block
+    constexpr int NG = NT / G;                  // groups per CTA
+    __shared__ R sm[NV][TN];
+    __shared__ uint32_t cbeg[NC], cend[NC];
+    __shared__ int s_tile;
+    const int lane = threadIdx.x & 31;
+    const int grp = threadIdx.x / G, lig = threadIdx.x % G;
+    const unsigned gmask = (G == 32) ? FULLMASK : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    const int ntiles = (int)*ntiles_p;
+    const R dt_dx = c.dt * c.inv_dx;
+    const R m = c.mass;
+    const R sC = (c.transfer == 0) ? m * c.inv_kdx : R(0);
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_ctr, 1u);
+        for (int i = threadIdx.x; i < NV * TN; i += NT) (&sm[0][0])[i] = R(0);
+        for (int i = threadIdx.x; i < NC; i += NT) { cbeg[i] = 0u; cend[i] = 0u; }
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= ntiles) break;
+        const uint32_t start = tiles[t], end = tiles[t + 1];
+        const uint32_t blk = skeys[start] >> (2 * D);
+        int bo[3] = {0, 0, 0};
+        block_coords<D, R>(blk, c, bo);
+#pragma unroll
+        for (int a = 0; a < D; ++a) bo[a] *= 4;
+        // runs of equal base cell inside the tile
+        for (uint32_t k = start + threadIdx.x; k < end; k += NT) {
+            const uint32_t cl = skeys[k] & (NC - 1);
+            if (k == start || (skeys[k - 1] & (NC - 1)) != cl) cbeg[cl] = k;
+            if (k + 1 == end || (skeys[k + 1] & (NC - 1)) != cl) cend[cl] = k + 1;
+        }
+        __syncthreads();
+        for (int cell = grp; cell < NC; cell += NG) {
+            const uint32_t kb = cbeg[cell], ke = cend[cell];
+            if (kb >= ke) continue;   // uniform across the group
+            int lb[3] = {cell & 3, (cell >> 2) & 3, (D == 3) ? (cell >> 4) : 0};
+            R cur[NVAL];
+#pragma unroll
+            for (int i = 0; i < NVAL; ++i) cur[i] = R(0);
+            for (uint32_t k = kb + lig; k < ke; k += G) {
+                Particle<D, R> p;
+                const uint32_t q = perm[k];
+                load_xF<D, R>(st, q, p);
+                load_vB<D, R>(st, q, p);
+                int base[D];
+                R w[D][K], dw[D][K], fx[D];
+                bool ok = particle_stencil<D, ORDER, R>(p.o, p.cell, c, base, fx, w, dw);
+#pragma unroll
+                for (int a = 0; a < D; ++a)
+                    if (base[a] - bo[a] != lb[a]) ok = false;
+                if (!ok) {
+                    set_err(err, APIC_ERRBIT_RANGE);
+                    continue;
+                }
+                R mv[D], mC[D * D], T[D * D];
+#pragma unroll
+                for (int a = 0; a < D; ++a) mv[a] = m * p.v[a];
+#pragma unroll
+                for (int i = 0; i < D * D; ++i) mC[i] = sC * p.B[i];
+                if (c.model == 1) {
+                    R tau[D * D];
+                    stress_tau<D, R>(p.F, c.mu, c.lam, c.vol, tau, fallbacks);
+#pragma unroll
+                    for (int i = 0; i < D * D; ++i) T[i] = dt_dx * tau[i];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < D * D; ++i) T[i] = R(0);
+                }
+#pragma unroll
+                for (int j = 0; j < NS; ++j) {
+                    const int ia = j % K, ib = (j / K) % K, ic = j / (K * K);
+                    R wv, g[D], r[D];
+                    if (D == 3) {
+                        const R wab = w[0][ia] * w[1][ib];
+                        wv = wab * w[2][ic];
+                        g[0] = dw[0][ia] * w[1][ib] * w[2][ic];
+                        g[1] = w[0][ia] * dw[1][ib] * w[2][ic];
+                        g[2] = wab * dw[2][ic];
+                        r[2] = R(ic) - fx[2];
+                    } else {
+                        wv = w[0][ia] * w[1][ib];
+                        g[0] = dw[0][ia] * w[1][ib];
+                        g[1] = w[0][ia] * dw[1][ib];
+                    }
+                    r[0] = R(ia) - fx[0];
+                    r[1] = R(ib) - fx[1];
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        R qv = mv[a];
+                        R f = R(0);
+#pragma unroll
+                        for (int b = 0; b < D; ++b) {
+                            qv += mC[a * D + b] * r[b];
+                            f += T[a * D + b] * g[b];
+                        }
+                        cur[j * NV + a] += wv * qv - f;
+                    }
+                    cur[j * NV + D] += wv * m;
+                }
+            }
+            int off = 0, cnt = NVAL;
+            ReduceScatter<R, NVAL, G>::run(cur, gmask, lig, off, cnt);
+            constexpr int FIN = ReduceScatter<R, NVAL, G>::FINAL;
+#pragma unroll
+            for (int i = 0; i < FIN; ++i) {
+                if (i < cnt) {
+                    const int idx = off + i;
+                    const int j = idx / NV, v = idx % NV;
+                    const int ia = j % K, ib = (j / K) % K, ic = j / (K * K);
+                    const int li = (lb[0] + ia) + TE * (lb[1] + ib) + (D == 3 ? TE * TE * (lb[2] + ic) : 0);
+                    if (cur[i] != R(0)) atomicAdd(&sm[v][li], cur[i]);
+                }
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < TN; i += NT) {
+            const R mm = sm[D][i];
+            if (mm == R(0)) continue;
+            int g[3];
+            g[0] = bo[0] + i % TE;
+            g[1] = bo[1] + (i / TE) % TE;
+            if (D == 3) g[2] = bo[2] + i / (TE * TE);
+            const uint32_t ni = node_index<D>(g, c.nb);
+            R* dst = acc + 4 * (size_t)ni;
+#pragma unroll
+            for (int a = 0; a < D; ++a) atomicAdd(dst + a, sm[a][i]);
+            atomicAdd(dst + 3, mm);
+        }
+        if (threadIdx.x < (1 << D)) {
+            int bb[3];
+            block_coords<D, R>(blk, c, bb);
+            bool in = true;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                bb[a] += (threadIdx.x >> a) & 1;
+                if (bb[a] >= c.nb[a]) in = false;
+            }
+            if (in) {
+                const uint32_t b2 = (D == 3) ? ((uint32_t)bb[2] * c.nb[1] + bb[1]) * c.nb[0] + bb[0]
+                                             : (uint32_t)bb[1] * c.nb[0] + bb[0];
+                flags[b2] = 1u;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- grid update (Sec. 3.3)
 // One warp per active node block: v~ = ((m v) + dt f) / m + dt g, sticky walls, v~ = 0 where
 // m = 0; writes (v~, m) to the velocity grid and clears the accumulation grid and flag.
@@ -382,8 +593,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 template <int D, int ORDER, typename R>
 __global__ void __launch_bounds__(TPB) k_g2p(PState<R> in, PState<R> out, const uint32_t* __restrict__ perm,
                                              const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ tiles,
-                                             const uint32_t* __restrict__ ntiles_p, const R* __restrict__ vel,
-                                             uint32_t* __restrict__ knext, DevCfg<R> c, uint32_t* err)
+                                             const uint32_t* __restrict__ ntiles_p, uint32_t* __restrict__ tile_ctr,
+                                             const R* __restrict__ vel, uint32_t* __restrict__ knext, DevCfg<R> c,
+                                             uint32_t* err)
 {
     constexpr int K = ORDER + 1;
     constexpr int BN = (D == 3) ? 64 : 16;
@@ -392,12 +604,16 @@ __global__ void __launch_bounds__(TPB) k_g2p(PState<R> in, PState<R> out, const 
     __shared__ __align__(128) R sv[NB][BN][4];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ int s_ok;
+    __shared__ int s_tile;
     if (threadIdx.x == 0) mbar_init(&mbar, 1);
-    __syncthreads();
     unsigned phase = 0;
     const int ntiles = (int)*ntiles_p;
     const R dt_dx = c.dt * c.inv_dx;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_ctr + 1, 1u);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= ntiles) break;
         const uint32_t start = tiles[t], end = tiles[t + 1];
         const uint32_t blk = skeys[start] >> (2 * D);
         int bc[3] = {0, 0, 0};
@@ -747,8 +963,18 @@ template <typename R> struct Impl {
         if (n == 0) return cudaSuccess;
         DevCfg<R> c = HostToDev<R>::make(h, n);
         PState<R> st = state_of<R>(b, cur);
-        APIC_DISPATCH(h, (k_p2g<D, O, R><<<L.p2g_grid, TPB, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, (R*)b.acc,
-                                                                      b.flags, c, b.err, b.fallbacks)));
+        if (h.dim == 3 && h.order == 2)
+            k_p2g_cells<3, 2, R, 8><<<L.p2g_grid, 128, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc,
+                                                                b.flags, c, b.err, b.fallbacks);
+        else if (h.dim == 2 && h.order == 2)
+            k_p2g_cells<2, 2, R, 8><<<L.p2g_grid, 128, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc,
+                                                                b.flags, c, b.err, b.fallbacks);
+        else if (h.dim == 2 && h.order == 3)
+            k_p2g_cells<2, 3, R, 8><<<L.p2g_grid, 128, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc,
+                                                                b.flags, c, b.err, b.fallbacks);
+        else
+            k_p2g<3, 3, R><<<L.p2g_grid, TPB, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, (R*)b.acc, b.flags, c, b.err,
+                                                      b.fallbacks);
         return cudaGetLastError();
     }
     static cudaError_t grid_update(const HostCfg& h, const Buffers& b, const Launch& L, cudaStream_t s)
@@ -765,7 +991,7 @@ template <typename R> struct Impl {
         if (n == 0) return cudaSuccess;
         DevCfg<R> c = HostToDev<R>::make(h, n);
         PState<R> in = state_of<R>(b, cur), out = state_of<R>(b, cur ^ 1);
-        APIC_DISPATCH(h, (k_g2p<D, O, R><<<L.g2p_grid, TPB, 0, s>>>(in, out, perm, sk, b.tiles, b.ntiles,
+        APIC_DISPATCH(h, (k_g2p<D, O, R><<<L.g2p_grid, TPB, 0, s>>>(in, out, perm, sk, b.tiles, b.ntiles, b.tile_ctr,
                                                                       (const R*)b.vel, b.knext, c, b.err)));
         return cudaGetLastError();
     }
@@ -826,7 +1052,10 @@ template <typename R> struct Impl {
     {
         cudaError_t e = cudaSuccess;
         APIC_DISPATCH(h, {
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g<D, O, R>, TPB, 0);
+            if (D == 3 && O == 3)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g<D, O, R>, TPB, 0);
+            else
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g_cells<D, (D == 3 ? 2 : O), R, 8>, 128, 0);
             if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(g2p_per_sm, k_g2p<D, O, R>, TPB, 0);
         });
         return e;
