@@ -77,13 +77,14 @@ def initial_state(sc, order):
     return sc.x, sc.v, B, F
 
 
-def lib_config(w, sc, precision=32):
+def lib_config(w, sc, precision=32, p2g_kernel=0, tile=0):
     from paper_1603_06188_gb300 import apic
 
     vol = sc.dx ** 3 / w["ppc"]
     return apic.make_config(dim=3, order=w["order"], precision=precision, res=(w["res"],) * 3, dx=sc.dx,
                             dt=w["dt"], gravity=w["gravity"], boundary=w["boundary"], wall=w["order"] + 1,
-                            model="fcr", E=w["E"], nu=w["nu"], particle_mass=w["rho"] * vol, particle_volume=vol)
+                            model="fcr", E=w["E"], nu=w["nu"], particle_mass=w["rho"] * vol, particle_volume=vol,
+                            p2g_kernel=p2g_kernel, tile_particles=tile)
 
 
 def oracle_config(w, sc):
@@ -253,6 +254,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=300000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--p2g-kernel", type=int, default=0)
+    ap.add_argument("--tile", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -275,7 +278,7 @@ def main():
         w["ppc"] = args.ppc
     sc = make_scene(w, seed=rank)
     x, v, B, F = initial_state(sc, w["order"])
-    cfg = lib_config(w, sc)
+    cfg = lib_config(w, sc, p2g_kernel=args.p2g_kernel, tile=args.tile)
     sim = apic.Sim(cfg, sc.n)
     sim.upload(x, v, B, F)
     stream = sim.stream

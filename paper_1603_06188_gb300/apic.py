@@ -40,13 +40,13 @@ class Config(C.Structure):
         ("boundary", C.c_int), ("wall", C.c_int), ("model", C.c_int),
         ("E", C.c_double), ("nu", C.c_double),
         ("particle_mass", C.c_double), ("particle_volume", C.c_double),
-        ("tile_particles", C.c_int),
+        ("tile_particles", C.c_int), ("p2g_kernel", C.c_int),
     ]
 
 
 def make_config(dim=3, order=2, precision=32, transfer="apic", res=(64, 64, 64), dx=1 / 64, origin=(0, 0, 0),
                 dt=0.0, gravity=(0, 0, 0), boundary="none", wall=0, model="none", E=0.0, nu=0.0,
-                particle_mass=1.0, particle_volume=1.0, tile_particles=0) -> Config:
+                particle_mass=1.0, particle_volume=1.0, tile_particles=0, p2g_kernel=0) -> Config:
     c = Config()
     c.dim, c.order, c.precision = dim, order, precision
     c.transfer = TRANSFER[transfer] if isinstance(transfer, str) else transfer
@@ -62,6 +62,7 @@ def make_config(dim=3, order=2, precision=32, transfer="apic", res=(64, 64, 64),
     c.E, c.nu = E, nu
     c.particle_mass, c.particle_volume = particle_mass, particle_volume
     c.tile_particles = tile_particles
+    c.p2g_kernel = p2g_kernel
     return c
 
 

@@ -97,6 +97,9 @@ apic_status fill_cfg(const apic_config* in, int64_t max_particles, HostCfg* c, s
     c->mass = in->particle_mass;
     c->vol = in->particle_volume;
     c->tile = tile;
+    if (in->p2g_kernel < 0 || in->p2g_kernel > 2) { *why = "p2g_kernel must be 0, 1 or 2"; return APIC_ERR_ARG; }
+    c->p2g_kernel = in->p2g_kernel == 0 ? 1 : in->p2g_kernel;
+    if (c->p2g_kernel == 2 && in->dim == 3 && in->order == 3) { *why = "the cell-parallel P2G does not cover 3-D cubic"; return APIC_ERR_UNSUPPORTED; }
     c->key_bits = 2 * in->dim + ceil_log2(c->nblocks);
     if (c->key_bits > 32) { *why = "grid too large for 32-bit cell keys"; return APIC_ERR_UNSUPPORTED; }
     c->capacity = max_particles;
@@ -306,7 +309,7 @@ apic_status apic_create(const apic_config* cfg, int64_t max_particles, void* wor
     }
     s->L.sms = sms;
     s->L.p2g_grid = sms * (p2g_per > 0 ? p2g_per : 1);
-    s->L.p2g_cells = !(c.dim == 3 && c.order == 3);
+    s->L.p2g_cells = c.p2g_kernel == 2;
     s->L.g2p_grid = sms * (g2p_per > 0 ? g2p_per : 1);
     s->L.mom_parts = kMomParts;
     const size_t bn = c.dim == 3 ? 64 : 16;

@@ -250,7 +250,9 @@ __device__ __forceinline__ void polar3(const R* F, R* Rot)
     for (int sweep = 0; sweep < 6; ++sweep) {
         const R off = fabs(S[1]) + fabs(S[2]) + fabs(S[5]);
         const R diag = fabs(S[0]) + fabs(S[4]) + fabs(S[8]);
-        if (off <= diag * (sizeof(R) == 4 ? R(1e-8) : R(1e-17))) break;
+        // stop once the off-diagonal part is at the rounding level of the type: further
+        // rotations cannot change R beyond rounding (FP32: ~4 eps, FP64: ~1e-16)
+        if (off <= diag * (sizeof(R) == 4 ? R(5e-7) : R(1e-16))) break;
         jacobi_rot(S, V, 0, 1, 2);
         jacobi_rot(S, V, 0, 2, 1);
         jacobi_rot(S, V, 1, 2, 0);

@@ -44,6 +44,7 @@ struct HostCfg {
     int boundary, wall, model;
     double mu, lam, mass, vol;
     int tile;                    // particles per tile (power of two)
+    int p2g_kernel;              // 1 warp-segmented, 2 cell-parallel
     int key_bits;
     int nblocks;
     int64_t capacity;

@@ -963,7 +963,10 @@ template <typename R> struct Impl {
         if (n == 0) return cudaSuccess;
         DevCfg<R> c = HostToDev<R>::make(h, n);
         PState<R> st = state_of<R>(b, cur);
-        if (h.dim == 3 && h.order == 2)
+        if (!L.p2g_cells)
+            APIC_DISPATCH(h, (k_p2g<D, O, R><<<L.p2g_grid, TPB, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, (R*)b.acc,
+                                                                          b.flags, c, b.err, b.fallbacks)));
+        else if (h.dim == 3 && h.order == 2)
             k_p2g_cells<3, 2, R, 8><<<L.p2g_grid, 128, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc,
                                                                 b.flags, c, b.err, b.fallbacks);
         else if (h.dim == 2 && h.order == 2)
@@ -1052,7 +1055,7 @@ template <typename R> struct Impl {
     {
         cudaError_t e = cudaSuccess;
         APIC_DISPATCH(h, {
-            if (D == 3 && O == 3)
+            if (h.p2g_kernel != 2)
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g<D, O, R>, TPB, 0);
             else
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g_cells<D, (D == 3 ? 2 : O), R, 8>, 128, 0);

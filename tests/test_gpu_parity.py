@@ -51,12 +51,12 @@ def _ids(c):
 
 
 def run_one_step(apic, dim, order, prec, res, ppc, model="fcr", transfer="apic", dt=2e-3, gravity=None,
-                 boundary="none", wall=0, tile=0, seed=0):
+                 boundary="none", wall=0, tile=0, seed=0, p2g_kernel=0):
     sc = cube_scene(dim, res, ppc, seed=seed)
     x, v, B, F = state_for(sc, order, seed=seed)
     g = gravity if gravity is not None else (0.0,) * dim
     gc, oc, m, vol = configs(dim, order, (res,) * dim, sc.dx, precision=prec, transfer=transfer, dt=dt,
-                             gravity=g, boundary=boundary, wall=wall, model=model, tile=tile)
+                             gravity=g, boundary=boundary, wall=wall, model=model, tile=tile, p2g_kernel=p2g_kernel)
     sim = apic.Sim(gc, len(x) + 7)
     sim.upload(x, v, B, F)
     x0, v0, B0, F0 = sim.download()          # the GPU's exact input state
@@ -150,11 +150,15 @@ def test_transfer_modes_and_transfer_only(apic, transfer):
 
 
 @pytest.mark.parametrize("tile", [256, 4096])
-def test_tile_sizes_agree(apic, tile):
-    r = run_one_step(apic, 3, 2, 32, 32, 8, tile=tile)
+@pytest.mark.parametrize("p2g_kernel", [1, 2])
+@pytest.mark.parametrize("dim,order,prec", [(3, 2, 32), (2, 2, 32), (2, 3, 32), (3, 2, 64), (2, 3, 64)])
+def test_p2g_variants_and_tile_sizes_agree(apic, tile, p2g_kernel, dim, order, prec):
+    r = run_one_step(apic, dim, order, prec, 32 if dim == 3 else 64, 8 if dim == 3 else 4, tile=tile,
+                     p2g_kernel=p2g_kernel)
     x0, v0, B0, F0 = r["in"]
     gm, gmv, gf, _ = oracle.p2g(r["oc"], x0, v0, B0, F0, r["m"], r["vol"])
-    assert relerr(r["grid_p2g"][1], gmv + r["oc"].dt * gf) <= 1e-5
+    assert relerr(r["grid_p2g"][0], gm) <= TOL[prec]
+    assert relerr(r["grid_p2g"][1], gmv + r["oc"].dt * gf) <= TOL[prec]
 
 
 def test_gpu_momentum_conservation_fp32(apic):
