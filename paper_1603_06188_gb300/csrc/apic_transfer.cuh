@@ -503,6 +503,166 @@ __global__ void __launch_bounds__(128, 2) k_p2g_cells(PState<R> st, const uint32
     }
 }
 
+// ---------------------------------------------------------------- P2G, cell-interleaved
+// Threads of a warp take particles of distinct base cells of the tile (thread t serves
+// cell t mod 4^D), so at every stencil node the lanes of a warp add into distinct
+// shared-memory nodes and the shared-memory atomics do not collide; no shuffle
+// reduction is needed.  Contributions as in k_p2g.
+template <int D, int ORDER, typename R>
+__global__ void __launch_bounds__(256) k_p2g_interleaved(PState<R> st, const uint32_t* __restrict__ perm,
+                                                         const uint32_t* __restrict__ skeys,
+                                                         const uint32_t* __restrict__ tiles,
+                                                         const uint32_t* __restrict__ ntiles_p,
+                                                         uint32_t* __restrict__ tile_ctr, R* __restrict__ acc,
+                                                         uint32_t* __restrict__ flags, DevCfg<R> c, uint32_t* err,
+                                                         uint32_t* fallbacks)
+{
+    constexpr int NT = 256;
+    constexpr int K = ORDER + 1;
+    constexpr int TE = 4 + ORDER;
+    constexpr int TN = (D == 3) ? TE * TE * TE : TE * TE;
+    constexpr int NV = D + 1;
+    constexpr int NC = (D == 3) ? 64 : 16;
+    constexpr int SLOTS = NT / NC;
+    __shared__ R sm[NV][TN];
+    __shared__ uint32_t cbeg[NC], cend[NC];
+    __shared__ int s_tile;
+    const int ntiles = (int)*ntiles_p;
+    const R dt_dx = c.dt * c.inv_dx;
+    const R m = c.mass;
+    const R sC = (c.transfer == 0) ? m * c.inv_kdx : R(0);
+    const int cell = threadIdx.x % NC, slot = threadIdx.x / NC;
+    const int lb[3] = {cell & 3, (cell >> 2) & 3, (D == 3) ? (cell >> 4) : 0};
+    const int lbase = lb[0] + TE * lb[1] + (D == 3 ? TE * TE * lb[2] : 0);
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_ctr, 1u);
+        for (int i = threadIdx.x; i < NV * TN; i += NT) (&sm[0][0])[i] = R(0);
+        for (int i = threadIdx.x; i < NC; i += NT) { cbeg[i] = 0u; cend[i] = 0u; }
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= ntiles) break;
+        const uint32_t start = tiles[t], end = tiles[t + 1];
+        const uint32_t blk = skeys[start] >> (2 * D);
+        int bo[3] = {0, 0, 0};
+        block_coords<D, R>(blk, c, bo);
+#pragma unroll
+        for (int a = 0; a < D; ++a) bo[a] *= 4;
+        for (uint32_t k = start + threadIdx.x; k < end; k += NT) {
+            const uint32_t cl = skeys[k] & (NC - 1);
+            if (k == start || (skeys[k - 1] & (NC - 1)) != cl) cbeg[cl] = k;
+            if (k + 1 == end || (skeys[k + 1] & (NC - 1)) != cl) cend[cl] = k + 1;
+        }
+        __syncthreads();
+        const uint32_t kb = cbeg[cell], ke = cend[cell];
+        for (uint32_t k = kb + slot; k < ke; k += SLOTS) {
+            Particle<D, R> p;
+            const uint32_t q = perm[k];
+            load_xF<D, R>(st, q, p);
+            load_vB<D, R>(st, q, p);
+            int base[D];
+            R w[D][K], dw[D][K], fx[D];
+            bool ok = particle_stencil<D, ORDER, R>(p.o, p.cell, c, base, fx, w, dw);
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+                if (base[a] - bo[a] != lb[a]) ok = false;
+            if (!ok) {
+                set_err(err, APIC_ERRBIT_RANGE);
+                continue;
+            }
+            R mv[D], mC[D * D], T[D * D];
+#pragma unroll
+            for (int a = 0; a < D; ++a) mv[a] = m * p.v[a];
+#pragma unroll
+            for (int i = 0; i < D * D; ++i) mC[i] = sC * p.B[i];
+            if (c.model == 1) {
+                R tau[D * D];
+                stress_tau<D, R>(p.F, c.mu, c.lam, c.vol, tau, fallbacks);
+#pragma unroll
+                for (int i = 0; i < D * D; ++i) T[i] = dt_dx * tau[i];
+            } else {
+#pragma unroll
+                for (int i = 0; i < D * D; ++i) T[i] = R(0);
+            }
+            if (D == 3) {
+                // per (a, b): q_ab = m v + mC (r0, r1, .), h = T (gx, gy, .), kz = T(., ., 2) w_ab
+#pragma unroll
+                for (int ia = 0; ia < K; ++ia)
+#pragma unroll
+                    for (int ib = 0; ib < K; ++ib) {
+                        const R wab = w[0][ia] * w[1][ib];
+                        const R gx = dw[0][ia] * w[1][ib], gy = w[0][ia] * dw[1][ib];
+                        const R r0 = R(ia) - fx[0], r1 = R(ib) - fx[1];
+                        R qab[3], h[3], kz[3];
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            qab[a] = mv[a] + mC[a * 3 + 0] * r0 + mC[a * 3 + 1] * r1;
+                            h[a] = T[a * 3 + 0] * gx + T[a * 3 + 1] * gy;
+                            kz[a] = T[a * 3 + 2] * wab;
+                        }
+#pragma unroll
+                        for (int ic = 0; ic < K; ++ic) {
+                            const R wz = w[2][ic], dwz = dw[2][ic], r2 = R(ic) - fx[2];
+                            const R wv = wab * wz;
+                            const int li = lbase + ia + TE * ib + TE * TE * ic;
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) {
+                                const R qv = qab[a] + mC[a * 3 + 2] * r2;
+                                atomicAdd(&sm[a][li], wv * qv - h[a] * wz - kz[a] * dwz);
+                            }
+                            atomicAdd(&sm[3][li], wv * m);
+                        }
+                    }
+            } else {
+#pragma unroll
+                for (int ia = 0; ia < K; ++ia)
+#pragma unroll
+                    for (int ib = 0; ib < K; ++ib) {
+                        const R wv = w[0][ia] * w[1][ib];
+                        const R g0 = dw[0][ia] * w[1][ib], g1 = w[0][ia] * dw[1][ib];
+                        const R r0 = R(ia) - fx[0], r1 = R(ib) - fx[1];
+                        const int li = lbase + ia + TE * ib;
+#pragma unroll
+                        for (int a = 0; a < 2; ++a) {
+                            const R qv = mv[a] + mC[a * 2 + 0] * r0 + mC[a * 2 + 1] * r1;
+                            atomicAdd(&sm[a][li], wv * qv - (T[a * 2 + 0] * g0 + T[a * 2 + 1] * g1));
+                        }
+                        atomicAdd(&sm[2][li], wv * m);
+                    }
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < TN; i += NT) {
+            const R mm = sm[D][i];
+            if (mm == R(0)) continue;
+            int g[3];
+            g[0] = bo[0] + i % TE;
+            g[1] = bo[1] + (i / TE) % TE;
+            if (D == 3) g[2] = bo[2] + i / (TE * TE);
+            const uint32_t ni = node_index<D>(g, c.nb);
+            R* dst = acc + 4 * (size_t)ni;
+#pragma unroll
+            for (int a = 0; a < D; ++a) atomicAdd(dst + a, sm[a][i]);
+            atomicAdd(dst + 3, mm);
+        }
+        if (threadIdx.x < (1 << D)) {
+            int bb[3];
+            block_coords<D, R>(blk, c, bb);
+            bool in = true;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                bb[a] += (threadIdx.x >> a) & 1;
+                if (bb[a] >= c.nb[a]) in = false;
+            }
+            if (in) {
+                const uint32_t b2 = (D == 3) ? ((uint32_t)bb[2] * c.nb[1] + bb[1]) * c.nb[0] + bb[0]
+                                             : (uint32_t)bb[1] * c.nb[0] + bb[0];
+                flags[b2] = 1u;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- grid update (Sec. 3.3)
 // One warp per active node block: v~ = ((m v) + dt f) / m + dt g, sticky walls, v~ = 0 where
 // m = 0; writes (v~, m) to the velocity grid and clears the accumulation grid and flag.
@@ -665,44 +825,77 @@ __global__ void __launch_bounds__(TPB) k_g2p(PState<R> in, PState<R> out, const 
                 if (lb[a] < 0 || lb[a] > 3) { ok = false; lb[a] = 0; }
             }
             if (!ok) set_err(err, APIC_ERRBIT_RANGE);
+            // Separable gather: the weights are tensor products, so the sums over the
+            // stencil are taken axis by axis (innermost axis first) instead of node by node:
+            //   vp   = sum_i w v~                  = sum_a wx R_a
+            //   G    = sum_i v~ grad^w^T           (columns: dwx R_a, wx S_a, wx T_a)
+            //   Bh   = sum_i w v~ r^T, r^ = node - fx (columns: rx wx R_a, wx Y_a, wx Zc_a)
+            // with per-(a,b) sums over c and per-a sums over b.
             R vp[D], Bh[D * D], G[D * D];
 #pragma unroll
             for (int a = 0; a < D; ++a) vp[a] = R(0);
 #pragma unroll
             for (int i = 0; i < D * D; ++i) { Bh[i] = R(0); G[i] = R(0); }
+            R rw[D][K];   // (node - fx) * w per axis
 #pragma unroll
-            for (int j = 0; j < NS; ++j) {
-                const int ia = j % K, ib = (j / K) % K, ic = j / (K * K);
-                const int L0 = lb[0] + ia, L1 = lb[1] + ib, L2 = (D == 3) ? lb[2] + ic : 0;
-                const int qb = (L0 >> 2) | ((L1 >> 2) << 1) | ((L2 >> 2) << 2);
-                const int ni = (L0 & 3) | ((L1 & 3) << 2) | ((L2 & 3) << 4);
-                const R* nv = &sv[qb][ni][0];
-                R vt[D];
+            for (int a = 0; a < D; ++a)
 #pragma unroll
-                for (int a = 0; a < D; ++a) vt[a] = nv[a];
-                R wv, g[D], r[D];
-                if (D == 3) {
-                    const R wab = w[0][ia] * w[1][ib];
-                    wv = wab * w[2][ic];
-                    g[0] = dw[0][ia] * w[1][ib] * w[2][ic];
-                    g[1] = w[0][ia] * dw[1][ib] * w[2][ic];
-                    g[2] = wab * dw[2][ic];
-                    r[2] = R(ic) - fx[2];
-                } else {
-                    wv = w[0][ia] * w[1][ib];
-                    g[0] = dw[0][ia] * w[1][ib];
-                    g[1] = w[0][ia] * dw[1][ib];
+                for (int j = 0; j < K; ++j) rw[a][j] = (R(j) - fx[a]) * w[a][j];
+#pragma unroll
+            for (int ia = 0; ia < K; ++ia) {
+                R Ra[D], Sa[D], Ta[D], Ya[D], Za[D];
+#pragma unroll
+                for (int a = 0; a < D; ++a) { Ra[a] = Sa[a] = Ta[a] = Ya[a] = Za[a] = R(0); }
+#pragma unroll
+                for (int ib = 0; ib < K; ++ib) {
+                    const int L0 = lb[0] + ia, L1 = lb[1] + ib;
+                    if (D == 3) {
+                        R P[3] = {R(0), R(0), R(0)}, Q[3] = {R(0), R(0), R(0)}, Z[3] = {R(0), R(0), R(0)};
+#pragma unroll
+                        for (int ic = 0; ic < K; ++ic) {
+                            const int L2 = lb[2] + ic;
+                            const int qb = (L0 >> 2) | ((L1 >> 2) << 1) | ((L2 >> 2) << 2);
+                            const int ni = (L0 & 3) | ((L1 & 3) << 2) | ((L2 & 3) << 4);
+                            const V4<R> nv = *reinterpret_cast<const V4<R>*>(&sv[qb][ni][0]);
+                            const R vt[3] = {nv.x, nv.y, nv.z};
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) {
+                                P[a] += w[2][ic] * vt[a];
+                                Q[a] += dw[2][ic] * vt[a];
+                                Z[a] += rw[2][ic] * vt[a];
+                            }
+                        }
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            Ra[a] += w[1][ib] * P[a];
+                            Sa[a] += dw[1][ib] * P[a];
+                            Ta[a] += w[1][ib] * Q[a];
+                            Ya[a] += rw[1][ib] * P[a];
+                            Za[a] += w[1][ib] * Z[a];
+                        }
+                    } else {
+                        const int qb = (L0 >> 2) | ((L1 >> 2) << 1);
+                        const int ni = (L0 & 3) | ((L1 & 3) << 2);
+                        const V4<R> nv = *reinterpret_cast<const V4<R>*>(&sv[qb][ni][0]);
+                        const R vt[2] = {nv.x, nv.y};
+#pragma unroll
+                        for (int a = 0; a < 2; ++a) {
+                            Ra[a] += w[1][ib] * vt[a];
+                            Sa[a] += dw[1][ib] * vt[a];
+                            Ya[a] += rw[1][ib] * vt[a];
+                        }
+                    }
                 }
-                r[0] = R(ia) - fx[0];
-                r[1] = R(ib) - fx[1];
 #pragma unroll
                 for (int a = 0; a < D; ++a) {
-                    const R wva = wv * vt[a];
-                    vp[a] += wva;
-#pragma unroll
-                    for (int b = 0; b < D; ++b) {
-                        Bh[a * D + b] += wva * r[b];
-                        G[a * D + b] += vt[a] * g[b];
+                    vp[a] += w[0][ia] * Ra[a];
+                    G[a * D + 0] += dw[0][ia] * Ra[a];
+                    G[a * D + 1] += w[0][ia] * Sa[a];
+                    Bh[a * D + 0] += rw[0][ia] * Ra[a];
+                    Bh[a * D + 1] += w[0][ia] * Ya[a];
+                    if (D == 3) {
+                        G[a * D + 2] += w[0][ia] * Ta[a];
+                        Bh[a * D + 2] += w[0][ia] * Za[a];
                     }
                 }
             }
@@ -963,7 +1156,10 @@ template <typename R> struct Impl {
         if (n == 0) return cudaSuccess;
         DevCfg<R> c = HostToDev<R>::make(h, n);
         PState<R> st = state_of<R>(b, cur);
-        if (!L.p2g_cells)
+        if (h.p2g_kernel == 3)
+            APIC_DISPATCH(h, (k_p2g_interleaved<D, O, R><<<L.p2g_grid, 256, 0, s>>>(
+                                 st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc, b.flags, c, b.err, b.fallbacks)));
+        else if (!L.p2g_cells)
             APIC_DISPATCH(h, (k_p2g<D, O, R><<<L.p2g_grid, TPB, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, (R*)b.acc,
                                                                           b.flags, c, b.err, b.fallbacks)));
         else if (h.dim == 3 && h.order == 2)
@@ -1055,7 +1251,9 @@ template <typename R> struct Impl {
     {
         cudaError_t e = cudaSuccess;
         APIC_DISPATCH(h, {
-            if (h.p2g_kernel != 2)
+            if (h.p2g_kernel == 3)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g_interleaved<D, O, R>, 256, 0);
+            else if (h.p2g_kernel != 2)
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g<D, O, R>, TPB, 0);
             else
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g_cells<D, (D == 3 ? 2 : O), R, 8>, 128, 0);
