@@ -83,7 +83,7 @@ def lib_config(w, sc, precision=32, p2g_kernel=0, tile=0):
     vol = sc.dx ** 3 / w["ppc"]
     return apic.make_config(dim=3, order=w["order"], precision=precision, res=(w["res"],) * 3, dx=sc.dx,
                             dt=w["dt"], gravity=w["gravity"], boundary=w["boundary"], wall=w["order"] + 1,
-                            model="fcr", E=w["E"], nu=w["nu"], particle_mass=w["rho"] * vol, particle_volume=vol,
+                            model=w.get("model", "fcr"), E=w["E"], nu=w["nu"], particle_mass=w["rho"] * vol, particle_volume=vol,
                             p2g_kernel=p2g_kernel, tile_particles=tile)
 
 

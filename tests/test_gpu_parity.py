@@ -242,8 +242,11 @@ def test_gpu_single_particle_stability(apic):
     sim.upload(x, v, B)
     sim.step(3)
     gx, gv, gB, gF = sim.download()
-    assert relerr(gv, v) <= 1e-6
-    assert relerr(gB, B) <= 1e-5
+    # FP32 bound per step as in the affine test: B is |v| dx / |B| times smaller than the
+    # velocities it is summed from
+    eps = np.finfo(np.float32).eps
+    assert relerr(gv, v) <= 3 * 16 * eps
+    assert relerr(gB, B) <= 3 * 16 * eps * np.abs(v).max() / 32 / np.abs(B).max()
     np.testing.assert_allclose(gx, x + 3e-3 * v, atol=1e-6 / 32)
 
 
