@@ -336,10 +336,12 @@ template <typename R, int N> struct ReduceScatter<R, N, 1> {
 
 // One CTA takes tiles from a shared counter.  In a tile (sorted particles of one node
 // block) every in-block base cell's particles are a contiguous run; a group of G lanes
-// owns one cell at a time, each lane summing the full (ORDER+1)^D-node stencil of its
-// particles in registers (lanes stride the run by G, so a group's loads are contiguous).
-// The group's sums are combined by the butterfly reduce-scatter and added into the
-// shared-memory tile; the tile goes to the global grid once.  Contributions as in k_p2g.
+// takes cells from a shared-memory counter, each lane summing the full (ORDER+1)^D-node
+// stencil of its particles in registers (lanes stride the run by G, so a group's loads
+// are contiguous).  The group's sums are combined by the butterfly reduce-scatter and
+// stored (plain stores, no atomics) as that cell's stencil sums; then every tile node
+// gathers, in a fixed order, the sums of the cells whose stencils cover it, and adds the
+// result to the global grid.  Contributions as in k_p2g.
 template <int D, int ORDER, typename R, int G>
 __global__ void __launch_bounds__(128, 2) k_p2g_cells(PState<R> st, const uint32_t* __restrict__ perm,
                                                       const uint32_t* __restrict__ skeys,
@@ -357,20 +359,23 @@ __global__ void __launch_bounds__(128, 2) k_p2g_cells(PState<R> st, const uint32
     constexpr int NV = D + 1;
     constexpr int NVAL = NS * NV;
     constexpr int NC = (D == 3) ? 64 : 16;      // base cells of a node block
-    constexpr int NG = NT / G;                  // groups per CTA
-    __shared__ R sm[NV][TN];
+    extern __shared__ __align__(16) unsigned char p2g_smem[];
+    R* cellsum = reinterpret_cast<R*>(p2g_smem);   // [NC][NVAL]
     __shared__ uint32_t cbeg[NC], cend[NC];
-    __shared__ int s_tile;
+    __shared__ int s_tile, s_cell;
     const int lane = threadIdx.x & 31;
-    const int grp = threadIdx.x / G, lig = threadIdx.x % G;
-    const unsigned gmask = (G == 32) ? FULLMASK : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    const int lig = threadIdx.x % G;
+    const int leader = lane & ~(G - 1);
+    const unsigned gmask = (G == 32) ? FULLMASK : (((1u << G) - 1u) << leader);
     const int ntiles = (int)*ntiles_p;
     const R dt_dx = c.dt * c.inv_dx;
     const R m = c.mass;
     const R sC = (c.transfer == 0) ? m * c.inv_kdx : R(0);
     for (;;) {
-        if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_ctr, 1u);
-        for (int i = threadIdx.x; i < NV * TN; i += NT) (&sm[0][0])[i] = R(0);
+        if (threadIdx.x == 0) {
+            s_tile = (int)atomicAdd(tile_ctr, 1u);
+            s_cell = 0;
+        }
         for (int i = threadIdx.x; i < NC; i += NT) { cbeg[i] = 0u; cend[i] = 0u; }
         __syncthreads();
         const int t = s_tile;
@@ -388,10 +393,14 @@ __global__ void __launch_bounds__(128, 2) k_p2g_cells(PState<R> st, const uint32
             if (k + 1 == end || (skeys[k + 1] & (NC - 1)) != cl) cend[cl] = k + 1;
         }
         __syncthreads();
-        for (int cell = grp; cell < NC; cell += NG) {
+        for (;;) {
+            int cell = 0;
+            if (lig == 0) cell = atomicAdd(&s_cell, 1);
+            cell = __shfl_sync(gmask, cell, leader);
+            if (cell >= NC) break;
             const uint32_t kb = cbeg[cell], ke = cend[cell];
             if (kb >= ke) continue;   // uniform across the group
-            int lb[3] = {cell & 3, (cell >> 2) & 3, (D == 3) ? (cell >> 4) : 0};
+            const int lb[3] = {cell & 3, (cell >> 2) & 3, (D == 3) ? (cell >> 4) : 0};
             R cur[NVAL];
 #pragma unroll
             for (int i = 0; i < NVAL; ++i) cur[i] = R(0);
@@ -424,65 +433,88 @@ __global__ void __launch_bounds__(128, 2) k_p2g_cells(PState<R> st, const uint32
 #pragma unroll
                     for (int i = 0; i < D * D; ++i) T[i] = R(0);
                 }
+                if (D == 3) {
 #pragma unroll
-                for (int j = 0; j < NS; ++j) {
-                    const int ia = j % K, ib = (j / K) % K, ic = j / (K * K);
-                    R wv, g[D], r[D];
-                    if (D == 3) {
-                        const R wab = w[0][ia] * w[1][ib];
-                        wv = wab * w[2][ic];
-                        g[0] = dw[0][ia] * w[1][ib] * w[2][ic];
-                        g[1] = w[0][ia] * dw[1][ib] * w[2][ic];
-                        g[2] = wab * dw[2][ic];
-                        r[2] = R(ic) - fx[2];
-                    } else {
-                        wv = w[0][ia] * w[1][ib];
-                        g[0] = dw[0][ia] * w[1][ib];
-                        g[1] = w[0][ia] * dw[1][ib];
-                    }
-                    r[0] = R(ia) - fx[0];
-                    r[1] = R(ib) - fx[1];
+                    for (int ia = 0; ia < K; ++ia)
 #pragma unroll
-                    for (int a = 0; a < D; ++a) {
-                        R qv = mv[a];
-                        R f = R(0);
+                        for (int ib = 0; ib < K; ++ib) {
+                            const R wab = w[0][ia] * w[1][ib];
+                            const R gx = dw[0][ia] * w[1][ib], gy = w[0][ia] * dw[1][ib];
+                            const R r0 = R(ia) - fx[0], r1 = R(ib) - fx[1];
+                            R qab[3], h[3], kz[3];
 #pragma unroll
-                        for (int b = 0; b < D; ++b) {
-                            qv += mC[a * D + b] * r[b];
-                            f += T[a * D + b] * g[b];
+                            for (int a = 0; a < 3; ++a) {
+                                qab[a] = mv[a] + mC[a * 3 + 0] * r0 + mC[a * 3 + 1] * r1;
+                                h[a] = T[a * 3 + 0] * gx + T[a * 3 + 1] * gy;
+                                kz[a] = T[a * 3 + 2] * wab;
+                            }
+#pragma unroll
+                            for (int ic = 0; ic < K; ++ic) {
+                                const R wz = w[2][ic], dwz = dw[2][ic], r2 = R(ic) - fx[2];
+                                const R wv = wab * wz;
+                                const int j = ia + K * ib + K * K * ic;
+#pragma unroll
+                                for (int a = 0; a < 3; ++a) {
+                                    const R qv = qab[a] + mC[a * 3 + 2] * r2;
+                                    cur[j * NV + a] += wv * qv - h[a] * wz - kz[a] * dwz;
+                                }
+                                cur[j * NV + 3] += wv * m;
+                            }
                         }
-                        cur[j * NV + a] += wv * qv - f;
-                    }
-                    cur[j * NV + D] += wv * m;
+                } else {
+#pragma unroll
+                    for (int ia = 0; ia < K; ++ia)
+#pragma unroll
+                        for (int ib = 0; ib < K; ++ib) {
+                            const R wv = w[0][ia] * w[1][ib];
+                            const R g0 = dw[0][ia] * w[1][ib], g1 = w[0][ia] * dw[1][ib];
+                            const R r0 = R(ia) - fx[0], r1 = R(ib) - fx[1];
+                            const int j = ia + K * ib;
+#pragma unroll
+                            for (int a = 0; a < 2; ++a) {
+                                const R qv = mv[a] + mC[a * 2 + 0] * r0 + mC[a * 2 + 1] * r1;
+                                cur[j * NV + a] += wv * qv - (T[a * 2 + 0] * g0 + T[a * 2 + 1] * g1);
+                            }
+                            cur[j * NV + 2] += wv * m;
+                        }
                 }
             }
             int off = 0, cnt = NVAL;
             ReduceScatter<R, NVAL, G>::run(cur, gmask, lig, off, cnt);
             constexpr int FIN = ReduceScatter<R, NVAL, G>::FINAL;
+            R* dst = cellsum + (size_t)cell * NVAL + off;
 #pragma unroll
-            for (int i = 0; i < FIN; ++i) {
-                if (i < cnt) {
-                    const int idx = off + i;
-                    const int j = idx / NV, v = idx % NV;
-                    const int ia = j % K, ib = (j / K) % K, ic = j / (K * K);
-                    const int li = (lb[0] + ia) + TE * (lb[1] + ib) + (D == 3 ? TE * TE * (lb[2] + ic) : 0);
-                    if (cur[i] != R(0)) atomicAdd(&sm[v][li], cur[i]);
-                }
-            }
+            for (int i = 0; i < FIN; ++i)
+                if (i < cnt) dst[i] = cur[i];
         }
         __syncthreads();
+        // gather: node n of the tile collects the stencil sums of cells n - (a, b, c)
         for (int i = threadIdx.x; i < TN; i += NT) {
-            const R mm = sm[D][i];
-            if (mm == R(0)) continue;
-            int g[3];
-            g[0] = bo[0] + i % TE;
-            g[1] = bo[1] + (i / TE) % TE;
-            if (D == 3) g[2] = bo[2] + i / (TE * TE);
-            const uint32_t ni = node_index<D>(g, c.nb);
-            R* dst = acc + 4 * (size_t)ni;
+            const int n0 = i % TE, n1 = (i / TE) % TE, n2 = (D == 3) ? i / (TE * TE) : 0;
+            R sum[NV];
 #pragma unroll
-            for (int a = 0; a < D; ++a) atomicAdd(dst + a, sm[a][i]);
-            atomicAdd(dst + 3, mm);
+            for (int v = 0; v < NV; ++v) sum[v] = R(0);
+#pragma unroll
+            for (int j = 0; j < NS; ++j) {
+                const int ia = j % K, ib = (j / K) % K, ic = j / (K * K);
+                const int c0 = n0 - ia, c1 = n1 - ib, c2 = (D == 3) ? n2 - ic : 0;
+                if (c0 < 0 || c0 > 3 || c1 < 0 || c1 > 3 || c2 < 0 || c2 > 3) continue;
+                const int cl = c0 | (c1 << 2) | (c2 << 4);
+                if (cbeg[cl] >= cend[cl]) continue;
+                const R* src = cellsum + (size_t)cl * NVAL + j * NV;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) sum[v] += src[v];
+            }
+            if (sum[D] == R(0)) continue;
+            int g[3];
+            g[0] = bo[0] + n0;
+            g[1] = bo[1] + n1;
+            g[2] = bo[2] + n2;
+            const uint32_t ni = node_index<D>(g, c.nb);
+            R* gdst = acc + 4 * (size_t)ni;
+#pragma unroll
+            for (int a = 0; a < D; ++a) atomicAdd(gdst + a, sum[a]);
+            atomicAdd(gdst + 3, sum[D]);
         }
         if (threadIdx.x < (1 << D)) {
             int bb[3];
@@ -501,6 +533,12 @@ __global__ void __launch_bounds__(128, 2) k_p2g_cells(PState<R> st, const uint32
         }
         __syncthreads();
     }
+}
+
+template <int D, int ORDER, typename R> constexpr size_t p2g_cells_smem()
+{
+    return (size_t)((D == 3) ? 64 : 16) * ((D == 3) ? (ORDER + 1) * (ORDER + 1) * (ORDER + 1) : (ORDER + 1) * (ORDER + 1)) *
+           (D + 1) * sizeof(R);
 }
 
 // ---------------------------------------------------------------- P2G, cell-interleaved
@@ -1163,13 +1201,13 @@ template <typename R> struct Impl {
             APIC_DISPATCH(h, (k_p2g<D, O, R><<<L.p2g_grid, TPB, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, (R*)b.acc,
                                                                           b.flags, c, b.err, b.fallbacks)));
         else if (h.dim == 3 && h.order == 2)
-            k_p2g_cells<3, 2, R, 8><<<L.p2g_grid, 128, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc,
+            k_p2g_cells<3, 2, R, 8><<<L.p2g_grid, 128, p2g_cells_smem<3, 2, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc,
                                                                 b.flags, c, b.err, b.fallbacks);
         else if (h.dim == 2 && h.order == 2)
-            k_p2g_cells<2, 2, R, 8><<<L.p2g_grid, 128, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc,
+            k_p2g_cells<2, 2, R, 8><<<L.p2g_grid, 128, p2g_cells_smem<2, 2, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc,
                                                                 b.flags, c, b.err, b.fallbacks);
         else if (h.dim == 2 && h.order == 3)
-            k_p2g_cells<2, 3, R, 8><<<L.p2g_grid, 128, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc,
+            k_p2g_cells<2, 3, R, 8><<<L.p2g_grid, 128, p2g_cells_smem<2, 3, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc,
                                                                 b.flags, c, b.err, b.fallbacks);
         else
             k_p2g<3, 3, R><<<L.p2g_grid, TPB, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, (R*)b.acc, b.flags, c, b.err,
@@ -1255,8 +1293,14 @@ template <typename R> struct Impl {
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g_interleaved<D, O, R>, 256, 0);
             else if (h.p2g_kernel != 2)
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g<D, O, R>, TPB, 0);
-            else
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g_cells<D, (D == 3 ? 2 : O), R, 8>, 128, 0);
+            else {
+                constexpr int O2 = (D == 3 ? 2 : O);
+                e = cudaFuncSetAttribute(k_p2g_cells<D, O2, R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)p2g_cells_smem<D, O2, R>());
+                if (e == cudaSuccess)
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g_cells<D, O2, R, 8>, 128,
+                                                                      p2g_cells_smem<D, O2, R>());
+            }
             if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(g2p_per_sm, k_g2p<D, O, R>, TPB, 0);
         });
         return e;
