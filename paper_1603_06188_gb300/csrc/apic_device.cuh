@@ -304,25 +304,24 @@ __device__ __forceinline__ void polar3(const R* F, R* Rot)
             Rot[a * 3 + b] = u0[a] * V[b * 3 + 0] + u1[a] * V[b * 3 + 1] + u2[a] * V[b * 3 + 2];
 }
 
-// residual of a polar rotation: asymmetry of R^T F relative to |F| plus non-orthogonality
+// residual of a polar rotation: asymmetry of R^T F relative to |F| (R is orthonormal by
+// construction, so a wrong R shows up as a non-symmetric stretch R^T F)
 template <typename R>
 __device__ __forceinline__ R polar_residual(const R* F, const R* Rot)
 {
-    R S[9];
     R fmax = R(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fmax = fmax > fabs(F[i]) ? fmax : fabs(F[i]);
+    R asym = R(0);
+#pragma unroll
     for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) {
-            S[a * 3 + b] = Rot[0 * 3 + a] * F[0 * 3 + b] + Rot[1 * 3 + a] * F[1 * 3 + b] + Rot[2 * 3 + a] * F[2 * 3 + b];
-            fmax = fmax > fabs(F[a * 3 + b]) ? fmax : fabs(F[a * 3 + b]);
+#pragma unroll
+        for (int b = a + 1; b < 3; ++b) {
+            const R sab = Rot[0 * 3 + a] * F[0 * 3 + b] + Rot[1 * 3 + a] * F[1 * 3 + b] + Rot[2 * 3 + a] * F[2 * 3 + b];
+            const R sba = Rot[0 * 3 + b] * F[0 * 3 + a] + Rot[1 * 3 + b] * F[1 * 3 + a] + Rot[2 * 3 + b] * F[2 * 3 + a];
+            asym += fabs(sab - sba);
         }
-    R asym = fabs(S[1] - S[3]) + fabs(S[2] - S[6]) + fabs(S[5] - S[7]);
-    R orth = R(0);
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) {
-            const R g = Rot[0 * 3 + a] * Rot[0 * 3 + b] + Rot[1 * 3 + a] * Rot[1 * 3 + b] + Rot[2 * 3 + a] * Rot[2 * 3 + b];
-            orth += fabs(g - (a == b ? R(1) : R(0)));
-        }
-    return asym / (fmax > R(0) ? fmax : R(1)) + orth;
+    return asym / (fmax > R(0) ? fmax : R(1));
 }
 
 // Kirchhoff-type stress tau = V_p P(F) F^T of the fixed-corotated model

@@ -16,6 +16,9 @@ namespace apic {
 
 constexpr unsigned FULLMASK = 0xffffffffu;
 constexpr int TPB = 256;
+#ifndef APIC_P2G_GROUP
+#define APIC_P2G_GROUP 4   // lanes that share one base cell in the cell-parallel P2G
+#endif
 
 template <typename R> struct HostToDev {
     static DevCfg<R> make(const HostCfg& h, int64_t n)
@@ -404,11 +407,20 @@ __global__ void __launch_bounds__(128, 2) k_p2g_cells(PState<R> st, const uint32
             R cur[NVAL];
 #pragma unroll
             for (int i = 0; i < NVAL; ++i) cur[i] = R(0);
+            // the next particle's state is requested before the current one is processed
+            Particle<D, R> nxt;
+            if (kb + lig < ke) {
+                const uint32_t q = perm[kb + lig];
+                load_xF<D, R>(st, q, nxt);
+                load_vB<D, R>(st, q, nxt);
+            }
             for (uint32_t k = kb + lig; k < ke; k += G) {
-                Particle<D, R> p;
-                const uint32_t q = perm[k];
-                load_xF<D, R>(st, q, p);
-                load_vB<D, R>(st, q, p);
+                const Particle<D, R> p = nxt;
+                if (k + G < ke) {
+                    const uint32_t q = perm[k + G];
+                    load_xF<D, R>(st, q, nxt);
+                    load_vB<D, R>(st, q, nxt);
+                }
                 int base[D];
                 R w[D][K], dw[D][K], fx[D];
                 bool ok = particle_stencil<D, ORDER, R>(p.o, p.cell, c, base, fx, w, dw);
@@ -848,12 +860,14 @@ __global__ void __launch_bounds__(TPB) k_g2p(PState<R> in, PState<R> out, const 
         __syncthreads();
         if (!s_ok) return;
         phase ^= 1u;
+        // the next round's particle is requested before the current one is processed
+        Particle<D, R> nxt;
+        if (start + threadIdx.x < end) load_xF<D, R>(in, perm[start + threadIdx.x], nxt);
         for (uint32_t k0 = start; k0 < end; k0 += TPB) {
             const uint32_t k = k0 + threadIdx.x;
             if (k >= end) continue;
-            Particle<D, R> p;
-            const uint32_t q = perm[k];
-            load_xF<D, R>(in, q, p);
+            Particle<D, R> p = nxt;
+            if (k + TPB < end) load_xF<D, R>(in, perm[k + TPB], nxt);
             int base[D], lb[D];
             R w[D][K], dw[D][K], fx[D];
             bool ok = particle_stencil<D, ORDER, R>(p.o, p.cell, c, base, fx, w, dw);
@@ -1201,13 +1215,13 @@ template <typename R> struct Impl {
             APIC_DISPATCH(h, (k_p2g<D, O, R><<<L.p2g_grid, TPB, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, (R*)b.acc,
                                                                           b.flags, c, b.err, b.fallbacks)));
         else if (h.dim == 3 && h.order == 2)
-            k_p2g_cells<3, 2, R, 8><<<L.p2g_grid, 128, p2g_cells_smem<3, 2, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc,
+            k_p2g_cells<3, 2, R, APIC_P2G_GROUP><<<L.p2g_grid, 128, p2g_cells_smem<3, 2, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc,
                                                                 b.flags, c, b.err, b.fallbacks);
         else if (h.dim == 2 && h.order == 2)
-            k_p2g_cells<2, 2, R, 8><<<L.p2g_grid, 128, p2g_cells_smem<2, 2, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc,
+            k_p2g_cells<2, 2, R, APIC_P2G_GROUP><<<L.p2g_grid, 128, p2g_cells_smem<2, 2, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc,
                                                                 b.flags, c, b.err, b.fallbacks);
         else if (h.dim == 2 && h.order == 3)
-            k_p2g_cells<2, 3, R, 8><<<L.p2g_grid, 128, p2g_cells_smem<2, 3, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc,
+            k_p2g_cells<2, 3, R, APIC_P2G_GROUP><<<L.p2g_grid, 128, p2g_cells_smem<2, 3, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc,
                                                                 b.flags, c, b.err, b.fallbacks);
         else
             k_p2g<3, 3, R><<<L.p2g_grid, TPB, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, (R*)b.acc, b.flags, c, b.err,
@@ -1295,10 +1309,10 @@ template <typename R> struct Impl {
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g<D, O, R>, TPB, 0);
             else {
                 constexpr int O2 = (D == 3 ? 2 : O);
-                e = cudaFuncSetAttribute(k_p2g_cells<D, O2, R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                e = cudaFuncSetAttribute(k_p2g_cells<D, O2, R, APIC_P2G_GROUP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)p2g_cells_smem<D, O2, R>());
                 if (e == cudaSuccess)
-                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g_cells<D, O2, R, 8>, 128,
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g_cells<D, O2, R, APIC_P2G_GROUP>, 128,
                                                                       p2g_cells_smem<D, O2, R>());
             }
             if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(g2p_per_sm, k_g2p<D, O, R>, TPB, 0);
