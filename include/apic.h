@@ -173,6 +173,67 @@ apic_status apic_profile(apic_sim* sim, int enable);
  * Synchronising, host pointers of APIC_NPHASE entries. */
 apic_status apic_profile_read(apic_sim* sim, double ms[APIC_NPHASE], int64_t launches[APIC_NPHASE]);
 
+/* ------------------------------------------------------------------------------------
+ * Batched stepping (no counterpart in the paper): many independent simulations of the
+ * same dimension, B-spline order and precision -- each with its own grid, size, material
+ * and time step -- advanced together, one persistent kernel launch per phase over a work
+ * list that spans all members.  A member keeps its own workspace; the batch adds a
+ * workspace for the shared work lists.  While a simulation is a member, apic_p2g /
+ * apic_grid_update / apic_g2p / apic_step / apic_upload on it return APIC_ERR_ARG;
+ * apic_download, apic_download_positions and apic_momentum synchronise with the batch
+ * first.  3-D cubic members are not supported (APIC_ERR_UNSUPPORTED).
+ * ------------------------------------------------------------------------------------ */
+typedef struct apic_batch apic_batch;
+
+typedef struct {
+    int dim, order, precision;   /* shared by every member */
+    int max_sims;                /* member capacity */
+    int64_t max_particles;       /* total particles over the members */
+    int64_t max_blocks;          /* total node blocks (4^d nodes) over the members' grids */
+    int tile_particles;          /* 1024, 2048 or 4096 particles per tile; 0 = 4096 */
+    int group;                   /* lanes sharing one cell in P2G: 4 or 8; 0 = 8 */
+    int use_graph;               /* 1 = replay each step as a captured CUDA graph (needs a
+                                    non-NULL stream) */
+} apic_batch_config;
+
+apic_status apic_batch_workspace_size(const apic_batch_config* cfg, size_t* bytes);
+
+/* `workspace`: caller-owned device memory (256-byte aligned), kept until apic_batch_destroy.
+ * Errors: APIC_ERR_ARG, APIC_ERR_UNSUPPORTED, APIC_ERR_OOM (workspace too small). */
+apic_status apic_batch_create(const apic_batch_config* cfg, void* workspace, size_t workspace_bytes,
+                              void* stream, apic_batch** out);
+
+/* Removes every member (as apic_batch_remove) and frees the host-side state. */
+apic_status apic_batch_destroy(apic_batch* batch);
+
+/* Add a simulation with n > 0 particles already uploaded.  Synchronises the simulation's
+ * stream.  Errors: APIC_ERR_ARG (incompatible, empty, or already a member), APIC_ERR_OOM
+ * (member, particle or block capacity), APIC_ERR_CUDA. */
+apic_status apic_batch_add(apic_batch* batch, apic_sim* sim);
+
+/* Take a simulation out; its state is current as of the last batched step.
+ * Synchronising. */
+apic_status apic_batch_remove(apic_batch* batch, apic_sim* sim);
+
+/* n batched steps of every member (each member does exactly what apic_step(sim, 1)
+ * would).  Asynchronous on the batch's stream. */
+apic_status apic_batch_step(apic_batch* batch, int n);
+
+/* Tile size and P2G lane group for the following steps (0 keeps the current value). */
+apic_status apic_batch_set_tuning(apic_batch* batch, int tile_particles, int group);
+
+/* Autotuner: times `steps` batched steps for every candidate (tile 1024 / 2048 / 4096 x
+ * group 4 / 8), keeps the fastest and reports it.  The trial steps are real steps of the
+ * members.  Results are cached per (dim, order, precision, particle-count bucket) for the
+ * life of the process; force = 1 re-measures.  Synchronising. */
+apic_status apic_batch_autotune(apic_batch* batch, int steps, int force, int* tile_particles, int* group);
+
+/* [0] members, [1] particles, [2] batched steps done, [3] kernels launched,
+ * [4] work tiles of the last step.  Synchronising. */
+apic_status apic_batch_stats(apic_batch* batch, int64_t out[5]);
+
+const char* apic_batch_last_error(apic_batch* batch);
+
 /* Stable radix sort of 32-bit keys that allocates nothing.  The paper has no counterpart:
  * this is a service for callers that cannot allocate device memory -- a host framework
  * that owns all device memory and gives plug-ins no allocator, or a real-time loop that

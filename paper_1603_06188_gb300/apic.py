@@ -66,6 +66,16 @@ def make_config(dim=3, order=2, precision=32, transfer="apic", res=(64, 64, 64),
     return c
 
 
+class BatchConfig(C.Structure):
+    """Mirror of ``apic_batch_config``."""
+
+    _fields_ = [
+        ("dim", C.c_int), ("order", C.c_int), ("precision", C.c_int), ("max_sims", C.c_int),
+        ("max_particles", C.c_int64), ("max_blocks", C.c_int64),
+        ("tile_particles", C.c_int), ("group", C.c_int), ("use_graph", C.c_int),
+    ]
+
+
 _lib = None
 SIGNATURES = {
     "apic_workspace_size": (C.c_int, [C.POINTER(Config), C.c_int64, C.POINTER(C.c_size_t)]),
@@ -85,6 +95,16 @@ SIGNATURES = {
     "apic_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
     "apic_last_error": (C.c_char_p, [C.c_void_p]),
     "apic_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "apic_batch_workspace_size": (C.c_int, [C.POINTER(BatchConfig), C.POINTER(C.c_size_t)]),
+    "apic_batch_create": (C.c_int, [C.POINTER(BatchConfig), C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "apic_batch_destroy": (C.c_int, [C.c_void_p]),
+    "apic_batch_add": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "apic_batch_remove": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "apic_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "apic_batch_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "apic_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "apic_batch_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "apic_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "apic_sort_keys_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "apic_profile_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
 }
@@ -228,6 +248,62 @@ def apic_profile_read(sim):
     return ms, launches
 
 
+def _bcheck(st: int, batch=None):
+    if st != APIC_OK:
+        msg = load().apic_batch_last_error(batch).decode() if batch else ""
+        raise ApicError(st, msg)
+
+
+def apic_batch_workspace_size(cfg: BatchConfig) -> int:
+    out = C.c_size_t(0)
+    _bcheck(load().apic_batch_workspace_size(C.byref(cfg), C.byref(out)))
+    return out.value
+
+
+def apic_batch_create(cfg: BatchConfig, workspace_ptr: int, workspace_bytes: int, stream_ptr: int):
+    h = C.c_void_p()
+    _bcheck(load().apic_batch_create(C.byref(cfg), C.c_void_p(workspace_ptr), workspace_bytes, C.c_void_p(stream_ptr),
+                                     C.byref(h)))
+    return h
+
+
+def apic_batch_destroy(batch):
+    _bcheck(load().apic_batch_destroy(batch))
+
+
+def apic_batch_add(batch, sim):
+    _bcheck(load().apic_batch_add(batch, sim), batch)
+
+
+def apic_batch_remove(batch, sim):
+    _bcheck(load().apic_batch_remove(batch, sim), batch)
+
+
+def apic_batch_step(batch, n: int):
+    _bcheck(load().apic_batch_step(batch, n), batch)
+
+
+def apic_batch_set_tuning(batch, tile_particles: int, group: int):
+    _bcheck(load().apic_batch_set_tuning(batch, tile_particles, group), batch)
+
+
+def apic_batch_autotune(batch, steps: int, force: int = 0):
+    t = C.c_int(0)
+    g = C.c_int(0)
+    _bcheck(load().apic_batch_autotune(batch, steps, force, C.byref(t), C.byref(g)), batch)
+    return t.value, g.value
+
+
+def apic_batch_stats(batch):
+    out = np.zeros(5, dtype=np.int64)
+    _bcheck(load().apic_batch_stats(batch, _ptr(out)), batch)
+    return out
+
+
+def apic_batch_last_error(batch) -> str:
+    return load().apic_batch_last_error(batch).decode()
+
+
 # ----------------------------------------------------------------------- convenience
 class Sim:
     """One simulation: config + torch-owned device workspace + the library handle."""
@@ -331,6 +407,66 @@ class Sim:
         if getattr(self, "handle", None):
             apic_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many simulations stepped together (one persistent launch per phase).
+
+    Uses its own CUDA stream (so steps can be captured in a CUDA graph) and a torch-owned
+    workspace for the shared work lists; members keep their own workspaces."""
+
+    def __init__(self, dim: int, order: int, precision: int = 32, max_sims: int = 64, max_particles: int = 1 << 22,
+                 max_blocks: int = 1 << 20, tile_particles: int = 0, group: int = 0, use_graph: bool = True,
+                 device=None):
+        import torch
+
+        self.cfg = BatchConfig()
+        self.cfg.dim, self.cfg.order, self.cfg.precision = dim, order, precision
+        self.cfg.max_sims, self.cfg.max_particles, self.cfg.max_blocks = max_sims, max_particles, max_blocks
+        self.cfg.tile_particles, self.cfg.group, self.cfg.use_graph = tile_particles, group, 1 if use_graph else 0
+        self.device = torch.device(device or "cuda")
+        nbytes = apic_batch_workspace_size(self.cfg)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = torch.cuda.Stream(self.device)
+        self.handle = apic_batch_create(self.cfg, self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
+        self.members = []
+
+    def add(self, sim: "Sim"):
+        apic_batch_add(self.handle, sim.handle)
+        self.members.append(sim)
+
+    def remove(self, sim: "Sim"):
+        apic_batch_remove(self.handle, sim.handle)
+        self.members.remove(sim)
+
+    def step(self, n: int = 1):
+        apic_batch_step(self.handle, n)
+
+    def set_tuning(self, tile_particles: int = 0, group: int = 0):
+        apic_batch_set_tuning(self.handle, tile_particles, group)
+
+    def autotune(self, steps: int = 3, force: bool = False):
+        return apic_batch_autotune(self.handle, steps, 1 if force else 0)
+
+    def stats(self) -> dict:
+        s = apic_batch_stats(self.handle)
+        return {"members": int(s[0]), "particles": int(s[1]), "steps": int(s[2]), "kernel_launches": int(s[3]),
+                "tiles": int(s[4])}
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            apic_batch_destroy(self.handle)
+            self.handle = None
+            self.members = []
 
     def __del__(self):
         try:

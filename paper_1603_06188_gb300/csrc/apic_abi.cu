@@ -7,8 +7,12 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <chrono>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "apic.h"
@@ -17,6 +21,7 @@
 using namespace apic;
 
 struct apic_sim {
+    apic_batch* batch;     // the batch this simulation belongs to, if any
     HostCfg c;
     Buffers b;
     Launch L;
@@ -233,6 +238,13 @@ struct PhaseScope {
     }
 };
 
+apic_status batch_sync_member(apic_sim* s);
+
+#define IN_BATCH_GUARD(s)                                                                       \
+    do {                                                                                        \
+        if ((s)->batch) return fail((s), APIC_ERR_ARG, "the simulation is a member of a batch"); \
+    } while (0)
+
 #define DISPATCH(s, fn, ...) ((s)->c.precision == 32 ? fn##_f32(__VA_ARGS__) : fn##_f64(__VA_ARGS__))
 
 }  // namespace
@@ -264,6 +276,7 @@ apic_status apic_create(const apic_config* cfg, int64_t max_particles, void* wor
     if (workspace_bytes < L.total) return APIC_ERR_OOM;
     apic_sim* s = new (std::nothrow) apic_sim();
     if (!s) return APIC_ERR_OOM;
+    s->batch = nullptr;
     s->c = c;
     s->stream = (cudaStream_t)stream;
     s->cur = 0;
@@ -341,6 +354,7 @@ apic_status apic_upload(apic_sim* s, int64_t n, const double* x, const double* v
                         int on_device)
 {
     if (!s) return APIC_ERR_ARG;
+    IN_BATCH_GUARD(s);
     if (n < 0) return fail(s, APIC_ERR_ARG, "n < 0");
     if (n > s->c.capacity) return fail(s, APIC_ERR_OOM, "n exceeds the particle capacity given to apic_create");
     if (n > 0 && !x) return fail(s, APIC_ERR_ARG, "positions are required");
@@ -375,6 +389,10 @@ apic_status apic_upload(apic_sim* s, int64_t n, const double* x, const double* v
 apic_status apic_download(apic_sim* s, double* x, double* v, double* B, double* F, int on_device)
 {
     if (!s) return APIC_ERR_ARG;
+    if (s->batch) {
+        apic_status bst = batch_sync_member(s);
+        if (bst != APIC_OK) return bst;
+    }
     CK(cudaSetDevice(s->device), "cudaSetDevice");
     const int64_t n = s->n;
     const int d = s->c.dim;
@@ -400,6 +418,10 @@ apic_status apic_download(apic_sim* s, double* x, double* v, double* B, double* 
 apic_status apic_download_positions(apic_sim* s, int32_t* cell, double* offset)
 {
     if (!s || !cell || !offset) return APIC_ERR_ARG;
+    if (s->batch) {
+        apic_status bst = batch_sync_member(s);
+        if (bst != APIC_OK) return bst;
+    }
     CK(cudaSetDevice(s->device), "cudaSetDevice");
     const int64_t n = s->n;
     const int d = s->c.dim;
@@ -416,6 +438,7 @@ apic_status apic_download_positions(apic_sim* s, int32_t* cell, double* offset)
 apic_status apic_p2g(apic_sim* s)
 {
     if (!s) return APIC_ERR_ARG;
+    IN_BATCH_GUARD(s);
     if (s->phase != 0) return fail(s, APIC_ERR_ARG, "apic_p2g called twice without apic_grid_update / apic_g2p");
     CK(cudaSetDevice(s->device), "cudaSetDevice");
     const int64_t n = s->n;
@@ -446,6 +469,7 @@ apic_status apic_p2g(apic_sim* s)
 apic_status apic_grid_update(apic_sim* s)
 {
     if (!s) return APIC_ERR_ARG;
+    IN_BATCH_GUARD(s);
     if (s->phase != 1) return fail(s, APIC_ERR_ARG, "apic_grid_update must follow apic_p2g");
     CK(cudaSetDevice(s->device), "cudaSetDevice");
     {
@@ -459,6 +483,7 @@ apic_status apic_grid_update(apic_sim* s)
 apic_status apic_g2p(apic_sim* s)
 {
     if (!s) return APIC_ERR_ARG;
+    IN_BATCH_GUARD(s);
     if (s->phase != 2) return fail(s, APIC_ERR_ARG, "apic_g2p must follow apic_grid_update");
     CK(cudaSetDevice(s->device), "cudaSetDevice");
     if (s->n > 0) {
@@ -476,6 +501,7 @@ apic_status apic_g2p(apic_sim* s)
 apic_status apic_step(apic_sim* s, int nsteps)
 {
     if (!s || nsteps < 0) return APIC_ERR_ARG;
+    IN_BATCH_GUARD(s);
     for (int i = 0; i < nsteps; ++i) {
         apic_status st = apic_p2g(s);
         if (st == APIC_OK) st = apic_grid_update(s);
@@ -488,6 +514,10 @@ apic_status apic_step(apic_sim* s, int nsteps)
 apic_status apic_momentum(apic_sim* s, int where, double p[3], double l[3])
 {
     if (!s || !p || !l) return APIC_ERR_ARG;
+    if (s->batch) {
+        apic_status bst = batch_sync_member(s);
+        if (bst != APIC_OK) return bst;
+    }
     CK(cudaSetDevice(s->device), "cudaSetDevice");
     int grid_phase = 0;
     if (where == APIC_WHERE_GRID) {
@@ -608,6 +638,478 @@ const char* apic_last_error(apic_sim* s)
 {
     if (!s) return "NULL simulation";
     return s->err.c_str();
+}
+
+}  // extern "C"
+
+// ====================================================================== batched stepping
+struct apic_batch {
+    int dim, order, precision;
+    int max_sims;
+    int64_t max_particles, max_blocks;
+    int tile, group;
+    bool use_graph;
+    cudaStream_t stream;
+    int device;
+    int sms;
+    // workspace
+    void* descs;
+    SortDesc* sortdescs;
+    uint32_t *rt_sim, *ch_sim, *bbase, *counts, *scan_part, *chunk_cnt, *tile_sim, *tile_start, *ntiles, *tile_ctr, *err;
+    int64_t max_rtiles, max_chunks, max_tiles;
+    size_t desc_bytes;
+    // membership
+    std::vector<apic_sim*> members;
+    bool dirty;
+    uint32_t total_rtiles, total_chunks, total_blocks;
+    int64_t total_particles;
+    int passes;
+    int p2g_grid, g2p_grid, grid_grid;
+    int64_t steps, launches;
+    // graph
+    cudaGraphExec_t gexec;
+    bool graph_valid;
+    std::string err_msg;
+};
+
+namespace {
+
+constexpr int kBatchTiles[3] = {1024, 2048, 4096};
+
+struct BatchLayout {
+    size_t descs, sortdescs, rt_sim, ch_sim, bbase, counts, scan_part, chunk_cnt, tile_sim, tile_start, ntiles, tile_ctr,
+        err, total;
+    int64_t max_rtiles, max_chunks, max_tiles;
+};
+
+BatchLayout batch_layout(const apic_batch_config* c)
+{
+    BatchLayout L;
+    Carve cv;
+    const size_t db = c->precision == 32 ? batch_desc_bytes_f32() : batch_desc_bytes_f64();
+    L.max_rtiles = c->max_particles / 2048 + c->max_sims + 1;
+    L.max_chunks = c->max_particles / 1024 + c->max_sims + 1;
+    L.max_tiles = L.max_chunks + (c->max_particles < c->max_blocks ? c->max_particles : c->max_blocks) + 2;
+    L.descs = cv.take((size_t)c->max_sims * db);
+    L.sortdescs = cv.take((size_t)c->max_sims * sizeof(SortDesc));
+    L.rt_sim = cv.take((size_t)L.max_rtiles * 4);
+    L.ch_sim = cv.take((size_t)L.max_chunks * 4);
+    L.bbase = cv.take((size_t)(c->max_sims + 1) * 4);
+    L.counts = cv.take((size_t)256 * L.max_rtiles * 4);
+    const int64_t scan_n = 256 * L.max_rtiles > L.max_chunks ? 256 * L.max_rtiles : L.max_chunks;
+    L.scan_part = cv.take(((size_t)(scan_n + 4095) / 4096 + 2) * 4);
+    L.chunk_cnt = cv.take((size_t)L.max_chunks * 4);
+    L.tile_sim = cv.take((size_t)L.max_tiles * 4);
+    L.tile_start = cv.take((size_t)L.max_tiles * 4);
+    L.ntiles = cv.take(4);
+    L.tile_ctr = cv.take(8);
+    L.err = cv.take(4);
+    L.total = cv.cur;
+    return L;
+}
+
+apic_status batch_fail(apic_batch* b, apic_status st, const std::string& why)
+{
+    if (b) b->err_msg = why;
+    return st;
+}
+
+#define BCK(expr, where)                                                                     \
+    do {                                                                                     \
+        cudaError_t e_ = (expr);                                                             \
+        if (e_ != cudaSuccess) return batch_fail(b, APIC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// copy the device-side state parity of every member back into its host struct
+apic_status batch_pull_cur(apic_batch* b)
+{
+    const size_t n = b->members.size();
+    if (n == 0) return APIC_OK;
+    std::vector<unsigned char> h(n * b->desc_bytes);
+    BCK(cudaMemcpyAsync(h.data(), b->descs, h.size(), cudaMemcpyDeviceToHost, b->stream), "read descriptors");
+    BCK(cudaStreamSynchronize(b->stream), "synchronize");
+    const int off = b->precision == 32 ? batch_desc_cur_offset_f32() : batch_desc_cur_offset_f64();
+    for (size_t i = 0; i < n; ++i) {
+        int cur;
+        memcpy(&cur, h.data() + i * b->desc_bytes + off, sizeof(int));
+        b->members[i]->cur = cur;
+    }
+    return APIC_OK;
+}
+
+apic_status batch_rebuild(apic_batch* b)
+{
+    const size_t S = b->members.size();
+    std::vector<unsigned char> descs(S * b->desc_bytes);
+    std::vector<SortDesc> sds(S);
+    std::vector<uint32_t> rt, ch, bb(S + 1, 0);
+    uint32_t pbase = 0, rbase = 0, cbase = 0, blocks = 0;
+    int maxbits = 1;
+    for (size_t i = 0; i < S; ++i) {
+        apic_sim* m = b->members[i];
+        if (b->precision == 32) batch_make_desc_f32(m->c, m->b, m->cur, m->n, descs.data() + i * b->desc_bytes);
+        else batch_make_desc_f64(m->c, m->b, m->cur, m->n, descs.data() + i * b->desc_bytes);
+        SortDesc& d = sds[i];
+        d.knext = m->b.knext;
+        d.kb[0] = m->b.kA;
+        d.kb[1] = m->b.kB;
+        d.vb[0] = m->b.vA;
+        d.vb[1] = m->b.vB;
+        d.n = (uint32_t)m->n;
+        d.ntl = (uint32_t)radix_tiles(m->n);
+        d.nch = (uint32_t)((m->n + b->tile - 1) / b->tile);
+        d.pbase = pbase;
+        d.rbase = rbase;
+        d.cbase = cbase;
+        for (uint32_t t = 0; t < d.ntl; ++t) rt.push_back((uint32_t)i);
+        for (uint32_t t = 0; t < d.nch; ++t) ch.push_back((uint32_t)i);
+        bb[i] = blocks;
+        pbase += d.n;
+        rbase += d.ntl;
+        cbase += d.nch;
+        blocks += (uint32_t)m->c.nblocks;
+        if (m->c.key_bits > maxbits) maxbits = m->c.key_bits;
+    }
+    bb[S] = blocks;
+    if ((int64_t)rt.size() > b->max_rtiles || (int64_t)ch.size() > b->max_chunks)
+        return batch_fail(b, APIC_ERR_OOM, "batch work-list capacity exceeded");
+    b->total_rtiles = rbase;
+    b->total_chunks = cbase;
+    b->total_blocks = blocks;
+    b->total_particles = pbase;
+    b->passes = (maxbits + 7) / 8;
+    if (S > 0) {
+        BCK(cudaMemcpyAsync(b->descs, descs.data(), descs.size(), cudaMemcpyHostToDevice, b->stream), "upload descriptors");
+        BCK(cudaMemcpyAsync(b->sortdescs, sds.data(), sds.size() * sizeof(SortDesc), cudaMemcpyHostToDevice, b->stream), "upload sort descriptors");
+        if (!rt.empty()) BCK(cudaMemcpyAsync(b->rt_sim, rt.data(), rt.size() * 4, cudaMemcpyHostToDevice, b->stream), "upload tables");
+        if (!ch.empty()) BCK(cudaMemcpyAsync(b->ch_sim, ch.data(), ch.size() * 4, cudaMemcpyHostToDevice, b->stream), "upload tables");
+        BCK(cudaMemcpyAsync(b->bbase, bb.data(), bb.size() * 4, cudaMemcpyHostToDevice, b->stream), "upload tables");
+        BCK(cudaStreamSynchronize(b->stream), "synchronize");   // host vectors die at return
+    }
+    int p2g_per = 1, g2p_per = 1;
+    cudaError_t e = b->precision == 32 ? batch_setup_f32(b->dim, b->order, b->group, &p2g_per, &g2p_per)
+                                       : batch_setup_f64(b->dim, b->order, b->group, &p2g_per, &g2p_per);
+    BCK(e, "batch kernel setup");
+    b->p2g_grid = b->sms * (p2g_per > 0 ? p2g_per : 1);
+    b->g2p_grid = b->sms * (g2p_per > 0 ? g2p_per : 1);
+    b->grid_grid = b->sms * 8;
+    if (b->graph_valid) {
+        cudaGraphExecDestroy(b->gexec);
+        b->graph_valid = false;
+    }
+    b->dirty = false;
+    return APIC_OK;
+}
+
+// the kernels of one batched step
+cudaError_t batch_enqueue(apic_batch* b)
+{
+    const int kpar = (b->passes - 1) & 1;
+    cudaError_t e = batch_radix_sort(b->sortdescs, b->rt_sim, b->total_rtiles, b->passes, b->counts, b->scan_part, b->stream);
+    if (e == cudaSuccess)
+        e = batch_build_tiles(b->sortdescs, b->ch_sim, b->total_chunks, b->dim, b->tile, kpar, b->chunk_cnt, b->scan_part,
+                              b->ntiles, b->max_tiles, b->tile_sim, b->tile_start, b->err, b->tile_ctr, b->stream);
+    const int S = (int)b->members.size();
+    if (e == cudaSuccess)
+        e = b->precision == 32 ? batch_p2g_f32(b->dim, b->order, b->group, b->descs, b->tile_sim, b->tile_start, b->ntiles,
+                                               b->tile_ctr, kpar, b->p2g_grid, b->stream)
+                               : batch_p2g_f64(b->dim, b->order, b->group, b->descs, b->tile_sim, b->tile_start, b->ntiles,
+                                               b->tile_ctr, kpar, b->p2g_grid, b->stream);
+    if (e == cudaSuccess)
+        e = b->precision == 32 ? batch_grid_f32(b->dim, b->descs, b->bbase, S, b->total_blocks, b->grid_grid, b->stream)
+                               : batch_grid_f64(b->dim, b->descs, b->bbase, S, b->total_blocks, b->grid_grid, b->stream);
+    if (e == cudaSuccess)
+        e = b->precision == 32 ? batch_g2p_f32(b->dim, b->order, b->descs, b->tile_sim, b->tile_start, b->ntiles,
+                                               b->tile_ctr, kpar, b->g2p_grid, b->stream)
+                               : batch_g2p_f64(b->dim, b->order, b->descs, b->tile_sim, b->tile_start, b->ntiles,
+                                               b->tile_ctr, kpar, b->g2p_grid, b->stream);
+    if (e == cudaSuccess) e = b->precision == 32 ? batch_finish_f32(b->descs, S, b->stream) : batch_finish_f64(b->descs, S, b->stream);
+    return e;
+}
+
+int64_t batch_kernels_per_step(const apic_batch* b) { return (int64_t)b->passes * 5 + 5 + 4; }
+
+apic_status batch_run(apic_batch* b, int n)
+{
+    if (b->dirty) {
+        apic_status st = batch_rebuild(b);
+        if (st != APIC_OK) return st;
+    }
+    if (b->members.empty()) return APIC_OK;
+    BCK(cudaSetDevice(b->device), "cudaSetDevice");
+    for (int i = 0; i < n; ++i) {
+        if (b->use_graph && b->stream) {
+            if (!b->graph_valid) {
+                cudaGraph_t g;
+                BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+                cudaError_t e = batch_enqueue(b);
+                cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+                BCK(e, "capture step");
+                BCK(e2, "end capture");
+                e = cudaGraphInstantiate(&b->gexec, g, 0);
+                cudaGraphDestroy(g);
+                BCK(e, "instantiate graph");
+                b->graph_valid = true;
+            }
+            BCK(cudaGraphLaunch(b->gexec, b->stream), "graph launch");
+        } else {
+            BCK(batch_enqueue(b), "batched step");
+        }
+        b->steps += 1;
+        b->launches += batch_kernels_per_step(b);
+    }
+    return APIC_OK;
+}
+
+// (dim, order, precision, log2 of particles) -> (tile, group)
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune_cache;
+
+apic_status batch_sync_member(apic_sim* s)
+{
+    apic_batch* b = s->batch;
+    apic_status st = batch_pull_cur(b);
+    if (st != APIC_OK) return fail(s, st, b->err_msg);
+    s->keys_valid = b->steps > 0 ? true : s->keys_valid;
+    return APIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+apic_status apic_batch_workspace_size(const apic_batch_config* c, size_t* bytes)
+{
+    if (!c || !bytes) return APIC_ERR_ARG;
+    if (c->max_sims <= 0 || c->max_particles <= 0 || c->max_blocks <= 0) return APIC_ERR_ARG;
+    if (c->precision != 32 && c->precision != 64) return APIC_ERR_ARG;
+    *bytes = batch_layout(c).total;
+    return APIC_OK;
+}
+
+apic_status apic_batch_create(const apic_batch_config* c, void* workspace, size_t workspace_bytes, void* stream,
+                              apic_batch** out)
+{
+    if (!c || !out) return APIC_ERR_ARG;
+    *out = nullptr;
+    if (c->dim == 3 && c->order == 3) return APIC_ERR_UNSUPPORTED;
+    if ((c->dim != 2 && c->dim != 3) || (c->order != 2 && c->order != 3)) return APIC_ERR_ARG;
+    if (c->precision != 32 && c->precision != 64) return APIC_ERR_ARG;
+    if (c->max_sims <= 0 || c->max_particles <= 0 || c->max_blocks <= 0) return APIC_ERR_ARG;
+    const int tile = c->tile_particles == 0 ? 4096 : c->tile_particles;
+    if (tile != 1024 && tile != 2048 && tile != 4096) return APIC_ERR_ARG;
+    const int group = c->group == 0 ? 8 : c->group;
+    if (group != 4 && group != 8) return APIC_ERR_ARG;
+    if (!workspace || ((uintptr_t)workspace & 255)) return APIC_ERR_ARG;
+    BatchLayout L = batch_layout(c);
+    if (workspace_bytes < L.total) return APIC_ERR_OOM;
+    apic_batch* b = new (std::nothrow) apic_batch();
+    if (!b) return APIC_ERR_OOM;
+    b->dim = c->dim;
+    b->order = c->order;
+    b->precision = c->precision;
+    b->max_sims = c->max_sims;
+    b->max_particles = c->max_particles;
+    b->max_blocks = c->max_blocks;
+    b->tile = tile;
+    b->group = group;
+    b->use_graph = c->use_graph != 0;
+    b->stream = (cudaStream_t)stream;
+    char* base = (char*)workspace;
+    b->descs = base + L.descs;
+    b->sortdescs = (SortDesc*)(base + L.sortdescs);
+    b->rt_sim = (uint32_t*)(base + L.rt_sim);
+    b->ch_sim = (uint32_t*)(base + L.ch_sim);
+    b->bbase = (uint32_t*)(base + L.bbase);
+    b->counts = (uint32_t*)(base + L.counts);
+    b->scan_part = (uint32_t*)(base + L.scan_part);
+    b->chunk_cnt = (uint32_t*)(base + L.chunk_cnt);
+    b->tile_sim = (uint32_t*)(base + L.tile_sim);
+    b->tile_start = (uint32_t*)(base + L.tile_start);
+    b->ntiles = (uint32_t*)(base + L.ntiles);
+    b->tile_ctr = (uint32_t*)(base + L.tile_ctr);
+    b->err = (uint32_t*)(base + L.err);
+    b->max_rtiles = L.max_rtiles;
+    b->max_chunks = L.max_chunks;
+    b->max_tiles = L.max_tiles;
+    b->desc_bytes = c->precision == 32 ? batch_desc_bytes_f32() : batch_desc_bytes_f64();
+    b->dirty = true;
+    b->total_rtiles = b->total_chunks = b->total_blocks = 0;
+    b->total_particles = 0;
+    b->passes = 1;
+    b->steps = b->launches = 0;
+    b->graph_valid = false;
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->err, 0, 4, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->ntiles, 0, 4, b->stream);
+    if (e != cudaSuccess) {
+        delete b;
+        return APIC_ERR_CUDA;
+    }
+    *out = b;
+    return APIC_OK;
+}
+
+apic_status apic_batch_destroy(apic_batch* b)
+{
+    if (!b) return APIC_ERR_ARG;
+    while (!b->members.empty()) apic_batch_remove(b, b->members.back());
+    if (b->graph_valid) cudaGraphExecDestroy(b->gexec);
+    cudaStreamSynchronize(b->stream);
+    delete b;
+    return APIC_OK;
+}
+
+apic_status apic_batch_add(apic_batch* b, apic_sim* s)
+{
+    if (!b || !s) return APIC_ERR_ARG;
+    if (s->batch) return batch_fail(b, APIC_ERR_ARG, "the simulation is already a member of a batch");
+    if (s->c.dim != b->dim || s->c.order != b->order || s->c.precision != b->precision)
+        return batch_fail(b, APIC_ERR_ARG, "dim, order and precision must match the batch");
+    if (s->n <= 0) return batch_fail(b, APIC_ERR_ARG, "the simulation has no particles");
+    if (s->phase != 0) return batch_fail(b, APIC_ERR_ARG, "the simulation is in the middle of a step");
+    if ((int)b->members.size() >= b->max_sims) return batch_fail(b, APIC_ERR_OOM, "batch member capacity reached");
+    int64_t parts = 0, blocks = 0;
+    for (apic_sim* m : b->members) {
+        parts += m->n;
+        blocks += m->c.nblocks;
+    }
+    if (parts + s->n > b->max_particles) return batch_fail(b, APIC_ERR_OOM, "batch particle capacity reached");
+    if (blocks + s->c.nblocks > b->max_blocks) return batch_fail(b, APIC_ERR_OOM, "batch block capacity reached");
+    BCK(cudaSetDevice(b->device), "cudaSetDevice");
+    apic_status st = batch_pull_cur(b);   // keep the members' parity before the descriptors are rebuilt
+    if (st != APIC_OK) return st;
+    if (!s->keys_valid) {
+        cudaError_t e = s->c.precision == 32 ? keys_f32(s->c, s->b, s->cur, s->n, s->stream)
+                                             : keys_f64(s->c, s->b, s->cur, s->n, s->stream);
+        BCK(e, "keys kernel");
+        s->keys_valid = true;
+        s->launches += 1;
+    }
+    BCK(cudaStreamSynchronize(s->stream), "synchronize member stream");
+    s->batch = b;
+    b->members.push_back(s);
+    b->dirty = true;
+    return APIC_OK;
+}
+
+apic_status apic_batch_remove(apic_batch* b, apic_sim* s)
+{
+    if (!b || !s || s->batch != b) return APIC_ERR_ARG;
+    apic_status st = batch_pull_cur(b);
+    if (st != APIC_OK) return st;
+    for (size_t i = 0; i < b->members.size(); ++i)
+        if (b->members[i] == s) {
+            b->members.erase(b->members.begin() + (long)i);
+            break;
+        }
+    s->batch = nullptr;
+    s->phase = 0;
+    if (b->steps > 0) {
+        const int kpar = (b->passes - 1) & 1;
+        s->skeys = kpar ? s->b.kB : s->b.kA;
+        s->perm = kpar ? s->b.vB : s->b.vA;
+        s->keys_valid = true;
+    }
+    b->dirty = true;
+    return APIC_OK;
+}
+
+apic_status apic_batch_step(apic_batch* b, int n)
+{
+    if (!b || n < 0) return APIC_ERR_ARG;
+    return batch_run(b, n);
+}
+
+apic_status apic_batch_set_tuning(apic_batch* b, int tile, int group)
+{
+    if (!b) return APIC_ERR_ARG;
+    if (tile != 0 && tile != 1024 && tile != 2048 && tile != 4096) return APIC_ERR_ARG;
+    if (group != 0 && group != 4 && group != 8) return APIC_ERR_ARG;
+    if (tile) b->tile = tile;
+    if (group) b->group = group;
+    b->dirty = true;
+    return APIC_OK;
+}
+
+apic_status apic_batch_autotune(apic_batch* b, int steps, int force, int* tile_out, int* group_out)
+{
+    if (!b || steps <= 0) return APIC_ERR_ARG;
+    int64_t parts = 0;
+    for (apic_sim* m : b->members) parts += m->n;
+    int bucket = 0;
+    while (((int64_t)1 << bucket) < parts) ++bucket;
+    const auto key = std::make_tuple(b->dim, b->order, b->precision, bucket);
+    if (!force) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            apic_batch_set_tuning(b, it->second.first, it->second.second);
+            if (tile_out) *tile_out = b->tile;
+            if (group_out) *group_out = b->group;
+            return APIC_OK;
+        }
+    }
+    if (b->members.empty()) return APIC_OK;
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0), "event");
+    BCK(cudaEventCreate(&e1), "event");
+    float best = 1e30f;
+    int bt = b->tile, bg = b->group;
+    const int groups[2] = {4, 8};
+    for (int tile : kBatchTiles)
+        for (int group : groups) {
+            apic_batch_set_tuning(b, tile, group);
+            apic_status st = batch_run(b, 1);   // warm-up (and graph capture)
+            if (st != APIC_OK) return st;
+            BCK(cudaEventRecord(e0, b->stream), "event record");
+            st = batch_run(b, steps);
+            if (st != APIC_OK) return st;
+            BCK(cudaEventRecord(e1, b->stream), "event record");
+            BCK(cudaEventSynchronize(e1), "event sync");
+            float ms = 0.f;
+            BCK(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+            if (ms < best) {
+                best = ms;
+                bt = tile;
+                bg = group;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    apic_batch_set_tuning(b, bt, bg);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = std::make_pair(bt, bg);
+    }
+    if (tile_out) *tile_out = bt;
+    if (group_out) *group_out = bg;
+    return APIC_OK;
+}
+
+apic_status apic_batch_stats(apic_batch* b, int64_t out[5])
+{
+    if (!b || !out) return APIC_ERR_ARG;
+    uint32_t nt = 0, e = 0;
+    BCK(cudaMemcpyAsync(&nt, b->ntiles, 4, cudaMemcpyDeviceToHost, b->stream), "read tile count");
+    BCK(cudaMemcpyAsync(&e, b->err, 4, cudaMemcpyDeviceToHost, b->stream), "read error word");
+    BCK(cudaStreamSynchronize(b->stream), "synchronize");
+    int64_t parts = 0;
+    for (apic_sim* m : b->members) parts += m->n;
+    out[0] = (int64_t)b->members.size();
+    out[1] = parts;
+    out[2] = b->steps;
+    out[3] = b->launches;
+    out[4] = nt;
+    if (e) return batch_fail(b, APIC_ERR_OOM, "batch tile capacity exceeded");
+    return APIC_OK;
+}
+
+const char* apic_batch_last_error(apic_batch* b)
+{
+    if (!b) return "NULL batch";
+    return b->err_msg.c_str();
 }
 
 }  // extern "C"

@@ -1,0 +1,244 @@
+// apic_batch.cuh -- batched form of the step: many independent simulations (same dim,
+// B-spline order and precision; their own grids, sizes and material constants) advanced
+// together, one persistent launch per phase.  Work items carry their simulation's index;
+// each CTA loads that simulation's descriptor (constants and buffer pointers) and runs the
+// same per-tile code as a single simulation.  Included after apic_transfer.cuh.
+#pragma once
+
+#include <stddef.h>
+
+#include "apic_transfer.cuh"
+
+namespace apic {
+
+template <typename R> struct SimDesc {
+    DevCfg<R> c;
+    PState<R> st[2];        // the two copies of the particle state
+    uint32_t* knext;        // keys of the current order (sort input)
+    uint32_t* kb[2];        // radix ping-pong keys
+    uint32_t* vb[2];        // radix ping-pong indices
+    R* acc;
+    R* vel;
+    uint32_t* flags;
+    uint32_t* err;
+    uint32_t* fallbacks;
+    int cur;                // copy holding the particles; flipped on the device after each step
+    int pad_;
+};
+
+template <typename R> SimDesc<R> make_desc(const HostCfg& h, const Buffers& b, int cur, int64_t n)
+{
+    SimDesc<R> d;
+    d.c = HostToDev<R>::make(h, n);
+    d.st[0] = state_of<R>(b, 0);
+    d.st[1] = state_of<R>(b, 1);
+    d.knext = b.knext;
+    d.kb[0] = b.kA;
+    d.kb[1] = b.kB;
+    d.vb[0] = b.vA;
+    d.vb[1] = b.vB;
+    d.acc = (R*)b.acc;
+    d.vel = (R*)b.vel;
+    d.flags = b.flags;
+    d.err = b.err;
+    d.fallbacks = b.fallbacks;
+    d.cur = cur;
+    d.pad_ = 0;
+    return d;
+}
+
+// copy a descriptor into shared memory with the whole CTA (caller synchronises)
+template <typename R> __device__ __forceinline__ void load_desc(SimDesc<R>* dst, const SimDesc<R>* src, int nthreads)
+{
+    static_assert(sizeof(SimDesc<R>) % 4 == 0, "descriptor is copied as 32-bit words");
+    const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+    uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(SimDesc<R>) / 4); i += nthreads) d[i] = s[i];
+}
+
+// end of a simulation's tile: the next tile of the same simulation starts it, else its n
+__device__ __forceinline__ uint32_t tile_end(const uint32_t* tile_sim, const uint32_t* tile_start, int t, int ntiles,
+                                             uint32_t sim, uint32_t n)
+{
+    return (t + 1 < ntiles && tile_sim[t + 1] == sim) ? tile_start[t + 1] : n;
+}
+
+template <int D, int ORDER, typename R, int G>
+__global__ void __launch_bounds__(128, 2) kb_p2g_cells(SimDesc<R>* __restrict__ descs,
+                                                       const uint32_t* __restrict__ tile_sim,
+                                                       const uint32_t* __restrict__ tile_start,
+                                                       const uint32_t* __restrict__ ntiles_p,
+                                                       uint32_t* __restrict__ tile_ctr, int kpar)
+{
+    constexpr int NC = (D == 3) ? 64 : 16;
+    extern __shared__ __align__(16) unsigned char p2g_smem[];
+    R* cellsum = reinterpret_cast<R*>(p2g_smem);
+    __shared__ uint32_t cbeg[NC], cend[NC];
+    __shared__ int s_tile, s_cell;
+    __shared__ __align__(16) SimDesc<R> sd;
+    const int ntiles = (int)*ntiles_p;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_tile = (int)atomicAdd(tile_ctr, 1u);
+            s_cell = 0;
+        }
+        for (int i = threadIdx.x; i < NC; i += 128) { cbeg[i] = 0u; cend[i] = 0u; }
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= ntiles) break;
+        const uint32_t sim = tile_sim[t];
+        load_desc<R>(&sd, descs + sim, 128);
+        __syncthreads();
+        const uint32_t start = tile_start[t];
+        const uint32_t end = tile_end(tile_sim, tile_start, t, ntiles, sim, (uint32_t)sd.c.n);
+        p2g_cells_tile<D, ORDER, R, G>(sd.st[sd.cur], sd.vb[kpar], sd.kb[kpar], start, end, sd.acc, sd.flags, sd.c,
+                                       sd.err, sd.fallbacks, cellsum, cbeg, cend, &s_cell);
+    }
+}
+
+template <int D, int ORDER, typename R>
+__global__ void __launch_bounds__(TPB) kb_g2p(SimDesc<R>* __restrict__ descs, const uint32_t* __restrict__ tile_sim,
+                                              const uint32_t* __restrict__ tile_start,
+                                              const uint32_t* __restrict__ ntiles_p, uint32_t* __restrict__ tile_ctr,
+                                              int kpar)
+{
+    constexpr int BN = (D == 3) ? 64 : 16;
+    constexpr int NB = 1 << D;
+    __shared__ __align__(128) R sv[NB][BN][4];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ int s_ok;
+    __shared__ int s_tile;
+    __shared__ __align__(16) SimDesc<R> sd;
+    if (threadIdx.x == 0) mbar_init(&mbar, 1);
+    unsigned phase = 0;
+    const int ntiles = (int)*ntiles_p;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_ctr + 1, 1u);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= ntiles) break;
+        const uint32_t sim = tile_sim[t];
+        load_desc<R>(&sd, descs + sim, TPB);
+        __syncthreads();
+        const uint32_t start = tile_start[t];
+        const uint32_t end = tile_end(tile_sim, tile_start, t, ntiles, sim, (uint32_t)sd.c.n);
+        if (!g2p_tile<D, ORDER, R>(sd.st[sd.cur], sd.st[sd.cur ^ 1], sd.vb[kpar], sd.kb[kpar], start, end, sd.vel,
+                                   sd.knext, sd.c, sd.err, sv, &mbar, phase, &s_ok))
+            return;
+    }
+}
+
+// one warp per node block of any member; bbase[s] = first global block of simulation s
+template <int D, typename R>
+__global__ void __launch_bounds__(TPB) kb_grid_update(SimDesc<R>* __restrict__ descs, const uint32_t* __restrict__ bbase,
+                                                      int nsims, uint32_t total_blocks)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t gw = (blockIdx.x * TPB + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * TPB) >> 5;
+    for (uint32_t gb = gw; gb < total_blocks; gb += nw) {
+        int lo = 0, hi = nsims - 1;   // last s with bbase[s] <= gb
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (bbase[mid] <= gb) lo = mid;
+            else hi = mid - 1;
+        }
+        const SimDesc<R>& d = descs[lo];
+        grid_update_block<D, R>(d.acc, d.vel, d.flags, d.c, (int)(gb - bbase[lo]), lane);
+    }
+}
+
+template <typename R> __global__ void kb_finish(SimDesc<R>* __restrict__ descs, int nsims)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nsims) descs[s].cur ^= 1;
+}
+
+template <typename R> struct BatchImpl {
+    template <int D, int O, int G> static cudaError_t setup_one(int* p2g_per_sm, int* g2p_per_sm)
+    {
+        const int smem = (int)p2g_cells_smem<D, O, R>();
+        cudaError_t e = cudaFuncSetAttribute(kb_p2g_cells<D, O, R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, kb_p2g_cells<D, O, R, G>, 128, smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(g2p_per_sm, kb_g2p<D, O, R>, TPB, 0);
+        return e;
+    }
+    static cudaError_t setup(int dim, int order, int group, int* p2g_per_sm, int* g2p_per_sm)
+    {
+        if (dim == 3 && order == 2) return group == 8 ? setup_one<3, 2, 8>(p2g_per_sm, g2p_per_sm) : setup_one<3, 2, 4>(p2g_per_sm, g2p_per_sm);
+        if (dim == 2 && order == 2) return group == 8 ? setup_one<2, 2, 8>(p2g_per_sm, g2p_per_sm) : setup_one<2, 2, 4>(p2g_per_sm, g2p_per_sm);
+        if (dim == 2 && order == 3) return group == 8 ? setup_one<2, 3, 8>(p2g_per_sm, g2p_per_sm) : setup_one<2, 3, 4>(p2g_per_sm, g2p_per_sm);
+        return cudaErrorInvalidValue;
+    }
+    template <int D, int O, int G>
+    static void p2g_one(void* descs, const uint32_t* ts, const uint32_t* tst, const uint32_t* nt, uint32_t* ctr, int kpar,
+                        int grid, cudaStream_t s)
+    {
+        kb_p2g_cells<D, O, R, G><<<grid, 128, p2g_cells_smem<D, O, R>(), s>>>((SimDesc<R>*)descs, ts, tst, nt, ctr, kpar);
+    }
+    static cudaError_t p2g(int dim, int order, int group, void* descs, const uint32_t* ts, const uint32_t* tst,
+                           const uint32_t* nt, uint32_t* ctr, int kpar, int grid, cudaStream_t s)
+    {
+        if (dim == 3 && order == 2) { if (group == 8) p2g_one<3, 2, 8>(descs, ts, tst, nt, ctr, kpar, grid, s); else p2g_one<3, 2, 4>(descs, ts, tst, nt, ctr, kpar, grid, s); }
+        else if (dim == 2 && order == 2) { if (group == 8) p2g_one<2, 2, 8>(descs, ts, tst, nt, ctr, kpar, grid, s); else p2g_one<2, 2, 4>(descs, ts, tst, nt, ctr, kpar, grid, s); }
+        else if (dim == 2 && order == 3) { if (group == 8) p2g_one<2, 3, 8>(descs, ts, tst, nt, ctr, kpar, grid, s); else p2g_one<2, 3, 4>(descs, ts, tst, nt, ctr, kpar, grid, s); }
+        else return cudaErrorInvalidValue;
+        return cudaGetLastError();
+    }
+    static cudaError_t grid(int dim, void* descs, const uint32_t* bbase, int nsims, uint32_t total_blocks, int grid,
+                            cudaStream_t s)
+    {
+        if (dim == 3) kb_grid_update<3, R><<<grid, TPB, 0, s>>>((SimDesc<R>*)descs, bbase, nsims, total_blocks);
+        else kb_grid_update<2, R><<<grid, TPB, 0, s>>>((SimDesc<R>*)descs, bbase, nsims, total_blocks);
+        return cudaGetLastError();
+    }
+    static cudaError_t g2p(int dim, int order, void* descs, const uint32_t* ts, const uint32_t* tst, const uint32_t* nt,
+                           uint32_t* ctr, int kpar, int grid, cudaStream_t s)
+    {
+        SimDesc<R>* d = (SimDesc<R>*)descs;
+        if (dim == 3 && order == 2) kb_g2p<3, 2, R><<<grid, TPB, 0, s>>>(d, ts, tst, nt, ctr, kpar);
+        else if (dim == 2 && order == 2) kb_g2p<2, 2, R><<<grid, TPB, 0, s>>>(d, ts, tst, nt, ctr, kpar);
+        else if (dim == 2 && order == 3) kb_g2p<2, 3, R><<<grid, TPB, 0, s>>>(d, ts, tst, nt, ctr, kpar);
+        else return cudaErrorInvalidValue;
+        return cudaGetLastError();
+    }
+    static cudaError_t finish(void* descs, int nsims, cudaStream_t s)
+    {
+        kb_finish<R><<<(nsims + 255) / 256, 256, 0, s>>>((SimDesc<R>*)descs, nsims);
+        return cudaGetLastError();
+    }
+};
+
+#define APIC_DEFINE_BATCH(R, SFX)                                                                              \
+    size_t batch_desc_bytes_##SFX() { return sizeof(SimDesc<R>); }                                            \
+    void batch_make_desc_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, void* out)             \
+    {                                                                                                          \
+        *reinterpret_cast<SimDesc<R>*>(out) = make_desc<R>(c, b, cur, n);                                      \
+    }                                                                                                          \
+    cudaError_t batch_setup_##SFX(int dim, int order, int group, int* p, int* g)                              \
+    {                                                                                                          \
+        return BatchImpl<R>::setup(dim, order, group, p, g);                                                   \
+    }                                                                                                          \
+    cudaError_t batch_p2g_##SFX(int dim, int order, int group, void* descs, const uint32_t* ts,              \
+                                const uint32_t* tst, const uint32_t* nt, uint32_t* ctr, int kpar, int grid,    \
+                                cudaStream_t s)                                                                \
+    {                                                                                                          \
+        return BatchImpl<R>::p2g(dim, order, group, descs, ts, tst, nt, ctr, kpar, grid, s);                   \
+    }                                                                                                          \
+    cudaError_t batch_grid_##SFX(int dim, void* descs, const uint32_t* bbase, int nsims, uint32_t tb, int grid, \
+                                 cudaStream_t s)                                                               \
+    {                                                                                                          \
+        return BatchImpl<R>::grid(dim, descs, bbase, nsims, tb, grid, s);                                      \
+    }                                                                                                          \
+    cudaError_t batch_g2p_##SFX(int dim, int order, void* descs, const uint32_t* ts, const uint32_t* tst,     \
+                                const uint32_t* nt, uint32_t* ctr, int kpar, int grid, cudaStream_t s)         \
+    {                                                                                                          \
+        return BatchImpl<R>::g2p(dim, order, descs, ts, tst, nt, ctr, kpar, grid, s);                          \
+    }                                                                                                          \
+    cudaError_t batch_finish_##SFX(void* descs, int nsims, cudaStream_t s)                                    \
+    {                                                                                                          \
+        return BatchImpl<R>::finish(descs, nsims, s);                                                          \
+    }                                                                                                          \
+    int batch_desc_cur_offset_##SFX() { return (int)offsetof(SimDesc<R>, cur); }
+
+}  // namespace apic

@@ -50,6 +50,19 @@ struct HostCfg {
     int64_t capacity;
 };
 
+// per-simulation view of the sort buffers, for the batched sort (apic_sort.cu)
+struct SortDesc {
+    const uint32_t* knext;
+    uint32_t* kb[2];
+    uint32_t* vb[2];
+    uint32_t n;       // particles
+    uint32_t ntl;     // radix tiles
+    uint32_t pbase;   // particles of the simulations before this one
+    uint32_t rbase;   // radix tiles of the simulations before this one
+    uint32_t cbase;   // tile-list chunks of the simulations before this one
+    uint32_t nch;     // tile-list chunks
+};
+
 // sort / tiles (apic_sort.cu)
 int radix_tiles(int64_t n);
 size_t scan_partials_needed(int64_t n);
@@ -60,6 +73,12 @@ cudaError_t build_tiles(const Buffers& b, const uint32_t* skeys, int64_t n, int 
                         int64_t max_tiles, cudaStream_t s);
 cudaError_t exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* part,
                            uint32_t* total, cudaStream_t s);
+cudaError_t batch_radix_sort(const SortDesc* sd, const uint32_t* rt_sim, uint32_t total_rtiles, int passes,
+                             uint32_t* counts, uint32_t* part, cudaStream_t s);
+cudaError_t batch_build_tiles(const SortDesc* sd, const uint32_t* ch_sim, uint32_t total_chunks, int dim, int tile,
+                              int kpar, uint32_t* cnt, uint32_t* part, uint32_t* ntiles, int64_t max_tiles,
+                              uint32_t* tile_sim, uint32_t* tile_start, uint32_t* err, uint32_t* tile_ctr,
+                              cudaStream_t s);
 
 // transfer kernels (apic_transfer_f32.cu / apic_transfer_f64.cu): one set per real type
 struct Launch {
@@ -87,7 +106,24 @@ struct Launch {
                                  cudaStream_t s);                                                               \
     cudaError_t occupancy_##SFX(const HostCfg& c, int* p2g_per_sm, int* g2p_per_sm);
 
+#define APIC_DECLARE_BATCH(SFX)                                                                              \
+    size_t batch_desc_bytes_##SFX();                                                                          \
+    void batch_make_desc_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, void* out);            \
+    cudaError_t batch_setup_##SFX(int dim, int order, int group, int* p2g_per_sm, int* g2p_per_sm);           \
+    cudaError_t batch_p2g_##SFX(int dim, int order, int group, void* descs, const uint32_t* tile_sim,         \
+                                const uint32_t* tile_start, const uint32_t* ntiles, uint32_t* ctr, int kpar,  \
+                                int grid, cudaStream_t s);                                                     \
+    cudaError_t batch_grid_##SFX(int dim, void* descs, const uint32_t* bbase, int nsims, uint32_t total_blocks, \
+                                 int grid, cudaStream_t s);                                                    \
+    cudaError_t batch_g2p_##SFX(int dim, int order, void* descs, const uint32_t* tile_sim,                    \
+                                const uint32_t* tile_start, const uint32_t* ntiles, uint32_t* ctr, int kpar,  \
+                                int grid, cudaStream_t s);                                                     \
+    cudaError_t batch_finish_##SFX(void* descs, int nsims, cudaStream_t s);                                   \
+    int batch_desc_cur_offset_##SFX();
+
 APIC_DECLARE_PRECISION(f32)
 APIC_DECLARE_PRECISION(f64)
+APIC_DECLARE_BATCH(f32)
+APIC_DECLARE_BATCH(f64)
 
 }  // namespace apic

@@ -29,17 +29,16 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return m;
 }
 
-// Per-tile digit histogram.  Warp w of tile t owns keys [t*RTILE + w*256, +256), walked in
+// Per-tile digit histogram.  Warp w of tile lt owns keys [lt*RTILE + w*256, +256), walked in
 // rounds of 32 (the same order the scatter uses).  Same-digit lanes are merged with
 // match.any so the shared-memory counter sees one add per distinct digit.
-__global__ void __launch_bounds__(RT) k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
-                                                   int ntiles, uint32_t* __restrict__ counts)
+__device__ __forceinline__ void radix_hist_tile(const uint32_t* __restrict__ keys, int64_t n, int64_t lt, int shift,
+                                                uint32_t* h)
 {
-    __shared__ uint32_t h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t base = (int64_t)blockIdx.x * RTILE + w * (RI * 32);
+    const int64_t base = lt * RTILE + w * (RI * 32);
 #pragma unroll
     for (int r = 0; r < RI; ++r) {
         const int64_t idx = base + r * 32 + lane;
@@ -49,22 +48,27 @@ __global__ void __launch_bounds__(RT) k_radix_hist(const uint32_t* __restrict__ 
         if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
+}
+
+__global__ void __launch_bounds__(RT) k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                                                   int ntiles, uint32_t* __restrict__ counts)
+{
+    __shared__ uint32_t h[256];
+    radix_hist_tile(keys, n, blockIdx.x, shift, h);
     counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
 // Stable scatter: rank = (global start of this digit in this tile) + (same digit in earlier
-// warps of the tile) + (same digit earlier in this warp).
-__global__ void __launch_bounds__(RT) k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                                                      uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
-                                                      int shift, int ntiles, const uint32_t* __restrict__ offsets)
+// warps of the tile) + (same digit earlier in this warp).  goff[d] (shared) holds the first
+// output slot of digit d for this tile.
+__device__ __forceinline__ void radix_scatter_tile(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                   uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
+                                                   int64_t lt, int shift, const uint32_t* goff, uint32_t (*wc)[256])
 {
-    __shared__ uint32_t wc[RW][256];
-    __shared__ uint32_t goff[256];
     for (int i = threadIdx.x; i < RW * 256; i += RT) (&wc[0][0])[i] = 0;
-    goff[threadIdx.x] = offsets[(int64_t)threadIdx.x * ntiles + blockIdx.x];
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t base = (int64_t)blockIdx.x * RTILE + w * (RI * 32);
+    const int64_t base = lt * RTILE + w * (RI * 32);
     uint32_t key[RI], val[RI], lr[RI];
     unsigned dig[RI];
 #pragma unroll
@@ -103,6 +107,16 @@ __global__ void __launch_bounds__(RT) k_radix_scatter(const uint32_t* __restrict
             vout[pos] = val[r];
         }
     }
+}
+
+__global__ void __launch_bounds__(RT) k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                      uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
+                                                      int shift, int ntiles, const uint32_t* __restrict__ offsets)
+{
+    __shared__ uint32_t wc[RW][256];
+    __shared__ uint32_t goff[256];
+    goff[threadIdx.x] = offsets[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+    radix_scatter_tile(kin, vin, kout, vout, n, blockIdx.x, shift, goff, wc);
 }
 
 // ---------------------------------------------------------------- exclusive scan
@@ -191,10 +205,9 @@ __device__ __forceinline__ bool is_head(const uint32_t* skeys, int64_t k, int64_
     return k == chunk_start || (skeys[k] >> sh) != (skeys[k - 1] >> sh);
 }
 
-__global__ void __launch_bounds__(256) k_tile_count(const uint32_t* __restrict__ skeys, int64_t n, int sh, int tile,
-                                                    uint32_t* __restrict__ cnt)
+__device__ __forceinline__ uint32_t count_heads(const uint32_t* __restrict__ skeys, int64_t n, int sh, int tile,
+                                                int64_t cs, uint32_t* first_local)
 {
-    const int64_t cs = (int64_t)blockIdx.x * tile;
     const int per = tile / 256;
     const int64_t k0 = cs + (int64_t)threadIdx.x * per;
     uint32_t c = 0;
@@ -204,6 +217,14 @@ __global__ void __launch_bounds__(256) k_tile_count(const uint32_t* __restrict__
     }
     uint32_t ex;
     const uint32_t tot = block_excl_scan(c, ex);
+    if (first_local) *first_local = ex;
+    return tot;
+}
+
+__global__ void __launch_bounds__(256) k_tile_count(const uint32_t* __restrict__ skeys, int64_t n, int sh, int tile,
+                                                    uint32_t* __restrict__ cnt)
+{
+    const uint32_t tot = count_heads(skeys, n, sh, tile, (int64_t)blockIdx.x * tile, nullptr);
     if (threadIdx.x == 0) cnt[blockIdx.x] = tot;
 }
 
@@ -216,13 +237,8 @@ __global__ void __launch_bounds__(256) k_tile_write(const uint32_t* __restrict__
     const int64_t cs = (int64_t)blockIdx.x * tile;
     const int per = tile / 256;
     const int64_t k0 = cs + (int64_t)threadIdx.x * per;
-    uint32_t c = 0;
-    for (int i = 0; i < per; ++i) {
-        const int64_t k = k0 + i;
-        if (k < n && is_head(skeys, k, cs, sh)) ++c;
-    }
     uint32_t ex;
-    const uint32_t tot = block_excl_scan(c, ex);
+    count_heads(skeys, n, sh, tile, cs, &ex);
     uint32_t pos = off[blockIdx.x] + ex;
     for (int i = 0; i < per; ++i) {
         const int64_t k = k0 + i;
@@ -235,7 +251,74 @@ __global__ void __launch_bounds__(256) k_tile_write(const uint32_t* __restrict__
         const uint32_t nt = *ntiles;
         if ((int64_t)nt < max_tiles) tiles[nt] = (uint32_t)n;
         else atomicOr(err, APIC_ERRBIT_CAPACITY);
-        (void)tot;
+    }
+}
+
+// ---------------------------------------------------------------- batched forms
+// Work item -> simulation tables (rt_sim per radix tile, ch_sim per chunk) are built on the
+// host when membership changes.  Counts of all simulations sit in one array laid out
+// [sim][digit][tile], so one exclusive scan over it gives every simulation's offsets shifted
+// by the particles of the simulations before it (pbase), which the scatter subtracts.
+__global__ void __launch_bounds__(RT) kb_radix_hist(const SortDesc* __restrict__ sd, const uint32_t* __restrict__ rt_sim,
+                                                    int shift, int pass, uint32_t* __restrict__ counts)
+{
+    __shared__ uint32_t h[256];
+    const SortDesc& d = sd[rt_sim[blockIdx.x]];
+    const int64_t lt = (int64_t)blockIdx.x - d.rbase;
+    const uint32_t* keys = pass == 0 ? d.knext : d.kb[(pass - 1) & 1];
+    radix_hist_tile(keys, d.n, lt, shift, h);
+    counts[(int64_t)256 * d.rbase + (int64_t)threadIdx.x * d.ntl + lt] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(RT) kb_radix_scatter(const SortDesc* __restrict__ sd, const uint32_t* __restrict__ rt_sim,
+                                                       int shift, int pass, const uint32_t* __restrict__ offsets)
+{
+    __shared__ uint32_t wc[RW][256];
+    __shared__ uint32_t goff[256];
+    const SortDesc& d = sd[rt_sim[blockIdx.x]];
+    const int64_t lt = (int64_t)blockIdx.x - d.rbase;
+    goff[threadIdx.x] = offsets[(int64_t)256 * d.rbase + (int64_t)threadIdx.x * d.ntl + lt] - d.pbase;
+    const uint32_t* kin = pass == 0 ? d.knext : d.kb[(pass - 1) & 1];
+    const uint32_t* vin = pass == 0 ? nullptr : d.vb[(pass - 1) & 1];
+    radix_scatter_tile(kin, vin, d.kb[pass & 1], d.vb[pass & 1], d.n, lt, shift, goff, wc);
+}
+
+__global__ void __launch_bounds__(256) kb_tile_count(const SortDesc* __restrict__ sd, const uint32_t* __restrict__ ch_sim,
+                                                     int sh, int tile, int kpar, uint32_t* __restrict__ cnt)
+{
+    const SortDesc& d = sd[ch_sim[blockIdx.x]];
+    const int64_t lc = (int64_t)blockIdx.x - d.cbase;
+    const uint32_t tot = count_heads(d.kb[kpar], d.n, sh, tile, lc * tile, nullptr);
+    if (threadIdx.x == 0) cnt[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(256) kb_tile_write(const SortDesc* __restrict__ sd, const uint32_t* __restrict__ ch_sim,
+                                                     int sh, int tile, int kpar, const uint32_t* __restrict__ off,
+                                                     int64_t max_tiles, uint32_t* __restrict__ tile_sim,
+                                                     uint32_t* __restrict__ tile_start, uint32_t* __restrict__ err,
+                                                     uint32_t* __restrict__ tile_ctr)
+{
+    if (blockIdx.x == 0 && threadIdx.x < 2) tile_ctr[threadIdx.x] = 0u;
+    const uint32_t sim = ch_sim[blockIdx.x];
+    const SortDesc& d = sd[sim];
+    const uint32_t* skeys = d.kb[kpar];
+    const int64_t cs = ((int64_t)blockIdx.x - d.cbase) * tile;
+    const int per = tile / 256;
+    const int64_t k0 = cs + (int64_t)threadIdx.x * per;
+    uint32_t ex;
+    count_heads(skeys, d.n, sh, tile, cs, &ex);
+    uint32_t pos = off[blockIdx.x] + ex;
+    for (int i = 0; i < per; ++i) {
+        const int64_t k = k0 + i;
+        if (k < d.n && is_head(skeys, k, cs, sh)) {
+            if ((int64_t)pos < max_tiles) {
+                tile_sim[pos] = sim;
+                tile_start[pos] = (uint32_t)k;
+            } else {
+                atomicOr(err, APIC_ERRBIT_CAPACITY);
+            }
+            ++pos;
+        }
     }
 }
 
@@ -284,6 +367,32 @@ cudaError_t radix_sort(const Buffers& b, int64_t n, int key_bits, cudaStream_t s
     }
     *keys_out = const_cast<uint32_t*>(kin);
     *vals_out = const_cast<uint32_t*>(vin);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_radix_sort(const SortDesc* sd, const uint32_t* rt_sim, uint32_t total_rtiles, int passes,
+                             uint32_t* counts, uint32_t* part, cudaStream_t s)
+{
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        kb_radix_hist<<<total_rtiles, RT, 0, s>>>(sd, rt_sim, shift, p, counts);
+        cudaError_t e = exclusive_scan(counts, counts, 256 * (int64_t)total_rtiles, part, nullptr, s);
+        if (e != cudaSuccess) return e;
+        kb_radix_scatter<<<total_rtiles, RT, 0, s>>>(sd, rt_sim, shift, p, counts);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t batch_build_tiles(const SortDesc* sd, const uint32_t* ch_sim, uint32_t total_chunks, int dim, int tile,
+                              int kpar, uint32_t* cnt, uint32_t* part, uint32_t* ntiles, int64_t max_tiles,
+                              uint32_t* tile_sim, uint32_t* tile_start, uint32_t* err, uint32_t* tile_ctr, cudaStream_t s)
+{
+    const int sh = 2 * dim;
+    kb_tile_count<<<total_chunks, 256, 0, s>>>(sd, ch_sim, sh, tile, kpar, cnt);
+    cudaError_t e = exclusive_scan(cnt, cnt, total_chunks, part, ntiles, s);
+    if (e != cudaSuccess) return e;
+    kb_tile_write<<<total_chunks, 256, 0, s>>>(sd, ch_sim, sh, tile, kpar, cnt, max_tiles, tile_sim, tile_start, err,
+                                               tile_ctr);
     return cudaGetLastError();
 }
 

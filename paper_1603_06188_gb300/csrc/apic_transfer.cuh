@@ -345,14 +345,15 @@ template <typename R, int N> struct ReduceScatter<R, N, 1> {
 // stored (plain stores, no atomics) as that cell's stencil sums; then every tile node
 // gathers, in a fixed order, the sums of the cells whose stencils cover it, and adds the
 // result to the global grid.  Contributions as in k_p2g.
+// One tile of the cell-parallel P2G (whole CTA, NT = 128 threads).  On entry the CTA is
+// converged; cbeg / cend hold zeros and *s_cell = 0 (set by the caller before its last
+// barrier).  Leaves the smem free for the next tile after its final barrier.
 template <int D, int ORDER, typename R, int G>
-__global__ void __launch_bounds__(128, 2) k_p2g_cells(PState<R> st, const uint32_t* __restrict__ perm,
-                                                      const uint32_t* __restrict__ skeys,
-                                                      const uint32_t* __restrict__ tiles,
-                                                      const uint32_t* __restrict__ ntiles_p,
-                                                      uint32_t* __restrict__ tile_ctr, R* __restrict__ acc,
-                                                      uint32_t* __restrict__ flags, DevCfg<R> c, uint32_t* err,
-                                                      uint32_t* fallbacks)
+__device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32_t* __restrict__ perm,
+                                               const uint32_t* __restrict__ skeys, uint32_t start, uint32_t end,
+                                               R* __restrict__ acc, uint32_t* __restrict__ flags, const DevCfg<R>& c,
+                                               uint32_t* err, uint32_t* fallbacks, R* cellsum, uint32_t* cbeg,
+                                               uint32_t* cend, int* s_cell)
 {
     constexpr int NT = 128;
     constexpr int K = ORDER + 1;
@@ -362,33 +363,18 @@ __global__ void __launch_bounds__(128, 2) k_p2g_cells(PState<R> st, const uint32
     constexpr int NV = D + 1;
     constexpr int NVAL = NS * NV;
     constexpr int NC = (D == 3) ? 64 : 16;      // base cells of a node block
-    extern __shared__ __align__(16) unsigned char p2g_smem[];
-    R* cellsum = reinterpret_cast<R*>(p2g_smem);   // [NC][NVAL]
-    __shared__ uint32_t cbeg[NC], cend[NC];
-    __shared__ int s_tile, s_cell;
     const int lane = threadIdx.x & 31;
     const int lig = threadIdx.x % G;
     const int leader = lane & ~(G - 1);
     const unsigned gmask = (G == 32) ? FULLMASK : (((1u << G) - 1u) << leader);
-    const int ntiles = (int)*ntiles_p;
     const R dt_dx = c.dt * c.inv_dx;
     const R m = c.mass;
     const R sC = (c.transfer == 0) ? m * c.inv_kdx : R(0);
-    for (;;) {
-        if (threadIdx.x == 0) {
-            s_tile = (int)atomicAdd(tile_ctr, 1u);
-            s_cell = 0;
-        }
-        for (int i = threadIdx.x; i < NC; i += NT) { cbeg[i] = 0u; cend[i] = 0u; }
-        __syncthreads();
-        const int t = s_tile;
-        if (t >= ntiles) break;
-        const uint32_t start = tiles[t], end = tiles[t + 1];
-        const uint32_t blk = skeys[start] >> (2 * D);
-        int bo[3] = {0, 0, 0};
-        block_coords<D, R>(blk, c, bo);
+    const uint32_t blk = skeys[start] >> (2 * D);
+    int bo[3] = {0, 0, 0};
+    block_coords<D, R>(blk, c, bo);
 #pragma unroll
-        for (int a = 0; a < D; ++a) bo[a] *= 4;
+    for (int a = 0; a < D; ++a) bo[a] *= 4;
         // runs of equal base cell inside the tile
         for (uint32_t k = start + threadIdx.x; k < end; k += NT) {
             const uint32_t cl = skeys[k] & (NC - 1);
@@ -398,7 +384,7 @@ __global__ void __launch_bounds__(128, 2) k_p2g_cells(PState<R> st, const uint32
         __syncthreads();
         for (;;) {
             int cell = 0;
-            if (lig == 0) cell = atomicAdd(&s_cell, 1);
+            if (lig == 0) cell = atomicAdd(s_cell, 1);
             cell = __shfl_sync(gmask, cell, leader);
             if (cell >= NC) break;
             const uint32_t kb = cbeg[cell], ke = cend[cell];
@@ -543,7 +529,35 @@ __global__ void __launch_bounds__(128, 2) k_p2g_cells(PState<R> st, const uint32
                 flags[b2] = 1u;
             }
         }
+    __syncthreads();
+}
+
+template <int D, int ORDER, typename R, int G>
+__global__ void __launch_bounds__(128, 2) k_p2g_cells(PState<R> st, const uint32_t* __restrict__ perm,
+                                                      const uint32_t* __restrict__ skeys,
+                                                      const uint32_t* __restrict__ tiles,
+                                                      const uint32_t* __restrict__ ntiles_p,
+                                                      uint32_t* __restrict__ tile_ctr, R* __restrict__ acc,
+                                                      uint32_t* __restrict__ flags, DevCfg<R> c, uint32_t* err,
+                                                      uint32_t* fallbacks)
+{
+    constexpr int NC = (D == 3) ? 64 : 16;
+    extern __shared__ __align__(16) unsigned char p2g_smem[];
+    R* cellsum = reinterpret_cast<R*>(p2g_smem);   // [NC][NVAL]
+    __shared__ uint32_t cbeg[NC], cend[NC];
+    __shared__ int s_tile, s_cell;
+    const int ntiles = (int)*ntiles_p;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_tile = (int)atomicAdd(tile_ctr, 1u);
+            s_cell = 0;
+        }
+        for (int i = threadIdx.x; i < NC; i += 128) { cbeg[i] = 0u; cend[i] = 0u; }
         __syncthreads();
+        const int t = s_tile;
+        if (t >= ntiles) break;
+        p2g_cells_tile<D, ORDER, R, G>(st, perm, skeys, tiles[t], tiles[t + 1], acc, flags, c, err, fallbacks, cellsum,
+                                       cbeg, cend, &s_cell);
     }
 }
 
@@ -716,46 +730,52 @@ __global__ void __launch_bounds__(256) k_p2g_interleaved(PState<R> st, const uin
 // ---------------------------------------------------------------- grid update (Sec. 3.3)
 // One warp per active node block: v~ = ((m v) + dt f) / m + dt g, sticky walls, v~ = 0 where
 // m = 0; writes (v~, m) to the velocity grid and clears the accumulation grid and flag.
+// one node block of the grid update, by one warp
+template <int D, typename R>
+__device__ __forceinline__ void grid_update_block(R* __restrict__ acc, R* __restrict__ vel,
+                                                  uint32_t* __restrict__ flags, const DevCfg<R>& c, int b, int lane)
+{
+    constexpr int BN = (D == 3) ? 64 : 16;
+    if (flags[b] == 0u) return;
+    int bc[3] = {0, 0, 0};
+    block_coords<D, R>((uint32_t)b, c, bc);
+    for (int i = lane; i < BN; i += 32) {
+        const size_t node = (size_t)b * BN + i;
+        V4<R> a = *reinterpret_cast<const V4<R>*>(acc + 4 * node);
+        int g[3];
+        g[0] = bc[0] * 4 + (i & 3);
+        g[1] = bc[1] * 4 + ((i >> 2) & 3);
+        g[2] = (D == 3) ? bc[2] * 4 + (i >> 4) : 0;
+        const R m = a.w;
+        R v[3] = {R(0), R(0), R(0)};
+        if (m > R(0)) {
+            const R inv = R(1) / m;
+            v[0] = a.x * inv + c.dt * c.gravity[0];
+            v[1] = a.y * inv + c.dt * c.gravity[1];
+            if (D == 3) v[2] = a.z * inv + c.dt * c.gravity[2];
+            if (c.boundary == 1) {
+                bool wall = false;
+#pragma unroll
+                for (int d = 0; d < D; ++d)
+                    if (g[d] < c.wall || g[d] >= c.res[d] - c.wall) wall = true;
+                if (wall) v[0] = v[1] = v[2] = R(0);
+            }
+        }
+        *reinterpret_cast<V4<R>*>(vel + 4 * node) = V4<R>{v[0], v[1], v[2], m};
+        *reinterpret_cast<V4<R>*>(acc + 4 * node) = V4<R>{R(0), R(0), R(0), R(0)};
+    }
+    __syncwarp();
+    if (lane == 0) flags[b] = 0u;
+}
+
 template <int D, typename R>
 __global__ void __launch_bounds__(TPB) k_grid_update(R* __restrict__ acc, R* __restrict__ vel,
                                                      uint32_t* __restrict__ flags, DevCfg<R> c)
 {
-    constexpr int BN = (D == 3) ? 64 : 16;
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * TPB + threadIdx.x) >> 5;
     const int nw = (gridDim.x * TPB) >> 5;
-    for (int b = gw; b < c.nblocks; b += nw) {
-        if (flags[b] == 0u) continue;
-        int bc[3] = {0, 0, 0};
-        block_coords<D, R>((uint32_t)b, c, bc);
-        for (int i = lane; i < BN; i += 32) {
-            const size_t node = (size_t)b * BN + i;
-            V4<R> a = *reinterpret_cast<const V4<R>*>(acc + 4 * node);
-            int g[3];
-            g[0] = bc[0] * 4 + (i & 3);
-            g[1] = bc[1] * 4 + ((i >> 2) & 3);
-            g[2] = (D == 3) ? bc[2] * 4 + (i >> 4) : 0;
-            const R m = a.w;
-            R v[3] = {R(0), R(0), R(0)};
-            if (m > R(0)) {
-                const R inv = R(1) / m;
-                v[0] = a.x * inv + c.dt * c.gravity[0];
-                v[1] = a.y * inv + c.dt * c.gravity[1];
-                if (D == 3) v[2] = a.z * inv + c.dt * c.gravity[2];
-                if (c.boundary == 1) {
-                    bool wall = false;
-#pragma unroll
-                    for (int d = 0; d < D; ++d)
-                        if (g[d] < c.wall || g[d] >= c.res[d] - c.wall) wall = true;
-                    if (wall) v[0] = v[1] = v[2] = R(0);
-                }
-            }
-            *reinterpret_cast<V4<R>*>(vel + 4 * node) = V4<R>{v[0], v[1], v[2], m};
-            *reinterpret_cast<V4<R>*>(acc + 4 * node) = V4<R>{R(0), R(0), R(0), R(0)};
-        }
-        __syncwarp();
-        if (lane == 0) flags[b] = 0u;
-    }
+    for (int b = gw; b < c.nblocks; b += nw) grid_update_block<D, R>(acc, vel, flags, c, b, lane);
 }
 
 // ---------------------------------------------------------------- mbarrier + bulk copy
@@ -800,6 +820,181 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 // gathers v_p = sum w v~, B_p = sum w v~ (x_i - x_p)^T, grad v = sum v~ grad w^T, updates
 // F_p <- (I + dt grad v) F_p and x_p <- x_p + dt v_p, and is written at its sorted slot
 // together with its next cell key.
+// One tile of G2P (whole CTA, TPB threads, converged on entry).  Returns false if the
+// bulk-copy wait timed out (the CTA must then leave).
+template <int D, int ORDER, typename R>
+__device__ __forceinline__ bool g2p_tile(const PState<R>& in, const PState<R>& out, const uint32_t* __restrict__ perm,
+                                         const uint32_t* __restrict__ skeys, uint32_t start, uint32_t end,
+                                         const R* __restrict__ vel, uint32_t* __restrict__ knext, const DevCfg<R>& c,
+                                         uint32_t* err, R (*sv)[(D == 3) ? 64 : 16][4], uint64_t* mbar,
+                                         unsigned& phase, int* s_ok)
+{
+    constexpr int K = ORDER + 1;
+    constexpr int BN = (D == 3) ? 64 : 16;
+    constexpr int NB = 1 << D;
+    const R dt_dx = c.dt * c.inv_dx;
+    const uint32_t blk = skeys[start] >> (2 * D);
+    int bc[3] = {0, 0, 0};
+    block_coords<D, R>(blk, c, bc);
+    if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        unsigned nblk = 0;
+        bool inb[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            inb[q] = true;
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+                if (bc[a] + ((q >> a) & 1) >= c.nb[a]) inb[q] = false;
+            nblk += inb[q] ? 1u : 0u;
+        }
+        const unsigned bytes = (unsigned)(BN * 4 * sizeof(R));
+        mbar_expect_tx(mbar, nblk * bytes);
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            if (!inb[q]) continue;
+            int bb[3] = {bc[0] + (q & 1), bc[1] + ((q >> 1) & 1), (D == 3) ? bc[2] + ((q >> 2) & 1) : 0};
+            const uint32_t b2 = (D == 3) ? ((uint32_t)bb[2] * c.nb[1] + bb[1]) * c.nb[0] + bb[0]
+                                         : (uint32_t)bb[1] * c.nb[0] + bb[0];
+            bulk_copy_g2s(&sv[q][0][0], vel + (size_t)b2 * BN * 4, bytes, mbar);
+        }
+        bool ok = mbar_wait_bounded(mbar, phase, 1u << 22);
+        if (!ok) {
+            set_err(err, APIC_ERRBIT_TIMEOUT);
+            mbar_wait_bounded(mbar, phase, 1u << 22);
+        }
+        *s_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    if (!*s_ok) return false;
+    phase ^= 1u;
+    // the next round's particle is requested before the current one is processed
+    Particle<D, R> nxt;
+    if (start + threadIdx.x < end) load_xF<D, R>(in, perm[start + threadIdx.x], nxt);
+    for (uint32_t k0 = start; k0 < end; k0 += TPB) {
+        const uint32_t k = k0 + threadIdx.x;
+        if (k >= end) continue;
+        Particle<D, R> p = nxt;
+        if (k + TPB < end) load_xF<D, R>(in, perm[k + TPB], nxt);
+        int base[D], lb[D];
+        R w[D][K], dw[D][K], fx[D];
+        bool ok = particle_stencil<D, ORDER, R>(p.o, p.cell, c, base, fx, w, dw);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            lb[a] = base[a] - 4 * bc[a];
+            if (lb[a] < 0 || lb[a] > 3) { ok = false; lb[a] = 0; }
+        }
+        if (!ok) set_err(err, APIC_ERRBIT_RANGE);
+        // Separable gather: the weights are tensor products, so the sums over the
+        // stencil are taken axis by axis (innermost axis first) instead of node by node:
+        //   vp   = sum_i w v~                  = sum_a wx R_a
+        //   G    = sum_i v~ grad^w^T           (columns: dwx R_a, wx S_a, wx T_a)
+        //   Bh   = sum_i w v~ r^T, r^ = node - fx (columns: rx wx R_a, wx Y_a, wx Zc_a)
+        // with per-(a,b) sums over c and per-a sums over b.
+        R vp[D], Bh[D * D], G[D * D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) vp[a] = R(0);
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) { Bh[i] = R(0); G[i] = R(0); }
+        R rw[D][K];   // (node - fx) * w per axis
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int j = 0; j < K; ++j) rw[a][j] = (R(j) - fx[a]) * w[a][j];
+#pragma unroll
+        for (int ia = 0; ia < K; ++ia) {
+            R Ra[D], Sa[D], Ta[D], Ya[D], Za[D];
+#pragma unroll
+            for (int a = 0; a < D; ++a) { Ra[a] = Sa[a] = Ta[a] = Ya[a] = Za[a] = R(0); }
+#pragma unroll
+            for (int ib = 0; ib < K; ++ib) {
+                const int L0 = lb[0] + ia, L1 = lb[1] + ib;
+                if (D == 3) {
+                    R P[3] = {R(0), R(0), R(0)}, Q[3] = {R(0), R(0), R(0)}, Z[3] = {R(0), R(0), R(0)};
+#pragma unroll
+                    for (int ic = 0; ic < K; ++ic) {
+                        const int L2 = lb[2] + ic;
+                        const int qb = (L0 >> 2) | ((L1 >> 2) << 1) | ((L2 >> 2) << 2);
+                        const int ni = (L0 & 3) | ((L1 & 3) << 2) | ((L2 & 3) << 4);
+                        const V4<R> nv = *reinterpret_cast<const V4<R>*>(&sv[qb][ni][0]);
+                        const R vt[3] = {nv.x, nv.y, nv.z};
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            P[a] += w[2][ic] * vt[a];
+                            Q[a] += dw[2][ic] * vt[a];
+                            Z[a] += rw[2][ic] * vt[a];
+                        }
+                    }
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        Ra[a] += w[1][ib] * P[a];
+                        Sa[a] += dw[1][ib] * P[a];
+                        Ta[a] += w[1][ib] * Q[a];
+                        Ya[a] += rw[1][ib] * P[a];
+                        Za[a] += w[1][ib] * Z[a];
+                    }
+                } else {
+                    const int qb = (L0 >> 2) | ((L1 >> 2) << 1);
+                    const int ni = (L0 & 3) | ((L1 & 3) << 2);
+                    const V4<R> nv = *reinterpret_cast<const V4<R>*>(&sv[qb][ni][0]);
+                    const R vt[2] = {nv.x, nv.y};
+#pragma unroll
+                    for (int a = 0; a < 2; ++a) {
+                        Ra[a] += w[1][ib] * vt[a];
+                        Sa[a] += dw[1][ib] * vt[a];
+                        Ya[a] += rw[1][ib] * vt[a];
+                    }
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                vp[a] += w[0][ia] * Ra[a];
+                G[a * D + 0] += dw[0][ia] * Ra[a];
+                G[a * D + 1] += w[0][ia] * Sa[a];
+                Bh[a * D + 0] += rw[0][ia] * Ra[a];
+                Bh[a * D + 1] += w[0][ia] * Ya[a];
+                if (D == 3) {
+                    G[a * D + 2] += w[0][ia] * Ta[a];
+                    Bh[a * D + 2] += w[0][ia] * Za[a];
+                }
+            }
+        }
+        // F <- (I + dt grad v) F with grad v = G / dx
+        R Fn[D * D];
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = 0; b < D; ++b) {
+                R s = p.F[a * D + b];
+#pragma unroll
+                for (int kk = 0; kk < D; ++kk) s += dt_dx * G[a * D + kk] * p.F[kk * D + b];
+                Fn[a * D + b] = s;
+            }
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) {
+            p.F[i] = Fn[i];
+            p.B[i] = (c.transfer == 0) ? c.dx * Bh[i] : R(0);
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            p.v[a] = vp[a];
+            R o = p.o[a] + dt_dx * vp[a];
+            const R fl = floor(o);
+            o -= fl;
+            int cl = p.cell[a] + (int)fl;
+            if (o >= R(1)) { o -= R(1); cl += 1; }
+            if (cl < 0) { cl = 0; o = R(0); set_err(err, APIC_ERRBIT_RANGE); }
+            if (cl > c.res[a] - 1) { cl = c.res[a] - 1; o = R(0); set_err(err, APIC_ERRBIT_RANGE); }
+            p.o[a] = o;
+            p.cell[a] = cl;
+        }
+        store_all<D, R>(out, k, p);
+        knext[k] = key_of<D, ORDER, R>(p.o, p.cell, c, err);
+    }
+    __syncthreads();
+    return true;
+}
+
 template <int D, int ORDER, typename R>
 __global__ void __launch_bounds__(TPB) k_g2p(PState<R> in, PState<R> out, const uint32_t* __restrict__ perm,
                                              const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ tiles,
@@ -807,10 +1002,8 @@ __global__ void __launch_bounds__(TPB) k_g2p(PState<R> in, PState<R> out, const 
                                              const R* __restrict__ vel, uint32_t* __restrict__ knext, DevCfg<R> c,
                                              uint32_t* err)
 {
-    constexpr int K = ORDER + 1;
     constexpr int BN = (D == 3) ? 64 : 16;
     constexpr int NB = 1 << D;
-    constexpr int NS = (D == 3) ? K * K * K : K * K;
     __shared__ __align__(128) R sv[NB][BN][4];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ int s_ok;
@@ -818,172 +1011,14 @@ __global__ void __launch_bounds__(TPB) k_g2p(PState<R> in, PState<R> out, const 
     if (threadIdx.x == 0) mbar_init(&mbar, 1);
     unsigned phase = 0;
     const int ntiles = (int)*ntiles_p;
-    const R dt_dx = c.dt * c.inv_dx;
     for (;;) {
         if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_ctr + 1, 1u);
         __syncthreads();
         const int t = s_tile;
         if (t >= ntiles) break;
-        const uint32_t start = tiles[t], end = tiles[t + 1];
-        const uint32_t blk = skeys[start] >> (2 * D);
-        int bc[3] = {0, 0, 0};
-        block_coords<D, R>(blk, c, bc);
-        if (threadIdx.x == 0) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            unsigned nblk = 0;
-            bool inb[NB];
-#pragma unroll
-            for (int q = 0; q < NB; ++q) {
-                inb[q] = true;
-#pragma unroll
-                for (int a = 0; a < D; ++a)
-                    if (bc[a] + ((q >> a) & 1) >= c.nb[a]) inb[q] = false;
-                nblk += inb[q] ? 1u : 0u;
-            }
-            const unsigned bytes = (unsigned)(BN * 4 * sizeof(R));
-            mbar_expect_tx(&mbar, nblk * bytes);
-#pragma unroll
-            for (int q = 0; q < NB; ++q) {
-                if (!inb[q]) continue;
-                int bb[3] = {bc[0] + (q & 1), bc[1] + ((q >> 1) & 1), (D == 3) ? bc[2] + ((q >> 2) & 1) : 0};
-                const uint32_t b2 = (D == 3) ? ((uint32_t)bb[2] * c.nb[1] + bb[1]) * c.nb[0] + bb[0]
-                                             : (uint32_t)bb[1] * c.nb[0] + bb[0];
-                bulk_copy_g2s(&sv[q][0][0], vel + (size_t)b2 * BN * 4, bytes, &mbar);
-            }
-            bool ok = mbar_wait_bounded(&mbar, phase, 1u << 22);
-            if (!ok) {
-                set_err(err, APIC_ERRBIT_TIMEOUT);
-                mbar_wait_bounded(&mbar, phase, 1u << 22);
-            }
-            s_ok = ok ? 1 : 0;
-        }
-        __syncthreads();
-        if (!s_ok) return;
-        phase ^= 1u;
-        // the next round's particle is requested before the current one is processed
-        Particle<D, R> nxt;
-        if (start + threadIdx.x < end) load_xF<D, R>(in, perm[start + threadIdx.x], nxt);
-        for (uint32_t k0 = start; k0 < end; k0 += TPB) {
-            const uint32_t k = k0 + threadIdx.x;
-            if (k >= end) continue;
-            Particle<D, R> p = nxt;
-            if (k + TPB < end) load_xF<D, R>(in, perm[k + TPB], nxt);
-            int base[D], lb[D];
-            R w[D][K], dw[D][K], fx[D];
-            bool ok = particle_stencil<D, ORDER, R>(p.o, p.cell, c, base, fx, w, dw);
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                lb[a] = base[a] - 4 * bc[a];
-                if (lb[a] < 0 || lb[a] > 3) { ok = false; lb[a] = 0; }
-            }
-            if (!ok) set_err(err, APIC_ERRBIT_RANGE);
-            // Separable gather: the weights are tensor products, so the sums over the
-            // stencil are taken axis by axis (innermost axis first) instead of node by node:
-            //   vp   = sum_i w v~                  = sum_a wx R_a
-            //   G    = sum_i v~ grad^w^T           (columns: dwx R_a, wx S_a, wx T_a)
-            //   Bh   = sum_i w v~ r^T, r^ = node - fx (columns: rx wx R_a, wx Y_a, wx Zc_a)
-            // with per-(a,b) sums over c and per-a sums over b.
-            R vp[D], Bh[D * D], G[D * D];
-#pragma unroll
-            for (int a = 0; a < D; ++a) vp[a] = R(0);
-#pragma unroll
-            for (int i = 0; i < D * D; ++i) { Bh[i] = R(0); G[i] = R(0); }
-            R rw[D][K];   // (node - fx) * w per axis
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-#pragma unroll
-                for (int j = 0; j < K; ++j) rw[a][j] = (R(j) - fx[a]) * w[a][j];
-#pragma unroll
-            for (int ia = 0; ia < K; ++ia) {
-                R Ra[D], Sa[D], Ta[D], Ya[D], Za[D];
-#pragma unroll
-                for (int a = 0; a < D; ++a) { Ra[a] = Sa[a] = Ta[a] = Ya[a] = Za[a] = R(0); }
-#pragma unroll
-                for (int ib = 0; ib < K; ++ib) {
-                    const int L0 = lb[0] + ia, L1 = lb[1] + ib;
-                    if (D == 3) {
-                        R P[3] = {R(0), R(0), R(0)}, Q[3] = {R(0), R(0), R(0)}, Z[3] = {R(0), R(0), R(0)};
-#pragma unroll
-                        for (int ic = 0; ic < K; ++ic) {
-                            const int L2 = lb[2] + ic;
-                            const int qb = (L0 >> 2) | ((L1 >> 2) << 1) | ((L2 >> 2) << 2);
-                            const int ni = (L0 & 3) | ((L1 & 3) << 2) | ((L2 & 3) << 4);
-                            const V4<R> nv = *reinterpret_cast<const V4<R>*>(&sv[qb][ni][0]);
-                            const R vt[3] = {nv.x, nv.y, nv.z};
-#pragma unroll
-                            for (int a = 0; a < 3; ++a) {
-                                P[a] += w[2][ic] * vt[a];
-                                Q[a] += dw[2][ic] * vt[a];
-                                Z[a] += rw[2][ic] * vt[a];
-                            }
-                        }
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            Ra[a] += w[1][ib] * P[a];
-                            Sa[a] += dw[1][ib] * P[a];
-                            Ta[a] += w[1][ib] * Q[a];
-                            Ya[a] += rw[1][ib] * P[a];
-                            Za[a] += w[1][ib] * Z[a];
-                        }
-                    } else {
-                        const int qb = (L0 >> 2) | ((L1 >> 2) << 1);
-                        const int ni = (L0 & 3) | ((L1 & 3) << 2);
-                        const V4<R> nv = *reinterpret_cast<const V4<R>*>(&sv[qb][ni][0]);
-                        const R vt[2] = {nv.x, nv.y};
-#pragma unroll
-                        for (int a = 0; a < 2; ++a) {
-                            Ra[a] += w[1][ib] * vt[a];
-                            Sa[a] += dw[1][ib] * vt[a];
-                            Ya[a] += rw[1][ib] * vt[a];
-                        }
-                    }
-                }
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    vp[a] += w[0][ia] * Ra[a];
-                    G[a * D + 0] += dw[0][ia] * Ra[a];
-                    G[a * D + 1] += w[0][ia] * Sa[a];
-                    Bh[a * D + 0] += rw[0][ia] * Ra[a];
-                    Bh[a * D + 1] += w[0][ia] * Ya[a];
-                    if (D == 3) {
-                        G[a * D + 2] += w[0][ia] * Ta[a];
-                        Bh[a * D + 2] += w[0][ia] * Za[a];
-                    }
-                }
-            }
-            // F <- (I + dt grad v) F with grad v = G / dx
-            R Fn[D * D];
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-#pragma unroll
-                for (int b = 0; b < D; ++b) {
-                    R s = p.F[a * D + b];
-#pragma unroll
-                    for (int kk = 0; kk < D; ++kk) s += dt_dx * G[a * D + kk] * p.F[kk * D + b];
-                    Fn[a * D + b] = s;
-                }
-#pragma unroll
-            for (int i = 0; i < D * D; ++i) {
-                p.F[i] = Fn[i];
-                p.B[i] = (c.transfer == 0) ? c.dx * Bh[i] : R(0);
-            }
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                p.v[a] = vp[a];
-                R o = p.o[a] + dt_dx * vp[a];
-                const R fl = floor(o);
-                o -= fl;
-                int cl = p.cell[a] + (int)fl;
-                if (o >= R(1)) { o -= R(1); cl += 1; }
-                if (cl < 0) { cl = 0; o = R(0); set_err(err, APIC_ERRBIT_RANGE); }
-                if (cl > c.res[a] - 1) { cl = c.res[a] - 1; o = R(0); set_err(err, APIC_ERRBIT_RANGE); }
-                p.o[a] = o;
-                p.cell[a] = cl;
-            }
-            store_all<D, R>(out, k, p);
-            knext[k] = key_of<D, ORDER, R>(p.o, p.cell, c, err);
-        }
-        __syncthreads();
+        if (!g2p_tile<D, ORDER, R>(in, out, perm, skeys, tiles[t], tiles[t + 1], vel, knext, c, err, sv, &mbar, phase,
+                                   &s_ok))
+            return;
     }
 }
 
