@@ -206,6 +206,137 @@ def recorded_traffic(kernel: str, workload: str):
     return None
 
 
+def batched_members(apic, count: int, seed: int, ppc: int = 8):
+    """Configs and initial states of `count` simulations of the batched mix: grid edge
+    U{32..96}, particle count log-uniform in [2k, 400k], box or sphere, random rigid motion,
+    fixed-corotated E = 1e4, nu = 0.3, rho = 1, gravity, sticky walls, dt = 2e-5, FP32."""
+    from paper_1603_06188_gb300 import scenes
+
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        spec = scenes.random_sim_spec(rng)
+        sc = scenes.sim_from_spec(spec, ppc=ppc)
+        vol = sc.dx ** 3 / ppc
+        cfg = apic.make_config(dim=3, order=2, precision=32, res=sc.res, dx=sc.dx, dt=2e-5, gravity=(0.0, -9.8, 0.0),
+                               boundary="sticky", wall=3, model="fcr", E=1e4, nu=0.3, particle_mass=vol,
+                               particle_volume=vol)
+        B = sc.grad_v * (0.25 * sc.dx * sc.dx)
+        out.append((cfg, sc.x, sc.v, B))
+    return out
+
+
+def run_batched(args) -> int:
+    """Many simulations: the batched form (one persistent launch per phase, graph-replayed,
+    autotuned tiles) against the plain form (each simulation stepped by its own launches)."""
+    import torch
+
+    from paper_1603_06188_gb300 import apic, build
+
+    build.build()
+    apic.load()
+    torch.cuda.set_device(0)
+    members = batched_members(apic, args.sims, seed=1234)
+    sims = []
+    for cfg, x, v, B in members:
+        sim = apic.Sim(cfg, len(x))
+        sim.upload(x, v, B)
+        sims.append(sim)
+    total = sum(s.n for s in sims)
+    blocks = sum(s.n_blocks for s in sims)
+    # plain form: every simulation stepped by its own launches, one after the other
+    for s in sims:
+        s.step(1)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plain_steps = max(1, args.steps // 4)
+    e0.record(stream)
+    for _ in range(plain_steps):
+        for s in sims:
+            s.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1) / plain_steps
+    plain_launches = sum(s.stats()["kernel_launches"] for s in sims)
+    # batched form
+    batch = apic.Batch(dim=3, order=2, precision=32, max_sims=len(sims), max_particles=total + 1,
+                       max_blocks=blocks + 1, use_graph=True)
+    for s in sims:
+        batch.add(s)
+    tile, group = batch.autotune(steps=2)
+    batch.step(args.warmup)
+    batch.synchronize()
+    l0 = batch.stats()["kernel_launches"]
+    e0.record(batch.stream)
+    batch.step(args.steps)
+    e1.record(batch.stream)
+    batch.synchronize()
+    batch_ms = e0.elapsed_time(e1) / args.steps
+    st = batch.stats()
+    out = {"metric": METRIC, "value": total / (batch_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": batch_ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"batched{len(sims)}", "sims": len(sims), "particles": total, "node_blocks": blocks,
+                      "description": "independent 3-D MPM+APIC sims, grid edge U{32..96}, particles log-uniform "
+                                     "2k-400k (target), box/sphere, random rigid velocity, quadratic, FP32, 8 ppc",
+                      "tile_particles": tile, "p2g_group": group, "cuda_graph": True},
+           "plain": {"value": total / (plain_ms / 1e3), "ms_per_step": plain_ms, "steps": plain_steps,
+                     "kernel_launches_per_step": plain_launches // max(1, (1 + plain_steps))},
+           "batched_over_plain": plain_ms / batch_ms,
+           "gpu_launches": st["kernel_launches"] - l0, "tiles": st["tiles"]}
+    print(json.dumps(out), flush=True)
+    batch.close()
+    for s in sims:
+        s.close()
+    return 0
+
+
+def run_serving(args) -> int:
+    """Continuous batching of a Poisson stream of simulations (sizes as in the batched mix,
+    steps U{50..2000}), admitted by device footprint under a memory budget."""
+    import torch
+
+    from paper_1603_06188_gb300 import apic, build, serving
+
+    build.build()
+    apic.load()
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(99)
+    members = batched_members(apic, args.requests, seed=4321)
+    arrivals = serving.poisson_arrivals(rng, args.rate, args.requests)
+    reqs = []
+    for i, (cfg, x, v, B) in enumerate(members):
+        steps = int(rng.integers(50, 2001))
+        reqs.append(serving.Request(i, float(arrivals[i]), steps, apic.apic_workspace_size(cfg, len(x)), len(x),
+                                    payload=(cfg, x, v, B)))
+    budget = int(args.budget_gb * 1e9)
+    batch = apic.Batch(dim=3, order=2, precision=32, max_sims=args.requests,
+                       max_particles=sum(r.particles for r in reqs) + 1,
+                       max_blocks=sum(int(np.prod([(c.res[a] + 3) // 4 for a in range(3)])) for c, *_ in members) + 1,
+                       use_graph=True)
+
+    def make_sim(r):
+        cfg, x, v, B = r.payload
+        sim = apic.Sim(cfg, len(x))
+        sim.upload(x, v, B)
+        return sim
+
+    rep, _ = serving.serve_gpu(reqs, make_sim, batch, budget, max_resident=args.requests, max_chunk=8)
+    offered = sum(r.particles * r.steps for r in reqs) / max(arrivals[-1], 1e-9)
+    out = {"metric": METRIC, "value": rep.throughput, "unit": UNIT, "n_gpus": 1, "steps": rep.batched_steps,
+           "warmup": 0, "ms_per_step": 1e3 * rep.makespan / max(1, rep.batched_steps), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "serving", "requests": args.requests, "rate_per_s": args.rate,
+                      "budget_gb": args.budget_gb, "steps_per_request": "U{50..2000}"},
+           "latency_s": {"p50": rep.percentile(50), "p99": rep.percentile(99), "max": max(rep.latencies)},
+           "offered_particle_steps_per_s": offered, "completed": rep.completed, "makespan_s": rep.makespan,
+           "max_resident": rep.max_resident, "max_resident_gb": rep.max_bytes / 1e9}
+    print(json.dumps(out), flush=True)
+    batch.close()
+    return 0
+
+
 def dist_setup(n_gpus: int):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -247,7 +378,11 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="cube128", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="cube128", choices=sorted(WORKLOADS) + ["batched", "serving"])
+    ap.add_argument("--sims", type=int, default=512)
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ppc", type=int, default=None)
     ap.add_argument("--ref-particles", type=int, default=20000)
@@ -262,6 +397,10 @@ def main():
     world, rank, local, dist = dist_setup(args.gpus)
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.workload == "batched":
+        return run_batched(args) if rank == 0 else 0
+    if args.workload == "serving":
+        return run_serving(args) if rank == 0 else 0
 
     import torch
 

@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(128, 2) kb_p2g_cells(SimDesc<R>* __restrict__ 
     constexpr int NC = (D == 3) ? 64 : 16;
     extern __shared__ __align__(16) unsigned char p2g_smem[];
     R* cellsum = reinterpret_cast<R*>(p2g_smem);
+    R* pslots = reinterpret_cast<R*>(p2g_smem + (p2g_cellsum_bytes<D, ORDER, R>() + 15) / 16 * 16);
     __shared__ uint32_t cbeg[NC], cend[NC];
     __shared__ int s_tile, s_cell;
     __shared__ __align__(16) SimDesc<R> sd;
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(128, 2) kb_p2g_cells(SimDesc<R>* __restrict__ 
         const uint32_t start = tile_start[t];
         const uint32_t end = tile_end(tile_sim, tile_start, t, ntiles, sim, (uint32_t)sd.c.n);
         p2g_cells_tile<D, ORDER, R, G>(sd.st[sd.cur], sd.vb[kpar], sd.kb[kpar], start, end, sd.acc, sd.flags, sd.c,
-                                       sd.err, sd.fallbacks, cellsum, cbeg, cend, &s_cell);
+                                       sd.err, sd.fallbacks, cellsum, cbeg, cend, &s_cell, pslots);
     }
 }
 

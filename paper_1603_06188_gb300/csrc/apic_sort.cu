@@ -205,26 +205,50 @@ __device__ __forceinline__ bool is_head(const uint32_t* skeys, int64_t k, int64_
     return k == chunk_start || (skeys[k] >> sh) != (skeys[k - 1] >> sh);
 }
 
+// Tile heads of chunk [cs, cs + tile) are found 256 consecutive keys at a time (coalesced
+// reads; a warp ballot ranks the heads of each round in order).
 __device__ __forceinline__ uint32_t count_heads(const uint32_t* __restrict__ skeys, int64_t n, int sh, int tile,
-                                                int64_t cs, uint32_t* first_local)
+                                                int64_t cs)
 {
-    const int per = tile / 256;
-    const int64_t k0 = cs + (int64_t)threadIdx.x * per;
+    const int64_t ce = cs + tile < n ? cs + tile : n;
     uint32_t c = 0;
-    for (int i = 0; i < per; ++i) {
-        const int64_t k = k0 + i;
-        if (k < n && is_head(skeys, k, cs, sh)) ++c;
-    }
+    for (int64_t k = cs + threadIdx.x; k < ce; k += 256)
+        if (is_head(skeys, k, cs, sh)) ++c;
     uint32_t ex;
-    const uint32_t tot = block_excl_scan(c, ex);
-    if (first_local) *first_local = ex;
-    return tot;
+    return block_excl_scan(c, ex);
+}
+
+// writes, in order, every head of the chunk through emit(position, k)
+template <class Emit>
+__device__ __forceinline__ void write_heads(const uint32_t* __restrict__ skeys, int64_t n, int sh, int tile, int64_t cs,
+                                            uint32_t pos0, Emit emit)
+{
+    __shared__ uint32_t wsum[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t ce = cs + tile < n ? cs + tile : n;
+    uint32_t pos = pos0;
+    for (int64_t r = cs; r < ce; r += 256) {
+        const int64_t k = r + threadIdx.x;
+        const bool h = k < ce && is_head(skeys, k, cs, sh);
+        const unsigned bal = __ballot_sync(0xffffffffu, h);
+        if (lane == 0) wsum[w] = (uint32_t)__popc(bal);
+        __syncthreads();
+        uint32_t before = 0, total = 0;
+        for (int i = 0; i < 8; ++i) {
+            const uint32_t v = wsum[i];
+            before += i < w ? v : 0u;
+            total += v;
+        }
+        if (h) emit(pos + before + (uint32_t)__popc(bal & lanemask_lt()), k);
+        pos += total;
+        __syncthreads();
+    }
 }
 
 __global__ void __launch_bounds__(256) k_tile_count(const uint32_t* __restrict__ skeys, int64_t n, int sh, int tile,
                                                     uint32_t* __restrict__ cnt)
 {
-    const uint32_t tot = count_heads(skeys, n, sh, tile, (int64_t)blockIdx.x * tile, nullptr);
+    const uint32_t tot = count_heads(skeys, n, sh, tile, (int64_t)blockIdx.x * tile);
     if (threadIdx.x == 0) cnt[blockIdx.x] = tot;
 }
 
@@ -235,18 +259,9 @@ __global__ void __launch_bounds__(256) k_tile_write(const uint32_t* __restrict__
 {
     if (blockIdx.x == 0 && threadIdx.x < 2) tile_ctr[threadIdx.x] = 0u;
     const int64_t cs = (int64_t)blockIdx.x * tile;
-    const int per = tile / 256;
-    const int64_t k0 = cs + (int64_t)threadIdx.x * per;
-    uint32_t ex;
-    count_heads(skeys, n, sh, tile, cs, &ex);
-    uint32_t pos = off[blockIdx.x] + ex;
-    for (int i = 0; i < per; ++i) {
-        const int64_t k = k0 + i;
-        if (k < n && is_head(skeys, k, cs, sh)) {
-            if ((int64_t)pos < max_tiles) tiles[pos] = (uint32_t)k;
-            ++pos;
-        }
-    }
+    write_heads(skeys, n, sh, tile, cs, off[blockIdx.x], [&](uint32_t pos, int64_t k) {
+        if ((int64_t)pos < max_tiles) tiles[pos] = (uint32_t)k;
+    });
     if (blockIdx.x == nchunks - 1 && threadIdx.x == 0) {
         const uint32_t nt = *ntiles;
         if ((int64_t)nt < max_tiles) tiles[nt] = (uint32_t)n;
@@ -288,7 +303,7 @@ __global__ void __launch_bounds__(256) kb_tile_count(const SortDesc* __restrict_
 {
     const SortDesc& d = sd[ch_sim[blockIdx.x]];
     const int64_t lc = (int64_t)blockIdx.x - d.cbase;
-    const uint32_t tot = count_heads(d.kb[kpar], d.n, sh, tile, lc * tile, nullptr);
+    const uint32_t tot = count_heads(d.kb[kpar], d.n, sh, tile, lc * tile);
     if (threadIdx.x == 0) cnt[blockIdx.x] = tot;
 }
 
@@ -301,25 +316,15 @@ __global__ void __launch_bounds__(256) kb_tile_write(const SortDesc* __restrict_
     if (blockIdx.x == 0 && threadIdx.x < 2) tile_ctr[threadIdx.x] = 0u;
     const uint32_t sim = ch_sim[blockIdx.x];
     const SortDesc& d = sd[sim];
-    const uint32_t* skeys = d.kb[kpar];
     const int64_t cs = ((int64_t)blockIdx.x - d.cbase) * tile;
-    const int per = tile / 256;
-    const int64_t k0 = cs + (int64_t)threadIdx.x * per;
-    uint32_t ex;
-    count_heads(skeys, d.n, sh, tile, cs, &ex);
-    uint32_t pos = off[blockIdx.x] + ex;
-    for (int i = 0; i < per; ++i) {
-        const int64_t k = k0 + i;
-        if (k < d.n && is_head(skeys, k, cs, sh)) {
-            if ((int64_t)pos < max_tiles) {
-                tile_sim[pos] = sim;
-                tile_start[pos] = (uint32_t)k;
-            } else {
-                atomicOr(err, APIC_ERRBIT_CAPACITY);
-            }
-            ++pos;
+    write_heads(d.kb[kpar], d.n, sh, tile, cs, off[blockIdx.x], [&](uint32_t pos, int64_t k) {
+        if ((int64_t)pos < max_tiles) {
+            tile_sim[pos] = sim;
+            tile_start[pos] = (uint32_t)k;
+        } else {
+            atomicOr(err, APIC_ERRBIT_CAPACITY);
         }
-    }
+    });
 }
 
 }  // namespace

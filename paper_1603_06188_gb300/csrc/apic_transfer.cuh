@@ -295,6 +295,94 @@ __global__ void __launch_bounds__(TPB) k_p2g(PState<R> st, const uint32_t* __res
     }
 }
 
+// ---------------------------------------------------------------- asynchronous particle staging
+// A particle's packed state copied global -> shared with cp.async (16-byte pieces; the 8-byte
+// Fc group of the FP32 layout with an 8-byte copy), so loads of the next particles overlap
+// the arithmetic of the current one without holding them in registers.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// slot of packed state, in units of R: 3-D A V Ba Bb Fa Fb Fc (+2 pad) = 28, 2-D A V Ba Fa = 16
+template <int D> __host__ __device__ constexpr int slot_words() { return D == 3 ? 28 : 16; }
+
+template <typename R> __device__ __forceinline__ void cp_group4(R* dst, const V4<R>* src)
+{
+    if (sizeof(R) == 4) {
+        cp_async16(dst, src);
+    } else {
+        cp_async16(dst, src);
+        cp_async16(dst + 2, reinterpret_cast<const R*>(src) + 2);
+    }
+}
+
+template <int D, typename R> __device__ __forceinline__ void stage_particle(R* slot, const PState<R>& s, uint32_t q)
+{
+    cp_group4<R>(slot + 0, s.A + q);
+    cp_group4<R>(slot + 4, s.V + q);
+    cp_group4<R>(slot + 8, s.Ba + q);
+    if (D == 3) {
+        cp_group4<R>(slot + 12, s.Bb + q);
+        cp_group4<R>(slot + 16, s.Fa + q);
+        cp_group4<R>(slot + 20, s.Fb + q);
+        if (sizeof(R) == 4) cp_async8(slot + 24, s.Fc + q);
+        else cp_async16(slot + 24, s.Fc + q);
+    } else {
+        cp_group4<R>(slot + 12, s.Fa + q);
+    }
+}
+
+template <int D, typename R> __device__ __forceinline__ void read_staged(const R* slot, Particle<D, R>& p)
+{
+    const V4<R> a = *reinterpret_cast<const V4<R>*>(slot + 0);
+    const V4<R> v = *reinterpret_cast<const V4<R>*>(slot + 4);
+    const V4<R> ba = *reinterpret_cast<const V4<R>*>(slot + 8);
+    if (D == 3) {
+        const V4<R> bb = *reinterpret_cast<const V4<R>*>(slot + 12);
+        const V4<R> fa = *reinterpret_cast<const V4<R>*>(slot + 16);
+        const V4<R> fb = *reinterpret_cast<const V4<R>*>(slot + 20);
+        const V2<R> fc = *reinterpret_cast<const V2<R>*>(slot + 24);
+        p.o[0] = a.x; p.o[1] = a.y; p.o[2] = a.z;
+        unpack_cell<D>(r2u(a.w), p.cell);
+        p.v[0] = v.x; p.v[1] = v.y; p.v[2] = v.z;
+        p.B[0] = v.w; p.B[1] = ba.x; p.B[2] = ba.y; p.B[3] = ba.z; p.B[4] = ba.w;
+        p.B[5] = bb.x; p.B[6] = bb.y; p.B[7] = bb.z; p.B[8] = bb.w;
+        p.F[0] = fa.x; p.F[1] = fa.y; p.F[2] = fa.z; p.F[3] = fa.w;
+        p.F[4] = fb.x; p.F[5] = fb.y; p.F[6] = fb.z; p.F[7] = fb.w;
+        p.F[8] = fc.x; p.id = r2u(fc.y);
+    } else {
+        const V4<R> fa = *reinterpret_cast<const V4<R>*>(slot + 12);
+        p.o[0] = a.x; p.o[1] = a.y;
+        unpack_cell<D>(r2u(a.z), p.cell);
+        p.id = r2u(a.w);
+        p.v[0] = v.x; p.v[1] = v.y;
+        p.B[0] = v.z; p.B[1] = v.w; p.B[2] = ba.x; p.B[3] = ba.y;
+        p.F[0] = fa.x; p.F[1] = fa.y; p.F[2] = fa.z; p.F[3] = fa.w;
+    }
+}
+
+// staging depth (particles in flight per lane) of the cell-parallel P2G
+template <typename R> __host__ __device__ constexpr int p2g_slots() { return sizeof(R) == 4 ? 3 : 2; }
+
+template <int D, int ORDER, typename R> __host__ __device__ constexpr size_t p2g_cellsum_bytes()
+{
+    return (size_t)((D == 3) ? 64 : 16) * ((D == 3) ? (ORDER + 1) * (ORDER + 1) * (ORDER + 1) : (ORDER + 1) * (ORDER + 1)) *
+           (D + 1) * sizeof(R);
+}
+// dynamic shared memory of the cell-parallel P2G: per-cell sums, then the staging slots
+template <int D, int ORDER, typename R> __host__ __device__ constexpr size_t p2g_cells_smem()
+{
+    return (p2g_cellsum_bytes<D, ORDER, R>() + 15) / 16 * 16 + (size_t)p2g_slots<R>() * 128 * slot_words<D>() * sizeof(R);
+}
+
 // ---------------------------------------------------------------- P2G, cell-parallel
 // Butterfly reduce-scatter of N register values over a group of lanes: at distance H the
 // lane with bit H set keeps the upper half of its values and receives its partner's upper
@@ -353,7 +441,7 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
                                                const uint32_t* __restrict__ skeys, uint32_t start, uint32_t end,
                                                R* __restrict__ acc, uint32_t* __restrict__ flags, const DevCfg<R>& c,
                                                uint32_t* err, uint32_t* fallbacks, R* cellsum, uint32_t* cbeg,
-                                               uint32_t* cend, int* s_cell)
+                                               uint32_t* cend, int* s_cell, R* pslots)
 {
     constexpr int NT = 128;
     constexpr int K = ORDER + 1;
@@ -393,19 +481,26 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
             R cur[NVAL];
 #pragma unroll
             for (int i = 0; i < NVAL; ++i) cur[i] = R(0);
-            // the next particle's state is requested before the current one is processed
-            Particle<D, R> nxt;
-            if (kb + lig < ke) {
-                const uint32_t q = perm[kb + lig];
-                load_xF<D, R>(st, q, nxt);
-                load_vB<D, R>(st, q, nxt);
+            // this lane's particles kb + lig + i G are staged NSL ahead through shared memory
+            constexpr int NSL = p2g_slots<R>();
+            constexpr int SW = slot_words<D>();
+#pragma unroll
+            for (int i = 0; i < NSL; ++i) {
+                const uint32_t kk = kb + lig + (uint32_t)(i * G);
+                if (kk < ke) stage_particle<D, R>(pslots + (size_t)(i * NT + threadIdx.x) * SW, st, perm[kk]);
+                cp_async_commit();
             }
-            for (uint32_t k = kb + lig; k < ke; k += G) {
-                const Particle<D, R> p = nxt;
-                if (k + G < ke) {
-                    const uint32_t q = perm[k + G];
-                    load_xF<D, R>(st, q, nxt);
-                    load_vB<D, R>(st, q, nxt);
+            int it = 0;
+            for (uint32_t k = kb + lig; k < ke; k += G, ++it) {
+                cp_async_wait<NSL - 1>();
+                const int sl = it % NSL;
+                R* slot = pslots + (size_t)(sl * NT + threadIdx.x) * SW;
+                Particle<D, R> p;
+                read_staged<D, R>(slot, p);
+                {
+                    const uint32_t kn = k + (uint32_t)(NSL * G);
+                    if (kn < ke) stage_particle<D, R>(slot, st, perm[kn]);
+                    cp_async_commit();
                 }
                 int base[D];
                 R w[D][K], dw[D][K], fx[D];
@@ -477,6 +572,7 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
                         }
                 }
             }
+            cp_async_wait<0>();
             int off = 0, cnt = NVAL;
             ReduceScatter<R, NVAL, G>::run(cur, gmask, lig, off, cnt);
             constexpr int FIN = ReduceScatter<R, NVAL, G>::FINAL;
@@ -544,6 +640,7 @@ __global__ void __launch_bounds__(128, 2) k_p2g_cells(PState<R> st, const uint32
     constexpr int NC = (D == 3) ? 64 : 16;
     extern __shared__ __align__(16) unsigned char p2g_smem[];
     R* cellsum = reinterpret_cast<R*>(p2g_smem);   // [NC][NVAL]
+    R* pslots = reinterpret_cast<R*>(p2g_smem + (p2g_cellsum_bytes<D, ORDER, R>() + 15) / 16 * 16);
     __shared__ uint32_t cbeg[NC], cend[NC];
     __shared__ int s_tile, s_cell;
     const int ntiles = (int)*ntiles_p;
@@ -557,15 +654,10 @@ __global__ void __launch_bounds__(128, 2) k_p2g_cells(PState<R> st, const uint32
         const int t = s_tile;
         if (t >= ntiles) break;
         p2g_cells_tile<D, ORDER, R, G>(st, perm, skeys, tiles[t], tiles[t + 1], acc, flags, c, err, fallbacks, cellsum,
-                                       cbeg, cend, &s_cell);
+                                       cbeg, cend, &s_cell, pslots);
     }
 }
 
-template <int D, int ORDER, typename R> constexpr size_t p2g_cells_smem()
-{
-    return (size_t)((D == 3) ? 64 : 16) * ((D == 3) ? (ORDER + 1) * (ORDER + 1) * (ORDER + 1) : (ORDER + 1) * (ORDER + 1)) *
-           (D + 1) * sizeof(R);
-}
 
 // ---------------------------------------------------------------- P2G, cell-interleaved
 // Threads of a warp take particles of distinct base cells of the tile (thread t serves
