@@ -146,14 +146,14 @@ Layout layout_of(const HostCfg& c)
     L.kB = cv.take((size_t)n * 4);
     L.vA = cv.take((size_t)n * 4);
     L.vB = cv.take((size_t)n * 4);
-    L.radix_counts = cv.take((size_t)256 * radix_tiles(n) * 4);
+    L.radix_counts = cv.take((size_t)256 * (radix_tiles(n) + 4) * 4);
     const int64_t nchunks = (n + c.tile - 1) / c.tile;
     L.scan_part = cv.take(scan_partials_needed(n > nchunks ? n : nchunks) * 4);
     L.max_tiles = nchunks + (n < c.nblocks ? n : c.nblocks) + 2;
     L.tiles = cv.take((size_t)(L.max_tiles + 1) * 4);
     L.chunk_cnt = cv.take((size_t)(nchunks + 1) * 4);
     L.ntiles = cv.take(4);
-    L.tile_ctr = cv.take(8);
+    L.tile_ctr = cv.take(16);
     const size_t bn = c.dim == 3 ? 64 : 16;
     L.acc = cv.take((size_t)c.nblocks * bn * 4 * R);
     L.vel = cv.take((size_t)c.nblocks * bn * 4 * R);
@@ -451,7 +451,7 @@ apic_status apic_p2g(apic_sim* s)
         CK(DISPATCH(s, keys, s->c, s->b, s->cur, n, s->stream), "keys kernel");
     }
     {
-        PhaseScope ps(s, APIC_PHASE_SORT, 5 * ((s->c.key_bits + 7) / 8));
+        PhaseScope ps(s, APIC_PHASE_SORT, 2 + ((s->c.key_bits + 7) / 8));
         CK(radix_sort(s->b, n, s->c.key_bits, s->stream, &s->skeys, &s->perm), "radix sort");
     }
     {

@@ -24,7 +24,7 @@ struct Buffers {
     uint32_t* tiles;             // tile start offsets (+ end sentinel)
     uint32_t* chunk_cnt;         // per-chunk tile counts (scanned in place)
     uint32_t* ntiles;            // device counter: number of tiles
-    uint32_t* tile_ctr;          // 2 work counters (P2G, G2P), zeroed with each tile list
+    uint32_t* tile_ctr;          // work counters: [0] P2G, [1] G2P (zeroed with each tile list), [2] sort tiles
     void* acc;                   // accumulation grid (4 lanes per node)
     void* vel;                   // velocity grid (4 lanes per node)
     uint32_t* flags;             // active node blocks

@@ -269,6 +269,145 @@ __global__ void __launch_bounds__(256) k_tile_write(const uint32_t* __restrict__
     }
 }
 
+// ---------------------------------------------------------------- one-sweep passes
+// All digit histograms in one read of the keys, then one kernel per pass: a tile ranks its
+// keys as in radix_scatter_tile, publishes its per-digit counts, and finds the counts of
+// all earlier tiles by looking back over their published words (decoupled look-back:
+// a word holds a flag -- tile aggregate, or inclusive prefix -- and a 30-bit count).
+// Tiles take their index from a counter, so every earlier tile is already resident and
+// the look-back always ends; each wait is still bounded and latches APIC_ERRBIT_TIMEOUT.
+constexpr uint32_t LB_AGG = 1u << 30;
+constexpr uint32_t LB_INC = 2u << 30;
+constexpr uint32_t LB_VAL = (1u << 30) - 1u;
+
+__global__ void __launch_bounds__(256) k_onesweep_hist(const uint32_t* __restrict__ keys, int64_t n, int passes,
+                                                       uint32_t* __restrict__ ghist)
+{
+    __shared__ uint32_t h[4][256];
+    for (int i = threadIdx.x; i < 4 * 256; i += 256) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * 256; base < n; base += (int64_t)gridDim.x * 256) {
+        const int64_t k = base + threadIdx.x;
+        const bool valid = k < n;
+        const uint32_t key = valid ? keys[k] : 0u;
+        for (int p = 0; p < passes; ++p) {
+            const unsigned d = valid ? (key >> (8 * p)) & 255u : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int p = 0; p < passes; ++p)
+        if (h[p][threadIdx.x]) atomicAdd(&ghist[p * 256 + threadIdx.x], h[p][threadIdx.x]);
+}
+
+// exclusive scan of each pass's 256-bin histogram, in place (one CTA)
+__global__ void __launch_bounds__(256) k_onesweep_digits(uint32_t* __restrict__ ghist, int passes)
+{
+    for (int p = 0; p < passes; ++p) {
+        const uint32_t v = ghist[p * 256 + threadIdx.x];
+        uint32_t ex;
+        block_excl_scan(v, ex);
+        ghist[p * 256 + threadIdx.x] = ex;
+    }
+}
+
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p)
+{
+    uint32_t v;
+    asm volatile("ld.volatile.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_volatile(uint32_t* p, uint32_t v)
+{
+    asm volatile("st.volatile.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__global__ void __launch_bounds__(RT) k_onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                      uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
+                                                      int shift, const uint32_t* __restrict__ dstart,
+                                                      uint32_t* __restrict__ status, uint32_t* __restrict__ tile_ctr,
+                                                      uint32_t* __restrict__ err)
+{
+    __shared__ uint32_t wc[RW][256];
+    __shared__ uint32_t goff[256];
+    __shared__ uint32_t s_t;
+    if (threadIdx.x == 0) s_t = atomicAdd(tile_ctr, 1u);
+    for (int i = threadIdx.x; i < RW * 256; i += RT) (&wc[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t t = s_t;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = (int64_t)t * RTILE + w * (RI * 32);
+    uint32_t key[RI], val[RI], lr[RI];
+    unsigned dig[RI];
+#pragma unroll
+    for (int r = 0; r < RI; ++r) {
+        const int64_t idx = base + r * 32 + lane;
+        const bool valid = idx < n;
+        key[r] = valid ? kin[idx] : 0u;
+        val[r] = valid ? (vin ? vin[idx] : (uint32_t)idx) : 0u;
+        const unsigned d = valid ? (key[r] >> shift) & 255u : 256u;
+        dig[r] = d;
+        const unsigned peers = __match_any_sync(FULL, d);
+        const unsigned before = (unsigned)__popc(peers & lanemask_lt());
+        const uint32_t cnt = valid ? wc[w][d] : 0u;
+        __syncwarp();
+        lr[r] = cnt + before;
+        if (valid && lane == __ffs(peers) - 1) wc[w][d] = cnt + (uint32_t)__popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // thread d: tile count of digit d, warp bases, then the look-back for digit d
+    {
+        const int d = threadIdx.x;
+        uint32_t run = 0;
+        for (int ww = 0; ww < RW; ++ww) {
+            const uint32_t c = wc[ww][d];
+            wc[ww][d] = run;
+            run += c;
+        }
+        uint32_t* my = status + (size_t)t * 256 + d;
+        if (t == 0) {
+            st_volatile(my, LB_INC | run);
+            goff[d] = dstart[d];
+        } else {
+            st_volatile(my, LB_AGG | run);
+            uint32_t excl = 0;
+            int64_t j = (int64_t)t - 1;
+            uint32_t spins = 0;
+            while (j >= 0) {
+                const uint32_t v = ld_volatile(status + (size_t)j * 256 + d);
+                const uint32_t f = v & ~LB_VAL;
+                if (f == 0u) {
+                    if (++spins > (1u << 22)) {   // bounded: a predecessor never published
+                        atomicOr(err, APIC_ERRBIT_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(32);
+                    continue;
+                }
+                excl += v & LB_VAL;
+                if (f == LB_INC) break;
+                --j;
+            }
+            st_volatile(my, LB_INC | (excl + run));
+            goff[d] = dstart[d] + excl;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RI; ++r) {
+        const int64_t idx = base + r * 32 + lane;
+        if (idx < n) {
+            const unsigned d = dig[r];
+            const uint32_t pos = goff[d] + wc[w][d] + lr[r];
+            kout[pos] = key[r];
+            vout[pos] = val[r];
+        }
+    }
+}
+
 // ---------------------------------------------------------------- batched forms
 // Work item -> simulation tables (rt_sim per radix tile, ch_sim per chunk) are built on the
 // host when membership changes.  Counts of all simulations sit in one array laid out
@@ -361,12 +500,21 @@ cudaError_t radix_sort(const Buffers& b, int64_t n, int key_bits, cudaStream_t s
     const uint32_t* vin = nullptr;
     uint32_t* kb[2] = {b.kA, b.kB};
     uint32_t* vb[2] = {b.vA, b.vB};
+    // one-sweep form: digit histograms of every pass in one read, then one kernel per pass
+    // (scratch: radix_counts holds [passes][256] digit starts, then the look-back words)
+    uint32_t* dstart = b.radix_counts;
+    uint32_t* status = b.radix_counts + 4 * 256;
+    cudaError_t e = cudaMemsetAsync(dstart, 0, sizeof(uint32_t) * 256 * passes, s);
+    if (e != cudaSuccess) return e;
+    int grid = nt < 1024 ? nt : 1024;
+    k_onesweep_hist<<<grid > 0 ? grid : 1, 256, 0, s>>>(b.knext, n, passes, dstart);
+    k_onesweep_digits<<<1, 256, 0, s>>>(dstart, passes);
     for (int p = 0; p < passes; ++p) {
-        const int shift = 8 * p;
-        k_radix_hist<<<nt, RT, 0, s>>>(kin, n, shift, nt, b.radix_counts);
-        cudaError_t e = exclusive_scan(b.radix_counts, b.radix_counts, 256 * (int64_t)nt, b.scan_part, nullptr, s);
+        e = cudaMemsetAsync(status, 0, sizeof(uint32_t) * 256 * (size_t)nt, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b.tile_ctr + 2, 0, sizeof(uint32_t), s);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<<<nt, RT, 0, s>>>(kin, vin, kb[p & 1], vb[p & 1], n, shift, nt, b.radix_counts);
+        k_onesweep_pass<<<nt, RT, 0, s>>>(kin, vin, kb[p & 1], vb[p & 1], n, 8 * p, dstart + 256 * p, status,
+                                          b.tile_ctr + 2, b.err);
         kin = kb[p & 1];
         vin = vb[p & 1];
     }
