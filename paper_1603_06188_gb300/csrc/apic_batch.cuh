@@ -98,34 +98,53 @@ __global__ void __launch_bounds__(128, 2) kb_p2g_cells(SimDesc<R>* __restrict__ 
 }
 
 template <int D, int ORDER, typename R>
-__global__ void __launch_bounds__(TPB) kb_g2p(SimDesc<R>* __restrict__ descs, const uint32_t* __restrict__ tile_sim,
+__global__ void __launch_bounds__(TPB, 2) kb_g2p(SimDesc<R>* __restrict__ descs, const uint32_t* __restrict__ tile_sim,
                                               const uint32_t* __restrict__ tile_start,
                                               const uint32_t* __restrict__ ntiles_p, uint32_t* __restrict__ tile_ctr,
                                               int kpar)
 {
     constexpr int BN = (D == 3) ? 64 : 16;
     constexpr int NB = 1 << D;
-    __shared__ __align__(128) R sv[NB][BN][4];
-    __shared__ __align__(8) uint64_t mbar;
-    __shared__ int s_ok;
-    __shared__ int s_tile;
+    __shared__ __align__(128) R sv[2][NB][BN][4];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ int s_ok, s_next;
     __shared__ __align__(16) SimDesc<R> sd;
-    if (threadIdx.x == 0) mbar_init(&mbar, 1);
-    unsigned phase = 0;
+    unsigned phase[2] = {0u, 0u};
     const int ntiles = (int)*ntiles_p;
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_ctr + 1, 1u);
-        __syncthreads();
-        const int t = s_tile;
-        if (t >= ntiles) break;
+    // thread 0 starts the grid-block copies of tile t (its simulation read from global)
+    auto issue = [&](int t, int b) {
+        const SimDesc<R>& d = descs[tile_sim[t]];
+        const uint32_t blk = d.kb[kpar][tile_start[t]] >> (2 * D);
+        g2p_issue<D, R>(d.vel, blk, d.c.nb, sv[b], &mbar[b]);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        const int t0 = (int)atomicAdd(tile_ctr + 1, 1u);
+        s_next = t0;
+        if (t0 < ntiles) issue(t0, 0);
+    }
+    __syncthreads();
+    int t = s_next, buf = 0;
+    while (t < ntiles) {
         const uint32_t sim = tile_sim[t];
         load_desc<R>(&sd, descs + sim, TPB);
+        if (threadIdx.x == 0) {
+            const int t1 = (int)atomicAdd(tile_ctr + 1, 1u);
+            s_next = t1;
+            if (t1 < ntiles) issue(t1, buf ^ 1);
+            s_ok = g2p_wait(&mbar[buf], phase[buf], sd.err) ? 1 : 0;
+        }
         __syncthreads();
+        if (!s_ok) return;
         const uint32_t start = tile_start[t];
         const uint32_t end = tile_end(tile_sim, tile_start, t, ntiles, sim, (uint32_t)sd.c.n);
-        if (!g2p_tile<D, ORDER, R>(sd.st[sd.cur], sd.st[sd.cur ^ 1], sd.vb[kpar], sd.kb[kpar], start, end, sd.vel,
-                                   sd.knext, sd.c, sd.err, sv, &mbar, phase, &s_ok))
-            return;
+        g2p_compute<D, ORDER, R>(sd.st[sd.cur], sd.st[sd.cur ^ 1], sd.vb[kpar], sd.kb[kpar], start, end, sd.knext, sd.c,
+                                 sd.err, sv[buf]);
+        __syncthreads();
+        phase[buf] ^= 1u;
+        buf ^= 1;
+        t = s_next;
     }
 }
 

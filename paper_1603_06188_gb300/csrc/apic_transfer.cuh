@@ -912,54 +912,69 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 // gathers v_p = sum w v~, B_p = sum w v~ (x_i - x_p)^T, grad v = sum v~ grad w^T, updates
 // F_p <- (I + dt grad v) F_p and x_p <- x_p + dt v_p, and is written at its sorted slot
 // together with its next cell key.
-// One tile of G2P (whole CTA, TPB threads, converged on entry).  Returns false if the
-// bulk-copy wait timed out (the CTA must then leave).
-template <int D, int ORDER, typename R>
-__device__ __forceinline__ bool g2p_tile(const PState<R>& in, const PState<R>& out, const uint32_t* __restrict__ perm,
-                                         const uint32_t* __restrict__ skeys, uint32_t start, uint32_t end,
-                                         const R* __restrict__ vel, uint32_t* __restrict__ knext, const DevCfg<R>& c,
-                                         uint32_t* err, R (*sv)[(D == 3) ? 64 : 16][4], uint64_t* mbar,
-                                         unsigned& phase, int* s_ok)
+// G2P works tile by tile with two staging buffers: while a tile's particles are processed,
+// the 2^D grid blocks of the next tile are already in flight (bulk copies completing on that
+// buffer's mbarrier), so the copy latency is hidden behind arithmetic.
+
+// thread 0: start the bulk copies of the 2^D velocity blocks around node block `blk`
+template <int D, typename R>
+__device__ __forceinline__ void g2p_issue(const R* __restrict__ vel, uint32_t blk, const int* nb,
+                                          R (*sv)[(D == 3) ? 64 : 16][4], uint64_t* mbar)
 {
-    constexpr int K = ORDER + 1;
     constexpr int BN = (D == 3) ? 64 : 16;
     constexpr int NB = 1 << D;
+    int bc[3];
+    bc[0] = (int)(blk % (uint32_t)nb[0]);
+    if (D == 3) {
+        bc[1] = (int)((blk / (uint32_t)nb[0]) % (uint32_t)nb[1]);
+        bc[2] = (int)(blk / ((uint32_t)nb[0] * (uint32_t)nb[1]));
+    } else {
+        bc[1] = (int)(blk / (uint32_t)nb[0]);
+        bc[2] = 0;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    unsigned nblk = 0;
+    bool inb[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        inb[q] = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            if (bc[a] + ((q >> a) & 1) >= nb[a]) inb[q] = false;
+        nblk += inb[q] ? 1u : 0u;
+    }
+    const unsigned bytes = (unsigned)(BN * 4 * sizeof(R));
+    mbar_expect_tx(mbar, nblk * bytes);
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        if (!inb[q]) continue;
+        const int bb[3] = {bc[0] + (q & 1), bc[1] + ((q >> 1) & 1), (D == 3) ? bc[2] + ((q >> 2) & 1) : 0};
+        const uint32_t b2 = (D == 3) ? ((uint32_t)bb[2] * nb[1] + bb[1]) * nb[0] + bb[0] : (uint32_t)bb[1] * nb[0] + bb[0];
+        bulk_copy_g2s(&sv[q][0][0], vel + (size_t)b2 * BN * 4, bytes, mbar);
+    }
+}
+
+// thread 0: wait (bounded) for a buffer's copies; false on timeout
+__device__ __forceinline__ bool g2p_wait(uint64_t* mbar, unsigned parity, uint32_t* err)
+{
+    if (mbar_wait_bounded(mbar, parity, 1u << 22)) return true;
+    set_err(err, APIC_ERRBIT_TIMEOUT);
+    mbar_wait_bounded(mbar, parity, 1u << 22);   // let the copies in flight land before leaving
+    return false;
+}
+
+// the particles of one tile, with its grid blocks already in sv (whole CTA)
+template <int D, int ORDER, typename R>
+__device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>& out, const uint32_t* __restrict__ perm,
+                                            const uint32_t* __restrict__ skeys, uint32_t start, uint32_t end,
+                                            uint32_t* __restrict__ knext, const DevCfg<R>& c, uint32_t* err,
+                                            const R (*sv)[(D == 3) ? 64 : 16][4])
+{
+    constexpr int K = ORDER + 1;
     const R dt_dx = c.dt * c.inv_dx;
     const uint32_t blk = skeys[start] >> (2 * D);
     int bc[3] = {0, 0, 0};
     block_coords<D, R>(blk, c, bc);
-    if (threadIdx.x == 0) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        unsigned nblk = 0;
-        bool inb[NB];
-#pragma unroll
-        for (int q = 0; q < NB; ++q) {
-            inb[q] = true;
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-                if (bc[a] + ((q >> a) & 1) >= c.nb[a]) inb[q] = false;
-            nblk += inb[q] ? 1u : 0u;
-        }
-        const unsigned bytes = (unsigned)(BN * 4 * sizeof(R));
-        mbar_expect_tx(mbar, nblk * bytes);
-#pragma unroll
-        for (int q = 0; q < NB; ++q) {
-            if (!inb[q]) continue;
-            int bb[3] = {bc[0] + (q & 1), bc[1] + ((q >> 1) & 1), (D == 3) ? bc[2] + ((q >> 2) & 1) : 0};
-            const uint32_t b2 = (D == 3) ? ((uint32_t)bb[2] * c.nb[1] + bb[1]) * c.nb[0] + bb[0]
-                                         : (uint32_t)bb[1] * c.nb[0] + bb[0];
-            bulk_copy_g2s(&sv[q][0][0], vel + (size_t)b2 * BN * 4, bytes, mbar);
-        }
-        bool ok = mbar_wait_bounded(mbar, phase, 1u << 22);
-        if (!ok) {
-            set_err(err, APIC_ERRBIT_TIMEOUT);
-            mbar_wait_bounded(mbar, phase, 1u << 22);
-        }
-        *s_ok = ok ? 1 : 0;
-    }
-    __syncthreads();
-    if (!*s_ok) return false;
-    phase ^= 1u;
     // the next round's particle is requested before the current one is processed
     Particle<D, R> nxt;
     if (start + threadIdx.x < end) load_xF<D, R>(in, perm[start + threadIdx.x], nxt);
@@ -1083,12 +1098,10 @@ __device__ __forceinline__ bool g2p_tile(const PState<R>& in, const PState<R>& o
         store_all<D, R>(out, k, p);
         knext[k] = key_of<D, ORDER, R>(p.o, p.cell, c, err);
     }
-    __syncthreads();
-    return true;
 }
 
 template <int D, int ORDER, typename R>
-__global__ void __launch_bounds__(TPB) k_g2p(PState<R> in, PState<R> out, const uint32_t* __restrict__ perm,
+__global__ void __launch_bounds__(TPB, 2) k_g2p(PState<R> in, PState<R> out, const uint32_t* __restrict__ perm,
                                              const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ tiles,
                                              const uint32_t* __restrict__ ntiles_p, uint32_t* __restrict__ tile_ctr,
                                              const R* __restrict__ vel, uint32_t* __restrict__ knext, DevCfg<R> c,
@@ -1096,22 +1109,36 @@ __global__ void __launch_bounds__(TPB) k_g2p(PState<R> in, PState<R> out, const 
 {
     constexpr int BN = (D == 3) ? 64 : 16;
     constexpr int NB = 1 << D;
-    __shared__ __align__(128) R sv[NB][BN][4];
-    __shared__ __align__(8) uint64_t mbar;
-    __shared__ int s_ok;
-    __shared__ int s_tile;
-    if (threadIdx.x == 0) mbar_init(&mbar, 1);
-    unsigned phase = 0;
+    __shared__ __align__(128) R sv[2][NB][BN][4];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ int s_ok, s_next;
+    unsigned phase[2] = {0u, 0u};
     const int ntiles = (int)*ntiles_p;
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_ctr + 1, 1u);
-        __syncthreads();
-        const int t = s_tile;
-        if (t >= ntiles) break;
-        if (!g2p_tile<D, ORDER, R>(in, out, perm, skeys, tiles[t], tiles[t + 1], vel, knext, c, err, sv, &mbar, phase,
-                                   &s_ok))
-            return;
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        const int t0 = (int)atomicAdd(tile_ctr + 1, 1u);
+        s_next = t0;
+        if (t0 < ntiles) g2p_issue<D, R>(vel, skeys[tiles[t0]] >> (2 * D), c.nb, sv[0], &mbar[0]);
     }
+    __syncthreads();
+    int t = s_next, buf = 0;
+    while (t < ntiles) {
+        if (threadIdx.x == 0) {
+            const int t1 = (int)atomicAdd(tile_ctr + 1, 1u);
+            s_next = t1;
+            if (t1 < ntiles) g2p_issue<D, R>(vel, skeys[tiles[t1]] >> (2 * D), c.nb, sv[buf ^ 1], &mbar[buf ^ 1]);
+            s_ok = g2p_wait(&mbar[buf], phase[buf], err) ? 1 : 0;
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        g2p_compute<D, ORDER, R>(in, out, perm, skeys, tiles[t], tiles[t + 1], knext, c, err, sv[buf]);
+        __syncthreads();
+        phase[buf] ^= 1u;
+        buf ^= 1;
+        t = s_next;
+    }
+    // a copy issued for a tile index past the end is never issued; nothing is left in flight
 }
 
 // ---------------------------------------------------------------- momentum (FP64)
