@@ -655,7 +655,8 @@ struct apic_batch {
     // workspace
     void* descs;
     SortDesc* sortdescs;
-    uint32_t *rt_sim, *ch_sim, *bbase, *counts, *scan_part, *chunk_cnt, *tile_sim, *tile_start, *ntiles, *tile_ctr, *err;
+    uint32_t *rt_sim, *ch_sim, *bbase, *counts, *scan_part, *chunk_cnt, *tile_sim, *tile_start, *ntiles, *tile_ctr, *err,
+        *digits;
     int64_t max_rtiles, max_chunks, max_tiles;
     size_t desc_bytes;
     // membership
@@ -678,7 +679,7 @@ constexpr int kBatchTiles[3] = {1024, 2048, 4096};
 
 struct BatchLayout {
     size_t descs, sortdescs, rt_sim, ch_sim, bbase, counts, scan_part, chunk_cnt, tile_sim, tile_start, ntiles, tile_ctr,
-        err, total;
+        err, digits, total;
     int64_t max_rtiles, max_chunks, max_tiles;
 };
 
@@ -702,8 +703,9 @@ BatchLayout batch_layout(const apic_batch_config* c)
     L.tile_sim = cv.take((size_t)L.max_tiles * 4);
     L.tile_start = cv.take((size_t)L.max_tiles * 4);
     L.ntiles = cv.take(4);
-    L.tile_ctr = cv.take(8);
+    L.tile_ctr = cv.take(16);
     L.err = cv.take(4);
+    L.digits = cv.take((size_t)c->max_sims * 4 * 256 * 4);
     L.total = cv.cur;
     return L;
 }
@@ -805,11 +807,12 @@ apic_status batch_rebuild(apic_batch* b)
 cudaError_t batch_enqueue(apic_batch* b)
 {
     const int kpar = (b->passes - 1) & 1;
-    cudaError_t e = batch_radix_sort(b->sortdescs, b->rt_sim, b->total_rtiles, b->passes, b->counts, b->scan_part, b->stream);
+    const int S = (int)b->members.size();
+    cudaError_t e = batch_radix_sort(b->sortdescs, b->rt_sim, b->total_rtiles, b->passes, S, b->digits, b->counts,
+                                     b->tile_ctr, b->err, b->stream);
     if (e == cudaSuccess)
         e = batch_build_tiles(b->sortdescs, b->ch_sim, b->total_chunks, b->dim, b->tile, kpar, b->chunk_cnt, b->scan_part,
                               b->ntiles, b->max_tiles, b->tile_sim, b->tile_start, b->err, b->tile_ctr, b->stream);
-    const int S = (int)b->members.size();
     if (e == cudaSuccess)
         e = b->precision == 32 ? batch_p2g_f32(b->dim, b->order, b->group, b->descs, b->tile_sim, b->tile_start, b->ntiles,
                                                b->tile_ctr, kpar, b->p2g_grid, b->stream)
@@ -827,7 +830,7 @@ cudaError_t batch_enqueue(apic_batch* b)
     return e;
 }
 
-int64_t batch_kernels_per_step(const apic_batch* b) { return (int64_t)b->passes * 5 + 5 + 4; }
+int64_t batch_kernels_per_step(const apic_batch* b) { return 2 + (int64_t)b->passes + 5 + 4; }
 
 apic_status batch_run(apic_batch* b, int n)
 {
@@ -929,6 +932,7 @@ apic_status apic_batch_create(const apic_batch_config* c, void* workspace, size_
     b->ntiles = (uint32_t*)(base + L.ntiles);
     b->tile_ctr = (uint32_t*)(base + L.tile_ctr);
     b->err = (uint32_t*)(base + L.err);
+    b->digits = (uint32_t*)(base + L.digits);
     b->max_rtiles = L.max_rtiles;
     b->max_chunks = L.max_chunks;
     b->max_tiles = L.max_tiles;
@@ -1102,6 +1106,7 @@ apic_status apic_batch_stats(apic_batch* b, int64_t out[5])
     out[2] = b->steps;
     out[3] = b->launches;
     out[4] = nt;
+    if (e & APIC_ERRBIT_TIMEOUT) return batch_fail(b, APIC_ERR_TIMEOUT, "a bounded device wait (sort look-back) ran out");
     if (e) return batch_fail(b, APIC_ERR_OOM, "batch tile capacity exceeded");
     return APIC_OK;
 }

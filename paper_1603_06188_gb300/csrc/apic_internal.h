@@ -74,7 +74,8 @@ cudaError_t build_tiles(const Buffers& b, const uint32_t* skeys, int64_t n, int 
 cudaError_t exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* part,
                            uint32_t* total, cudaStream_t s);
 cudaError_t batch_radix_sort(const SortDesc* sd, const uint32_t* rt_sim, uint32_t total_rtiles, int passes,
-                             uint32_t* counts, uint32_t* part, cudaStream_t s);
+                             int nsims, uint32_t* digits, uint32_t* status, uint32_t* tile_ctr, uint32_t* err,
+                             cudaStream_t s);
 cudaError_t batch_build_tiles(const SortDesc* sd, const uint32_t* ch_sim, uint32_t total_chunks, int dim, int tile,
                               int kpar, uint32_t* cnt, uint32_t* part, uint32_t* ntiles, int64_t max_tiles,
                               uint32_t* tile_sim, uint32_t* tile_start, uint32_t* err, uint32_t* tile_ctr,

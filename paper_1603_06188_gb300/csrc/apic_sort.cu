@@ -437,6 +437,135 @@ __global__ void __launch_bounds__(RT) kb_radix_scatter(const SortDesc* __restric
     radix_scatter_tile(kin, vin, d.kb[pass & 1], d.vb[pass & 1], d.n, lt, shift, goff, wc);
 }
 
+// one-sweep form of the batched sort: digit starts per (simulation, pass); the look-back of
+// a tile stops at its simulation's first tile
+__global__ void __launch_bounds__(RT) kb_onesweep_hist(const SortDesc* __restrict__ sd, const uint32_t* __restrict__ rt_sim,
+                                                       int passes, uint32_t* __restrict__ ghist)
+{
+    __shared__ uint32_t h[4][256];
+    for (int i = threadIdx.x; i < 4 * 256; i += RT) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t sim = rt_sim[blockIdx.x];
+    const SortDesc& d = sd[sim];
+    const int64_t lt = (int64_t)blockIdx.x - d.rbase;
+    const int lane = threadIdx.x & 31;
+    for (int r = 0; r < RI; ++r) {
+        const int64_t k = lt * RTILE + (int64_t)r * RT + threadIdx.x;
+        const bool valid = k < d.n;
+        const uint32_t key = valid ? d.knext[k] : 0u;
+        for (int p = 0; p < passes; ++p) {
+            const unsigned dg = valid ? (key >> (8 * p)) & 255u : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, dg);
+            if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[p][dg], (uint32_t)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int p = 0; p < passes; ++p)
+        if (h[p][threadIdx.x]) atomicAdd(&ghist[((size_t)sim * 4 + p) * 256 + threadIdx.x], h[p][threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(256) kb_onesweep_digits(uint32_t* __restrict__ ghist, int passes)
+{
+    uint32_t* g = ghist + (size_t)blockIdx.x * 4 * 256;
+    for (int p = 0; p < passes; ++p) {
+        const uint32_t v = g[p * 256 + threadIdx.x];
+        uint32_t ex;
+        block_excl_scan(v, ex);
+        g[p * 256 + threadIdx.x] = ex;
+    }
+}
+
+__global__ void __launch_bounds__(RT) kb_onesweep_pass(const SortDesc* __restrict__ sd, const uint32_t* __restrict__ rt_sim,
+                                                       int shift, int pass, const uint32_t* __restrict__ ghist,
+                                                       uint32_t* __restrict__ status, uint32_t* __restrict__ tile_ctr,
+                                                       uint32_t* __restrict__ err)
+{
+    __shared__ uint32_t wc[RW][256];
+    __shared__ uint32_t goff[256];
+    __shared__ uint32_t s_t;
+    if (threadIdx.x == 0) s_t = atomicAdd(tile_ctr, 1u);
+    for (int i = threadIdx.x; i < RW * 256; i += RT) (&wc[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t t = s_t;
+    const uint32_t sim = rt_sim[t];
+    const SortDesc& ds = sd[sim];
+    const int64_t lt = (int64_t)t - ds.rbase;
+    const int64_t n = ds.n;
+    const uint32_t* kin = pass == 0 ? ds.knext : ds.kb[(pass - 1) & 1];
+    const uint32_t* vin = pass == 0 ? nullptr : ds.vb[(pass - 1) & 1];
+    uint32_t* kout = ds.kb[pass & 1];
+    uint32_t* vout = ds.vb[pass & 1];
+    const uint32_t* dstart = ghist + ((size_t)sim * 4 + pass) * 256;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = lt * RTILE + w * (RI * 32);
+    uint32_t key[RI], val[RI], lr[RI];
+    unsigned dig[RI];
+#pragma unroll
+    for (int r = 0; r < RI; ++r) {
+        const int64_t idx = base + r * 32 + lane;
+        const bool valid = idx < n;
+        key[r] = valid ? kin[idx] : 0u;
+        val[r] = valid ? (vin ? vin[idx] : (uint32_t)idx) : 0u;
+        const unsigned d = valid ? (key[r] >> shift) & 255u : 256u;
+        dig[r] = d;
+        const unsigned peers = __match_any_sync(FULL, d);
+        const unsigned before = (unsigned)__popc(peers & lanemask_lt());
+        const uint32_t cnt = valid ? wc[w][d] : 0u;
+        __syncwarp();
+        lr[r] = cnt + before;
+        if (valid && lane == __ffs(peers) - 1) wc[w][d] = cnt + (uint32_t)__popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;
+        uint32_t run = 0;
+        for (int ww = 0; ww < RW; ++ww) {
+            const uint32_t c = wc[ww][d];
+            wc[ww][d] = run;
+            run += c;
+        }
+        uint32_t* my = status + (size_t)t * 256 + d;
+        if (lt == 0) {
+            st_volatile(my, LB_INC | run);
+            goff[d] = dstart[d];
+        } else {
+            st_volatile(my, LB_AGG | run);
+            uint32_t excl = 0;
+            int64_t j = (int64_t)t - 1;
+            uint32_t spins = 0;
+            while (j >= (int64_t)ds.rbase) {
+                const uint32_t v = ld_volatile(status + (size_t)j * 256 + d);
+                const uint32_t f = v & ~LB_VAL;
+                if (f == 0u) {
+                    if (++spins > (1u << 22)) {
+                        atomicOr(err, APIC_ERRBIT_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(32);
+                    continue;
+                }
+                excl += v & LB_VAL;
+                if (f == LB_INC) break;
+                --j;
+            }
+            st_volatile(my, LB_INC | (excl + run));
+            goff[d] = dstart[d] + excl;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RI; ++r) {
+        const int64_t idx = base + r * 32 + lane;
+        if (idx < n) {
+            const unsigned d = dig[r];
+            const uint32_t pos = goff[d] + wc[w][d] + lr[r];
+            kout[pos] = key[r];
+            vout[pos] = val[r];
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) kb_tile_count(const SortDesc* __restrict__ sd, const uint32_t* __restrict__ ch_sim,
                                                      int sh, int tile, int kpar, uint32_t* __restrict__ cnt)
 {
@@ -524,14 +653,19 @@ cudaError_t radix_sort(const Buffers& b, int64_t n, int key_bits, cudaStream_t s
 }
 
 cudaError_t batch_radix_sort(const SortDesc* sd, const uint32_t* rt_sim, uint32_t total_rtiles, int passes,
-                             uint32_t* counts, uint32_t* part, cudaStream_t s)
+                             int nsims, uint32_t* digits, uint32_t* status, uint32_t* tile_ctr, uint32_t* err,
+                             cudaStream_t s)
 {
+    if (total_rtiles == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(digits, 0, sizeof(uint32_t) * 4 * 256 * (size_t)nsims, s);
+    if (e != cudaSuccess) return e;
+    kb_onesweep_hist<<<total_rtiles, RT, 0, s>>>(sd, rt_sim, passes, digits);
+    kb_onesweep_digits<<<nsims, 256, 0, s>>>(digits, passes);
     for (int p = 0; p < passes; ++p) {
-        const int shift = 8 * p;
-        kb_radix_hist<<<total_rtiles, RT, 0, s>>>(sd, rt_sim, shift, p, counts);
-        cudaError_t e = exclusive_scan(counts, counts, 256 * (int64_t)total_rtiles, part, nullptr, s);
+        e = cudaMemsetAsync(status, 0, sizeof(uint32_t) * 256 * (size_t)total_rtiles, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(tile_ctr + 2, 0, sizeof(uint32_t), s);
         if (e != cudaSuccess) return e;
-        kb_radix_scatter<<<total_rtiles, RT, 0, s>>>(sd, rt_sim, shift, p, counts);
+        kb_onesweep_pass<<<total_rtiles, RT, 0, s>>>(sd, rt_sim, 8 * p, p, digits, status, tile_ctr + 2, err);
     }
     return cudaGetLastError();
 }
