@@ -1,0 +1,102 @@
+"""Parity at the benchmark's full size and launch configuration (128^3 grid, elastic cube of
+side 0.4 at 32 particles per cell = 4.29M particles, FP32, quadratic, fixed-corotated,
+gravity, sticky walls, default tile and P2G kernel, as bench.py runs it):
+
+- cell keys and the stable sort permutation, every particle, bit-exact;
+- P2G on sampled grid nodes: the oracle is given only the particles whose stencil reaches a
+  sampled node, so its values at those nodes are complete;
+- the grid update on the whole grid;
+- G2P on sampled particles, from the GPU's grid velocities.
+The initial state is deformed and moving (random F, v, B) so every term is exercised."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import kappa, relerr
+from paper_1603_06188_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def run():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import bench
+    from paper_1603_06188_gb300 import apic
+
+    apic.load(build_if_missing=True)
+    w = dict(bench.WORKLOADS["cube128"])
+    sc = scenes.falling_cube_3d(res=128, side=0.4, ppc=32, seed=7, omega=(0.3, -0.5, 1.0), v0=(0.2, 0.0, -0.1))
+    rng = np.random.default_rng(7)
+    x = sc.x
+    v = sc.v + 0.05 * rng.normal(size=sc.v.shape)
+    B = sc.grad_v * kappa(2) * sc.dx ** 2 + 1e-6 * rng.normal(size=(sc.n, 3, 3))
+    F = scenes.random_deformation(rng, sc.n, 3, 0.05)
+    cfg = bench.lib_config(w, sc)
+    sim = apic.Sim(cfg, sc.n)
+    sim.upload(x, v, B, F)
+    x0, v0, B0, F0 = sim.download()
+    cell0, off0 = sim.download_positions()
+    sim.p2g()
+    keys, perm = sim.keys()
+    m_g, p_g = sim.grid("momentum")
+    sim.grid_update()
+    m_v, vt = sim.grid("velocity")
+    sim.g2p()
+    out = sim.download()
+    sim.close()
+    oc = bench.oracle_config(w, sc)
+    vol = sc.dx ** 3 / w["ppc"]
+    return dict(sc=sc, oc=oc, vol=vol, mass=w["rho"] * vol, x0=x0, v0=v0, B0=B0, F0=F0, cell0=cell0, off0=off0,
+                keys=keys, perm=perm, m_g=m_g, p_g=p_g, m_v=m_v, vt=vt, out=out)
+
+
+def test_fullsize_keys_and_sort_bit_exact(run):
+    ref_keys = oracle.keys(run["oc"], 4, run["cell0"], run["off0"])
+    ref_perm = oracle.stable_sort(ref_keys)
+    np.testing.assert_array_equal(run["keys"], ref_keys[ref_perm])
+    np.testing.assert_array_equal(run["perm"].astype(np.int64), ref_perm)
+
+
+def test_fullsize_p2g_sampled_nodes(run):
+    sc, oc = run["sc"], run["oc"]
+    res = 128
+    occupied = np.flatnonzero(run["m_g"] > 0)
+    rng = np.random.default_rng(11)
+    nodes = rng.choice(occupied, size=48, replace=False)
+    ijk = np.stack([nodes % res, (nodes // res) % res, nodes // (res * res)], axis=1)
+    base = np.floor(run["x0"] / sc.dx - 0.5).astype(np.int64)       # quadratic stencil base
+    near = np.zeros(len(base), dtype=bool)
+    for n in ijk:
+        near |= np.all((base <= n) & (n <= base + 2), axis=1)
+    idx = np.flatnonzero(near)
+    gm, gmv, gf, bad = oracle.p2g(oc, run["x0"][idx], run["v0"][idx], run["B0"][idx], run["F0"][idx], run["mass"],
+                                  run["vol"])
+    assert bad == 0
+    ref_m = gm[nodes]
+    ref_p = (gmv + oc.dt * gf)[nodes]
+    assert relerr(run["m_g"][nodes], ref_m) <= TOL
+    assert relerr(run["p_g"][nodes], ref_p) <= TOL
+
+
+def test_fullsize_grid_update(run):
+    oc = run["oc"]
+    _, vt_ref = oracle.grid_update(oc, run["m_g"], run["p_g"], np.zeros_like(run["p_g"]))
+    np.testing.assert_array_equal(run["m_v"], run["m_g"])
+    assert relerr(run["vt"], vt_ref) <= TOL
+
+
+def test_fullsize_g2p_sampled_particles(run):
+    oc = run["oc"]
+    rng = np.random.default_rng(12)
+    idx = rng.choice(run["sc"].n, size=4000, replace=False)
+    x1, v1, B1, F1, bad = oracle.g2p(oc, run["x0"][idx], run["F0"][idx], run["vt"], run["vt"])
+    assert bad == 0
+    gx, gv, gB, gF = (a[idx] for a in run["out"])
+    assert relerr(gv, v1) <= TOL
+    assert relerr(gB, B1) <= TOL
+    assert relerr(gF, F1) <= TOL
+    assert relerr(gx - run["x0"][idx], x1 - run["x0"][idx]) <= TOL
