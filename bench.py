@@ -359,7 +359,9 @@ def run_reference(args, world, rank):
     oracle.build()
     w = WORKLOADS[args.workload]
     sc = make_scene(w)
-    target = args.ref_particles
+    # sample size so the whole run takes about two and a half minutes: the oracle costs about
+    # 2 us per particle-step plus ~0.15 s per step for its dense grid arrays
+    target = args.ref_particles or int(min(300_000, max(5_000, (150.0 / (args.steps + args.warmup) - 0.15) / 2e-6)))
     value, secs, n = time_oracle(w, sc, target, args.steps, warmup=args.warmup)
     sample = (f"slab of {n} of the {sc.n} particles (lowest x), full {w['res']}^3 grid, {args.steps} timed steps "
               f"after {args.warmup} warm-up, FP64 single-threaded oracle")
@@ -385,7 +387,7 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ppc", type=int, default=None)
-    ap.add_argument("--ref-particles", type=int, default=20000)
+    ap.add_argument("--ref-particles", type=int, default=0)
     ap.add_argument("--cpu-sample", type=int, default=300000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
