@@ -78,9 +78,9 @@ typedef struct {
     double particle_volume;  /* V_p (reference volume), the same for every particle */
     int tile_particles;      /* particles per P2G / G2P tile (power of two, 256..4096);
                                 0 = default */
-    int p2g_kernel;          /* P2G variant: 0 = default, 1 = warp-segmented reduction,
-                                2 = cell-parallel (not for 3-D cubic), 3 = cell-interleaved;
-                                results agree to rounding */
+    int p2g_kernel;          /* P2G variant: 0 = default (2, or 1 for 3-D cubic),
+                                1 = warp-segmented reduction, 2 = cell-parallel (not for 3-D
+                                cubic), 3 = cell-interleaved; results agree to rounding */
 } apic_config;
 
 /* Bytes of device workspace a simulation with this config and capacity needs.
