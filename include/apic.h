@@ -78,9 +78,9 @@ typedef struct {
     double particle_volume;  /* V_p (reference volume), the same for every particle */
     int tile_particles;      /* particles per P2G / G2P tile (power of two, 256..4096);
                                 0 = default */
-    int p2g_kernel;          /* P2G variant: 0 = default (2, or 1 for 3-D cubic),
-                                1 = warp-segmented reduction, 2 = cell-parallel (not for 3-D
-                                cubic), 3 = cell-interleaved; results agree to rounding */
+    int p2g_kernel;          /* P2G variant: 0 = default (2), 1 = warp-segmented reduction,
+                                2 = cell-parallel, 3 = cell-interleaved; results agree to
+                                rounding */
 } apic_config;
 
 /* Bytes of device workspace a simulation with this config and capacity needs.
@@ -181,7 +181,7 @@ apic_status apic_profile_read(apic_sim* sim, double ms[APIC_NPHASE], int64_t lau
  * workspace for the shared work lists.  While a simulation is a member, apic_p2g /
  * apic_grid_update / apic_g2p / apic_step / apic_upload on it return APIC_ERR_ARG;
  * apic_download, apic_download_positions and apic_momentum synchronise with the batch
- * first.  3-D cubic members are not supported (APIC_ERR_UNSUPPORTED).
+ * first.
  * ------------------------------------------------------------------------------------ */
 typedef struct apic_batch apic_batch;
 

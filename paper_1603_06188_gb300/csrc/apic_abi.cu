@@ -103,9 +103,7 @@ apic_status fill_cfg(const apic_config* in, int64_t max_particles, HostCfg* c, s
     c->vol = in->particle_volume;
     c->tile = tile;
     if (in->p2g_kernel < 0 || in->p2g_kernel > 3) { *why = "p2g_kernel must be 0, 1, 2 or 3"; return APIC_ERR_ARG; }
-    // default: the cell-parallel P2G where it exists (3-D cubic has no register budget for it)
-    c->p2g_kernel = in->p2g_kernel != 0 ? in->p2g_kernel : ((in->dim == 3 && in->order == 3) ? 1 : 2);
-    if (c->p2g_kernel == 2 && in->dim == 3 && in->order == 3) { *why = "the cell-parallel P2G does not cover 3-D cubic"; return APIC_ERR_UNSUPPORTED; }
+    c->p2g_kernel = in->p2g_kernel != 0 ? in->p2g_kernel : 2;   // default: cell-parallel
     c->key_bits = 2 * in->dim + ceil_log2(c->nblocks);
     if (c->key_bits > 32) { *why = "grid too large for 32-bit cell keys"; return APIC_ERR_UNSUPPORTED; }
     c->capacity = max_particles;
@@ -896,7 +894,6 @@ apic_status apic_batch_create(const apic_batch_config* c, void* workspace, size_
 {
     if (!c || !out) return APIC_ERR_ARG;
     *out = nullptr;
-    if (c->dim == 3 && c->order == 3) return APIC_ERR_UNSUPPORTED;
     if ((c->dim != 2 && c->dim != 3) || (c->order != 2 && c->order != 3)) return APIC_ERR_ARG;
     if (c->precision != 32 && c->precision != 64) return APIC_ERR_ARG;
     if (c->max_sims <= 0 || c->max_particles <= 0 || c->max_blocks <= 0) return APIC_ERR_ARG;

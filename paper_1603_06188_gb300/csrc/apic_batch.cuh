@@ -188,6 +188,7 @@ template <typename R> struct BatchImpl {
         if (dim == 3 && order == 2) return group == 8 ? setup_one<3, 2, 8>(p2g_per_sm, g2p_per_sm) : setup_one<3, 2, 4>(p2g_per_sm, g2p_per_sm);
         if (dim == 2 && order == 2) return group == 8 ? setup_one<2, 2, 8>(p2g_per_sm, g2p_per_sm) : setup_one<2, 2, 4>(p2g_per_sm, g2p_per_sm);
         if (dim == 2 && order == 3) return group == 8 ? setup_one<2, 3, 8>(p2g_per_sm, g2p_per_sm) : setup_one<2, 3, 4>(p2g_per_sm, g2p_per_sm);
+        if (dim == 3 && order == 3) return group == 8 ? setup_one<3, 3, 8>(p2g_per_sm, g2p_per_sm) : setup_one<3, 3, 4>(p2g_per_sm, g2p_per_sm);
         return cudaErrorInvalidValue;
     }
     template <int D, int O, int G>
@@ -202,6 +203,7 @@ template <typename R> struct BatchImpl {
         if (dim == 3 && order == 2) { if (group == 8) p2g_one<3, 2, 8>(descs, ts, tst, nt, ctr, kpar, grid, s); else p2g_one<3, 2, 4>(descs, ts, tst, nt, ctr, kpar, grid, s); }
         else if (dim == 2 && order == 2) { if (group == 8) p2g_one<2, 2, 8>(descs, ts, tst, nt, ctr, kpar, grid, s); else p2g_one<2, 2, 4>(descs, ts, tst, nt, ctr, kpar, grid, s); }
         else if (dim == 2 && order == 3) { if (group == 8) p2g_one<2, 3, 8>(descs, ts, tst, nt, ctr, kpar, grid, s); else p2g_one<2, 3, 4>(descs, ts, tst, nt, ctr, kpar, grid, s); }
+        else if (dim == 3 && order == 3) { if (group == 8) p2g_one<3, 3, 8>(descs, ts, tst, nt, ctr, kpar, grid, s); else p2g_one<3, 3, 4>(descs, ts, tst, nt, ctr, kpar, grid, s); }
         else return cudaErrorInvalidValue;
         return cudaGetLastError();
     }
@@ -219,6 +221,7 @@ template <typename R> struct BatchImpl {
         if (dim == 3 && order == 2) kb_g2p<3, 2, R><<<grid, TPB, 0, s>>>(d, ts, tst, nt, ctr, kpar);
         else if (dim == 2 && order == 2) kb_g2p<2, 2, R><<<grid, TPB, 0, s>>>(d, ts, tst, nt, ctr, kpar);
         else if (dim == 2 && order == 3) kb_g2p<2, 3, R><<<grid, TPB, 0, s>>>(d, ts, tst, nt, ctr, kpar);
+        else if (dim == 3 && order == 3) kb_g2p<3, 3, R><<<grid, TPB, 0, s>>>(d, ts, tst, nt, ctr, kpar);
         else return cudaErrorInvalidValue;
         return cudaGetLastError();
     }

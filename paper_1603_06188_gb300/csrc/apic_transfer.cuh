@@ -451,6 +451,10 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
     constexpr int NV = D + 1;
     constexpr int NVAL = NS * NV;
     constexpr int NC = (D == 3) ? 64 : 16;      // base cells of a node block
+    // 3-D cubic: the 64-node stencil is summed in two z-halves (128 register sums each)
+    constexpr int ZS = (D == 3 && ORDER == 3) ? 2 : 1;
+    constexpr int KZ = (D == 3) ? K / ZS : 1;
+    constexpr int NVS = NVAL / ZS;
     const int lane = threadIdx.x & 31;
     const int lig = threadIdx.x % G;
     const int leader = lane & ~(G - 1);
@@ -478,9 +482,11 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
             const uint32_t kb = cbeg[cell], ke = cend[cell];
             if (kb >= ke) continue;   // uniform across the group
             const int lb[3] = {cell & 3, (cell >> 2) & 3, (D == 3) ? (cell >> 4) : 0};
-            R cur[NVAL];
+#pragma unroll 1
+            for (int slab = 0; slab < ZS; ++slab) {
+            R cur[NVS];
 #pragma unroll
-            for (int i = 0; i < NVAL; ++i) cur[i] = R(0);
+            for (int i = 0; i < NVS; ++i) cur[i] = R(0);
             // this lane's particles kb + lig + i G are staged NSL ahead through shared memory
             constexpr int NSL = p2g_slots<R>();
             constexpr int SW = slot_words<D>();
@@ -542,10 +548,13 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
                                 kz[a] = T[a * 3 + 2] * wab;
                             }
 #pragma unroll
-                            for (int ic = 0; ic < K; ++ic) {
-                                const R wz = w[2][ic], dwz = dw[2][ic], r2 = R(ic) - fx[2];
+                            for (int icl = 0; icl < KZ; ++icl) {
+                                const int ic = slab * KZ + icl;
+                                const R wz = (ZS == 1) ? w[2][icl] : (slab ? w[2][KZ + icl] : w[2][icl]);
+                                const R dwz = (ZS == 1) ? dw[2][icl] : (slab ? dw[2][KZ + icl] : dw[2][icl]);
+                                const R r2 = R(ic) - fx[2];
                                 const R wv = wab * wz;
-                                const int j = ia + K * ib + K * K * ic;
+                                const int j = ia + K * ib + K * K * icl;
 #pragma unroll
                                 for (int a = 0; a < 3; ++a) {
                                     const R qv = qab[a] + mC[a * 3 + 2] * r2;
@@ -573,13 +582,14 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
                 }
             }
             cp_async_wait<0>();
-            int off = 0, cnt = NVAL;
-            ReduceScatter<R, NVAL, G>::run(cur, gmask, lig, off, cnt);
-            constexpr int FIN = ReduceScatter<R, NVAL, G>::FINAL;
-            R* dst = cellsum + (size_t)cell * NVAL + off;
+            int off = 0, cnt = NVS;
+            ReduceScatter<R, NVS, G>::run(cur, gmask, lig, off, cnt);
+            constexpr int FIN = ReduceScatter<R, NVS, G>::FINAL;
+            R* dst = cellsum + (size_t)cell * NVAL + (size_t)slab * NVS + off;
 #pragma unroll
             for (int i = 0; i < FIN; ++i)
                 if (i < cnt) dst[i] = cur[i];
+            }   // slab
         }
         __syncthreads();
         // gather: node n of the tile collects the stencil sums of cells n - (a, b, c)
@@ -1377,6 +1387,9 @@ template <typename R> struct Impl {
         else if (h.dim == 2 && h.order == 3)
             k_p2g_cells<2, 3, R, APIC_P2G_GROUP><<<L.p2g_grid, 128, p2g_cells_smem<2, 3, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc,
                                                                 b.flags, c, b.err, b.fallbacks);
+        else if (h.dim == 3 && h.order == 3)
+            k_p2g_cells<3, 3, R, APIC_P2G_GROUP><<<L.p2g_grid, 128, p2g_cells_smem<3, 3, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc,
+                                                                b.flags, c, b.err, b.fallbacks);
         else
             k_p2g<3, 3, R><<<L.p2g_grid, TPB, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, (R*)b.acc, b.flags, c, b.err,
                                                       b.fallbacks);
@@ -1462,7 +1475,7 @@ template <typename R> struct Impl {
             else if (h.p2g_kernel != 2)
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g<D, O, R>, TPB, 0);
             else {
-                constexpr int O2 = (D == 3 ? 2 : O);
+                constexpr int O2 = O;
                 e = cudaFuncSetAttribute(k_p2g_cells<D, O2, R, APIC_P2G_GROUP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)p2g_cells_smem<D, O2, R>());
                 if (e == cudaSuccess)

@@ -153,8 +153,6 @@ def test_transfer_modes_and_transfer_only(apic, transfer):
 @pytest.mark.parametrize("p2g_kernel", [1, 2, 3])
 @pytest.mark.parametrize("dim,order,prec", [(3, 2, 32), (2, 2, 32), (2, 3, 32), (3, 2, 64), (2, 3, 64), (3, 3, 32)])
 def test_p2g_variants_and_tile_sizes_agree(apic, tile, p2g_kernel, dim, order, prec):
-    if p2g_kernel == 2 and dim == 3 and order == 3:
-        pytest.skip("the cell-parallel P2G does not cover 3-D cubic")
     r = run_one_step(apic, dim, order, prec, 32 if dim == 3 else 64, 8 if dim == 3 else 4, tile=tile,
                      p2g_kernel=p2g_kernel)
     x0, v0, B0, F0 = r["in"]
