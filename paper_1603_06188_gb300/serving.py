@@ -122,8 +122,11 @@ def poisson_arrivals(rng: np.random.Generator, rate: float, count: int) -> np.nd
     return np.cumsum(rng.exponential(1.0 / rate, size=count))
 
 
-def serve_gpu(requests: list[Request], make_sim, batch, budget_bytes: int, max_resident: int, max_chunk: int = 8):
-    """Run the loop on the GPU.  make_sim(req) -> Sim (uploaded); batch: apic.Batch."""
+def serve_gpu(requests: list[Request], make_sim, batch, budget_bytes: int, max_resident: int, max_chunk: int = 8,
+              keep_state: bool = False):
+    """Run the loop on the GPU.  make_sim(req) -> Sim (uploaded); batch: apic.Batch.
+    Returns the report and, per request id, its final total momentum (or, with keep_state,
+    its downloaded particle state)."""
     import torch
 
     t0 = time.perf_counter()
@@ -139,7 +142,7 @@ def serve_gpu(requests: list[Request], make_sim, batch, budget_bytes: int, max_r
 
     def retire(r, sim):
         batch.remove(sim)          # synchronises with the batch
-        results[r.rid] = sim.momentum("particles")
+        results[r.rid] = sim.download() if keep_state else sim.momentum("particles")
         sim.close()
         del sim
 
