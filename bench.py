@@ -337,6 +337,20 @@ def run_serving(args) -> int:
     return 0
 
 
+def aggregate(local_ms: float, local_units: float, dist=None, device=None):
+    """Whole-job timing over replicas: the slowest rank's time and the sum of all ranks'
+    particle-steps (no collective touches the simulation data)."""
+    if dist is None:
+        return float(local_ms), float(local_units)
+    import torch
+
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    dist.all_reduce(u)
+    return float(t.item()), float(u.item())
+
+
 def dist_setup(n_gpus: int):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -459,15 +473,7 @@ def main():
     stats = sim.stats()
     launches = stats["kernel_launches"] - launches0
     p_after, l_after = sim.momentum("particles")
-    max_ms = ms
-    total_units = sc.n * args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        max_ms = float(t.item())
-        u = torch.tensor([float(total_units)], device="cuda", dtype=torch.float64)
-        dist.all_reduce(u)
-        total_units = float(u.item())
+    max_ms, total_units = aggregate(ms, sc.n * args.steps, dist, device="cuda")
     value = total_units / (max_ms / 1e3)
 
     # roofline of the dominant single-kernel phase
