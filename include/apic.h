@@ -52,8 +52,8 @@ typedef enum {
 } apic_status;
 
 enum { APIC_TRANSFER_APIC = 0, APIC_TRANSFER_PIC = 1 };
-enum { APIC_BOUNDARY_NONE = 0, APIC_BOUNDARY_STICKY = 1 };
-enum { APIC_MODEL_NONE = 0, APIC_MODEL_FIXED_COROTATED = 1 };
+enum { APIC_BOUNDARY_NONE = 0, APIC_BOUNDARY_STICKY = 1, APIC_BOUNDARY_SLIP = 2 };
+enum { APIC_MODEL_NONE = 0, APIC_MODEL_FIXED_COROTATED = 1, APIC_MODEL_NEOHOOKEAN = 2 };
 enum { APIC_WHERE_PARTICLES = 0, APIC_WHERE_GRID = 1 };
 enum { APIC_GRID_MOMENTUM = 0, APIC_GRID_VELOCITY = 1 };
 
@@ -69,10 +69,14 @@ typedef struct {
     double origin[3];        /* position of node 0 */
     double dt;               /* time step */
     double gravity[3];       /* added to v~ of nodes with mass (not in the paper) */
-    int boundary;            /* APIC_BOUNDARY_NONE or _STICKY: v~ = 0 on nodes within `wall`
-                                nodes of a face (not in the paper) */
+    int boundary;            /* APIC_BOUNDARY_NONE, _STICKY (v~ = 0 on nodes within `wall`
+                                nodes of a face) or _SLIP (only the component of v~ normal to
+                                that face is zeroed; the paper's Sec. 6.2 test uses slip) */
     int wall;                /* wall thickness in nodes */
-    int model;               /* APIC_MODEL_NONE (transfer only) or _FIXED_COROTATED */
+    int model;               /* APIC_MODEL_NONE (transfer only), _FIXED_COROTATED
+                                (P = 2 mu (F - R) + lam (J - 1) J F^-T) or _NEOHOOKEAN
+                                (P = mu (F - F^-T) + lam log(J) F^-T, the model of the
+                                paper's Sec. 6 experiments) */
     double E, nu;            /* Young's modulus, Poisson's ratio */
     double particle_mass;    /* m_p, the same for every particle of a simulation */
     double particle_volume;  /* V_p (reference volume), the same for every particle */
@@ -139,6 +143,12 @@ apic_status apic_step(apic_sim* sim, int n);
  * includes dt f_i) and sum x_i x (m v)_i; after apic_grid_update, sum m_i v~_i and
  * sum x_i x m_i v~_i.  In 2-D, l[0] is the z component.  Synchronising, host pointers. */
 apic_status apic_momentum(apic_sim* sim, int where, double p[3], double l[3]);
+
+/* Sec. 4.3 time-step bound: *max_speed = max_p (|v_p| + (6 sqrt(d) / dx) |B_p|_F), the
+ * (kappa / k) dx factor being the same for quadratic and cubic B-splines; a step with
+ * dt <= nu dx / *max_speed moves no particle more than nu dx at the grid velocity.
+ * Synchronising, host pointer. */
+apic_status apic_cfl(apic_sim* sim, double* max_speed);
 
 /* Dense copy of the grid (host pointers, res-box node order): which =
  * APIC_GRID_MOMENTUM after apic_p2g: m (nodes) and (m v)_i + dt f_i (nodes*d);

@@ -69,10 +69,10 @@ def make_cfg(dim=3, order=2, transfer="apic", res=(16, 16, 16), dx=1.0 / 16, ori
     c.dt = dt
     g = list(gravity) + [0.0] * (3 - len(gravity))
     c.gravity = (C.c_double * 3)(*g)
-    c.boundary = {"none": 0, "sticky": 1}[boundary]
+    c.boundary = {"none": 0, "sticky": 1, "slip": 2}[boundary]
     c.wall = wall
-    c.model = {"none": 0, "fcr": 1}[model]
-    if model == "fcr":
+    c.model = {"none": 0, "fcr": 1, "nh": 2}[model]
+    if model in ("fcr", "nh"):
         c.mu, c.lam = lame(E, nu)
     c.lambda_t = lambda_t
     return c
@@ -94,6 +94,9 @@ def _load():
                 "or_polar": (None, [C.c_int, cp, cp]),
                 "or_psi_fcr": (d, [C.c_int, d, d, cp]),
                 "or_stress_fcr": (None, [C.c_int, d, d, cp, cp]),
+                "or_psi_nh": (d, [C.c_int, d, d, cp]),
+                "or_stress_nh": (None, [C.c_int, d, d, cp, cp]),
+                "or_cfl_speed": (d, [cfgp, i64, cp, cp]),
                 "or_p2g": (i64, [cfgp, i64, cp, cp, cp, cp, cp, cp, cp, cp, cp]),
                 "or_grid_update": (None, [cfgp, cp, cp, cp, cp, cp]),
                 "or_g2p": (i64, [cfgp, i64, cp, cp, cp, cp, cp, cp]),
@@ -200,6 +203,25 @@ def stress_fcr(F, mu, lam):
     P = np.zeros_like(F)
     _load().or_stress_fcr(F.shape[0], mu, lam, _p(F), _p(P))
     return P
+
+
+def psi_nh(F, mu, lam) -> float:
+    F = _f64(F)
+    return _load().or_psi_nh(F.shape[0], mu, lam, _p(F))
+
+
+def stress_nh(F, mu, lam):
+    F = _f64(F)
+    P = np.zeros_like(F)
+    _load().or_stress_nh(F.shape[0], mu, lam, _p(F), _p(P))
+    return P
+
+
+def cfl_speed(cfg: Cfg, v, B) -> float:
+    """max_p (|v_p| + (kappa/k) dx |B_p|_F) of Sec. 4.3; dt <= nu dx / this."""
+    d = cfg.dim
+    n = len(v)
+    return _load().or_cfl_speed(C.byref(cfg), n, _p(_f64(v, (n, d))), _p(_f64(B, (n, d, d))))
 
 
 # --------------------------------------------------------------------------- transfers

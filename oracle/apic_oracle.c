@@ -27,8 +27,12 @@
  *   - kernel N: quadratic / cubic cardinal B-splines (never written out in the paper);
  *   - stencil base: floor(x/dx - 1/2) (quadratic), floor(x/dx) - 1 (cubic);
  *   - constitutive model: fixed-corotated, P = 2 mu (F - R) + lam (J - 1) J F^{-T};
- *   - gravity and sticky walls are not in the paper; they are applied in the grid
- *     update after the force, gravity only where m_i > 0.
+ *   - Neo-Hookean (named, not written out, by the paper's experiments):
+ *     Psi = mu/2 (tr(F^T F) - d) - mu log J + lam/2 (log J)^2,
+ *     P = mu (F - F^{-T}) + lam log(J) F^{-T};
+ *   - gravity and walls are not in the paper; they are applied in the grid update after
+ *     the force, gravity only where m_i > 0.  Sticky walls zero v~ on wall nodes; slip
+ *     walls zero only the component of v~ normal to each wall the node lies in.
  */
 #include <math.h>
 #include <stdint.h>
@@ -44,9 +48,9 @@ typedef struct {
     double origin[3];
     double dt;
     double gravity[3];
-    int boundary;       /* 0 = none, 1 = sticky walls */
+    int boundary;       /* 0 = none, 1 = sticky walls, 2 = slip walls */
     int wall;           /* wall thickness in nodes */
-    int model;          /* 0 = none (transfer only), 1 = fixed-corotated */
+    int model;          /* 0 = none (transfer only), 1 = fixed-corotated, 2 = Neo-Hookean */
     double mu, lam;     /* Lame parameters */
     double lambda_t;    /* integrator family parameter lambda of Sec. 3.3 */
 } or_cfg;
@@ -363,6 +367,36 @@ void or_stress_fcr(int d, double mu, double lam, const double* F, double* P)
     for (int k = 0; k < d * d; ++k) P[k] = 2.0 * mu * (F[k] - R[k]) + lam * (J - 1.0) * C[k];
 }
 
+/* Neo-Hookean energy density and stress (see the header comment). */
+double or_psi_nh(int d, double mu, double lam, const double* F)
+{
+    double s = 0.0;
+    for (int k = 0; k < d * d; ++k) s += F[k] * F[k];
+    double lj = log(det_d(d, F));
+    return 0.5 * mu * (s - d) - mu * lj + 0.5 * lam * lj * lj;
+}
+
+void or_stress_nh(int d, double mu, double lam, const double* F, double* P)
+{
+    double C[9];
+    cofactor_d(d, F, C);              /* J F^{-T} */
+    double J = det_d(d, F);
+    double lj = log(J);
+    for (int k = 0; k < d * d; ++k) P[k] = mu * (F[k] - C[k] / J) + lam * lj * C[k] / J;
+}
+
+static void stress_of(const or_cfg* c, const double* F, double* P)
+{
+    if (c->model == 2) or_stress_nh(c->dim, c->mu, c->lam, F, P);
+    else or_stress_fcr(c->dim, c->mu, c->lam, F, P);
+}
+
+static double psi_of(const or_cfg* c, const double* F)
+{
+    if (c->model == 2) return or_psi_nh(c->dim, c->mu, c->lam, F);
+    return or_psi_fcr(c->dim, c->mu, c->lam, F);
+}
+
 /* ------------------------------------------------------------------ */
 /* Sec. 3.2: transfer to grid.                                         */
 /* ------------------------------------------------------------------ */
@@ -399,9 +433,9 @@ int64_t or_p2g(const or_cfg* c, int64_t n, const double* x, const double* v, con
             matmul_d(d, B + p * d * d, Dinv, Cp);
         }
         double tau[9] = {0};
-        if (c->model == 1) {
+        if (c->model != 0) {
             double P[9];
-            or_stress_fcr(d, c->mu, c->lam, F + p * d * d, P);
+            stress_of(c, F + p * d * d, P);
             /* tau = V_p P F^T */
             const double* Fp = F + p * d * d;
             for (int a = 0; a < d; ++a)
@@ -421,7 +455,7 @@ int64_t or_p2g(const or_cfg* c, int64_t n, const double* x, const double* v, con
                 double vel = v[p * d + a];
                 for (int b = 0; b < d; ++b) vel += Cp[a * d + b] * r[b];
                 gmv[ni * d + a] += w[j] * mass[p] * vel;
-                if (c->model == 1) {
+                if (c->model != 0) {
                     double s = 0.0;
                     for (int b = 0; b < d; ++b) s += tau[a * d + b] * dw[j * d + b];
                     gf[ni * d + a] -= s;
@@ -452,15 +486,16 @@ void or_grid_update(const or_cfg* c, const double* gm, const double* gmv, const 
             for (int a = 0; a < d; ++a) { gv[idx * d + a] = 0.0; gvt[idx * d + a] = 0.0; }
             continue;
         }
-        int wall = 0;
-        if (c->boundary == 1)
-            for (int a = 0; a < d; ++a)
-                if (i[a] < c->wall || i[a] >= c->res[a] - c->wall) wall = 1;
+        int wall = 0, inwall[3] = {0, 0, 0};
+        for (int a = 0; a < d; ++a)
+            if (i[a] < c->wall || i[a] >= c->res[a] - c->wall) { wall = 1; inwall[a] = 1; }
         for (int a = 0; a < d; ++a) {
             double vi = gmv[idx * d + a] / gm[idx];
             double vt = vi + c->dt * gf[idx * d + a] / gm[idx] + c->dt * c->gravity[a];
             gv[idx * d + a] = vi;
-            gvt[idx * d + a] = wall ? 0.0 : vt;
+            if (c->boundary == 1 && wall) vt = 0.0;          /* sticky: the whole velocity */
+            if (c->boundary == 2 && inwall[a]) vt = 0.0;     /* slip: the normal component */
+            gvt[idx * d + a] = vt;
         }
     }
 }
@@ -593,7 +628,7 @@ double or_potential(const or_cfg* c, int64_t n, const double* x, const double* F
                 for (int b = 0; b < d; ++b) M[a * d + b] += dxg[ni * d + a] * dw[j * d + b];
         }
         matmul_d(d, M, F + p * d * d, Fh);
-        phi += vol[p] * or_psi_fcr(d, c->mu, c->lam, Fh);
+        phi += vol[p] * psi_of(c, Fh);
     }
     return phi;
 }
@@ -657,6 +692,27 @@ void or_momentum_grid(const or_cfg* c, const double* gmv, double* p, double* l)
             l[2] += xi[0] * q[1] - xi[1] * q[0];
         }
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 4.3: time-step bound dt <= nu dx / max_p (|v_p| + (kappa/k) dx |B_p|_F), where    */
+/* |x_i - x_p| <= kappa dx over the stencil and D_p = k I.                              */
+/* ------------------------------------------------------------------ */
+double or_cfl_speed(const or_cfg* c, int64_t n, const double* v, const double* B)
+{
+    const int d = c->dim;
+    const double kappa = (c->order == 2 ? 1.5 : 2.0) * sqrt((double)d);
+    const double k = (c->order == 2 ? 0.25 : 1.0 / 3.0) * c->dx * c->dx;
+    const double coef = kappa * c->dx / k;      /* (kappa / k) dx */
+    double mx = 0.0;
+    for (int64_t p = 0; p < n; ++p) {
+        double sv = 0.0, sb = 0.0;
+        for (int a = 0; a < d; ++a) sv += v[p * d + a] * v[p * d + a];
+        for (int a = 0; a < d * d; ++a) sb += B[p * d * d + a] * B[p * d * d + a];
+        double s = sqrt(sv) + coef * sqrt(sb);
+        if (s > mx) mx = s;
+    }
+    return mx;
 }
 
 /* ------------------------------------------------------------------ */

@@ -16,8 +16,8 @@ from . import build as _build
 
 APIC_OK, APIC_ERR_ARG, APIC_ERR_OOM, APIC_ERR_CUDA, APIC_ERR_TIMEOUT, APIC_ERR_NUMERIC, APIC_ERR_UNSUPPORTED = range(7)
 TRANSFER = {"apic": 0, "pic": 1}
-BOUNDARY = {"none": 0, "sticky": 1}
-MODEL = {"none": 0, "fcr": 1, "fixed_corotated": 1}
+BOUNDARY = {"none": 0, "sticky": 1, "slip": 2}
+MODEL = {"none": 0, "fcr": 1, "fixed_corotated": 1, "nh": 2, "neohookean": 2}
 WHERE_PARTICLES, WHERE_GRID = 0, 1
 GRID_MOMENTUM, GRID_VELOCITY = 0, 1
 STATUS_NAMES = {0: "APIC_OK", 1: "APIC_ERR_ARG", 2: "APIC_ERR_OOM", 3: "APIC_ERR_CUDA", 4: "APIC_ERR_TIMEOUT",
@@ -89,6 +89,7 @@ SIGNATURES = {
     "apic_g2p": (C.c_int, [C.c_void_p]),
     "apic_step": (C.c_int, [C.c_void_p, C.c_int]),
     "apic_momentum": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "apic_cfl": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "apic_grid_download": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "apic_keys_download": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "apic_grid_occupancy": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
@@ -200,6 +201,12 @@ def apic_momentum(sim, where: int):
     l = np.zeros(3)
     _check(load().apic_momentum(sim, where, _ptr(p), _ptr(l)), sim)
     return p, l
+
+
+def apic_cfl(sim) -> float:
+    out = C.c_double(0.0)
+    _check(load().apic_cfl(sim, C.byref(out)), sim)
+    return out.value
 
 
 def apic_grid_download(sim, which: int, m, mv):
@@ -373,6 +380,10 @@ class Sim:
 
     def momentum(self, where: str = "particles"):
         return apic_momentum(self.handle, WHERE_PARTICLES if where == "particles" else WHERE_GRID)
+
+    def cfl_speed(self) -> float:
+        """max_p(|v_p| + 6 sqrt(d)/dx |B_p|_F); dt <= nu dx / this (Sec. 4.3)."""
+        return apic_cfl(self.handle)
 
     def grid(self, which: str = "momentum"):
         m = np.zeros(self.n_nodes)

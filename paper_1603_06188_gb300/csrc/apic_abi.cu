@@ -66,8 +66,8 @@ apic_status fill_cfg(const apic_config* in, int64_t max_particles, HostCfg* c, s
     if (in->order != 2 && in->order != 3) { *why = "order must be 2 (quadratic) or 3 (cubic)"; return APIC_ERR_UNSUPPORTED; }
     if (in->precision != 32 && in->precision != 64) { *why = "precision must be 32 or 64"; return APIC_ERR_ARG; }
     if (in->transfer != APIC_TRANSFER_APIC && in->transfer != APIC_TRANSFER_PIC) { *why = "unknown transfer"; return APIC_ERR_ARG; }
-    if (in->boundary != APIC_BOUNDARY_NONE && in->boundary != APIC_BOUNDARY_STICKY) { *why = "unknown boundary"; return APIC_ERR_UNSUPPORTED; }
-    if (in->model != APIC_MODEL_NONE && in->model != APIC_MODEL_FIXED_COROTATED) { *why = "unknown constitutive model"; return APIC_ERR_UNSUPPORTED; }
+    if (in->boundary < APIC_BOUNDARY_NONE || in->boundary > APIC_BOUNDARY_SLIP) { *why = "unknown boundary"; return APIC_ERR_UNSUPPORTED; }
+    if (in->model < APIC_MODEL_NONE || in->model > APIC_MODEL_NEOHOOKEAN) { *why = "unknown constitutive model"; return APIC_ERR_UNSUPPORTED; }
     if (!(in->dx > 0.0)) { *why = "dx must be positive"; return APIC_ERR_ARG; }
     if (max_particles < 0 || max_particles > kMaxParticles) { *why = "max_particles out of range"; return APIC_ERR_ARG; }
     if (in->wall < 0) { *why = "wall must be >= 0"; return APIC_ERR_ARG; }
@@ -94,7 +94,7 @@ apic_status fill_cfg(const apic_config* in, int64_t max_particles, HostCfg* c, s
     c->boundary = in->boundary;
     c->wall = in->wall;
     c->model = in->model;
-    if (in->model == APIC_MODEL_FIXED_COROTATED) {
+    if (in->model != APIC_MODEL_NONE) {
         if (!(in->E > 0.0) || !(in->nu > -1.0 && in->nu < 0.5)) { *why = "E must be > 0 and -1 < nu < 0.5"; return APIC_ERR_ARG; }
         c->mu = in->E / (2.0 * (1.0 + in->nu));
         c->lam = in->E * in->nu / ((1.0 + in->nu) * (1.0 - 2.0 * in->nu));
@@ -539,6 +539,22 @@ apic_status apic_momentum(apic_sim* s, int where, double p[3], double l[3])
         l[1] = l[2] = 0.0;
     }
     return st;
+}
+
+apic_status apic_cfl(apic_sim* s, double* max_speed)
+{
+    if (!s || !max_speed) return APIC_ERR_ARG;
+    if (s->batch) {
+        apic_status bst = batch_sync_member(s);
+        if (bst != APIC_OK) return bst;
+    }
+    CK(cudaSetDevice(s->device), "cudaSetDevice");
+    *max_speed = 0.0;
+    if (s->n == 0) return APIC_OK;
+    CK(DISPATCH(s, cfl, s->c, s->b, s->cur, s->n, s->L, s->stream), "cfl kernel");
+    s->launches += 2;
+    CK(cudaMemcpyAsync(max_speed, s->b.mom_out, sizeof(double), cudaMemcpyDeviceToHost, s->stream), "read cfl");
+    return check_device(s);
 }
 
 apic_status apic_grid_download(apic_sim* s, int which, double* m, double* mv)

@@ -330,7 +330,7 @@ __device__ __forceinline__ R polar_residual(const R* F, const R* Rot)
 // check (nearly coincident singular values of F at FP32 resolution, or near-singular F);
 // each fallback is counted.
 template <int D, typename R>
-__device__ __forceinline__ void stress_tau(const R* F, R mu, R lam, R vol, R* tau, unsigned* fallbacks)
+__device__ __forceinline__ void stress_tau_fcr(const R* F, R mu, R lam, R vol, R* tau, unsigned* fallbacks)
 {
     R Rot[D * D];
     R J;
@@ -362,6 +362,31 @@ __device__ __forceinline__ void stress_tau(const R* F, R mu, R lam, R vol, R* ta
             for (int k = 0; k < D; ++k) s += (F[a * D + k] - Rot[a * D + k]) * F[b * D + k];
             tau[a * D + b] = vol * (two_mu * s + (a == b ? iso : R(0)));
         }
+}
+
+// Neo-Hookean: P = mu (F - F^{-T}) + lam log(J) F^{-T}  =>  tau = V (mu (F F^T - I) + lam log(J) I)
+template <int D, typename R>
+__device__ __forceinline__ void stress_tau_nh(const R* F, R mu, R lam, R vol, R* tau)
+{
+    const R J = (D == 3) ? det3<R>(F) : F[0] * F[3] - F[1] * F[2];
+    const R iso = lam * log(J) - mu;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            R s = R(0);
+#pragma unroll
+            for (int k = 0; k < D; ++k) s += F[a * D + k] * F[b * D + k];
+            tau[a * D + b] = vol * (mu * s + (a == b ? iso : R(0)));
+        }
+}
+
+// model 1: fixed-corotated, model 2: Neo-Hookean
+template <int D, typename R>
+__device__ __forceinline__ void stress_tau(int model, const R* F, R mu, R lam, R vol, R* tau, unsigned* fallbacks)
+{
+    if (model == 2) stress_tau_nh<D, R>(F, mu, lam, vol, tau);
+    else stress_tau_fcr<D, R>(F, mu, lam, vol, tau, fallbacks);
 }
 
 // ---------------------------------------------------------------- misc

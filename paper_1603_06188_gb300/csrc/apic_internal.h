@@ -105,7 +105,8 @@ struct Launch {
                                int grid_phase, const Launch& L, cudaStream_t s);                               \
     cudaError_t grid_dense_##SFX(const HostCfg& c, const Buffers& b, int which, double* m, double* mv,        \
                                  cudaStream_t s);                                                               \
-    cudaError_t occupancy_##SFX(const HostCfg& c, int* p2g_per_sm, int* g2p_per_sm);
+    cudaError_t occupancy_##SFX(const HostCfg& c, int* p2g_per_sm, int* g2p_per_sm);                         \
+    cudaError_t cfl_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const Launch& L, cudaStream_t s);
 
 #define APIC_DECLARE_BATCH(SFX)                                                                              \
     size_t batch_desc_bytes_##SFX();                                                                          \

@@ -185,9 +185,9 @@ __global__ void __launch_bounds__(TPB) k_p2g(PState<R> st, const uint32_t* __res
                 const R s = (c.transfer == 0) ? m * c.inv_kdx : R(0);
 #pragma unroll
                 for (int i = 0; i < D * D; ++i) mC[i] = s * p.B[i];
-                if (c.model == 1) {
+                if (c.model != 0) {
                     R tau[D * D];
-                    stress_tau<D, R>(p.F, c.mu, c.lam, c.vol, tau, fallbacks);
+                    stress_tau<D, R>(c.model, p.F, c.mu, c.lam, c.vol, tau, fallbacks);
 #pragma unroll
                     for (int i = 0; i < D * D; ++i) T[i] = dt_dx * tau[i];
                 } else {
@@ -523,9 +523,9 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
                 for (int a = 0; a < D; ++a) mv[a] = m * p.v[a];
 #pragma unroll
                 for (int i = 0; i < D * D; ++i) mC[i] = sC * p.B[i];
-                if (c.model == 1) {
+                if (c.model != 0) {
                     R tau[D * D];
-                    stress_tau<D, R>(p.F, c.mu, c.lam, c.vol, tau, fallbacks);
+                    stress_tau<D, R>(c.model, p.F, c.mu, c.lam, c.vol, tau, fallbacks);
 #pragma unroll
                     for (int i = 0; i < D * D; ++i) T[i] = dt_dx * tau[i];
                 } else {
@@ -740,9 +740,9 @@ __global__ void __launch_bounds__(256) k_p2g_interleaved(PState<R> st, const uin
             for (int a = 0; a < D; ++a) mv[a] = m * p.v[a];
 #pragma unroll
             for (int i = 0; i < D * D; ++i) mC[i] = sC * p.B[i];
-            if (c.model == 1) {
+            if (c.model != 0) {
                 R tau[D * D];
-                stress_tau<D, R>(p.F, c.mu, c.lam, c.vol, tau, fallbacks);
+                stress_tau<D, R>(c.model, p.F, c.mu, c.lam, c.vol, tau, fallbacks);
 #pragma unroll
                 for (int i = 0; i < D * D; ++i) T[i] = dt_dx * tau[i];
             } else {
@@ -855,12 +855,16 @@ __device__ __forceinline__ void grid_update_block(R* __restrict__ acc, R* __rest
             v[0] = a.x * inv + c.dt * c.gravity[0];
             v[1] = a.y * inv + c.dt * c.gravity[1];
             if (D == 3) v[2] = a.z * inv + c.dt * c.gravity[2];
-            if (c.boundary == 1) {
+            if (c.boundary == 1) {           // sticky: the whole velocity
                 bool wall = false;
 #pragma unroll
                 for (int d = 0; d < D; ++d)
                     if (g[d] < c.wall || g[d] >= c.res[d] - c.wall) wall = true;
                 if (wall) v[0] = v[1] = v[2] = R(0);
+            } else if (c.boundary == 2) {    // slip: the component normal to each wall
+#pragma unroll
+                for (int d = 0; d < D; ++d)
+                    if (g[d] < c.wall || g[d] >= c.res[d] - c.wall) v[d] = R(0);
             }
         }
         *reinterpret_cast<V4<R>*>(vel + 4 * node) = V4<R>{v[0], v[1], v[2], m};
@@ -1264,6 +1268,48 @@ __global__ void __launch_bounds__(TPB) k_mom_final(const double* __restrict__ pa
     if (threadIdx.x < 6) out[threadIdx.x] = s[threadIdx.x][0];
 }
 
+// Sec. 4.3: per-CTA max of |v_p| + (6 sqrt(d) / dx) |B_p|_F into part[blockIdx.x * 6]
+template <int D, typename R>
+__global__ void __launch_bounds__(TPB) k_cfl_particles(PState<R> st, DevCfg<R> c, double coef, double* part)
+{
+    __shared__ double s[TPB / 32];
+    double mx = 0.0;
+    for (int k = blockIdx.x * TPB + threadIdx.x; k < c.n; k += gridDim.x * TPB) {
+        Particle<D, R> p;
+        load_vB<D, R>(st, k, p);
+        double sv = 0.0, sb = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) sv += (double)p.v[a] * (double)p.v[a];
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) sb += (double)p.B[i] * (double)p.B[i];
+        mx = fmax(mx, sqrt(sv) + coef * sqrt(sb));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(FULLMASK, mx, o));
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < TPB / 32; ++w) t = fmax(t, s[w]);
+        part[(size_t)blockIdx.x * 6] = t;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(TPB) k_max_final(const double* __restrict__ part, int np, double* __restrict__ out)
+{
+    __shared__ double s[TPB];
+    double t = 0.0;
+    for (int b = threadIdx.x; b < np; b += TPB) t = fmax(t, part[(size_t)b * 6]);
+    s[threadIdx.x] = t;
+    __syncthreads();
+    for (int st = TPB / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) s[threadIdx.x] = fmax(s[threadIdx.x], s[threadIdx.x + st]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = s[0];
+}
+
 // ---------------------------------------------------------------- upload / download
 template <int D, typename R>
 __global__ void __launch_bounds__(TPB) k_upload(PState<R> st, DevCfg<R> c, double dx, double o0, double o1, double o2,
@@ -1458,6 +1504,16 @@ template <typename R> struct Impl {
         k_mom_final<R><<<1, TPB, 0, s>>>(b.mom_part, nparts, b.mom_out);
         return cudaGetLastError();
     }
+    static cudaError_t cfl(const HostCfg& h, const Buffers& b, int cur, int64_t n, const Launch& L, cudaStream_t s)
+    {
+        DevCfg<R> c = HostToDev<R>::make(h, n);
+        PState<R> st = state_of<R>(b, cur);
+        const double coef = 6.0 * sqrt((double)h.dim) / h.dx;   // (kappa / k) dx of Sec. 4.3, both splines
+        if (h.dim == 3) k_cfl_particles<3, R><<<L.mom_parts, TPB, 0, s>>>(st, c, coef, b.mom_part);
+        else k_cfl_particles<2, R><<<L.mom_parts, TPB, 0, s>>>(st, c, coef, b.mom_part);
+        k_max_final<R><<<1, TPB, 0, s>>>(b.mom_part, L.mom_parts, b.mom_out);
+        return cudaGetLastError();
+    }
     static cudaError_t grid_dense(const HostCfg& h, const Buffers& b, int which, double* m, double* mv, cudaStream_t s)
     {
         DevCfg<R> c = HostToDev<R>::make(h, 0);
@@ -1526,6 +1582,10 @@ template <typename R> struct Impl {
                                  cudaStream_t s)                                                                \
     {                                                                                                           \
         return Impl<R>::grid_dense(c, b, which, m, mv, s);                                                      \
+    }                                                                                                           \
+    cudaError_t cfl_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const Launch& L, cudaStream_t s) \
+    {                                                                                                           \
+        return Impl<R>::cfl(c, b, cur, n, L, s);                                                                \
     }                                                                                                           \
     cudaError_t occupancy_##SFX(const HostCfg& c, int* p2g_per_sm, int* g2p_per_sm)                            \
     {                                                                                                           \

@@ -49,7 +49,8 @@ def configs(dim, order, res, dx, precision=32, transfer="apic", dt=1e-3, gravity
                           gravity=gravity, boundary=boundary, wall=wall, model=model, E=E, nu=nu,
                           particle_mass=mass, particle_volume=vol, tile_particles=tile, p2g_kernel=p2g_kernel)
     oc = oracle.make_cfg(dim=dim, order=order, transfer=transfer, res=res, dx=dx, dt=dt, gravity=gravity,
-                         boundary=boundary, wall=wall, model="fcr" if model in ("fcr", "fixed_corotated") else "none",
+                         boundary=boundary, wall=wall,
+                         model={"fcr": "fcr", "fixed_corotated": "fcr", "nh": "nh", "neohookean": "nh"}.get(model, "none"),
                          E=E, nu=nu)
     return gc, oc, mass, vol
 

@@ -278,3 +278,35 @@ def test_out_of_grid_particle_is_reported(apic):
     sim.step(1)
     with pytest.raises(apic.ApicError):
         sim.download()
+
+
+@pytest.mark.parametrize("dim,order,prec", [(3, 2, 32), (3, 3, 32), (2, 2, 64)])
+def test_neohookean_and_slip_walls(apic, dim, order, prec):
+    """The Neo-Hookean stress in P2G and slip walls in the grid update, one transfer at a time."""
+    res = 32 if dim == 3 else 64
+    r = run_one_step(apic, dim, order, prec, res, 8 if dim == 3 else 4, model="nh", boundary="slip", wall=order + 1,
+                     gravity=(0.0, -9.8, 0.0)[:dim])
+    x0, v0, B0, F0 = r["in"]
+    gm, gmv, gf, _ = oracle.p2g(r["oc"], x0, v0, B0, F0, r["m"], r["vol"])
+    m_gpu, p_gpu = r["grid_p2g"]
+    assert relerr(p_gpu, gmv + r["oc"].dt * gf) <= TOL[prec]
+    _, vt_ref = oracle.grid_update(r["oc"], m_gpu, p_gpu, np.zeros_like(p_gpu))
+    assert relerr(r["grid_vel"][1], vt_ref) <= TOL[prec]
+    _, vt = r["grid_vel"]
+    x1, v1, B1, F1, _ = oracle.g2p(r["oc"], x0, F0, vt, vt)
+    gx, gv, gB, gF = r["out"]
+    assert relerr(gv, v1) <= TOL[prec] and relerr(gF, F1) <= TOL[prec]
+
+
+@pytest.mark.parametrize("dim,order,prec", [(3, 2, 32), (2, 3, 64)])
+def test_cfl_speed_matches_oracle(apic, dim, order, prec):
+    """Sec. 4.3 bound max_p(|v_p| + 6 sqrt(d)/dx |B_p|_F) from the device reduction."""
+    sc = cube_scene(dim, 32 if dim == 3 else 64, 8 if dim == 3 else 4, seed=5)
+    x, v, B, F = state_for(sc, order, seed=5)
+    gc, oc, m, vol = configs(dim, order, sc.res, sc.dx, precision=prec)
+    sim = apic.Sim(gc, sc.n)
+    sim.upload(x, v, B, F)
+    _, v0, B0, _ = sim.download()
+    got = sim.cfl_speed()
+    ref = oracle.cfl_speed(oc, v0, B0)
+    assert got == pytest.approx(ref, rel=1e-6 if prec == 32 else 1e-12)
