@@ -71,9 +71,9 @@ __global__ void __launch_bounds__(128, 2) kb_p2g_cells(SimDesc<R>* __restrict__ 
                                                        uint32_t* __restrict__ tile_ctr, int kpar)
 {
     constexpr int NC = (D == 3) ? 64 : 16;
-    extern __shared__ __align__(16) unsigned char p2g_smem[];
+    extern __shared__ __align__(32) unsigned char p2g_smem[];
     R* cellsum = reinterpret_cast<R*>(p2g_smem);
-    R* pslots = reinterpret_cast<R*>(p2g_smem + (p2g_cellsum_bytes<D, ORDER, R>() + 15) / 16 * 16);
+    R* pslots = reinterpret_cast<R*>(p2g_smem + (p2g_cellsum_bytes<D, ORDER, R>() + 31) / 32 * 32);
     __shared__ uint32_t cbeg[NC], cend[NC];
     __shared__ int s_tile, s_cell;
     __shared__ __align__(16) SimDesc<R> sd;

@@ -380,7 +380,7 @@ template <int D, int ORDER, typename R> __host__ __device__ constexpr size_t p2g
 // dynamic shared memory of the cell-parallel P2G: per-cell sums, then the staging slots
 template <int D, int ORDER, typename R> __host__ __device__ constexpr size_t p2g_cells_smem()
 {
-    return (p2g_cellsum_bytes<D, ORDER, R>() + 15) / 16 * 16 + (size_t)p2g_slots<R>() * 128 * slot_words<D>() * sizeof(R);
+    return (p2g_cellsum_bytes<D, ORDER, R>() + 31) / 32 * 32 + (size_t)p2g_slots<R>() * 128 * slot_words<D>() * sizeof(R);
 }
 
 // ---------------------------------------------------------------- P2G, cell-parallel
@@ -648,9 +648,9 @@ __global__ void __launch_bounds__(128, 2) k_p2g_cells(PState<R> st, const uint32
                                                       uint32_t* fallbacks)
 {
     constexpr int NC = (D == 3) ? 64 : 16;
-    extern __shared__ __align__(16) unsigned char p2g_smem[];
+    extern __shared__ __align__(32) unsigned char p2g_smem[];
     R* cellsum = reinterpret_cast<R*>(p2g_smem);   // [NC][NVAL]
-    R* pslots = reinterpret_cast<R*>(p2g_smem + (p2g_cellsum_bytes<D, ORDER, R>() + 15) / 16 * 16);
+    R* pslots = reinterpret_cast<R*>(p2g_smem + (p2g_cellsum_bytes<D, ORDER, R>() + 31) / 32 * 32);
     __shared__ uint32_t cbeg[NC], cend[NC];
     __shared__ int s_tile, s_cell;
     const int ntiles = (int)*ntiles_p;
