@@ -343,6 +343,7 @@ apic_status apic_create(const apic_config* cfg, int64_t max_particles, void* wor
 apic_status apic_destroy(apic_sim* s)
 {
     if (!s) return APIC_ERR_ARG;
+    if (s->batch) apic_batch_remove(s->batch, s);
     cudaError_t e = cudaStreamSynchronize(s->stream);
     for (cudaEvent_t ev : s->ev_pool) cudaEventDestroy(ev);
     delete s;
@@ -676,6 +677,7 @@ struct apic_batch {
     size_t desc_bytes;
     // membership
     std::vector<apic_sim*> members;
+    std::vector<apic_sim*> uploaded;   // simulations whose descriptors are on the device, in order
     bool dirty;
     uint32_t total_rtiles, total_chunks, total_blocks;
     int64_t total_particles;
@@ -737,10 +739,12 @@ apic_status batch_fail(apic_batch* b, apic_status st, const std::string& why)
         if (e_ != cudaSuccess) return batch_fail(b, APIC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-// copy the device-side state parity of every member back into its host struct
+// Copy the device-side state parity back into the host structs of the simulations whose
+// descriptors are on the device (the member list as of the last rebuild -- members added
+// since then have no descriptor yet and keep their host value).
 apic_status batch_pull_cur(apic_batch* b)
 {
-    const size_t n = b->members.size();
+    const size_t n = b->uploaded.size();
     if (n == 0) return APIC_OK;
     std::vector<unsigned char> h(n * b->desc_bytes);
     BCK(cudaMemcpyAsync(h.data(), b->descs, h.size(), cudaMemcpyDeviceToHost, b->stream), "read descriptors");
@@ -749,13 +753,19 @@ apic_status batch_pull_cur(apic_batch* b)
     for (size_t i = 0; i < n; ++i) {
         int cur;
         memcpy(&cur, h.data() + i * b->desc_bytes + off, sizeof(int));
-        b->members[i]->cur = cur;
+        if (!b->uploaded[i]) continue;
+        if (cur != 0 && cur != 1) return batch_fail(b, APIC_ERR_CUDA, "corrupt state parity in a batch descriptor");
+        b->uploaded[i]->cur = cur;
     }
     return APIC_OK;
 }
 
 apic_status batch_rebuild(apic_batch* b)
 {
+    {
+        apic_status st = batch_pull_cur(b);   // parity of the previous descriptors first
+        if (st != APIC_OK) return st;
+    }
     const size_t S = b->members.size();
     std::vector<unsigned char> descs(S * b->desc_bytes);
     std::vector<SortDesc> sds(S);
@@ -814,6 +824,7 @@ apic_status batch_rebuild(apic_batch* b)
         cudaGraphExecDestroy(b->gexec);
         b->graph_valid = false;
     }
+    b->uploaded = b->members;
     b->dirty = false;
     return APIC_OK;
 }
@@ -1022,6 +1033,10 @@ apic_status apic_batch_remove(apic_batch* b, apic_sim* s)
             b->members.erase(b->members.begin() + (long)i);
             break;
         }
+    // its descriptor stays on the device until the next rebuild, but its parity is now
+    // owned by the host again: forget it so no later pull overwrites it
+    for (size_t i = 0; i < b->uploaded.size(); ++i)
+        if (b->uploaded[i] == s) b->uploaded[i] = nullptr;
     s->batch = nullptr;
     s->phase = 0;
     if (b->steps > 0) {

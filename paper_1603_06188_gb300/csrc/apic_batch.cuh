@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(TPB, 2) kb_g2p(SimDesc<R>* __restrict__ descs,
             const int t1 = (int)atomicAdd(tile_ctr + 1, 1u);
             s_next = t1;
             if (t1 < ntiles) issue(t1, buf ^ 1);
-            s_ok = g2p_wait(&mbar[buf], phase[buf], sd.err) ? 1 : 0;
+            s_ok = g2p_wait(&mbar[buf], phase[buf], descs[sim].err) ? 1 : 0;   // sd is not complete before the barrier
         }
         __syncthreads();
         if (!s_ok) return;
