@@ -99,4 +99,8 @@ def test_fullsize_g2p_sampled_particles(run):
     assert relerr(gv, v1) <= TOL
     assert relerr(gB, B1) <= TOL
     assert relerr(gF, F1) <= TOL
-    assert relerr(gx - run["x0"][idx], x1 - run["x0"][idx]) <= TOL
+    # positions are cell + FP32 offset: one rounding of the offset is eps32 * dx absolute,
+    # which at dt = 2e-5 is not small against the displacement itself
+    disp_ref = x1 - run["x0"][idx]
+    bound = TOL * np.abs(disp_ref).max() + 2 * np.finfo(np.float32).eps * run["sc"].dx
+    assert np.abs((gx - run["x0"][idx]) - disp_ref).max() <= bound
