@@ -58,7 +58,7 @@ ALGO_BYTES = {
     # G2P reads x + F (52 B), writes x, v, B, F (100 B); reads v~ per node
     "g2p": (152, 16),
 }
-KERNEL_OF_PHASE = {"p2g": "k_p2g", "grid_update": "k_grid_update", "g2p": "k_g2p"}
+KERNEL_OF_PHASE = {"p2g": "k_p2g_cells", "grid_update": "k_grid_update", "g2p": "k_g2p"}
 
 
 def make_scene(w: dict, seed: int = 0):
