@@ -107,7 +107,8 @@ __global__ void __launch_bounds__(TPB, 2) kb_g2p(SimDesc<R>* __restrict__ descs,
     constexpr int NB = 1 << D;
     __shared__ __align__(128) R sv[2][NB][BN][4];
     __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ int s_ok, s_next;
+    // s_t[b]: the tile staged in buffer b (written and read as in k_g2p)
+    __shared__ int s_ok, s_t[2];
     __shared__ __align__(16) SimDesc<R> sd;
     unsigned phase[2] = {0u, 0u};
     const int ntiles = (int)*ntiles_p;
@@ -121,19 +122,22 @@ __global__ void __launch_bounds__(TPB, 2) kb_g2p(SimDesc<R>* __restrict__ descs,
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
         const int t0 = (int)atomicAdd(tile_ctr + 1, 1u);
-        s_next = t0;
+        s_t[0] = t0;
         if (t0 < ntiles) issue(t0, 0);
     }
     __syncthreads();
-    int t = s_next, buf = 0;
-    while (t < ntiles) {
+    for (int buf = 0;; buf ^= 1) {
+        const int t = s_t[buf];
+        if (t >= ntiles) break;
         const uint32_t sim = tile_sim[t];
         load_desc<R>(&sd, descs + sim, TPB);
         if (threadIdx.x == 0) {
             const int t1 = (int)atomicAdd(tile_ctr + 1, 1u);
-            s_next = t1;
+            s_t[buf ^ 1] = t1;
             if (t1 < ntiles) issue(t1, buf ^ 1);
-            s_ok = g2p_wait(&mbar[buf], phase[buf], descs[sim].err) ? 1 : 0;   // sd is not complete before the barrier
+            const bool ok = g2p_wait(&mbar[buf], phase[buf], descs[sim].err);   // sd is not complete before the barrier
+            if (!ok && t1 < ntiles) mbar_wait_bounded(&mbar[buf ^ 1], phase[buf ^ 1], 1u << 22);   // drain before leaving
+            s_ok = ok ? 1 : 0;
         }
         __syncthreads();
         if (!s_ok) return;
@@ -143,8 +147,6 @@ __global__ void __launch_bounds__(TPB, 2) kb_g2p(SimDesc<R>* __restrict__ descs,
                                  sd.err, sv[buf]);
         __syncthreads();
         phase[buf] ^= 1u;
-        buf ^= 1;
-        t = s_next;
     }
 }
 

@@ -1125,32 +1125,37 @@ __global__ void __launch_bounds__(TPB, 2) k_g2p(PState<R> in, PState<R> out, con
     constexpr int NB = 1 << D;
     __shared__ __align__(128) R sv[2][NB][BN][4];
     __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ int s_ok, s_next;
+    // s_t[b]: the tile whose grid blocks are staged in buffer b.  Thread 0 writes s_t[b ^ 1]
+    // before the first barrier of an iteration; every thread reads s_t[b] at the top of the
+    // iteration, after the previous iteration's closing barrier, and the entry is not written
+    // again until the next iteration has passed that same barrier.
+    __shared__ int s_ok, s_t[2];
     unsigned phase[2] = {0u, 0u};
     const int ntiles = (int)*ntiles_p;
     if (threadIdx.x == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
         const int t0 = (int)atomicAdd(tile_ctr + 1, 1u);
-        s_next = t0;
+        s_t[0] = t0;
         if (t0 < ntiles) g2p_issue<D, R>(vel, skeys[tiles[t0]] >> (2 * D), c.nb, sv[0], &mbar[0]);
     }
     __syncthreads();
-    int t = s_next, buf = 0;
-    while (t < ntiles) {
+    for (int buf = 0;; buf ^= 1) {
+        const int t = s_t[buf];
+        if (t >= ntiles) break;
         if (threadIdx.x == 0) {
             const int t1 = (int)atomicAdd(tile_ctr + 1, 1u);
-            s_next = t1;
+            s_t[buf ^ 1] = t1;
             if (t1 < ntiles) g2p_issue<D, R>(vel, skeys[tiles[t1]] >> (2 * D), c.nb, sv[buf ^ 1], &mbar[buf ^ 1]);
-            s_ok = g2p_wait(&mbar[buf], phase[buf], err) ? 1 : 0;
+            const bool ok = g2p_wait(&mbar[buf], phase[buf], err);
+            if (!ok && t1 < ntiles) mbar_wait_bounded(&mbar[buf ^ 1], phase[buf ^ 1], 1u << 22);   // drain before leaving
+            s_ok = ok ? 1 : 0;
         }
         __syncthreads();
         if (!s_ok) return;
         g2p_compute<D, ORDER, R>(in, out, perm, skeys, tiles[t], tiles[t + 1], knext, c, err, sv[buf]);
         __syncthreads();
         phase[buf] ^= 1u;
-        buf ^= 1;
-        t = s_next;
     }
     // a copy issued for a tile index past the end is never issued; nothing is left in flight
 }

@@ -6,7 +6,9 @@ gravity, sticky walls, default tile and P2G kernel, as bench.py runs it):
 - P2G on sampled grid nodes: the oracle is given only the particles whose stencil reaches a
   sampled node, so its values at those nodes are complete;
 - the grid update on the whole grid;
-- G2P on sampled particles, from the GPU's grid velocities.
+- G2P on every particle, from the GPU's grid velocities;
+- the next step's keys, which G2P writes, against keys recomputed from the new positions
+  (a particle that G2P skipped or wrote twice shows up here).
 The initial state is deformed and moving (random F, v, B) so every term is exercised."""
 import numpy as np
 import pytest
@@ -47,11 +49,14 @@ def run():
     m_v, vt = sim.grid("velocity")
     sim.g2p()
     out = sim.download()
+    cell1, off1 = sim.download_positions()
+    sim.p2g()                                   # sorts the keys written by G2P
+    keys1, _ = sim.keys()
     sim.close()
     oc = bench.oracle_config(w, sc)
     vol = sc.dx ** 3 / w["ppc"]
     return dict(sc=sc, oc=oc, vol=vol, mass=w["rho"] * vol, x0=x0, v0=v0, B0=B0, F0=F0, cell0=cell0, off0=off0,
-                keys=keys, perm=perm, m_g=m_g, p_g=p_g, m_v=m_v, vt=vt, out=out)
+                keys=keys, perm=perm, m_g=m_g, p_g=p_g, m_v=m_v, vt=vt, out=out, cell1=cell1, off1=off1, keys1=keys1)
 
 
 def test_fullsize_keys_and_sort_bit_exact(run):
@@ -89,11 +94,10 @@ def test_fullsize_grid_update(run):
     assert relerr(run["vt"], vt_ref) <= TOL
 
 
-def test_fullsize_g2p_sampled_particles(run):
+def test_fullsize_g2p_every_particle(run):
     oc = run["oc"]
-    rng = np.random.default_rng(12)
-    idx = rng.choice(run["sc"].n, size=4000, replace=False)
-    x1, v1, B1, F1, bad = oracle.g2p(oc, run["x0"][idx], run["F0"][idx], run["vt"], run["vt"])
+    idx = np.arange(run["sc"].n)
+    x1, v1, B1, F1, bad = oracle.g2p(oc, run["x0"], run["F0"], run["vt"], run["vt"])
     assert bad == 0
     gx, gv, gB, gF = (a[idx] for a in run["out"])
     assert relerr(gv, v1) <= TOL
@@ -104,3 +108,8 @@ def test_fullsize_g2p_sampled_particles(run):
     disp_ref = x1 - run["x0"][idx]
     bound = TOL * np.abs(disp_ref).max() + 2 * np.finfo(np.float32).eps * run["sc"].dx
     assert np.abs((gx - run["x0"][idx]) - disp_ref).max() <= bound
+
+
+def test_fullsize_next_keys_match_positions(run):
+    ref = oracle.keys(run["oc"], 4, run["cell1"], run["off1"])
+    np.testing.assert_array_equal(run["keys1"], np.sort(ref))

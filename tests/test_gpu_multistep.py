@@ -45,7 +45,11 @@ def test_consecutive_steps_match_oracle(apic, p2g_kernel, tile):
         gx, gv, gB, gF = got
         assert relerr(gv, ov) <= 1e-5, f"step {step}"
         assert relerr(gB, oB) <= 1e-4, f"step {step}"
-        assert relerr(gF - F0, oF - F0) <= 1e-4, f"step {step}"
+        assert relerr(gF, oF) <= 1e-5, f"step {step}"
+        # the change of F in one step is ~1e-5 of F, so it carries the FP32 rounding of the
+        # stored F (half an ulp of |F| ~ 1) on top of the relative error of the velocity gradient
+        dF_bound = 1e-5 * np.abs(oF - F0).max() + 2 * np.finfo(np.float32).eps * np.abs(oF).max()
+        assert np.abs((gF - F0) - (oF - F0)).max() <= dF_bound, f"step {step}"
         assert np.abs(gx - ox).max() <= 1e-5 * sc.dx, f"step {step}"
         state = got
     sim.close()
