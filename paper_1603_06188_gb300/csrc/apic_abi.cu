@@ -122,7 +122,7 @@ struct Carve {
 
 // offsets of every buffer inside the workspace (relative to its base)
 struct Layout {
-    size_t st[2][7];
+    size_t st[2][APIC_STATE_LANES];
     size_t knext, kA, kB, vA, vB, radix_counts, scan_part, tiles, chunk_cnt, ntiles, tile_ctr;
     size_t acc, vel, flags, mom_part, mom_out, err, fallbacks, staging;
     size_t staging_doubles;
@@ -137,8 +137,11 @@ Layout layout_of(const HostCfg& c)
     const int64_t n = c.capacity > 0 ? c.capacity : 1;
     const size_t R = c.precision == 32 ? 4 : 8;
     for (int s = 0; s < 2; ++s) {
-        for (int i = 0; i < 6; ++i) L.st[s][i] = cv.take((size_t)n * 4 * R);
-        L.st[s][6] = cv.take((size_t)n * 2 * R);
+        // lanes A V Ba Bb Fa Fb (4 reals), Fc (2), Ta (4), Tb (2); 2-D keeps A V Ba Fa Tb
+        static const int width[APIC_STATE_LANES] = {4, 4, 4, 4, 4, 4, 2, 4, 2};
+        static const bool used2d[APIC_STATE_LANES] = {true, true, true, false, true, false, false, false, true};
+        for (int i = 0; i < APIC_STATE_LANES; ++i)
+            L.st[s][i] = cv.take((c.dim == 3 || used2d[i]) ? (size_t)n * width[i] * R : 0);
     }
     L.knext = cv.take((size_t)n * 4);
     L.kA = cv.take((size_t)n * 4);
@@ -289,7 +292,7 @@ apic_status apic_create(const apic_config* cfg, int64_t max_particles, void* wor
     s->ev_used = 0;
     char* base = (char*)workspace;
     for (int a = 0; a < 2; ++a)
-        for (int i = 0; i < 7; ++i) s->b.st[a][i] = base + L.st[a][i];
+        for (int i = 0; i < APIC_STATE_LANES; ++i) s->b.st[a][i] = base + L.st[a][i];
     s->b.knext = (uint32_t*)(base + L.knext);
     s->b.kA = (uint32_t*)(base + L.kA);
     s->b.kB = (uint32_t*)(base + L.kB);

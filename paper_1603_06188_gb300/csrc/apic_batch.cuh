@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(TPB, 2) kb_g2p(SimDesc<R>* __restrict__ descs,
         const uint32_t start = tile_start[t];
         const uint32_t end = tile_end(tile_sim, tile_start, t, ntiles, sim, (uint32_t)sd.c.n);
         g2p_compute<D, ORDER, R>(sd.st[sd.cur], sd.st[sd.cur ^ 1], sd.vb[kpar], sd.kb[kpar], start, end, sd.knext, sd.c,
-                                 sd.err, sv[buf]);
+                                 sd.err, sd.fallbacks, sv[buf]);
         __syncthreads();
         phase[buf] ^= 1u;
     }

@@ -16,14 +16,18 @@ namespace apic {
 //   3-D: A  = (o0, o1, o2, cell)   V  = (v0, v1, v2, B00)
 //        Ba = (B01, B02, B10, B11) Bb = (B12, B20, B21, B22)
 //        Fa = (F00, F01, F02, F10) Fb = (F11, F12, F20, F21)   Fc = (F22, id)
+//        Ta = (t00, t11, t22, t01) Tb = (t02, t12)
 //   2-D: A  = (o0, o1, cell, id)   V  = (v0, v1, B00, B01)
-//        Ba = (B10, B11, -, -)     Fa = (F00, F01, F10, F11)
-// o = offset in [0,1) inside integer cell `cell` (packed per axis), id = upload index.
+//        Ba = (B10, B11, t00, t11) Fa = (F00, F01, F10, F11)   Tb = (t01, -)
+// o = offset in [0,1) inside integer cell `cell` (packed per axis), id = upload index,
+// t = the symmetric stress tau_p = V_p P(F_p) F_p^T of the current F_p (Sec. 3.3 force).
+// tau is written wherever F_p is (upload, G2P), so P2G reads position, v, B and tau --
+// never F -- and the polar decomposition runs once per particle and step, in G2P.
 template <typename R> struct alignas(4 * sizeof(R)) V4 { R x, y, z, w; };
 template <typename R> struct alignas(2 * sizeof(R)) V2 { R x, y; };
 
 template <typename R> struct PState {
-    V4<R>* A; V4<R>* V; V4<R>* Ba; V4<R>* Bb; V4<R>* Fa; V4<R>* Fb; V2<R>* Fc;
+    V4<R>* A; V4<R>* V; V4<R>* Ba; V4<R>* Bb; V4<R>* Fa; V4<R>* Fb; V2<R>* Fc; V4<R>* Ta; V2<R>* Tb;
 };
 
 __device__ __forceinline__ V4<float> ld4(const V4<float>* p)
@@ -85,7 +89,37 @@ template <int D, typename R> struct Particle {
     R v[D];
     R B[D * D];
     R F[D * D];
+    R tau[(D == 3) ? 6 : 3];   // 3-D: t00 t11 t22 t01 t02 t12; 2-D: t00 t11 t01
 };
+
+// full D x D matrix (row-major) of a symmetric stress held as its independent entries
+template <int D, typename R> __device__ __forceinline__ void tau_full(const R* t, R* T)
+{
+    if (D == 3) {
+        T[0] = t[0]; T[4] = t[1]; T[8] = t[2];
+        T[1] = T[3] = t[3];
+        T[2] = T[6] = t[4];
+        T[5] = T[7] = t[5];
+    } else {
+        T[0] = t[0]; T[3] = t[1];
+        T[1] = T[2] = t[2];
+    }
+}
+
+// position (offset, cell; + id in 2-D): what the key and P2G need
+template <int D, typename R>
+__device__ __forceinline__ void load_x(const PState<R>& s, uint32_t k, Particle<D, R>& p)
+{
+    const V4<R> a = ld4(s.A + k);
+    if (D == 3) {
+        p.o[0] = a.x; p.o[1] = a.y; p.o[2] = a.z;
+        unpack_cell<D>(r2u(a.w), p.cell);
+    } else {
+        p.o[0] = a.x; p.o[1] = a.y;
+        unpack_cell<D>(r2u(a.z), p.cell);
+        p.id = r2u(a.w);
+    }
+}
 
 // position (offset, cell) and F (+ id): what G2P needs
 template <int D, typename R>
@@ -125,8 +159,25 @@ __device__ __forceinline__ void load_vB(const PState<R>& s, uint32_t k, Particle
     }
 }
 
+// the stress of the particle (what P2G needs besides position, v and B)
 template <int D, typename R>
-__device__ __forceinline__ void store_all(const PState<R>& s, uint32_t k, const Particle<D, R>& p)
+__device__ __forceinline__ void load_tau(const PState<R>& s, uint32_t k, Particle<D, R>& p)
+{
+    if (D == 3) {
+        const V4<R> ta = ld4(s.Ta + k);
+        const V2<R> tb = ld2(s.Tb + k);
+        p.tau[0] = ta.x; p.tau[1] = ta.y; p.tau[2] = ta.z; p.tau[3] = ta.w;
+        p.tau[4] = tb.x; p.tau[5] = tb.y;
+    } else {
+        const V4<R> ba = ld4(s.Ba + k);
+        const V2<R> tb = ld2(s.Tb + k);
+        p.tau[0] = ba.z; p.tau[1] = ba.w; p.tau[2] = tb.x;
+    }
+}
+
+// every lane of the particle; the stress lanes only when `with_tau` (a model is set)
+template <int D, typename R>
+__device__ __forceinline__ void store_all(const PState<R>& s, uint32_t k, const Particle<D, R>& p, bool with_tau)
 {
     const R z = R(0);
     if (D == 3) {
@@ -137,11 +188,16 @@ __device__ __forceinline__ void store_all(const PState<R>& s, uint32_t k, const 
         st4(s.Fa + k, V4<R>{p.F[0], p.F[1], p.F[2], p.F[3]});
         st4(s.Fb + k, V4<R>{p.F[4], p.F[5], p.F[6], p.F[7]});
         st2(s.Fc + k, V2<R>{p.F[8], u2r(p.id, z)});
+        if (with_tau) {
+            st4(s.Ta + k, V4<R>{p.tau[0], p.tau[1], p.tau[2], p.tau[3]});
+            st2(s.Tb + k, V2<R>{p.tau[4], p.tau[5]});
+        }
     } else {
         st4(s.A + k, V4<R>{p.o[0], p.o[1], u2r(pack_cell<D>(p.cell), z), u2r(p.id, z)});
         st4(s.V + k, V4<R>{p.v[0], p.v[1], p.B[0], p.B[1]});
-        st4(s.Ba + k, V4<R>{p.B[2], p.B[3], z, z});
+        st4(s.Ba + k, V4<R>{p.B[2], p.B[3], with_tau ? p.tau[0] : z, with_tau ? p.tau[1] : z});
         st4(s.Fa + k, V4<R>{p.F[0], p.F[1], p.F[2], p.F[3]});
+        if (with_tau) st2(s.Tb + k, V2<R>{p.tau[2], z});
     }
 }
 
@@ -324,13 +380,68 @@ __device__ __forceinline__ R polar_residual(const R* F, const R* Rot)
     return asym / (fmax > R(0) ? fmax : R(1));
 }
 
-// Kirchhoff-type stress tau = V_p P(F) F^T of the fixed-corotated model
-// P = 2 mu (F - R) + lam (J - 1) J F^{-T}  =>  P F^T = 2 mu (F - R) F^T + lam (J - 1) J I.
-// FP32: the polar rotation is recomputed in FP64 when the FP32 one fails its residual
-// check (nearly coincident singular values of F at FP32 resolution, or near-singular F);
-// each fallback is counted.
+template <typename R> __device__ __forceinline__ R rcbrt_t(R x);
+template <> __device__ __forceinline__ float rcbrt_t<float>(float x) { return rcbrtf(x); }
+template <> __device__ __forceinline__ double rcbrt_t<double>(double x) { return rcbrt(x); }
+
+// Rotation of the polar decomposition F = R S by the scaled Newton iteration
+//   X <- (g X + X^{-T} / g) / 2,   g = |det X|^{-1/3},   X^{-T} = cof(X) / det X
+// (Higham 1986, "Computing the polar decomposition -- with applications", with the
+// determinant scaling; the scaling is dropped once the step is small, where the plain
+// iteration converges quadratically).  A step below 2e-4 (FP32) / 1e-8 (FP64) means the
+// next one would be below rounding, so the iterate is returned.  Returns false, leaving
+// Rot unset, when det F <= 0 (the orthogonal factor is then not the det R = +1 rotation)
+// or without convergence in 12 steps; the caller then takes the Jacobi route.
+template <typename R>
+__device__ __forceinline__ bool polar_newton3(const R* F, R* Rot)
+{
+    R X[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) X[i] = F[i];
+    const R tol = sizeof(R) == 4 ? R(2e-4) : R(1e-8);
+    bool scale = true;
+#pragma unroll 1
+    for (int it = 0; it < 12; ++it) {
+        R C[9];
+        C[0] = X[4] * X[8] - X[5] * X[7];
+        C[1] = X[5] * X[6] - X[3] * X[8];
+        C[2] = X[3] * X[7] - X[4] * X[6];
+        C[3] = X[2] * X[7] - X[1] * X[8];
+        C[4] = X[0] * X[8] - X[2] * X[6];
+        C[5] = X[1] * X[6] - X[0] * X[7];
+        C[6] = X[1] * X[5] - X[2] * X[4];
+        C[7] = X[2] * X[3] - X[0] * X[5];
+        C[8] = X[0] * X[4] - X[1] * X[3];
+        const R det = X[0] * C[0] + X[1] * C[1] + X[2] * C[2];
+        if (!(det > R(0))) return false;
+        const R g = scale ? rcbrt_t<R>(det) : R(1);
+        const R a = R(0.5) * g, b = R(0.5) / (g * det);
+        R d = R(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const R xn = a * X[i] + b * C[i];
+            d = fmax(d, fabs(xn - X[i]));
+            X[i] = xn;
+        }
+        if (d <= tol) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) Rot[i] = X[i];
+            return true;
+        }
+        scale = d > R(1e-2);
+    }
+    return false;
+}
+
+// Kirchhoff-type stress tau = V_p P(F) F^T, which is symmetric for both models, returned
+// as its independent entries (3-D: t00 t11 t22 t01 t02 t12; 2-D: t00 t11 t01).
+// Fixed-corotated: P = 2 mu (F - R) + lam (J - 1) J F^{-T}
+//   =>  P F^T = 2 mu (F - R) F^T + lam (J - 1) J I, off-diagonal entries symmetrised.
+// FP32: the rotation is recomputed in FP64 when the FP32 one fails its residual check
+// (nearly coincident singular values of F at FP32 resolution, or near-singular F); each
+// fallback is counted.
 template <int D, typename R>
-__device__ __forceinline__ void stress_tau_fcr(const R* F, R mu, R lam, R vol, R* tau, unsigned* fallbacks)
+__device__ __forceinline__ void stress_sym_fcr(const R* F, R mu, R lam, R vol, R* t, unsigned* fallbacks)
 {
     R Rot[D * D];
     R J;
@@ -342,7 +453,7 @@ __device__ __forceinline__ void stress_tau_fcr(const R* F, R mu, R lam, R vol, R
         Rot[0] = c; Rot[1] = -s; Rot[2] = s; Rot[3] = c;
         J = F[0] * F[3] - F[1] * F[2];
     } else {
-        polar3<R>(F, Rot);
+        if (!polar_newton3<R>(F, Rot)) polar3<R>(F, Rot);
         if (sizeof(R) == 4) {
             if (polar_residual<R>(F, Rot) > R(2e-5)) {
                 double Fd[9], Rd[9];
@@ -354,39 +465,61 @@ __device__ __forceinline__ void stress_tau_fcr(const R* F, R mu, R lam, R vol, R
         }
         J = det3<R>(F);
     }
-    const R two_mu = R(2) * mu;
-    const R iso = lam * (J - R(1)) * J;
-    for (int a = 0; a < D; ++a)
-        for (int b = 0; b < D; ++b) {
-            R s = R(0);
-            for (int k = 0; k < D; ++k) s += (F[a * D + k] - Rot[a * D + k]) * F[b * D + k];
-            tau[a * D + b] = vol * (two_mu * s + (a == b ? iso : R(0)));
-        }
+    const R c2 = R(2) * mu * vol;
+    const R iso = vol * lam * (J - R(1)) * J;
+    auto s = [&](int a, int b) {
+        R x = R(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) x += (F[a * D + k] - Rot[a * D + k]) * F[b * D + k];
+        return x;
+    };
+    if (D == 3) {
+        t[0] = c2 * s(0, 0) + iso;
+        t[1] = c2 * s(1, 1) + iso;
+        t[2] = c2 * s(2, 2) + iso;
+        t[3] = R(0.5) * c2 * (s(0, 1) + s(1, 0));
+        t[4] = R(0.5) * c2 * (s(0, 2) + s(2, 0));
+        t[5] = R(0.5) * c2 * (s(1, 2) + s(2, 1));
+    } else {
+        t[0] = c2 * s(0, 0) + iso;
+        t[1] = c2 * s(1, 1) + iso;
+        t[2] = R(0.5) * c2 * (s(0, 1) + s(1, 0));
+    }
 }
 
 // Neo-Hookean: P = mu (F - F^{-T}) + lam log(J) F^{-T}  =>  tau = V (mu (F F^T - I) + lam log(J) I)
 template <int D, typename R>
-__device__ __forceinline__ void stress_tau_nh(const R* F, R mu, R lam, R vol, R* tau)
+__device__ __forceinline__ void stress_sym_nh(const R* F, R mu, R lam, R vol, R* t)
 {
     const R J = (D == 3) ? det3<R>(F) : F[0] * F[3] - F[1] * F[2];
-    const R iso = lam * log(J) - mu;
+    const R iso = vol * (lam * log(J) - mu);
+    const R cm = vol * mu;
+    auto ff = [&](int a, int b) {
+        R x = R(0);
 #pragma unroll
-    for (int a = 0; a < D; ++a)
-#pragma unroll
-        for (int b = 0; b < D; ++b) {
-            R s = R(0);
-#pragma unroll
-            for (int k = 0; k < D; ++k) s += F[a * D + k] * F[b * D + k];
-            tau[a * D + b] = vol * (mu * s + (a == b ? iso : R(0)));
-        }
+        for (int k = 0; k < D; ++k) x += F[a * D + k] * F[b * D + k];
+        return x;
+    };
+    if (D == 3) {
+        t[0] = cm * ff(0, 0) + iso;
+        t[1] = cm * ff(1, 1) + iso;
+        t[2] = cm * ff(2, 2) + iso;
+        t[3] = cm * ff(0, 1);
+        t[4] = cm * ff(0, 2);
+        t[5] = cm * ff(1, 2);
+    } else {
+        t[0] = cm * ff(0, 0) + iso;
+        t[1] = cm * ff(1, 1) + iso;
+        t[2] = cm * ff(0, 1);
+    }
 }
 
-// model 1: fixed-corotated, model 2: Neo-Hookean
+// model 1: fixed-corotated, model 2: Neo-Hookean (model 0 has no stress and never calls this)
 template <int D, typename R>
-__device__ __forceinline__ void stress_tau(int model, const R* F, R mu, R lam, R vol, R* tau, unsigned* fallbacks)
+__device__ __forceinline__ void stress_sym(int model, const R* F, R mu, R lam, R vol, R* t, unsigned* fallbacks)
 {
-    if (model == 2) stress_tau_nh<D, R>(F, mu, lam, vol, tau);
-    else stress_tau_fcr<D, R>(F, mu, lam, vol, tau, fallbacks);
+    if (model == 2) stress_sym_nh<D, R>(F, mu, lam, vol, t);
+    else stress_sym_fcr<D, R>(F, mu, lam, vol, t, fallbacks);
 }
 
 // ---------------------------------------------------------------- misc

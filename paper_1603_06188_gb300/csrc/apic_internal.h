@@ -10,12 +10,15 @@
 #define APIC_ERRBIT_TIMEOUT 2u   // a bounded mbarrier wait ran out
 #define APIC_ERRBIT_CAPACITY 4u  // tile list overflow
 
+// particle state lanes per copy: A V Ba Bb Fa Fb Fc Ta Tb (layout in apic_device.cuh)
+#define APIC_STATE_LANES 9
+
 namespace apic {
 
 // Type-erased description of one simulation's device buffers, handed to the launchers.
 struct Buffers {
     // particle state: two copies (ping-pong), 7 arrays each, element size per precision
-    void* st[2][7];
+    void* st[2][APIC_STATE_LANES];
     uint32_t* knext;             // keys of the current particle order (input of the sort)
     uint32_t* kA; uint32_t* kB;  // radix ping-pong keys
     uint32_t* vA; uint32_t* vB;  // radix ping-pong values (particle indices)

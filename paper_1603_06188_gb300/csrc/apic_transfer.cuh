@@ -59,6 +59,8 @@ template <typename R> PState<R> state_of(const Buffers& b, int which)
     s.Fa = (V4<R>*)b.st[which][4];
     s.Fb = (V4<R>*)b.st[which][5];
     s.Fc = (V2<R>*)b.st[which][6];
+    s.Ta = (V4<R>*)b.st[which][7];
+    s.Tb = (V2<R>*)b.st[which][8];
     return s;
 }
 
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(TPB) k_keys(PState<R> st, DevCfg<R> c, uint32_
     const int k = blockIdx.x * TPB + threadIdx.x;
     if (k >= c.n) return;
     Particle<D, R> p;
-    load_xF<D, R>(st, k, p);
+    load_x<D, R>(st, k, p);
     keys[k] = key_of<D, ORDER, R>(p.o, p.cell, c, err);
 }
 
@@ -170,8 +172,9 @@ __global__ void __launch_bounds__(TPB) k_p2g(PState<R> st, const uint32_t* __res
             if (ok) {
                 Particle<D, R> p;
                 const uint32_t q = perm[k];
-                load_xF<D, R>(st, q, p);
+                load_x<D, R>(st, q, p);
                 load_vB<D, R>(st, q, p);
+                if (c.model != 0) load_tau<D, R>(st, q, p);
                 int base[D];
                 if (!particle_stencil<D, ORDER, R>(p.o, p.cell, c, base, fx, w, dw)) set_err(err, APIC_ERRBIT_RANGE);
 #pragma unroll
@@ -187,7 +190,7 @@ __global__ void __launch_bounds__(TPB) k_p2g(PState<R> st, const uint32_t* __res
                 for (int i = 0; i < D * D; ++i) mC[i] = s * p.B[i];
                 if (c.model != 0) {
                     R tau[D * D];
-                    stress_tau<D, R>(c.model, p.F, c.mu, c.lam, c.vol, tau, fallbacks);
+                    tau_full<D, R>(p.tau, tau);
 #pragma unroll
                     for (int i = 0; i < D * D; ++i) T[i] = dt_dx * tau[i];
                 } else {
@@ -311,8 +314,8 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// slot of packed state, in units of R: 3-D A V Ba Bb Fa Fb Fc (+2 pad) = 28, 2-D A V Ba Fa = 16
-template <int D> __host__ __device__ constexpr int slot_words() { return D == 3 ? 28 : 16; }
+// slot of packed state, in units of R: 3-D A V Ba Bb Ta Tb (+2 pad) = 24, 2-D A V Ba Tb (+2) = 16
+template <int D> __host__ __device__ constexpr int slot_words() { return D == 3 ? 24 : 16; }
 
 template <typename R> __device__ __forceinline__ void cp_group4(R* dst, const V4<R>* src)
 {
@@ -323,49 +326,59 @@ template <typename R> __device__ __forceinline__ void cp_group4(R* dst, const V4
         cp_async16(dst + 2, reinterpret_cast<const R*>(src) + 2);
     }
 }
+template <typename R> __device__ __forceinline__ void cp_group2(R* dst, const V2<R>* src)
+{
+    if (sizeof(R) == 4) cp_async8(dst, src);
+    else cp_async16(dst, src);
+}
 
-template <int D, typename R> __device__ __forceinline__ void stage_particle(R* slot, const PState<R>& s, uint32_t q)
+// what P2G reads of particle q: position, v, B and (with a stress model) tau
+template <int D, typename R>
+__device__ __forceinline__ void stage_particle(R* slot, const PState<R>& s, uint32_t q, bool with_tau)
 {
     cp_group4<R>(slot + 0, s.A + q);
     cp_group4<R>(slot + 4, s.V + q);
     cp_group4<R>(slot + 8, s.Ba + q);
     if (D == 3) {
         cp_group4<R>(slot + 12, s.Bb + q);
-        cp_group4<R>(slot + 16, s.Fa + q);
-        cp_group4<R>(slot + 20, s.Fb + q);
-        if (sizeof(R) == 4) cp_async8(slot + 24, s.Fc + q);
-        else cp_async16(slot + 24, s.Fc + q);
+        if (with_tau) {
+            cp_group4<R>(slot + 16, s.Ta + q);
+            cp_group2<R>(slot + 20, s.Tb + q);
+        }
     } else {
-        cp_group4<R>(slot + 12, s.Fa + q);
+        if (with_tau) cp_group2<R>(slot + 12, s.Tb + q);
     }
 }
 
-template <int D, typename R> __device__ __forceinline__ void read_staged(const R* slot, Particle<D, R>& p)
+template <int D, typename R>
+__device__ __forceinline__ void read_staged(const R* slot, Particle<D, R>& p, bool with_tau)
 {
     const V4<R> a = *reinterpret_cast<const V4<R>*>(slot + 0);
     const V4<R> v = *reinterpret_cast<const V4<R>*>(slot + 4);
     const V4<R> ba = *reinterpret_cast<const V4<R>*>(slot + 8);
     if (D == 3) {
         const V4<R> bb = *reinterpret_cast<const V4<R>*>(slot + 12);
-        const V4<R> fa = *reinterpret_cast<const V4<R>*>(slot + 16);
-        const V4<R> fb = *reinterpret_cast<const V4<R>*>(slot + 20);
-        const V2<R> fc = *reinterpret_cast<const V2<R>*>(slot + 24);
         p.o[0] = a.x; p.o[1] = a.y; p.o[2] = a.z;
         unpack_cell<D>(r2u(a.w), p.cell);
         p.v[0] = v.x; p.v[1] = v.y; p.v[2] = v.z;
         p.B[0] = v.w; p.B[1] = ba.x; p.B[2] = ba.y; p.B[3] = ba.z; p.B[4] = ba.w;
         p.B[5] = bb.x; p.B[6] = bb.y; p.B[7] = bb.z; p.B[8] = bb.w;
-        p.F[0] = fa.x; p.F[1] = fa.y; p.F[2] = fa.z; p.F[3] = fa.w;
-        p.F[4] = fb.x; p.F[5] = fb.y; p.F[6] = fb.z; p.F[7] = fb.w;
-        p.F[8] = fc.x; p.id = r2u(fc.y);
+        if (with_tau) {
+            const V4<R> ta = *reinterpret_cast<const V4<R>*>(slot + 16);
+            const V2<R> tb = *reinterpret_cast<const V2<R>*>(slot + 20);
+            p.tau[0] = ta.x; p.tau[1] = ta.y; p.tau[2] = ta.z; p.tau[3] = ta.w;
+            p.tau[4] = tb.x; p.tau[5] = tb.y;
+        }
     } else {
-        const V4<R> fa = *reinterpret_cast<const V4<R>*>(slot + 12);
         p.o[0] = a.x; p.o[1] = a.y;
         unpack_cell<D>(r2u(a.z), p.cell);
         p.id = r2u(a.w);
         p.v[0] = v.x; p.v[1] = v.y;
         p.B[0] = v.z; p.B[1] = v.w; p.B[2] = ba.x; p.B[3] = ba.y;
-        p.F[0] = fa.x; p.F[1] = fa.y; p.F[2] = fa.z; p.F[3] = fa.w;
+        if (with_tau) {
+            const V2<R> tb = *reinterpret_cast<const V2<R>*>(slot + 12);
+            p.tau[0] = ba.z; p.tau[1] = ba.w; p.tau[2] = tb.x;
+        }
     }
 }
 
@@ -457,11 +470,10 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
     constexpr int NVS = NVAL / ZS;
     const int lane = threadIdx.x & 31;
     const int lig = threadIdx.x % G;
-    const int leader = lane & ~(G - 1);
-    const unsigned gmask = (G == 32) ? FULLMASK : (((1u << G) - 1u) << leader);
     const R dt_dx = c.dt * c.inv_dx;
     const R m = c.mass;
     const R sC = (c.transfer == 0) ? m * c.inv_kdx : R(0);
+    const bool with_tau = c.model != 0;
     const uint32_t blk = skeys[start] >> (2 * D);
     int bo[3] = {0, 0, 0};
     block_coords<D, R>(blk, c, bo);
@@ -474,14 +486,25 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
             if (k + 1 == end || (skeys[k + 1] & (NC - 1)) != cl) cend[cl] = k + 1;
         }
         __syncthreads();
+        // A warp takes GPW cells at once (one per lane group) and runs a warp-uniform number
+        // of iterations -- the longest run among them -- so all lanes follow one instruction
+        // stream; lanes past their run carry a neutral particle that adds zeros.  (Groups
+        // taking cells on their own fall out of step once the run lengths differ, and the
+        // warp then executes them one after another.)
+        constexpr int GPW = 32 / G;
+        const int gw = lane / G;
         for (;;) {
-            int cell = 0;
-            if (lig == 0) cell = atomicAdd(s_cell, 1);
-            cell = __shfl_sync(gmask, cell, leader);
-            if (cell >= NC) break;
-            const uint32_t kb = cbeg[cell], ke = cend[cell];
-            if (kb >= ke) continue;   // uniform across the group
-            const int lb[3] = {cell & 3, (cell >> 2) & 3, (D == 3) ? (cell >> 4) : 0};
+            int cb = 0;
+            if (lane == 0) cb = atomicAdd(s_cell, GPW);
+            cb = __shfl_sync(FULLMASK, cb, 0);
+            if (cb >= NC) break;
+            const int cell = cb + gw;
+            const bool has = cell < NC;
+            const uint32_t kb = has ? cbeg[cell] : 0u, ke = has ? cend[cell] : 0u;
+            const int lb[3] = {cell & 3, (cell >> 2) & 3, (D == 3) ? ((cell >> 4) & 3) : 0};
+            const uint32_t mine = (ke > kb + (uint32_t)lig) ? (ke - kb - (uint32_t)lig + G - 1) / G : 0u;
+            const uint32_t iters = __reduce_max_sync(FULLMASK, mine);
+            if (iters == 0u) continue;
 #pragma unroll 1
             for (int slab = 0; slab < ZS; ++slab) {
             R cur[NVS];
@@ -493,20 +516,33 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
 #pragma unroll
             for (int i = 0; i < NSL; ++i) {
                 const uint32_t kk = kb + lig + (uint32_t)(i * G);
-                if (kk < ke) stage_particle<D, R>(pslots + (size_t)(i * NT + threadIdx.x) * SW, st, perm[kk]);
+                if (kk < ke) stage_particle<D, R>(pslots + (size_t)(i * NT + threadIdx.x) * SW, st, perm[kk], with_tau);
                 cp_async_commit();
             }
-            int it = 0;
-            for (uint32_t k = kb + lig; k < ke; k += G, ++it) {
+#pragma unroll 1
+            for (uint32_t it = 0; it < iters; ++it) {
+                const uint32_t k = kb + lig + it * G;
+                bool live = k < ke;
                 cp_async_wait<NSL - 1>();
-                const int sl = it % NSL;
-                R* slot = pslots + (size_t)(sl * NT + threadIdx.x) * SW;
+                R* slot = pslots + (size_t)((it % NSL) * NT + threadIdx.x) * SW;
                 Particle<D, R> p;
-                read_staged<D, R>(slot, p);
+                read_staged<D, R>(slot, p, with_tau);
                 {
                     const uint32_t kn = k + (uint32_t)(NSL * G);
-                    if (kn < ke) stage_particle<D, R>(slot, st, perm[kn]);
+                    if (kn < ke) stage_particle<D, R>(slot, st, perm[kn], with_tau);
                     cp_async_commit();
+                }
+                if (!live) {   // neutral: an in-cell position and zero state (finite weights, zero sums)
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        p.o[a] = R(0.5);
+                        p.cell[a] = bo[a] + lb[a] + (ORDER == 3 ? 1 : 0);
+                        p.v[a] = R(0);
+                    }
+#pragma unroll
+                    for (int i = 0; i < D * D; ++i) p.B[i] = R(0);
+#pragma unroll
+                    for (int i = 0; i < ((D == 3) ? 6 : 3); ++i) p.tau[i] = R(0);
                 }
                 int base[D];
                 R w[D][K], dw[D][K], fx[D];
@@ -514,20 +550,21 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
 #pragma unroll
                 for (int a = 0; a < D; ++a)
                     if (base[a] - bo[a] != lb[a]) ok = false;
-                if (!ok) {
+                if (live && !ok) {
                     set_err(err, APIC_ERRBIT_RANGE);
-                    continue;
+                    live = false;
                 }
+                const R ml = live ? m : R(0);
                 R mv[D], mC[D * D], T[D * D];
 #pragma unroll
-                for (int a = 0; a < D; ++a) mv[a] = m * p.v[a];
+                for (int a = 0; a < D; ++a) mv[a] = ml * p.v[a];
 #pragma unroll
-                for (int i = 0; i < D * D; ++i) mC[i] = sC * p.B[i];
-                if (c.model != 0) {
+                for (int i = 0; i < D * D; ++i) mC[i] = (live ? sC : R(0)) * p.B[i];
+                if (with_tau) {
                     R tau[D * D];
-                    stress_tau<D, R>(c.model, p.F, c.mu, c.lam, c.vol, tau, fallbacks);
+                    tau_full<D, R>(p.tau, tau);
 #pragma unroll
-                    for (int i = 0; i < D * D; ++i) T[i] = dt_dx * tau[i];
+                    for (int i = 0; i < D * D; ++i) T[i] = (live ? dt_dx : R(0)) * tau[i];
                 } else {
 #pragma unroll
                     for (int i = 0; i < D * D; ++i) T[i] = R(0);
@@ -560,7 +597,7 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
                                     const R qv = qab[a] + mC[a * 3 + 2] * r2;
                                     cur[j * NV + a] += wv * qv - h[a] * wz - kz[a] * dwz;
                                 }
-                                cur[j * NV + 3] += wv * m;
+                                cur[j * NV + 3] += wv * ml;
                             }
                         }
                 } else {
@@ -577,18 +614,20 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
                                 const R qv = mv[a] + mC[a * 2 + 0] * r0 + mC[a * 2 + 1] * r1;
                                 cur[j * NV + a] += wv * qv - (T[a * 2 + 0] * g0 + T[a * 2 + 1] * g1);
                             }
-                            cur[j * NV + 2] += wv * m;
+                            cur[j * NV + 2] += wv * ml;
                         }
                 }
             }
             cp_async_wait<0>();
             int off = 0, cnt = NVS;
-            ReduceScatter<R, NVS, G>::run(cur, gmask, lig, off, cnt);
+            ReduceScatter<R, NVS, G>::run(cur, FULLMASK, lig, off, cnt);
             constexpr int FIN = ReduceScatter<R, NVS, G>::FINAL;
-            R* dst = cellsum + (size_t)cell * NVAL + (size_t)slab * NVS + off;
+            if (has) {
+                R* dst = cellsum + (size_t)cell * NVAL + (size_t)slab * NVS + off;
 #pragma unroll
-            for (int i = 0; i < FIN; ++i)
-                if (i < cnt) dst[i] = cur[i];
+                for (int i = 0; i < FIN; ++i)
+                    if (i < cnt) dst[i] = cur[i];
+            }
             }   // slab
         }
         __syncthreads();
@@ -723,8 +762,9 @@ __global__ void __launch_bounds__(256) k_p2g_interleaved(PState<R> st, const uin
         for (uint32_t k = kb + slot; k < ke; k += SLOTS) {
             Particle<D, R> p;
             const uint32_t q = perm[k];
-            load_xF<D, R>(st, q, p);
+            load_x<D, R>(st, q, p);
             load_vB<D, R>(st, q, p);
+            if (c.model != 0) load_tau<D, R>(st, q, p);
             int base[D];
             R w[D][K], dw[D][K], fx[D];
             bool ok = particle_stencil<D, ORDER, R>(p.o, p.cell, c, base, fx, w, dw);
@@ -742,7 +782,7 @@ __global__ void __launch_bounds__(256) k_p2g_interleaved(PState<R> st, const uin
             for (int i = 0; i < D * D; ++i) mC[i] = sC * p.B[i];
             if (c.model != 0) {
                 R tau[D * D];
-                stress_tau<D, R>(c.model, p.F, c.mu, c.lam, c.vol, tau, fallbacks);
+                tau_full<D, R>(p.tau, tau);
 #pragma unroll
                 for (int i = 0; i < D * D; ++i) T[i] = dt_dx * tau[i];
             } else {
@@ -982,7 +1022,7 @@ template <int D, int ORDER, typename R>
 __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>& out, const uint32_t* __restrict__ perm,
                                             const uint32_t* __restrict__ skeys, uint32_t start, uint32_t end,
                                             uint32_t* __restrict__ knext, const DevCfg<R>& c, uint32_t* err,
-                                            const R (*sv)[(D == 3) ? 64 : 16][4])
+                                            uint32_t* fallbacks, const R (*sv)[(D == 3) ? 64 : 16][4])
 {
     constexpr int K = ORDER + 1;
     const R dt_dx = c.dt * c.inv_dx;
@@ -1109,7 +1149,9 @@ __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>
             p.o[a] = o;
             p.cell[a] = cl;
         }
-        store_all<D, R>(out, k, p);
+        // the stress of the new F_p, for the next P2G
+        if (c.model != 0) stress_sym<D, R>(c.model, p.F, c.mu, c.lam, c.vol, p.tau, fallbacks);
+        store_all<D, R>(out, k, p, c.model != 0);
         knext[k] = key_of<D, ORDER, R>(p.o, p.cell, c, err);
     }
 }
@@ -1119,7 +1161,7 @@ __global__ void __launch_bounds__(TPB, 2) k_g2p(PState<R> in, PState<R> out, con
                                              const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ tiles,
                                              const uint32_t* __restrict__ ntiles_p, uint32_t* __restrict__ tile_ctr,
                                              const R* __restrict__ vel, uint32_t* __restrict__ knext, DevCfg<R> c,
-                                             uint32_t* err)
+                                             uint32_t* err, uint32_t* fallbacks)
 {
     constexpr int BN = (D == 3) ? 64 : 16;
     constexpr int NB = 1 << D;
@@ -1153,7 +1195,7 @@ __global__ void __launch_bounds__(TPB, 2) k_g2p(PState<R> in, PState<R> out, con
         }
         __syncthreads();
         if (!s_ok) return;
-        g2p_compute<D, ORDER, R>(in, out, perm, skeys, tiles[t], tiles[t + 1], knext, c, err, sv[buf]);
+        g2p_compute<D, ORDER, R>(in, out, perm, skeys, tiles[t], tiles[t + 1], knext, c, err, fallbacks, sv[buf]);
         __syncthreads();
         phase[buf] ^= 1u;
     }
@@ -1320,7 +1362,7 @@ template <int D, typename R>
 __global__ void __launch_bounds__(TPB) k_upload(PState<R> st, DevCfg<R> c, double dx, double o0, double o1, double o2,
                                                 const double* __restrict__ x, const double* __restrict__ v,
                                                 const double* __restrict__ B, const double* __restrict__ F,
-                                                uint32_t* err)
+                                                uint32_t* err, uint32_t* fallbacks)
 {
     const int k = blockIdx.x * TPB + threadIdx.x;
     if (k >= c.n) return;
@@ -1348,7 +1390,8 @@ __global__ void __launch_bounds__(TPB) k_upload(PState<R> st, DevCfg<R> c, doubl
         p.B[i] = B ? (R)B[(size_t)k * D * D + i] : R(0);
         p.F[i] = F ? (R)F[(size_t)k * D * D + i] : ((i % (D + 1)) == 0 ? R(1) : R(0));
     }
-    store_all<D, R>(st, k, p);
+    if (c.model != 0) stress_sym<D, R>(c.model, p.F, c.mu, c.lam, c.vol, p.tau, fallbacks);
+    store_all<D, R>(st, k, p, c.model != 0);
 }
 
 template <int D, typename R>
@@ -1461,7 +1504,7 @@ template <typename R> struct Impl {
         DevCfg<R> c = HostToDev<R>::make(h, n);
         PState<R> in = state_of<R>(b, cur), out = state_of<R>(b, cur ^ 1);
         APIC_DISPATCH(h, (k_g2p<D, O, R><<<L.g2p_grid, TPB, 0, s>>>(in, out, perm, sk, b.tiles, b.ntiles, b.tile_ctr,
-                                                                      (const R*)b.vel, b.knext, c, b.err)));
+                                                                      (const R*)b.vel, b.knext, c, b.err, b.fallbacks)));
         return cudaGetLastError();
     }
     static cudaError_t upload(const HostCfg& h, const Buffers& b, int cur, int64_t n, const double* x,
@@ -1471,9 +1514,9 @@ template <typename R> struct Impl {
         DevCfg<R> c = HostToDev<R>::make(h, n);
         PState<R> st = state_of<R>(b, cur);
         if (h.dim == 3)
-            k_upload<3, R><<<blocks_for(n), TPB, 0, s>>>(st, c, h.dx, h.origin[0], h.origin[1], h.origin[2], x, v, B, F, b.err);
+            k_upload<3, R><<<blocks_for(n), TPB, 0, s>>>(st, c, h.dx, h.origin[0], h.origin[1], h.origin[2], x, v, B, F, b.err, b.fallbacks);
         else
-            k_upload<2, R><<<blocks_for(n), TPB, 0, s>>>(st, c, h.dx, h.origin[0], h.origin[1], h.origin[2], x, v, B, F, b.err);
+            k_upload<2, R><<<blocks_for(n), TPB, 0, s>>>(st, c, h.dx, h.origin[0], h.origin[1], h.origin[2], x, v, B, F, b.err, b.fallbacks);
         return cudaGetLastError();
     }
     static cudaError_t download(const HostCfg& h, const Buffers& b, int cur, int64_t n, double* x, double* v,
