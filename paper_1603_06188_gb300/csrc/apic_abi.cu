@@ -33,6 +33,8 @@ struct apic_sim {
     int phase;             // 0 idle, 1 after p2g, 2 after grid update
     uint32_t* skeys;       // last sort's keys / permutation (device)
     uint32_t* perm;
+    bool order_sorted;     // the particles are stored in the order of skeys (after G2P)
+    uint32_t epoch;        // look-back epoch of the incremental sort (0: words not cleared yet)
     int64_t max_tiles;
     std::string err;
     int64_t launches;      // kernels launched since creation
@@ -123,6 +125,7 @@ struct Carve {
 // offsets of every buffer inside the workspace (relative to its base)
 struct Layout {
     size_t st[2][APIC_STATE_LANES];
+    size_t mk[2], mv[2], midx, choff, mctl, lbs;
     size_t knext, kA, kB, vA, vB, radix_counts, scan_part, tiles, chunk_cnt, ntiles, tile_ctr;
     size_t acc, vel, flags, mom_part, mom_out, err, fallbacks, staging;
     size_t staging_doubles;
@@ -149,6 +152,14 @@ Layout layout_of(const HostCfg& c)
     L.vA = cv.take((size_t)n * 4);
     L.vB = cv.take((size_t)n * 4);
     L.radix_counts = cv.take((size_t)256 * (radix_tiles(n) + 4) * 4);
+    for (int i = 0; i < 2; ++i) {
+        L.mk[i] = cv.take((size_t)n * 4);
+        L.mv[i] = cv.take((size_t)n * 4);
+    }
+    L.midx = cv.take((size_t)n * 4);
+    L.choff = cv.take(((size_t)radix_tiles(n) + 1) * 4);
+    L.mctl = cv.take(kMsortCtlBytes);
+    L.lbs = cv.take((size_t)256 * ((size_t)radix_tiles(n) + 1) * 8);
     const int64_t nchunks = (n + c.tile - 1) / c.tile;
     L.scan_part = cv.take(scan_partials_needed(n > nchunks ? n : nchunks) * 4);
     L.max_tiles = nchunks + (n < c.nblocks ? n : c.nblocks) + 2;
@@ -286,6 +297,8 @@ apic_status apic_create(const apic_config* cfg, int64_t max_particles, void* wor
     s->keys_valid = false;
     s->phase = 0;
     s->skeys = s->perm = nullptr;
+    s->order_sorted = false;
+    s->epoch = 0;
     s->max_tiles = L.max_tiles;
     s->launches = 0;
     s->prof_on = false;
@@ -299,6 +312,15 @@ apic_status apic_create(const apic_config* cfg, int64_t max_particles, void* wor
     s->b.vA = (uint32_t*)(base + L.vA);
     s->b.vB = (uint32_t*)(base + L.vB);
     s->b.radix_counts = (uint32_t*)(base + L.radix_counts);
+    for (int i = 0; i < 2; ++i) {
+        s->b.mk[i] = (uint32_t*)(base + L.mk[i]);
+        s->b.mv[i] = (uint32_t*)(base + L.mv[i]);
+    }
+    s->b.midx = (uint32_t*)(base + L.midx);
+    s->b.choff = (uint32_t*)(base + L.choff);
+    s->b.mctl = (uint32_t*)(base + L.mctl);
+    s->b.mhist = s->b.mctl + 16;
+    s->b.lbs = (unsigned long long*)(base + L.lbs);
     s->b.scan_part = (uint32_t*)(base + L.scan_part);
     s->b.tiles = (uint32_t*)(base + L.tiles);
     s->b.chunk_cnt = (uint32_t*)(base + L.chunk_cnt);
@@ -384,6 +406,7 @@ apic_status apic_upload(apic_sim* s, int64_t n, const double* x, const double* v
     s->keys_valid = false;
     s->phase = 0;
     s->skeys = s->perm = nullptr;
+    s->order_sorted = false;
     CK(DISPATCH(s, upload, s->c, s->b, s->cur, n, dx_, dv, dB, dF, s->stream), "upload kernel");
     if (!on_device) return check_device(s);
     return APIC_OK;
@@ -453,7 +476,15 @@ apic_status apic_p2g(apic_sim* s)
         PhaseScope ps(s, APIC_PHASE_KEYS, 1);
         CK(DISPATCH(s, keys, s->c, s->b, s->cur, n, s->stream), "keys kernel");
     }
-    {
+    if (s->keys_valid && s->order_sorted && s->skeys) {
+        // particles are stored in the previous sorted order: sort only the moved keys
+        PhaseScope ps(s, APIC_PHASE_SORT, 2 + ((s->c.key_bits + 7) / 8));
+        uint32_t* kout = s->skeys == s->b.kA ? s->b.kB : s->b.kA;
+        uint32_t* vout = s->skeys == s->b.kA ? s->b.vB : s->b.vA;
+        CK(resort(s->b, n, s->c.key_bits, s->skeys, kout, vout, &s->epoch, s->L.sms, s->stream), "incremental sort");
+        s->skeys = kout;
+        s->perm = vout;
+    } else {
         PhaseScope ps(s, APIC_PHASE_SORT, 2 + ((s->c.key_bits + 7) / 8));
         CK(radix_sort(s->b, n, s->c.key_bits, s->stream, &s->skeys, &s->perm), "radix sort");
     }
@@ -496,6 +527,7 @@ apic_status apic_g2p(apic_sim* s)
         }
         s->cur ^= 1;
         s->keys_valid = true;
+        s->order_sorted = true;   // G2P wrote particle k of the sorted order at k
     }
     s->phase = 0;
     return APIC_OK;
@@ -1020,6 +1052,7 @@ apic_status apic_batch_add(apic_batch* b, apic_sim* s)
         s->launches += 1;
     }
     BCK(cudaStreamSynchronize(s->stream), "synchronize member stream");
+    s->order_sorted = false;
     s->batch = b;
     b->members.push_back(s);
     b->dirty = true;
@@ -1047,6 +1080,7 @@ apic_status apic_batch_remove(apic_batch* b, apic_sim* s)
         s->skeys = kpar ? s->b.kB : s->b.kA;
         s->perm = kpar ? s->b.vB : s->b.vA;
         s->keys_valid = true;
+        s->order_sorted = true;   // batched G2P also stores particle k of the sorted order at k
     }
     b->dirty = true;
     return APIC_OK;

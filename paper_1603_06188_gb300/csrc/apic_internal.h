@@ -23,6 +23,14 @@ struct Buffers {
     uint32_t* kA; uint32_t* kB;  // radix ping-pong keys
     uint32_t* vA; uint32_t* vB;  // radix ping-pong values (particle indices)
     uint32_t* radix_counts;      // 256 * radix tiles
+    // incremental sort: moved keys / indices (radix ping-pong), moved indices in index order,
+    // per-chunk moved offsets, control words + digit counts, epoch-stamped look-back words
+    uint32_t* mk[2]; uint32_t* mv[2];
+    uint32_t* midx;
+    uint32_t* choff;
+    uint32_t* mctl;              // [0] chunk counter, [1] moved count, [2..5] pass tile counters
+    uint32_t* mhist;             // [4][256] digit counts of the moved keys (follows mctl)
+    unsigned long long* lbs;     // 256 * (radix tiles + 1)
     uint32_t* scan_part;         // partial sums of the device scan
     uint32_t* tiles;             // tile start offsets (+ end sentinel)
     uint32_t* chunk_cnt;         // per-chunk tile counts (scanned in place)
@@ -70,6 +78,11 @@ struct SortDesc {
 int radix_tiles(int64_t n);
 size_t scan_partials_needed(int64_t n);
 // sorts knext (values = identity) into (*keys_out, *vals_out); returns the CUDA error
+constexpr size_t kMsortCtlBytes = 64 + 4 * 256 * 4;   // mctl words + mhist
+// Incremental stable sort of knext given the previous sorted keys pk, valid when the
+// particles are stored in that previous order; writes keys / permutation to kout / vout.
+cudaError_t resort(const Buffers& b, int64_t n, int key_bits, const uint32_t* pk, uint32_t* kout, uint32_t* vout,
+                   uint32_t* epoch, int sms, cudaStream_t s);
 cudaError_t radix_sort(const Buffers& b, int64_t n, int key_bits, cudaStream_t s,
                        uint32_t** keys_out, uint32_t** vals_out);
 cudaError_t build_tiles(const Buffers& b, const uint32_t* skeys, int64_t n, int dim, int tile,

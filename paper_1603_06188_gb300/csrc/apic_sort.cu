@@ -408,6 +408,299 @@ __global__ void __launch_bounds__(RT) k_onesweep_pass(const uint32_t* __restrict
     }
 }
 
+// ---------------------------------------------------------------- incremental sort
+// Between steps the particles are stored in the previous sorted order (G2P writes particle
+// k of that order at k), so with P = the previous sorted keys, the particles whose key did
+// not change, U = {k : knext[k] == P[k]}, are already in (key, k) order.  Only the moved
+// ones, M, are sorted -- stably, from index order, so by (key, k) -- and the two sorted
+// sequences are merged by (key, k): the result is the stable order of all keys, the same
+// permutation the full sort gives.
+//   k_moved       flags and compacts M in index order (chunk offsets by decoupled look-back),
+//                 counts M's digits for every pass, and stores m
+//   k_msort_pass  one LSD pass over M (m read on the device; tiles taken from a counter)
+//   k_merge       U element k goes to (k - #M before k) + #M below (key, k); M element j to
+//                 j + #U below (key, idx), found by binary search over P and M's indices
+// Look-back words are 64-bit: (epoch << 32) | flag | count, with a fresh epoch for every
+// use, so a word left from an earlier use reads as unpublished and nothing is cleared.
+constexpr unsigned long long LB64_AGG = 1ull << 30;
+constexpr unsigned long long LB64_INC = 2ull << 30;
+constexpr unsigned long long LB64_VAL = (1ull << 30) - 1ull;
+constexpr int MCTL_CHUNK = 0, MCTL_M = 1, MCTL_PASS = 2;   // mctl word indices (+ pass)
+
+__device__ __forceinline__ unsigned long long ld_volatile64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_volatile64(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("st.volatile.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// decoupled look-back over 64-bit epoch words: publishes `run` for slot `my` of tile t (stride
+// between tiles `stride`), returns the exclusive prefix of the earlier tiles
+__device__ __forceinline__ uint32_t lookback64(unsigned long long* words, uint32_t t, size_t stride, uint32_t run,
+                                               uint32_t epoch, uint32_t* err)
+{
+    const unsigned long long tag = (unsigned long long)epoch << 32;
+    unsigned long long* my = words + (size_t)t * stride;
+    if (t == 0) {
+        st_volatile64(my, tag | LB64_INC | run);
+        return 0u;
+    }
+    st_volatile64(my, tag | LB64_AGG | run);
+    uint32_t excl = 0;
+    int64_t j = (int64_t)t - 1;
+    uint32_t spins = 0;
+    while (j >= 0) {
+        const unsigned long long v = ld_volatile64(words + (size_t)j * stride);
+        if ((v >> 32) != (unsigned long long)epoch) {
+            if (++spins > (1u << 22)) {   // bounded: a predecessor never published
+                atomicOr(err, APIC_ERRBIT_TIMEOUT);
+                break;
+            }
+            __nanosleep(32);
+            continue;
+        }
+        excl += (uint32_t)(v & LB64_VAL);
+        if ((v & ~(LB64_VAL | (0xffffffffull << 32))) == LB64_INC) break;
+        --j;
+    }
+    st_volatile64(my, tag | LB64_INC | (excl + run));
+    return excl;
+}
+
+__global__ void __launch_bounds__(RT) k_moved(const uint32_t* __restrict__ knext, const uint32_t* __restrict__ pk,
+                                              int64_t n, uint32_t* __restrict__ ctl, unsigned long long* lbs,
+                                              uint32_t epoch, uint32_t* __restrict__ mk, uint32_t* __restrict__ mv,
+                                              uint32_t* __restrict__ midx, uint32_t* __restrict__ choff,
+                                              uint32_t* __restrict__ mhist, int passes, uint32_t* err)
+{
+    __shared__ uint32_t wc[RI][RW];
+    __shared__ uint32_t h[4][256];
+    __shared__ uint32_t s_t, s_excl;
+    if (threadIdx.x == 0) s_t = atomicAdd(ctl + MCTL_CHUNK, 1u);
+    for (int i = threadIdx.x; i < 4 * 256; i += RT) (&h[0][0])[i] = 0u;
+    __syncthreads();
+    const uint32_t t = s_t;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = (int64_t)t * RTILE;
+    uint32_t key[RI];
+    unsigned bal[RI];
+#pragma unroll
+    for (int r = 0; r < RI; ++r) {
+        const int64_t k = base + r * RT + threadIdx.x;
+        const bool moved = k < n && knext[k] != pk[k];
+        key[r] = moved ? knext[k] : 0u;
+        bal[r] = __ballot_sync(FULL, moved);
+        if (lane == 0) wc[r][w] = (uint32_t)__popc(bal[r]);
+        if (moved)
+            for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(key[r] >> (8 * p)) & 255u], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int r = 0; r < RI; ++r)
+            for (int ww = 0; ww < RW; ++ww) {
+                const uint32_t c = wc[r][ww];
+                wc[r][ww] = run;
+                run += c;
+            }
+        const uint32_t excl = lookback64(lbs, t, 1, run, epoch, err);
+        s_excl = excl;
+        choff[t] = excl;
+        if ((int64_t)(t + 1) * RTILE >= n) ctl[MCTL_M] = excl + run;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RI; ++r) {
+        if (bal[r] & (1u << lane)) {
+            const int64_t k = base + r * RT + threadIdx.x;
+            const uint32_t p = s_excl + wc[r][w] + (uint32_t)__popc(bal[r] & lanemask_lt());
+            mk[p] = key[r];
+            mv[p] = (uint32_t)k;
+            midx[p] = (uint32_t)k;
+        }
+    }
+    for (int i = threadIdx.x; i < passes * 256; i += RT) {
+        const uint32_t c = (&h[0][0])[i];
+        if (c) atomicAdd(mhist + i, c);
+    }
+}
+
+__global__ void __launch_bounds__(RT) k_msort_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                   uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                   uint32_t* __restrict__ ctl, int pass, const uint32_t* __restrict__ hist,
+                                                   unsigned long long* lbs, uint32_t epoch, uint32_t* err)
+{
+    __shared__ uint32_t wc[RW][256];
+    __shared__ uint32_t goff[256];
+    __shared__ uint32_t dst0[256];
+    __shared__ uint32_t s_t;
+    const uint32_t m = ctl[MCTL_M];
+    const uint32_t nt = (m + RTILE - 1) / RTILE;
+    if (blockIdx.x >= nt) return;
+    {
+        uint32_t ex;
+        block_excl_scan(hist[threadIdx.x], ex);
+        dst0[threadIdx.x] = ex;
+    }
+    const int shift = 8 * pass;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_t = atomicAdd(ctl + MCTL_PASS + pass, 1u);
+        for (int i = threadIdx.x; i < RW * 256; i += RT) (&wc[0][0])[i] = 0u;
+        __syncthreads();
+        const uint32_t t = s_t;
+        if (t >= nt) break;
+        const int64_t base = (int64_t)t * RTILE + w * (RI * 32);
+        uint32_t key[RI], val[RI], lr[RI];
+        unsigned dig[RI];
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+            const int64_t idx = base + r * 32 + lane;
+            const bool valid = idx < (int64_t)m;
+            key[r] = valid ? kin[idx] : 0u;
+            val[r] = valid ? vin[idx] : 0u;
+            const unsigned d = valid ? (key[r] >> shift) & 255u : 256u;
+            dig[r] = d;
+            const unsigned peers = __match_any_sync(FULL, d);
+            const unsigned before = (unsigned)__popc(peers & lanemask_lt());
+            const uint32_t cnt = valid ? wc[w][d] : 0u;
+            __syncwarp();
+            lr[r] = cnt + before;
+            if (valid && lane == __ffs(peers) - 1) wc[w][d] = cnt + (uint32_t)__popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        {
+            const int d = threadIdx.x;
+            uint32_t run = 0;
+            for (int ww = 0; ww < RW; ++ww) {
+                const uint32_t c = wc[ww][d];
+                wc[ww][d] = run;
+                run += c;
+            }
+            goff[d] = dst0[d] + lookback64(lbs + d, t, 256, run, epoch, err);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+            const int64_t idx = base + r * 32 + lane;
+            if (idx < (int64_t)m) {
+                const unsigned d = dig[r];
+                const uint32_t pos = goff[d] + wc[w][d] + lr[r];
+                if (pos < m) {
+                    kout[pos] = key[r];
+                    vout[pos] = val[r];
+                } else {
+                    atomicOr(err, APIC_ERRBIT_RANGE);   // inconsistent counts: never write past m
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// number of (msk[j], msv[j]) in [lo, hi) below (key, idx); the sequence is sorted by (key, index)
+__device__ __forceinline__ uint32_t below_m(const uint32_t* msk, const uint32_t* msv, uint32_t lo, uint32_t hi,
+                                            uint32_t key, uint32_t idx)
+{
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        const uint32_t a = msk[mid];
+        if (a < key || (a == key && msv[mid] < idx)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(RT) k_merge(const uint32_t* __restrict__ knext, const uint32_t* __restrict__ pk,
+                                              int64_t n, const uint32_t* __restrict__ choff,
+                                              const uint32_t* __restrict__ msk, const uint32_t* __restrict__ msv,
+                                              const uint32_t* __restrict__ midx, const uint32_t* __restrict__ ctl,
+                                              int nchunks, uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                              uint32_t* err)
+{
+    const uint32_t m = ctl[MCTL_M];
+    if ((int)blockIdx.x < nchunks) {
+        __shared__ uint32_t wc[RI][RW];
+        __shared__ uint32_t s_lo, s_hi;
+        const uint32_t t = blockIdx.x;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        const int64_t base = (int64_t)t * RTILE;
+        const int64_t kl = (base + RTILE < n ? base + RTILE : n) - 1;
+        if (threadIdx.x == 0) {
+            s_lo = below_m(msk, msv, 0u, m, pk[base], (uint32_t)base);
+            s_hi = below_m(msk, msv, s_lo, m, pk[kl], (uint32_t)kl + 1u);
+        }
+        unsigned bal[RI];
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+            const int64_t k = base + r * RT + threadIdx.x;
+            const bool moved = k < n && knext[k] != pk[k];
+            bal[r] = __ballot_sync(FULL, moved);
+            if (lane == 0) wc[r][w] = (uint32_t)__popc(bal[r]);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t run = choff[t];
+            for (int r = 0; r < RI; ++r)
+                for (int ww = 0; ww < RW; ++ww) {
+                    const uint32_t c = wc[r][ww];
+                    wc[r][ww] = run;
+                    run += c;
+                }
+        }
+        __syncthreads();
+        const uint32_t lo = s_lo, hi = s_hi;
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+            const int64_t k = base + r * RT + threadIdx.x;
+            if (k < n && !(bal[r] & (1u << lane))) {
+                const uint32_t before = wc[r][w] + (uint32_t)__popc(bal[r] & lanemask_lt());
+                const uint32_t key = pk[k];
+                const uint32_t pos = (uint32_t)k - before + below_m(msk, msv, lo, hi, key, (uint32_t)k);
+                if (pos < (uint32_t)n) {
+                    kout[pos] = key;
+                    vout[pos] = (uint32_t)k;
+                } else {
+                    atomicOr(err, APIC_ERRBIT_RANGE);
+                }
+            }
+        }
+    } else {
+        const uint32_t stride = (gridDim.x - nchunks) * RT;
+        for (uint32_t j = (blockIdx.x - nchunks) * RT + threadIdx.x; j < m; j += stride) {
+            const uint32_t key = msk[j], idx = msv[j];
+            // K = #k with (P[k], k) below (key, idx)
+            uint32_t lo = 0, hi = (uint32_t)n;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                const uint32_t a = pk[mid];
+                if (a < key || (a == key && mid < idx)) lo = mid + 1;
+                else hi = mid;
+            }
+            const uint32_t K = lo;
+            // moved indices below K
+            uint32_t a = 0, b = m;
+            while (a < b) {
+                const uint32_t mid = (a + b) >> 1;
+                if (midx[mid] < K) a = mid + 1;
+                else b = mid;
+            }
+            const uint32_t pos = j + K - a;
+            if (pos < (uint32_t)n) {
+                kout[pos] = key;
+                vout[pos] = idx;
+            } else {
+                atomicOr(err, APIC_ERRBIT_RANGE);
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- batched forms
 // Work item -> simulation tables (rt_sim per radix tile, ch_sim per chunk) are built on the
 // host when membership changes.  Counts of all simulations sit in one array laid out
@@ -649,6 +942,31 @@ cudaError_t radix_sort(const Buffers& b, int64_t n, int key_bits, cudaStream_t s
     }
     *keys_out = const_cast<uint32_t*>(kin);
     *vals_out = const_cast<uint32_t*>(vin);
+    return cudaGetLastError();
+}
+
+cudaError_t resort(const Buffers& b, int64_t n, int key_bits, const uint32_t* pk, uint32_t* kout, uint32_t* vout,
+                   uint32_t* epoch, int sms, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int nchunks = radix_tiles(n);
+    const int passes = (key_bits + 7) / 8;
+    cudaError_t e;
+    if (*epoch == 0u || *epoch > 0xfffffff0u) {   // first use, or the epoch is about to wrap
+        e = cudaMemsetAsync(b.lbs, 0, sizeof(unsigned long long) * 256 * ((size_t)nchunks + 1), s);
+        if (e != cudaSuccess) return e;
+        *epoch = 1u;
+    }
+    e = cudaMemsetAsync(b.mctl, 0, kMsortCtlBytes, s);   // counters, m, digit counts
+    if (e != cudaSuccess) return e;
+    k_moved<<<nchunks, RT, 0, s>>>(b.knext, pk, n, b.mctl, b.lbs, (*epoch)++, b.mk[0], b.mv[0], b.midx, b.choff,
+                                   b.mhist, passes, b.err);
+    const int grid = nchunks < sms * 8 ? nchunks : sms * 8;
+    for (int p = 0; p < passes; ++p)
+        k_msort_pass<<<grid, RT, 0, s>>>(b.mk[p & 1], b.mv[p & 1], b.mk[(p + 1) & 1], b.mv[(p + 1) & 1], b.mctl, p,
+                                         b.mhist + 256 * p, b.lbs, (*epoch)++, b.err);
+    k_merge<<<nchunks + 2 * sms, RT, 0, s>>>(b.knext, pk, n, b.choff, b.mk[passes & 1], b.mv[passes & 1], b.midx,
+                                              b.mctl, nchunks, kout, vout, b.err);
     return cudaGetLastError();
 }
 

@@ -7,7 +7,8 @@ gravity, sticky walls, default tile and P2G kernel, as bench.py runs it):
   sampled node, so its values at those nodes are complete;
 - the grid update on the whole grid;
 - G2P on every particle, from the GPU's grid velocities;
-- the next step's keys, which G2P writes, against keys recomputed from the new positions
+- the next step's sort (keys written by G2P, sorted incrementally), bit-exact against the
+  stable sort of keys recomputed from the new positions
   (a particle that G2P skipped or wrote twice shows up here).
 The initial state is deformed and moving (random F, v, B) so every term is exercised."""
 import numpy as np
@@ -51,12 +52,12 @@ def run():
     out = sim.download()
     cell1, off1 = sim.download_positions()
     sim.p2g()                                   # sorts the keys written by G2P
-    keys1, _ = sim.keys()
+    keys1, perm1 = sim.keys()
     sim.close()
     oc = bench.oracle_config(w, sc)
     vol = sc.dx ** 3 / w["ppc"]
     return dict(sc=sc, oc=oc, vol=vol, mass=w["rho"] * vol, x0=x0, v0=v0, B0=B0, F0=F0, cell0=cell0, off0=off0,
-                keys=keys, perm=perm, m_g=m_g, p_g=p_g, m_v=m_v, vt=vt, out=out, cell1=cell1, off1=off1, keys1=keys1)
+                keys=keys, perm=perm, m_g=m_g, p_g=p_g, m_v=m_v, vt=vt, out=out, cell1=cell1, off1=off1, keys1=keys1, perm1=perm1)
 
 
 def test_fullsize_keys_and_sort_bit_exact(run):
@@ -110,6 +111,11 @@ def test_fullsize_g2p_every_particle(run):
     assert np.abs((gx - run["x0"][idx]) - disp_ref).max() <= bound
 
 
-def test_fullsize_next_keys_match_positions(run):
-    ref = oracle.keys(run["oc"], 4, run["cell1"], run["off1"])
-    np.testing.assert_array_equal(run["keys1"], np.sort(ref))
+def test_fullsize_next_sort_bit_exact(run):
+    # after G2P the particles are stored in the first step's sorted order, so the keys G2P
+    # wrote are, in storage order, the oracle's keys of particle perm[k] at k
+    by_id = oracle.keys(run["oc"], 4, run["cell1"], run["off1"])
+    knext = by_id[run["perm"].astype(np.int64)]
+    ref_perm = oracle.stable_sort(knext)
+    np.testing.assert_array_equal(run["keys1"], knext[ref_perm])
+    np.testing.assert_array_equal(run["perm1"].astype(np.int64), ref_perm)
