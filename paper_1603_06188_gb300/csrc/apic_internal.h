@@ -28,7 +28,8 @@ struct Buffers {
     uint32_t* mk[2]; uint32_t* mv[2];
     uint32_t* midx;
     uint32_t* choff;
-    uint32_t* mctl;              // [0] chunk counter, [1] moved count, [2..5] pass tile counters
+    uint32_t* mcnt;              // moved count per chunk
+    uint32_t* mctl;              // [1] moved count, [2..5] pass tile counters
     uint32_t* mhist;             // [4][256] digit counts of the moved keys (follows mctl)
     unsigned long long* lbs;     // 256 * (radix tiles + 1)
     uint32_t* scan_part;         // partial sums of the device scan

@@ -21,6 +21,9 @@ constexpr int RTILE = RT * RI;       // keys per radix tile
 constexpr int RW = RT / 32;          // warps per CTA
 constexpr int SCH = 4096;            // elements per scan chunk (256 threads x 16)
 constexpr unsigned FULL = 0xffffffffu;
+// up to this many chunks, a chunk's offset is a block reduction over the earlier chunks'
+// counts (one kernel); above it, a device-wide scan computes the offsets first
+constexpr int kReduceChunks = 4096;
 
 __device__ __forceinline__ unsigned lanemask_lt()
 {
@@ -253,17 +256,34 @@ __global__ void __launch_bounds__(256) k_tile_count(const uint32_t* __restrict__
 }
 
 __global__ void __launch_bounds__(256) k_tile_write(const uint32_t* __restrict__ skeys, int64_t n, int sh, int tile,
-                                                    const uint32_t* __restrict__ off, const uint32_t* __restrict__ ntiles,
+                                                    const uint32_t* __restrict__ off, uint32_t* __restrict__ ntiles,
                                                     int64_t max_tiles, uint32_t* __restrict__ tiles, int nchunks,
-                                                    uint32_t* __restrict__ err, uint32_t* __restrict__ tile_ctr)
+                                                    uint32_t* __restrict__ err, uint32_t* __restrict__ tile_ctr,
+                                                    const uint32_t* __restrict__ cnt)
 {
+    // with cnt given, off[] and ntiles are computed here: chunk t's offset is the sum of the
+    // counts of chunks 0..t-1 (a block reduction, used while the chunks are few)
+    __shared__ uint32_t s_off;
     if (blockIdx.x == 0 && threadIdx.x < 2) tile_ctr[threadIdx.x] = 0u;
+    if (cnt) {
+        uint32_t part = 0;
+        for (uint32_t i = threadIdx.x; i < blockIdx.x; i += 256) part += cnt[i];
+        uint32_t ex;
+        const uint32_t o = block_excl_scan(part, ex);
+        if (threadIdx.x == 0) {
+            s_off = o;
+            if ((int)blockIdx.x == nchunks - 1) *ntiles = o + cnt[blockIdx.x];
+        }
+    } else if (threadIdx.x == 0) {
+        s_off = off[blockIdx.x];
+    }
+    __syncthreads();
     const int64_t cs = (int64_t)blockIdx.x * tile;
-    write_heads(skeys, n, sh, tile, cs, off[blockIdx.x], [&](uint32_t pos, int64_t k) {
+    write_heads(skeys, n, sh, tile, cs, s_off, [&](uint32_t pos, int64_t k) {
         if ((int64_t)pos < max_tiles) tiles[pos] = (uint32_t)k;
     });
-    if (blockIdx.x == nchunks - 1 && threadIdx.x == 0) {
-        const uint32_t nt = *ntiles;
+    if ((int)blockIdx.x == nchunks - 1 && threadIdx.x == 0) {
+        const uint32_t nt = cnt ? s_off + cnt[blockIdx.x] : *ntiles;
         if ((int64_t)nt < max_tiles) tiles[nt] = (uint32_t)n;
         else atomicOr(err, APIC_ERRBIT_CAPACITY);
     }
@@ -415,8 +435,8 @@ __global__ void __launch_bounds__(RT) k_onesweep_pass(const uint32_t* __restrict
 // ones, M, are sorted -- stably, from index order, so by (key, k) -- and the two sorted
 // sequences are merged by (key, k): the result is the stable order of all keys, the same
 // permutation the full sort gives.
-//   k_moved       flags and compacts M in index order (chunk offsets by decoupled look-back),
-//                 counts M's digits for every pass, and stores m
+//   k_moved_count    counts M per chunk and M's digits for every pass
+//   k_moved_compact  compacts M in index order (chunk offsets by reduction) and stores m
 //   k_msort_pass  one LSD pass over M (m read on the device; tiles taken from a counter)
 //   k_merge       U element k goes to (k - #M before k) + #M below (key, k); M element j to
 //                 j + #U below (key, idx), found by binary search over P and M's indices
@@ -425,7 +445,7 @@ __global__ void __launch_bounds__(RT) k_onesweep_pass(const uint32_t* __restrict
 constexpr unsigned long long LB64_AGG = 1ull << 30;
 constexpr unsigned long long LB64_INC = 2ull << 30;
 constexpr unsigned long long LB64_VAL = (1ull << 30) - 1ull;
-constexpr int MCTL_CHUNK = 0, MCTL_M = 1, MCTL_PASS = 2;   // mctl word indices (+ pass)
+constexpr int MCTL_M = 1, MCTL_PASS = 2;   // mctl word indices (+ pass)
 
 __device__ __forceinline__ unsigned long long ld_volatile64(const unsigned long long* p)
 {
@@ -471,19 +491,59 @@ __device__ __forceinline__ uint32_t lookback64(unsigned long long* words, uint32
     return excl;
 }
 
-__global__ void __launch_bounds__(RT) k_moved(const uint32_t* __restrict__ knext, const uint32_t* __restrict__ pk,
-                                              int64_t n, uint32_t* __restrict__ ctl, unsigned long long* lbs,
-                                              uint32_t epoch, uint32_t* __restrict__ mk, uint32_t* __restrict__ mv,
-                                              uint32_t* __restrict__ midx, uint32_t* __restrict__ choff,
-                                              uint32_t* __restrict__ mhist, int passes, uint32_t* err)
+// moved keys of chunk t (RTILE consecutive indices, thread-major rounds): count per chunk and
+// the digit counts of every pass
+__global__ void __launch_bounds__(RT) k_moved_count(const uint32_t* __restrict__ knext, const uint32_t* __restrict__ pk,
+                                                    int64_t n, uint32_t* __restrict__ cnt, uint32_t* __restrict__ mhist,
+                                                    int passes)
 {
-    __shared__ uint32_t wc[RI][RW];
     __shared__ uint32_t h[4][256];
-    __shared__ uint32_t s_t, s_excl;
-    if (threadIdx.x == 0) s_t = atomicAdd(ctl + MCTL_CHUNK, 1u);
     for (int i = threadIdx.x; i < 4 * 256; i += RT) (&h[0][0])[i] = 0u;
     __syncthreads();
-    const uint32_t t = s_t;
+    const int64_t base = (int64_t)blockIdx.x * RTILE;
+    uint32_t c = 0;
+#pragma unroll
+    for (int r = 0; r < RI; ++r) {
+        const int64_t k = base + r * RT + threadIdx.x;
+        if (k < n) {
+            const uint32_t key = knext[k];
+            if (key != pk[k]) {
+                ++c;
+                for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(key >> (8 * p)) & 255u], 1u);
+            }
+        }
+    }
+    uint32_t ex;
+    const uint32_t total = block_excl_scan(c, ex);
+    if (threadIdx.x == 0) cnt[blockIdx.x] = total;
+    for (int i = threadIdx.x; i < passes * 256; i += RT) {
+        const uint32_t v = (&h[0][0])[i];
+        if (v) atomicAdd(mhist + i, v);
+    }
+}
+
+// compaction of the moved keys in index order; chunk t's offset is off[t] (a device scan) or,
+// with off null, the sum of the counts of chunks 0..t-1 (a block reduction, used while the
+// chunks are few), the last chunk stores m
+__global__ void __launch_bounds__(RT) k_moved_compact(const uint32_t* __restrict__ knext, const uint32_t* __restrict__ pk,
+                                                      int64_t n, const uint32_t* __restrict__ cnt,
+                                                      const uint32_t* __restrict__ off, int nchunks,
+                                                      uint32_t* __restrict__ ctl, uint32_t* __restrict__ mk,
+                                                      uint32_t* __restrict__ mv, uint32_t* __restrict__ midx,
+                                                      uint32_t* __restrict__ choff)
+{
+    __shared__ uint32_t wc[RI][RW];
+    __shared__ uint32_t s_excl;
+    const uint32_t t = blockIdx.x;
+    uint32_t excl;
+    if (off) {
+        excl = off[t];
+    } else {
+        uint32_t part = 0;
+        for (uint32_t i = threadIdx.x; i < t; i += RT) part += cnt[i];
+        uint32_t ex;
+        excl = block_excl_scan(part, ex);
+    }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t base = (int64_t)t * RTILE;
     uint32_t key[RI];
@@ -495,37 +555,29 @@ __global__ void __launch_bounds__(RT) k_moved(const uint32_t* __restrict__ knext
         key[r] = moved ? knext[k] : 0u;
         bal[r] = __ballot_sync(FULL, moved);
         if (lane == 0) wc[r][w] = (uint32_t)__popc(bal[r]);
-        if (moved)
-            for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(key[r] >> (8 * p)) & 255u], 1u);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t run = 0;
+        uint32_t run = excl;
         for (int r = 0; r < RI; ++r)
             for (int ww = 0; ww < RW; ++ww) {
                 const uint32_t c = wc[r][ww];
                 wc[r][ww] = run;
                 run += c;
             }
-        const uint32_t excl = lookback64(lbs, t, 1, run, epoch, err);
-        s_excl = excl;
         choff[t] = excl;
-        if ((int64_t)(t + 1) * RTILE >= n) ctl[MCTL_M] = excl + run;
+        if ((int)t == nchunks - 1) ctl[MCTL_M] = run;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < RI; ++r) {
         if (bal[r] & (1u << lane)) {
             const int64_t k = base + r * RT + threadIdx.x;
-            const uint32_t p = s_excl + wc[r][w] + (uint32_t)__popc(bal[r] & lanemask_lt());
+            const uint32_t p = wc[r][w] + (uint32_t)__popc(bal[r] & lanemask_lt());
             mk[p] = key[r];
             mv[p] = (uint32_t)k;
             midx[p] = (uint32_t)k;
         }
-    }
-    for (int i = threadIdx.x; i < passes * 256; i += RT) {
-        const uint32_t c = (&h[0][0])[i];
-        if (c) atomicAdd(mhist + i, c);
     }
 }
 
@@ -959,8 +1011,15 @@ cudaError_t resort(const Buffers& b, int64_t n, int key_bits, const uint32_t* pk
     }
     e = cudaMemsetAsync(b.mctl, 0, kMsortCtlBytes, s);   // counters, m, digit counts
     if (e != cudaSuccess) return e;
-    k_moved<<<nchunks, RT, 0, s>>>(b.knext, pk, n, b.mctl, b.lbs, (*epoch)++, b.mk[0], b.mv[0], b.midx, b.choff,
-                                   b.mhist, passes, b.err);
+    k_moved_count<<<nchunks, RT, 0, s>>>(b.knext, pk, n, b.mcnt, b.mhist, passes);
+    const uint32_t* off = nullptr;
+    if (nchunks > kReduceChunks) {   // many chunks: offsets by the device scan instead
+        e = exclusive_scan(b.mcnt, b.choff, nchunks, b.scan_part, nullptr, s);
+        if (e != cudaSuccess) return e;
+        off = b.choff;
+    }
+    k_moved_compact<<<nchunks, RT, 0, s>>>(b.knext, pk, n, b.mcnt, off, nchunks, b.mctl, b.mk[0], b.mv[0], b.midx,
+                                           b.choff);
     const int grid = nchunks < sms * 8 ? nchunks : sms * 8;
     for (int p = 0; p < passes; ++p)
         k_msort_pass<<<grid, RT, 0, s>>>(b.mk[p & 1], b.mv[p & 1], b.mk[(p + 1) & 1], b.mv[(p + 1) & 1], b.mctl, p,
@@ -1007,10 +1066,15 @@ cudaError_t build_tiles(const Buffers& b, const uint32_t* skeys, int64_t n, int 
     const int64_t nchunks = (n + tile - 1) / tile;
     const int sh = 2 * dim;
     k_tile_count<<<(unsigned)nchunks, 256, 0, s>>>(skeys, n, sh, tile, b.chunk_cnt);
+    if (nchunks <= kReduceChunks) {
+        k_tile_write<<<(unsigned)nchunks, 256, 0, s>>>(skeys, n, sh, tile, nullptr, b.ntiles, max_tiles, b.tiles,
+                                                       (int)nchunks, b.err, b.tile_ctr, b.chunk_cnt);
+        return cudaGetLastError();
+    }
     cudaError_t e = exclusive_scan(b.chunk_cnt, b.chunk_cnt, nchunks, b.scan_part, b.ntiles, s);
     if (e != cudaSuccess) return e;
     k_tile_write<<<(unsigned)nchunks, 256, 0, s>>>(skeys, n, sh, tile, b.chunk_cnt, b.ntiles, max_tiles, b.tiles,
-                                                   (int)nchunks, b.err, b.tile_ctr);
+                                                   (int)nchunks, b.err, b.tile_ctr, nullptr);
     return cudaGetLastError();
 }
 

@@ -569,53 +569,68 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
 #pragma unroll
                     for (int i = 0; i < D * D; ++i) T[i] = R(0);
                 }
+                // The weights are tensor products, so the contributions separate axis by axis
+                // (r = node - fx in grid units, T = dt/dx tau, mC = m B D^{-1} dx):
+                //   dp_c(i,j,k) = w0_i P_c(j,k) + E_c(i) S(j,k),       mass = w0_i m S(j,k)
+                //   P_c(j,k) = w1_j Q_c(k) + H_c(j) w2_k,              S(j,k) = w1_j w2_k
+                //   Q_c(k) = m v_c w2_k + mC_c2 (r w)2_k - T_c2 dw2_k
+                //   H_c(j) = mC_c1 (r w)1_j - T_c1 dw1_j,  E_c(i) = mC_c0 (r w)0_i - T_c0 dw0_i
+                // which is w m (v + C (x_i - x_p)) - dt tau grad w summed in fewer operations.
                 if (D == 3) {
+                    R E[3][K], H[3][K];
 #pragma unroll
-                    for (int ia = 0; ia < K; ++ia)
+                    for (int i = 0; i < K; ++i) {
+                        const R rw0 = (R(i) - fx[0]) * w[0][i], rw1 = (R(i) - fx[1]) * w[1][i];
+#pragma unroll
+                        for (int cc = 0; cc < 3; ++cc) {
+                            E[cc][i] = mC[cc * 3 + 0] * rw0 - T[cc * 3 + 0] * dw[0][i];
+                            H[cc][i] = mC[cc * 3 + 1] * rw1 - T[cc * 3 + 1] * dw[1][i];
+                        }
+                    }
+#pragma unroll
+                    for (int icl = 0; icl < KZ; ++icl) {
+                        const int ic = slab * KZ + icl;
+                        const R w2 = w[2][ic], dw2 = dw[2][ic], rw2 = (R(ic) - fx[2]) * w2;
+                        R Q[3];
+#pragma unroll
+                        for (int cc = 0; cc < 3; ++cc) Q[cc] = mv[cc] * w2 + mC[cc * 3 + 2] * rw2 - T[cc * 3 + 2] * dw2;
 #pragma unroll
                         for (int ib = 0; ib < K; ++ib) {
-                            const R wab = w[0][ia] * w[1][ib];
-                            const R gx = dw[0][ia] * w[1][ib], gy = w[0][ia] * dw[1][ib];
-                            const R r0 = R(ia) - fx[0], r1 = R(ib) - fx[1];
-                            R qab[3], h[3], kz[3];
+                            const R S = w[1][ib] * w2, mS = ml * S;
+                            R P[3];
 #pragma unroll
-                            for (int a = 0; a < 3; ++a) {
-                                qab[a] = mv[a] + mC[a * 3 + 0] * r0 + mC[a * 3 + 1] * r1;
-                                h[a] = T[a * 3 + 0] * gx + T[a * 3 + 1] * gy;
-                                kz[a] = T[a * 3 + 2] * wab;
-                            }
+                            for (int cc = 0; cc < 3; ++cc) P[cc] = w[1][ib] * Q[cc] + H[cc][ib] * w2;
 #pragma unroll
-                            for (int icl = 0; icl < KZ; ++icl) {
-                                const int ic = slab * KZ + icl;
-                                const R wz = (ZS == 1) ? w[2][icl] : (slab ? w[2][KZ + icl] : w[2][icl]);
-                                const R dwz = (ZS == 1) ? dw[2][icl] : (slab ? dw[2][KZ + icl] : dw[2][icl]);
-                                const R r2 = R(ic) - fx[2];
-                                const R wv = wab * wz;
+                            for (int ia = 0; ia < K; ++ia) {
                                 const int j = ia + K * ib + K * K * icl;
 #pragma unroll
-                                for (int a = 0; a < 3; ++a) {
-                                    const R qv = qab[a] + mC[a * 3 + 2] * r2;
-                                    cur[j * NV + a] += wv * qv - h[a] * wz - kz[a] * dwz;
-                                }
-                                cur[j * NV + 3] += wv * ml;
+                                for (int cc = 0; cc < 3; ++cc) cur[j * NV + cc] += w[0][ia] * P[cc] + E[cc][ia] * S;
+                                cur[j * NV + 3] += w[0][ia] * mS;
                             }
                         }
+                    }
                 } else {
+                    R E[2][K];
 #pragma unroll
-                    for (int ia = 0; ia < K; ++ia)
+                    for (int i = 0; i < K; ++i) {
+                        const R rw0 = (R(i) - fx[0]) * w[0][i];
 #pragma unroll
-                        for (int ib = 0; ib < K; ++ib) {
-                            const R wv = w[0][ia] * w[1][ib];
-                            const R g0 = dw[0][ia] * w[1][ib], g1 = w[0][ia] * dw[1][ib];
-                            const R r0 = R(ia) - fx[0], r1 = R(ib) - fx[1];
+                        for (int cc = 0; cc < 2; ++cc) E[cc][i] = mC[cc * 2 + 0] * rw0 - T[cc * 2 + 0] * dw[0][i];
+                    }
+#pragma unroll
+                    for (int ib = 0; ib < K; ++ib) {
+                        const R w1 = w[1][ib], rw1 = (R(ib) - fx[1]) * w1, mw1 = ml * w1;
+                        R Q[2];
+#pragma unroll
+                        for (int cc = 0; cc < 2; ++cc) Q[cc] = mv[cc] * w1 + mC[cc * 2 + 1] * rw1 - T[cc * 2 + 1] * dw[1][ib];
+#pragma unroll
+                        for (int ia = 0; ia < K; ++ia) {
                             const int j = ia + K * ib;
 #pragma unroll
-                            for (int a = 0; a < 2; ++a) {
-                                const R qv = mv[a] + mC[a * 2 + 0] * r0 + mC[a * 2 + 1] * r1;
-                                cur[j * NV + a] += wv * qv - (T[a * 2 + 0] * g0 + T[a * 2 + 1] * g1);
-                            }
-                            cur[j * NV + 2] += wv * ml;
+                            for (int cc = 0; cc < 2; ++cc) cur[j * NV + cc] += w[0][ia] * Q[cc] + E[cc][ia] * w1;
+                            cur[j * NV + 2] += w[0][ia] * mw1;
                         }
+                    }
                 }
             }
             cp_async_wait<0>();
