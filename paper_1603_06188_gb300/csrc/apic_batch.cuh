@@ -185,12 +185,19 @@ template <typename R> struct BatchImpl {
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(g2p_per_sm, kb_g2p<D, O, R>, TPB, 0);
         return e;
     }
+    // lane groups of 2, 4 or 8 per base cell (fewer lanes suit fewer particles per cell)
+    template <int D, int O> static cudaError_t setup_dg(int group, int* p, int* g)
+    {
+        if (group == 8) return setup_one<D, O, 8>(p, g);
+        if (group == 2) return setup_one<D, O, 2>(p, g);
+        return setup_one<D, O, 4>(p, g);
+    }
     static cudaError_t setup(int dim, int order, int group, int* p2g_per_sm, int* g2p_per_sm)
     {
-        if (dim == 3 && order == 2) return group == 8 ? setup_one<3, 2, 8>(p2g_per_sm, g2p_per_sm) : setup_one<3, 2, 4>(p2g_per_sm, g2p_per_sm);
-        if (dim == 2 && order == 2) return group == 8 ? setup_one<2, 2, 8>(p2g_per_sm, g2p_per_sm) : setup_one<2, 2, 4>(p2g_per_sm, g2p_per_sm);
-        if (dim == 2 && order == 3) return group == 8 ? setup_one<2, 3, 8>(p2g_per_sm, g2p_per_sm) : setup_one<2, 3, 4>(p2g_per_sm, g2p_per_sm);
-        if (dim == 3 && order == 3) return group == 8 ? setup_one<3, 3, 8>(p2g_per_sm, g2p_per_sm) : setup_one<3, 3, 4>(p2g_per_sm, g2p_per_sm);
+        if (dim == 3 && order == 2) return setup_dg<3, 2>(group, p2g_per_sm, g2p_per_sm);
+        if (dim == 2 && order == 2) return setup_dg<2, 2>(group, p2g_per_sm, g2p_per_sm);
+        if (dim == 2 && order == 3) return setup_dg<2, 3>(group, p2g_per_sm, g2p_per_sm);
+        if (dim == 3 && order == 3) return setup_dg<3, 3>(group, p2g_per_sm, g2p_per_sm);
         return cudaErrorInvalidValue;
     }
     template <int D, int O, int G>
@@ -199,13 +206,21 @@ template <typename R> struct BatchImpl {
     {
         kb_p2g_cells<D, O, R, G><<<grid, 128, p2g_cells_smem<D, O, R>(), s>>>((SimDesc<R>*)descs, ts, tst, nt, ctr, kpar);
     }
+    template <int D, int O>
+    static void p2g_dg(int group, void* descs, const uint32_t* ts, const uint32_t* tst, const uint32_t* nt,
+                       uint32_t* ctr, int kpar, int grid, cudaStream_t s)
+    {
+        if (group == 8) p2g_one<D, O, 8>(descs, ts, tst, nt, ctr, kpar, grid, s);
+        else if (group == 2) p2g_one<D, O, 2>(descs, ts, tst, nt, ctr, kpar, grid, s);
+        else p2g_one<D, O, 4>(descs, ts, tst, nt, ctr, kpar, grid, s);
+    }
     static cudaError_t p2g(int dim, int order, int group, void* descs, const uint32_t* ts, const uint32_t* tst,
                            const uint32_t* nt, uint32_t* ctr, int kpar, int grid, cudaStream_t s)
     {
-        if (dim == 3 && order == 2) { if (group == 8) p2g_one<3, 2, 8>(descs, ts, tst, nt, ctr, kpar, grid, s); else p2g_one<3, 2, 4>(descs, ts, tst, nt, ctr, kpar, grid, s); }
-        else if (dim == 2 && order == 2) { if (group == 8) p2g_one<2, 2, 8>(descs, ts, tst, nt, ctr, kpar, grid, s); else p2g_one<2, 2, 4>(descs, ts, tst, nt, ctr, kpar, grid, s); }
-        else if (dim == 2 && order == 3) { if (group == 8) p2g_one<2, 3, 8>(descs, ts, tst, nt, ctr, kpar, grid, s); else p2g_one<2, 3, 4>(descs, ts, tst, nt, ctr, kpar, grid, s); }
-        else if (dim == 3 && order == 3) { if (group == 8) p2g_one<3, 3, 8>(descs, ts, tst, nt, ctr, kpar, grid, s); else p2g_one<3, 3, 4>(descs, ts, tst, nt, ctr, kpar, grid, s); }
+        if (dim == 3 && order == 2) p2g_dg<3, 2>(group, descs, ts, tst, nt, ctr, kpar, grid, s);
+        else if (dim == 2 && order == 2) p2g_dg<2, 2>(group, descs, ts, tst, nt, ctr, kpar, grid, s);
+        else if (dim == 2 && order == 3) p2g_dg<2, 3>(group, descs, ts, tst, nt, ctr, kpar, grid, s);
+        else if (dim == 3 && order == 3) p2g_dg<3, 3>(group, descs, ts, tst, nt, ctr, kpar, grid, s);
         else return cudaErrorInvalidValue;
         return cudaGetLastError();
     }

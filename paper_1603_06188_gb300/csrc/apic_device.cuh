@@ -437,9 +437,9 @@ __device__ __forceinline__ bool polar_newton3(const R* F, R* Rot)
 // as its independent entries (3-D: t00 t11 t22 t01 t02 t12; 2-D: t00 t11 t01).
 // Fixed-corotated: P = 2 mu (F - R) + lam (J - 1) J F^{-T}
 //   =>  P F^T = 2 mu (F - R) F^T + lam (J - 1) J I, off-diagonal entries symmetrised.
-// FP32: the rotation is recomputed in FP64 when the FP32 one fails its residual check
-// (nearly coincident singular values of F at FP32 resolution, or near-singular F); each
-// fallback is counted.
+// FP32: a rotation from the Jacobi route is recomputed in FP64 when it fails its residual
+// check (nearly coincident singular values of F at FP32 resolution, or near-singular F);
+// each fallback is counted.
 template <int D, typename R>
 __device__ __forceinline__ void stress_sym_fcr(const R* F, R mu, R lam, R vol, R* t, unsigned* fallbacks)
 {
@@ -453,9 +453,11 @@ __device__ __forceinline__ void stress_sym_fcr(const R* F, R mu, R lam, R vol, R
         Rot[0] = c; Rot[1] = -s; Rot[2] = s; Rot[3] = c;
         J = F[0] * F[3] - F[1] * F[2];
     } else {
-        if (!polar_newton3<R>(F, Rot)) polar3<R>(F, Rot);
-        if (sizeof(R) == 4) {
-            if (polar_residual<R>(F, Rot) > R(2e-5)) {
+        // a converged Newton iterate is the orthogonal polar factor to working precision; the
+        // Jacobi route (det F <= 0, or no convergence) is checked and redone in FP64 if needed
+        if (!polar_newton3<R>(F, Rot)) {
+            polar3<R>(F, Rot);
+            if (sizeof(R) == 4 && polar_residual<R>(F, Rot) > R(2e-5)) {
                 double Fd[9], Rd[9];
                 for (int i = 0; i < 9; ++i) Fd[i] = (double)F[i];
                 polar3<double>(Fd, Rd);

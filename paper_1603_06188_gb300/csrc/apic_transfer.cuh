@@ -1072,6 +1072,19 @@ __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>
         for (int a = 0; a < D; ++a) vp[a] = R(0);
 #pragma unroll
         for (int i = 0; i < D * D; ++i) { Bh[i] = R(0); G[i] = R(0); }
+        // node (i, j, k) of the stencil sits in staged block qb = (L0>>2) | (L1>>2)<<1 | (L2>>2)<<2
+        // at in-block index (L0&3) | (L1&3)<<2 | (L2&3)<<4 (L = lb + stencil index); its offset
+        // in the staging buffer is a sum of per-axis terms, taken once per particle
+        constexpr int BNN = (D == 3) ? 64 : 16;
+        int ox[D][K];
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const int L = lb[a] + i;
+                ox[a][i] = 4 * ((L >> 2) * (BNN << a) + (L & 3) * (1 << (2 * a)));
+            }
+        const R* svf = &sv[0][0][0];
         R rw[D][K];   // (node - fx) * w per axis
 #pragma unroll
         for (int a = 0; a < D; ++a)
@@ -1084,15 +1097,12 @@ __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>
             for (int a = 0; a < D; ++a) { Ra[a] = Sa[a] = Ta[a] = Ya[a] = Za[a] = R(0); }
 #pragma unroll
             for (int ib = 0; ib < K; ++ib) {
-                const int L0 = lb[0] + ia, L1 = lb[1] + ib;
+                const int o01 = ox[0][ia] + ox[1][ib];
                 if (D == 3) {
                     R P[3] = {R(0), R(0), R(0)}, Q[3] = {R(0), R(0), R(0)}, Z[3] = {R(0), R(0), R(0)};
 #pragma unroll
                     for (int ic = 0; ic < K; ++ic) {
-                        const int L2 = lb[2] + ic;
-                        const int qb = (L0 >> 2) | ((L1 >> 2) << 1) | ((L2 >> 2) << 2);
-                        const int ni = (L0 & 3) | ((L1 & 3) << 2) | ((L2 & 3) << 4);
-                        const V4<R> nv = *reinterpret_cast<const V4<R>*>(&sv[qb][ni][0]);
+                        const V4<R> nv = *reinterpret_cast<const V4<R>*>(svf + o01 + ox[D - 1][ic]);
                         const R vt[3] = {nv.x, nv.y, nv.z};
 #pragma unroll
                         for (int a = 0; a < 3; ++a) {
@@ -1110,9 +1120,7 @@ __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>
                         Za[a] += w[1][ib] * Z[a];
                     }
                 } else {
-                    const int qb = (L0 >> 2) | ((L1 >> 2) << 1);
-                    const int ni = (L0 & 3) | ((L1 & 3) << 2);
-                    const V4<R> nv = *reinterpret_cast<const V4<R>*>(&sv[qb][ni][0]);
+                    const V4<R> nv = *reinterpret_cast<const V4<R>*>(svf + o01);
                     const R vt[2] = {nv.x, nv.y};
 #pragma unroll
                     for (int a = 0; a < 2; ++a) {
