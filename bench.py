@@ -51,13 +51,16 @@ WORKLOADS = {
 
 # algorithmic bytes (FP32): per particle and per active grid node, for each single-kernel phase
 ALGO_BYTES = {
-    # P2G reads x (3 offsets + cell), v, B, F = 16 + 12 + 36 + 36 B; writes m and momentum per node
-    "p2g": (100, 16),
+    # P2G reads x (3 offsets + cell: 16), v and B (48), the symmetric stress tau (24) = 88 B;
+    # adds m and momentum into each active node (16 B)
+    "p2g": (88, 16),
     # grid update reads (m, momentum), writes (v~, m) and clears the accumulator
     "grid_update": (0, 48),
-    # G2P reads x + F (52 B), writes x, v, B, F (100 B); reads v~ per node
-    "g2p": (152, 16),
+    # G2P reads x + F + id (56 B), writes x, v, B, F + id and tau (128 B); reads v~ per node
+    "g2p": (184, 16),
 }
+# the whole step adds the keys G2P writes and the sort reads (8 B per particle)
+STEP_BYTES = (sum(b for b, _ in ALGO_BYTES.values()) + 8, sum(n for _, n in ALGO_BYTES.values()))
 KERNEL_OF_PHASE = {"p2g": "k_p2g_cells", "grid_update": "k_grid_update", "g2p": "k_g2p"}
 
 
@@ -402,7 +405,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ppc", type=int, default=None)
     ap.add_argument("--ref-particles", type=int, default=0)
-    ap.add_argument("--cpu-sample", type=int, default=300000)
+    ap.add_argument("--cpu-sample", type=int, default=2500000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--p2g-kernel", type=int, default=0)
@@ -492,6 +495,10 @@ def main():
             "unit": "GB/s", "frac": per_phase[dom]["gbs"] / peak, "traffic": traffic,
             "peak_source": f"{peak_kind} hbm_gbs",
             "algorithmic_bytes_per_launch": per_phase[dom]["algorithmic_bytes"]}
+    step_bytes = STEP_BYTES[0] * sc.n + STEP_BYTES[1] * active_nodes
+    step_gbs = step_bytes / (max_ms / args.steps * 1e-3) / 1e9
+    step_roof = {"bytes_per_step": step_bytes, "achieved": step_gbs, "peak": peak, "unit": "GB/s",
+                 "frac": step_gbs / peak, "per_particle_bytes": STEP_BYTES[0], "per_active_node_bytes": STEP_BYTES[1]}
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -536,6 +543,7 @@ def main():
                        "l2": f"inputs larger than L2: particle state {sc.n * 100 / 1e6:.0f} MB per copy",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof,
+            "step_roofline": step_roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
