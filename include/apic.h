@@ -83,8 +83,9 @@ typedef struct {
     int tile_particles;      /* particles per P2G / G2P tile (power of two, 256..4096);
                                 0 = default */
     int p2g_kernel;          /* P2G variant: 0 = default (2), 1 = warp-segmented reduction,
-                                2 = cell-parallel, 3 = cell-interleaved; results agree to
-                                rounding */
+                                2 = cell-parallel, 3 = cell-interleaved, 4 = node-split
+                                (the lanes of a group share the particles and split the
+                                stencil nodes); results agree to rounding */
 } apic_config;
 
 /* Bytes of device workspace a simulation with this config and capacity needs.

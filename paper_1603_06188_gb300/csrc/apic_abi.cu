@@ -104,7 +104,7 @@ apic_status fill_cfg(const apic_config* in, int64_t max_particles, HostCfg* c, s
     c->mass = in->particle_mass;
     c->vol = in->particle_volume;
     c->tile = tile;
-    if (in->p2g_kernel < 0 || in->p2g_kernel > 3) { *why = "p2g_kernel must be 0, 1, 2 or 3"; return APIC_ERR_ARG; }
+    if (in->p2g_kernel < 0 || in->p2g_kernel > 4) { *why = "p2g_kernel must be 0..4"; return APIC_ERR_ARG; }
     c->p2g_kernel = in->p2g_kernel != 0 ? in->p2g_kernel : 2;   // default: cell-parallel
     c->key_bits = 2 * in->dim + ceil_log2(c->nblocks);
     if (c->key_bits > 32) { *why = "grid too large for 32-bit cell keys"; return APIC_ERR_UNSUPPORTED; }

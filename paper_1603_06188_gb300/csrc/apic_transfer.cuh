@@ -446,6 +446,79 @@ template <typename R, int N> struct ReduceScatter<R, N, 1> {
 // stored (plain stores, no atomics) as that cell's stencil sums; then every tile node
 // gathers, in a fixed order, the sums of the cells whose stencils cover it, and adds the
 // result to the global grid.  Contributions as in k_p2g.
+// runs of equal base cell inside a tile (sorted keys of one node block): cbeg / cend per
+// in-block cell (whole CTA of nt threads; the caller synchronises afterwards)
+template <int D>
+__device__ __forceinline__ void tile_cell_runs(const uint32_t* __restrict__ skeys, uint32_t start, uint32_t end,
+                                               uint32_t* cbeg, uint32_t* cend, int nt)
+{
+    constexpr int NC = (D == 3) ? 64 : 16;
+    for (uint32_t k = start + threadIdx.x; k < end; k += nt) {
+        const uint32_t cl = skeys[k] & (NC - 1);
+        if (k == start || (skeys[k - 1] & (NC - 1)) != cl) cbeg[cl] = k;
+        if (k + 1 == end || (skeys[k + 1] & (NC - 1)) != cl) cend[cl] = k + 1;
+    }
+}
+
+// The tile's nodes from the per-cell stencil sums cellsum[cell][node j][lane v]: node n
+// collects, in a fixed order, the sums of the cells n - (a, b, c) whose stencils cover it,
+// and adds them to the global grid once; then the 2^D node blocks the tile reaches are
+// flagged active.  Whole CTA of nt threads, after a barrier that follows the sums.
+template <int D, int ORDER, typename R>
+__device__ __forceinline__ void tile_flush(const R* cellsum, const uint32_t* cbeg, const uint32_t* cend, const int* bo,
+                                           uint32_t blk, R* __restrict__ acc, uint32_t* __restrict__ flags,
+                                           const DevCfg<R>& c, int nt)
+{
+    constexpr int K = ORDER + 1;
+    constexpr int TE = 4 + ORDER;
+    constexpr int TN = (D == 3) ? TE * TE * TE : TE * TE;
+    constexpr int NS = (D == 3) ? K * K * K : K * K;
+    constexpr int NV = D + 1;
+    constexpr int NVAL = NS * NV;
+        for (int i = threadIdx.x; i < TN; i += nt) {
+            const int n0 = i % TE, n1 = (i / TE) % TE, n2 = (D == 3) ? i / (TE * TE) : 0;
+            R sum[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) sum[v] = R(0);
+#pragma unroll
+            for (int j = 0; j < NS; ++j) {
+                const int ia = j % K, ib = (j / K) % K, ic = j / (K * K);
+                const int c0 = n0 - ia, c1 = n1 - ib, c2 = (D == 3) ? n2 - ic : 0;
+                if (c0 < 0 || c0 > 3 || c1 < 0 || c1 > 3 || c2 < 0 || c2 > 3) continue;
+                const int cl = c0 | (c1 << 2) | (c2 << 4);
+                if (cbeg[cl] >= cend[cl]) continue;
+                const R* src = cellsum + (size_t)cl * NVAL + j * NV;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) sum[v] += src[v];
+            }
+            if (sum[D] == R(0)) continue;
+            int g[3];
+            g[0] = bo[0] + n0;
+            g[1] = bo[1] + n1;
+            g[2] = bo[2] + n2;
+            const uint32_t ni = node_index<D>(g, c.nb);
+            R* gdst = acc + 4 * (size_t)ni;
+#pragma unroll
+            for (int a = 0; a < D; ++a) atomicAdd(gdst + a, sum[a]);
+            atomicAdd(gdst + 3, sum[D]);
+        }
+        if (threadIdx.x < (1 << D)) {
+            int bb[3];
+            block_coords<D, R>(blk, c, bb);
+            bool in = true;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                bb[a] += (threadIdx.x >> a) & 1;
+                if (bb[a] >= c.nb[a]) in = false;
+            }
+            if (in) {
+                const uint32_t b2 = (D == 3) ? ((uint32_t)bb[2] * c.nb[1] + bb[1]) * c.nb[0] + bb[0]
+                                             : (uint32_t)bb[1] * c.nb[0] + bb[0];
+                flags[b2] = 1u;
+            }
+        }
+}
+
 // One tile of the cell-parallel P2G (whole CTA, NT = 128 threads).  On entry the CTA is
 // converged; cbeg / cend hold zeros and *s_cell = 0 (set by the caller before its last
 // barrier).  Leaves the smem free for the next tile after its final barrier.
@@ -479,12 +552,7 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
     block_coords<D, R>(blk, c, bo);
 #pragma unroll
     for (int a = 0; a < D; ++a) bo[a] *= 4;
-        // runs of equal base cell inside the tile
-        for (uint32_t k = start + threadIdx.x; k < end; k += NT) {
-            const uint32_t cl = skeys[k] & (NC - 1);
-            if (k == start || (skeys[k - 1] & (NC - 1)) != cl) cbeg[cl] = k;
-            if (k + 1 == end || (skeys[k + 1] & (NC - 1)) != cl) cend[cl] = k + 1;
-        }
+        tile_cell_runs<D>(skeys, start, end, cbeg, cend, NT);
         __syncthreads();
         // A warp takes GPW cells at once (one per lane group) and runs a warp-uniform number
         // of iterations -- the longest run among them -- so all lanes follow one instruction
@@ -519,6 +587,13 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
                 if (kk < ke) stage_particle<D, R>(pslots + (size_t)(i * NT + threadIdx.x) * SW, st, perm[kk], with_tau);
                 cp_async_commit();
             }
+            // the permutation entry of the particle staged next is read one iteration early,
+            // so the copy's address is ready when the copy is issued
+            uint32_t qn = 0u;
+            {
+                const uint32_t kn = kb + lig + (uint32_t)(NSL * G);
+                if (kn < ke) qn = perm[kn];
+            }
 #pragma unroll 1
             for (uint32_t it = 0; it < iters; ++it) {
                 const uint32_t k = kb + lig + it * G;
@@ -529,8 +604,10 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
                 read_staged<D, R>(slot, p, with_tau);
                 {
                     const uint32_t kn = k + (uint32_t)(NSL * G);
-                    if (kn < ke) stage_particle<D, R>(slot, st, perm[kn], with_tau);
+                    if (kn < ke) stage_particle<D, R>(slot, st, qn, with_tau);
                     cp_async_commit();
+                    const uint32_t kq = kn + (uint32_t)G;
+                    if (kq < ke) qn = perm[kq];
                 }
                 if (!live) {   // neutral: an in-cell position and zero state (finite weights, zero sums)
 #pragma unroll
@@ -646,49 +723,7 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
             }   // slab
         }
         __syncthreads();
-        // gather: node n of the tile collects the stencil sums of cells n - (a, b, c)
-        for (int i = threadIdx.x; i < TN; i += NT) {
-            const int n0 = i % TE, n1 = (i / TE) % TE, n2 = (D == 3) ? i / (TE * TE) : 0;
-            R sum[NV];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) sum[v] = R(0);
-#pragma unroll
-            for (int j = 0; j < NS; ++j) {
-                const int ia = j % K, ib = (j / K) % K, ic = j / (K * K);
-                const int c0 = n0 - ia, c1 = n1 - ib, c2 = (D == 3) ? n2 - ic : 0;
-                if (c0 < 0 || c0 > 3 || c1 < 0 || c1 > 3 || c2 < 0 || c2 > 3) continue;
-                const int cl = c0 | (c1 << 2) | (c2 << 4);
-                if (cbeg[cl] >= cend[cl]) continue;
-                const R* src = cellsum + (size_t)cl * NVAL + j * NV;
-#pragma unroll
-                for (int v = 0; v < NV; ++v) sum[v] += src[v];
-            }
-            if (sum[D] == R(0)) continue;
-            int g[3];
-            g[0] = bo[0] + n0;
-            g[1] = bo[1] + n1;
-            g[2] = bo[2] + n2;
-            const uint32_t ni = node_index<D>(g, c.nb);
-            R* gdst = acc + 4 * (size_t)ni;
-#pragma unroll
-            for (int a = 0; a < D; ++a) atomicAdd(gdst + a, sum[a]);
-            atomicAdd(gdst + 3, sum[D]);
-        }
-        if (threadIdx.x < (1 << D)) {
-            int bb[3];
-            block_coords<D, R>(blk, c, bb);
-            bool in = true;
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                bb[a] += (threadIdx.x >> a) & 1;
-                if (bb[a] >= c.nb[a]) in = false;
-            }
-            if (in) {
-                const uint32_t b2 = (D == 3) ? ((uint32_t)bb[2] * c.nb[1] + bb[1]) * c.nb[0] + bb[0]
-                                             : (uint32_t)bb[1] * c.nb[0] + bb[0];
-                flags[b2] = 1u;
-            }
-        }
+        tile_flush<D, ORDER, R>(cellsum, cbeg, cend, bo, blk, acc, flags, c, NT);
     __syncthreads();
 }
 
@@ -719,6 +754,238 @@ __global__ void __launch_bounds__(128, 2) k_p2g_cells(PState<R> st, const uint32
         if (t >= ntiles) break;
         p2g_cells_tile<D, ORDER, R, G>(st, perm, skeys, tiles[t], tiles[t + 1], acc, flags, c, err, fallbacks, cellsum,
                                        cbeg, cend, &s_cell, pslots);
+    }
+}
+
+
+// ---------------------------------------------------------------- P2G, node-split
+// The ORDER+1 lanes of a group take the same cell and walk the same particles (each particle
+// read once into shared memory by the group); lane r owns the x-plane ia = r of the stencil,
+// (ORDER+1)^(D-1) nodes, and sums its nodes' contributions in registers.  No lane holds the
+// whole stencil, so a lane needs a third (quadratic) of the accumulators of the
+// cell-parallel form and no reduce-scatter; more warps fit on an SM.  The per-particle set-up
+// (weights, the separable terms) is repeated by the group's lanes.  Cell loop, neutral
+// particles and the node gather as in the cell-parallel form.
+template <typename R> __host__ __device__ constexpr int split_slots() { return 4; }
+template <int D, int ORDER> __host__ __device__ constexpr int split_groups() { return 32 / (ORDER + 1); }
+template <int D, int ORDER, typename R> __host__ __device__ constexpr size_t p2g_split_smem()
+{
+    return (p2g_cellsum_bytes<D, ORDER, R>() + 31) / 32 * 32 +
+           (size_t)4 * split_groups<D, ORDER>() * split_slots<R>() * slot_words<D>() * sizeof(R);
+}
+
+// lane r of a group copies the 16-byte pieces c of particle q with c % G == r
+template <int D, typename R, int G>
+__device__ __forceinline__ void stage_particle_split(R* slot, const PState<R>& s, uint32_t q, int r, bool with_tau)
+{
+    if (D == 3) {
+        if (0 % G == r) cp_group4<R>(slot + 0, s.A + q);
+        if (1 % G == r) cp_group4<R>(slot + 4, s.V + q);
+        if (2 % G == r) cp_group4<R>(slot + 8, s.Ba + q);
+        if (3 % G == r) cp_group4<R>(slot + 12, s.Bb + q);
+        if (with_tau) {
+            if (4 % G == r) cp_group4<R>(slot + 16, s.Ta + q);
+            if (5 % G == r) cp_group2<R>(slot + 20, s.Tb + q);
+        }
+    } else {
+        if (0 % G == r) cp_group4<R>(slot + 0, s.A + q);
+        if (1 % G == r) cp_group4<R>(slot + 4, s.V + q);
+        if (2 % G == r) cp_group4<R>(slot + 8, s.Ba + q);
+        if (with_tau && 3 % G == r) cp_group2<R>(slot + 12, s.Tb + q);
+    }
+}
+
+template <int D, int ORDER, typename R>
+__device__ __forceinline__ void p2g_split_tile(const PState<R>& st, const uint32_t* __restrict__ perm,
+                                               const uint32_t* __restrict__ skeys, uint32_t start, uint32_t end,
+                                               R* __restrict__ acc, uint32_t* __restrict__ flags, const DevCfg<R>& c,
+                                               uint32_t* err, R* cellsum, uint32_t* cbeg, uint32_t* cend, int* s_cell,
+                                               R* pring)
+{
+    constexpr int NT = 128;
+    constexpr int K = ORDER + 1;
+    constexpr int G = K;
+    constexpr int GPW = split_groups<D, ORDER>();
+    constexpr int NS = (D == 3) ? K * K * K : K * K;
+    constexpr int NV = D + 1;
+    constexpr int NVAL = NS * NV;
+    constexpr int NC = (D == 3) ? 64 : 16;
+    constexpr int NPL = NS / K;             // nodes of a lane's plane
+    constexpr int NSL = split_slots<R>();
+    constexpr int SW = slot_words<D>();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gw = lane / G, r = lane % G;
+    const R dt_dx = c.dt * c.inv_dx;
+    const R m = c.mass;
+    const R sC = (c.transfer == 0) ? m * c.inv_kdx : R(0);
+    const bool with_tau = c.model != 0;
+    const uint32_t blk = skeys[start] >> (2 * D);
+    int bo[3] = {0, 0, 0};
+    block_coords<D, R>(blk, c, bo);
+#pragma unroll
+    for (int a = 0; a < D; ++a) bo[a] *= 4;
+    tile_cell_runs<D>(skeys, start, end, cbeg, cend, NT);
+    __syncthreads();
+    // lanes past GPW * G have no group: they follow the loop with empty cells
+    R* ring = pring + (size_t)(warp * GPW + (gw < GPW ? gw : 0)) * NSL * SW;
+    for (;;) {
+        int cb = 0;
+        if (lane == 0) cb = atomicAdd(s_cell, GPW);
+        cb = __shfl_sync(FULLMASK, cb, 0);
+        if (cb >= NC) break;
+        const int cell = cb + gw;
+        const bool has = gw < GPW && cell < NC;
+        const uint32_t kb = has ? cbeg[cell] : 0u, ke = has ? cend[cell] : 0u;
+        const uint32_t cnt = ke > kb ? ke - kb : 0u;
+        const int lb[3] = {cell & 3, (cell >> 2) & 3, (D == 3) ? ((cell >> 4) & 3) : 0};
+        const uint32_t iters = __reduce_max_sync(FULLMASK, cnt);
+        if (iters == 0u) continue;
+        R sum[NPL * NV];
+#pragma unroll
+        for (int i = 0; i < NPL * NV; ++i) sum[i] = R(0);
+#pragma unroll
+        for (int i = 0; i < NSL; ++i) {
+            if ((uint32_t)i < cnt) stage_particle_split<D, R, G>(ring + i * SW, st, perm[kb + i], r, with_tau);
+            cp_async_commit();
+        }
+#pragma unroll 1
+        for (uint32_t it = 0; it < iters; ++it) {
+            bool live = it < cnt;
+            cp_async_wait<NSL - 1>();
+            __syncwarp();                      // the group's pieces of this particle have landed
+            R* slot = ring + (it % NSL) * SW;
+            Particle<D, R> p;
+            read_staged<D, R>(slot, p, with_tau);
+            __syncwarp();                      // every lane has read the slot before it is refilled
+            {
+                const uint32_t kn = it + NSL;
+                if (kn < cnt) stage_particle_split<D, R, G>(slot, st, perm[kb + kn], r, with_tau);
+                cp_async_commit();
+            }
+            if (!live) {   // neutral: an in-cell position and zero state (finite weights, zero sums)
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    p.o[a] = R(0.5);
+                    p.cell[a] = bo[a] + lb[a] + (ORDER == 3 ? 1 : 0);
+                    p.v[a] = R(0);
+                }
+#pragma unroll
+                for (int i = 0; i < D * D; ++i) p.B[i] = R(0);
+#pragma unroll
+                for (int i = 0; i < ((D == 3) ? 6 : 3); ++i) p.tau[i] = R(0);
+            }
+            int base[D];
+            R w[D][K], dw[D][K], fx[D];
+            bool ok = particle_stencil<D, ORDER, R>(p.o, p.cell, c, base, fx, w, dw);
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+                if (base[a] - bo[a] != lb[a]) ok = false;
+            if (live && !ok) {
+                if (r == 0) set_err(err, APIC_ERRBIT_RANGE);
+                live = false;
+            }
+            const R ml = live ? m : R(0);
+            R mv[D], mC[D * D], T[D * D];
+#pragma unroll
+            for (int a = 0; a < D; ++a) mv[a] = ml * p.v[a];
+#pragma unroll
+            for (int i = 0; i < D * D; ++i) mC[i] = (live ? sC : R(0)) * p.B[i];
+            if (with_tau) {
+                R tau[D * D];
+                tau_full<D, R>(p.tau, tau);
+#pragma unroll
+                for (int i = 0; i < D * D; ++i) T[i] = (live ? dt_dx : R(0)) * tau[i];
+            } else {
+#pragma unroll
+                for (int i = 0; i < D * D; ++i) T[i] = R(0);
+            }
+            // this lane's plane ia = r (separable terms as in the cell-parallel form)
+            R w0 = w[0][0], dw0 = dw[0][0];
+#pragma unroll
+            for (int i = 1; i < K; ++i)
+                if (r == i) { w0 = w[0][i]; dw0 = dw[0][i]; }
+            const R rw0 = (R(r) - fx[0]) * w0;
+            R E[D];
+#pragma unroll
+            for (int cc = 0; cc < D; ++cc) E[cc] = mC[cc * D + 0] * rw0 - T[cc * D + 0] * dw0;
+            if (D == 3) {
+                R H[3][K];
+#pragma unroll
+                for (int i = 0; i < K; ++i) {
+                    const R rw1 = (R(i) - fx[1]) * w[1][i];
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc) H[cc][i] = mC[cc * 3 + 1] * rw1 - T[cc * 3 + 1] * dw[1][i];
+                }
+#pragma unroll
+                for (int ic = 0; ic < K; ++ic) {
+                    const R w2 = w[2][ic], dw2 = dw[2][ic], rw2 = (R(ic) - fx[2]) * w2;
+                    R Q[3];
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc) Q[cc] = mv[cc] * w2 + mC[cc * 3 + 2] * rw2 - T[cc * 3 + 2] * dw2;
+#pragma unroll
+                    for (int ib = 0; ib < K; ++ib) {
+                        const R S = w[1][ib] * w2;
+                        const int q = ib + K * ic;
+#pragma unroll
+                        for (int cc = 0; cc < 3; ++cc)
+                            sum[q * NV + cc] += w0 * (w[1][ib] * Q[cc] + H[cc][ib] * w2) + E[cc] * S;
+                        sum[q * NV + 3] += w0 * ml * S;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int ib = 0; ib < K; ++ib) {
+                    const R w1 = w[1][ib], rw1 = (R(ib) - fx[1]) * w1;
+#pragma unroll
+                    for (int cc = 0; cc < 2; ++cc) {
+                        const R Q = mv[cc] * w1 + mC[cc * 2 + 1] * rw1 - T[cc * 2 + 1] * dw[1][ib];
+                        sum[ib * NV + cc] += w0 * Q + E[cc] * w1;
+                    }
+                    sum[ib * NV + 2] += w0 * ml * w1;
+                }
+            }
+        }
+        cp_async_wait<0>();
+        if (has) {
+            // node j = r + K q of the cell's stencil
+#pragma unroll
+            for (int q = 0; q < NPL; ++q)
+#pragma unroll
+                for (int v = 0; v < NV; ++v) cellsum[(size_t)cell * NVAL + (r + K * q) * NV + v] = sum[q * NV + v];
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    tile_flush<D, ORDER, R>(cellsum, cbeg, cend, bo, blk, acc, flags, c, NT);
+    __syncthreads();
+}
+
+template <int D, int ORDER, typename R>
+__global__ void __launch_bounds__(128, 4) k_p2g_split(PState<R> st, const uint32_t* __restrict__ perm,
+                                                      const uint32_t* __restrict__ skeys,
+                                                      const uint32_t* __restrict__ tiles,
+                                                      const uint32_t* __restrict__ ntiles_p,
+                                                      uint32_t* __restrict__ tile_ctr, R* __restrict__ acc,
+                                                      uint32_t* __restrict__ flags, DevCfg<R> c, uint32_t* err)
+{
+    constexpr int NC = (D == 3) ? 64 : 16;
+    extern __shared__ __align__(32) unsigned char p2g_smem[];
+    R* cellsum = reinterpret_cast<R*>(p2g_smem);
+    R* pring = reinterpret_cast<R*>(p2g_smem + (p2g_cellsum_bytes<D, ORDER, R>() + 31) / 32 * 32);
+    __shared__ uint32_t cbeg[NC], cend[NC];
+    __shared__ int s_tile, s_cell;
+    const int ntiles = (int)*ntiles_p;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_tile = (int)atomicAdd(tile_ctr, 1u);
+            s_cell = 0;
+        }
+        for (int i = threadIdx.x; i < NC; i += 128) { cbeg[i] = 0u; cend[i] = 0u; }
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= ntiles) break;
+        p2g_split_tile<D, ORDER, R>(st, perm, skeys, tiles[t], tiles[t + 1], acc, flags, c, err, cellsum, cbeg, cend,
+                                    &s_cell, pring);
     }
 }
 
@@ -1045,13 +1312,16 @@ __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>
     int bc[3] = {0, 0, 0};
     block_coords<D, R>(blk, c, bc);
     // the next round's particle is requested before the current one is processed
+    // (and the permutation entry of the one after it, so that load's address is ready)
     Particle<D, R> nxt;
     if (start + threadIdx.x < end) load_xF<D, R>(in, perm[start + threadIdx.x], nxt);
+    uint32_t qn = (start + threadIdx.x + TPB < end) ? perm[start + threadIdx.x + TPB] : 0u;
     for (uint32_t k0 = start; k0 < end; k0 += TPB) {
         const uint32_t k = k0 + threadIdx.x;
         if (k >= end) continue;
         Particle<D, R> p = nxt;
-        if (k + TPB < end) load_xF<D, R>(in, perm[k + TPB], nxt);
+        if (k + TPB < end) load_xF<D, R>(in, qn, nxt);
+        if (k + 2 * TPB < end) qn = perm[k + 2 * TPB];
         int base[D], lb[D];
         R w[D][K], dw[D][K], fx[D];
         bool ok = particle_stencil<D, ORDER, R>(p.o, p.cell, c, base, fx, w, dw);
@@ -1489,7 +1759,10 @@ template <typename R> struct Impl {
         if (n == 0) return cudaSuccess;
         DevCfg<R> c = HostToDev<R>::make(h, n);
         PState<R> st = state_of<R>(b, cur);
-        if (h.p2g_kernel == 3)
+        if (h.p2g_kernel == 4)
+            APIC_DISPATCH(h, (k_p2g_split<D, O, R><<<L.p2g_grid, 128, p2g_split_smem<D, O, R>(), s>>>(
+                                 st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc, b.flags, c, b.err)));
+        else if (h.p2g_kernel == 3)
             APIC_DISPATCH(h, (k_p2g_interleaved<D, O, R><<<L.p2g_grid, 256, 0, s>>>(
                                  st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc, b.flags, c, b.err, b.fallbacks)));
         else if (!L.p2g_cells)
@@ -1597,7 +1870,13 @@ template <typename R> struct Impl {
     {
         cudaError_t e = cudaSuccess;
         APIC_DISPATCH(h, {
-            if (h.p2g_kernel == 3)
+            if (h.p2g_kernel == 4) {
+                e = cudaFuncSetAttribute(k_p2g_split<D, O, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)p2g_split_smem<D, O, R>());
+                if (e == cudaSuccess)
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g_split<D, O, R>, 128,
+                                                                      p2g_split_smem<D, O, R>());
+            } else if (h.p2g_kernel == 3)
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g_interleaved<D, O, R>, 256, 0);
             else if (h.p2g_kernel != 2)
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g<D, O, R>, TPB, 0);

@@ -150,7 +150,7 @@ def test_transfer_modes_and_transfer_only(apic, transfer):
 
 
 @pytest.mark.parametrize("tile", [256, 4096])
-@pytest.mark.parametrize("p2g_kernel", [1, 2, 3])
+@pytest.mark.parametrize("p2g_kernel", [1, 2, 3, 4])
 @pytest.mark.parametrize("dim,order,prec", [(3, 2, 32), (2, 2, 32), (2, 3, 32), (3, 2, 64), (2, 3, 64), (3, 3, 32)])
 def test_p2g_variants_and_tile_sizes_agree(apic, tile, p2g_kernel, dim, order, prec):
     r = run_one_step(apic, dim, order, prec, 32 if dim == 3 else 64, 8 if dim == 3 else 4, tile=tile,
