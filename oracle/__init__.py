@@ -98,6 +98,8 @@ def _load():
                 "or_stress_nh": (None, [C.c_int, d, d, cp, cp]),
                 "or_cfl_speed": (d, [cfgp, i64, cp, cp]),
                 "or_p2g": (i64, [cfgp, i64, cp, cp, cp, cp, cp, cp, cp, cp, cp]),
+                "or_p2g_mat": (i64, [cfgp, i64, cp, cp, cp, cp, cp, cp, cp, cp, cp, cp, cp]),
+                "or_step_mat": (i64, [cfgp, i64, cp, cp, cp, cp, cp, cp, cp, cp]),
                 "or_grid_update": (None, [cfgp, cp, cp, cp, cp, cp]),
                 "or_g2p": (i64, [cfgp, i64, cp, cp, cp, cp, cp, cp]),
                 "or_g2p_lambda0": (i64, [cfgp, i64, cp, cp, cp, cp, cp]),
@@ -225,16 +227,22 @@ def cfl_speed(cfg: Cfg, v, B) -> float:
 
 
 # --------------------------------------------------------------------------- transfers
-def p2g(cfg: Cfg, x, v, B, F, mass, vol):
-    """Sec. 3.2 transfer to grid plus the Sec. 3.3 force.  Returns (m, mv, f, n_skipped)."""
+def p2g(cfg: Cfg, x, v, B, F, mass, vol, mu=None, lam=None):
+    """Sec. 3.2 transfer to grid plus the Sec. 3.3 force.  Returns (m, mv, f, n_skipped).
+    mu, lam: per-particle Lame parameters (a material per particle); None = the config's."""
     d = cfg.dim
     n = len(x)
     x = _f64(x, (n, d)); v = _f64(v, (n, d)); B = _f64(B, (n, d, d)); F = _f64(F, (n, d, d))
     mass = _f64(np.broadcast_to(mass, (n,))); vol = _f64(np.broadcast_to(vol, (n,)))
     nn = _nodes(cfg)
     gm = np.zeros(nn); gmv = np.zeros((nn, d)); gf = np.zeros((nn, d))
-    bad = _load().or_p2g(C.byref(cfg), n, _p(x), _p(v), _p(B), _p(F), _p(mass), _p(vol),
-                         _p(gm), _p(gmv), _p(gf))
+    if mu is None:
+        bad = _load().or_p2g(C.byref(cfg), n, _p(x), _p(v), _p(B), _p(F), _p(mass), _p(vol),
+                             _p(gm), _p(gmv), _p(gf))
+    else:
+        mu = _f64(np.broadcast_to(mu, (n,))); lam = _f64(np.broadcast_to(lam, (n,)))
+        bad = _load().or_p2g_mat(C.byref(cfg), n, _p(x), _p(v), _p(B), _p(F), _p(mass), _p(vol), _p(mu),
+                                 _p(lam), _p(gm), _p(gmv), _p(gf))
     return gm, gmv, gf, bad
 
 
@@ -317,14 +325,21 @@ def stable_sort(k) -> np.ndarray:
     return perm
 
 
-def step(cfg: Cfg, x, v, B, F, mass, vol, nsteps: int = 1):
-    """nsteps whole explicit steps: P2G, grid update, G2P.  Returns (x, v, B, F, skipped)."""
+def step(cfg: Cfg, x, v, B, F, mass, vol, nsteps: int = 1, mu=None, lam=None):
+    """nsteps whole explicit steps: P2G, grid update, G2P.  Returns (x, v, B, F, skipped).
+    mu, lam: per-particle Lame parameters (a material per particle); None = the config's."""
     d = cfg.dim
     n = len(x)
     x = _f64(x, (n, d)).copy(); v = _f64(v, (n, d)).copy()
     B = _f64(B, (n, d, d)).copy(); F = _f64(F, (n, d, d)).copy()
     mass = _f64(np.broadcast_to(mass, (n,))); vol = _f64(np.broadcast_to(vol, (n,)))
+    if mu is not None:
+        mu = _f64(np.broadcast_to(mu, (n,))); lam = _f64(np.broadcast_to(lam, (n,)))
     bad = 0
     for _ in range(nsteps):
-        bad += _load().or_step(C.byref(cfg), n, _p(x), _p(v), _p(B), _p(F), _p(mass), _p(vol))
+        if mu is None:
+            bad += _load().or_step(C.byref(cfg), n, _p(x), _p(v), _p(B), _p(F), _p(mass), _p(vol))
+        else:
+            bad += _load().or_step_mat(C.byref(cfg), n, _p(x), _p(v), _p(B), _p(F), _p(mass), _p(vol),
+                                       _p(mu), _p(lam))
     return x, v, B, F, bad

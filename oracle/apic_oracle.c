@@ -385,10 +385,10 @@ void or_stress_nh(int d, double mu, double lam, const double* F, double* P)
     for (int k = 0; k < d * d; ++k) P[k] = mu * (F[k] - C[k] / J) + lam * lj * C[k] / J;
 }
 
-static void stress_of(const or_cfg* c, const double* F, double* P)
+static void stress_with(const or_cfg* c, double mu, double lam, const double* F, double* P)
 {
-    if (c->model == 2) or_stress_nh(c->dim, c->mu, c->lam, F, P);
-    else or_stress_fcr(c->dim, c->mu, c->lam, F, P);
+    if (c->model == 2) or_stress_nh(c->dim, mu, lam, F, P);
+    else or_stress_fcr(c->dim, mu, lam, F, P);
 }
 
 static double psi_of(const or_cfg* c, const double* F)
@@ -408,10 +408,12 @@ static double psi_of(const or_cfg* c, const double* F)
  * f_i = -sum_p V_p P(F_p) F_p^T grad w_ip   (Sec. 3.3, lambda = 0, sign reading above)
  * Grid arrays are accumulated into (callers zero them first).  Returns the number of
  * particles whose stencil left the grid (those are skipped).
+ * Per-particle Lame parameters mu_p, lam_p (a material per particle) replace c->mu, c->lam
+ * when given (or_p2g_mat); or_p2g uses the configuration's.
  */
-int64_t or_p2g(const or_cfg* c, int64_t n, const double* x, const double* v, const double* B,
-               const double* F, const double* mass, const double* vol, double* gm, double* gmv,
-               double* gf)
+int64_t or_p2g_mat(const or_cfg* c, int64_t n, const double* x, const double* v, const double* B,
+                   const double* F, const double* mass, const double* vol, const double* mu_p,
+                   const double* lam_p, double* gm, double* gmv, double* gf)
 {
     const int d = c->dim, ns = stencil_count(c);
     int64_t bad = 0;
@@ -435,7 +437,7 @@ int64_t or_p2g(const or_cfg* c, int64_t n, const double* x, const double* v, con
         double tau[9] = {0};
         if (c->model != 0) {
             double P[9];
-            stress_of(c, F + p * d * d, P);
+            stress_with(c, mu_p ? mu_p[p] : c->mu, lam_p ? lam_p[p] : c->lam, F + p * d * d, P);
             /* tau = V_p P F^T */
             const double* Fp = F + p * d * d;
             for (int a = 0; a < d; ++a)
@@ -464,6 +466,13 @@ int64_t or_p2g(const or_cfg* c, int64_t n, const double* x, const double* v, con
         }
     }
     return bad;
+}
+
+int64_t or_p2g(const or_cfg* c, int64_t n, const double* x, const double* v, const double* B,
+               const double* F, const double* mass, const double* vol, double* gm, double* gmv,
+               double* gf)
+{
+    return or_p2g_mat(c, n, x, v, B, F, mass, vol, NULL, NULL, gm, gmv, gf);
 }
 
 /* ------------------------------------------------------------------ */
@@ -769,8 +778,8 @@ void or_stable_sort(int64_t n, const uint32_t* keys, int64_t* perm)
 /* ------------------------------------------------------------------ */
 /* One whole explicit step: P2G, grid update, G2P (general form).       */
 /* ------------------------------------------------------------------ */
-int64_t or_step(const or_cfg* c, int64_t n, double* x, double* v, double* B, double* F,
-                const double* mass, const double* vol)
+int64_t or_step_mat(const or_cfg* c, int64_t n, double* x, double* v, double* B, double* F,
+                    const double* mass, const double* vol, const double* mu_p, const double* lam_p)
 {
     const int d = c->dim;
     const int64_t nn = node_count(c);
@@ -781,10 +790,16 @@ int64_t or_step(const or_cfg* c, int64_t n, double* x, double* v, double* B, dou
     double* gvt = (double*)calloc((size_t)nn * d, sizeof(double));
     int64_t bad = -1;
     if (gm && gmv && gf && gv && gvt) {
-        bad = or_p2g(c, n, x, v, B, F, mass, vol, gm, gmv, gf);
+        bad = or_p2g_mat(c, n, x, v, B, F, mass, vol, mu_p, lam_p, gm, gmv, gf);
         or_grid_update(c, gm, gmv, gf, gv, gvt);
         bad += or_g2p(c, n, x, v, B, F, gv, gvt);
     }
     free(gm); free(gmv); free(gf); free(gv); free(gvt);
     return bad;
+}
+
+int64_t or_step(const or_cfg* c, int64_t n, double* x, double* v, double* B, double* F,
+                const double* mass, const double* vol)
+{
+    return or_step_mat(c, n, x, v, B, F, mass, vol, NULL, NULL);
 }
