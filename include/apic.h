@@ -110,6 +110,18 @@ apic_status apic_destroy(apic_sim* sim);
 apic_status apic_upload(apic_sim* sim, int64_t n, const double* x, const double* v,
                         const double* B, const double* F, int on_device);
 
+/* A material per particle: Young's modulus E[i] > 0 and Poisson's ratio nu[i] in (-1, 0.5)
+ * for the particle uploaded at index i (n = the count of the last apic_upload), turned into
+ * Lame parameters mu = E / (2 (1 + nu)), lam = E nu / ((1 + nu)(1 - 2 nu)) that replace the
+ * configuration's in the particle's stress from now on (the first "next" extension of the
+ * paper's Sec. 3.3 force: the constitutive model is per particle; the paper's experiments
+ * use one material per body).  The current stress is recomputed.  Valid until the next
+ * apic_upload, which returns to the configuration's material.  `on_device` as in
+ * apic_upload; host values are checked, device values are not.  Not allowed between
+ * apic_p2g and apic_g2p, nor while the simulation is in a batch.  Synchronising when
+ * on_device = 0.  Errors: APIC_ERR_ARG, APIC_ERR_CUDA. */
+apic_status apic_upload_materials(apic_sim* sim, int64_t n, const double* E, const double* nu, int on_device);
+
 /* Copy the particle state back in upload order (any pointer may be NULL to skip that
  * field).  Synchronising.  Errors: APIC_ERR_ARG, APIC_ERR_CUDA, and a latched device error. */
 apic_status apic_download(apic_sim* sim, double* x, double* v, double* B, double* F, int on_device);

@@ -82,6 +82,7 @@ SIGNATURES = {
     "apic_create": (C.c_int, [C.POINTER(Config), C.c_int64, C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(C.c_void_p)]),
     "apic_destroy": (C.c_int, [C.c_void_p]),
     "apic_upload": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "apic_upload_materials": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int]),
     "apic_download": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "apic_download_positions": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "apic_p2g": (C.c_int, [C.c_void_p]),
@@ -170,6 +171,10 @@ def apic_destroy(sim):
 
 def apic_upload(sim, n, x, v=None, B=None, F=None, on_device=0):
     _check(load().apic_upload(sim, n, _ptr(x), _ptr(v), _ptr(B), _ptr(F), on_device), sim)
+
+
+def apic_upload_materials(sim, n, E, nu, on_device=0):
+    _check(load().apic_upload_materials(sim, n, _ptr(E), _ptr(nu), on_device), sim)
 
 
 def apic_download(sim, x=None, v=None, B=None, F=None, on_device=0):
@@ -340,6 +345,12 @@ class Sim:
     @property
     def n_blocks(self) -> int:
         return int(np.prod([(r + 3) // 4 for r in self.res]))
+
+    def upload_materials(self, E, nu):
+        """Young's modulus and Poisson's ratio per particle (upload order); scalars broadcast."""
+        E = np.ascontiguousarray(np.broadcast_to(np.asarray(E, dtype=np.float64), (self.n,)))
+        nu = np.ascontiguousarray(np.broadcast_to(np.asarray(nu, dtype=np.float64), (self.n,)))
+        apic_upload_materials(self.handle, self.n, E, nu, on_device=0)
 
     def upload(self, x, v=None, B=None, F=None):
         """Host numpy arrays (float64) or CUDA float64 tensors."""

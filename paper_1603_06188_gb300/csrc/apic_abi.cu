@@ -96,6 +96,7 @@ apic_status fill_cfg(const apic_config* in, int64_t max_particles, HostCfg* c, s
     c->boundary = in->boundary;
     c->wall = in->wall;
     c->model = in->model;
+    c->mat = 0;
     if (in->model != APIC_MODEL_NONE) {
         if (!(in->E > 0.0) || !(in->nu > -1.0 && in->nu < 0.5)) { *why = "E must be > 0 and -1 < nu < 0.5"; return APIC_ERR_ARG; }
         c->mu = in->E / (2.0 * (1.0 + in->nu));
@@ -140,9 +141,9 @@ Layout layout_of(const HostCfg& c)
     const int64_t n = c.capacity > 0 ? c.capacity : 1;
     const size_t R = c.precision == 32 ? 4 : 8;
     for (int s = 0; s < 2; ++s) {
-        // lanes A V Ba Bb Fa Fb (4 reals), Fc (2), Ta (4), Tb (2); 2-D keeps A V Ba Fa Tb
-        static const int width[APIC_STATE_LANES] = {4, 4, 4, 4, 4, 4, 2, 4, 2};
-        static const bool used2d[APIC_STATE_LANES] = {true, true, true, false, true, false, false, false, true};
+        // lanes A V Ba Bb Fa Fb (4 reals), Fc (2), Ta (4), Tb (2), M (2); 2-D keeps A V Ba Fa Tb M
+        static const int width[APIC_STATE_LANES] = {4, 4, 4, 4, 4, 4, 2, 4, 2, 2};
+        static const bool used2d[APIC_STATE_LANES] = {true, true, true, false, true, false, false, false, true, true};
         for (int i = 0; i < APIC_STATE_LANES; ++i)
             L.st[s][i] = cv.take((c.dim == 3 || used2d[i]) ? (size_t)n * width[i] * R : 0);
     }
@@ -409,7 +410,39 @@ apic_status apic_upload(apic_sim* s, int64_t n, const double* x, const double* v
     s->phase = 0;
     s->skeys = s->perm = nullptr;
     s->order_sorted = false;
+    s->c.mat = 0;   // a new particle set: materials come from the configuration until set again
     CK(DISPATCH(s, upload, s->c, s->b, s->cur, n, dx_, dv, dB, dF, s->stream), "upload kernel");
+    if (!on_device) return check_device(s);
+    return APIC_OK;
+}
+
+apic_status apic_upload_materials(apic_sim* s, int64_t n, const double* E, const double* nu, int on_device)
+{
+    if (!s) return APIC_ERR_ARG;
+    IN_BATCH_GUARD(s);
+    if (s->phase != 0) return fail(s, APIC_ERR_ARG, "apic_upload_materials between apic_p2g and apic_g2p");
+    if (n != s->n) return fail(s, APIC_ERR_ARG, "n must equal the particle count of the last apic_upload");
+    if (n > 0 && (!E || !nu)) return fail(s, APIC_ERR_ARG, "E and nu are required");
+    CK(cudaSetDevice(s->device), "cudaSetDevice");
+    if (n == 0) {
+        s->c.mat = 1;
+        return APIC_OK;
+    }
+    const double *dE = E, *dnu = nu;
+    if (!on_device) {
+        for (int64_t i = 0; i < n; ++i)
+            if (!(E[i] > 0.0) || !(nu[i] > -1.0 && nu[i] < 0.5))
+                return fail(s, APIC_ERR_ARG, "each E must be > 0 and each nu in (-1, 0.5)");
+        double* sE = s->b.staging;
+        double* snu = sE + n;
+        CK(cudaMemcpyAsync(sE, E, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream), "upload E");
+        CK(cudaMemcpyAsync(snu, nu, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream), "upload nu");
+        dE = sE;
+        dnu = snu;
+    }
+    s->c.mat = 1;
+    CK(DISPATCH(s, set_materials, s->c, s->b, s->cur, n, dE, dnu, s->stream), "materials kernel");
+    s->launches += 1;
     if (!on_device) return check_device(s);
     return APIC_OK;
 }

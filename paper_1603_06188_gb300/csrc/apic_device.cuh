@@ -19,6 +19,8 @@ namespace apic {
 //        Ta = (t00, t11, t22, t01) Tb = (t02, t12)
 //   2-D: A  = (o0, o1, cell, id)   V  = (v0, v1, B00, B01)
 //        Ba = (B10, B11, t00, t11) Fa = (F00, F01, F10, F11)   Tb = (t01, -)
+//   both: M = (mu, lam), the particle's Lame parameters, kept only once a material per
+//        particle is set (otherwise the configuration's mu, lam hold for every particle)
 // o = offset in [0,1) inside integer cell `cell` (packed per axis), id = upload index,
 // t = the symmetric stress tau_p = V_p P(F_p) F_p^T of the current F_p (Sec. 3.3 force).
 // tau is written wherever F_p is (upload, G2P), so P2G reads position, v, B and tau --
@@ -27,7 +29,7 @@ template <typename R> struct alignas(4 * sizeof(R)) V4 { R x, y, z, w; };
 template <typename R> struct alignas(2 * sizeof(R)) V2 { R x, y; };
 
 template <typename R> struct PState {
-    V4<R>* A; V4<R>* V; V4<R>* Ba; V4<R>* Bb; V4<R>* Fa; V4<R>* Fb; V2<R>* Fc; V4<R>* Ta; V2<R>* Tb;
+    V4<R>* A; V4<R>* V; V4<R>* Ba; V4<R>* Bb; V4<R>* Fa; V4<R>* Fb; V2<R>* Fc; V4<R>* Ta; V2<R>* Tb; V2<R>* M;
 };
 
 __device__ __forceinline__ V4<float> ld4(const V4<float>* p)
@@ -90,6 +92,7 @@ template <int D, typename R> struct Particle {
     R B[D * D];
     R F[D * D];
     R tau[(D == 3) ? 6 : 3];   // 3-D: t00 t11 t22 t01 t02 t12; 2-D: t00 t11 t01
+    R mu, lam;                 // Lame parameters, when a material per particle is set
 };
 
 // full D x D matrix (row-major) of a symmetric stress held as its independent entries
@@ -175,11 +178,22 @@ __device__ __forceinline__ void load_tau(const PState<R>& s, uint32_t k, Particl
     }
 }
 
-// every lane of the particle; the stress lanes only when `with_tau` (a model is set)
 template <int D, typename R>
-__device__ __forceinline__ void store_all(const PState<R>& s, uint32_t k, const Particle<D, R>& p, bool with_tau)
+__device__ __forceinline__ void load_mat(const PState<R>& s, uint32_t k, Particle<D, R>& p)
+{
+    const V2<R> m = ld2(s.M + k);
+    p.mu = m.x;
+    p.lam = m.y;
+}
+
+// every lane of the particle; the stress lanes only when `with_tau` (a model is set), the
+// material lane only when `with_mat` (a material per particle is set)
+template <int D, typename R>
+__device__ __forceinline__ void store_all(const PState<R>& s, uint32_t k, const Particle<D, R>& p, bool with_tau,
+                                          bool with_mat = false)
 {
     const R z = R(0);
+    if (with_mat) st2(s.M + k, V2<R>{p.mu, p.lam});
     if (D == 3) {
         st4(s.A + k, V4<R>{p.o[0], p.o[1], p.o[2], u2r(pack_cell<D>(p.cell), z)});
         st4(s.V + k, V4<R>{p.v[0], p.v[1], p.v[2], p.B[0]});
@@ -210,6 +224,7 @@ template <typename R> struct DevCfg {
     R dt;
     R gravity[3];
     int boundary, wall, model, transfer;
+    int mat;             // 1: per-particle Lame parameters in lane M
     R mu, lam;
     R mass, vol;
     R inv_kdx;           // 1 / (kappa dx): B_p D_p^{-1} (x_i - x_p) = (B_p / (kappa dx)) r^, r^ = (x_i - x_p)/dx

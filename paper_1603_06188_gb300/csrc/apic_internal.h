@@ -10,8 +10,8 @@
 #define APIC_ERRBIT_TIMEOUT 2u   // a bounded mbarrier wait ran out
 #define APIC_ERRBIT_CAPACITY 4u  // tile list overflow
 
-// particle state lanes per copy: A V Ba Bb Fa Fb Fc Ta Tb (layout in apic_device.cuh)
-#define APIC_STATE_LANES 9
+// particle state lanes per copy: A V Ba Bb Fa Fb Fc Ta Tb M (layout in apic_device.cuh)
+#define APIC_STATE_LANES 10
 
 namespace apic {
 
@@ -54,6 +54,7 @@ struct HostCfg {
     int nb[3];
     double dx, origin[3], dt, gravity[3];
     int boundary, wall, model;
+    int mat;                     // 1: per-particle Lame parameters (lane M), else mu, lam
     double mu, lam, mass, vol;
     int tile;                    // particles per tile (power of two)
     int p2g_kernel;              // 1 warp-segmented, 2 cell-parallel
@@ -123,7 +124,9 @@ struct Launch {
     cudaError_t grid_dense_##SFX(const HostCfg& c, const Buffers& b, int which, double* m, double* mv,        \
                                  cudaStream_t s);                                                               \
     cudaError_t occupancy_##SFX(const HostCfg& c, int* p2g_per_sm, int* g2p_per_sm);                         \
-    cudaError_t cfl_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const Launch& L, cudaStream_t s);
+    cudaError_t cfl_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const Launch& L, cudaStream_t s); \
+    cudaError_t set_materials_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const double* E,     \
+                                    const double* nu, cudaStream_t s);
 
 #define APIC_DECLARE_BATCH(SFX)                                                                              \
     size_t batch_desc_bytes_##SFX();                                                                          \

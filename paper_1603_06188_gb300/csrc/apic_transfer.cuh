@@ -36,6 +36,7 @@ template <typename R> struct HostToDev {
         c.boundary = h.boundary;
         c.wall = h.wall;
         c.model = h.model;
+        c.mat = h.mat;
         c.transfer = h.transfer;
         c.mu = (R)h.mu;
         c.lam = (R)h.lam;
@@ -61,6 +62,7 @@ template <typename R> PState<R> state_of(const Buffers& b, int which)
     s.Fc = (V2<R>*)b.st[which][6];
     s.Ta = (V4<R>*)b.st[which][7];
     s.Tb = (V2<R>*)b.st[which][8];
+    s.M = (V2<R>*)b.st[which][9];
     return s;
 }
 
@@ -1314,13 +1316,20 @@ __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>
     // the next round's particle is requested before the current one is processed
     // (and the permutation entry of the one after it, so that load's address is ready)
     Particle<D, R> nxt;
-    if (start + threadIdx.x < end) load_xF<D, R>(in, perm[start + threadIdx.x], nxt);
+    if (start + threadIdx.x < end) {
+        const uint32_t q0 = perm[start + threadIdx.x];
+        load_xF<D, R>(in, q0, nxt);
+        if (c.mat) load_mat<D, R>(in, q0, nxt);
+    }
     uint32_t qn = (start + threadIdx.x + TPB < end) ? perm[start + threadIdx.x + TPB] : 0u;
     for (uint32_t k0 = start; k0 < end; k0 += TPB) {
         const uint32_t k = k0 + threadIdx.x;
         if (k >= end) continue;
         Particle<D, R> p = nxt;
-        if (k + TPB < end) load_xF<D, R>(in, qn, nxt);
+        if (k + TPB < end) {
+            load_xF<D, R>(in, qn, nxt);
+            if (c.mat) load_mat<D, R>(in, qn, nxt);
+        }
         if (k + 2 * TPB < end) qn = perm[k + 2 * TPB];
         int base[D], lb[D];
         R w[D][K], dw[D][K], fx[D];
@@ -1443,8 +1452,9 @@ __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>
             p.cell[a] = cl;
         }
         // the stress of the new F_p, for the next P2G
-        if (c.model != 0) stress_sym<D, R>(c.model, p.F, c.mu, c.lam, c.vol, p.tau, fallbacks);
-        store_all<D, R>(out, k, p, c.model != 0);
+        if (c.model != 0)
+            stress_sym<D, R>(c.model, p.F, c.mat ? p.mu : c.mu, c.mat ? p.lam : c.lam, c.vol, p.tau, fallbacks);
+        store_all<D, R>(out, k, p, c.model != 0, c.mat != 0);
         knext[k] = key_of<D, ORDER, R>(p.o, p.cell, c, err);
     }
 }
@@ -1687,6 +1697,24 @@ __global__ void __launch_bounds__(TPB) k_upload(PState<R> st, DevCfg<R> c, doubl
     store_all<D, R>(st, k, p, c.model != 0);
 }
 
+// a material per particle: Lame parameters from (E, nu) given in upload order (index = id),
+// stored in lane M of the particle wherever it now sits, and its stress recomputed
+template <int D, typename R>
+__global__ void __launch_bounds__(TPB) k_set_materials(PState<R> st, DevCfg<R> c, const double* __restrict__ E,
+                                                       const double* __restrict__ nu, uint32_t* fallbacks)
+{
+    const int k = blockIdx.x * TPB + threadIdx.x;
+    if (k >= c.n) return;
+    Particle<D, R> p;
+    load_xF<D, R>(st, k, p);
+    load_vB<D, R>(st, k, p);
+    const double e = E[p.id], v = nu[p.id];
+    p.mu = (R)(e / (2.0 * (1.0 + v)));
+    p.lam = (R)(e * v / ((1.0 + v) * (1.0 - 2.0 * v)));
+    if (c.model != 0) stress_sym<D, R>(c.model, p.F, p.mu, p.lam, c.vol, p.tau, fallbacks);
+    store_all<D, R>(st, k, p, c.model != 0, true);
+}
+
 template <int D, typename R>
 __global__ void __launch_bounds__(TPB) k_download(PState<R> st, DevCfg<R> c, double dx, double o0, double o1, double o2,
                                                   double* __restrict__ x, double* __restrict__ v, double* __restrict__ B,
@@ -1803,6 +1831,16 @@ template <typename R> struct Impl {
                                                                       (const R*)b.vel, b.knext, c, b.err, b.fallbacks)));
         return cudaGetLastError();
     }
+    static cudaError_t set_materials(const HostCfg& h, const Buffers& b, int cur, int64_t n, const double* E,
+                                     const double* nu, cudaStream_t s)
+    {
+        if (n == 0) return cudaSuccess;
+        DevCfg<R> c = HostToDev<R>::make(h, n);
+        PState<R> st = state_of<R>(b, cur);
+        if (h.dim == 3) k_set_materials<3, R><<<blocks_for(n), TPB, 0, s>>>(st, c, E, nu, b.fallbacks);
+        else k_set_materials<2, R><<<blocks_for(n), TPB, 0, s>>>(st, c, E, nu, b.fallbacks);
+        return cudaGetLastError();
+    }
     static cudaError_t upload(const HostCfg& h, const Buffers& b, int cur, int64_t n, const double* x,
                               const double* v, const double* B, const double* F, cudaStream_t s)
     {
@@ -1912,6 +1950,11 @@ template <typename R> struct Impl {
                           const uint32_t* perm, int64_t n, const Launch& L, cudaStream_t s)                     \
     {                                                                                                           \
         return Impl<R>::g2p(c, b, cur, skeys, perm, n, L, s);                                                   \
+    }                                                                                                           \
+    cudaError_t set_materials_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const double* E,   \
+                                    const double* nu, cudaStream_t s)                                          \
+    {                                                                                                           \
+        return Impl<R>::set_materials(c, b, cur, n, E, nu, s);                                                  \
     }                                                                                                           \
     cudaError_t upload_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const double* x,          \
                              const double* v, const double* B, const double* F, cudaStream_t s)                 \
