@@ -150,6 +150,18 @@ apic_status apic_g2p(apic_sim* sim);
 /* n whole steps (apic_p2g, apic_grid_update, apic_g2p).  Asynchronous. */
 apic_status apic_step(apic_sim* sim, int n);
 
+/* nsteps explicit steps whose time step follows the Sec. 4.3 bound: before each step
+ * dt = min(dt_max, nu * dx / max_p(|v_p| + 6 sqrt(d)/dx |B_p|_F)) (nu = the CFL number; the
+ * paper uses nu = 1 with its implicit integrator -- an explicit elastic run also needs
+ * dt_max under its wave-speed limit).  The first maximum is reduced from the current state
+ * in FP64; each later one is reduced by G2P from the state it writes (FP32 in the FP32
+ * build), and the time step is set on the device, so the steps run without host
+ * synchronisation.  The configured dt is not changed.  `elapsed` (may be NULL) receives
+ * the simulated time of the steps; then the call synchronises.  Not allowed between
+ * apic_p2g and apic_g2p, nor in a batch.  Errors: as apic_step, APIC_ERR_ARG for nu or
+ * dt_max <= 0. */
+apic_status apic_step_adaptive(apic_sim* sim, int nsteps, double nu, double dt_max, double* elapsed);
+
 /* Total linear momentum p and angular momentum l about the world origin, accumulated in
  * FP64 (Sec. 3.1; Sec. 5.3 for the particle form l = sum x_p x m_p v_p + m_p B_p^T : eps).
  * where = APIC_WHERE_PARTICLES, or APIC_WHERE_GRID: after apic_p2g, sum (m v)_i (which

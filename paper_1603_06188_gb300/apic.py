@@ -89,6 +89,7 @@ SIGNATURES = {
     "apic_grid_update": (C.c_int, [C.c_void_p]),
     "apic_g2p": (C.c_int, [C.c_void_p]),
     "apic_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "apic_step_adaptive": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_double)]),
     "apic_momentum": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "apic_cfl": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "apic_grid_download": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
@@ -206,6 +207,12 @@ def apic_momentum(sim, where: int):
     l = np.zeros(3)
     _check(load().apic_momentum(sim, where, _ptr(p), _ptr(l)), sim)
     return p, l
+
+
+def apic_step_adaptive(sim, n: int, nu: float, dt_max: float) -> float:
+    out = C.c_double(0.0)
+    _check(load().apic_step_adaptive(sim, n, nu, dt_max, C.byref(out)), sim)
+    return out.value
 
 
 def apic_cfl(sim) -> float:
@@ -388,6 +395,10 @@ class Sim:
 
     def step(self, n: int = 1):
         apic_step(self.handle, n)
+
+    def step_adaptive(self, n: int, nu: float, dt_max: float) -> float:
+        """n steps at dt = min(dt_max, nu dx / max speed) (Sec. 4.3); returns the simulated time."""
+        return apic_step_adaptive(self.handle, n, nu, dt_max)
 
     def momentum(self, where: str = "particles"):
         return apic_momentum(self.handle, WHERE_PARTICLES if where == "particles" else WHERE_GRID)

@@ -97,6 +97,7 @@ apic_status fill_cfg(const apic_config* in, int64_t max_particles, HostCfg* c, s
     c->wall = in->wall;
     c->model = in->model;
     c->mat = 0;
+    c->adaptive = 0;
     if (in->model != APIC_MODEL_NONE) {
         if (!(in->E > 0.0) || !(in->nu > -1.0 && in->nu < 0.5)) { *why = "E must be > 0 and -1 < nu < 0.5"; return APIC_ERR_ARG; }
         c->mu = in->E / (2.0 * (1.0 + in->nu));
@@ -126,7 +127,7 @@ struct Carve {
 // offsets of every buffer inside the workspace (relative to its base)
 struct Layout {
     size_t st[2][APIC_STATE_LANES];
-    size_t mk[2], mv[2], midx, choff, mcnt, mctl, lbs;
+    size_t mk[2], mv[2], midx, choff, mcnt, mctl, lbs, step_words;
     size_t knext, kA, kB, vA, vB, radix_counts, scan_part, tiles, chunk_cnt, ntiles, tile_ctr;
     size_t acc, vel, flags, mom_part, mom_out, err, fallbacks, staging;
     size_t staging_doubles;
@@ -177,6 +178,7 @@ Layout layout_of(const HostCfg& c)
     L.mom_out = cv.take(6 * 8);
     L.err = cv.take(4);
     L.fallbacks = cv.take(4);
+    L.step_words = cv.take(32);   // dt word (8), speed maximum (4), elapsed time (8 at +16)
     const int d = c.dim;
     size_t nn = 1;
     for (int a = 0; a < d; ++a) nn *= (size_t)c.res[a];
@@ -336,6 +338,9 @@ apic_status apic_create(const apic_config* cfg, int64_t max_particles, void* wor
     s->b.mom_out = (double*)(base + L.mom_out);
     s->b.err = (uint32_t*)(base + L.err);
     s->b.fallbacks = (uint32_t*)(base + L.fallbacks);
+    s->b.dt_word = base + L.step_words;
+    s->b.smax_word = (uint32_t*)(base + L.step_words + 8);
+    s->b.elapsed = (double*)(base + L.step_words + 16);
     s->b.staging = (double*)(base + L.staging);
     s->b.staging_doubles = L.staging_doubles;
     cudaError_t e = cudaGetDevice(&s->device);
@@ -358,6 +363,7 @@ apic_status apic_create(const apic_config* cfg, int64_t max_particles, void* wor
     if (e == cudaSuccess) e = cudaMemsetAsync(s->b.vel, 0, gbytes, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->b.flags, 0, (size_t)c.nblocks * 4, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->b.err, 0, 4, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->b.dt_word, 0, 32, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->b.fallbacks, 0, 4, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->b.ntiles, 0, 4, s->stream);
     if (e != cudaSuccess) {
@@ -577,6 +583,41 @@ apic_status apic_step(apic_sim* s, int nsteps)
         if (st == APIC_OK) st = apic_grid_update(s);
         if (st == APIC_OK) st = apic_g2p(s);
         if (st != APIC_OK) return st;
+    }
+    return APIC_OK;
+}
+
+apic_status apic_step_adaptive(apic_sim* s, int nsteps, double nu, double dt_max, double* elapsed)
+{
+    if (!s || nsteps < 0 || !(nu > 0.0) || !(dt_max > 0.0)) return APIC_ERR_ARG;
+    IN_BATCH_GUARD(s);
+    if (s->phase != 0) return fail(s, APIC_ERR_ARG, "apic_step_adaptive between apic_p2g and apic_g2p");
+    CK(cudaSetDevice(s->device), "cudaSetDevice");
+    if (elapsed) *elapsed = 0.0;
+    if (s->n == 0 || nsteps == 0) return APIC_OK;
+    // first time step from the FP64 speed maximum of the current state
+    CK(DISPATCH(s, cfl, s->c, s->b, s->cur, s->n, s->L, s->stream), "cfl kernel");
+    CK(DISPATCH(s, adapt_dt, s->c, s->b, nu, dt_max, 1, s->stream), "time step kernel");
+    s->launches += 3;
+    s->c.adaptive = 1;
+    apic_status st = APIC_OK;
+    for (int i = 0; i < nsteps && st == APIC_OK; ++i) {
+        st = apic_p2g(s);
+        if (st == APIC_OK) st = apic_grid_update(s);
+        if (st == APIC_OK) st = apic_g2p(s);
+        if (st == APIC_OK) {
+            // adds this step's dt to the elapsed time, takes the next from G2P's speed maximum
+            cudaError_t e = s->c.precision == 32 ? adapt_dt_f32(s->c, s->b, nu, dt_max, 0, s->stream)
+                                                 : adapt_dt_f64(s->c, s->b, nu, dt_max, 0, s->stream);
+            if (e != cudaSuccess) st = cuda_fail(s, e, "time step kernel");
+            s->launches += 1;
+        }
+    }
+    s->c.adaptive = 0;
+    if (st != APIC_OK) return st;
+    if (elapsed) {
+        CK(cudaMemcpyAsync(elapsed, s->b.elapsed, sizeof(double), cudaMemcpyDeviceToHost, s->stream), "read time");
+        return check_device(s);
     }
     return APIC_OK;
 }
@@ -917,10 +958,12 @@ cudaError_t batch_enqueue(apic_batch* b)
     if (e == cudaSuccess)
         e = b->precision == 32 ? batch_grid_f32(b->dim, b->descs, b->bbase, S, b->total_blocks, b->grid_grid, b->stream)
                                : batch_grid_f64(b->dim, b->descs, b->bbase, S, b->total_blocks, b->grid_grid, b->stream);
+    int ext = 0;   // some member carries a material per particle
+    for (apic_sim* m : b->members) ext |= m->c.mat;
     if (e == cudaSuccess)
-        e = b->precision == 32 ? batch_g2p_f32(b->dim, b->order, b->descs, b->tile_sim, b->tile_start, b->ntiles,
+        e = b->precision == 32 ? batch_g2p_f32(b->dim, b->order, ext, b->descs, b->tile_sim, b->tile_start, b->ntiles,
                                                b->tile_ctr, kpar, b->g2p_grid, b->stream)
-                               : batch_g2p_f64(b->dim, b->order, b->descs, b->tile_sim, b->tile_start, b->ntiles,
+                               : batch_g2p_f64(b->dim, b->order, ext, b->descs, b->tile_sim, b->tile_start, b->ntiles,
                                                b->tile_ctr, kpar, b->g2p_grid, b->stream);
     if (e == cudaSuccess) e = b->precision == 32 ? batch_finish_f32(b->descs, S, b->stream) : batch_finish_f64(b->descs, S, b->stream);
     return e;

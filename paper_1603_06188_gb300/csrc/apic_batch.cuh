@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(128, 2) kb_p2g_cells(SimDesc<R>* __restrict__ 
     }
 }
 
-template <int D, int ORDER, typename R>
+template <int D, int ORDER, typename R, bool EXT>
 __global__ void __launch_bounds__(TPB, 2) kb_g2p(SimDesc<R>* __restrict__ descs, const uint32_t* __restrict__ tile_sim,
                                               const uint32_t* __restrict__ tile_start,
                                               const uint32_t* __restrict__ ntiles_p, uint32_t* __restrict__ tile_ctr,
@@ -143,8 +143,9 @@ __global__ void __launch_bounds__(TPB, 2) kb_g2p(SimDesc<R>* __restrict__ descs,
         if (!s_ok) return;
         const uint32_t start = tile_start[t];
         const uint32_t end = tile_end(tile_sim, tile_start, t, ntiles, sim, (uint32_t)sd.c.n);
-        g2p_compute<D, ORDER, R>(sd.st[sd.cur], sd.st[sd.cur ^ 1], sd.vb[kpar], sd.kb[kpar], start, end, sd.knext, sd.c,
-                                 sd.err, sd.fallbacks, sv[buf]);
+        float smax_unused = 0.0f;   // members are stepped at their fixed dt
+        g2p_compute<D, ORDER, R, EXT>(sd.st[sd.cur], sd.st[sd.cur ^ 1], sd.vb[kpar], sd.kb[kpar], start, end, sd.knext, sd.c,
+                                 sd.err, sd.fallbacks, sv[buf], smax_unused);
         __syncthreads();
         phase[buf] ^= 1u;
     }
@@ -182,7 +183,7 @@ template <typename R> struct BatchImpl {
         const int smem = (int)p2g_cells_smem<D, O, R>();
         cudaError_t e = cudaFuncSetAttribute(kb_p2g_cells<D, O, R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, kb_p2g_cells<D, O, R, G>, 128, smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(g2p_per_sm, kb_g2p<D, O, R>, TPB, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(g2p_per_sm, kb_g2p<D, O, R, false>, TPB, 0);
         return e;
     }
     // lane groups of 2, 4 or 8 per base cell (fewer lanes suit fewer particles per cell)
@@ -231,14 +232,21 @@ template <typename R> struct BatchImpl {
         else kb_grid_update<2, R><<<grid, TPB, 0, s>>>((SimDesc<R>*)descs, bbase, nsims, total_blocks);
         return cudaGetLastError();
     }
-    static cudaError_t g2p(int dim, int order, void* descs, const uint32_t* ts, const uint32_t* tst, const uint32_t* nt,
-                           uint32_t* ctr, int kpar, int grid, cudaStream_t s)
+    template <int D, int O>
+    static void g2p_one(int ext, SimDesc<R>* d, const uint32_t* ts, const uint32_t* tst, const uint32_t* nt,
+                        uint32_t* ctr, int kpar, int grid, cudaStream_t s)
+    {
+        if (ext) kb_g2p<D, O, R, true><<<grid, TPB, 0, s>>>(d, ts, tst, nt, ctr, kpar);
+        else kb_g2p<D, O, R, false><<<grid, TPB, 0, s>>>(d, ts, tst, nt, ctr, kpar);
+    }
+    static cudaError_t g2p(int dim, int order, int ext, void* descs, const uint32_t* ts, const uint32_t* tst,
+                           const uint32_t* nt, uint32_t* ctr, int kpar, int grid, cudaStream_t s)
     {
         SimDesc<R>* d = (SimDesc<R>*)descs;
-        if (dim == 3 && order == 2) kb_g2p<3, 2, R><<<grid, TPB, 0, s>>>(d, ts, tst, nt, ctr, kpar);
-        else if (dim == 2 && order == 2) kb_g2p<2, 2, R><<<grid, TPB, 0, s>>>(d, ts, tst, nt, ctr, kpar);
-        else if (dim == 2 && order == 3) kb_g2p<2, 3, R><<<grid, TPB, 0, s>>>(d, ts, tst, nt, ctr, kpar);
-        else if (dim == 3 && order == 3) kb_g2p<3, 3, R><<<grid, TPB, 0, s>>>(d, ts, tst, nt, ctr, kpar);
+        if (dim == 3 && order == 2) g2p_one<3, 2>(ext, d, ts, tst, nt, ctr, kpar, grid, s);
+        else if (dim == 2 && order == 2) g2p_one<2, 2>(ext, d, ts, tst, nt, ctr, kpar, grid, s);
+        else if (dim == 2 && order == 3) g2p_one<2, 3>(ext, d, ts, tst, nt, ctr, kpar, grid, s);
+        else if (dim == 3 && order == 3) g2p_one<3, 3>(ext, d, ts, tst, nt, ctr, kpar, grid, s);
         else return cudaErrorInvalidValue;
         return cudaGetLastError();
     }
@@ -270,10 +278,11 @@ template <typename R> struct BatchImpl {
     {                                                                                                          \
         return BatchImpl<R>::grid(dim, descs, bbase, nsims, tb, grid, s);                                      \
     }                                                                                                          \
-    cudaError_t batch_g2p_##SFX(int dim, int order, void* descs, const uint32_t* ts, const uint32_t* tst,     \
-                                const uint32_t* nt, uint32_t* ctr, int kpar, int grid, cudaStream_t s)         \
+    cudaError_t batch_g2p_##SFX(int dim, int order, int ext, void* descs, const uint32_t* ts,                \
+                                const uint32_t* tst, const uint32_t* nt, uint32_t* ctr, int kpar, int grid,    \
+                                cudaStream_t s)                                                                \
     {                                                                                                          \
-        return BatchImpl<R>::g2p(dim, order, descs, ts, tst, nt, ctr, kpar, grid, s);                          \
+        return BatchImpl<R>::g2p(dim, order, ext, descs, ts, tst, nt, ctr, kpar, grid, s);                     \
     }                                                                                                          \
     cudaError_t batch_finish_##SFX(void* descs, int nsims, cudaStream_t s)                                    \
     {                                                                                                          \

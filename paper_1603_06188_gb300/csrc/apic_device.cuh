@@ -230,7 +230,13 @@ template <typename R> struct DevCfg {
     R inv_kdx;           // 1 / (kappa dx): B_p D_p^{-1} (x_i - x_p) = (B_p / (kappa dx)) r^, r^ = (x_i - x_p)/dx
     int n;               // particles
     int nblocks;         // node blocks
+    const R* dtp;        // when set, the time step is read here (adaptive stepping), else dt
+    uint32_t* smax;      // when set, G2P max-reduces the Sec. 4.3 particle speed here (FP32 bits)
+    R cfl_coef;          // 6 sqrt(d) / dx of the Sec. 4.3 speed |v| + 6 sqrt(d)/dx |B|_F
 };
+
+// the step's time step: fixed, or the adaptive one on the device
+template <typename R> __device__ __forceinline__ R step_dt(const DevCfg<R>& c) { return c.dtp ? *c.dtp : c.dt; }
 
 // ---------------------------------------------------------------- stencil (Sec. 3.5)
 // Base node and 1-D weights / derivatives in grid units for one axis.  u = cell + o.

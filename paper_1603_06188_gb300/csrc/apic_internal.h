@@ -44,6 +44,9 @@ struct Buffers {
     double* mom_out;             // 6 doubles
     uint32_t* err;               // latched error bits
     uint32_t* fallbacks;         // FP64 polar fallbacks
+    void* dt_word;               // the current time step (one real) of adaptive stepping
+    uint32_t* smax_word;         // max over particles of the Sec. 4.3 speed, FP32 bits (G2P)
+    double* elapsed;             // simulated time of an adaptive run
     double* staging;             // FP64 staging for upload / download
     size_t staging_doubles;
 };
@@ -55,6 +58,7 @@ struct HostCfg {
     double dx, origin[3], dt, gravity[3];
     int boundary, wall, model;
     int mat;                     // 1: per-particle Lame parameters (lane M), else mu, lam
+    int adaptive;                // 1: kernels read the time step from Buffers::dt_word
     double mu, lam, mass, vol;
     int tile;                    // particles per tile (power of two)
     int p2g_kernel;              // 1 warp-segmented, 2 cell-parallel
@@ -126,7 +130,9 @@ struct Launch {
     cudaError_t occupancy_##SFX(const HostCfg& c, int* p2g_per_sm, int* g2p_per_sm);                         \
     cudaError_t cfl_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const Launch& L, cudaStream_t s); \
     cudaError_t set_materials_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const double* E,     \
-                                    const double* nu, cudaStream_t s);
+                                    const double* nu, cudaStream_t s);                                             \
+    cudaError_t adapt_dt_##SFX(const HostCfg& c, const Buffers& b, double nu, double dt_max, int first,         \
+                               cudaStream_t s);
 
 #define APIC_DECLARE_BATCH(SFX)                                                                              \
     size_t batch_desc_bytes_##SFX();                                                                          \
@@ -137,7 +143,7 @@ struct Launch {
                                 int grid, cudaStream_t s);                                                     \
     cudaError_t batch_grid_##SFX(int dim, void* descs, const uint32_t* bbase, int nsims, uint32_t total_blocks, \
                                  int grid, cudaStream_t s);                                                    \
-    cudaError_t batch_g2p_##SFX(int dim, int order, void* descs, const uint32_t* tile_sim,                    \
+    cudaError_t batch_g2p_##SFX(int dim, int order, int ext, void* descs, const uint32_t* tile_sim,           \
                                 const uint32_t* tile_start, const uint32_t* ntiles, uint32_t* ctr, int kpar,  \
                                 int grid, cudaStream_t s);                                                     \
     cudaError_t batch_finish_##SFX(void* descs, int nsims, cudaStream_t s);                                   \

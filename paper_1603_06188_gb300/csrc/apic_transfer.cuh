@@ -46,6 +46,18 @@ template <typename R> struct HostToDev {
         c.inv_kdx = (R)(1.0 / (kappa * h.dx));
         c.n = (int)n;
         c.nblocks = h.nblocks;
+        c.dtp = nullptr;
+        c.smax = nullptr;
+        c.cfl_coef = (R)(6.0 * sqrt((double)h.dim) / h.dx);
+        return c;
+    }
+    // the per-simulation words of adaptive stepping: the time step and the fused speed
+    // maximum (plain steps use neither)
+    static DevCfg<R> make(const HostCfg& h, const Buffers& b, int64_t n)
+    {
+        DevCfg<R> c = make(h, n);
+        c.dtp = h.adaptive ? (const R*)b.dt_word : nullptr;
+        c.smax = h.adaptive ? b.smax_word : nullptr;
         return c;
     }
 };
@@ -153,7 +165,7 @@ __global__ void __launch_bounds__(TPB) k_p2g(PState<R> st, const uint32_t* __res
     __shared__ R sm[NV][TN];
     const int lane = threadIdx.x & 31;
     const int ntiles = (int)*ntiles_p;
-    const R dt_dx = c.dt * c.inv_dx;
+    const R dt_dx = step_dt(c) * c.inv_dx;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         for (int i = threadIdx.x; i < NV * TN; i += TPB) (&sm[0][0])[i] = R(0);
         const uint32_t start = tiles[t], end = tiles[t + 1];
@@ -545,7 +557,7 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
     constexpr int NVS = NVAL / ZS;
     const int lane = threadIdx.x & 31;
     const int lig = threadIdx.x % G;
-    const R dt_dx = c.dt * c.inv_dx;
+    const R dt_dx = step_dt(c) * c.inv_dx;
     const R m = c.mass;
     const R sC = (c.transfer == 0) ? m * c.inv_kdx : R(0);
     const bool with_tau = c.model != 0;
@@ -817,7 +829,7 @@ __device__ __forceinline__ void p2g_split_tile(const PState<R>& st, const uint32
     constexpr int SW = slot_words<D>();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gw = lane / G, r = lane % G;
-    const R dt_dx = c.dt * c.inv_dx;
+    const R dt_dx = step_dt(c) * c.inv_dx;
     const R m = c.mass;
     const R sC = (c.transfer == 0) ? m * c.inv_kdx : R(0);
     const bool with_tau = c.model != 0;
@@ -1017,7 +1029,7 @@ __global__ void __launch_bounds__(256) k_p2g_interleaved(PState<R> st, const uin
     __shared__ uint32_t cbeg[NC], cend[NC];
     __shared__ int s_tile;
     const int ntiles = (int)*ntiles_p;
-    const R dt_dx = c.dt * c.inv_dx;
+    const R dt_dx = step_dt(c) * c.inv_dx;
     const R m = c.mass;
     const R sC = (c.transfer == 0) ? m * c.inv_kdx : R(0);
     const int cell = threadIdx.x % NC, slot = threadIdx.x / NC;
@@ -1176,9 +1188,10 @@ __device__ __forceinline__ void grid_update_block(R* __restrict__ acc, R* __rest
         R v[3] = {R(0), R(0), R(0)};
         if (m > R(0)) {
             const R inv = R(1) / m;
-            v[0] = a.x * inv + c.dt * c.gravity[0];
-            v[1] = a.y * inv + c.dt * c.gravity[1];
-            if (D == 3) v[2] = a.z * inv + c.dt * c.gravity[2];
+            const R dt = step_dt(c);
+            v[0] = a.x * inv + dt * c.gravity[0];
+            v[1] = a.y * inv + dt * c.gravity[1];
+            if (D == 3) v[2] = a.z * inv + dt * c.gravity[2];
             if (c.boundary == 1) {           // sticky: the whole velocity
                 bool wall = false;
 #pragma unroll
@@ -1205,6 +1218,7 @@ __global__ void __launch_bounds__(TPB) k_grid_update(R* __restrict__ acc, R* __r
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * TPB + threadIdx.x) >> 5;
     const int nw = (gridDim.x * TPB) >> 5;
+    if (c.smax && blockIdx.x == 0 && threadIdx.x == 0) *c.smax = 0u;   // G2P, next, max-reduces into it
     for (int b = gw; b < c.nblocks; b += nw) grid_update_block<D, R>(acc, vel, flags, c, b, lane);
 }
 
@@ -1302,14 +1316,16 @@ __device__ __forceinline__ bool g2p_wait(uint64_t* mbar, unsigned parity, uint32
 }
 
 // the particles of one tile, with its grid blocks already in sv (whole CTA)
-template <int D, int ORDER, typename R>
+// EXT: the material lane and the fused speed maximum may be in use (else compiled out)
+template <int D, int ORDER, typename R, bool EXT>
 __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>& out, const uint32_t* __restrict__ perm,
                                             const uint32_t* __restrict__ skeys, uint32_t start, uint32_t end,
                                             uint32_t* __restrict__ knext, const DevCfg<R>& c, uint32_t* err,
-                                            uint32_t* fallbacks, const R (*sv)[(D == 3) ? 64 : 16][4])
+                                            uint32_t* fallbacks, const R (*sv)[(D == 3) ? 64 : 16][4],
+                                            float& smax_l)
 {
     constexpr int K = ORDER + 1;
-    const R dt_dx = c.dt * c.inv_dx;
+    const R dt_dx = step_dt(c) * c.inv_dx;
     const uint32_t blk = skeys[start] >> (2 * D);
     int bc[3] = {0, 0, 0};
     block_coords<D, R>(blk, c, bc);
@@ -1319,7 +1335,7 @@ __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>
     if (start + threadIdx.x < end) {
         const uint32_t q0 = perm[start + threadIdx.x];
         load_xF<D, R>(in, q0, nxt);
-        if (c.mat) load_mat<D, R>(in, q0, nxt);
+        if (EXT && c.mat) load_mat<D, R>(in, q0, nxt);
     }
     uint32_t qn = (start + threadIdx.x + TPB < end) ? perm[start + threadIdx.x + TPB] : 0u;
     for (uint32_t k0 = start; k0 < end; k0 += TPB) {
@@ -1328,7 +1344,7 @@ __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>
         Particle<D, R> p = nxt;
         if (k + TPB < end) {
             load_xF<D, R>(in, qn, nxt);
-            if (c.mat) load_mat<D, R>(in, qn, nxt);
+            if (EXT && c.mat) load_mat<D, R>(in, qn, nxt);
         }
         if (k + 2 * TPB < end) qn = perm[k + 2 * TPB];
         int base[D], lb[D];
@@ -1451,15 +1467,25 @@ __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>
             p.o[a] = o;
             p.cell[a] = cl;
         }
+        // the Sec. 4.3 speed of the new state, |v_p| + 6 sqrt(d)/dx |B_p|_F, for the next step's bound
+        if (EXT && c.smax) {
+            R vv = R(0), bb = R(0);
+#pragma unroll
+            for (int a = 0; a < D; ++a) vv += p.v[a] * p.v[a];
+#pragma unroll
+            for (int i = 0; i < D * D; ++i) bb += p.B[i] * p.B[i];
+            smax_l = fmaxf(smax_l, (float)(sqrt(vv) + c.cfl_coef * sqrt(bb)));
+        }
         // the stress of the new F_p, for the next P2G
         if (c.model != 0)
-            stress_sym<D, R>(c.model, p.F, c.mat ? p.mu : c.mu, c.mat ? p.lam : c.lam, c.vol, p.tau, fallbacks);
-        store_all<D, R>(out, k, p, c.model != 0, c.mat != 0);
+            stress_sym<D, R>(c.model, p.F, (EXT && c.mat) ? p.mu : c.mu, (EXT && c.mat) ? p.lam : c.lam, c.vol,
+                             p.tau, fallbacks);
+        store_all<D, R>(out, k, p, c.model != 0, EXT && c.mat != 0);
         knext[k] = key_of<D, ORDER, R>(p.o, p.cell, c, err);
     }
 }
 
-template <int D, int ORDER, typename R>
+template <int D, int ORDER, typename R, bool EXT>
 __global__ void __launch_bounds__(TPB, 2) k_g2p(PState<R> in, PState<R> out, const uint32_t* __restrict__ perm,
                                              const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ tiles,
                                              const uint32_t* __restrict__ ntiles_p, uint32_t* __restrict__ tile_ctr,
@@ -1476,6 +1502,7 @@ __global__ void __launch_bounds__(TPB, 2) k_g2p(PState<R> in, PState<R> out, con
     // again until the next iteration has passed that same barrier.
     __shared__ int s_ok, s_t[2];
     unsigned phase[2] = {0u, 0u};
+    float smax_l = 0.0f;
     const int ntiles = (int)*ntiles_p;
     if (threadIdx.x == 0) {
         mbar_init(&mbar[0], 1);
@@ -1498,9 +1525,15 @@ __global__ void __launch_bounds__(TPB, 2) k_g2p(PState<R> in, PState<R> out, con
         }
         __syncthreads();
         if (!s_ok) return;
-        g2p_compute<D, ORDER, R>(in, out, perm, skeys, tiles[t], tiles[t + 1], knext, c, err, fallbacks, sv[buf]);
+        g2p_compute<D, ORDER, R, EXT>(in, out, perm, skeys, tiles[t], tiles[t + 1], knext, c, err, fallbacks, sv[buf],
+                                      smax_l);
         __syncthreads();
         phase[buf] ^= 1u;
+    }
+    // the CTA's speed maximum (non-negative floats order like their bit patterns)
+    if (EXT && c.smax) {
+        const unsigned mx = __reduce_max_sync(FULLMASK, __float_as_uint(smax_l));
+        if ((threadIdx.x & 31) == 0 && mx) atomicMax(c.smax, mx);
     }
     // a copy issued for a tile index past the end is never issued; nothing is left in flight
 }
@@ -1715,6 +1748,20 @@ __global__ void __launch_bounds__(TPB) k_set_materials(PState<R> st, DevCfg<R> c
     store_all<D, R>(st, k, p, c.model != 0, true);
 }
 
+// adaptive time step (Sec. 4.3): dt = min(dt_max, nu dx / speed), speed = the FP64 reduction
+// of the current state (first) or the maximum G2P reduced into smax (after a step, whose dt
+// is first added to the elapsed time); one thread
+template <typename R>
+__global__ void k_adapt_dt(R* dtw, const uint32_t* smax, const double* speed64, double* elapsed, double dx,
+                           double nu, double dt_max, int first)
+{
+    if (first) *elapsed = 0.0;
+    else *elapsed += (double)*dtw;
+    const double sp = first ? speed64[0] : (double)__uint_as_float(*smax);
+    const double dt = sp > 0.0 ? fmin(dt_max, nu * dx / sp) : dt_max;
+    *dtw = (R)dt;
+}
+
 template <int D, typename R>
 __global__ void __launch_bounds__(TPB) k_download(PState<R> st, DevCfg<R> c, double dx, double o0, double o1, double o2,
                                                   double* __restrict__ x, double* __restrict__ v, double* __restrict__ B,
@@ -1785,7 +1832,7 @@ template <typename R> struct Impl {
                            int64_t n, const Launch& L, cudaStream_t s)
     {
         if (n == 0) return cudaSuccess;
-        DevCfg<R> c = HostToDev<R>::make(h, n);
+        DevCfg<R> c = HostToDev<R>::make(h, b, n);
         PState<R> st = state_of<R>(b, cur);
         if (h.p2g_kernel == 4)
             APIC_DISPATCH(h, (k_p2g_split<D, O, R><<<L.p2g_grid, 128, p2g_split_smem<D, O, R>(), s>>>(
@@ -1815,7 +1862,7 @@ template <typename R> struct Impl {
     }
     static cudaError_t grid_update(const HostCfg& h, const Buffers& b, const Launch& L, cudaStream_t s)
     {
-        DevCfg<R> c = HostToDev<R>::make(h, 0);
+        DevCfg<R> c = HostToDev<R>::make(h, b, 0);
         const int grid = L.sms * 8;
         if (h.dim == 3) k_grid_update<3, R><<<grid, TPB, 0, s>>>((R*)b.acc, (R*)b.vel, b.flags, c);
         else k_grid_update<2, R><<<grid, TPB, 0, s>>>((R*)b.acc, (R*)b.vel, b.flags, c);
@@ -1825,10 +1872,19 @@ template <typename R> struct Impl {
                            int64_t n, const Launch& L, cudaStream_t s)
     {
         if (n == 0) return cudaSuccess;
-        DevCfg<R> c = HostToDev<R>::make(h, n);
+        DevCfg<R> c = HostToDev<R>::make(h, b, n);
         PState<R> in = state_of<R>(b, cur), out = state_of<R>(b, cur ^ 1);
-        APIC_DISPATCH(h, (k_g2p<D, O, R><<<L.g2p_grid, TPB, 0, s>>>(in, out, perm, sk, b.tiles, b.ntiles, b.tile_ctr,
-                                                                      (const R*)b.vel, b.knext, c, b.err, b.fallbacks)));
+        if (h.mat || h.adaptive)
+            APIC_DISPATCH(h, (k_g2p<D, O, R, true><<<L.g2p_grid, TPB, 0, s>>>(in, out, perm, sk, b.tiles, b.ntiles,
+                                     b.tile_ctr, (const R*)b.vel, b.knext, c, b.err, b.fallbacks)));
+        else
+            APIC_DISPATCH(h, (k_g2p<D, O, R, false><<<L.g2p_grid, TPB, 0, s>>>(in, out, perm, sk, b.tiles, b.ntiles,
+                                     b.tile_ctr, (const R*)b.vel, b.knext, c, b.err, b.fallbacks)));
+        return cudaGetLastError();
+    }
+    static cudaError_t adapt_dt(const HostCfg& h, const Buffers& b, double nu, double dt_max, int first, cudaStream_t s)
+    {
+        k_adapt_dt<R><<<1, 1, 0, s>>>((R*)b.dt_word, b.smax_word, b.mom_out, b.elapsed, h.dx, nu, dt_max, first);
         return cudaGetLastError();
     }
     static cudaError_t set_materials(const HostCfg& h, const Buffers& b, int cur, int64_t n, const double* E,
@@ -1926,7 +1982,7 @@ template <typename R> struct Impl {
                     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g_cells<D, O2, R, APIC_P2G_GROUP>, 128,
                                                                       p2g_cells_smem<D, O2, R>());
             }
-            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(g2p_per_sm, k_g2p<D, O, R>, TPB, 0);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(g2p_per_sm, k_g2p<D, O, R, false>, TPB, 0);
         });
         return e;
     }
@@ -1950,6 +2006,11 @@ template <typename R> struct Impl {
                           const uint32_t* perm, int64_t n, const Launch& L, cudaStream_t s)                     \
     {                                                                                                           \
         return Impl<R>::g2p(c, b, cur, skeys, perm, n, L, s);                                                   \
+    }                                                                                                           \
+    cudaError_t adapt_dt_##SFX(const HostCfg& c, const Buffers& b, double nu, double dt_max, int first,        \
+                               cudaStream_t s)                                                                  \
+    {                                                                                                           \
+        return Impl<R>::adapt_dt(c, b, nu, dt_max, first, s);                                                   \
     }                                                                                                           \
     cudaError_t set_materials_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const double* E,   \
                                     const double* nu, cudaStream_t s)                                          \
