@@ -46,7 +46,7 @@ class Cfg(C.Structure):
         ("res", C.c_int * 3), ("dx", C.c_double), ("origin", C.c_double * 3),
         ("dt", C.c_double), ("gravity", C.c_double * 3),
         ("boundary", C.c_int), ("wall", C.c_int), ("model", C.c_int),
-        ("mu", C.c_double), ("lam", C.c_double), ("lambda_t", C.c_double),
+        ("mu", C.c_double), ("lam", C.c_double), ("lambda_t", C.c_double), ("flip_alpha", C.c_double),
     ]
 
 
@@ -57,10 +57,12 @@ def lame(E: float, nu: float) -> tuple[float, float]:
 
 def make_cfg(dim=3, order=2, transfer="apic", res=(16, 16, 16), dx=1.0 / 16, origin=(0, 0, 0),
              dt=0.0, gravity=(0, 0, 0), boundary="none", wall=0, model="none", E=0.0, nu=0.0,
-             lambda_t=0.0) -> Cfg:
+             lambda_t=0.0, flip_alpha=1.0) -> Cfg:
+    """transfer: "apic", "pic" or "flip" (a PIC/FLIP blend with weight flip_alpha on FLIP)."""
     c = Cfg()
     c.dim, c.order = dim, order
-    c.transfer = {"apic": 0, "pic": 1}[transfer]
+    c.transfer = {"apic": 0, "pic": 1, "flip": 2}[transfer]
+    c.flip_alpha = flip_alpha
     r = list(res) + [1] * (3 - len(res))
     c.res = (C.c_int * 3)(*r)
     c.dx = dx
@@ -256,12 +258,14 @@ def grid_update(cfg: Cfg, gm, gmv, gf):
     return gv, gvt
 
 
-def g2p(cfg: Cfg, x, F, gv, gvt):
-    """Sec. 3.4 general transfer to particles.  Returns (x, v, B, F, n_skipped)."""
+def g2p(cfg: Cfg, x, F, gv, gvt, v=None):
+    """Sec. 3.4 general transfer to particles.  Returns (x, v, B, F, n_skipped).
+    v: the particles' velocities (read by the FLIP transfer only)."""
     d = cfg.dim
     n = len(x)
     x = _f64(x, (n, d)).copy(); F = _f64(F, (n, d, d)).copy()
-    v = np.zeros((n, d)); B = np.zeros((n, d, d))
+    v = np.zeros((n, d)) if v is None else _f64(v, (n, d)).copy()
+    B = np.zeros((n, d, d))
     nn = _nodes(cfg)
     bad = _load().or_g2p(C.byref(cfg), n, _p(x), _p(v), _p(B), _p(F),
                          _p(_f64(gv, (nn, d))), _p(_f64(gvt, (nn, d))))

@@ -42,7 +42,7 @@
 typedef struct {
     int dim;            /* 2 or 3 */
     int order;          /* 2 = quadratic, 3 = cubic B-spline */
-    int transfer;       /* 0 = APIC, 1 = PIC (C_p = 0, no B on the way back) */
+    int transfer;       /* 0 = APIC, 1 = PIC (C_p = 0, no B on the way back), 2 = PIC/FLIP blend */
     int res[3];         /* grid nodes per axis */
     double dx;
     double origin[3];
@@ -53,6 +53,7 @@ typedef struct {
     int model;          /* 0 = none (transfer only), 1 = fixed-corotated, 2 = Neo-Hookean */
     double mu, lam;     /* Lame parameters */
     double lambda_t;    /* integrator family parameter lambda of Sec. 3.3 */
+    double flip_alpha;  /* transfer 2: weight of the FLIP update in a PIC/FLIP blend (1 = FLIP) */
 } or_cfg;
 
 /* ------------------------------------------------------------------ */
@@ -520,6 +521,10 @@ void or_grid_update(const or_cfg* c, const double* gm, const double* gmv, const 
  *                              + (x_i - x_p - x~_i + x_p^{n+1}) v~_i^T )   (APIC)
  * B_p^{n+1} = 0                                                            (PIC)
  * F_p^{n+1} = (I + sum_i (x~_i - x_i) (grad w_ip)^T) F_p^n
+ * FLIP (Sec. 1): the particle-to-grid transfer is PIC's, and the velocity is incremented by
+ * the interpolated grid change, v_p + sum_i w_ip (v~_i - v_i); transfer 2 blends it with the
+ * PIC velocity: v_p^{n+1} = alpha (v_p + sum_i w (v~_i - v_i)) + (1 - alpha) sum_i w v~_i,
+ * B_p^{n+1} = 0 (v holds the particles' velocities on entry).
  * x, F updated in place; v, B written.  Returns the number of skipped particles.
  */
 int64_t or_g2p(const or_cfg* c, int64_t n, double* x, double* v, double* B, double* F,
@@ -533,7 +538,7 @@ int64_t or_g2p(const or_cfg* c, int64_t n, double* x, double* v, double* B, doub
         double* xp = x + p * d;
         int base[3];
         if (or_stencil(c, xp, base, w, dw) != 0) { ++bad; continue; }
-        double xn[3] = {0, 0, 0}, vn[3] = {0, 0, 0}, G[9] = {0};
+        double xn[3] = {0, 0, 0}, vn[3] = {0, 0, 0}, dv[3] = {0, 0, 0}, G[9] = {0};
         for (int j = 0; j < ns; ++j) {
             int i[3]; double xi[3];
             stencil_node(c, base, j, i, xi);
@@ -542,9 +547,13 @@ int64_t or_g2p(const or_cfg* c, int64_t n, double* x, double* v, double* B, doub
                 double xt = xi[a] + c->dt * (lt * gv[ni * d + a] + (1.0 - lt) * gvt[ni * d + a]);
                 xn[a] += w[j] * xt;
                 vn[a] += w[j] * gvt[ni * d + a];
+                dv[a] += w[j] * (gvt[ni * d + a] - gv[ni * d + a]);
                 for (int b = 0; b < d; ++b) G[a * d + b] += (xt - xi[a]) * dw[j * d + b];
             }
         }
+        if (c->transfer == 2)
+            for (int a = 0; a < d; ++a)
+                vn[a] = c->flip_alpha * (v[p * d + a] + dv[a]) + (1.0 - c->flip_alpha) * vn[a];
         double Bn[9] = {0};
         if (c->transfer == 0) {
             for (int j = 0; j < ns; ++j) {
