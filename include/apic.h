@@ -51,7 +51,7 @@ typedef enum {
     APIC_ERR_UNSUPPORTED = 6   /* configuration the library does not implement */
 } apic_status;
 
-enum { APIC_TRANSFER_APIC = 0, APIC_TRANSFER_PIC = 1 };
+enum { APIC_TRANSFER_APIC = 0, APIC_TRANSFER_PIC = 1, APIC_TRANSFER_FLIP = 2 };
 enum { APIC_BOUNDARY_NONE = 0, APIC_BOUNDARY_STICKY = 1, APIC_BOUNDARY_SLIP = 2 };
 enum { APIC_MODEL_NONE = 0, APIC_MODEL_FIXED_COROTATED = 1, APIC_MODEL_NEOHOOKEAN = 2 };
 enum { APIC_WHERE_PARTICLES = 0, APIC_WHERE_GRID = 1 };
@@ -63,7 +63,9 @@ typedef struct {
                                 is rejected with APIC_ERR_UNSUPPORTED: the B_p transfer is
                                 unstable for it (Sec. 5.9) */
     int precision;           /* 32 or 64: arithmetic type of particle and grid state */
-    int transfer;            /* APIC_TRANSFER_APIC, or APIC_TRANSFER_PIC (C_p = 0, Sec. 5.6) */
+    int transfer;            /* APIC_TRANSFER_APIC, APIC_TRANSFER_PIC (C_p = 0, Sec. 5.6), or
+                                APIC_TRANSFER_FLIP: PIC's transfer to the grid and the FLIP
+                                velocity update of Sec. 1, blended with PIC's by flip_alpha */
     int res[3];              /* grid nodes per axis (res[2] ignored in 2-D); <= 1024 in 3-D */
     double dx;               /* grid spacing */
     double origin[3];        /* position of node 0 */
@@ -86,6 +88,10 @@ typedef struct {
                                 2 = cell-parallel, 3 = cell-interleaved, 4 = node-split
                                 (the lanes of a group share the particles and split the
                                 stencil nodes); results agree to rounding */
+    double flip_alpha;       /* APIC_TRANSFER_FLIP only: v_p <- a (v_p + sum w (v~_i - v_i)) +
+                                (1 - a) sum w v~_i, a in [0, 1] (1 = the paper's FLIP); the
+                                velocities v_i before the grid update are kept (+32 B per
+                                node); not available in batches */
 } apic_config;
 
 /* Bytes of device workspace a simulation with this config and capacity needs.
@@ -242,8 +248,9 @@ apic_status apic_batch_create(const apic_batch_config* cfg, void* workspace, siz
 apic_status apic_batch_destroy(apic_batch* batch);
 
 /* Add a simulation with n > 0 particles already uploaded.  Synchronises the simulation's
- * stream.  Errors: APIC_ERR_ARG (incompatible, empty, or already a member), APIC_ERR_OOM
- * (member, particle or block capacity), APIC_ERR_CUDA. */
+ * stream.  Errors: APIC_ERR_ARG (incompatible, empty, or already a member),
+ * APIC_ERR_UNSUPPORTED (a FLIP simulation), APIC_ERR_OOM (member, particle or block
+ * capacity), APIC_ERR_CUDA. */
 apic_status apic_batch_add(apic_batch* batch, apic_sim* sim);
 
 /* Take a simulation out; its state is current as of the last batched step.

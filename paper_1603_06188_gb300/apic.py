@@ -15,7 +15,7 @@ import numpy as np
 from . import build as _build
 
 APIC_OK, APIC_ERR_ARG, APIC_ERR_OOM, APIC_ERR_CUDA, APIC_ERR_TIMEOUT, APIC_ERR_NUMERIC, APIC_ERR_UNSUPPORTED = range(7)
-TRANSFER = {"apic": 0, "pic": 1}
+TRANSFER = {"apic": 0, "pic": 1, "flip": 2}
 BOUNDARY = {"none": 0, "sticky": 1, "slip": 2}
 MODEL = {"none": 0, "fcr": 1, "fixed_corotated": 1, "nh": 2, "neohookean": 2}
 WHERE_PARTICLES, WHERE_GRID = 0, 1
@@ -40,14 +40,15 @@ class Config(C.Structure):
         ("boundary", C.c_int), ("wall", C.c_int), ("model", C.c_int),
         ("E", C.c_double), ("nu", C.c_double),
         ("particle_mass", C.c_double), ("particle_volume", C.c_double),
-        ("tile_particles", C.c_int), ("p2g_kernel", C.c_int),
+        ("tile_particles", C.c_int), ("p2g_kernel", C.c_int), ("flip_alpha", C.c_double),
     ]
 
 
 def make_config(dim=3, order=2, precision=32, transfer="apic", res=(64, 64, 64), dx=1 / 64, origin=(0, 0, 0),
                 dt=0.0, gravity=(0, 0, 0), boundary="none", wall=0, model="none", E=0.0, nu=0.0,
-                particle_mass=1.0, particle_volume=1.0, tile_particles=0, p2g_kernel=0) -> Config:
+                particle_mass=1.0, particle_volume=1.0, tile_particles=0, p2g_kernel=0, flip_alpha=1.0) -> Config:
     c = Config()
+    c.flip_alpha = flip_alpha
     c.dim, c.order, c.precision = dim, order, precision
     c.transfer = TRANSFER[transfer] if isinstance(transfer, str) else transfer
     r = list(res) + [1] * (3 - len(res))

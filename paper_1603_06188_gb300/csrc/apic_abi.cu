@@ -67,7 +67,8 @@ apic_status fill_cfg(const apic_config* in, int64_t max_particles, HostCfg* c, s
     if (in->order == 1) { *why = "multilinear weights are not supported: the B_p transfer is unstable for them (Sec. 5.9)"; return APIC_ERR_UNSUPPORTED; }
     if (in->order != 2 && in->order != 3) { *why = "order must be 2 (quadratic) or 3 (cubic)"; return APIC_ERR_UNSUPPORTED; }
     if (in->precision != 32 && in->precision != 64) { *why = "precision must be 32 or 64"; return APIC_ERR_ARG; }
-    if (in->transfer != APIC_TRANSFER_APIC && in->transfer != APIC_TRANSFER_PIC) { *why = "unknown transfer"; return APIC_ERR_ARG; }
+    if (in->transfer != APIC_TRANSFER_APIC && in->transfer != APIC_TRANSFER_PIC && in->transfer != APIC_TRANSFER_FLIP) { *why = "unknown transfer"; return APIC_ERR_ARG; }
+    if (in->transfer == APIC_TRANSFER_FLIP && !(in->flip_alpha >= 0.0 && in->flip_alpha <= 1.0)) { *why = "flip_alpha must be in [0, 1]"; return APIC_ERR_ARG; }
     if (in->boundary < APIC_BOUNDARY_NONE || in->boundary > APIC_BOUNDARY_SLIP) { *why = "unknown boundary"; return APIC_ERR_UNSUPPORTED; }
     if (in->model < APIC_MODEL_NONE || in->model > APIC_MODEL_NEOHOOKEAN) { *why = "unknown constitutive model"; return APIC_ERR_UNSUPPORTED; }
     if (!(in->dx > 0.0)) { *why = "dx must be positive"; return APIC_ERR_ARG; }
@@ -83,6 +84,7 @@ apic_status fill_cfg(const apic_config* in, int64_t max_particles, HostCfg* c, s
     c->order = in->order;
     c->precision = in->precision;
     c->transfer = in->transfer;
+    c->flip_alpha = in->transfer == APIC_TRANSFER_FLIP ? in->flip_alpha : 0.0;
     c->nblocks = 1;
     for (int a = 0; a < 3; ++a) {
         c->res[a] = a < in->dim ? in->res[a] : 1;
@@ -127,7 +129,7 @@ struct Carve {
 // offsets of every buffer inside the workspace (relative to its base)
 struct Layout {
     size_t st[2][APIC_STATE_LANES];
-    size_t mk[2], mv[2], midx, choff, mcnt, mctl, lbs, step_words;
+    size_t mk[2], mv[2], midx, choff, mcnt, mctl, lbs, step_words, acc2, vdel;
     size_t knext, kA, kB, vA, vB, radix_counts, scan_part, tiles, chunk_cnt, ntiles, tile_ctr;
     size_t acc, vel, flags, mom_part, mom_out, err, fallbacks, staging;
     size_t staging_doubles;
@@ -173,6 +175,10 @@ Layout layout_of(const HostCfg& c)
     const size_t bn = c.dim == 3 ? 64 : 16;
     L.acc = cv.take((size_t)c.nblocks * bn * 4 * R);
     L.vel = cv.take((size_t)c.nblocks * bn * 4 * R);
+    // FLIP: PIC momentum without the force, and the grid change v~ - v (4 lanes per node each)
+    const size_t flip_bytes = c.transfer == APIC_TRANSFER_FLIP ? (size_t)c.nblocks * bn * 4 * R : 0;
+    L.acc2 = cv.take(flip_bytes);
+    L.vdel = cv.take(flip_bytes);
     L.flags = cv.take((size_t)c.nblocks * 4);
     L.mom_part = cv.take((size_t)kMomParts * 6 * 8);
     L.mom_out = cv.take(6 * 8);
@@ -333,6 +339,8 @@ apic_status apic_create(const apic_config* cfg, int64_t max_particles, void* wor
     s->b.tile_ctr = (uint32_t*)(base + L.tile_ctr);
     s->b.acc = base + L.acc;
     s->b.vel = base + L.vel;
+    s->b.acc2 = c.transfer == APIC_TRANSFER_FLIP ? base + L.acc2 : nullptr;
+    s->b.vdel = c.transfer == APIC_TRANSFER_FLIP ? base + L.vdel : nullptr;
     s->b.flags = (uint32_t*)(base + L.flags);
     s->b.mom_part = (double*)(base + L.mom_part);
     s->b.mom_out = (double*)(base + L.mom_out);
@@ -361,6 +369,8 @@ apic_status apic_create(const apic_config* cfg, int64_t max_particles, void* wor
     const size_t gbytes = (size_t)c.nblocks * bn * 4 * (c.precision == 32 ? 4 : 8);
     e = cudaMemsetAsync(s->b.acc, 0, gbytes, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->b.vel, 0, gbytes, s->stream);
+    if (e == cudaSuccess && s->b.acc2) e = cudaMemsetAsync(s->b.acc2, 0, gbytes, s->stream);
+    if (e == cudaSuccess && s->b.vdel) e = cudaMemsetAsync(s->b.vdel, 0, gbytes, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->b.flags, 0, (size_t)c.nblocks * 4, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->b.err, 0, 4, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->b.dt_word, 0, 32, s->stream);
@@ -1111,6 +1121,8 @@ apic_status apic_batch_add(apic_batch* b, apic_sim* s)
         return batch_fail(b, APIC_ERR_ARG, "dim, order and precision must match the batch");
     if (s->n <= 0) return batch_fail(b, APIC_ERR_ARG, "the simulation has no particles");
     if (s->phase != 0) return batch_fail(b, APIC_ERR_ARG, "the simulation is in the middle of a step");
+    if (s->c.transfer == APIC_TRANSFER_FLIP)
+        return batch_fail(b, APIC_ERR_UNSUPPORTED, "FLIP simulations are stepped on their own, not in batches");
     if ((int)b->members.size() >= b->max_sims) return batch_fail(b, APIC_ERR_OOM, "batch member capacity reached");
     int64_t parts = 0, blocks = 0;
     for (apic_sim* m : b->members) {

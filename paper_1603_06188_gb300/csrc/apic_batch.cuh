@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(TPB, 2) kb_g2p(SimDesc<R>* __restrict__ descs,
         const uint32_t end = tile_end(tile_sim, tile_start, t, ntiles, sim, (uint32_t)sd.c.n);
         float smax_unused = 0.0f;   // members are stepped at their fixed dt
         g2p_compute<D, ORDER, R, EXT>(sd.st[sd.cur], sd.st[sd.cur ^ 1], sd.vb[kpar], sd.kb[kpar], start, end, sd.knext, sd.c,
-                                 sd.err, sd.fallbacks, sv[buf], smax_unused);
+                                 sd.err, sd.fallbacks, sv[buf], smax_unused, nullptr);
         __syncthreads();
         phase[buf] ^= 1u;
     }

@@ -178,6 +178,16 @@ __device__ __forceinline__ void load_tau(const PState<R>& s, uint32_t k, Particl
     }
 }
 
+// the velocity alone (what the FLIP update adds to)
+template <int D, typename R>
+__device__ __forceinline__ void load_v(const PState<R>& s, uint32_t k, Particle<D, R>& p)
+{
+    const V4<R> v = ld4(s.V + k);
+    p.v[0] = v.x;
+    p.v[1] = v.y;
+    if (D == 3) p.v[D - 1] = v.z;
+}
+
 template <int D, typename R>
 __device__ __forceinline__ void load_mat(const PState<R>& s, uint32_t k, Particle<D, R>& p)
 {
@@ -233,6 +243,7 @@ template <typename R> struct DevCfg {
     const R* dtp;        // when set, the time step is read here (adaptive stepping), else dt
     uint32_t* smax;      // when set, G2P max-reduces the Sec. 4.3 particle speed here (FP32 bits)
     R cfl_coef;          // 6 sqrt(d) / dx of the Sec. 4.3 speed |v| + 6 sqrt(d)/dx |B|_F
+    R flip_alpha;        // transfer 2: weight of the FLIP update
 };
 
 // the step's time step: fixed, or the adaptive one on the device

@@ -39,6 +39,8 @@ struct Buffers {
     uint32_t* tile_ctr;          // work counters: [0] P2G, [1] G2P (zeroed with each tile list), [2] sort tiles
     void* acc;                   // accumulation grid (4 lanes per node)
     void* vel;                   // velocity grid (4 lanes per node)
+    void* acc2;                  // FLIP only: PIC momentum without the force (4 lanes per node)
+    void* vdel;                  // FLIP only: the grid change (v~ - v, m) (4 lanes per node)
     uint32_t* flags;             // active node blocks
     double* mom_part;            // per-CTA momentum partials
     double* mom_out;             // 6 doubles
@@ -59,6 +61,7 @@ struct HostCfg {
     int boundary, wall, model;
     int mat;                     // 1: per-particle Lame parameters (lane M), else mu, lam
     int adaptive;                // 1: kernels read the time step from Buffers::dt_word
+    double flip_alpha;           // transfer 2: weight of the FLIP update
     double mu, lam, mass, vol;
     int tile;                    // particles per tile (power of two)
     int p2g_kernel;              // 1 warp-segmented, 2 cell-parallel

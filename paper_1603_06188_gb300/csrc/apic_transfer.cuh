@@ -49,6 +49,7 @@ template <typename R> struct HostToDev {
         c.dtp = nullptr;
         c.smax = nullptr;
         c.cfl_coef = (R)(6.0 * sqrt((double)h.dim) / h.dx);
+        c.flip_alpha = (R)h.flip_alpha;
         return c;
     }
     // the per-simulation words of adaptive stepping: the time step and the fused speed
@@ -1171,7 +1172,8 @@ __global__ void __launch_bounds__(256) k_p2g_interleaved(PState<R> st, const uin
 // one node block of the grid update, by one warp
 template <int D, typename R>
 __device__ __forceinline__ void grid_update_block(R* __restrict__ acc, R* __restrict__ vel,
-                                                  uint32_t* __restrict__ flags, const DevCfg<R>& c, int b, int lane)
+                                                  uint32_t* __restrict__ flags, const DevCfg<R>& c, int b, int lane,
+                                                  R* __restrict__ acc2 = nullptr, R* __restrict__ vdel = nullptr)
 {
     constexpr int BN = (D == 3) ? 64 : 16;
     if (flags[b] == 0u) return;
@@ -1206,6 +1208,18 @@ __device__ __forceinline__ void grid_update_block(R* __restrict__ acc, R* __rest
         }
         *reinterpret_cast<V4<R>*>(vel + 4 * node) = V4<R>{v[0], v[1], v[2], m};
         *reinterpret_cast<V4<R>*>(acc + 4 * node) = V4<R>{R(0), R(0), R(0), R(0)};
+        if (acc2) {   // FLIP: the change v~ - v against the velocity before the update
+            const V4<R> a2 = *reinterpret_cast<const V4<R>*>(acc2 + 4 * node);
+            R dv[3] = {R(0), R(0), R(0)};
+            if (m > R(0)) {
+                const R inv = R(1) / m;
+                dv[0] = v[0] - a2.x * inv;
+                dv[1] = v[1] - a2.y * inv;
+                if (D == 3) dv[2] = v[2] - a2.z * inv;
+            }
+            *reinterpret_cast<V4<R>*>(vdel + 4 * node) = V4<R>{dv[0], dv[1], dv[2], m};
+            *reinterpret_cast<V4<R>*>(acc2 + 4 * node) = V4<R>{R(0), R(0), R(0), R(0)};
+        }
     }
     __syncwarp();
     if (lane == 0) flags[b] = 0u;
@@ -1213,13 +1227,13 @@ __device__ __forceinline__ void grid_update_block(R* __restrict__ acc, R* __rest
 
 template <int D, typename R>
 __global__ void __launch_bounds__(TPB) k_grid_update(R* __restrict__ acc, R* __restrict__ vel,
-                                                     uint32_t* __restrict__ flags, DevCfg<R> c)
+                                                     uint32_t* __restrict__ flags, DevCfg<R> c, R* acc2, R* vdel)
 {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * TPB + threadIdx.x) >> 5;
     const int nw = (gridDim.x * TPB) >> 5;
     if (c.smax && blockIdx.x == 0 && threadIdx.x == 0) *c.smax = 0u;   // G2P, next, max-reduces into it
-    for (int b = gw; b < c.nblocks; b += nw) grid_update_block<D, R>(acc, vel, flags, c, b, lane);
+    for (int b = gw; b < c.nblocks; b += nw) grid_update_block<D, R>(acc, vel, flags, c, b, lane, acc2, vdel);
 }
 
 // ---------------------------------------------------------------- mbarrier + bulk copy
@@ -1316,13 +1330,14 @@ __device__ __forceinline__ bool g2p_wait(uint64_t* mbar, unsigned parity, uint32
 }
 
 // the particles of one tile, with its grid blocks already in sv (whole CTA)
-// EXT: the material lane and the fused speed maximum may be in use (else compiled out)
+// EXT: the material lane, the fused speed maximum and the FLIP update may be in use (else
+// compiled out)
 template <int D, int ORDER, typename R, bool EXT>
 __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>& out, const uint32_t* __restrict__ perm,
                                             const uint32_t* __restrict__ skeys, uint32_t start, uint32_t end,
                                             uint32_t* __restrict__ knext, const DevCfg<R>& c, uint32_t* err,
                                             uint32_t* fallbacks, const R (*sv)[(D == 3) ? 64 : 16][4],
-                                            float& smax_l)
+                                            float& smax_l, const R* __restrict__ vdel)
 {
     constexpr int K = ORDER + 1;
     const R dt_dx = step_dt(c) * c.inv_dx;
@@ -1336,6 +1351,7 @@ __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>
         const uint32_t q0 = perm[start + threadIdx.x];
         load_xF<D, R>(in, q0, nxt);
         if (EXT && c.mat) load_mat<D, R>(in, q0, nxt);
+        if (EXT && c.transfer == 2) load_v<D, R>(in, q0, nxt);
     }
     uint32_t qn = (start + threadIdx.x + TPB < end) ? perm[start + threadIdx.x + TPB] : 0u;
     for (uint32_t k0 = start; k0 < end; k0 += TPB) {
@@ -1345,6 +1361,7 @@ __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>
         if (k + TPB < end) {
             load_xF<D, R>(in, qn, nxt);
             if (EXT && c.mat) load_mat<D, R>(in, qn, nxt);
+            if (EXT && c.transfer == 2) load_v<D, R>(in, qn, nxt);
         }
         if (k + 2 * TPB < end) qn = perm[k + 2 * TPB];
         int base[D], lb[D];
@@ -1454,9 +1471,32 @@ __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>
             p.F[i] = Fn[i];
             p.B[i] = (c.transfer == 0) ? c.dx * Bh[i] : R(0);
         }
+        R vnew[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) vnew[a] = vp[a];
+        if (EXT && c.transfer == 2) {
+            // FLIP (Sec. 1): the particle's own velocity plus the interpolated grid change
+            // v~_i - v_i, blended with the PIC velocity by flip_alpha
+            R dv[3] = {R(0), R(0), R(0)};
+#pragma unroll
+            for (int ia = 0; ia < K; ++ia)
+#pragma unroll
+                for (int ib = 0; ib < K; ++ib)
+#pragma unroll
+                    for (int ic = 0; ic < ((D == 3) ? K : 1); ++ic) {
+                        int g[3] = {base[0] + ia, base[1] + ib, (D == 3) ? base[D - 1] + ic : 0};
+                        const V4<R> d4 = ld4(reinterpret_cast<const V4<R>*>(vdel) + node_index<D>(g, c.nb));
+                        const R wt = w[0][ia] * w[1][ib] * ((D == 3) ? w[D - 1][ic] : R(1));
+                        dv[0] += wt * d4.x;
+                        dv[1] += wt * d4.y;
+                        dv[2] += wt * d4.z;
+                    }
+#pragma unroll
+            for (int a = 0; a < D; ++a) vnew[a] = c.flip_alpha * (p.v[a] + dv[a]) + (R(1) - c.flip_alpha) * vp[a];
+        }
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            p.v[a] = vp[a];
+            p.v[a] = vnew[a];
             R o = p.o[a] + dt_dx * vp[a];
             const R fl = floor(o);
             o -= fl;
@@ -1490,7 +1530,7 @@ __global__ void __launch_bounds__(TPB, 2) k_g2p(PState<R> in, PState<R> out, con
                                              const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ tiles,
                                              const uint32_t* __restrict__ ntiles_p, uint32_t* __restrict__ tile_ctr,
                                              const R* __restrict__ vel, uint32_t* __restrict__ knext, DevCfg<R> c,
-                                             uint32_t* err, uint32_t* fallbacks)
+                                             uint32_t* err, uint32_t* fallbacks, const R* __restrict__ vdel)
 {
     constexpr int BN = (D == 3) ? 64 : 16;
     constexpr int NB = 1 << D;
@@ -1526,7 +1566,7 @@ __global__ void __launch_bounds__(TPB, 2) k_g2p(PState<R> in, PState<R> out, con
         __syncthreads();
         if (!s_ok) return;
         g2p_compute<D, ORDER, R, EXT>(in, out, perm, skeys, tiles[t], tiles[t + 1], knext, c, err, fallbacks, sv[buf],
-                                      smax_l);
+                                      smax_l, vdel);
         __syncthreads();
         phase[buf] ^= 1u;
     }
@@ -1832,40 +1872,53 @@ template <typename R> struct Impl {
                            int64_t n, const Launch& L, cudaStream_t s)
     {
         if (n == 0) return cudaSuccess;
-        DevCfg<R> c = HostToDev<R>::make(h, b, n);
+        const DevCfg<R> c0 = HostToDev<R>::make(h, b, n);
         PState<R> st = state_of<R>(b, cur);
+        auto launch = [&](const DevCfg<R>& c, R* acc) {
         if (h.p2g_kernel == 4)
             APIC_DISPATCH(h, (k_p2g_split<D, O, R><<<L.p2g_grid, 128, p2g_split_smem<D, O, R>(), s>>>(
-                                 st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc, b.flags, c, b.err)));
+                                 st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc, b.flags, c, b.err)));
         else if (h.p2g_kernel == 3)
             APIC_DISPATCH(h, (k_p2g_interleaved<D, O, R><<<L.p2g_grid, 256, 0, s>>>(
-                                 st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc, b.flags, c, b.err, b.fallbacks)));
+                                 st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc, b.flags, c, b.err, b.fallbacks)));
         else if (!L.p2g_cells)
-            APIC_DISPATCH(h, (k_p2g<D, O, R><<<L.p2g_grid, TPB, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, (R*)b.acc,
+            APIC_DISPATCH(h, (k_p2g<D, O, R><<<L.p2g_grid, TPB, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, acc,
                                                                           b.flags, c, b.err, b.fallbacks)));
         else if (h.dim == 3 && h.order == 2)
-            k_p2g_cells<3, 2, R, APIC_P2G_GROUP><<<L.p2g_grid, 128, p2g_cells_smem<3, 2, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc,
+            k_p2g_cells<3, 2, R, APIC_P2G_GROUP><<<L.p2g_grid, 128, p2g_cells_smem<3, 2, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc,
                                                                 b.flags, c, b.err, b.fallbacks);
         else if (h.dim == 2 && h.order == 2)
-            k_p2g_cells<2, 2, R, APIC_P2G_GROUP><<<L.p2g_grid, 128, p2g_cells_smem<2, 2, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc,
+            k_p2g_cells<2, 2, R, APIC_P2G_GROUP><<<L.p2g_grid, 128, p2g_cells_smem<2, 2, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc,
                                                                 b.flags, c, b.err, b.fallbacks);
         else if (h.dim == 2 && h.order == 3)
-            k_p2g_cells<2, 3, R, APIC_P2G_GROUP><<<L.p2g_grid, 128, p2g_cells_smem<2, 3, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc,
+            k_p2g_cells<2, 3, R, APIC_P2G_GROUP><<<L.p2g_grid, 128, p2g_cells_smem<2, 3, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc,
                                                                 b.flags, c, b.err, b.fallbacks);
         else if (h.dim == 3 && h.order == 3)
-            k_p2g_cells<3, 3, R, APIC_P2G_GROUP><<<L.p2g_grid, 128, p2g_cells_smem<3, 3, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, (R*)b.acc,
+            k_p2g_cells<3, 3, R, APIC_P2G_GROUP><<<L.p2g_grid, 128, p2g_cells_smem<3, 3, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc,
                                                                 b.flags, c, b.err, b.fallbacks);
         else
-            k_p2g<3, 3, R><<<L.p2g_grid, TPB, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, (R*)b.acc, b.flags, c, b.err,
+            k_p2g<3, 3, R><<<L.p2g_grid, TPB, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, acc, b.flags, c, b.err,
                                                       b.fallbacks);
         return cudaGetLastError();
+        };
+        cudaError_t e = launch(c0, (R*)b.acc);
+        if (e == cudaSuccess && h.transfer == 2) {
+            // FLIP keeps the grid velocity before the update: a second pass sums the PIC
+            // momentum alone (no stress, no affine term) into acc2
+            DevCfg<R> c2 = c0;
+            c2.model = 0;
+            c2.transfer = 1;
+            e = cudaMemsetAsync(b.tile_ctr, 0, sizeof(uint32_t), s);
+            if (e == cudaSuccess) e = launch(c2, (R*)b.acc2);
+        }
+        return e;
     }
     static cudaError_t grid_update(const HostCfg& h, const Buffers& b, const Launch& L, cudaStream_t s)
     {
         DevCfg<R> c = HostToDev<R>::make(h, b, 0);
         const int grid = L.sms * 8;
-        if (h.dim == 3) k_grid_update<3, R><<<grid, TPB, 0, s>>>((R*)b.acc, (R*)b.vel, b.flags, c);
-        else k_grid_update<2, R><<<grid, TPB, 0, s>>>((R*)b.acc, (R*)b.vel, b.flags, c);
+        if (h.dim == 3) k_grid_update<3, R><<<grid, TPB, 0, s>>>((R*)b.acc, (R*)b.vel, b.flags, c, (R*)b.acc2, (R*)b.vdel);
+        else k_grid_update<2, R><<<grid, TPB, 0, s>>>((R*)b.acc, (R*)b.vel, b.flags, c, (R*)b.acc2, (R*)b.vdel);
         return cudaGetLastError();
     }
     static cudaError_t g2p(const HostCfg& h, const Buffers& b, int cur, const uint32_t* sk, const uint32_t* perm,
@@ -1874,12 +1927,12 @@ template <typename R> struct Impl {
         if (n == 0) return cudaSuccess;
         DevCfg<R> c = HostToDev<R>::make(h, b, n);
         PState<R> in = state_of<R>(b, cur), out = state_of<R>(b, cur ^ 1);
-        if (h.mat || h.adaptive)
+        if (h.mat || h.adaptive || h.transfer == 2)
             APIC_DISPATCH(h, (k_g2p<D, O, R, true><<<L.g2p_grid, TPB, 0, s>>>(in, out, perm, sk, b.tiles, b.ntiles,
-                                     b.tile_ctr, (const R*)b.vel, b.knext, c, b.err, b.fallbacks)));
+                                     b.tile_ctr, (const R*)b.vel, b.knext, c, b.err, b.fallbacks, (const R*)b.vdel)));
         else
             APIC_DISPATCH(h, (k_g2p<D, O, R, false><<<L.g2p_grid, TPB, 0, s>>>(in, out, perm, sk, b.tiles, b.ntiles,
-                                     b.tile_ctr, (const R*)b.vel, b.knext, c, b.err, b.fallbacks)));
+                                     b.tile_ctr, (const R*)b.vel, b.knext, c, b.err, b.fallbacks, nullptr)));
         return cudaGetLastError();
     }
     static cudaError_t adapt_dt(const HostCfg& h, const Buffers& b, double nu, double dt_max, int first, cudaStream_t s)
