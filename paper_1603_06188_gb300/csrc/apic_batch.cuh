@@ -156,18 +156,33 @@ template <int D, typename R>
 __global__ void __launch_bounds__(TPB) kb_grid_update(SimDesc<R>* __restrict__ descs, const uint32_t* __restrict__ bbase,
                                                       int nsims, uint32_t total_blocks)
 {
+    // a warp takes 32 consecutive blocks: each lane finds its block's simulation and flag,
+    // then the warp updates the flagged ones (most blocks of sparse grids are not)
     const int lane = threadIdx.x & 31;
     const uint32_t gw = (blockIdx.x * TPB + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * TPB) >> 5;
-    for (uint32_t gb = gw; gb < total_blocks; gb += nw) {
-        int lo = 0, hi = nsims - 1;   // last s with bbase[s] <= gb
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (bbase[mid] <= gb) lo = mid;
-            else hi = mid - 1;
+    for (uint32_t g0 = gw * 32u; g0 < total_blocks; g0 += nw * 32u) {
+        const uint32_t gb = g0 + (uint32_t)lane;
+        int sim = 0;
+        bool on = false;
+        if (gb < total_blocks) {
+            int lo = 0, hi = nsims - 1;   // last s with bbase[s] <= gb
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (bbase[mid] <= gb) lo = mid;
+                else hi = mid - 1;
+            }
+            sim = lo;
+            on = descs[sim].flags[gb - bbase[sim]] != 0u;
         }
-        const SimDesc<R>& d = descs[lo];
-        grid_update_block<D, R>(d.acc, d.vel, d.flags, d.c, (int)(gb - bbase[lo]), lane);
+        unsigned todo = __ballot_sync(FULLMASK, on);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const int s2 = __shfl_sync(FULLMASK, sim, src);
+            const SimDesc<R>& d = descs[s2];
+            grid_update_block<D, R>(d.acc, d.vel, d.flags, d.c, (int)(g0 + (uint32_t)src - bbase[s2]), lane);
+        }
     }
 }
 

@@ -398,7 +398,7 @@ __device__ __forceinline__ void read_staged(const R* slot, Particle<D, R>& p, bo
 }
 
 // staging depth (particles in flight per lane) of the cell-parallel P2G
-template <typename R> __host__ __device__ constexpr int p2g_slots() { return sizeof(R) == 4 ? 3 : 2; }
+template <typename R> __host__ __device__ constexpr int p2g_slots() { return 2; }
 
 template <int D, int ORDER, typename R> __host__ __device__ constexpr size_t p2g_cellsum_bytes()
 {
@@ -1608,31 +1608,36 @@ template <int D, typename R>
 __global__ void __launch_bounds__(TPB) k_mom_particles(PState<R> st, DevCfg<R> c, double mass, double dx,
                                                        double o0, double o1, double o2, double* part)
 {
+    // each particle's terms in the state's precision (FP64 arithmetic is slow on this part
+    // and adds nothing to FP32 state), their sums in FP64
     double a[6] = {0, 0, 0, 0, 0, 0};
-    const double org[3] = {o0, o1, o2};
+    const R org[3] = {(R)o0, (R)o1, (R)o2};
+    const R ms = (R)mass, h = (R)dx;
     for (int k = blockIdx.x * TPB + threadIdx.x; k < c.n; k += gridDim.x * TPB) {
         Particle<D, R> p;
-        load_xF<D, R>(st, k, p);
+        load_x<D, R>(st, k, p);
         load_vB<D, R>(st, k, p);
-        double x[3] = {0, 0, 0}, v[3] = {0, 0, 0};
+        R x[3] = {R(0), R(0), R(0)}, v[3] = {R(0), R(0), R(0)};
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-            x[d] = org[d] + ((double)p.cell[d] + (double)p.o[d]) * dx;
-            v[d] = mass * (double)p.v[d];
-            a[d] += v[d];
+            x[d] = org[d] + ((R)p.cell[d] + p.o[d]) * h;
+            v[d] = ms * p.v[d];
+            a[d] += (double)v[d];
         }
         if (D == 3) {
-            a[3] += x[1] * v[2] - x[2] * v[1];
-            a[4] += x[2] * v[0] - x[0] * v[2];
-            a[5] += x[0] * v[1] - x[1] * v[0];
+            R l[3] = {x[1] * v[2] - x[2] * v[1], x[2] * v[0] - x[0] * v[2], x[0] * v[1] - x[1] * v[0]};
             if (c.transfer == 0) {
-                a[3] += mass * ((double)p.B[7] - (double)p.B[5]);
-                a[4] += mass * ((double)p.B[2] - (double)p.B[6]);
-                a[5] += mass * ((double)p.B[3] - (double)p.B[1]);
+                l[0] += ms * (p.B[7] - p.B[5]);
+                l[1] += ms * (p.B[2] - p.B[6]);
+                l[2] += ms * (p.B[3] - p.B[1]);
             }
+            a[3] += (double)l[0];
+            a[4] += (double)l[1];
+            a[5] += (double)l[2];
         } else {
-            a[3] += x[0] * v[1] - x[1] * v[0];
-            if (c.transfer == 0) a[3] += mass * ((double)p.B[2] - (double)p.B[1]);
+            R l = x[0] * v[1] - x[1] * v[0];
+            if (c.transfer == 0) l += ms * (p.B[2] - p.B[1]);
+            a[3] += (double)l;
         }
     }
     block_sum6(a, part);
