@@ -490,6 +490,16 @@ __device__ __forceinline__ void tile_flush(const R* cellsum, const uint32_t* cbe
     constexpr int NS = (D == 3) ? K * K * K : K * K;
     constexpr int NV = D + 1;
     constexpr int NVAL = NS * NV;
+    // the tile's occupied cells as a bit mask (one register): a cell test is then a shift
+    // instead of two shared-memory loads (most tests of a sparse tile fail)
+    __shared__ uint32_t s_occ[2];
+    if (threadIdx.x < 64) {   // two whole warps
+        const bool o = threadIdx.x < ((D == 3) ? 64 : 16) && cbeg[threadIdx.x] < cend[threadIdx.x];
+        const unsigned bits = __ballot_sync(0xffffffffu, o);
+        if ((threadIdx.x & 31) == 0) s_occ[threadIdx.x >> 5] = bits;
+    }
+    __syncthreads();
+    const uint64_t occ = (uint64_t)s_occ[0] | ((uint64_t)s_occ[1] << 32);
         for (int i = threadIdx.x; i < TN; i += nt) {
             const int n0 = i % TE, n1 = (i / TE) % TE, n2 = (D == 3) ? i / (TE * TE) : 0;
             R sum[NV];
@@ -501,7 +511,7 @@ __device__ __forceinline__ void tile_flush(const R* cellsum, const uint32_t* cbe
                 const int c0 = n0 - ia, c1 = n1 - ib, c2 = (D == 3) ? n2 - ic : 0;
                 if (c0 < 0 || c0 > 3 || c1 < 0 || c1 > 3 || c2 < 0 || c2 > 3) continue;
                 const int cl = c0 | (c1 << 2) | (c2 << 4);
-                if (cbeg[cl] >= cend[cl]) continue;
+                if (!((occ >> cl) & 1ull)) continue;
                 const R* src = cellsum + (size_t)cl * NVAL + j * NV;
 #pragma unroll
                 for (int v = 0; v < NV; ++v) sum[v] += src[v];
