@@ -232,7 +232,7 @@ typedef struct {
     int64_t max_particles;       /* total particles over the members */
     int64_t max_blocks;          /* total node blocks (4^d nodes) over the members' grids */
     int tile_particles;          /* 1024, 2048 or 4096 particles per tile; 0 = 4096 */
-    int group;                   /* lanes sharing one cell in P2G: 2, 4 or 8; 0 = 8 */
+    int group;                   /* lanes sharing one cell in P2G: 1, 2, 4 or 8; 0 = 8 */
     int use_graph;               /* 1 = replay each step as a captured CUDA graph (needs a
                                     non-NULL stream) */
 } apic_batch_config;
@@ -265,7 +265,7 @@ apic_status apic_batch_step(apic_batch* batch, int n);
 apic_status apic_batch_set_tuning(apic_batch* batch, int tile_particles, int group);
 
 /* Autotuner: times `steps` batched steps for every candidate (tile 1024 / 2048 / 4096 x
- * group 2 / 4 / 8), keeps the fastest and reports it.  The trial steps are real steps of the
+ * group 1 / 2 / 4 / 8), keeps the fastest and reports it.  The trial steps are real steps of the
  * members.  Results are cached per (dim, order, precision, particle-count bucket) for the
  * life of the process; force = 1 re-measures.  Synchronising. */
 apic_status apic_batch_autotune(apic_batch* batch, int steps, int force, int* tile_particles, int* group);

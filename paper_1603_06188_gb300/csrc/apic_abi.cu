@@ -1050,7 +1050,7 @@ apic_status apic_batch_create(const apic_batch_config* c, void* workspace, size_
     const int tile = c->tile_particles == 0 ? 4096 : c->tile_particles;
     if (tile != 1024 && tile != 2048 && tile != 4096) return APIC_ERR_ARG;
     const int group = c->group == 0 ? 8 : c->group;
-    if (group != 2 && group != 4 && group != 8) return APIC_ERR_ARG;
+    if (group != 1 && group != 2 && group != 4 && group != 8) return APIC_ERR_ARG;
     if (!workspace || ((uintptr_t)workspace & 255)) return APIC_ERR_ARG;
     BatchLayout L = batch_layout(c);
     if (workspace_bytes < L.total) return APIC_ERR_OOM;
@@ -1186,7 +1186,7 @@ apic_status apic_batch_set_tuning(apic_batch* b, int tile, int group)
 {
     if (!b) return APIC_ERR_ARG;
     if (tile != 0 && tile != 1024 && tile != 2048 && tile != 4096) return APIC_ERR_ARG;
-    if (group != 0 && group != 2 && group != 4 && group != 8) return APIC_ERR_ARG;
+    if (group != 0 && group != 1 && group != 2 && group != 4 && group != 8) return APIC_ERR_ARG;
     if (tile) b->tile = tile;
     if (group) b->group = group;
     b->dirty = true;
@@ -1217,7 +1217,7 @@ apic_status apic_batch_autotune(apic_batch* b, int steps, int force, int* tile_o
     BCK(cudaEventCreate(&e1), "event");
     float best = 1e30f;
     int bt = b->tile, bg = b->group;
-    const int groups[3] = {2, 4, 8};
+    const int groups[4] = {1, 2, 4, 8};
     for (int tile : kBatchTiles)
         for (int group : groups) {
             apic_batch_set_tuning(b, tile, group);

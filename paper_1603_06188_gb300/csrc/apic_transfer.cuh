@@ -1342,7 +1342,7 @@ __device__ __forceinline__ bool g2p_wait(uint64_t* mbar, unsigned parity, uint32
 // the particles of one tile, with its grid blocks already in sv (whole CTA)
 // EXT: the material lane, the fused speed maximum and the FLIP update may be in use (else
 // compiled out)
-template <int D, int ORDER, typename R, bool EXT>
+template <int D, int ORDER, typename R, bool EXT, int NTH = TPB>
 __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>& out, const uint32_t* __restrict__ perm,
                                             const uint32_t* __restrict__ skeys, uint32_t start, uint32_t end,
                                             uint32_t* __restrict__ knext, const DevCfg<R>& c, uint32_t* err,
@@ -1363,17 +1363,17 @@ __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>
         if (EXT && c.mat) load_mat<D, R>(in, q0, nxt);
         if (EXT && c.transfer == 2) load_v<D, R>(in, q0, nxt);
     }
-    uint32_t qn = (start + threadIdx.x + TPB < end) ? perm[start + threadIdx.x + TPB] : 0u;
-    for (uint32_t k0 = start; k0 < end; k0 += TPB) {
+    uint32_t qn = (start + threadIdx.x + NTH < end) ? perm[start + threadIdx.x + NTH] : 0u;
+    for (uint32_t k0 = start; k0 < end; k0 += NTH) {
         const uint32_t k = k0 + threadIdx.x;
         if (k >= end) continue;
         Particle<D, R> p = nxt;
-        if (k + TPB < end) {
+        if (k + NTH < end) {
             load_xF<D, R>(in, qn, nxt);
             if (EXT && c.mat) load_mat<D, R>(in, qn, nxt);
             if (EXT && c.transfer == 2) load_v<D, R>(in, qn, nxt);
         }
-        if (k + 2 * TPB < end) qn = perm[k + 2 * TPB];
+        if (k + 2 * NTH < end) qn = perm[k + 2 * NTH];
         int base[D], lb[D];
         R w[D][K], dw[D][K], fx[D];
         bool ok = particle_stencil<D, ORDER, R>(p.o, p.cell, c, base, fx, w, dw);
