@@ -97,12 +97,8 @@ __global__ void __launch_bounds__(128, 2) kb_p2g_cells(SimDesc<R>* __restrict__ 
     }
 }
 
-// 128-thread CTAs: the batched mix's tiles are small (a few hundred particles), so fewer
-// threads per tile idle less at the per-tile barriers
-constexpr int KB_G2P_THREADS = 128;
-
 template <int D, int ORDER, typename R, bool EXT>
-__global__ void __launch_bounds__(KB_G2P_THREADS, 4) kb_g2p(SimDesc<R>* __restrict__ descs, const uint32_t* __restrict__ tile_sim,
+__global__ void __launch_bounds__(G2P_THREADS, 4) kb_g2p(SimDesc<R>* __restrict__ descs, const uint32_t* __restrict__ tile_sim,
                                               const uint32_t* __restrict__ tile_start,
                                               const uint32_t* __restrict__ ntiles_p, uint32_t* __restrict__ tile_ctr,
                                               int kpar)
@@ -134,7 +130,7 @@ __global__ void __launch_bounds__(KB_G2P_THREADS, 4) kb_g2p(SimDesc<R>* __restri
         const int t = s_t[buf];
         if (t >= ntiles) break;
         const uint32_t sim = tile_sim[t];
-        load_desc<R>(&sd, descs + sim, KB_G2P_THREADS);
+        load_desc<R>(&sd, descs + sim, G2P_THREADS);
         if (threadIdx.x == 0) {
             const int t1 = (int)atomicAdd(tile_ctr + 1, 1u);
             s_t[buf ^ 1] = t1;
@@ -148,7 +144,7 @@ __global__ void __launch_bounds__(KB_G2P_THREADS, 4) kb_g2p(SimDesc<R>* __restri
         const uint32_t start = tile_start[t];
         const uint32_t end = tile_end(tile_sim, tile_start, t, ntiles, sim, (uint32_t)sd.c.n);
         float smax_unused = 0.0f;   // members are stepped at their fixed dt
-        g2p_compute<D, ORDER, R, EXT, KB_G2P_THREADS>(sd.st[sd.cur], sd.st[sd.cur ^ 1], sd.vb[kpar], sd.kb[kpar], start, end, sd.knext, sd.c,
+        g2p_compute<D, ORDER, R, EXT, G2P_THREADS>(sd.st[sd.cur], sd.st[sd.cur ^ 1], sd.vb[kpar], sd.kb[kpar], start, end, sd.knext, sd.c,
                                  sd.err, sd.fallbacks, sv[buf], smax_unused, nullptr);
         __syncthreads();
         phase[buf] ^= 1u;
@@ -202,7 +198,7 @@ template <typename R> struct BatchImpl {
         const int smem = (int)p2g_cells_smem<D, O, R>();
         cudaError_t e = cudaFuncSetAttribute(kb_p2g_cells<D, O, R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, kb_p2g_cells<D, O, R, G>, 128, smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(g2p_per_sm, kb_g2p<D, O, R, false>, KB_G2P_THREADS, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(g2p_per_sm, kb_g2p<D, O, R, false>, G2P_THREADS, 0);
         return e;
     }
     // lane groups of 1, 2, 4 or 8 per base cell (fewer lanes suit fewer particles per cell)
@@ -257,8 +253,8 @@ template <typename R> struct BatchImpl {
     static void g2p_one(int ext, SimDesc<R>* d, const uint32_t* ts, const uint32_t* tst, const uint32_t* nt,
                         uint32_t* ctr, int kpar, int grid, cudaStream_t s)
     {
-        if (ext) kb_g2p<D, O, R, true><<<grid, KB_G2P_THREADS, 0, s>>>(d, ts, tst, nt, ctr, kpar);
-        else kb_g2p<D, O, R, false><<<grid, KB_G2P_THREADS, 0, s>>>(d, ts, tst, nt, ctr, kpar);
+        if (ext) kb_g2p<D, O, R, true><<<grid, G2P_THREADS, 0, s>>>(d, ts, tst, nt, ctr, kpar);
+        else kb_g2p<D, O, R, false><<<grid, G2P_THREADS, 0, s>>>(d, ts, tst, nt, ctr, kpar);
     }
     static cudaError_t g2p(int dim, int order, int ext, void* descs, const uint32_t* ts, const uint32_t* tst,
                            const uint32_t* nt, uint32_t* ctr, int kpar, int grid, cudaStream_t s)

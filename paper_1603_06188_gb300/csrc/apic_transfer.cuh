@@ -1535,8 +1535,13 @@ __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>
     }
 }
 
+// G2P runs in 128-thread CTAs (four per SM): a tile's particles then take more rounds per
+// thread and fewer threads idle at the per-tile barriers (0.226 vs 0.238 ms with 256 on the
+// 128^3 cube; batches of small tiles gain more)
+constexpr int G2P_THREADS = 128;
+
 template <int D, int ORDER, typename R, bool EXT>
-__global__ void __launch_bounds__(TPB, 2) k_g2p(PState<R> in, PState<R> out, const uint32_t* __restrict__ perm,
+__global__ void __launch_bounds__(G2P_THREADS, 4) k_g2p(PState<R> in, PState<R> out, const uint32_t* __restrict__ perm,
                                              const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ tiles,
                                              const uint32_t* __restrict__ ntiles_p, uint32_t* __restrict__ tile_ctr,
                                              const R* __restrict__ vel, uint32_t* __restrict__ knext, DevCfg<R> c,
@@ -1575,7 +1580,7 @@ __global__ void __launch_bounds__(TPB, 2) k_g2p(PState<R> in, PState<R> out, con
         }
         __syncthreads();
         if (!s_ok) return;
-        g2p_compute<D, ORDER, R, EXT>(in, out, perm, skeys, tiles[t], tiles[t + 1], knext, c, err, fallbacks, sv[buf],
+        g2p_compute<D, ORDER, R, EXT, G2P_THREADS>(in, out, perm, skeys, tiles[t], tiles[t + 1], knext, c, err, fallbacks, sv[buf],
                                       smax_l, vdel);
         __syncthreads();
         phase[buf] ^= 1u;
@@ -1943,10 +1948,10 @@ template <typename R> struct Impl {
         DevCfg<R> c = HostToDev<R>::make(h, b, n);
         PState<R> in = state_of<R>(b, cur), out = state_of<R>(b, cur ^ 1);
         if (h.mat || h.adaptive || h.transfer == 2)
-            APIC_DISPATCH(h, (k_g2p<D, O, R, true><<<L.g2p_grid, TPB, 0, s>>>(in, out, perm, sk, b.tiles, b.ntiles,
+            APIC_DISPATCH(h, (k_g2p<D, O, R, true><<<L.g2p_grid, G2P_THREADS, 0, s>>>(in, out, perm, sk, b.tiles, b.ntiles,
                                      b.tile_ctr, (const R*)b.vel, b.knext, c, b.err, b.fallbacks, (const R*)b.vdel)));
         else
-            APIC_DISPATCH(h, (k_g2p<D, O, R, false><<<L.g2p_grid, TPB, 0, s>>>(in, out, perm, sk, b.tiles, b.ntiles,
+            APIC_DISPATCH(h, (k_g2p<D, O, R, false><<<L.g2p_grid, G2P_THREADS, 0, s>>>(in, out, perm, sk, b.tiles, b.ntiles,
                                      b.tile_ctr, (const R*)b.vel, b.knext, c, b.err, b.fallbacks, nullptr)));
         return cudaGetLastError();
     }
@@ -2050,7 +2055,7 @@ template <typename R> struct Impl {
                     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g_cells<D, O2, R, APIC_P2G_GROUP>, 128,
                                                                       p2g_cells_smem<D, O2, R>());
             }
-            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(g2p_per_sm, k_g2p<D, O, R, false>, TPB, 0);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(g2p_per_sm, k_g2p<D, O, R, false>, G2P_THREADS, 0);
         });
         return e;
     }
