@@ -228,7 +228,7 @@ typedef struct apic_batch apic_batch;
 
 typedef struct {
     int dim, order, precision;   /* shared by every member */
-    int max_sims;                /* member capacity */
+    int max_sims;                /* member capacity, 1..12000 */
     int64_t max_particles;       /* total particles over the members */
     int64_t max_blocks;          /* total node blocks (4^d nodes) over the members' grids */
     int tile_particles;          /* 1024, 2048 or 4096 particles per tile; 0 = 4096 */

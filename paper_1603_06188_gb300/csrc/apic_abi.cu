@@ -792,8 +792,8 @@ struct apic_batch {
     // workspace
     void* descs;
     SortDesc* sortdescs;
-    uint32_t *rt_sim, *ch_sim, *bbase, *counts, *scan_part, *chunk_cnt, *tile_sim, *tile_start, *ntiles, *tile_ctr, *err,
-        *digits;
+    uint32_t *rt_sim, *ch_sim, *bbase, *scan_part, *chunk_cnt, *tile_sim, *tile_start, *ntiles, *tile_ctr, *err,
+        *bsorted, *bctl;
     int64_t max_rtiles, max_chunks, max_tiles;
     size_t desc_bytes;
     // membership
@@ -816,8 +816,8 @@ namespace {
 constexpr int kBatchTiles[3] = {1024, 2048, 4096};
 
 struct BatchLayout {
-    size_t descs, sortdescs, rt_sim, ch_sim, bbase, counts, scan_part, chunk_cnt, tile_sim, tile_start, ntiles, tile_ctr,
-        err, digits, total;
+    size_t descs, sortdescs, rt_sim, ch_sim, bbase, scan_part, chunk_cnt, tile_sim, tile_start, ntiles, tile_ctr,
+        err, bsorted, bctl, total;
     int64_t max_rtiles, max_chunks, max_tiles;
 };
 
@@ -834,8 +834,7 @@ BatchLayout batch_layout(const apic_batch_config* c)
     L.rt_sim = cv.take((size_t)L.max_rtiles * 4);
     L.ch_sim = cv.take((size_t)L.max_chunks * 4);
     L.bbase = cv.take((size_t)(c->max_sims + 1) * 4);
-    L.counts = cv.take((size_t)256 * L.max_rtiles * 4);
-    const int64_t scan_n = 256 * L.max_rtiles > L.max_chunks ? 256 * L.max_rtiles : L.max_chunks;
+    const int64_t scan_n = L.max_chunks;
     L.scan_part = cv.take(((size_t)(scan_n + 4095) / 4096 + 2) * 4);
     L.chunk_cnt = cv.take((size_t)L.max_chunks * 4);
     L.tile_sim = cv.take((size_t)L.max_tiles * 4);
@@ -843,7 +842,8 @@ BatchLayout batch_layout(const apic_batch_config* c)
     L.ntiles = cv.take(4);
     L.tile_ctr = cv.take(16);
     L.err = cv.take(4);
-    L.digits = cv.take((size_t)c->max_sims * 4 * 256 * 4);
+    L.bsorted = cv.take((size_t)c->max_sims * 4);   // member stored in its previous sorted order
+    L.bctl = cv.take(32);                            // sort epoch, pass tile counters
     L.total = cv.cur;
     return L;
 }
@@ -903,6 +903,15 @@ apic_status batch_rebuild(apic_batch* b)
         d.kb[1] = m->b.kB;
         d.vb[0] = m->b.vA;
         d.vb[1] = m->b.vB;
+        for (int q = 0; q < 2; ++q) {
+            d.mk[q] = m->b.mk[q];
+            d.mv[q] = m->b.mv[q];
+        }
+        d.midx = m->b.midx;
+        d.choff = m->b.choff;
+        d.mcnt = m->b.mcnt;
+        d.mctl = m->b.mctl;
+        d.lbs = m->b.lbs;
         d.n = (uint32_t)m->n;
         d.ntl = (uint32_t)radix_tiles(m->n);
         d.nch = (uint32_t)((m->n + b->tile - 1) / b->tile);
@@ -932,6 +941,9 @@ apic_status batch_rebuild(apic_batch* b)
         if (!rt.empty()) BCK(cudaMemcpyAsync(b->rt_sim, rt.data(), rt.size() * 4, cudaMemcpyHostToDevice, b->stream), "upload tables");
         if (!ch.empty()) BCK(cudaMemcpyAsync(b->ch_sim, ch.data(), ch.size() * 4, cudaMemcpyHostToDevice, b->stream), "upload tables");
         BCK(cudaMemcpyAsync(b->bbase, bb.data(), bb.size() * 4, cudaMemcpyHostToDevice, b->stream), "upload tables");
+        // after a membership change every member takes one full sort (its keys' home buffer
+        // follows the pass count, which the new members may change)
+        BCK(cudaMemsetAsync(b->bsorted, 0, S * sizeof(uint32_t), b->stream), "clear sorted flags");
         BCK(cudaStreamSynchronize(b->stream), "synchronize");   // host vectors die at return
     }
     int p2g_per = 1, g2p_per = 1;
@@ -955,8 +967,8 @@ cudaError_t batch_enqueue(apic_batch* b)
 {
     const int kpar = (b->passes - 1) & 1;
     const int S = (int)b->members.size();
-    cudaError_t e = batch_radix_sort(b->sortdescs, b->rt_sim, b->total_rtiles, b->passes, S, b->digits, b->counts,
-                                     b->tile_ctr, b->err, b->stream);
+    cudaError_t e = batch_resort(b->sortdescs, b->rt_sim, b->total_rtiles, S, b->passes, kpar, b->bsorted, b->bctl,
+                                 b->err, b->sms, b->stream);
     if (e == cudaSuccess)
         e = batch_build_tiles(b->sortdescs, b->ch_sim, b->total_chunks, b->dim, b->tile, kpar, b->chunk_cnt, b->scan_part,
                               b->ntiles, b->max_tiles, b->tile_sim, b->tile_start, b->err, b->tile_ctr, b->stream);
@@ -975,7 +987,9 @@ cudaError_t batch_enqueue(apic_batch* b)
                                                b->tile_ctr, kpar, b->g2p_grid, b->stream)
                                : batch_g2p_f64(b->dim, b->order, ext, b->descs, b->tile_sim, b->tile_start, b->ntiles,
                                                b->tile_ctr, kpar, b->g2p_grid, b->stream);
-    if (e == cudaSuccess) e = b->precision == 32 ? batch_finish_f32(b->descs, S, b->stream) : batch_finish_f64(b->descs, S, b->stream);
+    if (e == cudaSuccess)
+        e = b->precision == 32 ? batch_finish_f32(b->descs, S, b->bsorted, b->stream)
+                               : batch_finish_f64(b->descs, S, b->bsorted, b->stream);
     return e;
 }
 
@@ -1033,7 +1047,7 @@ extern "C" {
 apic_status apic_batch_workspace_size(const apic_batch_config* c, size_t* bytes)
 {
     if (!c || !bytes) return APIC_ERR_ARG;
-    if (c->max_sims <= 0 || c->max_particles <= 0 || c->max_blocks <= 0) return APIC_ERR_ARG;
+    if (c->max_sims <= 0 || c->max_sims > 12000 || c->max_particles <= 0 || c->max_blocks <= 0) return APIC_ERR_ARG;
     if (c->precision != 32 && c->precision != 64) return APIC_ERR_ARG;
     *bytes = batch_layout(c).total;
     return APIC_OK;
@@ -1046,7 +1060,7 @@ apic_status apic_batch_create(const apic_batch_config* c, void* workspace, size_
     *out = nullptr;
     if ((c->dim != 2 && c->dim != 3) || (c->order != 2 && c->order != 3)) return APIC_ERR_ARG;
     if (c->precision != 32 && c->precision != 64) return APIC_ERR_ARG;
-    if (c->max_sims <= 0 || c->max_particles <= 0 || c->max_blocks <= 0) return APIC_ERR_ARG;
+    if (c->max_sims <= 0 || c->max_sims > 12000 || c->max_particles <= 0 || c->max_blocks <= 0) return APIC_ERR_ARG;
     const int tile = c->tile_particles == 0 ? 4096 : c->tile_particles;
     if (tile != 1024 && tile != 2048 && tile != 4096) return APIC_ERR_ARG;
     const int group = c->group == 0 ? 8 : c->group;
@@ -1072,7 +1086,7 @@ apic_status apic_batch_create(const apic_batch_config* c, void* workspace, size_
     b->rt_sim = (uint32_t*)(base + L.rt_sim);
     b->ch_sim = (uint32_t*)(base + L.ch_sim);
     b->bbase = (uint32_t*)(base + L.bbase);
-    b->counts = (uint32_t*)(base + L.counts);
+
     b->scan_part = (uint32_t*)(base + L.scan_part);
     b->chunk_cnt = (uint32_t*)(base + L.chunk_cnt);
     b->tile_sim = (uint32_t*)(base + L.tile_sim);
@@ -1080,7 +1094,8 @@ apic_status apic_batch_create(const apic_batch_config* c, void* workspace, size_
     b->ntiles = (uint32_t*)(base + L.ntiles);
     b->tile_ctr = (uint32_t*)(base + L.tile_ctr);
     b->err = (uint32_t*)(base + L.err);
-    b->digits = (uint32_t*)(base + L.digits);
+    b->bsorted = (uint32_t*)(base + L.bsorted);
+    b->bctl = (uint32_t*)(base + L.bctl);
     b->max_rtiles = L.max_rtiles;
     b->max_chunks = L.max_chunks;
     b->max_tiles = L.max_tiles;
@@ -1095,6 +1110,7 @@ apic_status apic_batch_create(const apic_batch_config* c, void* workspace, size_
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->err, 0, 4, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->ntiles, 0, 4, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->bctl, 0, 32, b->stream);
     if (e != cudaSuccess) {
         delete b;
         return APIC_ERR_CUDA;
@@ -1141,6 +1157,9 @@ apic_status apic_batch_add(apic_batch* b, apic_sim* s)
         s->keys_valid = true;
         s->launches += 1;
     }
+    // look-back words of the batch's sort epochs start clear
+    BCK(cudaMemsetAsync(s->b.lbs, 0, sizeof(unsigned long long) * 256 * ((size_t)radix_tiles(s->c.capacity) + 1),
+                        s->stream), "clear look-back words");
     BCK(cudaStreamSynchronize(s->stream), "synchronize member stream");
     s->order_sorted = false;
     s->batch = b;
@@ -1172,6 +1191,7 @@ apic_status apic_batch_remove(apic_batch* b, apic_sim* s)
         s->keys_valid = true;
         s->order_sorted = true;   // batched G2P also stores particle k of the sorted order at k
     }
+    s->epoch = 0;   // its look-back words hold batch epochs: the next single sort clears them
     b->dirty = true;
     return APIC_OK;
 }

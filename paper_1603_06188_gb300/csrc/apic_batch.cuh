@@ -186,10 +186,15 @@ __global__ void __launch_bounds__(TPB) kb_grid_update(SimDesc<R>* __restrict__ d
     }
 }
 
-template <typename R> __global__ void kb_finish(SimDesc<R>* __restrict__ descs, int nsims)
+// end of a batched step: flip each member's state parity; G2P has stored its particles in
+// sorted order, so the next sort may be incremental
+template <typename R> __global__ void kb_finish(SimDesc<R>* __restrict__ descs, int nsims, uint32_t* bsorted)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < nsims) descs[s].cur ^= 1;
+    if (s < nsims) {
+        descs[s].cur ^= 1;
+        bsorted[s] = 1u;
+    }
 }
 
 template <typename R> struct BatchImpl {
@@ -267,9 +272,9 @@ template <typename R> struct BatchImpl {
         else return cudaErrorInvalidValue;
         return cudaGetLastError();
     }
-    static cudaError_t finish(void* descs, int nsims, cudaStream_t s)
+    static cudaError_t finish(void* descs, int nsims, uint32_t* bsorted, cudaStream_t s)
     {
-        kb_finish<R><<<(nsims + 255) / 256, 256, 0, s>>>((SimDesc<R>*)descs, nsims);
+        kb_finish<R><<<(nsims + 255) / 256, 256, 0, s>>>((SimDesc<R>*)descs, nsims, bsorted);
         return cudaGetLastError();
     }
 };
@@ -301,9 +306,9 @@ template <typename R> struct BatchImpl {
     {                                                                                                          \
         return BatchImpl<R>::g2p(dim, order, ext, descs, ts, tst, nt, ctr, kpar, grid, s);                     \
     }                                                                                                          \
-    cudaError_t batch_finish_##SFX(void* descs, int nsims, cudaStream_t s)                                    \
+    cudaError_t batch_finish_##SFX(void* descs, int nsims, uint32_t* bsorted, cudaStream_t s)                 \
     {                                                                                                          \
-        return BatchImpl<R>::finish(descs, nsims, s);                                                          \
+        return BatchImpl<R>::finish(descs, nsims, bsorted, s);                                                 \
     }                                                                                                          \
     int batch_desc_cur_offset_##SFX() { return (int)offsetof(SimDesc<R>, cur); }
 

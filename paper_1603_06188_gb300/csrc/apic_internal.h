@@ -81,6 +81,14 @@ struct SortDesc {
     uint32_t rbase;   // radix tiles of the simulations before this one
     uint32_t cbase;   // tile-list chunks of the simulations before this one
     uint32_t nch;     // tile-list chunks
+    // the member's incremental-sort buffers (Buffers of the same names)
+    uint32_t* mk[2];
+    uint32_t* mv[2];
+    uint32_t* midx;
+    uint32_t* choff;
+    uint32_t* mcnt;
+    uint32_t* mctl;   // + 16: digit counts
+    unsigned long long* lbs;
 };
 
 // sort / tiles (apic_sort.cu)
@@ -98,9 +106,10 @@ cudaError_t build_tiles(const Buffers& b, const uint32_t* skeys, int64_t n, int 
                         int64_t max_tiles, cudaStream_t s);
 cudaError_t exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* part,
                            uint32_t* total, cudaStream_t s);
-cudaError_t batch_radix_sort(const SortDesc* sd, const uint32_t* rt_sim, uint32_t total_rtiles, int passes,
-                             int nsims, uint32_t* digits, uint32_t* status, uint32_t* tile_ctr, uint32_t* err,
-                             cudaStream_t s);
+// incremental stable sort of every member's knext into kb[kpar] / vb[kpar]; members with
+// bsorted[s] = 0 are sorted in full; bctl = [epoch, pass tile counters x4] on the device
+cudaError_t batch_resort(const SortDesc* sd, const uint32_t* rt_sim, uint32_t total_rtiles, int nsims, int passes,
+                         int kpar, const uint32_t* bsorted, uint32_t* bctl, uint32_t* err, int sms, cudaStream_t s);
 cudaError_t batch_build_tiles(const SortDesc* sd, const uint32_t* ch_sim, uint32_t total_chunks, int dim, int tile,
                               int kpar, uint32_t* cnt, uint32_t* part, uint32_t* ntiles, int64_t max_tiles,
                               uint32_t* tile_sim, uint32_t* tile_start, uint32_t* err, uint32_t* tile_ctr,
@@ -149,7 +158,7 @@ struct Launch {
     cudaError_t batch_g2p_##SFX(int dim, int order, int ext, void* descs, const uint32_t* tile_sim,           \
                                 const uint32_t* tile_start, const uint32_t* ntiles, uint32_t* ctr, int kpar,  \
                                 int grid, cudaStream_t s);                                                     \
-    cudaError_t batch_finish_##SFX(void* descs, int nsims, cudaStream_t s);                                   \
+    cudaError_t batch_finish_##SFX(void* descs, int nsims, uint32_t* bsorted, cudaStream_t s);                                   \
     int batch_desc_cur_offset_##SFX();
 
 APIC_DECLARE_PRECISION(f32)

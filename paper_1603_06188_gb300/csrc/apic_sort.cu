@@ -755,158 +755,319 @@ __global__ void __launch_bounds__(RT) k_merge(const uint32_t* __restrict__ knext
 
 // ---------------------------------------------------------------- batched forms
 // Work item -> simulation tables (rt_sim per radix tile, ch_sim per chunk) are built on the
-// host when membership changes.  Counts of all simulations sit in one array laid out
-// [sim][digit][tile], so one exclusive scan over it gives every simulation's offsets shifted
-// by the particles of the simulations before it (pbase), which the scatter subtracts.
-__global__ void __launch_bounds__(RT) kb_radix_hist(const SortDesc* __restrict__ sd, const uint32_t* __restrict__ rt_sim,
-                                                    int shift, int pass, uint32_t* __restrict__ counts)
+// host when membership changes.
+
+// ---------------------------------------------------------------- batched incremental sort
+// The incremental sort above, per member of a batch.  A member whose particles are not yet
+// in its previous sorted order (bsorted[s] = 0: new in the batch) counts every key as
+// changed, which makes the same kernels a full stable sort of it.  The previous sorted keys
+// P are copied from kb[kpar] to kb[kpar ^ 1] while the changed keys are counted, so the
+// output stays in kb[kpar] / vb[kpar], where the batched P2G and G2P read it.  The look-back
+// epoch and the pass tile counters are device words (bctl: [0] epoch, [1 + p] pass p's
+// counter), advanced on the device, so a captured step graph replays correctly.
+
+__global__ void __launch_bounds__(256) kb_rs_init(const SortDesc* __restrict__ sd, uint32_t* __restrict__ bctl)
 {
-    __shared__ uint32_t h[256];
-    const SortDesc& d = sd[rt_sim[blockIdx.x]];
-    const int64_t lt = (int64_t)blockIdx.x - d.rbase;
-    const uint32_t* keys = pass == 0 ? d.knext : d.kb[(pass - 1) & 1];
-    radix_hist_tile(keys, d.n, lt, shift, h);
-    counts[(int64_t)256 * d.rbase + (int64_t)threadIdx.x * d.ntl + lt] = h[threadIdx.x];
+    // one CTA per member: clear its control words and digit counts
+    uint32_t* ctl = sd[blockIdx.x].mctl;
+    for (int i = threadIdx.x; i < 16 + 4 * 256; i += 256) ctl[i] = 0u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        bctl[0] += 8u;
+        bctl[1] = bctl[2] = bctl[3] = bctl[4] = 0u;
+    }
 }
 
-__global__ void __launch_bounds__(RT) kb_radix_scatter(const SortDesc* __restrict__ sd, const uint32_t* __restrict__ rt_sim,
-                                                       int shift, int pass, const uint32_t* __restrict__ offsets)
-{
-    __shared__ uint32_t wc[RW][256];
-    __shared__ uint32_t goff[256];
-    const SortDesc& d = sd[rt_sim[blockIdx.x]];
-    const int64_t lt = (int64_t)blockIdx.x - d.rbase;
-    goff[threadIdx.x] = offsets[(int64_t)256 * d.rbase + (int64_t)threadIdx.x * d.ntl + lt] - d.pbase;
-    const uint32_t* kin = pass == 0 ? d.knext : d.kb[(pass - 1) & 1];
-    const uint32_t* vin = pass == 0 ? nullptr : d.vb[(pass - 1) & 1];
-    radix_scatter_tile(kin, vin, d.kb[pass & 1], d.vb[pass & 1], d.n, lt, shift, goff, wc);
-}
-
-// one-sweep form of the batched sort: digit starts per (simulation, pass); the look-back of
-// a tile stops at its simulation's first tile
-__global__ void __launch_bounds__(RT) kb_onesweep_hist(const SortDesc* __restrict__ sd, const uint32_t* __restrict__ rt_sim,
-                                                       int passes, uint32_t* __restrict__ ghist)
+__global__ void __launch_bounds__(RT) kb_moved_count(const SortDesc* __restrict__ sd, const uint32_t* __restrict__ rt_sim,
+                                                     const uint32_t* __restrict__ bsorted, int kpar, int passes)
 {
     __shared__ uint32_t h[4][256];
-    for (int i = threadIdx.x; i < 4 * 256; i += RT) (&h[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < 4 * 256; i += RT) (&h[0][0])[i] = 0u;
     __syncthreads();
     const uint32_t sim = rt_sim[blockIdx.x];
     const SortDesc& d = sd[sim];
     const int64_t lt = (int64_t)blockIdx.x - d.rbase;
-    const int lane = threadIdx.x & 31;
+    const int64_t n = d.n;
+    const int64_t base = lt * RTILE;
+    const uint32_t* P = bsorted[sim] ? d.kb[kpar] : nullptr;
+    uint32_t* Pc = d.kb[kpar ^ 1];
+    uint32_t c = 0;
+#pragma unroll
     for (int r = 0; r < RI; ++r) {
-        const int64_t k = lt * RTILE + (int64_t)r * RT + threadIdx.x;
-        const bool valid = k < d.n;
-        const uint32_t key = valid ? d.knext[k] : 0u;
-        for (int p = 0; p < passes; ++p) {
-            const unsigned dg = valid ? (key >> (8 * p)) & 255u : 256u;
-            const unsigned peers = __match_any_sync(0xffffffffu, dg);
-            if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[p][dg], (uint32_t)__popc(peers));
+        const int64_t k = base + r * RT + threadIdx.x;
+        if (k < n) {
+            const uint32_t key = d.knext[k];
+            bool moved = true;
+            if (P) {
+                const uint32_t pk = P[k];
+                Pc[k] = pk;
+                moved = key != pk;
+            }
+            if (moved) {
+                ++c;
+                for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(key >> (8 * p)) & 255u], 1u);
+            }
         }
     }
-    __syncthreads();
-    for (int p = 0; p < passes; ++p)
-        if (h[p][threadIdx.x]) atomicAdd(&ghist[((size_t)sim * 4 + p) * 256 + threadIdx.x], h[p][threadIdx.x]);
-}
-
-__global__ void __launch_bounds__(256) kb_onesweep_digits(uint32_t* __restrict__ ghist, int passes)
-{
-    uint32_t* g = ghist + (size_t)blockIdx.x * 4 * 256;
-    for (int p = 0; p < passes; ++p) {
-        const uint32_t v = g[p * 256 + threadIdx.x];
-        uint32_t ex;
-        block_excl_scan(v, ex);
-        g[p * 256 + threadIdx.x] = ex;
+    uint32_t ex;
+    const uint32_t total = block_excl_scan(c, ex);
+    if (threadIdx.x == 0) d.mcnt[lt] = total;
+    uint32_t* mh = d.mctl + 16;
+    for (int i = threadIdx.x; i < passes * 256; i += RT) {
+        const uint32_t v = (&h[0][0])[i];
+        if (v) atomicAdd(mh + i, v);
     }
 }
 
-__global__ void __launch_bounds__(RT) kb_onesweep_pass(const SortDesc* __restrict__ sd, const uint32_t* __restrict__ rt_sim,
-                                                       int shift, int pass, const uint32_t* __restrict__ ghist,
-                                                       uint32_t* __restrict__ status, uint32_t* __restrict__ tile_ctr,
-                                                       uint32_t* __restrict__ err)
+__global__ void __launch_bounds__(RT) kb_moved_compact(const SortDesc* __restrict__ sd, const uint32_t* __restrict__ rt_sim,
+                                                       const uint32_t* __restrict__ bsorted, int kpar)
 {
+    __shared__ uint32_t wc[RI][RW];
+    const uint32_t sim = rt_sim[blockIdx.x];
+    const SortDesc& d = sd[sim];
+    const uint32_t t = blockIdx.x - d.rbase;
+    const int64_t n = d.n;
+    const uint32_t* P = bsorted[sim] ? d.kb[kpar ^ 1] : nullptr;   // the copy of the previous keys
+    uint32_t part = 0;
+    for (uint32_t i = threadIdx.x; i < t; i += RT) part += d.mcnt[i];
+    uint32_t ex;
+    const uint32_t excl = block_excl_scan(part, ex);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = (int64_t)t * RTILE;
+    uint32_t key[RI];
+    unsigned bal[RI];
+#pragma unroll
+    for (int r = 0; r < RI; ++r) {
+        const int64_t k = base + r * RT + threadIdx.x;
+        const bool moved = k < n && (!P || d.knext[k] != P[k]);
+        key[r] = moved ? d.knext[k] : 0u;
+        bal[r] = __ballot_sync(FULL, moved);
+        if (lane == 0) wc[r][w] = (uint32_t)__popc(bal[r]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = excl;
+        for (int r = 0; r < RI; ++r)
+            for (int ww = 0; ww < RW; ++ww) {
+                const uint32_t cc = wc[r][ww];
+                wc[r][ww] = run;
+                run += cc;
+            }
+        d.choff[t] = excl;
+        if (t + 1 == d.ntl) d.mctl[MCTL_M] = run;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RI; ++r) {
+        if (bal[r] & (1u << lane)) {
+            const int64_t k = base + r * RT + threadIdx.x;
+            const uint32_t p = wc[r][w] + (uint32_t)__popc(bal[r] & lanemask_lt());
+            d.mk[0][p] = key[r];
+            d.mv[0][p] = (uint32_t)k;
+            d.midx[p] = (uint32_t)k;
+        }
+    }
+}
+
+// one LSD pass over every member's changed keys; tiles are numbered across members and
+// taken from a counter, each tile's look-back stops at its member's first tile
+__global__ void __launch_bounds__(RT) kb_msort_pass(const SortDesc* __restrict__ sd, int nsims, int pass,
+                                                    uint32_t* __restrict__ bctl, uint32_t* err)
+{
+    extern __shared__ uint32_t pre[];      // [nsims + 1]: first tile of each member
     __shared__ uint32_t wc[RW][256];
     __shared__ uint32_t goff[256];
+    __shared__ uint32_t dst0[256];
     __shared__ uint32_t s_t;
-    if (threadIdx.x == 0) s_t = atomicAdd(tile_ctr, 1u);
-    for (int i = threadIdx.x; i < RW * 256; i += RT) (&wc[0][0])[i] = 0;
+    uint32_t carry = 0;
+    for (int b0 = 0; b0 < nsims; b0 += RT) {
+        const int i = b0 + threadIdx.x;
+        const uint32_t v = i < nsims ? (sd[i].mctl[MCTL_M] + RTILE - 1) / RTILE : 0u;
+        uint32_t ex;
+        const uint32_t tot = block_excl_scan(v, ex);
+        if (i < nsims) pre[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) pre[nsims] = carry;
     __syncthreads();
-    const uint32_t t = s_t;
-    const uint32_t sim = rt_sim[t];
-    const SortDesc& ds = sd[sim];
-    const int64_t lt = (int64_t)t - ds.rbase;
-    const int64_t n = ds.n;
-    const uint32_t* kin = pass == 0 ? ds.knext : ds.kb[(pass - 1) & 1];
-    const uint32_t* vin = pass == 0 ? nullptr : ds.vb[(pass - 1) & 1];
-    uint32_t* kout = ds.kb[pass & 1];
-    uint32_t* vout = ds.vb[pass & 1];
-    const uint32_t* dstart = ghist + ((size_t)sim * 4 + pass) * 256;
+    const uint32_t total = pre[nsims];
+    if (blockIdx.x >= total) return;
+    const uint32_t epoch = bctl[0] + (uint32_t)pass;
+    const int shift = 8 * pass;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t base = lt * RTILE + w * (RI * 32);
-    uint32_t key[RI], val[RI], lr[RI];
-    unsigned dig[RI];
-#pragma unroll
-    for (int r = 0; r < RI; ++r) {
-        const int64_t idx = base + r * 32 + lane;
-        const bool valid = idx < n;
-        key[r] = valid ? kin[idx] : 0u;
-        val[r] = valid ? (vin ? vin[idx] : (uint32_t)idx) : 0u;
-        const unsigned d = valid ? (key[r] >> shift) & 255u : 256u;
-        dig[r] = d;
-        const unsigned peers = __match_any_sync(FULL, d);
-        const unsigned before = (unsigned)__popc(peers & lanemask_lt());
-        const uint32_t cnt = valid ? wc[w][d] : 0u;
-        __syncwarp();
-        lr[r] = cnt + before;
-        if (valid && lane == __ffs(peers) - 1) wc[w][d] = cnt + (uint32_t)__popc(peers);
-        __syncwarp();
-    }
-    __syncthreads();
-    {
-        const int d = threadIdx.x;
-        uint32_t run = 0;
-        for (int ww = 0; ww < RW; ++ww) {
-            const uint32_t c = wc[ww][d];
-            wc[ww][d] = run;
-            run += c;
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) s_t = atomicAdd(bctl + 1 + pass, 1u);
+        for (int i = threadIdx.x; i < RW * 256; i += RT) (&wc[0][0])[i] = 0u;
+        __syncthreads();
+        const uint32_t t = s_t;
+        if (t >= total) break;
+        int lo = 0, hi = nsims - 1;   // last member with pre <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (pre[mid] <= t) lo = mid;
+            else hi = mid - 1;
         }
-        uint32_t* my = status + (size_t)t * 256 + d;
-        if (lt == 0) {
-            st_volatile(my, LB_INC | run);
-            goff[d] = dstart[d];
-        } else {
-            st_volatile(my, LB_AGG | run);
-            uint32_t excl = 0;
-            int64_t j = (int64_t)t - 1;
-            uint32_t spins = 0;
-            while (j >= (int64_t)ds.rbase) {
-                const uint32_t v = ld_volatile(status + (size_t)j * 256 + d);
-                const uint32_t f = v & ~LB_VAL;
-                if (f == 0u) {
-                    if (++spins > (1u << 22)) {
-                        atomicOr(err, APIC_ERRBIT_TIMEOUT);
-                        break;
-                    }
-                    __nanosleep(32);
-                    continue;
-                }
-                excl += v & LB_VAL;
-                if (f == LB_INC) break;
-                --j;
+        const SortDesc& d = sd[lo];
+        if (lo != cur) {   // uniform: the member's digit starts of this pass
+            uint32_t ex;
+            block_excl_scan(d.mctl[16 + pass * 256 + threadIdx.x], ex);
+            dst0[threadIdx.x] = ex;
+            cur = lo;
+        }
+        const uint32_t m = d.mctl[MCTL_M];
+        const uint32_t lt = t - pre[lo];
+        const uint32_t* kin = d.mk[pass & 1];
+        const uint32_t* vin = d.mv[pass & 1];
+        uint32_t* kout = d.mk[(pass + 1) & 1];
+        uint32_t* vout = d.mv[(pass + 1) & 1];
+        const int64_t base = (int64_t)lt * RTILE + w * (RI * 32);
+        uint32_t key[RI], val[RI], lr[RI];
+        unsigned dig[RI];
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+            const int64_t idx = base + r * 32 + lane;
+            const bool valid = idx < (int64_t)m;
+            key[r] = valid ? kin[idx] : 0u;
+            val[r] = valid ? vin[idx] : 0u;
+            const unsigned dg = valid ? (key[r] >> shift) & 255u : 256u;
+            dig[r] = dg;
+            const unsigned peers = __match_any_sync(FULL, dg);
+            const unsigned before = (unsigned)__popc(peers & lanemask_lt());
+            const uint32_t cnt = valid ? wc[w][dg] : 0u;
+            __syncwarp();
+            lr[r] = cnt + before;
+            if (valid && lane == __ffs(peers) - 1) wc[w][dg] = cnt + (uint32_t)__popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        {
+            const int dg = threadIdx.x;
+            uint32_t run = 0;
+            for (int ww = 0; ww < RW; ++ww) {
+                const uint32_t c = wc[ww][dg];
+                wc[ww][dg] = run;
+                run += c;
             }
-            st_volatile(my, LB_INC | (excl + run));
-            goff[d] = dstart[d] + excl;
+            goff[dg] = dst0[dg] + lookback64(d.lbs + dg, lt, 256, run, epoch, err);
         }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+            const int64_t idx = base + r * 32 + lane;
+            if (idx < (int64_t)m) {
+                const unsigned dg = dig[r];
+                const uint32_t pos = goff[dg] + wc[w][dg] + lr[r];
+                if (pos < m) {
+                    kout[pos] = key[r];
+                    vout[pos] = val[r];
+                } else {
+                    atomicOr(err, APIC_ERRBIT_RANGE);
+                }
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
+}
+
+// unchanged keys of every member chunk into place (members not yet sorted have none)
+__global__ void __launch_bounds__(RT) kb_merge_u(const SortDesc* __restrict__ sd, const uint32_t* __restrict__ rt_sim,
+                                                 const uint32_t* __restrict__ bsorted, int kpar, int passes,
+                                                 uint32_t* err)
+{
+    __shared__ uint32_t wc[RI][RW];
+    __shared__ uint32_t s_lo, s_hi;
+    const uint32_t sim = rt_sim[blockIdx.x];
+    if (!bsorted[sim]) return;
+    const SortDesc& d = sd[sim];
+    const uint32_t t = blockIdx.x - d.rbase;
+    const int64_t n = d.n;
+    const uint32_t* pk = d.kb[kpar ^ 1];
+    const uint32_t* msk = d.mk[passes & 1];
+    const uint32_t* msv = d.mv[passes & 1];
+    const uint32_t m = d.mctl[MCTL_M];
+    uint32_t* kout = d.kb[kpar];
+    uint32_t* vout = d.vb[kpar];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = (int64_t)t * RTILE;
+    const int64_t kl = (base + RTILE < n ? base + RTILE : n) - 1;
+    if (threadIdx.x == 0) {
+        s_lo = below_m(msk, msv, 0u, m, pk[base], (uint32_t)base);
+        s_hi = below_m(msk, msv, s_lo, m, pk[kl], (uint32_t)kl + 1u);
+    }
+    unsigned bal[RI];
 #pragma unroll
     for (int r = 0; r < RI; ++r) {
-        const int64_t idx = base + r * 32 + lane;
-        if (idx < n) {
-            const unsigned d = dig[r];
-            const uint32_t pos = goff[d] + wc[w][d] + lr[r];
-            kout[pos] = key[r];
-            vout[pos] = val[r];
+        const int64_t k = base + r * RT + threadIdx.x;
+        const bool moved = k < n && d.knext[k] != pk[k];
+        bal[r] = __ballot_sync(FULL, moved);
+        if (lane == 0) wc[r][w] = (uint32_t)__popc(bal[r]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = d.choff[t];
+        for (int r = 0; r < RI; ++r)
+            for (int ww = 0; ww < RW; ++ww) {
+                const uint32_t c = wc[r][ww];
+                wc[r][ww] = run;
+                run += c;
+            }
+    }
+    __syncthreads();
+    const uint32_t lo = s_lo, hi = s_hi;
+#pragma unroll
+    for (int r = 0; r < RI; ++r) {
+        const int64_t k = base + r * RT + threadIdx.x;
+        if (k < n && !(bal[r] & (1u << lane))) {
+            const uint32_t before = wc[r][w] + (uint32_t)__popc(bal[r] & lanemask_lt());
+            const uint32_t key = pk[k];
+            const uint32_t pos = (uint32_t)k - before + below_m(msk, msv, lo, hi, key, (uint32_t)k);
+            if (pos < (uint32_t)n) {
+                kout[pos] = key;
+                vout[pos] = (uint32_t)k;
+            } else {
+                atomicOr(err, APIC_ERRBIT_RANGE);
+            }
+        }
+    }
+}
+
+// changed keys of member blockIdx.y into place
+__global__ void __launch_bounds__(RT) kb_merge_m(const SortDesc* __restrict__ sd, const uint32_t* __restrict__ bsorted,
+                                                 int kpar, int passes, uint32_t* err)
+{
+    const uint32_t sim = blockIdx.y;
+    const SortDesc& d = sd[sim];
+    const bool sorted = bsorted[sim] != 0u;
+    const uint32_t n = d.n, m = d.mctl[MCTL_M];
+    const uint32_t* pk = d.kb[kpar ^ 1];
+    const uint32_t* msk = d.mk[passes & 1];
+    const uint32_t* msv = d.mv[passes & 1];
+    uint32_t* kout = d.kb[kpar];
+    uint32_t* vout = d.vb[kpar];
+    for (uint32_t j = blockIdx.x * RT + threadIdx.x; j < m; j += gridDim.x * RT) {
+        const uint32_t key = msk[j], idx = msv[j];
+        uint32_t pos = j;
+        if (sorted) {
+            uint32_t lo = 0, hi = n;   // K = #k with (P[k], k) below (key, idx)
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                const uint32_t a = pk[mid];
+                if (a < key || (a == key && mid < idx)) lo = mid + 1;
+                else hi = mid;
+            }
+            uint32_t a = 0, b = m;     // changed indices below K
+            while (a < b) {
+                const uint32_t mid = (a + b) >> 1;
+                if (d.midx[mid] < lo) a = mid + 1;
+                else b = mid;
+            }
+            pos = j + lo - a;
+        }
+        if (pos < n) {
+            kout[pos] = key;
+            vout[pos] = idx;
+        } else {
+            atomicOr(err, APIC_ERRBIT_RANGE);
         }
     }
 }
@@ -1029,21 +1190,19 @@ cudaError_t resort(const Buffers& b, int64_t n, int key_bits, const uint32_t* pk
     return cudaGetLastError();
 }
 
-cudaError_t batch_radix_sort(const SortDesc* sd, const uint32_t* rt_sim, uint32_t total_rtiles, int passes,
-                             int nsims, uint32_t* digits, uint32_t* status, uint32_t* tile_ctr, uint32_t* err,
-                             cudaStream_t s)
+cudaError_t batch_resort(const SortDesc* sd, const uint32_t* rt_sim, uint32_t total_rtiles, int nsims, int passes,
+                         int kpar, const uint32_t* bsorted, uint32_t* bctl, uint32_t* err, int sms, cudaStream_t s)
 {
-    if (total_rtiles == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(digits, 0, sizeof(uint32_t) * 4 * 256 * (size_t)nsims, s);
-    if (e != cudaSuccess) return e;
-    kb_onesweep_hist<<<total_rtiles, RT, 0, s>>>(sd, rt_sim, passes, digits);
-    kb_onesweep_digits<<<nsims, 256, 0, s>>>(digits, passes);
-    for (int p = 0; p < passes; ++p) {
-        e = cudaMemsetAsync(status, 0, sizeof(uint32_t) * 256 * (size_t)total_rtiles, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(tile_ctr + 2, 0, sizeof(uint32_t), s);
-        if (e != cudaSuccess) return e;
-        kb_onesweep_pass<<<total_rtiles, RT, 0, s>>>(sd, rt_sim, 8 * p, p, digits, status, tile_ctr + 2, err);
-    }
+    if (total_rtiles == 0 || nsims == 0) return cudaSuccess;
+    if (nsims > 12000) return cudaErrorInvalidValue;   // grid y and the per-member prefix in shared memory
+    kb_rs_init<<<nsims, 256, 0, s>>>(sd, bctl);
+    kb_moved_count<<<total_rtiles, RT, 0, s>>>(sd, rt_sim, bsorted, kpar, passes);
+    kb_moved_compact<<<total_rtiles, RT, 0, s>>>(sd, rt_sim, bsorted, kpar);
+    const int grid = (int)total_rtiles < sms * 8 ? (int)total_rtiles : sms * 8;
+    const size_t smem = sizeof(uint32_t) * ((size_t)nsims + 1);
+    for (int p = 0; p < passes; ++p) kb_msort_pass<<<grid, RT, smem, s>>>(sd, nsims, p, bctl, err);
+    kb_merge_u<<<total_rtiles, RT, 0, s>>>(sd, rt_sim, bsorted, kpar, passes, err);
+    kb_merge_m<<<dim3(8, (unsigned)nsims), RT, 0, s>>>(sd, bsorted, kpar, passes, err);
     return cudaGetLastError();
 }
 

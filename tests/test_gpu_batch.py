@@ -166,3 +166,33 @@ def test_batch_rejects_incompatible(apic):
     with pytest.raises(apic.ApicError):
         sims[0].step(1)                   # members are stepped by the batch only
     batch.close()
+
+
+def test_batch_fast_motion_equals_alone(apic):
+    """Fast rigid rotation in every member, so a large share of the cell keys changes every
+    step: the batched sort of the changed keys (several radix tiles per member for the larger
+    ones, none at all for the smallest) must reproduce stepping each member alone."""
+    rng = np.random.default_rng(21)
+    members = []
+    for n_target, edge in ((200000, 48), (40000, 32), (3000, 24)):
+        res = edge
+        side = min(0.5, (n_target / 8) ** (1 / 3) / res)
+        sc = scenes.falling_cube_3d(res=res, side=side, ppc=8, seed=int(rng.integers(1 << 30)))
+        w = rng.normal(size=3) * 60.0
+        v = np.cross(w, sc.x - 0.5)
+        vol = sc.dx ** 3 / 8
+        cfg = apic.make_config(dim=3, order=2, res=(res,) * 3, dx=sc.dx, dt=1e-4, model="fcr", E=1e4, nu=0.3,
+                               particle_mass=vol, particle_volume=vol)
+        members.append((cfg, sc.x, v, None, None))
+    steps = 4
+    ref = run_alone(apic, members, steps)
+    batch = apic.Batch(dim=3, order=2, max_sims=4, max_particles=400000, max_blocks=200000)
+    sims = []
+    for cfg, x, v, B, F in members:
+        sim = apic.Sim(cfg, len(x))
+        sim.upload(x, v, B, F)
+        batch.add(sim)
+        sims.append(sim)
+    batch.step(steps)
+    check_same([s.download() for s in sims], ref)
+    batch.close()
