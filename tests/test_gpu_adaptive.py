@@ -1,5 +1,5 @@
 """Steps whose time step follows the Sec. 4.3 bound, dt = min(dt_max, nu dx / max_p(|v_p| +
-6 sqrt(d)/dx |B_p|_F)), on the GPU (SURVEY's second "next" row): one step at a time
+6 sqrt(d)/dx |B_p|_F)), on the GPU: one step at a time
 against the oracle taking its own time step by the same rule (the first maximum of a call
 is the library's FP64 reduction of the current state); several steps in one call, where
 the maximum comes from G2P's fused FP32 reduction; and a small dt_max, where the run

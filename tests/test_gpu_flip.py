@@ -1,4 +1,4 @@
-"""FLIP and PIC/FLIP blends on the GPU (SURVEY's third "next" row): whole steps against the
+"""FLIP and PIC/FLIP blends on the GPU: whole steps against the
 oracle's transfer 2 (the FLIP update of Sec. 1 blended with PIC's by flip_alpha) in 3-D FP32
 and 2-D cubic FP64, with elastic forces and gravity; FLIP keeps particle velocities when the
 grid leaves them unchanged while PIC filters them; batches refuse FLIP simulations; the

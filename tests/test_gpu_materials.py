@@ -1,4 +1,4 @@
-"""A material per particle on the GPU (SURVEY's first "next" row): two materials in one
+"""A material per particle on the GPU: two materials in one
 body (soft half, stiff half) against the oracle with per-particle Lame parameters --
 the P2G force alone (v = B = 0, so the grid momentum is dt f), then several whole steps --
 in 3-D FP32 and 2-D cubic FP64; uniform per-particle values against the configuration's

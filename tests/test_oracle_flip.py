@@ -1,4 +1,4 @@
-"""Pins of the oracle's FLIP transfer and PIC/FLIP blend (SURVEY's third "next" row; the
+"""Pins of the oracle's FLIP transfer and PIC/FLIP blend (the
 FLIP update is the one the paper states in Sec. 1, the blend weight is an extension):
 alpha = 0 is PIC exactly; with no force and no gravity the grid leaves velocities unchanged,
 so FLIP keeps every particle velocity exactly where PIC filters them; gravity alone adds

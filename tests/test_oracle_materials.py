@@ -1,5 +1,5 @@
-"""Pins of the oracle's per-particle materials (a Lame pair per particle; SURVEY's first
-"next" row): uniform per-particle values reproduce the configuration's material exactly,
+"""Pins of the oracle's per-particle materials (a Lame pair per particle): uniform
+per-particle values reproduce the configuration's material exactly,
 P2G is linear in the particles so a two-material set equals the sum of its two
 single-material halves, the force is minus the gradient of the sum of the halves' elastic
 energies, and a mixed-material step conserves momentum (Sec. 5.2, 5.3)."""
