@@ -544,6 +544,21 @@ __device__ __forceinline__ void tile_flush(const R* cellsum, const uint32_t* cbe
         }
 }
 
+// two FP32 fused multiply-adds in one packed instruction (c0 += a0 b0, c1 += a1 b1), each
+// rounded as a scalar fmaf; the FP64 form is two scalar fmas
+template <typename R> __device__ __forceinline__ void fma_pair(R& c0, R& c1, R a0, R a1, R b0, R b1)
+{
+    c0 = fma(a0, b0, c0);
+    c1 = fma(a1, b1, c1);
+}
+template <> __device__ __forceinline__ void fma_pair<float>(float& c0, float& c1, float a0, float a1, float b0, float b1)
+{
+    asm("{\n\t.reg .b64 pa, pb, pc;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\tmov.b64 pc, {%0, %1};\n\t"
+        "fma.rn.f32x2 pc, pa, pb, pc;\n\tmov.b64 {%0, %1}, pc;\n\t}"
+        : "+f"(c0), "+f"(c1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
 // One tile of the cell-parallel P2G (whole CTA, NT = 128 threads).  On entry the CTA is
 // converged; cbeg / cend hold zeros and *s_cell = 0 (set by the caller before its last
 // barrier).  Leaves the smem free for the next tile after its final barrier.
@@ -705,9 +720,11 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
 #pragma unroll
                             for (int ia = 0; ia < K; ++ia) {
                                 const int j = ia + K * ib + K * K * icl;
-#pragma unroll
-                                for (int cc = 0; cc < 3; ++cc) cur[j * NV + cc] += w[0][ia] * P[cc] + E[cc][ia] * S;
-                                cur[j * NV + 3] += w[0][ia] * mS;
+                                // (c0, c1) and (c2, mass) as packed pairs
+                                fma_pair<R>(cur[j * NV + 0], cur[j * NV + 1], E[0][ia], E[1][ia], S, S);
+                                fma_pair<R>(cur[j * NV + 0], cur[j * NV + 1], w[0][ia], w[0][ia], P[0], P[1]);
+                                fma_pair<R>(cur[j * NV + 2], cur[j * NV + 3], E[2][ia], R(0), S, S);
+                                fma_pair<R>(cur[j * NV + 2], cur[j * NV + 3], w[0][ia], w[0][ia], P[2], mS);
                             }
                         }
                     }
@@ -1426,12 +1443,12 @@ __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>
                     for (int ic = 0; ic < K; ++ic) {
                         const V4<R> nv = *reinterpret_cast<const V4<R>*>(svf + o01 + ox[D - 1][ic]);
                         const R vt[3] = {nv.x, nv.y, nv.z};
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            P[a] += w[2][ic] * vt[a];
-                            Q[a] += dw[2][ic] * vt[a];
-                            Z[a] += rw[2][ic] * vt[a];
-                        }
+                        // components (0, 1) as packed pairs, component 2 of P and Q as one more
+                        fma_pair<R>(P[0], P[1], w[2][ic], w[2][ic], vt[0], vt[1]);
+                        fma_pair<R>(Q[0], Q[1], dw[2][ic], dw[2][ic], vt[0], vt[1]);
+                        fma_pair<R>(Z[0], Z[1], rw[2][ic], rw[2][ic], vt[0], vt[1]);
+                        fma_pair<R>(P[2], Q[2], w[2][ic], dw[2][ic], vt[2], vt[2]);
+                        Z[2] += rw[2][ic] * vt[2];
                     }
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
