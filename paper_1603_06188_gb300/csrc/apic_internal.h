@@ -64,7 +64,7 @@ struct HostCfg {
     double flip_alpha;           // transfer 2: weight of the FLIP update
     double mu, lam, mass, vol;
     int tile;                    // particles per tile (power of two)
-    int p2g_kernel;              // 1 warp-segmented, 2 cell-parallel
+    int p2g_kernel;              // 1 warp-segmented, 2 cell-parallel, 3 interleaved, 4 node-split
     int key_bits;
     int nblocks;
     int64_t capacity;

@@ -475,14 +475,28 @@ __device__ __forceinline__ void tile_cell_runs(const uint32_t* __restrict__ skey
     }
 }
 
+// The tile's occupied base cells as a bit mask, written to occ[0..1] by two whole warps (a
+// cell test is then a shift instead of two shared-memory loads; most tests of a sparse tile
+// fail).  The caller synchronises before reading it.
+template <int D>
+__device__ __forceinline__ void tile_occupancy(const uint32_t* cbeg, const uint32_t* cend, uint32_t* occ)
+{
+    if (threadIdx.x < 64) {
+        const bool o = threadIdx.x < ((D == 3) ? 64 : 16) && cbeg[threadIdx.x] < cend[threadIdx.x];
+        const unsigned bits = __ballot_sync(0xffffffffu, o);
+        if ((threadIdx.x & 31) == 0) occ[threadIdx.x >> 5] = bits;
+    }
+}
+
 // The tile's nodes from the per-cell stencil sums cellsum[cell][node j][lane v]: node n
-// collects, in a fixed order, the sums of the cells n - (a, b, c) whose stencils cover it,
-// and adds them to the global grid once; then the 2^D node blocks the tile reaches are
-// flagged active.  Whole CTA of nt threads, after a barrier that follows the sums.
+// collects, in a fixed order, the sums of the occupied cells n - (a, b, c) whose stencils
+// cover it, and adds them to the global grid once; then the 2^D node blocks the tile
+// reaches are flagged active.  Whole CTA of nt threads, after a barrier that follows the
+// sums.
 template <int D, int ORDER, typename R>
-__device__ __forceinline__ void tile_flush(const R* cellsum, const uint32_t* cbeg, const uint32_t* cend, const int* bo,
-                                           uint32_t blk, R* __restrict__ acc, uint32_t* __restrict__ flags,
-                                           const DevCfg<R>& c, int nt)
+__device__ __forceinline__ void tile_flush_nodes(const R* cellsum, uint64_t occ, const int* bo, uint32_t blk,
+                                                 R* __restrict__ acc, uint32_t* __restrict__ flags,
+                                                 const DevCfg<R>& c, int nt)
 {
     constexpr int K = ORDER + 1;
     constexpr int TE = 4 + ORDER;
@@ -490,58 +504,61 @@ __device__ __forceinline__ void tile_flush(const R* cellsum, const uint32_t* cbe
     constexpr int NS = (D == 3) ? K * K * K : K * K;
     constexpr int NV = D + 1;
     constexpr int NVAL = NS * NV;
-    // the tile's occupied cells as a bit mask (one register): a cell test is then a shift
-    // instead of two shared-memory loads (most tests of a sparse tile fail)
-    __shared__ uint32_t s_occ[2];
-    if (threadIdx.x < 64) {   // two whole warps
-        const bool o = threadIdx.x < ((D == 3) ? 64 : 16) && cbeg[threadIdx.x] < cend[threadIdx.x];
-        const unsigned bits = __ballot_sync(0xffffffffu, o);
-        if ((threadIdx.x & 31) == 0) s_occ[threadIdx.x >> 5] = bits;
+    for (int i = threadIdx.x; i < TN; i += nt) {
+        const int n0 = i % TE, n1 = (i / TE) % TE, n2 = (D == 3) ? i / (TE * TE) : 0;
+        R sum[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sum[v] = R(0);
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+            const int ia = j % K, ib = (j / K) % K, ic = j / (K * K);
+            const int c0 = n0 - ia, c1 = n1 - ib, c2 = (D == 3) ? n2 - ic : 0;
+            if (c0 < 0 || c0 > 3 || c1 < 0 || c1 > 3 || c2 < 0 || c2 > 3) continue;
+            const int cl = c0 | (c1 << 2) | (c2 << 4);
+            if (!((occ >> cl) & 1ull)) continue;
+            const R* src = cellsum + (size_t)cl * NVAL + j * NV;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) sum[v] += src[v];
+        }
+        if (sum[D] == R(0)) continue;
+        int g[3];
+        g[0] = bo[0] + n0;
+        g[1] = bo[1] + n1;
+        g[2] = bo[2] + n2;
+        const uint32_t ni = node_index<D>(g, c.nb);
+        R* gdst = acc + 4 * (size_t)ni;
+#pragma unroll
+        for (int a = 0; a < D; ++a) atomicAdd(gdst + a, sum[a]);
+        atomicAdd(gdst + 3, sum[D]);
     }
+    if (threadIdx.x < (1 << D)) {
+        int bb[3];
+        block_coords<D, R>(blk, c, bb);
+        bool in = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            bb[a] += (threadIdx.x >> a) & 1;
+            if (bb[a] >= c.nb[a]) in = false;
+        }
+        if (in) {
+            const uint32_t b2 = (D == 3) ? ((uint32_t)bb[2] * c.nb[1] + bb[1]) * c.nb[0] + bb[0]
+                                         : (uint32_t)bb[1] * c.nb[0] + bb[0];
+            flags[b2] = 1u;
+        }
+    }
+}
+
+// occupancy, then the nodes (whole CTA, after a barrier that follows the sums)
+template <int D, int ORDER, typename R>
+__device__ __forceinline__ void tile_flush(const R* cellsum, const uint32_t* cbeg, const uint32_t* cend, const int* bo,
+                                           uint32_t blk, R* __restrict__ acc, uint32_t* __restrict__ flags,
+                                           const DevCfg<R>& c, int nt)
+{
+    __shared__ uint32_t s_occ[2];
+    tile_occupancy<D>(cbeg, cend, s_occ);
     __syncthreads();
     const uint64_t occ = (uint64_t)s_occ[0] | ((uint64_t)s_occ[1] << 32);
-        for (int i = threadIdx.x; i < TN; i += nt) {
-            const int n0 = i % TE, n1 = (i / TE) % TE, n2 = (D == 3) ? i / (TE * TE) : 0;
-            R sum[NV];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) sum[v] = R(0);
-#pragma unroll
-            for (int j = 0; j < NS; ++j) {
-                const int ia = j % K, ib = (j / K) % K, ic = j / (K * K);
-                const int c0 = n0 - ia, c1 = n1 - ib, c2 = (D == 3) ? n2 - ic : 0;
-                if (c0 < 0 || c0 > 3 || c1 < 0 || c1 > 3 || c2 < 0 || c2 > 3) continue;
-                const int cl = c0 | (c1 << 2) | (c2 << 4);
-                if (!((occ >> cl) & 1ull)) continue;
-                const R* src = cellsum + (size_t)cl * NVAL + j * NV;
-#pragma unroll
-                for (int v = 0; v < NV; ++v) sum[v] += src[v];
-            }
-            if (sum[D] == R(0)) continue;
-            int g[3];
-            g[0] = bo[0] + n0;
-            g[1] = bo[1] + n1;
-            g[2] = bo[2] + n2;
-            const uint32_t ni = node_index<D>(g, c.nb);
-            R* gdst = acc + 4 * (size_t)ni;
-#pragma unroll
-            for (int a = 0; a < D; ++a) atomicAdd(gdst + a, sum[a]);
-            atomicAdd(gdst + 3, sum[D]);
-        }
-        if (threadIdx.x < (1 << D)) {
-            int bb[3];
-            block_coords<D, R>(blk, c, bb);
-            bool in = true;
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                bb[a] += (threadIdx.x >> a) & 1;
-                if (bb[a] >= c.nb[a]) in = false;
-            }
-            if (in) {
-                const uint32_t b2 = (D == 3) ? ((uint32_t)bb[2] * c.nb[1] + bb[1]) * c.nb[0] + bb[0]
-                                             : (uint32_t)bb[1] * c.nb[0] + bb[0];
-                flags[b2] = 1u;
-            }
-        }
+    tile_flush_nodes<D, ORDER, R>(cellsum, occ, bo, blk, acc, flags, c, nt);
 }
 
 // two FP32 fused multiply-adds in one packed instruction (c0 += a0 b0, c1 += a1 b1), each
@@ -559,6 +576,121 @@ template <> __device__ __forceinline__ void fma_pair<float>(float& c0, float& c1
         : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
 }
 
+// One particle's stencil sums added to a lane's registers cur (the z-slab SLAB of the
+// stencil for 3-D cubic).  A lane past its cell's run (live false) carries a neutral
+// particle: an in-cell position and zero state, so its weights are finite and it adds
+// zeros.  A particle outside the tile's reach sets the range error and adds nothing.
+template <int D, int ORDER, typename R, int KZ, int SLAB>
+__device__ __forceinline__ void p2g_cells_particle(Particle<D, R>& p, bool live, const int* lb, const int* bo,
+                                                   const DevCfg<R>& c, uint32_t* err, R m, R sC, R dt_dx,
+                                                   bool with_tau, R* cur)
+{
+    constexpr int K = ORDER + 1;
+    constexpr int NV = D + 1;
+    if (!live) {   // neutral: an in-cell position and zero state (finite weights, zero sums)
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            p.o[a] = R(0.5);
+            p.cell[a] = bo[a] + lb[a] + (ORDER == 3 ? 1 : 0);
+            p.v[a] = R(0);
+        }
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) p.B[i] = R(0);
+#pragma unroll
+        for (int i = 0; i < ((D == 3) ? 6 : 3); ++i) p.tau[i] = R(0);
+    }
+    int base[D];
+    R w[D][K], dw[D][K], fx[D];
+    bool ok = particle_stencil<D, ORDER, R>(p.o, p.cell, c, base, fx, w, dw);
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+        if (base[a] - bo[a] != lb[a]) ok = false;
+    if (live && !ok) {
+        set_err(err, APIC_ERRBIT_RANGE);
+        live = false;
+    }
+    const R ml = live ? m : R(0);
+    R mv[D], mC[D * D], T[D * D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) mv[a] = ml * p.v[a];
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) mC[i] = (live ? sC : R(0)) * p.B[i];
+    if (with_tau) {
+        R tau[D * D];
+        tau_full<D, R>(p.tau, tau);
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) T[i] = (live ? dt_dx : R(0)) * tau[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) T[i] = R(0);
+    }
+    // The weights are tensor products, so the contributions separate axis by axis
+    // (r = node - fx in grid units, T = dt/dx tau, mC = m B D^{-1} dx):
+    //   dp_c(i,j,k) = w0_i P_c(j,k) + E_c(i) S(j,k),       mass = w0_i m S(j,k)
+    //   P_c(j,k) = w1_j Q_c(k) + H_c(j) w2_k,              S(j,k) = w1_j w2_k
+    //   Q_c(k) = m v_c w2_k + mC_c2 (r w)2_k - T_c2 dw2_k
+    //   H_c(j) = mC_c1 (r w)1_j - T_c1 dw1_j,  E_c(i) = mC_c0 (r w)0_i - T_c0 dw0_i
+    // which is w m (v + C (x_i - x_p)) - dt tau grad w summed in fewer operations.
+    if (D == 3) {
+        R E[3][K], H[3][K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            const R rw0 = (R(i) - fx[0]) * w[0][i], rw1 = (R(i) - fx[1]) * w[1][i];
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                E[cc][i] = mC[cc * 3 + 0] * rw0 - T[cc * 3 + 0] * dw[0][i];
+                H[cc][i] = mC[cc * 3 + 1] * rw1 - T[cc * 3 + 1] * dw[1][i];
+            }
+        }
+#pragma unroll
+        for (int icl = 0; icl < KZ; ++icl) {
+            const int ic = SLAB * KZ + icl;
+            const R w2 = w[2][ic], dw2 = dw[2][ic], rw2 = (R(ic) - fx[2]) * w2;
+            R Q[3];
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) Q[cc] = mv[cc] * w2 + mC[cc * 3 + 2] * rw2 - T[cc * 3 + 2] * dw2;
+#pragma unroll
+            for (int ib = 0; ib < K; ++ib) {
+                const R S = w[1][ib] * w2, mS = ml * S;
+                R P[3];
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) P[cc] = w[1][ib] * Q[cc] + H[cc][ib] * w2;
+#pragma unroll
+                for (int ia = 0; ia < K; ++ia) {
+                    const int j = ia + K * ib + K * K * icl;
+                    // (c0, c1) and (c2, mass) as packed pairs
+                    fma_pair<R>(cur[j * NV + 0], cur[j * NV + 1], E[0][ia], E[1][ia], S, S);
+                    fma_pair<R>(cur[j * NV + 0], cur[j * NV + 1], w[0][ia], w[0][ia], P[0], P[1]);
+                    fma_pair<R>(cur[j * NV + 2], cur[j * NV + 3], E[2][ia], R(0), S, S);
+                    fma_pair<R>(cur[j * NV + 2], cur[j * NV + 3], w[0][ia], w[0][ia], P[2], mS);
+                }
+            }
+        }
+    } else {
+        R E[2][K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            const R rw0 = (R(i) - fx[0]) * w[0][i];
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) E[cc][i] = mC[cc * 2 + 0] * rw0 - T[cc * 2 + 0] * dw[0][i];
+        }
+#pragma unroll
+        for (int ib = 0; ib < K; ++ib) {
+            const R w1 = w[1][ib], rw1 = (R(ib) - fx[1]) * w1, mw1 = ml * w1;
+            R Q[2];
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) Q[cc] = mv[cc] * w1 + mC[cc * 2 + 1] * rw1 - T[cc * 2 + 1] * dw[1][ib];
+#pragma unroll
+            for (int ia = 0; ia < K; ++ia) {
+                const int j = ia + K * ib;
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) cur[j * NV + cc] += w[0][ia] * Q[cc] + E[cc][ia] * w1;
+                cur[j * NV + 2] += w[0][ia] * mw1;
+            }
+        }
+    }
+}
+
 // One tile of the cell-parallel P2G (whole CTA, NT = 128 threads).  On entry the CTA is
 // converged; cbeg / cend hold zeros and *s_cell = 0 (set by the caller before its last
 // barrier).  Leaves the smem free for the next tile after its final barrier.
@@ -571,8 +703,6 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
 {
     constexpr int NT = 128;
     constexpr int K = ORDER + 1;
-    constexpr int TE = 4 + ORDER;
-    constexpr int TN = (D == 3) ? TE * TE * TE : TE * TE;
     constexpr int NS = (D == 3) ? K * K * K : K * K;
     constexpr int NV = D + 1;
     constexpr int NVAL = NS * NV;
@@ -649,108 +779,10 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
                     const uint32_t kq = kn + (uint32_t)G;
                     if (kq < ke) qn = perm[kq];
                 }
-                if (!live) {   // neutral: an in-cell position and zero state (finite weights, zero sums)
-#pragma unroll
-                    for (int a = 0; a < D; ++a) {
-                        p.o[a] = R(0.5);
-                        p.cell[a] = bo[a] + lb[a] + (ORDER == 3 ? 1 : 0);
-                        p.v[a] = R(0);
-                    }
-#pragma unroll
-                    for (int i = 0; i < D * D; ++i) p.B[i] = R(0);
-#pragma unroll
-                    for (int i = 0; i < ((D == 3) ? 6 : 3); ++i) p.tau[i] = R(0);
-                }
-                int base[D];
-                R w[D][K], dw[D][K], fx[D];
-                bool ok = particle_stencil<D, ORDER, R>(p.o, p.cell, c, base, fx, w, dw);
-#pragma unroll
-                for (int a = 0; a < D; ++a)
-                    if (base[a] - bo[a] != lb[a]) ok = false;
-                if (live && !ok) {
-                    set_err(err, APIC_ERRBIT_RANGE);
-                    live = false;
-                }
-                const R ml = live ? m : R(0);
-                R mv[D], mC[D * D], T[D * D];
-#pragma unroll
-                for (int a = 0; a < D; ++a) mv[a] = ml * p.v[a];
-#pragma unroll
-                for (int i = 0; i < D * D; ++i) mC[i] = (live ? sC : R(0)) * p.B[i];
-                if (with_tau) {
-                    R tau[D * D];
-                    tau_full<D, R>(p.tau, tau);
-#pragma unroll
-                    for (int i = 0; i < D * D; ++i) T[i] = (live ? dt_dx : R(0)) * tau[i];
-                } else {
-#pragma unroll
-                    for (int i = 0; i < D * D; ++i) T[i] = R(0);
-                }
-                // The weights are tensor products, so the contributions separate axis by axis
-                // (r = node - fx in grid units, T = dt/dx tau, mC = m B D^{-1} dx):
-                //   dp_c(i,j,k) = w0_i P_c(j,k) + E_c(i) S(j,k),       mass = w0_i m S(j,k)
-                //   P_c(j,k) = w1_j Q_c(k) + H_c(j) w2_k,              S(j,k) = w1_j w2_k
-                //   Q_c(k) = m v_c w2_k + mC_c2 (r w)2_k - T_c2 dw2_k
-                //   H_c(j) = mC_c1 (r w)1_j - T_c1 dw1_j,  E_c(i) = mC_c0 (r w)0_i - T_c0 dw0_i
-                // which is w m (v + C (x_i - x_p)) - dt tau grad w summed in fewer operations.
-                if (D == 3) {
-                    R E[3][K], H[3][K];
-#pragma unroll
-                    for (int i = 0; i < K; ++i) {
-                        const R rw0 = (R(i) - fx[0]) * w[0][i], rw1 = (R(i) - fx[1]) * w[1][i];
-#pragma unroll
-                        for (int cc = 0; cc < 3; ++cc) {
-                            E[cc][i] = mC[cc * 3 + 0] * rw0 - T[cc * 3 + 0] * dw[0][i];
-                            H[cc][i] = mC[cc * 3 + 1] * rw1 - T[cc * 3 + 1] * dw[1][i];
-                        }
-                    }
-#pragma unroll
-                    for (int icl = 0; icl < KZ; ++icl) {
-                        const int ic = slab * KZ + icl;
-                        const R w2 = w[2][ic], dw2 = dw[2][ic], rw2 = (R(ic) - fx[2]) * w2;
-                        R Q[3];
-#pragma unroll
-                        for (int cc = 0; cc < 3; ++cc) Q[cc] = mv[cc] * w2 + mC[cc * 3 + 2] * rw2 - T[cc * 3 + 2] * dw2;
-#pragma unroll
-                        for (int ib = 0; ib < K; ++ib) {
-                            const R S = w[1][ib] * w2, mS = ml * S;
-                            R P[3];
-#pragma unroll
-                            for (int cc = 0; cc < 3; ++cc) P[cc] = w[1][ib] * Q[cc] + H[cc][ib] * w2;
-#pragma unroll
-                            for (int ia = 0; ia < K; ++ia) {
-                                const int j = ia + K * ib + K * K * icl;
-                                // (c0, c1) and (c2, mass) as packed pairs
-                                fma_pair<R>(cur[j * NV + 0], cur[j * NV + 1], E[0][ia], E[1][ia], S, S);
-                                fma_pair<R>(cur[j * NV + 0], cur[j * NV + 1], w[0][ia], w[0][ia], P[0], P[1]);
-                                fma_pair<R>(cur[j * NV + 2], cur[j * NV + 3], E[2][ia], R(0), S, S);
-                                fma_pair<R>(cur[j * NV + 2], cur[j * NV + 3], w[0][ia], w[0][ia], P[2], mS);
-                            }
-                        }
-                    }
-                } else {
-                    R E[2][K];
-#pragma unroll
-                    for (int i = 0; i < K; ++i) {
-                        const R rw0 = (R(i) - fx[0]) * w[0][i];
-#pragma unroll
-                        for (int cc = 0; cc < 2; ++cc) E[cc][i] = mC[cc * 2 + 0] * rw0 - T[cc * 2 + 0] * dw[0][i];
-                    }
-#pragma unroll
-                    for (int ib = 0; ib < K; ++ib) {
-                        const R w1 = w[1][ib], rw1 = (R(ib) - fx[1]) * w1, mw1 = ml * w1;
-                        R Q[2];
-#pragma unroll
-                        for (int cc = 0; cc < 2; ++cc) Q[cc] = mv[cc] * w1 + mC[cc * 2 + 1] * rw1 - T[cc * 2 + 1] * dw[1][ib];
-#pragma unroll
-                        for (int ia = 0; ia < K; ++ia) {
-                            const int j = ia + K * ib;
-#pragma unroll
-                            for (int cc = 0; cc < 2; ++cc) cur[j * NV + cc] += w[0][ia] * Q[cc] + E[cc][ia] * w1;
-                            cur[j * NV + 2] += w[0][ia] * mw1;
-                        }
-                    }
-                }
+                if (ZS == 1 || slab == 0)
+                    p2g_cells_particle<D, ORDER, R, KZ, 0>(p, live, lb, bo, c, err, m, sC, dt_dx, with_tau, cur);
+                else
+                    p2g_cells_particle<D, ORDER, R, KZ, ZS - 1>(p, live, lb, bo, c, err, m, sC, dt_dx, with_tau, cur);
             }
             cp_async_wait<0>();
             int off = 0, cnt = NVS;
