@@ -203,49 +203,62 @@ __global__ void __launch_bounds__(256) k_scan_down(const uint32_t* in, uint32_t*
 // ---------------------------------------------------------------- tiles
 // A tile is a maximal run of sorted particles with the same node block inside one aligned
 // chunk of `tile` particles; a new tile starts at every chunk start and every block change.
-__device__ __forceinline__ bool is_head(const uint32_t* skeys, int64_t k, int64_t chunk_start, int sh)
+// Tile heads of chunk [cs, cs + tile), tile <= 4096: thread t of the 256 takes the kpt =
+// tile / 256 consecutive keys from cs + kpt t (four 16-byte loads for a full aligned chunk of
+// 4096) plus the key before them, so the chunk costs about one memory latency; bit i of the
+// result flags a head at cs + kpt t + i.
+__device__ __forceinline__ unsigned chunk_head_bits(const uint32_t* __restrict__ skeys, int64_t n, int sh, int tile,
+                                                    int64_t cs)
 {
-    return k == chunk_start || (skeys[k] >> sh) != (skeys[k - 1] >> sh);
+    const int kpt = tile >> 8;
+    const int64_t ce = cs + tile < n ? cs + tile : n;
+    const int64_t k0 = cs + (int64_t)threadIdx.x * kpt;
+    uint32_t key[16];
+    if (kpt == 16 && k0 + 16 <= ce && ((reinterpret_cast<uintptr_t>(skeys + k0) & 15u) == 0u)) {
+        const uint4* q = reinterpret_cast<const uint4*>(skeys + k0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint4 v = __ldg(q + j);
+            key[4 * j + 0] = v.x;
+            key[4 * j + 1] = v.y;
+            key[4 * j + 2] = v.z;
+            key[4 * j + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) key[i] = (i < kpt && k0 + i < ce) ? skeys[k0 + i] : 0u;
+    }
+    const uint32_t prev = (k0 > cs && k0 < ce) ? skeys[k0 - 1] : 0u;
+    unsigned bits = 0u;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const uint32_t pk = i == 0 ? prev : key[i - 1];
+        if (i < kpt && k0 + i < ce && (k0 + i == cs || (key[i] >> sh) != (pk >> sh))) bits |= 1u << i;
+    }
+    return bits;
 }
 
-// Tile heads of chunk [cs, cs + tile) are found 256 consecutive keys at a time (coalesced
-// reads; a warp ballot ranks the heads of each round in order).
+// number of heads of the chunk (whole block of 256)
 __device__ __forceinline__ uint32_t count_heads(const uint32_t* __restrict__ skeys, int64_t n, int sh, int tile,
                                                 int64_t cs)
 {
-    const int64_t ce = cs + tile < n ? cs + tile : n;
-    uint32_t c = 0;
-    for (int64_t k = cs + threadIdx.x; k < ce; k += 256)
-        if (is_head(skeys, k, cs, sh)) ++c;
     uint32_t ex;
-    return block_excl_scan(c, ex);
+    return block_excl_scan((uint32_t)__popc(chunk_head_bits(skeys, n, sh, tile, cs)), ex);
 }
 
-// writes, in order, every head of the chunk through emit(position, k)
+// writes, in index order, every head of the chunk through emit(position, k) (whole block of
+// 256): one block scan of the per-thread head counts gives each thread its first position
 template <class Emit>
 __device__ __forceinline__ void write_heads(const uint32_t* __restrict__ skeys, int64_t n, int sh, int tile, int64_t cs,
                                             uint32_t pos0, Emit emit)
 {
-    __shared__ uint32_t wsum[8];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t ce = cs + tile < n ? cs + tile : n;
-    uint32_t pos = pos0;
-    for (int64_t r = cs; r < ce; r += 256) {
-        const int64_t k = r + threadIdx.x;
-        const bool h = k < ce && is_head(skeys, k, cs, sh);
-        const unsigned bal = __ballot_sync(0xffffffffu, h);
-        if (lane == 0) wsum[w] = (uint32_t)__popc(bal);
-        __syncthreads();
-        uint32_t before = 0, total = 0;
-        for (int i = 0; i < 8; ++i) {
-            const uint32_t v = wsum[i];
-            before += i < w ? v : 0u;
-            total += v;
-        }
-        if (h) emit(pos + before + (uint32_t)__popc(bal & lanemask_lt()), k);
-        pos += total;
-        __syncthreads();
-    }
+    const unsigned bits = chunk_head_bits(skeys, n, sh, tile, cs);
+    uint32_t ex;
+    block_excl_scan((uint32_t)__popc(bits), ex);
+    const int64_t k0 = cs + (int64_t)threadIdx.x * (tile >> 8);
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        if ((bits >> i) & 1u) emit(pos0 + ex + (uint32_t)__popc(bits & ((1u << i) - 1u)), k0 + i);
 }
 
 __global__ void __launch_bounds__(256) k_tile_count(const uint32_t* __restrict__ skeys, int64_t n, int sh, int tile,
@@ -533,7 +546,6 @@ __global__ void __launch_bounds__(RT) k_moved_compact(const uint32_t* __restrict
                                                       uint32_t* __restrict__ choff)
 {
     __shared__ uint32_t wc[RI][RW];
-    __shared__ uint32_t s_excl;
     const uint32_t t = blockIdx.x;
     uint32_t excl;
     if (off) {
