@@ -30,7 +30,7 @@ struct Buffers {
     uint32_t* choff;
     uint32_t* mcnt;              // moved count per chunk
     uint32_t* mctl;              // [1] moved count, [2..5] pass tile counters
-    uint32_t* mhist;             // [4][256] digit counts of the moved keys (follows mctl)
+    uint32_t* mhist;             // [kMhistCopies][4][256] digit counts of the moved keys (follows mctl)
     unsigned long long* lbs;     // 256 * (radix tiles + 1)
     uint32_t* scan_part;         // partial sums of the device scan
     uint32_t* tiles;             // tile start offsets (+ end sentinel)
@@ -95,7 +95,10 @@ struct SortDesc {
 int radix_tiles(int64_t n);
 size_t scan_partials_needed(int64_t n);
 // sorts knext (values = identity) into (*keys_out, *vals_out); returns the CUDA error
-constexpr size_t kMsortCtlBytes = 64 + 4 * 256 * 4;   // mctl words + mhist
+// copies of the incremental sort's digit histogram (chunk t adds to copy t % kMhistCopies;
+// batched members use copy 0 only)
+constexpr int kMhistCopies = 16;
+constexpr size_t kMsortCtlBytes = 64 + (size_t)kMhistCopies * 4 * 256 * 4;   // mctl words + mhist
 // Incremental stable sort of knext given the previous sorted keys pk, valid when the
 // particles are stored in that previous order; writes keys / permutation to kout / vout.
 cudaError_t resort(const Buffers& b, int64_t n, int key_bits, const uint32_t* pk, uint32_t* kout, uint32_t* vout,

@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(RT) k_onesweep_pass(const uint32_t* __restrict
 //   k_moved_compact  compacts M in index order (chunk offsets by reduction) and stores m
 //   k_msort_pass  one LSD pass over M (m read on the device; tiles taken from a counter)
 //   k_merge       U element k goes to (k - #M before k) + #M below (key, k); M element j to
-//                 j + #U below (key, idx), found by binary search over P and M's indices
+//                 j + #U below (key, idx), counted by the chunk of P whose key range holds it
 // Look-back words are 64-bit: (epoch << 32) | flag | count, with a fresh epoch for every
 // use, so a word left from an earlier use reads as unpublished and nothing is cleared.
 constexpr unsigned long long LB64_AGG = 1ull << 30;
@@ -505,33 +505,40 @@ __device__ __forceinline__ uint32_t lookback64(unsigned long long* words, uint32
 }
 
 // moved keys of chunk t (RTILE consecutive indices, thread-major rounds): count per chunk and
-// the digit counts of every pass
+// the digit counts of every pass.  All keys of the thread are loaded before any is counted
+// (the shared-memory atomics would otherwise hold back the later loads), and the digit counts
+// go to copy t % kMhistCopies of the histogram: the high digits of the moved keys are nearly
+// all alike, and one global counter per digit would take every chunk's add in turn.
 __global__ void __launch_bounds__(RT) k_moved_count(const uint32_t* __restrict__ knext, const uint32_t* __restrict__ pk,
                                                     int64_t n, uint32_t* __restrict__ cnt, uint32_t* __restrict__ mhist,
                                                     int passes)
 {
     __shared__ uint32_t h[4][256];
     for (int i = threadIdx.x; i < 4 * 256; i += RT) (&h[0][0])[i] = 0u;
-    __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * RTILE;
-    uint32_t c = 0;
+    uint32_t kn[RI], kp[RI];
 #pragma unroll
     for (int r = 0; r < RI; ++r) {
         const int64_t k = base + r * RT + threadIdx.x;
-        if (k < n) {
-            const uint32_t key = knext[k];
-            if (key != pk[k]) {
-                ++c;
-                for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(key >> (8 * p)) & 255u], 1u);
-            }
+        kn[r] = k < n ? knext[k] : 0u;
+        kp[r] = k < n ? pk[k] : 0u;
+    }
+    __syncthreads();
+    uint32_t c = 0;
+#pragma unroll
+    for (int r = 0; r < RI; ++r) {
+        if (kn[r] != kp[r]) {
+            ++c;
+            for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(kn[r] >> (8 * p)) & 255u], 1u);
         }
     }
     uint32_t ex;
     const uint32_t total = block_excl_scan(c, ex);
     if (threadIdx.x == 0) cnt[blockIdx.x] = total;
+    uint32_t* hc = mhist + (size_t)(blockIdx.x % kMhistCopies) * (4 * 256);
     for (int i = threadIdx.x; i < passes * 256; i += RT) {
         const uint32_t v = (&h[0][0])[i];
-        if (v) atomicAdd(mhist + i, v);
+        if (v) atomicAdd(hc + i, v);
     }
 }
 
@@ -542,8 +549,8 @@ __global__ void __launch_bounds__(RT) k_moved_compact(const uint32_t* __restrict
                                                       int64_t n, const uint32_t* __restrict__ cnt,
                                                       const uint32_t* __restrict__ off, int nchunks,
                                                       uint32_t* __restrict__ ctl, uint32_t* __restrict__ mk,
-                                                      uint32_t* __restrict__ mv, uint32_t* __restrict__ midx,
-                                                      uint32_t* __restrict__ choff)
+                                                      uint32_t* __restrict__ mv,
+                                                      uint32_t* __restrict__ choff, uint32_t* __restrict__ err)
 {
     __shared__ uint32_t wc[RI][RW];
     const uint32_t t = blockIdx.x;
@@ -578,7 +585,12 @@ __global__ void __launch_bounds__(RT) k_moved_compact(const uint32_t* __restrict
                 run += c;
             }
         choff[t] = excl;
-        if ((int)t == nchunks - 1) ctl[MCTL_M] = run;
+        if ((int)t == nchunks - 1) {
+            // counts that add up to more than n keys cannot come from knext: the range
+            // error is raised and nothing is sorted
+            if (run > (uint32_t)n) atomicOr(err, APIC_ERRBIT_RANGE);
+            ctl[MCTL_M] = run <= (uint32_t)n ? run : 0u;
+        }
     }
     __syncthreads();
 #pragma unroll
@@ -586,9 +598,12 @@ __global__ void __launch_bounds__(RT) k_moved_compact(const uint32_t* __restrict
         if (bal[r] & (1u << lane)) {
             const int64_t k = base + r * RT + threadIdx.x;
             const uint32_t p = wc[r][w] + (uint32_t)__popc(bal[r] & lanemask_lt());
-            mk[p] = key[r];
-            mv[p] = (uint32_t)k;
-            midx[p] = (uint32_t)k;
+            if (p < (uint32_t)n) {
+                mk[p] = key[r];
+                mv[p] = (uint32_t)k;
+            } else {
+                atomicOr(err, APIC_ERRBIT_RANGE);
+            }
         }
     }
 }
@@ -606,8 +621,10 @@ __global__ void __launch_bounds__(RT) k_msort_pass(const uint32_t* __restrict__ 
     const uint32_t nt = (m + RTILE - 1) / RTILE;
     if (blockIdx.x >= nt) return;
     {
-        uint32_t ex;
-        block_excl_scan(hist[threadIdx.x], ex);
+        uint32_t hv = 0, ex;   // the digit's count, summed over the histogram's copies
+#pragma unroll
+        for (int cp = 0; cp < kMhistCopies; ++cp) hv += hist[cp * (4 * 256) + threadIdx.x];
+        block_excl_scan(hv, ex);
         dst0[threadIdx.x] = ex;
     }
     const int shift = 8 * pass;
@@ -680,87 +697,103 @@ __device__ __forceinline__ uint32_t below_m(const uint32_t* msk, const uint32_t*
     return lo;
 }
 
+// moved keys of a chunk's key range staged in shared memory for the merge's searches
+constexpr uint32_t MERGE_MCAP = 2048;
+
+// Chunk t of P (indices [base, end)) owns the moved keys M[j] with j in [s_lo, s_nx): those at
+// or above (P[base], base) and below the next chunk's first (P[end], end) (chunk 0 also the
+// ones below its first key).  Its unmoved keys u get c_u = #M below (P[k], k) by a search of
+// that range (staged in shared memory) and go to (k - #moved before k) + c_u.  A moved key
+// M[j] of the range lies above every unmoved key of the earlier chunks and below every one of
+// the later chunks, and above the chunk's own unmoved u exactly when c_u <= j; so it goes to
+// j + #unmoved before the chunk + #{u : c_u <= j}, counted by a search of the c_u (kept in
+// order in shared memory).
 __global__ void __launch_bounds__(RT) k_merge(const uint32_t* __restrict__ knext, const uint32_t* __restrict__ pk,
                                               int64_t n, const uint32_t* __restrict__ choff,
                                               const uint32_t* __restrict__ msk, const uint32_t* __restrict__ msv,
-                                              const uint32_t* __restrict__ midx, const uint32_t* __restrict__ ctl,
-                                              int nchunks, uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                                              uint32_t* err)
+                                              const uint32_t* __restrict__ ctl, int nchunks,
+                                              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, uint32_t* err)
 {
+    __shared__ uint32_t wc[RI][RW];
+    __shared__ uint32_t s_lo, s_nx, s_nm;
+    __shared__ uint32_t sk[MERGE_MCAP], sv[MERGE_MCAP];
+    __shared__ uint32_t cu[RTILE];
     const uint32_t m = ctl[MCTL_M];
-    if ((int)blockIdx.x < nchunks) {
-        __shared__ uint32_t wc[RI][RW];
-        __shared__ uint32_t s_lo, s_hi;
-        const uint32_t t = blockIdx.x;
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        const int64_t base = (int64_t)t * RTILE;
-        const int64_t kl = (base + RTILE < n ? base + RTILE : n) - 1;
-        if (threadIdx.x == 0) {
-            s_lo = below_m(msk, msv, 0u, m, pk[base], (uint32_t)base);
-            s_hi = below_m(msk, msv, s_lo, m, pk[kl], (uint32_t)kl + 1u);
-        }
-        unsigned bal[RI];
+    const uint32_t t = blockIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = (int64_t)t * RTILE;
+    const int64_t end = base + RTILE < n ? base + RTILE : n;
+    // the two bounds of the chunk's range, by two warps at once
+    if (threadIdx.x == 0) s_lo = below_m(msk, msv, 0u, m, pk[base], (uint32_t)base);
+    if (threadIdx.x == 32) s_nx = end < n ? below_m(msk, msv, 0u, m, pk[end], (uint32_t)end) : m;
+    unsigned bal[RI];
 #pragma unroll
-        for (int r = 0; r < RI; ++r) {
-            const int64_t k = base + r * RT + threadIdx.x;
-            const bool moved = k < n && knext[k] != pk[k];
-            bal[r] = __ballot_sync(FULL, moved);
-            if (lane == 0) wc[r][w] = (uint32_t)__popc(bal[r]);
+    for (int r = 0; r < RI; ++r) {
+        const int64_t k = base + r * RT + threadIdx.x;
+        const bool moved = k < n && knext[k] != pk[k];
+        bal[r] = __ballot_sync(FULL, moved);
+        if (lane == 0) wc[r][w] = (uint32_t)__popc(bal[r]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = choff[t];
+        for (int r = 0; r < RI; ++r)
+            for (int ww = 0; ww < RW; ++ww) {
+                const uint32_t c = wc[r][ww];
+                wc[r][ww] = run;
+                run += c;
+            }
+        s_nm = run - choff[t];
+    }
+    const uint32_t lo = s_lo, hi = s_nx > s_lo ? s_nx : s_lo;
+    const bool staged = hi - lo <= MERGE_MCAP;
+    if (staged)
+        for (uint32_t j = lo + threadIdx.x; j < hi; j += RT) {
+            sk[j - lo] = msk[j];
+            sv[j - lo] = msv[j];
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t run = choff[t];
-            for (int r = 0; r < RI; ++r)
-                for (int ww = 0; ww < RW; ++ww) {
-                    const uint32_t c = wc[r][ww];
-                    wc[r][ww] = run;
-                    run += c;
-                }
-        }
-        __syncthreads();
-        const uint32_t lo = s_lo, hi = s_hi;
+    __syncthreads();
+    const uint32_t uoff = (uint32_t)base - choff[t];   // unmoved keys before the chunk
 #pragma unroll
-        for (int r = 0; r < RI; ++r) {
-            const int64_t k = base + r * RT + threadIdx.x;
-            if (k < n && !(bal[r] & (1u << lane))) {
-                const uint32_t before = wc[r][w] + (uint32_t)__popc(bal[r] & lanemask_lt());
-                const uint32_t key = pk[k];
-                const uint32_t pos = (uint32_t)k - before + below_m(msk, msv, lo, hi, key, (uint32_t)k);
-                if (pos < (uint32_t)n) {
-                    kout[pos] = key;
-                    vout[pos] = (uint32_t)k;
-                } else {
-                    atomicOr(err, APIC_ERRBIT_RANGE);
-                }
-            }
-        }
-    } else {
-        const uint32_t stride = (gridDim.x - nchunks) * RT;
-        for (uint32_t j = (blockIdx.x - nchunks) * RT + threadIdx.x; j < m; j += stride) {
-            const uint32_t key = msk[j], idx = msv[j];
-            // K = #k with (P[k], k) below (key, idx)
-            uint32_t lo = 0, hi = (uint32_t)n;
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi) >> 1;
-                const uint32_t a = pk[mid];
-                if (a < key || (a == key && mid < idx)) lo = mid + 1;
-                else hi = mid;
-            }
-            const uint32_t K = lo;
-            // moved indices below K
-            uint32_t a = 0, b = m;
-            while (a < b) {
-                const uint32_t mid = (a + b) >> 1;
-                if (midx[mid] < K) a = mid + 1;
-                else b = mid;
-            }
-            const uint32_t pos = j + K - a;
+    for (int r = 0; r < RI; ++r) {
+        const int64_t k = base + r * RT + threadIdx.x;
+        if (k < n && !(bal[r] & (1u << lane))) {
+            const uint32_t before = wc[r][w] + (uint32_t)__popc(bal[r] & lanemask_lt());
+            const uint32_t key = pk[k];
+            const uint32_t c = staged ? lo + below_m(sk, sv, 0u, hi - lo, key, (uint32_t)k)
+                                      : below_m(msk, msv, lo, hi, key, (uint32_t)k);
+            const uint32_t u = (uint32_t)k - before;
+            if (u - uoff < (uint32_t)RTILE) cu[u - uoff] = c;
+            const uint32_t pos = u + c;
             if (pos < (uint32_t)n) {
                 kout[pos] = key;
-                vout[pos] = idx;
+                vout[pos] = (uint32_t)k;
             } else {
                 atomicOr(err, APIC_ERRBIT_RANGE);
             }
+        }
+    }
+    __syncthreads();
+    const uint32_t len = (uint32_t)(end - base);
+    if (s_nm > len) {   // moved counts that do not fit the chunk: report, place nothing more
+        if (threadIdx.x == 0) atomicOr(err, APIC_ERRBIT_RANGE);
+        return;
+    }
+    const uint32_t nu = len - s_nm;
+    for (uint32_t j = (t == 0 ? 0u : lo) + threadIdx.x; j < hi; j += RT) {
+        uint32_t a = 0, b = nu;
+        while (a < b) {
+            const uint32_t mid = (a + b) >> 1;
+            if (cu[mid] <= j) a = mid + 1;
+            else b = mid;
+        }
+        const bool in = staged && j >= lo;
+        const uint32_t pos = j + uoff + a;
+        if (pos < (uint32_t)n) {
+            kout[pos] = in ? sk[j - lo] : msk[j];
+            vout[pos] = in ? sv[j - lo] : msv[j];
+        } else {
+            atomicOr(err, APIC_ERRBIT_RANGE);
         }
     }
 }
@@ -1191,14 +1224,14 @@ cudaError_t resort(const Buffers& b, int64_t n, int key_bits, const uint32_t* pk
         if (e != cudaSuccess) return e;
         off = b.choff;
     }
-    k_moved_compact<<<nchunks, RT, 0, s>>>(b.knext, pk, n, b.mcnt, off, nchunks, b.mctl, b.mk[0], b.mv[0], b.midx,
-                                           b.choff);
+    k_moved_compact<<<nchunks, RT, 0, s>>>(b.knext, pk, n, b.mcnt, off, nchunks, b.mctl, b.mk[0], b.mv[0],
+                                           b.choff, b.err);
     const int grid = nchunks < sms * 8 ? nchunks : sms * 8;
     for (int p = 0; p < passes; ++p)
         k_msort_pass<<<grid, RT, 0, s>>>(b.mk[p & 1], b.mv[p & 1], b.mk[(p + 1) & 1], b.mv[(p + 1) & 1], b.mctl, p,
                                          b.mhist + 256 * p, b.lbs, (*epoch)++, b.err);
-    k_merge<<<nchunks + 2 * sms, RT, 0, s>>>(b.knext, pk, n, b.choff, b.mk[passes & 1], b.mv[passes & 1], b.midx,
-                                              b.mctl, nchunks, kout, vout, b.err);
+    k_merge<<<nchunks, RT, 0, s>>>(b.knext, pk, n, b.choff, b.mk[passes & 1], b.mv[passes & 1], b.mctl, nchunks,
+                                    kout, vout, b.err);
     return cudaGetLastError();
 }
 
