@@ -835,21 +835,23 @@ __global__ void __launch_bounds__(RT) kb_moved_count(const SortDesc* __restrict_
     const int64_t base = lt * RTILE;
     const uint32_t* P = bsorted[sim] ? d.kb[kpar] : nullptr;
     uint32_t* Pc = d.kb[kpar ^ 1];
+    // every key of the thread is loaded before any is counted (as in k_moved_count)
+    uint32_t kn[RI], kp[RI];
+#pragma unroll
+    for (int r = 0; r < RI; ++r) {
+        const int64_t k = base + r * RT + threadIdx.x;
+        kn[r] = k < n ? d.knext[k] : 0u;
+        kp[r] = (k < n && P) ? P[k] : 0u;
+    }
     uint32_t c = 0;
 #pragma unroll
     for (int r = 0; r < RI; ++r) {
         const int64_t k = base + r * RT + threadIdx.x;
         if (k < n) {
-            const uint32_t key = d.knext[k];
-            bool moved = true;
-            if (P) {
-                const uint32_t pk = P[k];
-                Pc[k] = pk;
-                moved = key != pk;
-            }
-            if (moved) {
+            if (P) Pc[k] = kp[r];
+            if (!P || kn[r] != kp[r]) {
                 ++c;
-                for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(key >> (8 * p)) & 255u], 1u);
+                for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(kn[r] >> (8 * p)) & 255u], 1u);
             }
         }
     }
