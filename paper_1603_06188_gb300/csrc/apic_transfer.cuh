@@ -632,7 +632,9 @@ __device__ __forceinline__ void p2g_cells_particle(Particle<D, R>& p, bool live,
     //   H_c(j) = mC_c1 (r w)1_j - T_c1 dw1_j,  E_c(i) = mC_c0 (r w)0_i - T_c0 dw0_i
     // which is w m (v + C (x_i - x_p)) - dt tau grad w summed in fewer operations.
     if (D == 3) {
-        R E[3][K], H[3][K];
+        R E[3][K], H[3][K], mw0[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) mw0[i] = ml * w[0][i];
 #pragma unroll
         for (int i = 0; i < K; ++i) {
             const R rw0 = (R(i) - fx[0]) * w[0][i], rw1 = (R(i) - fx[1]) * w[1][i];
@@ -651,7 +653,7 @@ __device__ __forceinline__ void p2g_cells_particle(Particle<D, R>& p, bool live,
             for (int cc = 0; cc < 3; ++cc) Q[cc] = mv[cc] * w2 + mC[cc * 3 + 2] * rw2 - T[cc * 3 + 2] * dw2;
 #pragma unroll
             for (int ib = 0; ib < K; ++ib) {
-                const R S = w[1][ib] * w2, mS = ml * S;
+                const R S = w[1][ib] * w2;
                 R P[3];
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc) P[cc] = w[1][ib] * Q[cc] + H[cc][ib] * w2;
@@ -661,8 +663,8 @@ __device__ __forceinline__ void p2g_cells_particle(Particle<D, R>& p, bool live,
                     // (c0, c1) and (c2, mass) as packed pairs
                     fma_pair<R>(cur[j * NV + 0], cur[j * NV + 1], E[0][ia], E[1][ia], S, S);
                     fma_pair<R>(cur[j * NV + 0], cur[j * NV + 1], w[0][ia], w[0][ia], P[0], P[1]);
-                    fma_pair<R>(cur[j * NV + 2], cur[j * NV + 3], E[2][ia], R(0), S, S);
-                    fma_pair<R>(cur[j * NV + 2], cur[j * NV + 3], w[0][ia], w[0][ia], P[2], mS);
+                    cur[j * NV + 2] += E[2][ia] * S;
+                    fma_pair<R>(cur[j * NV + 2], cur[j * NV + 3], w[0][ia], mw0[ia], P[2], S);
                 }
             }
         }

@@ -84,3 +84,14 @@ def test_resort_small_tiles(apic):
     sc = scenes.falling_cube_3d(res=32, side=0.5, ppc=8, seed=3)
     w = np.array([0.0, 150.0, -100.0])
     run_and_check(apic, 32, 0.5, 8, lambda rng, n: np.cross(w, sc.x - 0.5), steps=3, tile=256)
+
+
+def test_resort_collapse(apic):
+    # an affine velocity field that carries every particle 90 % of the way to the centre in
+    # one step: the changed keys crowd into a few node blocks, so a chunk of the previous
+    # order owns far more changed keys than the merge stages in shared memory
+    dt, res = 2e-5, 32
+    sc = scenes.falling_cube_3d(res=res, side=0.5, ppc=8, seed=3)
+    centre = sc.x.mean(axis=0)
+    moved = run_and_check(apic, res, 0.5, 8, lambda rng, n: -(sc.x - centre) * (0.9 / dt), steps=3, dt=dt)
+    assert moved[0] > 0.9 * sc.n
