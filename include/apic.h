@@ -92,6 +92,11 @@ typedef struct {
                                 (1 - a) sum w v~_i, a in [0, 1] (1 = the paper's FLIP); the
                                 velocities v_i before the grid update are kept (+32 B per
                                 node); not available in batches */
+    int p2g_group;           /* lanes that share one base cell in the cell-parallel P2G: 2 or
+                                4; 0 = chosen after the first sort following each upload from
+                                the particles per occupied node block (2 below 16 particles
+                                per cell, else 4) -- that apic_p2g reads the tile count back
+                                and so synchronises once.  Results agree to rounding. */
 } apic_config;
 
 /* Bytes of device workspace a simulation with this config and capacity needs.

@@ -34,6 +34,7 @@ struct apic_sim {
     uint32_t* skeys;       // last sort's keys / permutation (device)
     uint32_t* perm;
     bool order_sorted;     // the particles are stored in the order of skeys (after G2P)
+    bool group_pending;    // p2g_group is chosen after the next full sort (auto, new upload)
     uint32_t epoch;        // look-back epoch of the incremental sort (0: words not cleared yet)
     int64_t max_tiles;
     std::string err;
@@ -110,6 +111,9 @@ apic_status fill_cfg(const apic_config* in, int64_t max_particles, HostCfg* c, s
     c->tile = tile;
     if (in->p2g_kernel < 0 || in->p2g_kernel > 4) { *why = "p2g_kernel must be 0..4"; return APIC_ERR_ARG; }
     c->p2g_kernel = in->p2g_kernel != 0 ? in->p2g_kernel : 2;   // default: cell-parallel
+    if (in->p2g_group != 0 && in->p2g_group != 2 && in->p2g_group != 4) { *why = "p2g_group must be 0, 2 or 4"; return APIC_ERR_ARG; }
+    c->p2g_group = in->p2g_group != 0 ? in->p2g_group : 4;
+    c->p2g_group_auto = in->p2g_group == 0;
     c->key_bits = 2 * in->dim + ceil_log2(c->nblocks);
     if (c->key_bits > 32) { *why = "grid too large for 32-bit cell keys"; return APIC_ERR_UNSUPPORTED; }
     c->capacity = max_particles;
@@ -308,6 +312,7 @@ apic_status apic_create(const apic_config* cfg, int64_t max_particles, void* wor
     s->phase = 0;
     s->skeys = s->perm = nullptr;
     s->order_sorted = false;
+    s->group_pending = false;
     s->epoch = 0;
     s->max_tiles = L.max_tiles;
     s->launches = 0;
@@ -426,6 +431,7 @@ apic_status apic_upload(apic_sim* s, int64_t n, const double* x, const double* v
     s->phase = 0;
     s->skeys = s->perm = nullptr;
     s->order_sorted = false;
+    s->group_pending = s->c.p2g_group_auto != 0;   // the new particle set's density decides
     s->c.mat = 0;   // a new particle set: materials come from the configuration until set again
     CK(DISPATCH(s, upload, s->c, s->b, s->cur, n, dx_, dv, dB, dF, s->stream), "upload kernel");
     if (!on_device) return check_device(s);
@@ -542,6 +548,16 @@ apic_status apic_p2g(apic_sim* s)
     {
         PhaseScope ps(s, APIC_PHASE_TILES, 5);
         CK(build_tiles(s->b, s->skeys, n, s->c.dim, s->c.tile, s->max_tiles, s->stream), "tile list");
+    }
+    if (s->group_pending) {
+        // particles per occupied base cell, from the tile count (a node block of 4^d cells
+        // holds one tile up to tile_particles particles): fewer than 16 take groups of 2
+        uint32_t nt = 0;
+        CK(cudaMemcpyAsync(&nt, s->b.ntiles, sizeof(nt), cudaMemcpyDeviceToHost, s->stream), "read tile count");
+        CK(cudaStreamSynchronize(s->stream), "synchronize");
+        const double cells = (double)(nt ? nt : 1u) * (s->c.dim == 3 ? 64.0 : 16.0);
+        s->c.p2g_group = (double)n / cells < 16.0 ? 2 : 4;
+        s->group_pending = false;
     }
     {
         PhaseScope ps(s, APIC_PHASE_P2G, 1);

@@ -65,6 +65,8 @@ struct HostCfg {
     double mu, lam, mass, vol;
     int tile;                    // particles per tile (power of two)
     int p2g_kernel;              // 1 warp-segmented, 2 cell-parallel, 3 interleaved, 4 node-split
+    int p2g_group;               // lanes per base cell of the cell-parallel P2G (2 or 4)
+    int p2g_group_auto;          // 1: p2g_group follows the density after each upload
     int key_bits;
     int nblocks;
     int64_t capacity;

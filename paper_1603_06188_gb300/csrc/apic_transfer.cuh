@@ -16,9 +16,6 @@ namespace apic {
 
 constexpr unsigned FULLMASK = 0xffffffffu;
 constexpr int TPB = 256;
-#ifndef APIC_P2G_GROUP
-#define APIC_P2G_GROUP 4   // lanes that share one base cell in the cell-parallel P2G
-#endif
 
 template <typename R> struct HostToDev {
     static DevCfg<R> make(const HostCfg& h, int64_t n)
@@ -1955,21 +1952,12 @@ template <typename R> struct Impl {
         else if (!L.p2g_cells)
             APIC_DISPATCH(h, (k_p2g<D, O, R><<<L.p2g_grid, TPB, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, acc,
                                                                           b.flags, c, b.err, b.fallbacks)));
-        else if (h.dim == 3 && h.order == 2)
-            k_p2g_cells<3, 2, R, APIC_P2G_GROUP><<<L.p2g_grid, 128, p2g_cells_smem<3, 2, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc,
-                                                                b.flags, c, b.err, b.fallbacks);
-        else if (h.dim == 2 && h.order == 2)
-            k_p2g_cells<2, 2, R, APIC_P2G_GROUP><<<L.p2g_grid, 128, p2g_cells_smem<2, 2, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc,
-                                                                b.flags, c, b.err, b.fallbacks);
-        else if (h.dim == 2 && h.order == 3)
-            k_p2g_cells<2, 3, R, APIC_P2G_GROUP><<<L.p2g_grid, 128, p2g_cells_smem<2, 3, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc,
-                                                                b.flags, c, b.err, b.fallbacks);
-        else if (h.dim == 3 && h.order == 3)
-            k_p2g_cells<3, 3, R, APIC_P2G_GROUP><<<L.p2g_grid, 128, p2g_cells_smem<3, 3, R>(), s>>>(st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc,
-                                                                b.flags, c, b.err, b.fallbacks);
+        else if (h.p2g_group == 2)
+            APIC_DISPATCH(h, (k_p2g_cells<D, O, R, 2><<<L.p2g_grid, 128, p2g_cells_smem<D, O, R>(), s>>>(
+                                 st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc, b.flags, c, b.err, b.fallbacks)));
         else
-            k_p2g<3, 3, R><<<L.p2g_grid, TPB, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, acc, b.flags, c, b.err,
-                                                      b.fallbacks);
+            APIC_DISPATCH(h, (k_p2g_cells<D, O, R, 4><<<L.p2g_grid, 128, p2g_cells_smem<D, O, R>(), s>>>(
+                                 st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc, b.flags, c, b.err, b.fallbacks)));
         return cudaGetLastError();
         };
         cudaError_t e = launch(c0, (R*)b.acc);
@@ -2100,11 +2088,20 @@ template <typename R> struct Impl {
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g<D, O, R>, TPB, 0);
             else {
                 constexpr int O2 = O;
-                e = cudaFuncSetAttribute(k_p2g_cells<D, O2, R, APIC_P2G_GROUP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                // both lane groups are set up: the group can change at the next upload
+                e = cudaFuncSetAttribute(k_p2g_cells<D, O2, R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)p2g_cells_smem<D, O2, R>());
                 if (e == cudaSuccess)
-                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g_cells<D, O2, R, APIC_P2G_GROUP>, 128,
+                    e = cudaFuncSetAttribute(k_p2g_cells<D, O2, R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)p2g_cells_smem<D, O2, R>());
+                int per2 = 0;
+                if (e == cudaSuccess)
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_p2g_cells<D, O2, R, 2>, 128,
                                                                       p2g_cells_smem<D, O2, R>());
+                if (e == cudaSuccess)
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g_cells<D, O2, R, 4>, 128,
+                                                                      p2g_cells_smem<D, O2, R>());
+                if (e == cudaSuccess && per2 < *p2g_per_sm) *p2g_per_sm = per2;
             }
             if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(g2p_per_sm, k_g2p<D, O, R, false>, G2P_THREADS, 0);
         });

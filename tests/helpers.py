@@ -39,7 +39,7 @@ def state_for(scene: scenes.Scene, order: int, seed: int = 0, vscale: float = 1.
 
 def configs(dim, order, res, dx, precision=32, transfer="apic", dt=1e-3, gravity=(0, 0, 0),
             boundary="none", wall=0, model="fcr", E=E_DEFAULT, nu=NU_DEFAULT, mass=1.0, vol=None,
-            tile=0, p2g_kernel=0):
+            tile=0, p2g_kernel=0, p2g_group=0):
     """Matching (library config, oracle config, mass, volume)."""
     from paper_1603_06188_gb300 import apic
 
@@ -47,7 +47,8 @@ def configs(dim, order, res, dx, precision=32, transfer="apic", dt=1e-3, gravity
         vol = dx ** dim / 8
     gc = apic.make_config(dim=dim, order=order, precision=precision, transfer=transfer, res=res, dx=dx, dt=dt,
                           gravity=gravity, boundary=boundary, wall=wall, model=model, E=E, nu=nu,
-                          particle_mass=mass, particle_volume=vol, tile_particles=tile, p2g_kernel=p2g_kernel)
+                          particle_mass=mass, particle_volume=vol, tile_particles=tile, p2g_kernel=p2g_kernel,
+                          p2g_group=p2g_group)
     oc = oracle.make_cfg(dim=dim, order=order, transfer=transfer, res=res, dx=dx, dt=dt, gravity=gravity,
                          boundary=boundary, wall=wall,
                          model={"fcr": "fcr", "fixed_corotated": "fcr", "nh": "nh", "neohookean": "nh"}.get(model, "none"),

@@ -51,12 +51,13 @@ def _ids(c):
 
 
 def run_one_step(apic, dim, order, prec, res, ppc, model="fcr", transfer="apic", dt=2e-3, gravity=None,
-                 boundary="none", wall=0, tile=0, seed=0, p2g_kernel=0):
+                 boundary="none", wall=0, tile=0, seed=0, p2g_kernel=0, p2g_group=0):
     sc = cube_scene(dim, res, ppc, seed=seed)
     x, v, B, F = state_for(sc, order, seed=seed)
     g = gravity if gravity is not None else (0.0,) * dim
     gc, oc, m, vol = configs(dim, order, (res,) * dim, sc.dx, precision=prec, transfer=transfer, dt=dt,
-                             gravity=g, boundary=boundary, wall=wall, model=model, tile=tile, p2g_kernel=p2g_kernel)
+                             gravity=g, boundary=boundary, wall=wall, model=model, tile=tile, p2g_kernel=p2g_kernel,
+                             p2g_group=p2g_group)
     sim = apic.Sim(gc, len(x) + 7)
     sim.upload(x, v, B, F)
     x0, v0, B0, F0 = sim.download()          # the GPU's exact input state
@@ -159,6 +160,31 @@ def test_p2g_variants_and_tile_sizes_agree(apic, tile, p2g_kernel, dim, order, p
     gm, gmv, gf, _ = oracle.p2g(r["oc"], x0, v0, B0, F0, r["m"], r["vol"])
     assert relerr(r["grid_p2g"][0], gm) <= TOL[prec]
     assert relerr(r["grid_p2g"][1], gmv + r["oc"].dt * gf) <= TOL[prec]
+
+
+@pytest.mark.parametrize("p2g_group", [0, 2, 4])
+@pytest.mark.parametrize("ppc", [8, 32])
+@pytest.mark.parametrize("dim,order,prec", [(3, 2, 32), (3, 3, 32), (2, 2, 64)])
+def test_p2g_lane_groups_agree(apic, p2g_group, ppc, dim, order, prec):
+    """The cell-parallel P2G with two or four lanes per base cell, and the choice made from
+    the particle density (0), gives the oracle's grid momentum and the same G2P output."""
+    if dim == 2:
+        ppc = ppc // 2
+    r = run_one_step(apic, dim, order, prec, 24 if dim == 3 else 64, ppc, p2g_group=p2g_group)
+    x0, v0, B0, F0 = r["in"]
+    gm, gmv, gf, _ = oracle.p2g(r["oc"], x0, v0, B0, F0, r["m"], r["vol"])
+    assert relerr(r["grid_p2g"][0], gm) <= TOL[prec]
+    assert relerr(r["grid_p2g"][1], gmv + r["oc"].dt * gf) <= TOL[prec]
+    _, vt = r["grid_vel"]
+    _, v1, B1, _, _ = oracle.g2p(r["oc"], x0, F0, vt, vt)
+    gx, gv, gB, gF = r["out"]
+    assert relerr(gv, v1) <= TOL[prec]
+    assert relerr(gB, B1) <= TOL[prec]
+
+
+def test_p2g_group_argument_checked(apic):
+    with pytest.raises(apic.ApicError):
+        apic.Sim(apic.make_config(dim=3, order=2, res=(16,) * 3, dx=1 / 16, p2g_group=3), 10)
 
 
 def test_gpu_momentum_conservation_fp32(apic):
