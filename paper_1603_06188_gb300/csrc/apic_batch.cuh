@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(G2P_THREADS, 4) kb_g2p(SimDesc<R>* __restrict_
     constexpr int BN = (D == 3) ? 64 : 16;
     constexpr int NB = 1 << D;
     __shared__ __align__(128) R sv[2][NB][BN][4];
+    __shared__ __align__(16) R stage[g2p_staged<R>() ? 2 * G2P_THREADS * kG2PSlot : 1];
     __shared__ __align__(8) uint64_t mbar[2];
     // s_t[b]: the tile staged in buffer b (written and read as in k_g2p)
     __shared__ int s_ok, s_t[2];
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(G2P_THREADS, 4) kb_g2p(SimDesc<R>* __restrict_
         const uint32_t end = tile_end(tile_sim, tile_start, t, ntiles, sim, (uint32_t)sd.c.n);
         float smax_unused = 0.0f;   // members are stepped at their fixed dt
         g2p_compute<D, ORDER, R, EXT, G2P_THREADS>(sd.st[sd.cur], sd.st[sd.cur ^ 1], sd.vb[kpar], sd.kb[kpar], start, end, sd.knext, sd.c,
-                                 sd.err, sd.fallbacks, sv[buf], smax_unused, nullptr);
+                                 sd.err, sd.fallbacks, sv[buf], smax_unused, nullptr, stage);
         __syncthreads();
         phase[buf] ^= 1u;
     }

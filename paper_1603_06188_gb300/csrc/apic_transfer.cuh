@@ -1387,6 +1387,42 @@ __device__ __forceinline__ bool g2p_wait(uint64_t* mbar, unsigned parity, uint32
     return false;
 }
 
+// G2P's read-ahead of the next particle's x and F goes through shared memory in FP32 (a slot
+// of 16 words per thread and buffer: A, Fa, Fb, Fc), not registers: the kernel works at its
+// register cap, and the 16 registers a staged particle would hold are worth more there.
+template <typename R> __host__ __device__ constexpr bool g2p_staged() { return sizeof(R) == 4; }
+constexpr int kG2PSlot = 16;
+template <int D, typename R>
+__device__ __forceinline__ void stage_xF(R* slot, const PState<R>& s, uint32_t q)
+{
+    cp_async16(slot + 0, s.A + q);
+    cp_async16(slot + 4, s.Fa + q);
+    if (D == 3) {
+        cp_async16(slot + 8, s.Fb + q);
+        cp_async8(slot + 12, s.Fc + q);
+    }
+}
+template <int D, typename R>
+__device__ __forceinline__ void read_xF(const R* slot, Particle<D, R>& p)
+{
+    const V4<R> a = *reinterpret_cast<const V4<R>*>(slot + 0);
+    const V4<R> fa = *reinterpret_cast<const V4<R>*>(slot + 4);
+    if (D == 3) {
+        const V4<R> fb = *reinterpret_cast<const V4<R>*>(slot + 8);
+        const V2<R> fc = *reinterpret_cast<const V2<R>*>(slot + 12);
+        p.o[0] = a.x; p.o[1] = a.y; p.o[2] = a.z;
+        unpack_cell<D>(r2u(a.w), p.cell);
+        p.F[0] = fa.x; p.F[1] = fa.y; p.F[2] = fa.z; p.F[3] = fa.w;
+        p.F[4] = fb.x; p.F[5] = fb.y; p.F[6] = fb.z; p.F[7] = fb.w;
+        p.F[8] = fc.x; p.id = r2u(fc.y);
+    } else {
+        p.o[0] = a.x; p.o[1] = a.y;
+        unpack_cell<D>(r2u(a.z), p.cell);
+        p.id = r2u(a.w);
+        p.F[0] = fa.x; p.F[1] = fa.y; p.F[2] = fa.z; p.F[3] = fa.w;
+    }
+}
+
 // the particles of one tile, with its grid blocks already in sv (whole CTA)
 // EXT: the material lane, the fused speed maximum and the FLIP update may be in use (else
 // compiled out)
@@ -1395,9 +1431,10 @@ __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>
                                             const uint32_t* __restrict__ skeys, uint32_t start, uint32_t end,
                                             uint32_t* __restrict__ knext, const DevCfg<R>& c, uint32_t* err,
                                             uint32_t* fallbacks, const R (*sv)[(D == 3) ? 64 : 16][4],
-                                            float& smax_l, const R* __restrict__ vdel)
+                                            float& smax_l, const R* __restrict__ vdel, R* stage)
 {
     constexpr int K = ORDER + 1;
+    constexpr bool STG = g2p_staged<R>();
     const R dt_dx = step_dt(c) * c.inv_dx;
     const uint32_t blk = skeys[start] >> (2 * D);
     int bc[3] = {0, 0, 0};
@@ -1405,19 +1442,31 @@ __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>
     // the next round's particle is requested before the current one is processed
     // (and the permutation entry of the one after it, so that load's address is ready)
     Particle<D, R> nxt;
+    R* const slot0 = STG ? stage + (size_t)threadIdx.x * kG2PSlot : nullptr;
+    R* const slot1 = STG ? stage + (size_t)(NTH + threadIdx.x) * kG2PSlot : nullptr;
     if (start + threadIdx.x < end) {
         const uint32_t q0 = perm[start + threadIdx.x];
-        load_xF<D, R>(in, q0, nxt);
+        if (STG) stage_xF<D, R>(slot0, in, q0);
+        else load_xF<D, R>(in, q0, nxt);
         if (EXT && c.mat) load_mat<D, R>(in, q0, nxt);
         if (EXT && c.transfer == 2) load_v<D, R>(in, q0, nxt);
     }
+    if (STG) cp_async_commit();
     uint32_t qn = (start + threadIdx.x + NTH < end) ? perm[start + threadIdx.x + NTH] : 0u;
     for (uint32_t k0 = start; k0 < end; k0 += NTH) {
         const uint32_t k = k0 + threadIdx.x;
         if (k >= end) continue;
         Particle<D, R> p = nxt;
+        if (STG) {   // this particle from its slot, the next one's copies into the other
+            const bool odd = (((k0 - start) / NTH) & 1u) != 0u;
+            R* cur = odd ? slot1 : slot0;
+            cp_async_wait<0>();
+            read_xF<D, R>(cur, p);
+            if (k + NTH < end) stage_xF<D, R>(odd ? slot0 : slot1, in, qn);
+            cp_async_commit();
+        }
         if (k + NTH < end) {
-            load_xF<D, R>(in, qn, nxt);
+            if (!STG) load_xF<D, R>(in, qn, nxt);
             if (EXT && c.mat) load_mat<D, R>(in, qn, nxt);
             if (EXT && c.transfer == 2) load_v<D, R>(in, qn, nxt);
         }
@@ -1598,6 +1647,7 @@ __global__ void __launch_bounds__(G2P_THREADS, 4) k_g2p(PState<R> in, PState<R> 
     constexpr int BN = (D == 3) ? 64 : 16;
     constexpr int NB = 1 << D;
     __shared__ __align__(128) R sv[2][NB][BN][4];
+    __shared__ __align__(16) R stage[g2p_staged<R>() ? 2 * G2P_THREADS * kG2PSlot : 1];
     __shared__ __align__(8) uint64_t mbar[2];
     // s_t[b]: the tile whose grid blocks are staged in buffer b.  Thread 0 writes s_t[b ^ 1]
     // before the first barrier of an iteration; every thread reads s_t[b] at the top of the
@@ -1629,7 +1679,7 @@ __global__ void __launch_bounds__(G2P_THREADS, 4) k_g2p(PState<R> in, PState<R> 
         __syncthreads();
         if (!s_ok) return;
         g2p_compute<D, ORDER, R, EXT, G2P_THREADS>(in, out, perm, skeys, tiles[t], tiles[t + 1], knext, c, err, fallbacks, sv[buf],
-                                      smax_l, vdel);
+                                      smax_l, vdel, stage);
         __syncthreads();
         phase[buf] ^= 1u;
     }
