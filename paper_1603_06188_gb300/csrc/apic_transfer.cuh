@@ -1530,14 +1530,14 @@ __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>
                         fma_pair<R>(P[2], Q[2], w[2][ic], dw[2][ic], vt[2], vt[2]);
                         Z[2] += rw[2][ic] * vt[2];
                     }
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        Ra[a] += w[1][ib] * P[a];
-                        Sa[a] += dw[1][ib] * P[a];
-                        Ta[a] += w[1][ib] * Q[a];
-                        Ya[a] += rw[1][ib] * P[a];
-                        Za[a] += w[1][ib] * Z[a];
-                    }
+                    fma_pair<R>(Ra[0], Ra[1], w[1][ib], w[1][ib], P[0], P[1]);
+                    fma_pair<R>(Sa[0], Sa[1], dw[1][ib], dw[1][ib], P[0], P[1]);
+                    fma_pair<R>(Ta[0], Ta[1], w[1][ib], w[1][ib], Q[0], Q[1]);
+                    fma_pair<R>(Ya[0], Ya[1], rw[1][ib], rw[1][ib], P[0], P[1]);
+                    fma_pair<R>(Za[0], Za[1], w[1][ib], w[1][ib], Z[0], Z[1]);
+                    fma_pair<R>(Ra[2], Sa[2], w[1][ib], dw[1][ib], P[2], P[2]);
+                    fma_pair<R>(Ta[2], Za[2], w[1][ib], w[1][ib], Q[2], Z[2]);
+                    Ya[2] += rw[1][ib] * P[2];
                 } else {
                     const V4<R> nv = *reinterpret_cast<const V4<R>*>(svf + o01);
                     const R vt[2] = {nv.x, nv.y};
