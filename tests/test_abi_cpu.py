@@ -1,8 +1,12 @@
 """Host-only checks of the C ABI: the library builds for sm_103a, loads without a GPU,
 exports every entry point include/apic.h declares, and validates configurations before
 touching the device."""
+import ctypes
 import os
 import re
+import shutil
+import subprocess
+import tempfile
 
 import pytest
 
@@ -54,6 +58,8 @@ def test_workspace_size_and_validation(lib):
         (dict(res=(2048, 64, 64)), apic.APIC_ERR_ARG),
         (dict(dx=0.0), apic.APIC_ERR_ARG),
         (dict(tile_particles=100), apic.APIC_ERR_ARG),
+        (dict(p2g_group=3), apic.APIC_ERR_ARG),
+        (dict(p2g_kernel=9), apic.APIC_ERR_ARG),
         (dict(model="fcr", E=-1.0, nu=0.3), apic.APIC_ERR_ARG),
         (dict(model="fcr", E=1.0, nu=0.5), apic.APIC_ERR_ARG),
     ]
@@ -74,3 +80,26 @@ def test_create_rejects_bad_workspace_without_touching_the_gpu(lib):
     with pytest.raises(apic.ApicError) as e:
         apic.apic_create(cfg, 10, 1 << 20, need - 1, 0)   # never dereferenced: size check comes first
     assert e.value.status == apic.APIC_ERR_OOM
+
+
+@pytest.mark.parametrize("cname,pytype", [("apic_config", "Config"), ("apic_batch_config", "BatchConfig")])
+def test_binding_structs_match_the_header(cname, pytype):
+    """The ctypes mirrors of the configuration structs have the header's size and field
+    offsets: a C program compiled against include/apic.h prints them."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    st = getattr(apic, pytype)
+    lines = [f'printf("size %zu\\n", sizeof({cname}));']
+    for name, _ in st._fields_:
+        lines.append(f'printf("{name} %zu\\n", offsetof({cname}, {name}));')
+    src = "#include <stddef.h>\n#include <stdio.h>\n#include \"apic.h\"\nint main(void) {\n" + "\n".join(lines) + "\nreturn 0;\n}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c_path, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(c_path, "w").write(src)
+        subprocess.run([cc, "-I", os.path.join(ROOT, "include"), c_path, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    got = dict(zip(out[0::2], (int(v) for v in out[1::2])))
+    assert got["size"] == ctypes.sizeof(st)
+    for name, _ in st._fields_:
+        assert got[name] == getattr(st, name).offset, name
