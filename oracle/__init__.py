@@ -106,6 +106,8 @@ def _load():
                 "or_g2p": (i64, [cfgp, i64, cp, cp, cp, cp, cp, cp]),
                 "or_g2p_lambda0": (i64, [cfgp, i64, cp, cp, cp, cp, cp]),
                 "or_potential": (d, [cfgp, i64, cp, cp, cp, cp]),
+                "or_force_at": (i64, [cfgp, i64, cp, cp, cp, cp, cp]),
+                "or_step_lambda1": (i64, [cfgp, i64, cp, cp, cp, cp, cp, cp]),
                 "or_momentum_particles": (None, [cfgp, i64, cp, cp, cp, cp, cp, cp]),
                 "or_momentum_grid": (None, [cfgp, cp, cp, cp]),
                 "or_keys": (None, [cfgp, C.c_int, i64, cp, cp, cp]),
@@ -290,6 +292,32 @@ def potential(cfg: Cfg, x, F, vol, dxg) -> float:
     nn = _nodes(cfg)
     return _load().or_potential(C.byref(cfg), n, _p(_f64(x, (n, d))), _p(_f64(F, (n, d, d))),
                                 _p(_f64(np.broadcast_to(vol, (n,)))), _p(_f64(dxg, (nn, d))))
+
+
+def force_at(cfg: Cfg, x, F, vol, dxg):
+    """f_i = -sum_p V_p P(F^_p) (F_p^n)^T grad w_ip with F^_p = (I + sum_i dxg_i grad w^T) F_p^n
+    (Sec. 3.3 with F^{n+lambda} = F^_p).  Returns (f, n_skipped)."""
+    d = cfg.dim
+    n = len(x)
+    nn = _nodes(cfg)
+    gf = np.zeros((nn, d))
+    bad = _load().or_force_at(C.byref(cfg), n, _p(_f64(x, (n, d))), _p(_f64(F, (n, d, d))),
+                              _p(_f64(np.broadcast_to(vol, (n,)))), _p(_f64(dxg, (nn, d))), _p(gf))
+    return gf, bad
+
+
+def step_lambda1(cfg: Cfg, x, v, B, F, mass, vol, nsteps: int = 1):
+    """nsteps explicit steps of the member lambda = 1 (Sec. 3.3): forces at F^{n+1} from the
+    grid velocities before the update, positions moved with them.  Returns (x, v, B, F, skipped)."""
+    d = cfg.dim
+    n = len(x)
+    x = _f64(x, (n, d)).copy(); v = _f64(v, (n, d)).copy()
+    B = _f64(B, (n, d, d)).copy(); F = _f64(F, (n, d, d)).copy()
+    mass = _f64(np.broadcast_to(mass, (n,))); vol = _f64(np.broadcast_to(vol, (n,)))
+    bad = 0
+    for _ in range(nsteps):
+        bad += _load().or_step_lambda1(C.byref(cfg), n, _p(x), _p(v), _p(B), _p(F), _p(mass), _p(vol))
+    return x, v, B, F, bad
 
 
 def momentum_particles(cfg: Cfg, x, v, B, mass):

@@ -18,8 +18,9 @@
  *   - w_ip = N((x_p - x_i)/dx) as a tensor product of 1-D cardinal B-splines
  *     (Sec. 3.5); grad w_ip is the gradient with respect to x_p, which is what
  *     makes sum_i x_i (grad w_ip)^T = I (Sec. 3.5).
- *   - Integrator family parameter lambda (Sec. 3.3); forces are evaluated for the
- *     explicit member lambda = 0 only (F^{n+lambda} = F^n).
+ *   - Integrator family parameter lambda (Sec. 3.3).  or_p2g evaluates forces for the
+ *     explicit member lambda = 0 (F^{n+lambda} = F^n); or_force_at and or_step_lambda1
+ *     evaluate them for the other explicit member, lambda = 1 (F^{n+lambda} = F^{n+1}).
  *
  * Readings of the paper taken here (each is listed with its reason in the design notes):
  *   - force sign: f_i = -sum_p V_p P(F_p^n) (F_p^n)^T grad w_ip, i.e. f = -dPhi/dx~
@@ -649,6 +650,98 @@ double or_potential(const or_cfg* c, int64_t n, const double* x, const double* F
         phi += vol[p] * psi_of(c, Fh);
     }
     return phi;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 3.3: force at a displaced grid, and the explicit member        */
+/* lambda = 1.                                                          */
+/* ------------------------------------------------------------------ */
+/*
+ * f_i = -sum_p V_p P(F^_p) (F_p^n)^T grad w_ip,  F^_p = (I + sum_i dxg_i (grad w_ip)^T) F_p^n,
+ * with dxg_i = x~_i - x_i per node: the force of Sec. 3.3 with F^{n+lambda} = F^_p (sign
+ * reading above).  It is -dPhi/dx~ for Phi(x~) = sum_p V_p Psi(F^_p(x~)) (or_potential).
+ * dxg = 0 gives or_p2g's force (lambda = 0); dxg_i = dt v_i gives the member lambda = 1.
+ * gf is accumulated into (callers zero it).  Returns the number of skipped particles.
+ */
+int64_t or_force_at(const or_cfg* c, int64_t n, const double* x, const double* F, const double* vol,
+                    const double* dxg, double* gf)
+{
+    const int d = c->dim, ns = stencil_count(c);
+    int64_t bad = 0;
+    double w[64], dw[192];
+    if (c->model == 0) return 0;
+    for (int64_t p = 0; p < n; ++p) {
+        int base[3];
+        if (or_stencil(c, x + p * d, base, w, dw) != 0) { ++bad; continue; }
+        const double* Fp = F + p * d * d;
+        double M[9], Fh[9], P[9], A[9];
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) M[a * d + b] = (a == b) ? 1.0 : 0.0;
+        for (int j = 0; j < ns; ++j) {
+            int i[3]; double xi[3];
+            stencil_node(c, base, j, i, xi);
+            int64_t ni = node_index(c, i);
+            for (int a = 0; a < d; ++a)
+                for (int b = 0; b < d; ++b) M[a * d + b] += dxg[ni * d + a] * dw[j * d + b];
+        }
+        matmul_d(d, M, Fp, Fh);
+        stress_with(c, c->mu, c->lam, Fh, P);
+        /* A = V_p P(F^) (F^n)^T */
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) {
+                double s = 0.0;
+                for (int k = 0; k < d; ++k) s += P[a * d + k] * Fp[b * d + k];
+                A[a * d + b] = vol[p] * s;
+            }
+        for (int j = 0; j < ns; ++j) {
+            int i[3]; double xi[3];
+            stencil_node(c, base, j, i, xi);
+            int64_t ni = node_index(c, i);
+            for (int a = 0; a < d; ++a) {
+                double s = 0.0;
+                for (int b = 0; b < d; ++b) s += A[a * d + b] * dw[j * d + b];
+                gf[ni * d + a] -= s;
+            }
+        }
+    }
+    return bad;
+}
+
+/*
+ * One explicit step of the member lambda = 1 of Sec. 3.3, in the paper's order:
+ *   P2G of mass and momentum (Sec. 3.2), v_i = (m v)_i / m_i;
+ *   x~_i = x_i + dt v_i (lambda = 1), so F_p^{n+1} = (I + dt sum_i v_i (grad w_ip)^T) F_p^n
+ *   and the force f_i = -sum_p V_p P(F_p^{n+1}) (F_p^n)^T grad w_ip;
+ *   v~_i = v_i + dt f_i / m_i (with gravity and walls as in or_grid_update);
+ *   the general transfer to particles (Sec. 3.4) with lambda = 1.
+ * Returns the number of skipped particles (-1 when memory runs out).
+ */
+int64_t or_step_lambda1(const or_cfg* c, int64_t n, double* x, double* v, double* B, double* F,
+                        const double* mass, const double* vol)
+{
+    const int d = c->dim;
+    const int64_t nn = node_count(c);
+    double* gm = (double*)calloc((size_t)nn, sizeof(double));
+    double* gmv = (double*)calloc((size_t)nn * d, sizeof(double));
+    double* gf = (double*)calloc((size_t)nn * d, sizeof(double));
+    double* gv = (double*)calloc((size_t)nn * d, sizeof(double));
+    double* gvt = (double*)calloc((size_t)nn * d, sizeof(double));
+    double* dxg = (double*)calloc((size_t)nn * d, sizeof(double));
+    int64_t bad = -1;
+    if (gm && gmv && gf && gv && gvt && dxg) {
+        or_cfg c1 = *c;
+        c1.lambda_t = 1.0;
+        or_cfg c0 = c1;
+        c0.model = 0;                                   /* mass and momentum only */
+        bad = or_p2g(&c0, n, x, v, B, F, mass, vol, gm, gmv, gf);
+        or_grid_update(&c1, gm, gmv, gf, gv, gvt);      /* gv = v_i (gf is zero here) */
+        for (int64_t k = 0; k < nn * d; ++k) dxg[k] = c->dt * gv[k];
+        bad += or_force_at(&c1, n, x, F, vol, dxg, gf);
+        or_grid_update(&c1, gm, gmv, gf, gv, gvt);
+        bad += or_g2p(&c1, n, x, v, B, F, gv, gvt);
+    }
+    free(gm); free(gmv); free(gf); free(gv); free(gvt); free(dxg);
+    return bad;
 }
 
 /* ------------------------------------------------------------------ */
