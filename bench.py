@@ -7,6 +7,10 @@ Workloads (seeded synthetic inputs shaped like the paper's elastic-body scenes):
             fixed-corotated E = 1e4, nu = 0.3, rho = 1, gravity -9.8, dt = 2e-5, sticky walls
   spheres256  3-D, cubic B-splines, 256^3, two spheres r = 0.15 approaching at +-1, 32 ppc
             (15.2M particles), E = 5e4, nu = 0.4, dt = 5e-6
+  batched   512 simulations of the batched mix (grid edge 32..96, 2k..400k particles,
+            8 ppc) stepped together in one batch, against the same simulations one by one
+  serving   a seeded Poisson stream of such simulations (--rate per second, --requests,
+            --budget-gb) through the continuous-batching loop: throughput, p50 / p99 latency
 
 One "step" = the whole hot path: cell keys, radix sort, tile list, P2G (+force), grid
 update, G2P.  `value` is device-timed (CUDA events on the simulation's stream, inputs
