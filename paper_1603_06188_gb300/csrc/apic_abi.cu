@@ -535,18 +535,18 @@ apic_status apic_p2g(apic_sim* s)
     }
     if (s->keys_valid && s->order_sorted && s->skeys) {
         // particles are stored in the previous sorted order: sort only the moved keys
-        PhaseScope ps(s, APIC_PHASE_SORT, 2 + ((s->c.key_bits + 7) / 8));
+        PhaseScope ps(s, APIC_PHASE_SORT, resort_kernels(n, s->c.key_bits));
         uint32_t* kout = s->skeys == s->b.kA ? s->b.kB : s->b.kA;
         uint32_t* vout = s->skeys == s->b.kA ? s->b.vB : s->b.vA;
         CK(resort(s->b, n, s->c.key_bits, s->skeys, kout, vout, &s->epoch, s->L.sms, s->stream), "incremental sort");
         s->skeys = kout;
         s->perm = vout;
     } else {
-        PhaseScope ps(s, APIC_PHASE_SORT, 2 + ((s->c.key_bits + 7) / 8));
+        PhaseScope ps(s, APIC_PHASE_SORT, radix_sort_kernels(s->c.key_bits));
         CK(radix_sort(s->b, n, s->c.key_bits, s->stream, &s->skeys, &s->perm), "radix sort");
     }
     {
-        PhaseScope ps(s, APIC_PHASE_TILES, 5);
+        PhaseScope ps(s, APIC_PHASE_TILES, build_tiles_kernels(n, s->c.tile));
         CK(build_tiles(s->b, s->skeys, n, s->c.dim, s->c.tile, s->max_tiles, s->stream), "tile list");
     }
     if (s->group_pending) {
@@ -560,7 +560,7 @@ apic_status apic_p2g(apic_sim* s)
         s->group_pending = false;
     }
     {
-        PhaseScope ps(s, APIC_PHASE_P2G, 1);
+        PhaseScope ps(s, APIC_PHASE_P2G, s->c.transfer == 2 ? 2 : 1);   // FLIP: a second pass
         CK(DISPATCH(s, p2g, s->c, s->b, s->cur, s->skeys, s->perm, n, s->L, s->stream), "p2g kernel");
     }
     s->phase = 1;
@@ -1009,7 +1009,8 @@ cudaError_t batch_enqueue(apic_batch* b)
     return e;
 }
 
-int64_t batch_kernels_per_step(const apic_batch* b) { return 2 + (int64_t)b->passes + 5 + 4; }
+// sort and tile list, then P2G, grid update, G2P and the parity flip
+int64_t batch_kernels_per_step(const apic_batch* b) { return batch_sort_and_tiles_kernels(b->passes) + 4; }
 
 apic_status batch_run(apic_batch* b, int n)
 {

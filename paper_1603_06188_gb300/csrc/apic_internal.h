@@ -95,6 +95,12 @@ struct SortDesc {
 
 // sort / tiles (apic_sort.cu)
 int radix_tiles(int64_t n);
+// kernels launched by radix_sort, resort, build_tiles, and by batch_resort plus
+// batch_build_tiles together (for the launch counters)
+int radix_sort_kernels(int key_bits);
+int resort_kernels(int64_t n, int key_bits);
+int build_tiles_kernels(int64_t n, int tile);
+int batch_sort_and_tiles_kernels(int passes);
 size_t scan_partials_needed(int64_t n);
 // sorts knext (values = identity) into (*keys_out, *vals_out); returns the CUDA error
 // copies of the incremental sort's digit histogram (chunk t adds to copy t % kMhistCopies;

@@ -1152,6 +1152,16 @@ __global__ void __launch_bounds__(256) kb_tile_write(const SortDesc* __restrict_
 
 int radix_tiles(int64_t n) { return (int)((n + RTILE - 1) / RTILE); }
 
+// kernels the routines below launch (memsets not counted), for the launch counters
+int radix_sort_kernels(int key_bits) { return 2 + (key_bits + 7) / 8; }
+int resort_kernels(int64_t n, int key_bits)
+{
+    if (n <= 0) return 0;
+    return 3 + (key_bits + 7) / 8 + (radix_tiles(n) > kReduceChunks ? 3 : 0);
+}
+int build_tiles_kernels(int64_t n, int tile) { return (n + tile - 1) / tile <= kReduceChunks ? 2 : 5; }
+int batch_sort_and_tiles_kernels(int passes) { return (5 + passes) + 5; }
+
 size_t scan_partials_needed(int64_t n)
 {
     const int64_t m = 256 * (int64_t)radix_tiles(n) + 1;
