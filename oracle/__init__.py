@@ -108,6 +108,11 @@ def _load():
                 "or_potential": (d, [cfgp, i64, cp, cp, cp, cp]),
                 "or_force_at": (i64, [cfgp, i64, cp, cp, cp, cp, cp]),
                 "or_step_lambda1": (i64, [cfgp, i64, cp, cp, cp, cp, cp, cp]),
+                "or_dstress_fcr": (None, [C.c_int, d, d, cp, cp, cp]),
+                "or_dstress_nh": (None, [C.c_int, d, d, cp, cp, cp]),
+                "or_force_diff_at": (i64, [cfgp, i64, cp, cp, cp, cp, cp, cp]),
+                "or_step_midpoint": (i64, [cfgp, i64, cp, cp, cp, cp, cp, cp, C.c_int, C.c_int, d]),
+                "or_midpoint_solve": (C.c_int, [cfgp, i64, cp, cp, cp, cp, cp, C.c_int, C.c_int, d, cp]),
                 "or_momentum_particles": (None, [cfgp, i64, cp, cp, cp, cp, cp, cp]),
                 "or_momentum_grid": (None, [cfgp, cp, cp, cp]),
                 "or_keys": (None, [cfgp, C.c_int, i64, cp, cp, cp]),
@@ -317,6 +322,55 @@ def step_lambda1(cfg: Cfg, x, v, B, F, mass, vol, nsteps: int = 1):
     bad = 0
     for _ in range(nsteps):
         bad += _load().or_step_lambda1(C.byref(cfg), n, _p(x), _p(v), _p(B), _p(F), _p(mass), _p(vol))
+    return x, v, B, F, bad
+
+
+def dstress(model: str, F, dF, mu, lam):
+    """dP = dP/dF : dF of the fixed-corotated ("fcr") or Neo-Hookean ("nh") stress."""
+    F = _f64(F); dF = _f64(dF)
+    d = F.shape[0]
+    out = np.zeros((d, d))
+    fn = _load().or_dstress_nh if model == "nh" else _load().or_dstress_fcr
+    fn(d, mu, lam, _p(F), _p(dF), _p(out))
+    return out
+
+
+def force_diff_at(cfg: Cfg, x, F, vol, dxg, du):
+    """sum_j (d f_i / d x~_j) du_j at the displacement dxg (Sec. 3.3).  Returns (df, n_skipped)."""
+    d = cfg.dim
+    n = len(x)
+    nn = _nodes(cfg)
+    gdf = np.zeros((nn, d))
+    bad = _load().or_force_diff_at(C.byref(cfg), n, _p(_f64(x, (n, d))), _p(_f64(F, (n, d, d))),
+                                   _p(_f64(np.broadcast_to(vol, (n,)))), _p(_f64(dxg, (nn, d))),
+                                   _p(_f64(du, (nn, d))), _p(gdf))
+    return gdf, bad
+
+
+def midpoint_solve(cfg: Cfg, x, F, vol, gm, gv, newton: int = 20, cg: int = 200, tol: float = 1e-13, dv=None):
+    """The grid solve of the implicit midpoint rule: dv = v~ - v with
+    m_i dv_i = dt f_i(x_i + dt/2 v_i + dt/4 dv_i).  Returns (dv, Newton iterations)."""
+    d = cfg.dim
+    n = len(x)
+    nn = _nodes(cfg)
+    dv = np.zeros((nn, d)) if dv is None else _f64(dv, (nn, d)).copy()
+    it = _load().or_midpoint_solve(C.byref(cfg), n, _p(_f64(x, (n, d))), _p(_f64(F, (n, d, d))),
+                                   _p(_f64(np.broadcast_to(vol, (n,)))), _p(_f64(gm)), _p(_f64(gv, (nn, d))),
+                                   newton, cg, tol, _p(dv))
+    return dv, it
+
+
+def step_midpoint(cfg: Cfg, x, v, B, F, mass, vol, newton: int = 20, cg: int = 200, tol: float = 1e-13):
+    """One implicit midpoint step (lambda = 1/2, Sec. 4.1-4.2): Newton on the grid velocity
+    change, each system by mass-inner-product conjugate gradients (Algorithm 1).
+    Returns (x, v, B, F, skipped)."""
+    d = cfg.dim
+    n = len(x)
+    x = _f64(x, (n, d)).copy(); v = _f64(v, (n, d)).copy()
+    B = _f64(B, (n, d, d)).copy(); F = _f64(F, (n, d, d)).copy()
+    mass = _f64(np.broadcast_to(mass, (n,))); vol = _f64(np.broadcast_to(vol, (n,)))
+    bad = _load().or_step_midpoint(C.byref(cfg), n, _p(x), _p(v), _p(B), _p(F), _p(mass), _p(vol),
+                                   newton, cg, tol)
     return x, v, B, F, bad
 
 

@@ -20,7 +20,10 @@
  *     makes sum_i x_i (grad w_ip)^T = I (Sec. 3.5).
  *   - Integrator family parameter lambda (Sec. 3.3).  or_p2g evaluates forces for the
  *     explicit member lambda = 0 (F^{n+lambda} = F^n); or_force_at and or_step_lambda1
- *     evaluate them for the other explicit member, lambda = 1 (F^{n+lambda} = F^{n+1}).
+ *     evaluate them for the other explicit member, lambda = 1 (F^{n+lambda} = F^{n+1});
+ *     or_step_midpoint takes the implicit midpoint rule, lambda = 1/2 (Sec. 4.1-4.2), with
+ *     Newton on the grid velocity change and mass-inner-product conjugate gradients
+ *     (Algorithm 1) on the force-derivative product.
  *
  * Readings of the paper taken here (each is listed with its reason in the design notes):
  *   - force sign: f_i = -sum_p V_p P(F_p^n) (F_p^n)^T grad w_ip, i.e. f = -dPhi/dx~
@@ -387,6 +390,94 @@ void or_stress_nh(int d, double mu, double lam, const double* F, double* P)
     for (int k = 0; k < d * d; ++k) P[k] = mu * (F[k] - C[k] / J) + lam * lj * C[k] / J;
 }
 
+/*
+ * Directional derivatives of the stresses, dP = dP/dF : dF, which the force-derivative
+ * product of Sec. 3.3 needs.
+ * Fixed-corotated: dP = 2 mu (dF - dR) + lam (cof F : dF) cof F + lam (J - 1) d(cof F), where
+ *   d(cof F) = (cof F : dF) F^{-T} - J F^{-T} dF^T F^{-T}   (cof F = J F^{-T}, d log J = F^{-T} : dF),
+ *   dR = R W, and W (skew) solves S W + W S = R^T dF - dF^T R for F = R S (S = R^T F symmetric).
+ *   In 3-D, with W = [w]x and R^T dF - dF^T R = [k]x, that is (tr(S) I - S) w = k; in 2-D,
+ *   W = [[0, -t], [t, 0]] with t = k / tr(S).
+ * Neo-Hookean: dP = mu dF + (mu - lam log J) F^{-T} dF^T F^{-T} + lam (F^{-T} : dF) F^{-T}.
+ */
+static void fit_dft_fit(int d, const double* FiT, const double* dF, double* T)
+{
+    /* T = F^{-T} dF^T F^{-T} */
+    double A[9];
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) {
+            double s = 0.0;
+            for (int k = 0; k < d; ++k) s += FiT[a * d + k] * dF[b * d + k];
+            A[a * d + b] = s;
+        }
+    matmul_d(d, A, FiT, T);
+}
+
+void or_dstress_fcr(int d, double mu, double lam, const double* F, const double* dF, double* dP)
+{
+    double R[9], S[9], K[9], W[9], dR[9], C[9], FiT[9], T[9];
+    or_polar(d, F, R);
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) {
+            double s = 0.0, k = 0.0;
+            for (int m = 0; m < d; ++m) {
+                s += R[m * d + a] * F[m * d + b];
+                k += R[m * d + a] * dF[m * d + b] - dF[m * d + a] * R[m * d + b];
+            }
+            S[a * d + b] = s;
+            K[a * d + b] = k;
+        }
+    if (d == 3) {
+        const double kv[3] = {K[7], K[2], K[3]};   /* (K21, K02, K10) */
+        const double tr = S[0] + S[4] + S[8];
+        double M[9], Mi[9], w[3];
+        for (int k = 0; k < 9; ++k) M[k] = -S[k];
+        M[0] += tr; M[4] += tr; M[8] += tr;
+        inverse_d(3, M, Mi);
+        for (int a = 0; a < 3; ++a) w[a] = Mi[a * 3 + 0] * kv[0] + Mi[a * 3 + 1] * kv[1] + Mi[a * 3 + 2] * kv[2];
+        W[0] = 0.0;   W[1] = -w[2]; W[2] = w[1];
+        W[3] = w[2];  W[4] = 0.0;   W[5] = -w[0];
+        W[6] = -w[1]; W[7] = w[0];  W[8] = 0.0;
+    } else {
+        const double t = K[2] / (S[0] + S[3]);   /* K10 / tr(S) */
+        W[0] = 0.0; W[1] = -t; W[2] = t; W[3] = 0.0;
+    }
+    matmul_d(d, R, W, dR);
+    cofactor_d(d, F, C);
+    const double J = det_d(d, F);
+    double cdf = 0.0;
+    for (int k = 0; k < d * d; ++k) {
+        FiT[k] = C[k] / J;
+        cdf += C[k] * dF[k];
+    }
+    fit_dft_fit(d, FiT, dF, T);
+    for (int k = 0; k < d * d; ++k) {
+        const double dcof = cdf * FiT[k] - J * T[k];
+        dP[k] = 2.0 * mu * (dF[k] - dR[k]) + lam * cdf * C[k] + lam * (J - 1.0) * dcof;
+    }
+}
+
+void or_dstress_nh(int d, double mu, double lam, const double* F, const double* dF, double* dP)
+{
+    double C[9], FiT[9], T[9];
+    cofactor_d(d, F, C);
+    const double J = det_d(d, F);
+    const double lj = log(J);
+    double tr = 0.0;
+    for (int k = 0; k < d * d; ++k) {
+        FiT[k] = C[k] / J;
+        tr += FiT[k] * dF[k];
+    }
+    fit_dft_fit(d, FiT, dF, T);
+    for (int k = 0; k < d * d; ++k) dP[k] = mu * dF[k] + (mu - lam * lj) * T[k] + lam * tr * FiT[k];
+}
+
+static void dstress_with(const or_cfg* c, const double* F, const double* dF, double* dP)
+{
+    if (c->model == 2) or_dstress_nh(c->dim, c->mu, c->lam, F, dF, dP);
+    else or_dstress_fcr(c->dim, c->mu, c->lam, F, dF, dP);
+}
+
 static void stress_with(const or_cfg* c, double mu, double lam, const double* F, double* P)
 {
     if (c->model == 2) or_stress_nh(c->dim, mu, lam, F, P);
@@ -741,6 +832,169 @@ int64_t or_step_lambda1(const or_cfg* c, int64_t n, double* x, double* v, double
         bad += or_g2p(&c1, n, x, v, B, F, gv, gvt);
     }
     free(gm); free(gmv); free(gf); free(gv); free(gvt); free(dxg);
+    return bad;
+}
+
+/*
+ * Force-derivative product of Sec. 3.3 at a displaced grid (F^_p as in or_force_at):
+ *   A_p = dP/dF(F^_p) : ((sum_j du_j (grad w_jp)^T) F_p^n),
+ *   df_i = -sum_p V_p A_p (F_p^n)^T grad w_ip  = sum_j (d f_i / d x~_j) du_j.
+ * gdf is accumulated into (callers zero it).  Returns the number of skipped particles.
+ */
+int64_t or_force_diff_at(const or_cfg* c, int64_t n, const double* x, const double* F, const double* vol,
+                         const double* dxg, const double* du, double* gdf)
+{
+    const int d = c->dim, ns = stencil_count(c);
+    int64_t bad = 0;
+    double w[64], dw[192];
+    if (c->model == 0) return 0;
+    for (int64_t p = 0; p < n; ++p) {
+        int base[3];
+        if (or_stencil(c, x + p * d, base, w, dw) != 0) { ++bad; continue; }
+        const double* Fp = F + p * d * d;
+        double M[9], D[9], Fh[9], dFh[9], dP[9], A[9];
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) { M[a * d + b] = (a == b) ? 1.0 : 0.0; D[a * d + b] = 0.0; }
+        for (int j = 0; j < ns; ++j) {
+            int i[3]; double xi[3];
+            stencil_node(c, base, j, i, xi);
+            int64_t ni = node_index(c, i);
+            for (int a = 0; a < d; ++a)
+                for (int b = 0; b < d; ++b) {
+                    M[a * d + b] += dxg[ni * d + a] * dw[j * d + b];
+                    D[a * d + b] += du[ni * d + a] * dw[j * d + b];
+                }
+        }
+        matmul_d(d, M, Fp, Fh);
+        matmul_d(d, D, Fp, dFh);
+        dstress_with(c, Fh, dFh, dP);
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) {
+                double s = 0.0;
+                for (int k = 0; k < d; ++k) s += dP[a * d + k] * Fp[b * d + k];
+                A[a * d + b] = vol[p] * s;
+            }
+        for (int j = 0; j < ns; ++j) {
+            int i[3]; double xi[3];
+            stencil_node(c, base, j, i, xi);
+            int64_t ni = node_index(c, i);
+            for (int a = 0; a < d; ++a) {
+                double s = 0.0;
+                for (int b = 0; b < d; ++b) s += A[a * d + b] * dw[j * d + b];
+                gdf[ni * d + a] -= s;
+            }
+        }
+    }
+    return bad;
+}
+
+/* <u, v>_M = sum_i m_i u_i . v_i over the nodes with mass */
+static double dot_m(int64_t nn, int d, const double* gm, const double* u, const double* v)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < nn; ++i)
+        if (gm[i] > 0.0)
+            for (int a = 0; a < d; ++a) s += gm[i] * u[i * d + a] * v[i * d + a];
+    return s;
+}
+
+/*
+ * The grid solve of the implicit midpoint rule (lambda = 1/2), as Sec. 4.1-4.2 do it:
+ * Newton iterations on dv = v~ - v for  m_i dv_i = dt f_i(x_i + dt/2 v_i + dt/4 dv_i)
+ * (F^{n+1/2} is F^ of or_force_at at the displacement dt/2 v + dt/4 dv), the gradient of the
+ * objective being g_i = m_i/4 dv_i - dt/4 f_i; each Newton system (M/4 - dt^2/16 df/dx) du = -g
+ * solved by conjugate gradients (Algorithm 1) on its velocity-like form
+ * (I - dt^2/4 M^{-1} df/dx) du = -4 M^{-1} g with the mass inner product <u, v> = u^T M v,
+ * from du = 0.  Only nodes with mass carry unknowns (dv = 0 elsewhere).  newton, cg:
+ * iteration caps; the Newton loop ends when |4 M^{-1} g|_M <= tol max(|v|_M, tiny), a CG
+ * solve when |r|_M <= tol |r_0|_M.  gv: v_i; dv: in (start) and out.  Returns the Newton
+ * iterations taken, or -1 when memory runs out.
+ */
+int or_midpoint_solve(const or_cfg* c, int64_t n, const double* x, const double* F, const double* vol,
+                      const double* gm, const double* gv, int newton, int cg, double tol, double* dv)
+{
+    const int d = c->dim;
+    const int64_t nn = node_count(c), nv = nn * d;
+    double* dxg = (double*)calloc((size_t)nv, sizeof(double));
+    double* f = (double*)calloc((size_t)nv, sizeof(double));
+    double* r = (double*)calloc((size_t)nv, sizeof(double));
+    double* pd = (double*)calloc((size_t)nv, sizeof(double));
+    double* sv = (double*)calloc((size_t)nv, sizeof(double));
+    double* du = (double*)calloc((size_t)nv, sizeof(double));
+    int it = -1;
+    if (dxg && f && r && pd && sv && du) {
+        const double vnorm = sqrt(dot_m(nn, d, gm, gv, gv));
+        const double dt = c->dt;
+        for (it = 0; it < newton; ++it) {
+            for (int64_t k = 0; k < nv; ++k) { dxg[k] = 0.5 * dt * gv[k] + 0.25 * dt * dv[k]; f[k] = 0.0; }
+            or_force_at(c, n, x, F, vol, dxg, f);
+            /* r = -4 M^{-1} g = dt M^{-1} f - dv */
+            for (int64_t i = 0; i < nn; ++i)
+                for (int a = 0; a < d; ++a)
+                    r[i * d + a] = gm[i] > 0.0 ? dt * f[i * d + a] / gm[i] - dv[i * d + a] : 0.0;
+            const double rn0 = sqrt(dot_m(nn, d, gm, r, r));
+            if (rn0 <= tol * (vnorm > 1e-300 ? vnorm : 1e-300)) break;
+            /* Algorithm 1 on A2 du = r, du = 0 */
+            for (int64_t k = 0; k < nv; ++k) { du[k] = 0.0; pd[k] = r[k]; }
+            double gamma = rn0 * rn0;
+            for (int k = 0; k < cg && gamma > 0.0; ++k) {
+                for (int64_t q = 0; q < nv; ++q) sv[q] = 0.0;
+                or_force_diff_at(c, n, x, F, vol, dxg, pd, sv);            /* df/dx p */
+                for (int64_t i = 0; i < nn; ++i)
+                    for (int a = 0; a < d; ++a) {
+                        const int64_t q = i * d + a;
+                        sv[q] = gm[i] > 0.0 ? pd[q] - 0.25 * dt * dt * sv[q] / gm[i] : 0.0;   /* s = A2 p */
+                    }
+                const double ps = dot_m(nn, d, gm, pd, sv);
+                if (!(ps > 0.0)) break;
+                const double alpha = gamma / ps;
+                for (int64_t q = 0; q < nv; ++q) { du[q] += alpha * pd[q]; r[q] -= alpha * sv[q]; }
+                const double kappa = dot_m(nn, d, gm, r, r);
+                if (sqrt(kappa) <= tol * rn0) break;
+                const double beta = kappa / gamma;
+                for (int64_t q = 0; q < nv; ++q) pd[q] = r[q] + beta * pd[q];
+                gamma = kappa;
+            }
+            for (int64_t q = 0; q < nv; ++q) dv[q] += du[q];
+        }
+    }
+    free(dxg); free(f); free(r); free(pd); free(sv); free(du);
+    return it;
+}
+
+/*
+ * One step of the implicit midpoint rule: P2G of mass and momentum, v_i = (m v)_i / m_i,
+ * the grid solve above from dv = 0, v~ = v + dv, and the general transfer to particles with
+ * lambda = 1/2.  Gravity and walls are not applied (neither is in the paper).  Returns the
+ * number of skipped particles (-1 when memory runs out).
+ */
+int64_t or_step_midpoint(const or_cfg* c, int64_t n, double* x, double* v, double* B, double* F,
+                         const double* mass, const double* vol, int newton, int cg, double tol)
+{
+    const int d = c->dim;
+    const int64_t nn = node_count(c), nv = nn * d;
+    double* gm = (double*)calloc((size_t)nn, sizeof(double));
+    double* gmv = (double*)calloc((size_t)nv, sizeof(double));
+    double* gv = (double*)calloc((size_t)nv, sizeof(double));
+    double* gvt = (double*)calloc((size_t)nv, sizeof(double));
+    double* dv = (double*)calloc((size_t)nv, sizeof(double));
+    double* f = (double*)calloc((size_t)nv, sizeof(double));
+    int64_t bad = -1;
+    if (gm && gmv && gv && gvt && dv && f) {
+        or_cfg ch = *c;
+        ch.lambda_t = 0.5;
+        ch.boundary = 0;
+        for (int a = 0; a < 3; ++a) ch.gravity[a] = 0.0;
+        or_cfg c0 = ch;
+        c0.model = 0;                                   /* mass and momentum only */
+        bad = or_p2g(&c0, n, x, v, B, F, mass, vol, gm, gmv, f);
+        for (int64_t i = 0; i < nn; ++i)
+            for (int a = 0; a < d; ++a) gv[i * d + a] = gm[i] > 0.0 ? gmv[i * d + a] / gm[i] : 0.0;
+        if (or_midpoint_solve(&ch, n, x, F, vol, gm, gv, newton, cg, tol, dv) < 0) bad = -1;
+        for (int64_t q = 0; q < nv; ++q) gvt[q] = gv[q] + dv[q];
+        if (bad >= 0) bad += or_g2p(&ch, n, x, v, B, F, gv, gvt);
+    }
+    free(gm); free(gmv); free(gv); free(gvt); free(dv); free(f);
     return bad;
 }
 
