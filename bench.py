@@ -12,6 +12,13 @@ Workloads (seeded synthetic inputs shaped like the paper's elastic-body scenes):
   serving   a seeded Poisson stream of such simulations (--rate per second, --requests,
             --budget-gb) through the continuous-batching loop: throughput, p50 / p99 latency
 
+The default run (--workload cube128) prints one JSON line: the cube128 step is the headline
+`value`, and the line carries a block for each of the other workloads, each device-timed
+with its own clock record: `spheres256` (full size, with the HBM roofline of its dominant
+kernel and the FP32 ALU fraction of P2G), `batched` (--block-sims simulations of the mix,
+batched against plain) and `serving` (--block-requests requests at --rate per second).
+--no-blocks leaves them out.
+
 One "step" = the whole hot path: cell keys, radix sort, tile list, P2G (+force), grid
 update, G2P.  `value` is device-timed (CUDA events on the simulation's stream, inputs
 resident in HBM and larger than L2); `e2e` goes through the C ABI with pinned host buffers
@@ -65,6 +72,8 @@ ALGO_BYTES = {
 }
 # the whole step adds the keys G2P writes and the sort reads (8 B per particle)
 STEP_BYTES = (sum(b for b, _ in ALGO_BYTES.values()) + 8, sum(n for _, n in ALGO_BYTES.values()))
+# stored particle state per copy (FP32, 3-D): A V Ba Bb Fa Fb (16 B each), Fc (8), Ta (16), Tb (8)
+STATE_BYTES_PER_PARTICLE = 6 * 16 + 8 + 16 + 8
 KERNEL_OF_PHASE = {"p2g": "k_p2g_cells", "grid_update": "k_grid_update", "g2p": "k_g2p"}
 
 
@@ -233,17 +242,15 @@ def batched_members(apic, count: int, seed: int, ppc: int = 8):
     return out
 
 
-def run_batched(args) -> int:
-    """Many simulations: the batched form (one persistent launch per phase, graph-replayed,
-    autotuned tiles) against the plain form (each simulation stepped by its own launches)."""
+def batched_block(nsims: int, steps: int, warmup: int) -> dict:
+    """Many simulations of the batched mix: the batched form (one persistent launch per
+    phase, graph-replayed, autotuned tiles) against the plain form (each simulation stepped
+    by its own launches), both device-timed with CUDA events, clocks sampled meanwhile."""
     import torch
 
-    from paper_1603_06188_gb300 import apic, build
+    from paper_1603_06188_gb300 import apic
 
-    build.build()
-    apic.load()
-    torch.cuda.set_device(0)
-    members = batched_members(apic, args.sims, seed=1234)
+    members = batched_members(apic, nsims, seed=1234)
     sims = []
     for cfg, x, v, B in members:
         sim = apic.Sim(cfg, len(x))
@@ -251,13 +258,17 @@ def run_batched(args) -> int:
         sims.append(sim)
     total = sum(s.n for s in sims)
     blocks = sum(s.n_blocks for s in sims)
-    # plain form: every simulation stepped by its own launches, one after the other
     for s in sims:
         s.step(1)
     torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    # plain form: every simulation stepped by its own launches, one after the other
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    plain_steps = max(1, args.steps // 4)
+    plain_steps = max(1, steps // 4)
+    l0 = sum(s.stats()["kernel_launches"] for s in sims)
     e0.record(stream)
     for _ in range(plain_steps):
         for s in sims:
@@ -265,60 +276,57 @@ def run_batched(args) -> int:
     e1.record(stream)
     torch.cuda.synchronize()
     plain_ms = e0.elapsed_time(e1) / plain_steps
-    plain_launches = sum(s.stats()["kernel_launches"] for s in sims)
+    plain_launches = (sum(s.stats()["kernel_launches"] for s in sims) - l0) // plain_steps
     # batched form
     batch = apic.Batch(dim=3, order=2, precision=32, max_sims=len(sims), max_particles=total + 1,
                        max_blocks=blocks + 1, use_graph=True)
     for s in sims:
         batch.add(s)
     tile, group = batch.autotune(steps=2)
-    batch.step(args.warmup)
+    batch.step(warmup)
     batch.synchronize()
-    l0 = batch.stats()["kernel_launches"]
+    b0 = batch.stats()["kernel_launches"]
     e0.record(batch.stream)
-    batch.step(args.steps)
+    batch.step(steps)
     e1.record(batch.stream)
     batch.synchronize()
-    batch_ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    batch_ms = e0.elapsed_time(e1) / steps
     st = batch.stats()
-    out = {"metric": METRIC, "value": total / (batch_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": batch_ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+    out = {"value": total / (batch_ms / 1e3), "unit": UNIT, "ms_per_step": batch_ms, "steps": steps,
+           "warmup": warmup,
            "config": {"workload": f"batched{len(sims)}", "sims": len(sims), "particles": total, "node_blocks": blocks,
                       "description": "independent 3-D MPM+APIC sims, grid edge U{32..96}, particles log-uniform "
                                      "2k-400k (target), box/sphere, random rigid velocity, quadratic, FP32, 8 ppc",
                       "tile_particles": tile, "p2g_group": group, "cuda_graph": True},
            "plain": {"value": total / (plain_ms / 1e3), "ms_per_step": plain_ms, "steps": plain_steps,
-                     "kernel_launches_per_step": plain_launches // max(1, (1 + plain_steps))},
+                     "kernel_launches_per_step": plain_launches},
            "batched_over_plain": plain_ms / batch_ms,
-           "gpu_launches": st["kernel_launches"] - l0, "tiles": st["tiles"]}
-    print(json.dumps(out), flush=True)
+           "gpu_launches": st["kernel_launches"] - b0, "tiles": st["tiles"], "clocks": clk}
     batch.close()
     for s in sims:
         s.close()
-    return 0
+    return out
 
 
-def run_serving(args) -> int:
+def serving_block(nreq: int, rate: float, budget_gb: float) -> dict:
     """Continuous batching of a Poisson stream of simulations (sizes as in the batched mix,
-    steps U{50..2000}), admitted by device footprint under a memory budget."""
+    steps U{50..2000}), admitted by device footprint under a memory budget; clocks sampled
+    over the whole stream."""
     import torch
 
-    from paper_1603_06188_gb300 import apic, build, serving
+    from paper_1603_06188_gb300 import apic, serving
 
-    build.build()
-    apic.load()
-    torch.cuda.set_device(0)
     rng = np.random.default_rng(99)
-    members = batched_members(apic, args.requests, seed=4321)
-    arrivals = serving.poisson_arrivals(rng, args.rate, args.requests)
+    members = batched_members(apic, nreq, seed=4321)
+    arrivals = serving.poisson_arrivals(rng, rate, nreq)
     reqs = []
     for i, (cfg, x, v, B) in enumerate(members):
         steps = int(rng.integers(50, 2001))
         reqs.append(serving.Request(i, float(arrivals[i]), steps, apic.apic_workspace_size(cfg, len(x)), len(x),
                                     payload=(cfg, x, v, B)))
-    budget = int(args.budget_gb * 1e9)
-    batch = apic.Batch(dim=3, order=2, precision=32, max_sims=args.requests,
+    budget = int(budget_gb * 1e9)
+    batch = apic.Batch(dim=3, order=2, precision=32, max_sims=nreq,
                        max_particles=sum(r.particles for r in reqs) + 1,
                        max_blocks=sum(int(np.prod([(c.res[a] + 3) // 4 for a in range(3)])) for c, *_ in members) + 1,
                        use_graph=True)
@@ -329,18 +337,58 @@ def run_serving(args) -> int:
         sim.upload(x, v, B)
         return sim
 
-    rep, _ = serving.serve_gpu(reqs, make_sim, batch, budget, max_resident=args.requests, max_chunk=8)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    rep, _ = serving.serve_gpu(reqs, make_sim, batch, budget, max_resident=nreq, max_chunk=8)
+    clk = clocks.stop()
     offered = sum(r.particles * r.steps for r in reqs) / max(arrivals[-1], 1e-9)
-    out = {"metric": METRIC, "value": rep.throughput, "unit": UNIT, "n_gpus": 1, "steps": rep.batched_steps,
-           "warmup": 0, "ms_per_step": 1e3 * rep.makespan / max(1, rep.batched_steps), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "serving", "requests": args.requests, "rate_per_s": args.rate,
-                      "budget_gb": args.budget_gb, "steps_per_request": "U{50..2000}"},
-           "latency_s": {"p50": rep.percentile(50), "p99": rep.percentile(99), "max": max(rep.latencies)},
-           "offered_particle_steps_per_s": offered, "completed": rep.completed, "makespan_s": rep.makespan,
-           "max_resident": rep.max_resident, "max_resident_gb": rep.max_bytes / 1e9}
-    print(json.dumps(out), flush=True)
+    out = {"value": rep.throughput, "unit": UNIT, "batched_steps": rep.batched_steps,
+           "ms_per_batched_step": 1e3 * rep.makespan / max(1, rep.batched_steps),
+           "config": {"workload": f"serving{nreq}", "requests": nreq, "rate_per_s": rate, "budget_gb": budget_gb,
+                      "steps_per_request": "U{50..2000}", "sizes": "as the batched mix"},
+           "latency_s": {"p50": rep.percentile(50), "p99": rep.percentile(99),
+                         "max": max(rep.latencies) if rep.latencies else None},
+           "offered_particle_steps_per_s": offered, "achieved_over_offered": rep.throughput / offered,
+           "completed": rep.completed, "rejected": len(rep.rejected), "failed": len(rep.failed),
+           "makespan_s": rep.makespan, "max_resident": rep.max_resident, "max_resident_gb": rep.max_bytes / 1e9,
+           "clocks": clk}
     batch.close()
+    return out
+
+
+def run_batched(args) -> int:
+    import torch
+
+    from paper_1603_06188_gb300 import apic, build
+
+    build.build()
+    apic.load()
+    torch.cuda.set_device(0)
+    b = batched_block(args.sims, args.steps, args.warmup)
+    out = {"metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": b["config"], "plain": b["plain"],
+           "batched_over_plain": b["batched_over_plain"], "gpu_launches": b["gpu_launches"], "clocks": b["clocks"]}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_serving(args) -> int:
+    import torch
+
+    from paper_1603_06188_gb300 import apic, build
+
+    build.build()
+    apic.load()
+    torch.cuda.set_device(0)
+    b = serving_block(args.requests, args.rate, args.budget_gb)
+    out = {"metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": 1, "steps": b["batched_steps"],
+           "warmup": 0, "ms_per_step": b["ms_per_batched_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": b["config"],
+           "latency_s": b["latency_s"], "offered_particle_steps_per_s": b["offered_particle_steps_per_s"],
+           "completed": b["completed"], "clocks": b["clocks"]}
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -396,47 +444,29 @@ def run_reference(args, world, rank):
     return 0
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="cube128", choices=sorted(WORKLOADS) + ["batched", "serving"])
-    ap.add_argument("--sims", type=int, default=512)
-    ap.add_argument("--requests", type=int, default=200)
-    ap.add_argument("--rate", type=float, default=200.0)
-    ap.add_argument("--budget-gb", type=float, default=150.0)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--ppc", type=int, default=None)
-    ap.add_argument("--ref-particles", type=int, default=0)
-    ap.add_argument("--cpu-sample", type=int, default=2500000)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--p2g-kernel", type=int, default=0)
-    ap.add_argument("--tile", type=int, default=0)
-    args = ap.parse_args()
-    if args.warmup < 3:
-        args.warmup = 3
-    world, rank, local, dist = dist_setup(args.gpus)
-    if args.impl == "reference":
-        return run_reference(args, world, rank)
-    if args.workload == "batched":
-        return run_batched(args) if rank == 0 else 0
-    if args.workload == "serving":
-        return run_serving(args) if rank == 0 else 0
+# FP32 operations per particle of P2G in the separable form the kernel evaluates (an FMA
+# counts two): per stencil node the four sums take 7 FMAs; per (j, k) pair of the two outer
+# axes the three partial momenta take 6 FMAs; the per-axis weights, their derivatives and the
+# per-axis factors of the affine and stress terms take about 60 (quadratic) / 90 (cubic)
+P2G_FLOPS = {2: 27 * 14 + 9 * 12 + 60 * 2, 3: 64 * 14 + 16 * 12 + 90 * 2}
 
+
+def fp32_peak_flops(sm_mhz: float | None) -> float:
+    """FP32 FMA peak: 152 SMs x 128 lanes x 2 flops per clock at the sampled SM clock (the
+    maximum, 2070 MHz, when no sample is available)."""
+    return 152 * 128 * 2 * (sm_mhz or 2070.0) * 1e6
+
+
+def single_block(args, wname: str, rank: int, world: int, local: int, dist, with_e2e: bool, with_cpu: bool,
+                 steps: int) -> dict:
+    """One large simulation (cube128 or spheres256): device-timed steps, per-phase times,
+    the roofline of the dominant kernel and of the whole step, e2e through the C ABI."""
     import torch
 
-    from paper_1603_06188_gb300 import apic, build
+    from paper_1603_06188_gb300 import apic
 
-    torch.cuda.set_device(local)
-    if rank == 0:
-        build.build()
-    if dist:
-        dist.barrier()
-    apic.load()
-    w = dict(WORKLOADS[args.workload])
-    if args.ppc:
+    w = dict(WORKLOADS[wname])
+    if args.ppc and wname == args.workload:
         w["ppc"] = args.ppc
     sc = make_scene(w, seed=rank)
     x, v, B, F = initial_state(sc, w["order"])
@@ -466,7 +496,7 @@ def main():
     if dist:
         dist.barrier()
     ev0.record(stream)
-    sim.step(args.steps)                      # the timed steps carry no instrumentation
+    sim.step(steps)                           # the timed steps carry no instrumentation
     ev1.record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -478,13 +508,13 @@ def main():
     launches = stats["kernel_launches"] - launches0
     p_after, l_after = sim.momentum("particles")
     # per-phase times (the library's CUDA events around each phase) from further steps
-    prof_steps = max(1, min(args.steps, 100))
+    prof_steps = max(1, min(steps, 100))
     sim.profile(True)
     sim.step(prof_steps)
     torch.cuda.synchronize()
     sim.profile(False)
     phases = sim.profile_read()
-    max_ms, total_units = aggregate(ms, sc.n * args.steps, dist, device="cuda")
+    max_ms, total_units = aggregate(ms, sc.n * steps, dist, device="cuda")
     value = total_units / (max_ms / 1e3)
 
     # roofline of the dominant single-kernel phase
@@ -498,25 +528,32 @@ def main():
         algo = bp * sc.n + bn * active_nodes
         per_phase[name] = {"ms_per_launch": 1e3 * t_launch, "algorithmic_bytes": algo, "gbs": algo / t_launch / 1e9}
     dom = max(per_phase, key=lambda k: per_phase[k]["ms_per_launch"])
-    traffic = recorded_traffic(KERNEL_OF_PHASE[dom], args.workload)
+    traffic = recorded_traffic(KERNEL_OF_PHASE[dom], wname)
     roof = {"bound": "hbm", "kernel": KERNEL_OF_PHASE[dom], "achieved": per_phase[dom]["gbs"], "peak": peak,
             "unit": "GB/s", "frac": per_phase[dom]["gbs"] / peak, "traffic": traffic,
             "peak_source": f"{peak_kind} hbm_gbs",
             "algorithmic_bytes_per_launch": per_phase[dom]["algorithmic_bytes"]}
     step_bytes = STEP_BYTES[0] * sc.n + STEP_BYTES[1] * active_nodes
-    step_gbs = step_bytes / (max_ms / args.steps * 1e-3) / 1e9
+    step_gbs = step_bytes / (max_ms / steps * 1e-3) / 1e9
     step_roof = {"bytes_per_step": step_bytes, "achieved": step_gbs, "peak": peak, "unit": "GB/s",
                  "frac": step_gbs / peak, "per_particle_bytes": STEP_BYTES[0], "per_active_node_bytes": STEP_BYTES[1]}
+    p2g_t = per_phase["p2g"]["ms_per_launch"] * 1e-3
+    flops = P2G_FLOPS[w["order"]] * sc.n
+    alu_peak = fp32_peak_flops(clk["sm_mhz"] if clk else None)
+    alu_roof = {"bound": "alu", "kernel": KERNEL_OF_PHASE["p2g"], "achieved": flops / p2g_t / 1e12,
+                "peak": alu_peak / 1e12, "unit": "TFLOP/s", "frac": flops / p2g_t / alu_peak,
+                "flops_per_particle": P2G_FLOPS[w["order"]],
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x sampled SM clock"}
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
-    if not args.no_e2e:
+    if with_e2e:
         n = sc.n
         pin = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
         hx, hv, hB, hF = pin((n, 3)), pin((n, 3)), pin((n, 3, 3)), pin((n, 3, 3))
         hx[:], hv[:], hB[:], hF[:] = x, v, B, F
         ox, ov, oB, oF = pin((n, 3)), pin((n, 3)), pin((n, 3, 3)), pin((n, 3, 3))
-        e_steps = max(1, min(args.steps, 100))
+        e_steps = max(1, min(steps, 100))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         apic.apic_upload(sim.handle, n, hx, hv, hB, hF, on_device=0)
@@ -528,10 +565,12 @@ def main():
         et = time.perf_counter() - t0
         state_bytes = n * (3 + 3 + 9 + 9) * 8
         e2e = {"value": n * e_steps / et * world, "unit": UNIT, "steps": e_steps,
+               "note": f"one upload and one download of the whole state around {e_steps} steps, the FP64 "
+                       "momentum read back after every step",
                "h2d_bytes_per_step": state_bytes / e_steps, "d2h_bytes_per_step": state_bytes / e_steps + 48}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if with_cpu:
         import oracle
 
         oracle.build()
@@ -539,32 +578,98 @@ def main():
         cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"2 steps of a slab of {cn} of the {sc.n} particles (lowest x) on the full grid, "
                          f"{csecs:.1f} s, FP64 single-threaded"}
-
-    if rank == 0:
-        sp = np.abs(p_after - p_before).max()
-        out = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "description": w["desc"], "particles": sc.n, "ppc": w["ppc"],
-                       "grid": [w["res"]] * 3, "order": w["order"], "dt": w["dt"], "active_nodes": active_nodes,
-                       "l2": f"inputs larger than L2: particle state {sc.n * 100 / 1e6:.0f} MB per copy",
-                       "parallelism": f"replicas x{world}"},
-            "roofline": roof,
-            "step_roofline": step_roof,
-            "cpu_baseline": cpu,
-            "e2e": e2e,
-            "gpu_launches": launches,
-            "clocks": clk,
-            "phases_ms_per_step": {k: v_["ms"] / prof_steps for k, v_ in phases.items()},
-            "phases_measured_over_steps": prof_steps,
-            "per_kernel": per_phase,
-            "polar_fp64_fallbacks": stats["polar_fp64_fallbacks"],
-            "momentum_change_over_timed_steps": {"p": (p_after - p_before).tolist(), "l": (l_after - l_before).tolist(),
-                                                 "finite": bool(np.isfinite(p_after).all() and np.isfinite(l_after).all())},
-        }
-        print(json.dumps(out), flush=True)
+    state_bytes_per_copy = sc.n * STATE_BYTES_PER_PARTICLE
+    out = {
+        "value": value, "unit": UNIT, "ms_per_step": max_ms / steps, "steps": steps, "warmup": args.warmup,
+        "config": {"workload": wname, "description": w["desc"], "particles": sc.n, "ppc": w["ppc"],
+                   "grid": [w["res"]] * 3, "order": w["order"], "dt": w["dt"], "active_nodes": active_nodes,
+                   "l2": f"inputs larger than L2: particle state {state_bytes_per_copy / 1e6:.0f} MB per copy "
+                         f"({STATE_BYTES_PER_PARTICLE} B per particle)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof,
+        "step_roofline": step_roof,
+        "alu_roofline": alu_roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "phases_ms_per_step": {k: v_["ms"] / prof_steps for k, v_ in phases.items()},
+        "phases_measured_over_steps": prof_steps,
+        "per_kernel": per_phase,
+        "polar_fp64_fallbacks": stats["polar_fp64_fallbacks"],
+        "momentum_change_over_timed_steps": {"p": (p_after - p_before).tolist(), "l": (l_after - l_before).tolist(),
+                                             "finite": bool(np.isfinite(p_after).all() and np.isfinite(l_after).all())},
+    }
     sim.close()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="cube128", choices=sorted(WORKLOADS) + ["batched", "serving"])
+    ap.add_argument("--sims", type=int, default=512)
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ppc", type=int, default=None)
+    ap.add_argument("--ref-particles", type=int, default=0)
+    ap.add_argument("--cpu-sample", type=int, default=2500000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-blocks", action="store_true",
+                    help="only the headline workload (no spheres256 / batched / serving blocks)")
+    ap.add_argument("--block-sims", type=int, default=128, help="simulations of the batched block")
+    ap.add_argument("--block-requests", type=int, default=100, help="requests of the serving block")
+    ap.add_argument("--p2g-kernel", type=int, default=0)
+    ap.add_argument("--tile", type=int, default=0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local, dist = dist_setup(args.gpus)
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    if args.workload == "batched":
+        return run_batched(args) if rank == 0 else 0
+    if args.workload == "serving":
+        return run_serving(args) if rank == 0 else 0
+
+    import torch
+
+    from paper_1603_06188_gb300 import apic, build
+
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    apic.load()
+    head = single_block(args, args.workload, rank, world, local, dist, with_e2e=not args.no_e2e,
+                        with_cpu=rank == 0 and world == 1 and not args.no_cpu_baseline, steps=args.steps)
+    blocks = {}
+    if rank == 0 and world == 1 and not args.no_blocks and args.workload == "cube128":
+        # the other headline workloads, scaled to finish within the run: the 256^3 cubic step
+        # at its full size, the batched mix and the serving stream with fewer simulations
+        blocks["spheres256"] = single_block(args, "spheres256", 0, 1, local, None, with_e2e=False, with_cpu=False,
+                                            steps=args.steps)
+        blocks["batched"] = batched_block(args.block_sims, args.steps, args.warmup)
+        blocks["serving"] = serving_block(args.block_requests, args.rate, args.budget_gb)
+    if rank == 0:
+        out = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
+        for k in ("config", "roofline", "step_roofline", "alu_roofline", "cpu_baseline", "e2e", "gpu_launches",
+                  "clocks", "phases_ms_per_step", "phases_measured_over_steps", "per_kernel", "polar_fp64_fallbacks",
+                  "momentum_change_over_timed_steps"):
+            out[k] = head[k]
+        for name, b in blocks.items():
+            out[name] = b
+        if "batched" in blocks:
+            out["batched_over_plain"] = blocks["batched"]["batched_over_plain"]
+        print(json.dumps(out), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()

@@ -47,7 +47,8 @@ typedef enum {
     APIC_ERR_OOM = 2,          /* workspace too small or particle capacity exceeded */
     APIC_ERR_CUDA = 3,         /* a CUDA runtime call failed */
     APIC_ERR_TIMEOUT = 4,      /* a bounded device-side wait ran out */
-    APIC_ERR_NUMERIC = 5,      /* a particle's stencil left the grid (it was clamped) */
+    APIC_ERR_NUMERIC = 5,      /* a particle's stencil left the grid (it was clamped), or a
+                                  non-finite value was uploaded */
     APIC_ERR_UNSUPPORTED = 6   /* configuration the library does not implement */
 } apic_status;
 
@@ -84,10 +85,8 @@ typedef struct {
     double particle_volume;  /* V_p (reference volume), the same for every particle */
     int tile_particles;      /* particles per P2G / G2P tile (power of two, 256..4096);
                                 0 = default */
-    int p2g_kernel;          /* P2G variant: 0 = default (2), 1 = warp-segmented reduction,
-                                2 = cell-parallel, 3 = cell-interleaved, 4 = node-split
-                                (the lanes of a group share the particles and split the
-                                stencil nodes); results agree to rounding */
+    int p2g_kernel;          /* P2G kernel: 0 = default, 2 = the cell-parallel kernel (the
+                                only one; other values return APIC_ERR_ARG) */
     double flip_alpha;       /* APIC_TRANSFER_FLIP only: v_p <- a (v_p + sum w (v~_i - v_i)) +
                                 (1 - a) sum w v~_i, a in [0, 1] (1 = the paper's FLIP); the
                                 velocities v_i before the grid update are kept (+32 B per
@@ -117,7 +116,12 @@ apic_status apic_destroy(apic_sim* sim);
  * F (n*d*d).  v, B may be NULL (zero); F may be NULL (identity).  `on_device` = 1 if the
  * pointers are device memory, 0 for host memory.  The data are copied; the library keeps
  * no pointer.  Synchronising when on_device = 0.
- * Errors: APIC_ERR_ARG, APIC_ERR_OOM (n > capacity), APIC_ERR_CUDA. */
+ * Every value is checked on the device.  A NaN or Inf anywhere in x, v, B or F gives
+ * APIC_ERR_NUMERIC: for host input from this call, which then discards the upload (the
+ * simulation holds no particles); for device input from the next synchronising call.  A
+ * position outside the grid is clamped into it and also gives APIC_ERR_NUMERIC; the
+ * particles are kept.
+ * Errors: APIC_ERR_ARG, APIC_ERR_OOM (n > capacity), APIC_ERR_NUMERIC, APIC_ERR_CUDA. */
 apic_status apic_upload(apic_sim* sim, int64_t n, const double* x, const double* v,
                         const double* B, const double* F, int on_device);
 
@@ -266,6 +270,31 @@ apic_status apic_batch_remove(apic_batch* batch, apic_sim* sim);
  * would).  Asynchronous on the batch's stream. */
 apic_status apic_batch_step(apic_batch* batch, int n);
 
+/* Serving (continuous batching; no counterpart in the paper).  Admit a simulation that will
+ * run `steps` batched steps and occupies `footprint_bytes` of device memory while resident
+ * (typically its apic_workspace_size): if the footprints of the members admitted this way
+ * plus this one exceed `budget_bytes`, nothing changes and APIC_ERR_OOM is returned (the
+ * caller keeps it queued and retries after a completion); otherwise it joins the batch as
+ * apic_batch_add would.  Synchronises the simulation's stream.
+ * Errors: APIC_ERR_ARG (steps <= 0, negative sizes, as apic_batch_add), APIC_ERR_OOM (over
+ * the budget, or a batch capacity), APIC_ERR_UNSUPPORTED, APIC_ERR_CUDA. */
+apic_status apic_batch_admit(apic_batch* batch, apic_sim* sim, int steps, int64_t footprint_bytes,
+                             int64_t budget_bytes);
+
+/* Step every member min(max_steps, the fewest steps any admitted member has left) batched
+ * steps -- so no admitted member passes its completion -- then take the admitted members
+ * whose steps are done out of the batch (as apic_batch_remove: their state is current and
+ * their memory counts no more against the budget) and write them to finished[0 ..
+ * *n_finished - 1] in membership order.  Members added with apic_batch_add have no step
+ * count and stay.  `finished` needs room for every admitted member.  *steps_done (may be
+ * NULL) receives the steps taken.  Synchronises when a member finishes.
+ * Errors: APIC_ERR_ARG, and those of apic_batch_step / apic_batch_remove. */
+apic_status apic_batch_run(apic_batch* batch, int max_steps, apic_sim** finished, int max_finished,
+                           int* n_finished, int* steps_done);
+
+/* Device bytes of the members admitted with apic_batch_admit and still resident. */
+apic_status apic_batch_resident_bytes(apic_batch* batch, int64_t* bytes);
+
 /* Tile size and P2G lane group for the following steps (0 keeps the current value). */
 apic_status apic_batch_set_tuning(apic_batch* batch, int tile_particles, int group);
 
@@ -288,26 +317,40 @@ const char* apic_batch_last_error(apic_batch* batch);
  * unbounded time).  Such a caller passes only its inputs and outputs; the sort's own
  * scratch (ping-pong keys and indices, digit histograms, scan partials) lives in a
  * fixed-size static device array inside the library, which every GPU that loads the
- * library holds until the process exits (about 9 MB).
+ * library holds until the process exits (about 9 MB).  It is a plain LSD radix sort, one
+ * pass per 8-bit digit (a histogram, a device-wide exclusive scan, a stable scatter); it
+ * does not use the one-sweep and incremental kernels of apic_p2g's sort, but gives the
+ * same result: the stable sort of the keys.
  *   keys        device pointer, n keys (read only)
  *   key_bits    number of low key bits to sort on, 1..32 (higher bits must be zero)
  *   sorted_keys device pointer, n entries: the keys in ascending order
  *   perm        device pointer, n entries: perm[k] = input index of the k-th sorted key;
- *               equal keys keep their input order (stable), the same result apic_p2g's
- *               sort produces (see apic_keys_download)
+ *               equal keys keep their input order (stable)
  *   stream      cudaStream_t (or NULL); the call is asynchronous on it.
+ * The three buffers must not overlap (a pass reads its input while other CTAs write its
+ * output); overlapping buffers return APIC_ERR_ARG.
  * n <= APIC_SORT_NOALLOC_MAX_KEYS; larger n returns APIC_ERR_OOM before any launch.
  * The first call on each device looks up the static array's device address
  * (cudaGetSymbolAddress, with that device current) and caches it; make that first call
  * before any stream capture.  Every call reuses the same array, so calls whose work
  * overlaps on the GPU (other streams, other threads) race on it: serialise them.
  * Every scratch word a call reads is written earlier in the same call, so nothing left
- * by a previous call is used.
- * Errors: APIC_ERR_ARG (NULL pointer, n < 0, key_bits out of range), APIC_ERR_OOM,
- * APIC_ERR_CUDA. */
+ * by a previous call is used.  A CUDA error already pending on the calling thread when
+ * the call starts is left pending, nothing is launched, and APIC_ERR_CUDA is returned.
+ * Errors: APIC_ERR_ARG (NULL pointer, n < 0, key_bits out of range, overlapping buffers),
+ * APIC_ERR_OOM, APIC_ERR_CUDA. */
 #define APIC_SORT_NOALLOC_MAX_KEYS (1 << 20)
 apic_status apic_sort_keys_noalloc(const uint32_t* keys, int64_t n, int key_bits, uint32_t* sorted_keys,
                                    uint32_t* perm, void* stream);
+
+/* Fault-injection hook for tests of the timeout path (the paper has no counterpart): the
+ * number of polls G2P's first wait for a tile's staged grid blocks makes before it gives up
+ * (default 4194304, several seconds).  With 0 the wait gives up at once: the CTA latches
+ * APIC_ERR_TIMEOUT, waits (bounded) for its copies in flight to land, and leaves without
+ * writing its particles, so the next synchronising call returns APIC_ERR_TIMEOUT and the
+ * particle state of that step is not valid; the device stays usable.  Host-only
+ * bookkeeping.  Errors: APIC_ERR_ARG (NULL, or the simulation is in a batch). */
+apic_status apic_set_wait_limit(apic_sim* sim, unsigned polls);
 
 /* Reason for the last failing call on this simulation ("" if none). */
 const char* apic_last_error(apic_sim* sim);

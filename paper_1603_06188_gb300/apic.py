@@ -114,6 +114,11 @@ SIGNATURES = {
     "apic_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "apic_sort_keys_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "apic_profile_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "apic_set_wait_limit": (C.c_int, [C.c_void_p, C.c_uint]),
+    "apic_batch_admit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_int64]),
+    "apic_batch_run": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_int),
+                                 C.POINTER(C.c_int)]),
+    "apic_batch_resident_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
 }
 PHASES = ["keys", "sort", "tiles", "p2g", "grid_update", "g2p"]
 
@@ -243,6 +248,10 @@ def apic_stats(sim):
     return out
 
 
+def apic_set_wait_limit(sim, polls: int):
+    _check(load().apic_set_wait_limit(sim, polls), sim)
+
+
 def apic_last_error(sim) -> str:
     return load().apic_last_error(sim).decode()
 
@@ -306,6 +315,26 @@ def apic_batch_step(batch, n: int):
     _bcheck(load().apic_batch_step(batch, n), batch)
 
 
+def apic_batch_admit(batch, sim, steps: int, footprint_bytes: int, budget_bytes: int):
+    _bcheck(load().apic_batch_admit(batch, sim, steps, footprint_bytes, budget_bytes), batch)
+
+
+def apic_batch_run(batch, max_steps: int, max_finished: int):
+    """Returns (handles of the finished members, steps taken)."""
+    cap = max(int(max_finished), 1)
+    out = (C.c_void_p * cap)()
+    n = C.c_int(0)
+    done = C.c_int(0)
+    _bcheck(load().apic_batch_run(batch, max_steps, out, cap, C.byref(n), C.byref(done)), batch)
+    return [out[i] for i in range(n.value)], done.value
+
+
+def apic_batch_resident_bytes(batch) -> int:
+    out = C.c_int64(0)
+    _bcheck(load().apic_batch_resident_bytes(batch, C.byref(out)))
+    return out.value
+
+
 def apic_batch_set_tuning(batch, tile_particles: int, group: int):
     _bcheck(load().apic_batch_set_tuning(batch, tile_particles, group), batch)
 
@@ -365,16 +394,20 @@ class Sim:
 
     def upload(self, x, v=None, B=None, F=None):
         """Host numpy arrays (float64) or CUDA float64 tensors."""
-        d = self.dim
         n = len(x)
-        self.n = n          # the library holds n particles even when it reports a range error
-        if isinstance(x, np.ndarray):
-            arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (x, v, B, F)]
-            apic_upload(self.handle, n, *arrs, on_device=0)
-        else:
-            arrs = [None if a is None else a.contiguous() for a in (x, v, B, F)]
-            apic_upload(self.handle, n, *arrs, on_device=1)
-            self._keep = arrs
+        self.n = n
+        try:
+            if isinstance(x, np.ndarray):
+                arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (x, v, B, F)]
+                apic_upload(self.handle, n, *arrs, on_device=0)
+            else:
+                arrs = [None if a is None else a.contiguous() for a in (x, v, B, F)]
+                apic_upload(self.handle, n, *arrs, on_device=1)
+                self._keep = arrs
+        except ApicError:
+            # a range error keeps the (clamped) particles; a rejected upload keeps none
+            self.n = int(apic_stats(self.handle)[0])
+            raise
 
     def download(self):
         d, n = self.dim, self.n
@@ -484,6 +517,25 @@ class Batch:
 
     def step(self, n: int = 1):
         apic_batch_step(self.handle, n)
+
+    def admit(self, sim: "Sim", steps: int, footprint_bytes: int, budget_bytes: int):
+        """Join the batch for `steps` steps if its footprint fits the budget (else ApicError
+        with status APIC_ERR_OOM and nothing changes)."""
+        apic_batch_admit(self.handle, sim.handle, steps, footprint_bytes, budget_bytes)
+        self.members.append(sim)
+
+    def run(self, max_steps: int):
+        """Steps to the nearest completion (at most max_steps); returns (the Sims that
+        finished and left the batch, steps taken)."""
+        handles, done = apic_batch_run(self.handle, max_steps, len(self.members))
+        by_handle = {s.handle.value: s for s in self.members}
+        fin = [by_handle[h] for h in handles]
+        for sim in fin:
+            self.members.remove(sim)
+        return fin, done
+
+    def resident_bytes(self) -> int:
+        return apic_batch_resident_bytes(self.handle)
 
     def set_tuning(self, tile_particles: int = 0, group: int = 0):
         apic_batch_set_tuning(self.handle, tile_particles, group)

@@ -109,14 +109,15 @@ apic_status fill_cfg(const apic_config* in, int64_t max_particles, HostCfg* c, s
     c->mass = in->particle_mass;
     c->vol = in->particle_volume;
     c->tile = tile;
-    if (in->p2g_kernel < 0 || in->p2g_kernel > 4) { *why = "p2g_kernel must be 0..4"; return APIC_ERR_ARG; }
-    c->p2g_kernel = in->p2g_kernel != 0 ? in->p2g_kernel : 2;   // default: cell-parallel
+    if (in->p2g_kernel != 0 && in->p2g_kernel != 2) { *why = "p2g_kernel must be 0 or 2"; return APIC_ERR_ARG; }
+    c->p2g_kernel = 2;   // the cell-parallel kernel
     if (in->p2g_group != 0 && in->p2g_group != 2 && in->p2g_group != 4) { *why = "p2g_group must be 0, 2 or 4"; return APIC_ERR_ARG; }
     c->p2g_group = in->p2g_group != 0 ? in->p2g_group : 4;
     c->p2g_group_auto = in->p2g_group == 0;
     c->key_bits = 2 * in->dim + ceil_log2(c->nblocks);
     if (c->key_bits > 32) { *why = "grid too large for 32-bit cell keys"; return APIC_ERR_UNSUPPORTED; }
     c->capacity = max_particles;
+    c->wait_limit = APIC_DEFAULT_WAIT_LIMIT;
     return APIC_OK;
 }
 
@@ -218,17 +219,21 @@ apic_status cuda_fail(apic_sim* s, cudaError_t e, const char* where)
         if (e_ != cudaSuccess) return cuda_fail(s, e_, where); \
     } while (0)
 
-// read and clear the latched device error word (synchronises the stream)
-apic_status check_device(apic_sim* s)
+// read and clear the latched device error word (synchronises the stream); *bits (may be
+// NULL) receives the bits that were set
+apic_status check_device(apic_sim* s, uint32_t* bits = nullptr)
 {
     uint32_t e = 0;
+    if (bits) *bits = 0;
     CK(cudaMemcpyAsync(&e, s->b.err, 4, cudaMemcpyDeviceToHost, s->stream), "read error word");
     CK(cudaStreamSynchronize(s->stream), "synchronize");
     if (e == 0) return APIC_OK;
+    if (bits) *bits = e;
     CK(cudaMemsetAsync(s->b.err, 0, 4, s->stream), "clear error word");
     CK(cudaStreamSynchronize(s->stream), "synchronize");
     if (e & APIC_ERRBIT_TIMEOUT) return fail(s, APIC_ERR_TIMEOUT, "a bounded device wait (bulk copy completion) ran out");
     if (e & APIC_ERRBIT_CAPACITY) return fail(s, APIC_ERR_OOM, "tile list capacity exceeded");
+    if (e & APIC_ERRBIT_NONFINITE) return fail(s, APIC_ERR_NUMERIC, "a non-finite value (NaN or Inf) in the uploaded state");
     return fail(s, APIC_ERR_NUMERIC, "a particle's stencil left the grid; it was clamped to the boundary");
 }
 
@@ -367,7 +372,7 @@ apic_status apic_create(const apic_config* cfg, int64_t max_particles, void* wor
     }
     s->L.sms = sms;
     s->L.p2g_grid = sms * (p2g_per > 0 ? p2g_per : 1);
-    s->L.p2g_cells = c.p2g_kernel == 2;
+    s->L.p2g_cells = 1;
     s->L.g2p_grid = sms * (g2p_per > 0 ? g2p_per : 1);
     s->L.mom_parts = kMomParts;
     const size_t bn = c.dim == 3 ? 64 : 16;
@@ -434,7 +439,12 @@ apic_status apic_upload(apic_sim* s, int64_t n, const double* x, const double* v
     s->group_pending = s->c.p2g_group_auto != 0;   // the new particle set's density decides
     s->c.mat = 0;   // a new particle set: materials come from the configuration until set again
     CK(DISPATCH(s, upload, s->c, s->b, s->cur, n, dx_, dv, dB, dF, s->stream), "upload kernel");
-    if (!on_device) return check_device(s);
+    if (!on_device) {
+        uint32_t bits = 0;
+        apic_status st = check_device(s, &bits);
+        if (bits & APIC_ERRBIT_NONFINITE) s->n = 0;   // a rejected upload leaves no particles
+        return st;
+    }
     return APIC_OK;
 }
 
@@ -787,6 +797,14 @@ apic_status apic_profile_read(apic_sim* s, double ms[APIC_NPHASE], int64_t launc
     return APIC_OK;
 }
 
+apic_status apic_set_wait_limit(apic_sim* s, unsigned polls)
+{
+    if (!s) return APIC_ERR_ARG;
+    if (s->batch) return fail(s, APIC_ERR_ARG, "the simulation is a member of a batch");
+    s->c.wait_limit = polls;
+    return APIC_OK;
+}
+
 const char* apic_last_error(apic_sim* s)
 {
     if (!s) return "NULL simulation";
@@ -825,6 +843,11 @@ struct apic_batch {
     cudaGraphExec_t gexec;
     bool graph_valid;
     std::string err_msg;
+    // serving ledger: steps left and device footprint of the members admitted with
+    // apic_batch_admit (members added with apic_batch_add have no entry)
+    struct Ledger { int steps_left; int64_t footprint; };
+    std::map<apic_sim*, Ledger> ledger;
+    int64_t resident_bytes;
 };
 
 namespace {
@@ -1123,6 +1146,7 @@ apic_status apic_batch_create(const apic_batch_config* c, void* workspace, size_
     b->passes = 1;
     b->steps = b->launches = 0;
     b->graph_valid = false;
+    b->resident_bytes = 0;
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->err, 0, 4, b->stream);
@@ -1209,7 +1233,63 @@ apic_status apic_batch_remove(apic_batch* b, apic_sim* s)
         s->order_sorted = true;   // batched G2P also stores particle k of the sorted order at k
     }
     s->epoch = 0;   // its look-back words hold batch epochs: the next single sort clears them
+    auto it = b->ledger.find(s);
+    if (it != b->ledger.end()) {
+        b->resident_bytes -= it->second.footprint;
+        b->ledger.erase(it);
+    }
     b->dirty = true;
+    return APIC_OK;
+}
+
+apic_status apic_batch_admit(apic_batch* b, apic_sim* s, int steps, int64_t footprint_bytes, int64_t budget_bytes)
+{
+    if (!b || !s || steps <= 0 || footprint_bytes < 0 || budget_bytes < 0) return APIC_ERR_ARG;
+    if (b->resident_bytes + footprint_bytes > budget_bytes)
+        return batch_fail(b, APIC_ERR_OOM, "the simulation's footprint does not fit the memory budget now");
+    apic_status st = apic_batch_add(b, s);
+    if (st != APIC_OK) return st;
+    b->ledger[s] = {steps, footprint_bytes};
+    b->resident_bytes += footprint_bytes;
+    return APIC_OK;
+}
+
+apic_status apic_batch_run(apic_batch* b, int max_steps, apic_sim** finished, int max_finished, int* n_finished,
+                           int* steps_done)
+{
+    if (!b || max_steps <= 0 || !n_finished) return APIC_ERR_ARG;
+    *n_finished = 0;
+    if (steps_done) *steps_done = 0;
+    if (!b->ledger.empty() && (!finished || max_finished < (int)b->ledger.size()))
+        return batch_fail(b, APIC_ERR_ARG, "`finished` needs room for every admitted member");
+    if (b->members.empty()) return APIC_OK;
+    int k = max_steps;
+    for (const auto& e : b->ledger) k = e.second.steps_left < k ? e.second.steps_left : k;
+    apic_status st = batch_run(b, k);
+    if (st != APIC_OK) return st;
+    if (steps_done) *steps_done = k;
+    std::vector<apic_sim*> done;
+    for (auto& e : b->ledger) {
+        e.second.steps_left -= k;
+        if (e.second.steps_left == 0) done.push_back(e.first);
+    }
+    // retire in membership order, so the report does not depend on pointer values
+    std::vector<apic_sim*> order;
+    for (apic_sim* m : b->members)
+        for (apic_sim* d : done)
+            if (d == m) order.push_back(m);
+    for (apic_sim* m : order) {
+        st = apic_batch_remove(b, m);
+        if (st != APIC_OK) return st;
+        finished[(*n_finished)++] = m;
+    }
+    return APIC_OK;
+}
+
+apic_status apic_batch_resident_bytes(apic_batch* b, int64_t* bytes)
+{
+    if (!b || !bytes) return APIC_ERR_ARG;
+    *bytes = b->resident_bytes;
     return APIC_OK;
 }
 

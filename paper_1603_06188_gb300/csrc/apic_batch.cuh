@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(G2P_THREADS, 4) kb_g2p(SimDesc<R>* __restrict_
             const int t1 = (int)atomicAdd(tile_ctr + 1, 1u);
             s_t[buf ^ 1] = t1;
             if (t1 < ntiles) issue(t1, buf ^ 1);
-            const bool ok = g2p_wait(&mbar[buf], phase[buf], descs[sim].err);   // sd is not complete before the barrier
+            const bool ok = g2p_wait(&mbar[buf], phase[buf], descs[sim].err, descs[sim].c.wait_limit);   // sd is not complete before the barrier
             if (!ok && t1 < ntiles) mbar_wait_bounded(&mbar[buf ^ 1], phase[buf ^ 1], 1u << 22);   // drain before leaving
             s_ok = ok ? 1 : 0;
         }

@@ -244,6 +244,7 @@ template <typename R> struct DevCfg {
     uint32_t* smax;      // when set, G2P max-reduces the Sec. 4.3 particle speed here (FP32 bits)
     R cfl_coef;          // 6 sqrt(d) / dx of the Sec. 4.3 speed |v| + 6 sqrt(d)/dx |B|_F
     R flip_alpha;        // transfer 2: weight of the FLIP update
+    unsigned wait_limit; // polls of G2P's first wait for its staged grid blocks before it gives up
 };
 
 // the step's time step: fixed, or the adaptive one on the device

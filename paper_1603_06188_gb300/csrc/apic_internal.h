@@ -9,6 +9,8 @@
 #define APIC_ERRBIT_RANGE 1u     // a particle's stencil left the grid (clamped)
 #define APIC_ERRBIT_TIMEOUT 2u   // a bounded mbarrier wait ran out
 #define APIC_ERRBIT_CAPACITY 4u  // tile list overflow
+#define APIC_ERRBIT_NONFINITE 8u // a non-finite value in uploaded state
+#define APIC_DEFAULT_WAIT_LIMIT (1u << 22)
 
 // particle state lanes per copy: A V Ba Bb Fa Fb Fc Ta Tb M (layout in apic_device.cuh)
 #define APIC_STATE_LANES 10
@@ -64,12 +66,13 @@ struct HostCfg {
     double flip_alpha;           // transfer 2: weight of the FLIP update
     double mu, lam, mass, vol;
     int tile;                    // particles per tile (power of two)
-    int p2g_kernel;              // 1 warp-segmented, 2 cell-parallel, 3 interleaved, 4 node-split
+    int p2g_kernel;              // 2: the cell-parallel kernel
     int p2g_group;               // lanes per base cell of the cell-parallel P2G (2 or 4)
     int p2g_group_auto;          // 1: p2g_group follows the density after each upload
     int key_bits;
     int nblocks;
     int64_t capacity;
+    unsigned wait_limit;         // polls of G2P's first bounded wait (APIC_DEFAULT_WAIT_LIMIT)
 };
 
 // per-simulation view of the sort buffers, for the batched sort (apic_sort.cu)

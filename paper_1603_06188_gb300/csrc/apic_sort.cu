@@ -1297,7 +1297,8 @@ cudaError_t build_tiles(const Buffers& b, const uint32_t* skeys, int64_t n, int 
 }  // namespace apic
 
 // ---------------------------------------------------------------- sort without allocation
-// apic_sort_keys_noalloc: the same kernels, with all scratch in one static device array.
+// apic_sort_keys_noalloc: a plain LSD radix sort (per 8-bit digit: a histogram pass, a
+// device-wide exclusive scan and a stable scatter), with all scratch in one static device array.
 namespace apic {
 namespace {
 
@@ -1334,6 +1335,15 @@ cudaError_t noalloc_scratch(uint32_t** out)
 }  // namespace
 }  // namespace apic
 
+namespace {
+// [a, a + n) and [b, b + n) share a word
+bool overlaps(const uint32_t* a, const uint32_t* b, int64_t n)
+{
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b, len = (uintptr_t)n * sizeof(uint32_t);
+    return x < y + len && y < x + len;
+}
+}  // namespace
+
 extern "C" apic_status apic_sort_keys_noalloc(const uint32_t* keys, int64_t n, int key_bits, uint32_t* sorted_keys,
                                               uint32_t* perm, void* stream)
 {
@@ -1342,6 +1352,12 @@ extern "C" apic_status apic_sort_keys_noalloc(const uint32_t* keys, int64_t n, i
     if (n > kNoAllocMaxKeys) return APIC_ERR_OOM;
     if (n == 0) return APIC_OK;
     if (!keys || !sorted_keys || !perm) return APIC_ERR_ARG;
+    // a pass reads keys while other CTAs already write its output: the buffers must be apart
+    if (overlaps(keys, sorted_keys, n) || overlaps(keys, perm, n) || overlaps(sorted_keys, perm, n))
+        return APIC_ERR_ARG;
+    // an error left pending by earlier work on this thread is not this call's: leave it
+    // in place for its owner and launch nothing
+    if (cudaPeekAtLastError() != cudaSuccess) return APIC_ERR_CUDA;
     uint32_t* scratch = nullptr;
     if (noalloc_scratch(&scratch) != cudaSuccess) return APIC_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1360,10 +1376,12 @@ extern "C" apic_status apic_sort_keys_noalloc(const uint32_t* keys, int64_t n, i
         uint32_t* vout = to_out ? perm : tmp_vals;
         const int shift = 8 * p;
         k_radix_hist<<<nt, RT, 0, s>>>(kin, n, shift, nt, counts);
+        if (cudaGetLastError() != cudaSuccess) return APIC_ERR_CUDA;
         if (exclusive_scan(counts, counts, 256 * (int64_t)nt, part, nullptr, s) != cudaSuccess) return APIC_ERR_CUDA;
         k_radix_scatter<<<nt, RT, 0, s>>>(kin, vin, kout, vout, n, shift, nt, counts);
+        if (cudaGetLastError() != cudaSuccess) return APIC_ERR_CUDA;
         kin = kout;
         vin = vout;
     }
-    return cudaGetLastError() == cudaSuccess ? APIC_OK : APIC_ERR_CUDA;
+    return APIC_OK;
 }

@@ -1,7 +1,8 @@
 // apic_transfer.cuh -- the per-step kernels of the APIC / explicit MPM method
 // (arXiv:1603.06188), templated on dimension D, B-spline order and real type R:
 //   k_keys         cell keys of the current particle order
-//   k_p2g          Sec. 3.2 transfer to grid + Sec. 3.3 force, shared-memory tile per node block
+//   k_p2g_cells    Sec. 3.2 transfer to grid + Sec. 3.3 force, per-cell register sums and a
+//                  deterministic gather per node block
 //   k_grid_update  Sec. 3.3 explicit (lambda = 0) grid update
 //   k_g2p          Sec. 3.4 transfer to particles (lambda = 0 form of Sec. 5.7), grid blocks
 //                  staged in shared memory by bulk asynchronous copies (TMA engine)
@@ -47,6 +48,7 @@ template <typename R> struct HostToDev {
         c.smax = nullptr;
         c.cfl_coef = (R)(6.0 * sqrt((double)h.dim) / h.dx);
         c.flip_alpha = (R)h.flip_alpha;
+        c.wait_limit = h.wait_limit;
         return c;
     }
     // the per-simulation words of adaptive stepping: the time step and the fused speed
@@ -138,176 +140,6 @@ __global__ void __launch_bounds__(TPB) k_keys(PState<R> st, DevCfg<R> c, uint32_
     Particle<D, R> p;
     load_x<D, R>(st, k, p);
     keys[k] = key_of<D, ORDER, R>(p.o, p.cell, c, err);
-}
-
-// ---------------------------------------------------------------- P2G (Sec. 3.2, 3.3)
-// One CTA walks tiles (a run of sorted particles of one node block).  Each particle's
-// contributions to its (ORDER+1)^D stencil nodes are first summed over the run of lanes
-// that share the same stencil base node (a segmented shuffle reduction; the sort makes
-// such lanes adjacent), then the run's head adds them into a shared-memory tile of
-// (4+ORDER)^D nodes; the tile is added to the global grid once.
-//   mass:     w m_p
-//   momentum: w m_p (v_p + B_p D_p^{-1} (x_i - x_p)) - dt V_p P F^T grad w
-template <int D, int ORDER, typename R>
-__global__ void __launch_bounds__(TPB) k_p2g(PState<R> st, const uint32_t* __restrict__ perm,
-                                             const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ tiles,
-                                             const uint32_t* __restrict__ ntiles_p, R* __restrict__ acc,
-                                             uint32_t* __restrict__ flags, DevCfg<R> c, uint32_t* err,
-                                             uint32_t* fallbacks)
-{
-    constexpr int K = ORDER + 1;
-    constexpr int TE = 4 + ORDER;
-    constexpr int TN = (D == 3) ? TE * TE * TE : TE * TE;
-    constexpr int NS = (D == 3) ? K * K * K : K * K;
-    constexpr int NV = D + 1;   // momentum lanes + mass
-    __shared__ R sm[NV][TN];
-    const int lane = threadIdx.x & 31;
-    const int ntiles = (int)*ntiles_p;
-    const R dt_dx = step_dt(c) * c.inv_dx;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        for (int i = threadIdx.x; i < NV * TN; i += TPB) (&sm[0][0])[i] = R(0);
-        const uint32_t start = tiles[t], end = tiles[t + 1];
-        const uint32_t blk = skeys[start] >> (2 * D);
-        int bo[3] = {0, 0, 0};
-        block_coords<D, R>(blk, c, bo);
-#pragma unroll
-        for (int a = 0; a < D; ++a) bo[a] *= 4;
-        __syncthreads();
-        for (uint32_t k0 = start; k0 < end; k0 += TPB) {
-            const uint32_t k = k0 + threadIdx.x;
-            bool ok = k < end;
-            uint32_t key = ok ? skeys[k] : FULLMASK;
-            R w[D][K], dw[D][K], fx[D];
-            int lb[D];
-            R mv[D], mC[D * D], T[D * D];
-            const R m = c.mass;
-            if (ok) {
-                Particle<D, R> p;
-                const uint32_t q = perm[k];
-                load_x<D, R>(st, q, p);
-                load_vB<D, R>(st, q, p);
-                if (c.model != 0) load_tau<D, R>(st, q, p);
-                int base[D];
-                if (!particle_stencil<D, ORDER, R>(p.o, p.cell, c, base, fx, w, dw)) set_err(err, APIC_ERRBIT_RANGE);
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    lb[a] = base[a] - bo[a];
-                    if (lb[a] < 0 || lb[a] > 3) ok = false;
-                }
-                if (!ok) set_err(err, APIC_ERRBIT_RANGE);
-#pragma unroll
-                for (int a = 0; a < D; ++a) mv[a] = m * p.v[a];
-                const R s = (c.transfer == 0) ? m * c.inv_kdx : R(0);
-#pragma unroll
-                for (int i = 0; i < D * D; ++i) mC[i] = s * p.B[i];
-                if (c.model != 0) {
-                    R tau[D * D];
-                    tau_full<D, R>(p.tau, tau);
-#pragma unroll
-                    for (int i = 0; i < D * D; ++i) T[i] = dt_dx * tau[i];
-                } else {
-#pragma unroll
-                    for (int i = 0; i < D * D; ++i) T[i] = R(0);
-                }
-            }
-            if (!ok) {
-                key = FULLMASK;
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    lb[a] = 0;
-                    fx[a] = R(0);
-                    mv[a] = R(0);
-#pragma unroll
-                    for (int j = 0; j < K; ++j) { w[a][j] = R(0); dw[a][j] = R(0); }
-                }
-#pragma unroll
-                for (int i = 0; i < D * D; ++i) { mC[i] = R(0); T[i] = R(0); }
-            }
-            // segments of lanes with equal keys (= equal stencil base node)
-            const uint32_t prev = __shfl_up_sync(FULLMASK, key, 1);
-            const bool head = (lane == 0) || (key != prev);
-            const uint32_t H = __ballot_sync(FULLMASK, head);
-            const uint32_t after = (lane == 31) ? 0u : (H & (FULLMASK << (lane + 1)));
-            const int seg_end = after ? (__ffs(after) - 1) : 32;
-            int lbase = lb[0] + TE * lb[1];
-            if (D == 3) lbase += TE * TE * lb[2];
-#pragma unroll
-            for (int j = 0; j < NS; ++j) {
-                const int ia = j % K, ib = (j / K) % K, ic = j / (K * K);
-                R wv, g[D], r[D];
-                if (D == 3) {
-                    const R wab = w[0][ia] * w[1][ib];
-                    wv = wab * w[2][ic];
-                    g[0] = dw[0][ia] * w[1][ib] * w[2][ic];
-                    g[1] = w[0][ia] * dw[1][ib] * w[2][ic];
-                    g[2] = wab * dw[2][ic];
-                    r[2] = R(ic) - fx[2];
-                } else {
-                    wv = w[0][ia] * w[1][ib];
-                    g[0] = dw[0][ia] * w[1][ib];
-                    g[1] = w[0][ia] * dw[1][ib];
-                }
-                r[0] = R(ia) - fx[0];
-                r[1] = R(ib) - fx[1];
-                R val[NV];
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    R q = mv[a];
-                    R f = R(0);
-#pragma unroll
-                    for (int b = 0; b < D; ++b) {
-                        q += mC[a * D + b] * r[b];
-                        f += T[a * D + b] * g[b];
-                    }
-                    val[a] = wv * q - f;
-                }
-                val[D] = wv * m;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) {
-                        const R other = __shfl_down_sync(FULLMASK, val[v], o);
-                        if (lane + o < seg_end) val[v] += other;
-                    }
-                }
-                if (head && ok) {
-                    const int li = lbase + ia + TE * ib + (D == 3 ? TE * TE * ic : 0);
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) atomicAdd(&sm[v][li], val[v]);
-                }
-            }
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < TN; i += TPB) {
-            const R mm = sm[D][i];
-            if (mm == R(0)) continue;
-            int g[3];
-            g[0] = bo[0] + i % TE;
-            g[1] = bo[1] + (i / TE) % TE;
-            if (D == 3) g[2] = bo[2] + i / (TE * TE);
-            const uint32_t ni = node_index<D>(g, c.nb);
-            R* dst = acc + 4 * (size_t)ni;
-#pragma unroll
-            for (int a = 0; a < D; ++a) atomicAdd(dst + a, sm[a][i]);
-            atomicAdd(dst + 3, mm);
-        }
-        if (threadIdx.x < (1 << D)) {
-            int bb[3];
-            block_coords<D, R>(blk, c, bb);
-            bool in = true;
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                bb[a] += (threadIdx.x >> a) & 1;
-                if (bb[a] >= c.nb[a]) in = false;
-            }
-            if (in) {
-                const uint32_t b2 = (D == 3) ? ((uint32_t)bb[2] * c.nb[1] + bb[1]) * c.nb[0] + bb[0]
-                                             : (uint32_t)bb[1] * c.nb[0] + bb[0];
-                flags[b2] = 1u;
-            }
-        }
-        __syncthreads();
-    }
 }
 
 // ---------------------------------------------------------------- asynchronous particle staging
@@ -831,399 +663,6 @@ __global__ void __launch_bounds__(128, 2) k_p2g_cells(PState<R> st, const uint32
 }
 
 
-// ---------------------------------------------------------------- P2G, node-split
-// The ORDER+1 lanes of a group take the same cell and walk the same particles (each particle
-// read once into shared memory by the group); lane r owns the x-plane ia = r of the stencil,
-// (ORDER+1)^(D-1) nodes, and sums its nodes' contributions in registers.  No lane holds the
-// whole stencil, so a lane needs a third (quadratic) of the accumulators of the
-// cell-parallel form and no reduce-scatter; more warps fit on an SM.  The per-particle set-up
-// (weights, the separable terms) is repeated by the group's lanes.  Cell loop, neutral
-// particles and the node gather as in the cell-parallel form.
-template <typename R> __host__ __device__ constexpr int split_slots() { return 4; }
-template <int D, int ORDER> __host__ __device__ constexpr int split_groups() { return 32 / (ORDER + 1); }
-template <int D, int ORDER, typename R> __host__ __device__ constexpr size_t p2g_split_smem()
-{
-    return (p2g_cellsum_bytes<D, ORDER, R>() + 31) / 32 * 32 +
-           (size_t)4 * split_groups<D, ORDER>() * split_slots<R>() * slot_words<D>() * sizeof(R);
-}
-
-// lane r of a group copies the 16-byte pieces c of particle q with c % G == r
-template <int D, typename R, int G>
-__device__ __forceinline__ void stage_particle_split(R* slot, const PState<R>& s, uint32_t q, int r, bool with_tau)
-{
-    if (D == 3) {
-        if (0 % G == r) cp_group4<R>(slot + 0, s.A + q);
-        if (1 % G == r) cp_group4<R>(slot + 4, s.V + q);
-        if (2 % G == r) cp_group4<R>(slot + 8, s.Ba + q);
-        if (3 % G == r) cp_group4<R>(slot + 12, s.Bb + q);
-        if (with_tau) {
-            if (4 % G == r) cp_group4<R>(slot + 16, s.Ta + q);
-            if (5 % G == r) cp_group2<R>(slot + 20, s.Tb + q);
-        }
-    } else {
-        if (0 % G == r) cp_group4<R>(slot + 0, s.A + q);
-        if (1 % G == r) cp_group4<R>(slot + 4, s.V + q);
-        if (2 % G == r) cp_group4<R>(slot + 8, s.Ba + q);
-        if (with_tau && 3 % G == r) cp_group2<R>(slot + 12, s.Tb + q);
-    }
-}
-
-template <int D, int ORDER, typename R>
-__device__ __forceinline__ void p2g_split_tile(const PState<R>& st, const uint32_t* __restrict__ perm,
-                                               const uint32_t* __restrict__ skeys, uint32_t start, uint32_t end,
-                                               R* __restrict__ acc, uint32_t* __restrict__ flags, const DevCfg<R>& c,
-                                               uint32_t* err, R* cellsum, uint32_t* cbeg, uint32_t* cend, int* s_cell,
-                                               R* pring)
-{
-    constexpr int NT = 128;
-    constexpr int K = ORDER + 1;
-    constexpr int G = K;
-    constexpr int GPW = split_groups<D, ORDER>();
-    constexpr int NS = (D == 3) ? K * K * K : K * K;
-    constexpr int NV = D + 1;
-    constexpr int NVAL = NS * NV;
-    constexpr int NC = (D == 3) ? 64 : 16;
-    constexpr int NPL = NS / K;             // nodes of a lane's plane
-    constexpr int NSL = split_slots<R>();
-    constexpr int SW = slot_words<D>();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gw = lane / G, r = lane % G;
-    const R dt_dx = step_dt(c) * c.inv_dx;
-    const R m = c.mass;
-    const R sC = (c.transfer == 0) ? m * c.inv_kdx : R(0);
-    const bool with_tau = c.model != 0;
-    const uint32_t blk = skeys[start] >> (2 * D);
-    int bo[3] = {0, 0, 0};
-    block_coords<D, R>(blk, c, bo);
-#pragma unroll
-    for (int a = 0; a < D; ++a) bo[a] *= 4;
-    tile_cell_runs<D>(skeys, start, end, cbeg, cend, NT);
-    __syncthreads();
-    // lanes past GPW * G have no group: they follow the loop with empty cells
-    R* ring = pring + (size_t)(warp * GPW + (gw < GPW ? gw : 0)) * NSL * SW;
-    for (;;) {
-        int cb = 0;
-        if (lane == 0) cb = atomicAdd(s_cell, GPW);
-        cb = __shfl_sync(FULLMASK, cb, 0);
-        if (cb >= NC) break;
-        const int cell = cb + gw;
-        const bool has = gw < GPW && cell < NC;
-        const uint32_t kb = has ? cbeg[cell] : 0u, ke = has ? cend[cell] : 0u;
-        const uint32_t cnt = ke > kb ? ke - kb : 0u;
-        const int lb[3] = {cell & 3, (cell >> 2) & 3, (D == 3) ? ((cell >> 4) & 3) : 0};
-        const uint32_t iters = __reduce_max_sync(FULLMASK, cnt);
-        if (iters == 0u) continue;
-        R sum[NPL * NV];
-#pragma unroll
-        for (int i = 0; i < NPL * NV; ++i) sum[i] = R(0);
-#pragma unroll
-        for (int i = 0; i < NSL; ++i) {
-            if ((uint32_t)i < cnt) stage_particle_split<D, R, G>(ring + i * SW, st, perm[kb + i], r, with_tau);
-            cp_async_commit();
-        }
-#pragma unroll 1
-        for (uint32_t it = 0; it < iters; ++it) {
-            bool live = it < cnt;
-            cp_async_wait<NSL - 1>();
-            __syncwarp();                      // the group's pieces of this particle have landed
-            R* slot = ring + (it % NSL) * SW;
-            Particle<D, R> p;
-            read_staged<D, R>(slot, p, with_tau);
-            __syncwarp();                      // every lane has read the slot before it is refilled
-            {
-                const uint32_t kn = it + NSL;
-                if (kn < cnt) stage_particle_split<D, R, G>(slot, st, perm[kb + kn], r, with_tau);
-                cp_async_commit();
-            }
-            if (!live) {   // neutral: an in-cell position and zero state (finite weights, zero sums)
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    p.o[a] = R(0.5);
-                    p.cell[a] = bo[a] + lb[a] + (ORDER == 3 ? 1 : 0);
-                    p.v[a] = R(0);
-                }
-#pragma unroll
-                for (int i = 0; i < D * D; ++i) p.B[i] = R(0);
-#pragma unroll
-                for (int i = 0; i < ((D == 3) ? 6 : 3); ++i) p.tau[i] = R(0);
-            }
-            int base[D];
-            R w[D][K], dw[D][K], fx[D];
-            bool ok = particle_stencil<D, ORDER, R>(p.o, p.cell, c, base, fx, w, dw);
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-                if (base[a] - bo[a] != lb[a]) ok = false;
-            if (live && !ok) {
-                if (r == 0) set_err(err, APIC_ERRBIT_RANGE);
-                live = false;
-            }
-            const R ml = live ? m : R(0);
-            R mv[D], mC[D * D], T[D * D];
-#pragma unroll
-            for (int a = 0; a < D; ++a) mv[a] = ml * p.v[a];
-#pragma unroll
-            for (int i = 0; i < D * D; ++i) mC[i] = (live ? sC : R(0)) * p.B[i];
-            if (with_tau) {
-                R tau[D * D];
-                tau_full<D, R>(p.tau, tau);
-#pragma unroll
-                for (int i = 0; i < D * D; ++i) T[i] = (live ? dt_dx : R(0)) * tau[i];
-            } else {
-#pragma unroll
-                for (int i = 0; i < D * D; ++i) T[i] = R(0);
-            }
-            // this lane's plane ia = r (separable terms as in the cell-parallel form)
-            R w0 = w[0][0], dw0 = dw[0][0];
-#pragma unroll
-            for (int i = 1; i < K; ++i)
-                if (r == i) { w0 = w[0][i]; dw0 = dw[0][i]; }
-            const R rw0 = (R(r) - fx[0]) * w0;
-            R E[D];
-#pragma unroll
-            for (int cc = 0; cc < D; ++cc) E[cc] = mC[cc * D + 0] * rw0 - T[cc * D + 0] * dw0;
-            if (D == 3) {
-                R H[3][K];
-#pragma unroll
-                for (int i = 0; i < K; ++i) {
-                    const R rw1 = (R(i) - fx[1]) * w[1][i];
-#pragma unroll
-                    for (int cc = 0; cc < 3; ++cc) H[cc][i] = mC[cc * 3 + 1] * rw1 - T[cc * 3 + 1] * dw[1][i];
-                }
-#pragma unroll
-                for (int ic = 0; ic < K; ++ic) {
-                    const R w2 = w[2][ic], dw2 = dw[2][ic], rw2 = (R(ic) - fx[2]) * w2;
-                    R Q[3];
-#pragma unroll
-                    for (int cc = 0; cc < 3; ++cc) Q[cc] = mv[cc] * w2 + mC[cc * 3 + 2] * rw2 - T[cc * 3 + 2] * dw2;
-#pragma unroll
-                    for (int ib = 0; ib < K; ++ib) {
-                        const R S = w[1][ib] * w2;
-                        const int q = ib + K * ic;
-#pragma unroll
-                        for (int cc = 0; cc < 3; ++cc)
-                            sum[q * NV + cc] += w0 * (w[1][ib] * Q[cc] + H[cc][ib] * w2) + E[cc] * S;
-                        sum[q * NV + 3] += w0 * ml * S;
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int ib = 0; ib < K; ++ib) {
-                    const R w1 = w[1][ib], rw1 = (R(ib) - fx[1]) * w1;
-#pragma unroll
-                    for (int cc = 0; cc < 2; ++cc) {
-                        const R Q = mv[cc] * w1 + mC[cc * 2 + 1] * rw1 - T[cc * 2 + 1] * dw[1][ib];
-                        sum[ib * NV + cc] += w0 * Q + E[cc] * w1;
-                    }
-                    sum[ib * NV + 2] += w0 * ml * w1;
-                }
-            }
-        }
-        cp_async_wait<0>();
-        if (has) {
-            // node j = r + K q of the cell's stencil
-#pragma unroll
-            for (int q = 0; q < NPL; ++q)
-#pragma unroll
-                for (int v = 0; v < NV; ++v) cellsum[(size_t)cell * NVAL + (r + K * q) * NV + v] = sum[q * NV + v];
-        }
-        __syncwarp();
-    }
-    __syncthreads();
-    tile_flush<D, ORDER, R>(cellsum, cbeg, cend, bo, blk, acc, flags, c, NT);
-    __syncthreads();
-}
-
-template <int D, int ORDER, typename R>
-__global__ void __launch_bounds__(128, 4) k_p2g_split(PState<R> st, const uint32_t* __restrict__ perm,
-                                                      const uint32_t* __restrict__ skeys,
-                                                      const uint32_t* __restrict__ tiles,
-                                                      const uint32_t* __restrict__ ntiles_p,
-                                                      uint32_t* __restrict__ tile_ctr, R* __restrict__ acc,
-                                                      uint32_t* __restrict__ flags, DevCfg<R> c, uint32_t* err)
-{
-    constexpr int NC = (D == 3) ? 64 : 16;
-    extern __shared__ __align__(32) unsigned char p2g_smem[];
-    R* cellsum = reinterpret_cast<R*>(p2g_smem);
-    R* pring = reinterpret_cast<R*>(p2g_smem + (p2g_cellsum_bytes<D, ORDER, R>() + 31) / 32 * 32);
-    __shared__ uint32_t cbeg[NC], cend[NC];
-    __shared__ int s_tile, s_cell;
-    const int ntiles = (int)*ntiles_p;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            s_tile = (int)atomicAdd(tile_ctr, 1u);
-            s_cell = 0;
-        }
-        for (int i = threadIdx.x; i < NC; i += 128) { cbeg[i] = 0u; cend[i] = 0u; }
-        __syncthreads();
-        const int t = s_tile;
-        if (t >= ntiles) break;
-        p2g_split_tile<D, ORDER, R>(st, perm, skeys, tiles[t], tiles[t + 1], acc, flags, c, err, cellsum, cbeg, cend,
-                                    &s_cell, pring);
-    }
-}
-
-
-// ---------------------------------------------------------------- P2G, cell-interleaved
-// Threads of a warp take particles of distinct base cells of the tile (thread t serves
-// cell t mod 4^D), so at every stencil node the lanes of a warp add into distinct
-// shared-memory nodes and the shared-memory atomics do not collide; no shuffle
-// reduction is needed.  Contributions as in k_p2g.
-template <int D, int ORDER, typename R>
-__global__ void __launch_bounds__(256) k_p2g_interleaved(PState<R> st, const uint32_t* __restrict__ perm,
-                                                         const uint32_t* __restrict__ skeys,
-                                                         const uint32_t* __restrict__ tiles,
-                                                         const uint32_t* __restrict__ ntiles_p,
-                                                         uint32_t* __restrict__ tile_ctr, R* __restrict__ acc,
-                                                         uint32_t* __restrict__ flags, DevCfg<R> c, uint32_t* err,
-                                                         uint32_t* fallbacks)
-{
-    constexpr int NT = 256;
-    constexpr int K = ORDER + 1;
-    constexpr int TE = 4 + ORDER;
-    constexpr int TN = (D == 3) ? TE * TE * TE : TE * TE;
-    constexpr int NV = D + 1;
-    constexpr int NC = (D == 3) ? 64 : 16;
-    constexpr int SLOTS = NT / NC;
-    __shared__ R sm[NV][TN];
-    __shared__ uint32_t cbeg[NC], cend[NC];
-    __shared__ int s_tile;
-    const int ntiles = (int)*ntiles_p;
-    const R dt_dx = step_dt(c) * c.inv_dx;
-    const R m = c.mass;
-    const R sC = (c.transfer == 0) ? m * c.inv_kdx : R(0);
-    const int cell = threadIdx.x % NC, slot = threadIdx.x / NC;
-    const int lb[3] = {cell & 3, (cell >> 2) & 3, (D == 3) ? (cell >> 4) : 0};
-    const int lbase = lb[0] + TE * lb[1] + (D == 3 ? TE * TE * lb[2] : 0);
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_ctr, 1u);
-        for (int i = threadIdx.x; i < NV * TN; i += NT) (&sm[0][0])[i] = R(0);
-        for (int i = threadIdx.x; i < NC; i += NT) { cbeg[i] = 0u; cend[i] = 0u; }
-        __syncthreads();
-        const int t = s_tile;
-        if (t >= ntiles) break;
-        const uint32_t start = tiles[t], end = tiles[t + 1];
-        const uint32_t blk = skeys[start] >> (2 * D);
-        int bo[3] = {0, 0, 0};
-        block_coords<D, R>(blk, c, bo);
-#pragma unroll
-        for (int a = 0; a < D; ++a) bo[a] *= 4;
-        for (uint32_t k = start + threadIdx.x; k < end; k += NT) {
-            const uint32_t cl = skeys[k] & (NC - 1);
-            if (k == start || (skeys[k - 1] & (NC - 1)) != cl) cbeg[cl] = k;
-            if (k + 1 == end || (skeys[k + 1] & (NC - 1)) != cl) cend[cl] = k + 1;
-        }
-        __syncthreads();
-        const uint32_t kb = cbeg[cell], ke = cend[cell];
-        for (uint32_t k = kb + slot; k < ke; k += SLOTS) {
-            Particle<D, R> p;
-            const uint32_t q = perm[k];
-            load_x<D, R>(st, q, p);
-            load_vB<D, R>(st, q, p);
-            if (c.model != 0) load_tau<D, R>(st, q, p);
-            int base[D];
-            R w[D][K], dw[D][K], fx[D];
-            bool ok = particle_stencil<D, ORDER, R>(p.o, p.cell, c, base, fx, w, dw);
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-                if (base[a] - bo[a] != lb[a]) ok = false;
-            if (!ok) {
-                set_err(err, APIC_ERRBIT_RANGE);
-                continue;
-            }
-            R mv[D], mC[D * D], T[D * D];
-#pragma unroll
-            for (int a = 0; a < D; ++a) mv[a] = m * p.v[a];
-#pragma unroll
-            for (int i = 0; i < D * D; ++i) mC[i] = sC * p.B[i];
-            if (c.model != 0) {
-                R tau[D * D];
-                tau_full<D, R>(p.tau, tau);
-#pragma unroll
-                for (int i = 0; i < D * D; ++i) T[i] = dt_dx * tau[i];
-            } else {
-#pragma unroll
-                for (int i = 0; i < D * D; ++i) T[i] = R(0);
-            }
-            if (D == 3) {
-                // per (a, b): q_ab = m v + mC (r0, r1, .), h = T (gx, gy, .), kz = T(., ., 2) w_ab
-#pragma unroll
-                for (int ia = 0; ia < K; ++ia)
-#pragma unroll
-                    for (int ib = 0; ib < K; ++ib) {
-                        const R wab = w[0][ia] * w[1][ib];
-                        const R gx = dw[0][ia] * w[1][ib], gy = w[0][ia] * dw[1][ib];
-                        const R r0 = R(ia) - fx[0], r1 = R(ib) - fx[1];
-                        R qab[3], h[3], kz[3];
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            qab[a] = mv[a] + mC[a * 3 + 0] * r0 + mC[a * 3 + 1] * r1;
-                            h[a] = T[a * 3 + 0] * gx + T[a * 3 + 1] * gy;
-                            kz[a] = T[a * 3 + 2] * wab;
-                        }
-#pragma unroll
-                        for (int ic = 0; ic < K; ++ic) {
-                            const R wz = w[2][ic], dwz = dw[2][ic], r2 = R(ic) - fx[2];
-                            const R wv = wab * wz;
-                            const int li = lbase + ia + TE * ib + TE * TE * ic;
-#pragma unroll
-                            for (int a = 0; a < 3; ++a) {
-                                const R qv = qab[a] + mC[a * 3 + 2] * r2;
-                                atomicAdd(&sm[a][li], wv * qv - h[a] * wz - kz[a] * dwz);
-                            }
-                            atomicAdd(&sm[3][li], wv * m);
-                        }
-                    }
-            } else {
-#pragma unroll
-                for (int ia = 0; ia < K; ++ia)
-#pragma unroll
-                    for (int ib = 0; ib < K; ++ib) {
-                        const R wv = w[0][ia] * w[1][ib];
-                        const R g0 = dw[0][ia] * w[1][ib], g1 = w[0][ia] * dw[1][ib];
-                        const R r0 = R(ia) - fx[0], r1 = R(ib) - fx[1];
-                        const int li = lbase + ia + TE * ib;
-#pragma unroll
-                        for (int a = 0; a < 2; ++a) {
-                            const R qv = mv[a] + mC[a * 2 + 0] * r0 + mC[a * 2 + 1] * r1;
-                            atomicAdd(&sm[a][li], wv * qv - (T[a * 2 + 0] * g0 + T[a * 2 + 1] * g1));
-                        }
-                        atomicAdd(&sm[2][li], wv * m);
-                    }
-            }
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < TN; i += NT) {
-            const R mm = sm[D][i];
-            if (mm == R(0)) continue;
-            int g[3];
-            g[0] = bo[0] + i % TE;
-            g[1] = bo[1] + (i / TE) % TE;
-            if (D == 3) g[2] = bo[2] + i / (TE * TE);
-            const uint32_t ni = node_index<D>(g, c.nb);
-            R* dst = acc + 4 * (size_t)ni;
-#pragma unroll
-            for (int a = 0; a < D; ++a) atomicAdd(dst + a, sm[a][i]);
-            atomicAdd(dst + 3, mm);
-        }
-        if (threadIdx.x < (1 << D)) {
-            int bb[3];
-            block_coords<D, R>(blk, c, bb);
-            bool in = true;
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                bb[a] += (threadIdx.x >> a) & 1;
-                if (bb[a] >= c.nb[a]) in = false;
-            }
-            if (in) {
-                const uint32_t b2 = (D == 3) ? ((uint32_t)bb[2] * c.nb[1] + bb[1]) * c.nb[0] + bb[0]
-                                             : (uint32_t)bb[1] * c.nb[0] + bb[0];
-                flags[b2] = 1u;
-            }
-        }
-        __syncthreads();
-    }
-}
-
 // ---------------------------------------------------------------- grid update (Sec. 3.3)
 // One warp per active node block: v~ = ((m v) + dt f) / m + dt g, sticky walls, v~ = 0 where
 // m = 0; writes (v~, m) to the velocity grid and clears the accumulation grid and flag.
@@ -1378,10 +817,11 @@ __device__ __forceinline__ void g2p_issue(const R* __restrict__ vel, uint32_t bl
     }
 }
 
-// thread 0: wait (bounded) for a buffer's copies; false on timeout
-__device__ __forceinline__ bool g2p_wait(uint64_t* mbar, unsigned parity, uint32_t* err)
+// thread 0: wait (at most `limit` polls) for a buffer's copies; false on timeout, after a
+// second bounded wait that lets the copies in flight land before the CTA leaves
+__device__ __forceinline__ bool g2p_wait(uint64_t* mbar, unsigned parity, uint32_t* err, unsigned limit)
 {
-    if (mbar_wait_bounded(mbar, parity, 1u << 22)) return true;
+    if (mbar_wait_bounded(mbar, parity, limit)) return true;
     set_err(err, APIC_ERRBIT_TIMEOUT);
     mbar_wait_bounded(mbar, parity, 1u << 22);   // let the copies in flight land before leaving
     return false;
@@ -1672,7 +1112,7 @@ __global__ void __launch_bounds__(G2P_THREADS, 4) k_g2p(PState<R> in, PState<R> 
             const int t1 = (int)atomicAdd(tile_ctr + 1, 1u);
             s_t[buf ^ 1] = t1;
             if (t1 < ntiles) g2p_issue<D, R>(vel, skeys[tiles[t1]] >> (2 * D), c.nb, sv[buf ^ 1], &mbar[buf ^ 1]);
-            const bool ok = g2p_wait(&mbar[buf], phase[buf], err);
+            const bool ok = g2p_wait(&mbar[buf], phase[buf], err, c.wait_limit);
             if (!ok && t1 < ntiles) mbar_wait_bounded(&mbar[buf ^ 1], phase[buf ^ 1], 1u << 22);   // drain before leaving
             s_ok = ok ? 1 : 0;
         }
@@ -1721,36 +1161,35 @@ template <int D, typename R>
 __global__ void __launch_bounds__(TPB) k_mom_particles(PState<R> st, DevCfg<R> c, double mass, double dx,
                                                        double o0, double o1, double o2, double* part)
 {
-    // each particle's terms in the state's precision (FP64 arithmetic is slow on this part
-    // and adds nothing to FP32 state), their sums in FP64
+    // every particle's terms in FP64 from its state widened exactly (the position as
+    // origin + (cell + offset) dx, so the offset keeps its full precision), sums in FP64
     double a[6] = {0, 0, 0, 0, 0, 0};
-    const R org[3] = {(R)o0, (R)o1, (R)o2};
-    const R ms = (R)mass, h = (R)dx;
+    const double org[3] = {o0, o1, o2};
     for (int k = blockIdx.x * TPB + threadIdx.x; k < c.n; k += gridDim.x * TPB) {
         Particle<D, R> p;
         load_x<D, R>(st, k, p);
         load_vB<D, R>(st, k, p);
-        R x[3] = {R(0), R(0), R(0)}, v[3] = {R(0), R(0), R(0)};
+        double x[3] = {0.0, 0.0, 0.0}, v[3] = {0.0, 0.0, 0.0};
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-            x[d] = org[d] + ((R)p.cell[d] + p.o[d]) * h;
-            v[d] = ms * p.v[d];
-            a[d] += (double)v[d];
+            x[d] = org[d] + ((double)p.cell[d] + (double)p.o[d]) * dx;
+            v[d] = mass * (double)p.v[d];
+            a[d] += v[d];
         }
         if (D == 3) {
-            R l[3] = {x[1] * v[2] - x[2] * v[1], x[2] * v[0] - x[0] * v[2], x[0] * v[1] - x[1] * v[0]};
-            if (c.transfer == 0) {
-                l[0] += ms * (p.B[7] - p.B[5]);
-                l[1] += ms * (p.B[2] - p.B[6]);
-                l[2] += ms * (p.B[3] - p.B[1]);
+            double l[3] = {x[1] * v[2] - x[2] * v[1], x[2] * v[0] - x[0] * v[2], x[0] * v[1] - x[1] * v[0]};
+            if (c.transfer == 0) {   // m_p (B_p)^T : eps of Sec. 5.3
+                l[0] += mass * ((double)p.B[7] - (double)p.B[5]);
+                l[1] += mass * ((double)p.B[2] - (double)p.B[6]);
+                l[2] += mass * ((double)p.B[3] - (double)p.B[1]);
             }
-            a[3] += (double)l[0];
-            a[4] += (double)l[1];
-            a[5] += (double)l[2];
+            a[3] += l[0];
+            a[4] += l[1];
+            a[5] += l[2];
         } else {
-            R l = x[0] * v[1] - x[1] * v[0];
-            if (c.transfer == 0) l += ms * (p.B[2] - p.B[1]);
-            a[3] += (double)l;
+            double l = x[0] * v[1] - x[1] * v[0];
+            if (c.transfer == 0) l += mass * ((double)p.B[2] - (double)p.B[1]);
+            a[3] += l;
         }
     }
     block_sum6(a, part);
@@ -1863,9 +1302,28 @@ __global__ void __launch_bounds__(TPB) k_upload(PState<R> st, DevCfg<R> c, doubl
     const double org[3] = {o0, o1, o2};
     Particle<D, R> p;
     p.id = (uint32_t)k;
+    // a non-finite input value is reported (the particle is stored with zeros in its place)
+    bool finite = true;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        const double u = (x[(size_t)k * D + a] - org[a]) / dx;
+        finite &= isfinite(x[(size_t)k * D + a]);
+        if (v) finite &= isfinite(v[(size_t)k * D + a]);
+    }
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) {
+        if (B) finite &= isfinite(B[(size_t)k * D * D + i]);
+        if (F) finite &= isfinite(F[(size_t)k * D * D + i]);
+    }
+    if (!finite) {
+        set_err(err, APIC_ERRBIT_NONFINITE);
+        x = nullptr;
+        v = nullptr;
+        B = nullptr;
+        F = nullptr;
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const double u = x ? (x[(size_t)k * D + a] - org[a]) / dx : 0.0;
         double cl = floor(u);
         R o = (R)(u - cl);
         if (o >= R(1)) { o = R(0); cl += 1.0; }
@@ -1892,13 +1350,18 @@ __global__ void __launch_bounds__(TPB) k_upload(PState<R> st, DevCfg<R> c, doubl
 // stored in lane M of the particle wherever it now sits, and its stress recomputed
 template <int D, typename R>
 __global__ void __launch_bounds__(TPB) k_set_materials(PState<R> st, DevCfg<R> c, const double* __restrict__ E,
-                                                       const double* __restrict__ nu, uint32_t* fallbacks)
+                                                       const double* __restrict__ nu, uint32_t* fallbacks,
+                                                       uint32_t* err)
 {
     const int k = blockIdx.x * TPB + threadIdx.x;
     if (k >= c.n) return;
     Particle<D, R> p;
     load_xF<D, R>(st, k, p);
     load_vB<D, R>(st, k, p);
+    if (p.id >= (uint32_t)c.n) {   // an id is an upload index; anything else is not valid state
+        set_err(err, APIC_ERRBIT_RANGE);
+        return;
+    }
     const double e = E[p.id], v = nu[p.id];
     p.mu = (R)(e / (2.0 * (1.0 + v)));
     p.lam = (R)(e * v / ((1.0 + v) * (1.0 - 2.0 * v)));
@@ -1924,7 +1387,7 @@ template <int D, typename R>
 __global__ void __launch_bounds__(TPB) k_download(PState<R> st, DevCfg<R> c, double dx, double o0, double o1, double o2,
                                                   double* __restrict__ x, double* __restrict__ v, double* __restrict__ B,
                                                   double* __restrict__ F, int32_t* __restrict__ cell,
-                                                  double* __restrict__ off)
+                                                  double* __restrict__ off, uint32_t* err)
 {
     const int k = blockIdx.x * TPB + threadIdx.x;
     if (k >= c.n) return;
@@ -1933,6 +1396,10 @@ __global__ void __launch_bounds__(TPB) k_download(PState<R> st, DevCfg<R> c, dou
     load_xF<D, R>(st, k, p);
     load_vB<D, R>(st, k, p);
     const size_t id = p.id;
+    if (id >= (size_t)c.n) {   // not valid state (e.g. a step whose G2P gave up): write nothing
+        set_err(err, APIC_ERRBIT_RANGE);
+        return;
+    }
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         if (x) x[id * D + a] = org[a] + ((double)p.cell[a] + (double)p.o[a]) * dx;
@@ -1993,16 +1460,7 @@ template <typename R> struct Impl {
         const DevCfg<R> c0 = HostToDev<R>::make(h, b, n);
         PState<R> st = state_of<R>(b, cur);
         auto launch = [&](const DevCfg<R>& c, R* acc) {
-        if (h.p2g_kernel == 4)
-            APIC_DISPATCH(h, (k_p2g_split<D, O, R><<<L.p2g_grid, 128, p2g_split_smem<D, O, R>(), s>>>(
-                                 st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc, b.flags, c, b.err)));
-        else if (h.p2g_kernel == 3)
-            APIC_DISPATCH(h, (k_p2g_interleaved<D, O, R><<<L.p2g_grid, 256, 0, s>>>(
-                                 st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc, b.flags, c, b.err, b.fallbacks)));
-        else if (!L.p2g_cells)
-            APIC_DISPATCH(h, (k_p2g<D, O, R><<<L.p2g_grid, TPB, 0, s>>>(st, perm, sk, b.tiles, b.ntiles, acc,
-                                                                          b.flags, c, b.err, b.fallbacks)));
-        else if (h.p2g_group == 2)
+        if (h.p2g_group == 2)
             APIC_DISPATCH(h, (k_p2g_cells<D, O, R, 2><<<L.p2g_grid, 128, p2g_cells_smem<D, O, R>(), s>>>(
                                  st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc, b.flags, c, b.err, b.fallbacks)));
         else
@@ -2055,8 +1513,8 @@ template <typename R> struct Impl {
         if (n == 0) return cudaSuccess;
         DevCfg<R> c = HostToDev<R>::make(h, n);
         PState<R> st = state_of<R>(b, cur);
-        if (h.dim == 3) k_set_materials<3, R><<<blocks_for(n), TPB, 0, s>>>(st, c, E, nu, b.fallbacks);
-        else k_set_materials<2, R><<<blocks_for(n), TPB, 0, s>>>(st, c, E, nu, b.fallbacks);
+        if (h.dim == 3) k_set_materials<3, R><<<blocks_for(n), TPB, 0, s>>>(st, c, E, nu, b.fallbacks, b.err);
+        else k_set_materials<2, R><<<blocks_for(n), TPB, 0, s>>>(st, c, E, nu, b.fallbacks, b.err);
         return cudaGetLastError();
     }
     static cudaError_t upload(const HostCfg& h, const Buffers& b, int cur, int64_t n, const double* x,
@@ -2078,9 +1536,9 @@ template <typename R> struct Impl {
         DevCfg<R> c = HostToDev<R>::make(h, n);
         PState<R> st = state_of<R>(b, cur);
         if (h.dim == 3)
-            k_download<3, R><<<blocks_for(n), TPB, 0, s>>>(st, c, h.dx, h.origin[0], h.origin[1], h.origin[2], x, v, B, F, cell, off);
+            k_download<3, R><<<blocks_for(n), TPB, 0, s>>>(st, c, h.dx, h.origin[0], h.origin[1], h.origin[2], x, v, B, F, cell, off, b.err);
         else
-            k_download<2, R><<<blocks_for(n), TPB, 0, s>>>(st, c, h.dx, h.origin[0], h.origin[1], h.origin[2], x, v, B, F, cell, off);
+            k_download<2, R><<<blocks_for(n), TPB, 0, s>>>(st, c, h.dx, h.origin[0], h.origin[1], h.origin[2], x, v, B, F, cell, off, b.err);
         return cudaGetLastError();
     }
     static cudaError_t momentum(const HostCfg& h, const Buffers& b, int cur, int64_t n, int where, int grid_phase,
@@ -2126,31 +1584,20 @@ template <typename R> struct Impl {
     {
         cudaError_t e = cudaSuccess;
         APIC_DISPATCH(h, {
-            if (h.p2g_kernel == 4) {
-                e = cudaFuncSetAttribute(k_p2g_split<D, O, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)p2g_split_smem<D, O, R>());
-                if (e == cudaSuccess)
-                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g_split<D, O, R>, 128,
-                                                                      p2g_split_smem<D, O, R>());
-            } else if (h.p2g_kernel == 3)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g_interleaved<D, O, R>, 256, 0);
-            else if (h.p2g_kernel != 2)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g<D, O, R>, TPB, 0);
-            else {
-                constexpr int O2 = O;
+            {
                 // both lane groups are set up: the group can change at the next upload
-                e = cudaFuncSetAttribute(k_p2g_cells<D, O2, R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)p2g_cells_smem<D, O2, R>());
+                e = cudaFuncSetAttribute(k_p2g_cells<D, O, R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)p2g_cells_smem<D, O, R>());
                 if (e == cudaSuccess)
-                    e = cudaFuncSetAttribute(k_p2g_cells<D, O2, R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)p2g_cells_smem<D, O2, R>());
+                    e = cudaFuncSetAttribute(k_p2g_cells<D, O, R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)p2g_cells_smem<D, O, R>());
                 int per2 = 0;
                 if (e == cudaSuccess)
-                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_p2g_cells<D, O2, R, 2>, 128,
-                                                                      p2g_cells_smem<D, O2, R>());
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_p2g_cells<D, O, R, 2>, 128,
+                                                                      p2g_cells_smem<D, O, R>());
                 if (e == cudaSuccess)
-                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g_cells<D, O2, R, 4>, 128,
-                                                                      p2g_cells_smem<D, O2, R>());
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g_cells<D, O, R, 4>, 128,
+                                                                      p2g_cells_smem<D, O, R>());
                 if (e == cudaSuccess && per2 < *p2g_per_sm) *p2g_per_sm = per2;
             }
             if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(g2p_per_sm, k_g2p<D, O, R, false>, G2P_THREADS, 0);

@@ -78,3 +78,56 @@ def occupancy_rule(keys: np.ndarray, dim: int, res) -> np.ndarray:
             mult *= nb[a]
         out[lin[ok]] = 1
     return out
+
+
+def nodewise_err(got, ref, mass) -> float:
+    """Largest error at any grid node relative to that node's own scale: |ref_i| or, where
+    larger, the node's share of the mass times the largest |ref| (so a node that holds 1 % of
+    the mass of the heaviest node gets a bound 100 times tighter than the normwise one).
+    Nodes with no mass and a zero reference must be exactly zero."""
+    got = np.asarray(got, dtype=np.float64).reshape(len(mass), -1)
+    ref = np.asarray(ref, dtype=np.float64).reshape(len(mass), -1)
+    mass = np.asarray(mass, dtype=np.float64)
+    big = np.abs(ref).max() if ref.size else 0.0
+    mmax = mass.max() if mass.size else 0.0
+    scale = np.maximum(np.abs(ref).max(axis=1), (mass / mmax if mmax > 0 else 0.0) * big)
+    err = np.abs(got - ref).max(axis=1)
+    zero = scale == 0.0
+    if np.any(err[zero] != 0.0):
+        return float("inf")
+    return float((err[~zero] / scale[~zero]).max()) if np.any(~zero) else 0.0
+
+
+def stencil_max_speed(x, gv, res, dx, order) -> np.ndarray:
+    """Per particle, the largest |v~_i| over the nodes of its B-spline stencil (dense grid
+    velocities gv of shape (nodes, d), node index i0 + N0 (i1 + N1 i2))."""
+    x = np.asarray(x, dtype=np.float64)
+    n, d = x.shape
+    u = x / dx
+    base = np.floor(u - 0.5).astype(np.int64) if order == 2 else np.floor(u).astype(np.int64) - 1
+    speed = np.sqrt((np.asarray(gv) ** 2).sum(axis=1))
+    out = np.zeros(n)
+    k = order + 1
+    for off in np.ndindex(*([k] * d)):
+        idx = np.zeros(n, dtype=np.int64)
+        mult = 1
+        ok = np.ones(n, dtype=bool)
+        for a in range(d):
+            g = base[:, a] + off[a]
+            ok &= (g >= 0) & (g < res[a])
+            idx += np.clip(g, 0, res[a] - 1) * mult
+            mult *= res[a]
+        out = np.maximum(out, np.where(ok, speed[idx], 0.0))
+    return out
+
+
+def particlewise_err(got, ref, scale) -> float:
+    """Largest error of any particle's entries relative to that particle's own scale."""
+    got = np.asarray(got, dtype=np.float64).reshape(len(scale), -1)
+    ref = np.asarray(ref, dtype=np.float64).reshape(len(scale), -1)
+    scale = np.asarray(scale, dtype=np.float64)
+    err = np.abs(got - ref).max(axis=1)
+    zero = scale == 0.0
+    if np.any(err[zero] != 0.0):
+        return float("inf")
+    return float((err[~zero] / scale[~zero]).max()) if np.any(~zero) else 0.0

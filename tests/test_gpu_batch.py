@@ -196,3 +196,48 @@ def test_batch_fast_motion_equals_alone(apic):
     batch.step(steps)
     check_same([s.download() for s in sims], ref)
     batch.close()
+
+
+@pytest.mark.parametrize("dim,order,precision", [(3, 2, 32), (3, 3, 32), (2, 3, 64), (2, 2, 32)])
+def test_batch_members_match_oracle(apic, dim, order, precision):
+    """Every member of a batch against the FP64 oracle, not only against stepping it alone:
+    after one batched step, the oracle's step from that member's downloaded input; after two
+    more, the oracle's two steps from the state downloaded after the first (each member with
+    its own grid, size, material, gravity and walls)."""
+    import oracle
+    from helpers import configs
+
+    members = make_members(apic, 3, seed=31 + order + dim, dim=dim, order=order, precision=precision,
+                           ppc=8 if dim == 3 else 4)
+    batch = apic.Batch(dim=dim, order=order, precision=precision, max_sims=4, max_particles=300000,
+                       max_blocks=200000)
+    sims, inputs, ocfgs = [], [], []
+    for i, (cfg, x, v, B, F) in enumerate(members):
+        sim = apic.Sim(cfg, len(x))
+        sim.upload(x, v, B, F)
+        inputs.append(sim.download())                       # the member's exact input state
+        res = tuple(cfg.res[a] for a in range(dim))
+        g = tuple(cfg.gravity[a] for a in range(dim))
+        _, oc, _, _ = configs(dim, order, res, cfg.dx, precision=precision, dt=cfg.dt, gravity=g,
+                              boundary="sticky", wall=order + 1, model="fcr", E=cfg.E, nu=cfg.nu)
+        ocfgs.append((oc, cfg.particle_mass, cfg.particle_volume))
+        batch.add(sim)
+        sims.append(sim)
+    tol = 1e-5 if precision == 32 else 1e-11
+    for nsteps in (1, 2):
+        batch.step(nsteps)
+        outs = [s.download() for s in sims]
+        for i, s in enumerate(sims):
+            oc, m, vol = ocfgs[i]
+            x0, v0, B0, F0 = inputs[i]
+            ox, ov, oB, oF, bad = oracle.step(oc, x0, v0, B0, F0, m, vol, nsteps=nsteps)
+            assert bad == 0
+            gx, gv, gB, gF = outs[i]
+            assert relerr(gv, ov) <= nsteps * tol, f"member {i} after {nsteps} step(s)"
+            assert relerr(gB, oB) <= 10 * nsteps * tol, f"member {i}"
+            assert relerr(gF, oF) <= nsteps * tol, f"member {i}"
+            dx = oc.dx
+            bound = nsteps * (tol * np.abs(ox - x0).max() + 2 * np.finfo(np.float32 if precision == 32 else np.float64).eps * dx)
+            assert np.abs((gx - x0) - (ox - x0)).max() <= bound, f"member {i}"
+        inputs = outs
+    batch.close()
