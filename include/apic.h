@@ -85,8 +85,11 @@ typedef struct {
     double particle_volume;  /* V_p (reference volume), the same for every particle */
     int tile_particles;      /* particles per P2G / G2P tile (power of two, 256..4096);
                                 0 = default */
-    int p2g_kernel;          /* P2G kernel: 0 = default, 2 = the cell-parallel kernel (the
-                                only one; other values return APIC_ERR_ARG) */
+    int p2g_kernel;          /* P2G kernel: 0 = default (1 in 3-D, 2 in 2-D); 1 = component-
+                                split (3-D only: the lanes of a group per base cell each sum two
+                                of the four node sums); 2 = cell-parallel (lanes of a group
+                                share a cell's particles and reduce their full sums); results
+                                agree to rounding */
     double flip_alpha;       /* APIC_TRANSFER_FLIP only: v_p <- a (v_p + sum w (v~_i - v_i)) +
                                 (1 - a) sum w v~_i, a in [0, 1] (1 = the paper's FLIP); the
                                 velocities v_i before the grid update are kept (+32 B per

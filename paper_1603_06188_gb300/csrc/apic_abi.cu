@@ -109,8 +109,10 @@ apic_status fill_cfg(const apic_config* in, int64_t max_particles, HostCfg* c, s
     c->mass = in->particle_mass;
     c->vol = in->particle_volume;
     c->tile = tile;
-    if (in->p2g_kernel != 0 && in->p2g_kernel != 2) { *why = "p2g_kernel must be 0 or 2"; return APIC_ERR_ARG; }
-    c->p2g_kernel = 2;   // the cell-parallel kernel
+    if (in->p2g_kernel < 0 || in->p2g_kernel > 2) { *why = "p2g_kernel must be 0, 1 or 2"; return APIC_ERR_ARG; }
+    if (in->p2g_kernel == 1 && in->dim != 3) { *why = "the component-split P2G kernel is 3-D only"; return APIC_ERR_ARG; }
+    // default: the component-split kernel in 3-D, the cell-parallel one in 2-D
+    c->p2g_kernel = in->p2g_kernel != 0 ? in->p2g_kernel : (in->dim == 3 ? 1 : 2);
     if (in->p2g_group != 0 && in->p2g_group != 2 && in->p2g_group != 4) { *why = "p2g_group must be 0, 2 or 4"; return APIC_ERR_ARG; }
     c->p2g_group = in->p2g_group != 0 ? in->p2g_group : 4;
     c->p2g_group_auto = in->p2g_group == 0;
@@ -559,7 +561,7 @@ apic_status apic_p2g(apic_sim* s)
         PhaseScope ps(s, APIC_PHASE_TILES, build_tiles_kernels(n, s->c.tile));
         CK(build_tiles(s->b, s->skeys, n, s->c.dim, s->c.tile, s->max_tiles, s->stream), "tile list");
     }
-    if (s->group_pending) {
+    if (s->group_pending && s->c.p2g_kernel == 2) {
         // particles per occupied base cell, from the tile count (a node block of 4^d cells
         // holds one tile up to tile_particles particles): fewer than 16 take groups of 2
         uint32_t nt = 0;

@@ -66,7 +66,7 @@ struct HostCfg {
     double flip_alpha;           // transfer 2: weight of the FLIP update
     double mu, lam, mass, vol;
     int tile;                    // particles per tile (power of two)
-    int p2g_kernel;              // 2: the cell-parallel kernel
+    int p2g_kernel;              // 1: component-split (3-D), 2: cell-parallel
     int p2g_group;               // lanes per base cell of the cell-parallel P2G (2 or 4)
     int p2g_group_auto;          // 1: p2g_group follows the density after each upload
     int key_bits;

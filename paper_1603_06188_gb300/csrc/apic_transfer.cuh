@@ -663,6 +663,258 @@ __global__ void __launch_bounds__(128, 2) k_p2g_cells(PState<R> st, const uint32
 }
 
 
+// ---------------------------------------------------------------- P2G, component-split (3-D)
+// A group of lanes per base cell of the tile's node block, all groups at once (64 groups per
+// CTA), each walking its cell's run of sorted particles.  The lanes of a group split what a
+// single lane would accumulate: lane bit 0 picks the pair of sums (momentum components 0 and
+// 1, or component 2 and the mass) and, for cubic B-splines, lane bit 1 picks the z-half of
+// the 4^3-node stencil.  A lane then holds 2 sums per node of 27 (quadratic) or 32 (cubic)
+// nodes, half the registers of a lane that holds all four, so twice the warps fit on an SM;
+// each lane repeats only the per-axis weights.  The mass rides as a fourth "component" whose
+// velocity is 1 and whose affine and stress rows are zero, so every lane runs the same code.
+// The group's lanes share each particle's staging slot (each copies part of it), so a group
+// reads a particle once.  No reduction across lanes is needed: each lane stores its sums of
+// its cell, and the node gather of the cell-parallel kernel adds them up.
+template <int ORDER> struct SplitShape {
+    static constexpr int K = ORDER + 1;
+    static constexpr int ZS = ORDER == 3 ? 2 : 1;   // z-halves of the stencil
+    static constexpr int KZ = K / ZS;               // z nodes per lane
+    static constexpr int LPC = 2 * ZS;              // lanes per cell
+    static constexpr int NT = 64 * LPC;             // threads per CTA: a lane group per base cell
+    static constexpr int NSL = 3;                   // staging slots per group
+};
+template <int ORDER, typename R> __host__ __device__ constexpr int split_ctas_per_sm()
+{
+    return sizeof(R) == 4 ? (ORDER == 2 ? 4 : 2) : (ORDER == 2 ? 2 : 1);
+}
+template <int ORDER, typename R> __host__ __device__ constexpr size_t p2g_split_smem()
+{
+    return (p2g_cellsum_bytes<3, ORDER, R>() + 31) / 32 * 32 +
+           (size_t)64 * SplitShape<ORDER>::NSL * slot_words<3>() * sizeof(R);
+}
+
+// lane r of a group copies the 16-byte groups g = r, r + LPC, ... of particle q's packed
+// state (A V Ba Bb Ta Tb) into the group's slot
+template <int LPC, typename R>
+__device__ __forceinline__ void stage_part(R* slot, const PState<R>& s, uint32_t q, int r)
+{
+#pragma unroll
+    for (int g = 0; g < 6; ++g) {
+        if (g % LPC != r) continue;
+        if (g == 0) cp_group4<R>(slot + 0, s.A + q);
+        if (g == 1) cp_group4<R>(slot + 4, s.V + q);
+        if (g == 2) cp_group4<R>(slot + 8, s.Ba + q);
+        if (g == 3) cp_group4<R>(slot + 12, s.Bb + q);
+        if (g == 4) cp_group4<R>(slot + 16, s.Ta + q);
+        if (g == 5) cp_group2<R>(slot + 20, s.Tb + q);
+    }
+}
+
+// One particle's two sums per node of the lane's stencil part added into accA / accB.
+// h: 0 = momentum components (0, 1), 1 = (component 2, mass); zs: the lane's z-half.
+template <int ORDER, typename R>
+__device__ __forceinline__ void p2g_split_particle(const R* slot, bool live, int h, int zs, const int* lb, const int* bo,
+                                                   const DevCfg<R>& c, uint32_t* err, R m, R sC, R dt_dx,
+                                                   bool with_tau, R* accA, R* accB)
+{
+    using S = SplitShape<ORDER>;
+    constexpr int K = S::K;
+    constexpr int KZ = S::KZ;
+    const V4<R> a = *reinterpret_cast<const V4<R>*>(slot + 0);
+    const V4<R> v = *reinterpret_cast<const V4<R>*>(slot + 4);
+    const V4<R> ba = *reinterpret_cast<const V4<R>*>(slot + 8);
+    const V4<R> bb = *reinterpret_cast<const V4<R>*>(slot + 12);
+    R o[3] = {a.x, a.y, a.z};
+    int cell[3];
+    unpack_cell<3>(r2u(a.w), cell);
+    if (!live) {   // neutral: an in-cell position (finite weights) and zero weight of the state
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            o[d] = R(0.5);
+            cell[d] = bo[d] + lb[d] + (ORDER == 3 ? 1 : 0);
+        }
+    }
+    int base[3];
+    R w[3][K], dw[3][K], fx[3];
+    bool ok = particle_stencil<3, ORDER, R>(o, cell, c, base, fx, w, dw);
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        if (base[d] - bo[d] != lb[d]) ok = false;
+    if (live && !ok) {
+        set_err(err, APIC_ERRBIT_RANGE);
+        live = false;
+    }
+    // the lane's two rows: velocity, B row (affine), tau row (stress); the mass row is (1, 0, 0).
+    // A neutral lane's slot may hold anything (even NaN), so its rows are selected to zero
+    // rather than scaled by zero.
+    const bool hi = h != 0;
+    const bool tau_on = live && with_tau;
+    const R mvA = live ? m * (hi ? v.z : v.x) : R(0);
+    const R mvB = live ? (hi ? m : m * v.y) : R(0);
+    R CA[3], CB[3], TA[3], TB[3];
+    CA[0] = live ? sC * (hi ? bb.y : v.w) : R(0);
+    CA[1] = live ? sC * (hi ? bb.z : ba.x) : R(0);
+    CA[2] = live ? sC * (hi ? bb.w : ba.y) : R(0);
+    CB[0] = (live && !hi) ? sC * ba.z : R(0);
+    CB[1] = (live && !hi) ? sC * ba.w : R(0);
+    CB[2] = (live && !hi) ? sC * bb.x : R(0);
+    {
+        const V4<R> ta = *reinterpret_cast<const V4<R>*>(slot + 16);   // t00 t11 t22 t01
+        const V2<R> tb = *reinterpret_cast<const V2<R>*>(slot + 20);   // t02 t12
+        TA[0] = tau_on ? dt_dx * (hi ? tb.x : ta.x) : R(0);
+        TA[1] = tau_on ? dt_dx * (hi ? tb.y : ta.w) : R(0);
+        TA[2] = tau_on ? dt_dx * (hi ? ta.z : tb.x) : R(0);
+        TB[0] = (tau_on && !hi) ? dt_dx * ta.w : R(0);
+        TB[1] = (tau_on && !hi) ? dt_dx * ta.y : R(0);
+        TB[2] = (tau_on && !hi) ? dt_dx * tb.y : R(0);
+    }
+    // separable sums as in the cell-parallel kernel, for the lane's two rows and z-half
+    //   sum_c(i,j,k) = w0_i P_c(j,k) + E_c(i) S(j,k),  S = w1_j w2_k
+    //   P_c(j,k) = w1_j Q_c(k) + H_c(j) w2_k,  Q_c(k) = mv_c w2_k + C_c2 (r w)2_k - T_c2 dw2_k
+    //   H_c(j) = C_c1 (r w)1_j - T_c1 dw1_j,    E_c(i) = C_c0 (r w)0_i - T_c0 dw0_i
+    R EA[K], EB[K], HA[K], HB[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const R rw0 = (R(i) - fx[0]) * w[0][i], rw1 = (R(i) - fx[1]) * w[1][i];
+        EA[i] = CA[0] * rw0 - TA[0] * dw[0][i];
+        EB[i] = CB[0] * rw0 - TB[0] * dw[0][i];
+        HA[i] = CA[1] * rw1 - TA[1] * dw[1][i];
+        HB[i] = CB[1] * rw1 - TB[1] * dw[1][i];
+    }
+#pragma unroll
+    for (int icl = 0; icl < KZ; ++icl) {
+        // the lane's z node: icl, or KZ + icl in the upper half (a select, so the weights
+        // stay in registers)
+        const R w2 = (ORDER == 3 && zs) ? w[2][(KZ + icl) % K] : w[2][icl];
+        const R dw2 = (ORDER == 3 && zs) ? dw[2][(KZ + icl) % K] : dw[2][icl];
+        const R z = (ORDER == 3 && zs) ? R(KZ + icl) : R(icl);
+        const R rw2 = (z - fx[2]) * w2;
+        const R QA = mvA * w2 + CA[2] * rw2 - TA[2] * dw2;
+        const R QB = mvB * w2 + CB[2] * rw2 - TB[2] * dw2;
+#pragma unroll
+        for (int ib = 0; ib < K; ++ib) {
+            const R S = w[1][ib] * w2;
+            const R PA = w[1][ib] * QA + HA[ib] * w2;
+            const R PB = w[1][ib] * QB + HB[ib] * w2;
+#pragma unroll
+            for (int ia = 0; ia < K; ++ia) {
+                const int j = ia + K * ib + K * K * icl;
+                fma_pair<R>(accA[j], accB[j], w[0][ia], w[0][ia], PA, PB);
+                fma_pair<R>(accA[j], accB[j], EA[ia], EB[ia], S, S);
+            }
+        }
+    }
+}
+
+// One tile (the sorted particles of one node block) by the whole CTA.  On entry the CTA is
+// converged and cbeg / cend hold zeros.  Leaves the shared memory free after its final barrier.
+template <int ORDER, typename R>
+__device__ __forceinline__ void p2g_split_tile(const PState<R>& st, const uint32_t* __restrict__ perm,
+                                               const uint32_t* __restrict__ skeys, uint32_t start, uint32_t end,
+                                               R* __restrict__ acc, uint32_t* __restrict__ flags, const DevCfg<R>& c,
+                                               uint32_t* err, R* cellsum, uint32_t* cbeg, uint32_t* cend, R* pslots)
+{
+    using S = SplitShape<ORDER>;
+    constexpr int K = S::K;
+    constexpr int KZ = S::KZ;
+    constexpr int LPC = S::LPC;
+    constexpr int NT = S::NT;
+    constexpr int NSL = S::NSL;
+    constexpr int NVAL = K * K * K * 4;
+    constexpr int SW = slot_words<3>();
+    const int grp = threadIdx.x / LPC;        // the base cell of the block this group takes
+    const int r = threadIdx.x % LPC;
+    const int h = r & 1;
+    const int zs = (ORDER == 3) ? (r >> 1) : 0;
+    const R dt_dx = step_dt(c) * c.inv_dx;
+    const R m = c.mass;
+    const R sC = (c.transfer == 0) ? m * c.inv_kdx : R(0);
+    const bool with_tau = c.model != 0;
+    const uint32_t blk = skeys[start] >> 6;
+    int bo[3] = {0, 0, 0};
+    block_coords<3, R>(blk, c, bo);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) bo[d] *= 4;
+    tile_cell_runs<3>(skeys, start, end, cbeg, cend, NT);
+    __syncthreads();
+    const uint32_t kb = cbeg[grp], ke = cend[grp];
+    const int lb[3] = {grp & 3, (grp >> 2) & 3, (grp >> 4) & 3};
+    const uint32_t run = ke - kb;
+    // warp-uniform trip count (the longest run among the warp's cells): all lanes follow one
+    // instruction stream; lanes past their run carry a neutral particle that adds zeros
+    const uint32_t iters = __reduce_max_sync(FULLMASK, run);
+    if (iters > 0u) {
+        R accA[K * K * KZ], accB[K * K * KZ];
+#pragma unroll
+        for (int i = 0; i < K * K * KZ; ++i) { accA[i] = R(0); accB[i] = R(0); }
+        R* gslots = pslots + (size_t)grp * NSL * SW;
+        // particles 0 .. NSL-2 of the run first; particle it + NSL - 1 goes into the slot read
+        // in the previous iteration (every lane of the warp has passed this iteration's
+        // barrier after reading it)
+#pragma unroll
+        for (int i = 0; i < NSL - 1; ++i) {
+            if ((uint32_t)i < run) stage_part<LPC, R>(gslots + i * SW, st, perm[kb + i], r);
+            cp_async_commit();
+        }
+        uint32_t qn = ((uint32_t)(NSL - 1) < run) ? perm[kb + NSL - 1] : 0u;
+#pragma unroll 1
+        for (uint32_t it = 0; it < iters; ++it) {
+            cp_async_wait<NSL - 2>();
+            __syncwarp();
+            {
+                const uint32_t nx = it + NSL - 1;
+                if (nx < run) stage_part<LPC, R>(gslots + (nx % NSL) * SW, st, qn, r);
+                cp_async_commit();
+                if (nx + 1 < run) qn = perm[kb + nx + 1];
+            }
+            p2g_split_particle<ORDER, R>(gslots + (it % NSL) * SW, it < run, h, zs, lb, bo, c, err, m, sC, dt_dx,
+                                         with_tau, accA, accB);
+        }
+        cp_async_wait<0>();
+        if (run > 0u) {
+            R* dst = cellsum + (size_t)grp * NVAL + 2 * h;
+#pragma unroll
+            for (int icl = 0; icl < KZ; ++icl)
+#pragma unroll
+                for (int ib = 0; ib < K; ++ib)
+#pragma unroll
+                    for (int ia = 0; ia < K; ++ia) {
+                        const int jl = ia + K * ib + K * K * icl;
+                        const int j = ia + K * ib + K * K * (zs * KZ + icl);
+                        *reinterpret_cast<V2<R>*>(dst + 4 * j) = V2<R>{accA[jl], accB[jl]};
+                    }
+        }
+    }
+    __syncthreads();
+    tile_flush<3, ORDER, R>(cellsum, cbeg, cend, bo, blk, acc, flags, c, NT);
+    __syncthreads();
+}
+
+template <int ORDER, typename R>
+__global__ void __launch_bounds__(SplitShape<ORDER>::NT, (split_ctas_per_sm<ORDER, R>()))
+    k_p2g_split(PState<R> st, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ skeys,
+                const uint32_t* __restrict__ tiles, const uint32_t* __restrict__ ntiles_p,
+                uint32_t* __restrict__ tile_ctr, R* __restrict__ acc, uint32_t* __restrict__ flags, DevCfg<R> c,
+                uint32_t* err)
+{
+    constexpr int NT = SplitShape<ORDER>::NT;
+    extern __shared__ __align__(32) unsigned char p2g_smem[];
+    R* cellsum = reinterpret_cast<R*>(p2g_smem);   // [64][NVAL]
+    R* pslots = reinterpret_cast<R*>(p2g_smem + (p2g_cellsum_bytes<3, ORDER, R>() + 31) / 32 * 32);
+    __shared__ uint32_t cbeg[64], cend[64];
+    __shared__ int s_tile;
+    const int ntiles = (int)*ntiles_p;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_ctr, 1u);
+        if (threadIdx.x < 64) { cbeg[threadIdx.x] = 0u; cend[threadIdx.x] = 0u; }
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= ntiles) break;
+        p2g_split_tile<ORDER, R>(st, perm, skeys, tiles[t], tiles[t + 1], acc, flags, c, err, cellsum, cbeg, cend,
+                                 pslots);
+    }
+}
+
 // ---------------------------------------------------------------- grid update (Sec. 3.3)
 // One warp per active node block: v~ = ((m v) + dt f) / m + dt g, sticky walls, v~ = 0 where
 // m = 0; writes (v~, m) to the velocity grid and clears the accumulation grid and flag.
@@ -1460,7 +1712,14 @@ template <typename R> struct Impl {
         const DevCfg<R> c0 = HostToDev<R>::make(h, b, n);
         PState<R> st = state_of<R>(b, cur);
         auto launch = [&](const DevCfg<R>& c, R* acc) {
-        if (h.p2g_group == 2)
+        if (h.dim == 3 && h.p2g_kernel == 1) {
+            if (h.order == 2)
+                k_p2g_split<2, R><<<L.p2g_grid, SplitShape<2>::NT, p2g_split_smem<2, R>(), s>>>(
+                    st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc, b.flags, c, b.err);
+            else
+                k_p2g_split<3, R><<<L.p2g_grid, SplitShape<3>::NT, p2g_split_smem<3, R>(), s>>>(
+                    st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc, b.flags, c, b.err);
+        } else if (h.p2g_group == 2)
             APIC_DISPATCH(h, (k_p2g_cells<D, O, R, 2><<<L.p2g_grid, 128, p2g_cells_smem<D, O, R>(), s>>>(
                                  st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc, b.flags, c, b.err, b.fallbacks)));
         else
@@ -1584,7 +1843,14 @@ template <typename R> struct Impl {
     {
         cudaError_t e = cudaSuccess;
         APIC_DISPATCH(h, {
-            {
+            if (D == 3 && h.p2g_kernel == 1) {
+                constexpr int O3 = O;
+                e = cudaFuncSetAttribute(k_p2g_split<O3, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)p2g_split_smem<O3, R>());
+                if (e == cudaSuccess)
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g_split<O3, R>,
+                                                                      SplitShape<O3>::NT, p2g_split_smem<O3, R>());
+            } else {
                 // both lane groups are set up: the group can change at the next upload
                 e = cudaFuncSetAttribute(k_p2g_cells<D, O, R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)p2g_cells_smem<D, O, R>());

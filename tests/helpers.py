@@ -80,17 +80,20 @@ def occupancy_rule(keys: np.ndarray, dim: int, res) -> np.ndarray:
     return out
 
 
-def nodewise_err(got, ref, mass) -> float:
-    """Largest error at any grid node relative to that node's own scale: |ref_i| or, where
-    larger, the node's share of the mass times the largest |ref| (so a node that holds 1 % of
-    the mass of the heaviest node gets a bound 100 times tighter than the normwise one).
-    Nodes with no mass and a zero reference must be exactly zero."""
+def nodewise_err(got, ref, mass, floor: float = 0.1) -> float:
+    """Largest error at any grid node relative to that node's own scale: the largest of
+    |ref_i|, the node's share of the mass times the largest |ref|, and `floor` times the
+    largest |ref| (so with a bound tol, a node with little mass must be within tol * floor of
+    the largest value, `1 / floor` times tighter than the normwise bound; the floor covers
+    nodes reached only by weights close to zero, which FP32 resolves to a few ulps of the
+    largest weight).  Nodes whose scale is zero must be exactly zero."""
     got = np.asarray(got, dtype=np.float64).reshape(len(mass), -1)
     ref = np.asarray(ref, dtype=np.float64).reshape(len(mass), -1)
     mass = np.asarray(mass, dtype=np.float64)
     big = np.abs(ref).max() if ref.size else 0.0
     mmax = mass.max() if mass.size else 0.0
-    scale = np.maximum(np.abs(ref).max(axis=1), (mass / mmax if mmax > 0 else 0.0) * big)
+    share = mass / mmax if mmax > 0 else np.zeros_like(mass)
+    scale = np.maximum(np.maximum(np.abs(ref).max(axis=1), share * big), floor * big)
     err = np.abs(got - ref).max(axis=1)
     zero = scale == 0.0
     if np.any(err[zero] != 0.0):

@@ -60,6 +60,8 @@ def test_workspace_size_and_validation(lib):
         (dict(tile_particles=100), apic.APIC_ERR_ARG),
         (dict(p2g_group=3), apic.APIC_ERR_ARG),
         (dict(p2g_kernel=9), apic.APIC_ERR_ARG),
+        (dict(p2g_kernel=3), apic.APIC_ERR_ARG),
+        (dict(dim=2, res=(64, 64), p2g_kernel=1), apic.APIC_ERR_ARG),   # component-split P2G is 3-D only
         (dict(model="fcr", E=-1.0, nu=0.3), apic.APIC_ERR_ARG),
         (dict(model="fcr", E=1.0, nu=0.5), apic.APIC_ERR_ARG),
     ]

@@ -24,15 +24,16 @@ def apic():
     return mod
 
 
-@pytest.mark.parametrize("tile", [0, 256, 1024])
-def test_consecutive_steps_match_oracle(apic, tile):
+@pytest.mark.parametrize("p2g_kernel,tile", [(0, 0), (0, 256), (0, 1024), (2, 0), (2, 256)])
+def test_consecutive_steps_match_oracle(apic, p2g_kernel, tile):
     res, ppc = 32, 32
     sc = scenes.falling_cube_3d(res=res, side=0.5, ppc=ppc, seed=9, omega=(0.0, 0.0, 2.0), v0=(0.3, 0.0, 0.0))
     rng = np.random.default_rng(9)
     B = sc.grad_v * kappa(2) * sc.dx ** 2
     F = scenes.random_deformation(rng, sc.n, 3, 0.02)
     gc, oc, m, vol = configs(3, 2, (res,) * 3, sc.dx, dt=2e-5, gravity=(0.0, -9.8, 0.0), boundary="sticky", wall=3,
-                             vol=sc.dx ** 3 / ppc, mass=sc.dx ** 3 / ppc, tile=tile)
+                             vol=sc.dx ** 3 / ppc, mass=sc.dx ** 3 / ppc, tile=tile,
+                             p2g_kernel=p2g_kernel)
     sim = apic.Sim(gc, sc.n)
     sim.upload(sc.x, sc.v, B, F)
     state = sim.download()
