@@ -99,7 +99,15 @@ typedef struct {
                                 the particles per occupied node block (2 below 16 particles
                                 per cell, else 4) -- that apic_p2g reads the tile count back
                                 and so synchronises once.  Results agree to rounding. */
+    int integrator;          /* member of the Sec. 3.3 family: APIC_INTEGRATOR_LAMBDA0 (0, the
+                                explicit symplectic Euler step) or APIC_INTEGRATOR_LAMBDA1 (1:
+                                the force at F^{n+1} = (I + dt sum_i v_i grad w^T) F^n from the
+                                grid velocities before the update, particles moved with them,
+                                the general transfer of Sec. 3.4); lambda = 1 is for single
+                                APIC / PIC simulations (not FLIP, batches or adaptive steps) */
 } apic_config;
+
+enum { APIC_INTEGRATOR_LAMBDA0 = 0, APIC_INTEGRATOR_LAMBDA1 = 1 };
 
 /* Bytes of device workspace a simulation with this config and capacity needs.
  * Errors: APIC_ERR_ARG (NULL pointer, bad config), APIC_ERR_UNSUPPORTED. */
@@ -156,12 +164,20 @@ apic_status apic_download_positions(apic_sim* sim, int32_t* cell, double* offset
 apic_status apic_p2g(apic_sim* sim);
 
 /* Sec. 3.3, lambda = 0: v~_i = ((m v)_i + dt f_i) / m_i + dt g, sticky walls, v~ = 0 where
- * m_i = 0.  Clears the accumulation grid for the next step.  Asynchronous. */
+ * m_i = 0.  Clears the accumulation grid for the next step.  Asynchronous.
+ * lambda = 1 (APIC_INTEGRATOR_LAMBDA1; apic_p2g then transfers mass and momentum only):
+ * v_i = (m v)_i / m_i, the force f_i = -sum_p V_p P(F_p^{n+1}) (F_p^n)^T grad w_ip at
+ * F_p^{n+1} = (I + dt sum_i v_i grad w_ip^T) F_p^n, then v~_i = v_i + dt f_i / m_i + dt g and
+ * the walls; v_i is kept for apic_g2p. */
 apic_status apic_grid_update(apic_sim* sim);
 
 /* Sec. 3.4 with Sec. 5.7 (lambda = 0): v_p = sum_i w_ip v~_i, B_p = sum_i w_ip v~_i
  * (x_i - x_p)^T (zero for PIC), F_p <- (I + dt sum_i v~_i grad w_ip^T) F_p,
  * x_p <- x_p + dt v_p.  Writes the particles in sorted order and their next cell keys.
+ * lambda = 1: the general form of Sec. 3.4 with x~_i = x_i + dt v_i: v_p = sum_i w v~_i,
+ * x_p <- sum_i w x~_i, F_p <- (I + dt sum_i v_i grad w^T) F_p, and the symmetrised B_p of
+ * Sec. 3.4 (which adds to the lambda = 0 sum dt/2 times the antisymmetric
+ * sum_i w (v~_i v_i^T - v_i v~_i^T) - (v_p vbar_p^T - vbar_p v_p^T), vbar_p = sum_i w v_i).
  * Asynchronous. */
 apic_status apic_g2p(apic_sim* sim);
 

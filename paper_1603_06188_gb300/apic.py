@@ -41,15 +41,17 @@ class Config(C.Structure):
         ("E", C.c_double), ("nu", C.c_double),
         ("particle_mass", C.c_double), ("particle_volume", C.c_double),
         ("tile_particles", C.c_int), ("p2g_kernel", C.c_int), ("flip_alpha", C.c_double),
-        ("p2g_group", C.c_int),
+        ("p2g_group", C.c_int), ("integrator", C.c_int),
     ]
 
 
 def make_config(dim=3, order=2, precision=32, transfer="apic", res=(64, 64, 64), dx=1 / 64, origin=(0, 0, 0),
                 dt=0.0, gravity=(0, 0, 0), boundary="none", wall=0, model="none", E=0.0, nu=0.0,
                 particle_mass=1.0, particle_volume=1.0, tile_particles=0, p2g_kernel=0, flip_alpha=1.0,
-                p2g_group=0) -> Config:
+                p2g_group=0, integrator=0) -> Config:
+    """integrator: 0 = lambda = 0 (symplectic Euler), 1 = the explicit member lambda = 1."""
     c = Config()
+    c.integrator = integrator
     c.p2g_group = p2g_group
     c.flip_alpha = flip_alpha
     c.dim, c.order, c.precision = dim, order, precision

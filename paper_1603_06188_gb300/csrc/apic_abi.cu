@@ -120,6 +120,15 @@ apic_status fill_cfg(const apic_config* in, int64_t max_particles, HostCfg* c, s
     if (c->key_bits > 32) { *why = "grid too large for 32-bit cell keys"; return APIC_ERR_UNSUPPORTED; }
     c->capacity = max_particles;
     c->wait_limit = APIC_DEFAULT_WAIT_LIMIT;
+    if (in->integrator != APIC_INTEGRATOR_LAMBDA0 && in->integrator != APIC_INTEGRATOR_LAMBDA1) {
+        *why = "integrator must be APIC_INTEGRATOR_LAMBDA0 or APIC_INTEGRATOR_LAMBDA1";
+        return APIC_ERR_ARG;
+    }
+    if (in->integrator == APIC_INTEGRATOR_LAMBDA1 && in->transfer == APIC_TRANSFER_FLIP) {
+        *why = "the lambda = 1 member is built for the APIC and PIC transfers";
+        return APIC_ERR_UNSUPPORTED;
+    }
+    c->integrator = in->integrator;
     return APIC_OK;
 }
 
@@ -136,7 +145,7 @@ struct Carve {
 // offsets of every buffer inside the workspace (relative to its base)
 struct Layout {
     size_t st[2][APIC_STATE_LANES];
-    size_t mk[2], mv[2], midx, choff, mcnt, mctl, lbs, step_words, acc2, vdel;
+    size_t mk[2], mv[2], midx, choff, mcnt, mctl, lbs, step_words, acc2, vdel, vel1;
     size_t knext, kA, kB, vA, vB, radix_counts, scan_part, tiles, chunk_cnt, ntiles, tile_ctr;
     size_t acc, vel, flags, mom_part, mom_out, err, fallbacks, staging;
     size_t staging_doubles;
@@ -186,6 +195,8 @@ Layout layout_of(const HostCfg& c)
     const size_t flip_bytes = c.transfer == APIC_TRANSFER_FLIP ? (size_t)c.nblocks * bn * 4 * R : 0;
     L.acc2 = cv.take(flip_bytes);
     L.vdel = cv.take(flip_bytes);
+    // lambda = 1: the grid velocity before the update (4 lanes per node)
+    L.vel1 = cv.take(c.integrator == APIC_INTEGRATOR_LAMBDA1 ? (size_t)c.nblocks * bn * 4 * R : 0);
     L.flags = cv.take((size_t)c.nblocks * 4);
     L.mom_part = cv.take((size_t)kMomParts * 6 * 8);
     L.mom_out = cv.take(6 * 8);
@@ -353,6 +364,7 @@ apic_status apic_create(const apic_config* cfg, int64_t max_particles, void* wor
     s->b.vel = base + L.vel;
     s->b.acc2 = c.transfer == APIC_TRANSFER_FLIP ? base + L.acc2 : nullptr;
     s->b.vdel = c.transfer == APIC_TRANSFER_FLIP ? base + L.vdel : nullptr;
+    s->b.vel1 = c.integrator == APIC_INTEGRATOR_LAMBDA1 ? base + L.vel1 : nullptr;
     s->b.flags = (uint32_t*)(base + L.flags);
     s->b.mom_part = (double*)(base + L.mom_part);
     s->b.mom_out = (double*)(base + L.mom_out);
@@ -383,6 +395,7 @@ apic_status apic_create(const apic_config* cfg, int64_t max_particles, void* wor
     if (e == cudaSuccess) e = cudaMemsetAsync(s->b.vel, 0, gbytes, s->stream);
     if (e == cudaSuccess && s->b.acc2) e = cudaMemsetAsync(s->b.acc2, 0, gbytes, s->stream);
     if (e == cudaSuccess && s->b.vdel) e = cudaMemsetAsync(s->b.vdel, 0, gbytes, s->stream);
+    if (e == cudaSuccess && s->b.vel1) e = cudaMemsetAsync(s->b.vel1, 0, gbytes, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->b.flags, 0, (size_t)c.nblocks * 4, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->b.err, 0, 4, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->b.dt_word, 0, 32, s->stream);
@@ -585,7 +598,11 @@ apic_status apic_grid_update(apic_sim* s)
     IN_BATCH_GUARD(s);
     if (s->phase != 1) return fail(s, APIC_ERR_ARG, "apic_grid_update must follow apic_p2g");
     CK(cudaSetDevice(s->device), "cudaSetDevice");
-    {
+    if (s->c.integrator == APIC_INTEGRATOR_LAMBDA1) {
+        PhaseScope ps(s, APIC_PHASE_GRID, (s->c.model != 0 && s->n > 0) ? 3 : 2);
+        CK(DISPATCH(s, grid_update_lambda1, s->c, s->b, s->cur, s->skeys, s->perm, s->n, s->L, s->stream),
+           "lambda = 1 grid kernels");
+    } else {
         PhaseScope ps(s, APIC_PHASE_GRID, 1);
         CK(DISPATCH(s, grid_update, s->c, s->b, s->L, s->stream), "grid update kernel");
     }
@@ -602,7 +619,10 @@ apic_status apic_g2p(apic_sim* s)
     if (s->n > 0) {
         {
             PhaseScope ps(s, APIC_PHASE_G2P, 1);
-            CK(DISPATCH(s, g2p, s->c, s->b, s->cur, s->skeys, s->perm, s->n, s->L, s->stream), "g2p kernel");
+            if (s->c.integrator == APIC_INTEGRATOR_LAMBDA1)
+                CK(DISPATCH(s, g2p_lambda1, s->c, s->b, s->cur, s->perm, s->n, s->L, s->stream), "lambda = 1 g2p kernel");
+            else
+                CK(DISPATCH(s, g2p, s->c, s->b, s->cur, s->skeys, s->perm, s->n, s->L, s->stream), "g2p kernel");
         }
         s->cur ^= 1;
         s->keys_valid = true;
@@ -630,6 +650,8 @@ apic_status apic_step_adaptive(apic_sim* s, int nsteps, double nu, double dt_max
     if (!s || nsteps < 0 || !(nu > 0.0) || !(dt_max > 0.0)) return APIC_ERR_ARG;
     IN_BATCH_GUARD(s);
     if (s->phase != 0) return fail(s, APIC_ERR_ARG, "apic_step_adaptive between apic_p2g and apic_g2p");
+    if (s->c.integrator == APIC_INTEGRATOR_LAMBDA1)
+        return fail(s, APIC_ERR_UNSUPPORTED, "adaptive steps are built for the lambda = 0 integrator");
     CK(cudaSetDevice(s->device), "cudaSetDevice");
     if (elapsed) *elapsed = 0.0;
     if (s->n == 0 || nsteps == 0) return APIC_OK;
@@ -1182,6 +1204,8 @@ apic_status apic_batch_add(apic_batch* b, apic_sim* s)
     if (s->phase != 0) return batch_fail(b, APIC_ERR_ARG, "the simulation is in the middle of a step");
     if (s->c.transfer == APIC_TRANSFER_FLIP)
         return batch_fail(b, APIC_ERR_UNSUPPORTED, "FLIP simulations are stepped on their own, not in batches");
+    if (s->c.integrator == APIC_INTEGRATOR_LAMBDA1)
+        return batch_fail(b, APIC_ERR_UNSUPPORTED, "lambda = 1 simulations are stepped on their own, not in batches");
     if ((int)b->members.size() >= b->max_sims) return batch_fail(b, APIC_ERR_OOM, "batch member capacity reached");
     int64_t parts = 0, blocks = 0;
     for (apic_sim* m : b->members) {

@@ -328,8 +328,10 @@ __device__ __forceinline__ void jacobi_rot(R* S, R* V, int p, int q, int r)
     }
 }
 
+// gap (may be NULL): (sigma_2^2 - sigma_3^2) / sigma_1^2 of the two smallest singular values,
+// which decides how well the rotation of an inverted F is resolved
 template <typename R>
-__device__ __forceinline__ void polar3(const R* F, R* Rot)
+__device__ __forceinline__ void polar3(const R* F, R* Rot, R* gap = nullptr)
 {
     R S[9], V[9] = {R(1), R(0), R(0), R(0), R(1), R(0), R(0), R(0), R(1)};
     for (int a = 0; a < 3; ++a)
@@ -363,6 +365,7 @@ __device__ __forceinline__ void polar3(const R* F, R* Rot)
     if (nrm[1] > nrm[0]) swapc(0, 1);
     if (nrm[2] > nrm[0]) swapc(0, 2);
     if (nrm[2] > nrm[1]) swapc(1, 2);
+    if (gap) *gap = nrm[0] > R(0) ? (nrm[1] - nrm[2]) / nrm[0] : R(0);
     if (det3(V) < R(0))
         for (int i = 0; i < 3; ++i) V[i * 3 + 2] = -V[i * 3 + 2];
     // U by Gram-Schmidt; degenerate columns completed from the coordinate axes
@@ -466,6 +469,17 @@ __device__ __forceinline__ bool polar_newton3(const R* F, R* Rot)
     return false;
 }
 
+// For an inverted F (det F <= 0) the rotation's sign convention puts the negative singular
+// value last; the rotation in the plane of the two smallest singular values is then
+// determined only to eps / gap (it is not corrected through U = F V as for det F > 0), and
+// the residual of polar_residual does not see it (the two eigenvalues of R^T F in that plane
+// nearly cancel).  Below gap = 1/8 the FP32 rotation can be off by more than ~1e-6, so it is
+// recomputed in FP64: the "nearly coincident singular values" case of the FP64 fallback.
+template <typename R> __device__ __forceinline__ bool inverted_unresolved(const R* F, R gap)
+{
+    return gap < R(0.125) && det3<R>(F) <= R(0);
+}
+
 // Kirchhoff-type stress tau = V_p P(F) F^T, which is symmetric for both models, returned
 // as its independent entries (3-D: t00 t11 t22 t01 t02 t12; 2-D: t00 t11 t01).
 // Fixed-corotated: P = 2 mu (F - R) + lam (J - 1) J F^{-T}
@@ -489,8 +503,9 @@ __device__ __forceinline__ void stress_sym_fcr(const R* F, R mu, R lam, R vol, R
         // a converged Newton iterate is the orthogonal polar factor to working precision; the
         // Jacobi route (det F <= 0, or no convergence) is checked and redone in FP64 if needed
         if (!polar_newton3<R>(F, Rot)) {
-            polar3<R>(F, Rot);
-            if (sizeof(R) == 4 && polar_residual<R>(F, Rot) > R(2e-5)) {
+            R gap = R(1);
+            polar3<R>(F, Rot, &gap);
+            if (sizeof(R) == 4 && (polar_residual<R>(F, Rot) > R(2e-5) || inverted_unresolved<R>(F, gap))) {
                 double Fd[9], Rd[9];
                 for (int i = 0; i < 9; ++i) Fd[i] = (double)F[i];
                 polar3<double>(Fd, Rd);

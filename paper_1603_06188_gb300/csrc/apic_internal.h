@@ -43,6 +43,7 @@ struct Buffers {
     void* vel;                   // velocity grid (4 lanes per node)
     void* acc2;                  // FLIP only: PIC momentum without the force (4 lanes per node)
     void* vdel;                  // FLIP only: the grid change (v~ - v, m) (4 lanes per node)
+    void* vel1;                  // lambda = 1 only: the grid velocity before the update (v, m)
     uint32_t* flags;             // active node blocks
     double* mom_part;            // per-CTA momentum partials
     double* mom_out;             // 6 doubles
@@ -73,6 +74,7 @@ struct HostCfg {
     int nblocks;
     int64_t capacity;
     unsigned wait_limit;         // polls of G2P's first bounded wait (APIC_DEFAULT_WAIT_LIMIT)
+    int integrator;              // 0: lambda = 0 (symplectic Euler), 1: the explicit member lambda = 1
 };
 
 // per-simulation view of the sort buffers, for the batched sort (apic_sort.cu)
@@ -158,7 +160,11 @@ struct Launch {
     cudaError_t set_materials_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const double* E,     \
                                     const double* nu, cudaStream_t s);                                             \
     cudaError_t adapt_dt_##SFX(const HostCfg& c, const Buffers& b, double nu, double dt_max, int first,         \
-                               cudaStream_t s);
+                               cudaStream_t s);                                                                 \
+    cudaError_t grid_update_lambda1_##SFX(const HostCfg& c, const Buffers& b, int cur, const uint32_t* skeys,   \
+                                          const uint32_t* perm, int64_t n, const Launch& L, cudaStream_t s);    \
+    cudaError_t g2p_lambda1_##SFX(const HostCfg& c, const Buffers& b, int cur, const uint32_t* perm, int64_t n,  \
+                                  const Launch& L, cudaStream_t s);
 
 #define APIC_DECLARE_BATCH(SFX)                                                                              \
     size_t batch_desc_bytes_##SFX();                                                                          \

@@ -11,6 +11,8 @@
 // and apic_transfer_f64.cu, which instantiate it for one real type each.
 #pragma once
 
+#include <algorithm>
+
 #include "apic_device.cuh"
 
 namespace apic {
@@ -1685,6 +1687,12 @@ __global__ void __launch_bounds__(TPB) k_grid_dense(const R* __restrict__ grid, 
     }
 }
 
+}  // namespace apic
+
+#include "apic_lambda1.cuh"
+
+namespace apic {
+
 // ---------------------------------------------------------------- launchers
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + TPB - 1) / TPB); }
 
@@ -1709,7 +1717,8 @@ template <typename R> struct Impl {
                            int64_t n, const Launch& L, cudaStream_t s)
     {
         if (n == 0) return cudaSuccess;
-        const DevCfg<R> c0 = HostToDev<R>::make(h, b, n);
+        DevCfg<R> c0 = HostToDev<R>::make(h, b, n);
+        if (h.integrator == 1) c0.model = 0;   // lambda = 1: the force is taken after the grid velocity
         PState<R> st = state_of<R>(b, cur);
         auto launch = [&](const DevCfg<R>& c, R* acc) {
         if (h.dim == 3 && h.p2g_kernel == 1) {
@@ -1759,6 +1768,42 @@ template <typename R> struct Impl {
         else
             APIC_DISPATCH(h, (k_g2p<D, O, R, false><<<L.g2p_grid, G2P_THREADS, 0, s>>>(in, out, perm, sk, b.tiles, b.ntiles,
                                      b.tile_ctr, (const R*)b.vel, b.knext, c, b.err, b.fallbacks, nullptr)));
+        return cudaGetLastError();
+    }
+    // the grid phase of the lambda = 1 member: grid velocity, the force at F^{n+1}, the update
+    static cudaError_t grid_update_lambda1(const HostCfg& h, const Buffers& b, int cur, const uint32_t* sk,
+                                           const uint32_t* perm, int64_t n, const Launch& L, cudaStream_t s)
+    {
+        DevCfg<R> c = HostToDev<R>::make(h, b, n);
+        const int grid = L.sms * 8;
+        if (h.dim == 3) k_grid_velocity<3, R><<<grid, TPB, 0, s>>>((R*)b.acc, (R*)b.vel1, b.flags, c);
+        else k_grid_velocity<2, R><<<grid, TPB, 0, s>>>((R*)b.acc, (R*)b.vel1, b.flags, c);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && h.model != 0 && n > 0) {
+            e = cudaMemsetAsync(b.tile_ctr + 3, 0, sizeof(uint32_t), s);
+            PState<R> st = state_of<R>(b, cur);
+            if (e == cudaSuccess)
+                APIC_DISPATCH(h, (k_force_lambda1<D, O, R><<<L.sms * 4, 128, 0, s>>>(
+                                     st, perm, sk, b.tiles, b.ntiles, b.tile_ctr + 3, (const R*)b.vel1, (R*)b.acc, c,
+                                     b.err, b.fallbacks)));
+            if (e == cudaSuccess) e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            if (h.dim == 3) k_grid_update_lambda1<3, R><<<grid, TPB, 0, s>>>((R*)b.acc, (R*)b.vel, (const R*)b.vel1, b.flags, c);
+            else k_grid_update_lambda1<2, R><<<grid, TPB, 0, s>>>((R*)b.acc, (R*)b.vel, (const R*)b.vel1, b.flags, c);
+            e = cudaGetLastError();
+        }
+        return e;
+    }
+    static cudaError_t g2p_lambda1(const HostCfg& h, const Buffers& b, int cur, const uint32_t* perm, int64_t n,
+                                   const Launch& L, cudaStream_t s)
+    {
+        if (n == 0) return cudaSuccess;
+        DevCfg<R> c = HostToDev<R>::make(h, b, n);
+        PState<R> in = state_of<R>(b, cur), out = state_of<R>(b, cur ^ 1);
+        const unsigned grid = (unsigned)std::min<int64_t>((n + 127) / 128, (int64_t)L.sms * 16);
+        APIC_DISPATCH(h, (k_g2p_lambda1<D, O, R><<<grid, 128, 0, s>>>(in, out, perm, (const R*)b.vel, (const R*)b.vel1,
+                                                                       b.knext, c, b.err)));
         return cudaGetLastError();
     }
     static cudaError_t adapt_dt(const HostCfg& h, const Buffers& b, double nu, double dt_max, int first, cudaStream_t s)
@@ -1895,6 +1940,16 @@ template <typename R> struct Impl {
                                cudaStream_t s)                                                                  \
     {                                                                                                           \
         return Impl<R>::adapt_dt(c, b, nu, dt_max, first, s);                                                   \
+    }                                                                                                           \
+    cudaError_t grid_update_lambda1_##SFX(const HostCfg& c, const Buffers& b, int cur, const uint32_t* skeys,  \
+                                          const uint32_t* perm, int64_t n, const Launch& L, cudaStream_t s)     \
+    {                                                                                                           \
+        return Impl<R>::grid_update_lambda1(c, b, cur, skeys, perm, n, L, s);                                   \
+    }                                                                                                           \
+    cudaError_t g2p_lambda1_##SFX(const HostCfg& c, const Buffers& b, int cur, const uint32_t* perm, int64_t n, \
+                                  const Launch& L, cudaStream_t s)                                              \
+    {                                                                                                           \
+        return Impl<R>::g2p_lambda1(c, b, cur, perm, n, L, s);                                                  \
     }                                                                                                           \
     cudaError_t set_materials_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const double* E,   \
                                     const double* nu, cudaStream_t s)                                          \

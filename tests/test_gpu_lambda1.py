@@ -1,0 +1,203 @@
+"""The explicit member lambda = 1 of the Sec. 3.3 integrator family on the GPU, through the C
+ABI, against the FP64 oracle (or_step_lambda1 and its parts), each phase fed the GPU's own
+input state:
+
+- P2G transfers mass and momentum only (the force comes later);
+- the grid phase: v_i = (m v)_i / m_i, the force at F^{n+1} = (I + dt sum_i v_i grad w^T) F^n
+  (oracle.force_at at the displacement dt v_i), v~_i = v_i + dt f_i / m_i, gravity, walls;
+- G2P: the general transfer of Sec. 3.4 at lambda = 1 (oracle.g2p with lambda_t = 1) from
+  the GPU's v~ and the v_i the oracle forms from the GPU's own P2G grid;
+- whole steps against oracle.step_lambda1, step after step from the GPU's state;
+- p and l conserved (Sec. 5.2 / 5.3 hold for every member of the family);
+- without a constitutive model the member coincides with lambda = 0.
+Bars: 1e-5 normwise (FP32), 1e-11 (FP64), per node and per particle as in the lambda = 0
+parity tests."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import (configs, kappa, nodewise_err, particlewise_err, relerr, state_for, stencil_max_speed)
+from paper_1603_06188_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+TOL = {32: 1e-5, 64: 1e-11}
+
+CASES = [
+    # dim, order, precision, res, ppc, model
+    (3, 2, 32, 32, 8, "fcr"),
+    (3, 3, 32, 32, 8, "fcr"),
+    (2, 2, 32, 64, 4, "fcr"),
+    (2, 3, 32, 64, 4, "nh"),
+    (3, 2, 64, 24, 8, "nh"),
+    (3, 3, 64, 24, 8, "fcr"),
+    (2, 2, 64, 64, 4, "fcr"),
+    (2, 3, 64, 64, 4, "fcr"),
+]
+
+
+def _ids(c):
+    return f"d{c[0]}_o{c[1]}_fp{c[2]}_{c[5]}"
+
+
+@pytest.fixture(scope="module")
+def apic():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1603_06188_gb300 import apic as mod
+
+    mod.load(build_if_missing=True)
+    return mod
+
+
+def scene(dim, res, ppc, seed):
+    if dim == 3:
+        return scenes.falling_cube_3d(res=res, side=0.5, ppc=ppc, seed=seed, omega=(0.5, -1.0, 2.0), v0=(0.3, 0.1, -0.2))
+    return scenes.rotating_disk_2d(res=res, radius=0.25, ppc=ppc, seed=seed, omega=2.0)
+
+
+def setup(apic, case, seed=0, dt=2e-3, gravity=True, walls=True, model=None, light=False):
+    """light: particle mass = its volume (density 1), so the elastic force dominates the grid
+    velocity change of one step; otherwise mass 1 (a heavy, slowly responding body)."""
+    dim, order, prec, res, ppc, mdl = case
+    sc = scene(dim, res, ppc, seed)
+    x, v, B, F = state_for(sc, order, seed=seed, Fscale=0.1)
+    g = (0.0, -9.8, 0.0)[:dim] if gravity else (0.0,) * dim
+    vol = sc.dx ** dim / 8
+    gc, oc, m, vol = configs(dim, order, (res,) * dim, sc.dx, precision=prec, dt=dt, gravity=g,
+                             boundary="sticky" if walls else "none", wall=order + 1 if walls else 0,
+                             model=model or mdl, mass=vol if light else 1.0, vol=vol)
+    gc.integrator = 1
+    oc.lambda_t = 1.0
+    sim = apic.Sim(gc, len(x))
+    sim.upload(x, v, B, F)
+    return sim, sc, oc, m, vol
+
+
+@pytest.mark.parametrize("case", CASES, ids=_ids)
+def test_lambda1_phases_match_oracle(apic, case):
+    dim, order, prec, res, ppc, mdl = case
+    sim, sc, oc, m, vol = setup(apic, case, light=True)
+    x0, v0, B0, F0 = sim.download()
+    tol = TOL[prec]
+    # P2G: mass and momentum, no force folded in
+    sim.p2g()
+    m_g, mv_g = sim.grid("momentum")
+    oc0 = oracle.make_cfg(dim=dim, order=order, res=(res,) * dim, dx=sc.dx, dt=oc.dt)
+    gm, gmv, _, bad = oracle.p2g(oc0, x0, v0, B0, F0, m, vol)
+    assert bad == 0
+    assert relerr(m_g, gm) <= tol and relerr(mv_g, gmv) <= tol
+    assert nodewise_err(mv_g, gmv, gm) <= tol
+    # the grid phase, from the GPU's own P2G grid
+    sim.grid_update()
+    m_v, vt_g = sim.grid("velocity")
+    np.testing.assert_array_equal(m_v, m_g)
+    gv = np.where(m_g[:, None] > 0, mv_g / np.where(m_g > 0, m_g, 1.0)[:, None], 0.0)
+    gf, bad = oracle.force_at(oc, x0, F0, vol, oc.dt * gv)
+    assert bad == 0
+    _, vt_ref = oracle.grid_update(oc, m_g, mv_g, gf)
+    assert relerr(vt_g, vt_ref) <= tol
+    # the velocity change alone, (v~ - v) m = dt (f + m g), away from the walls
+    dv_g = (vt_g - gv) * m_g[:, None]
+    dv_ref = (vt_ref - gv) * m_g[:, None]
+    inner = np.ones(len(m_g), dtype=bool)
+    idx = np.indices((res,) * dim).reshape(dim, -1)[::-1].T      # node coordinates, axis 0 fastest
+    for a in range(dim):
+        inner &= (idx[:, a] >= order + 1) & (idx[:, a] < res - order - 1)
+    assert relerr(dv_g[inner], dv_ref[inner]) <= 10 * tol
+    # G2P at lambda = 1 from the GPU's v~ and the v_i of its P2G grid
+    sim.g2p()
+    gx, gvp, gB, gF = sim.download()
+    x1, v1, B1, F1, bad = oracle.g2p(oc, x0, F0, gv, vt_g)
+    assert bad == 0
+    assert relerr(gvp, v1) <= tol
+    assert relerr(gB, B1) <= tol
+    assert relerr(gF, F1) <= tol
+    assert relerr(gF - F0, F1 - F0) <= 10 * tol
+    smax = stencil_max_speed(x0, np.maximum(np.abs(vt_g), np.abs(gv)), (res,) * dim, sc.dx, order)
+    assert particlewise_err(gvp, v1, smax) <= tol
+    assert particlewise_err(gB, B1, smax * sc.dx) <= tol
+    eps = np.finfo(np.float32 if prec == 32 else np.float64).eps
+    bound = tol * np.abs(x1 - x0).max() + 2 * eps * sc.dx + 4 * np.finfo(np.float64).eps
+    assert np.abs((gx - x0) - (x1 - x0)).max() <= bound
+    sim.close()
+
+
+@pytest.mark.parametrize("case", CASES[:4] + CASES[5:6], ids=_ids)
+def test_lambda1_steps_match_oracle(apic, case):
+    """Three whole steps, each compared with oracle.step_lambda1 from the GPU's state."""
+    dim, order, prec, res, ppc, mdl = case
+    sim, sc, oc, m, vol = setup(apic, case, seed=3, dt=1e-3)
+    state = sim.download()
+    tol = TOL[prec]
+    for step in range(3):
+        sim.step(1)
+        got = sim.download()
+        x0, v0, B0, F0 = state
+        ox, ov, oB, oF, bad = oracle.step_lambda1(oc, x0, v0, B0, F0, m, vol)
+        assert bad == 0
+        gx, gv, gB, gF = got
+        assert relerr(gv, ov) <= tol, f"step {step}"
+        assert relerr(gB, oB) <= 10 * tol, f"step {step}"
+        assert relerr(gF, oF) <= tol, f"step {step}"
+        eps = np.finfo(np.float32 if prec == 32 else np.float64).eps
+        assert np.abs((gx - x0) - (ox - x0)).max() <= tol * np.abs(ox - x0).max() + 2 * eps * sc.dx + 1e-15
+        state = got
+    sim.close()
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[4], CASES[6]], ids=_ids)
+def test_lambda1_conserves_momentum(apic, case):
+    """Elastic forces only (no gravity, no walls): p and l after three lambda = 1 steps equal
+    their values before, to the working precision (FP32: 1e-5, FP64: 1e-12 of the sums'
+    magnitudes)."""
+    dim, order, prec, res, ppc, mdl = case
+    sim, sc, oc, m, vol = setup(apic, case, seed=5, dt=1e-3, gravity=False, walls=False)
+    x, v, B, F = sim.download()
+    p0, l0 = sim.momentum("particles")
+    sim.step(3)
+    p1, l1 = sim.momentum("particles")
+    sp = m * np.linalg.norm(v, axis=1).sum()
+    sl = m * (np.linalg.norm(x, axis=1) * np.linalg.norm(v, axis=1)).sum() + m * np.abs(B).sum()
+    t = 1e-5 if prec == 32 else 1e-12
+    assert np.abs(p1 - p0).max() <= t * sp
+    assert np.abs(l1 - l0).max() <= t * sl
+    sim.close()
+
+
+@pytest.mark.parametrize("dim,order", [(3, 2), (2, 3)])
+def test_lambda1_without_forces_is_the_lambda0_step(apic, dim, order):
+    """With no constitutive model v_i = v~_i (no force, no gravity), and the lambda = 1 step is
+    the lambda = 0 one: the same state after two steps, to rounding."""
+    case = (dim, order, 64, 32 if dim == 3 else 64, 8 if dim == 3 else 4, "none")
+    sim1, sc, oc, m, vol = setup(apic, case, seed=7, gravity=False, walls=False, model="none")
+    x, v, B, F = sim1.download()
+    gc0, _, _, _ = configs(dim, order, sc.res, sc.dx, precision=64, dt=2e-3, model="none")
+    sim0 = apic.Sim(gc0, len(x))
+    sim0.upload(x, v, B, F)
+    sim1.step(2)
+    sim0.step(2)
+    a, b = sim1.download(), sim0.download()
+    for u, w in zip(a, b):
+        assert relerr(u, w) <= 1e-12
+    sim1.close()
+    sim0.close()
+
+
+def test_lambda1_rejects_what_it_does_not_support(apic):
+    base = dict(dim=3, order=2, res=(16,) * 3, dx=1 / 16, integrator=1)
+    with pytest.raises(apic.ApicError) as e:
+        apic.Sim(apic.make_config(transfer="flip", **base), 10)
+    assert e.value.status == apic.APIC_ERR_UNSUPPORTED
+    sim = apic.Sim(apic.make_config(model="fcr", E=1e4, nu=0.3, dt=1e-4, particle_volume=1e-5, **base), 10)
+    sim.upload(np.full((10, 3), 0.5))
+    with pytest.raises(apic.ApicError) as e:
+        sim.step_adaptive(2, 1.0, 1e-4)
+    assert e.value.status == apic.APIC_ERR_UNSUPPORTED
+    batch = apic.Batch(dim=3, order=2, max_sims=2, max_particles=100, max_blocks=1000)
+    with pytest.raises(apic.ApicError) as e:
+        batch.add(sim)
+    assert e.value.status == apic.APIC_ERR_UNSUPPORTED
+    batch.close()
+    sim.close()
