@@ -392,6 +392,124 @@ def run_serving(args) -> int:
     return 0
 
 
+def _norm_rel(a, b) -> float:
+    den = float(np.abs(b).max())
+    return float(np.abs(a - b).max() / den) if den > 0 else float(np.abs(a).max())
+
+
+def run_drift(args) -> int:
+    """Drift of the FP32 path over many steps, written to profiles/drift_fp32.md and printed
+    as one JSON line:
+      (a) FP32 GPU against the FP64 oracle on a reduced cube (64^3, cube side 0.4, 8 ppc,
+          the cube's material, gravity, walls and dt = 2e-5, rotating and deformed), both
+          started from the same state and stepped 200 times, compared every 20 steps;
+      (b) FP32 GPU against FP64 GPU on reduced colliding spheres (cubic, 128^3, r = 0.15,
+          8 ppc, +-1, E = 5e4, nu = 0.4, dt = 5e-6), 2000 steps, compared every 200."""
+    import torch
+
+    import oracle
+    from paper_1603_06188_gb300 import apic, build, scenes
+
+    build.build()
+    apic.load()
+    oracle.build()
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(2024)
+    # (a)
+    w = dict(WORKLOADS["cube128"])
+    res, ppc = 64, 8
+    sc = scenes.falling_cube_3d(res=res, side=0.4, ppc=ppc, seed=11, omega=(0.5, -1.0, 2.0), v0=(0.2, 0.0, -0.1))
+    B = sc.grad_v * (0.25 * sc.dx ** 2)
+    F = scenes.random_deformation(rng, sc.n, 3, 0.02)
+    vol = sc.dx ** 3 / ppc
+    mass = w["rho"] * vol
+    cfg = apic.make_config(dim=3, order=2, precision=32, res=(res,) * 3, dx=sc.dx, dt=w["dt"], gravity=w["gravity"],
+                           boundary=w["boundary"], wall=3, model="fcr", E=w["E"], nu=w["nu"], particle_mass=mass,
+                           particle_volume=vol)
+    oc = oracle.make_cfg(dim=3, order=2, res=(res,) * 3, dx=sc.dx, dt=w["dt"], gravity=w["gravity"],
+                         boundary=w["boundary"], wall=3, model="fcr", E=w["E"], nu=w["nu"])
+    sim = apic.Sim(cfg, sc.n)
+    sim.upload(sc.x, sc.v, B, F)
+    ox, ov, oB, oF = sim.download()          # both start from the FP32 state widened exactly
+    rows_a = []
+    t0 = time.perf_counter()
+    p_start = oracle.momentum_particles(oc, ox, ov, oB, mass)
+    for chunk in range(10):
+        sim.step(20)
+        gx, gv, gB, gF = sim.download()
+        ox, ov, oB, oF, bad = oracle.step(oc, ox, ov, oB, oF, mass, vol, nsteps=20)
+        po, lo = oracle.momentum_particles(oc, ox, ov, oB, mass)
+        pg, lg = sim.momentum("particles")
+        rows_a.append({"step": 20 * (chunk + 1), "v": _norm_rel(gv, ov), "B": _norm_rel(gB, oB), "F": _norm_rel(gF, oF),
+                       "x_cells": float(np.abs(gx - ox).max() / sc.dx),
+                       "p_gpu_minus_oracle": float(np.abs(pg - po).max() / (mass * np.linalg.norm(ov, axis=1).sum())),
+                       "l_gpu_minus_oracle": float(np.abs(lg - lo).max() /
+                                                   (mass * (np.linalg.norm(ox, axis=1) * np.linalg.norm(ov, axis=1)).sum())),
+                       "oracle_skipped": int(bad)})
+    secs_a = time.perf_counter() - t0
+    sim.close()
+    # (b)
+    res3 = 128
+    sp = scenes.colliding_spheres_3d(res=res3, radius=0.15, ppc=8, speed=1.0, seed=12)
+    B3 = sp.grad_v * (sp.dx ** 2 / 3.0)
+    vol3 = sp.dx ** 3 / 8
+    sims = {}
+    for prec in (32, 64):
+        c3 = apic.make_config(dim=3, order=3, precision=prec, res=(res3,) * 3, dx=sp.dx, dt=5e-6, boundary="sticky",
+                              wall=4, model="fcr", E=5e4, nu=0.4, particle_mass=vol3, particle_volume=vol3)
+        s3 = apic.Sim(c3, sp.n)
+        s3.upload(sp.x, sp.v, B3)
+        sims[prec] = s3
+    x32 = sims[32].download()
+    sims[64].upload(*x32)                    # the FP64 run starts from the FP32 state exactly
+    rows_b = []
+    p0 = {k: s.momentum("particles") for k, s in sims.items()}
+    for chunk in range(10):
+        for s in sims.values():
+            s.step(200)
+        a, b = sims[32].download(), sims[64].download()
+        m32, m64 = sims[32].momentum("particles"), sims[64].momentum("particles")
+        sv = vol3 * np.linalg.norm(b[1], axis=1).sum()
+        rows_b.append({"step": 200 * (chunk + 1), "v": _norm_rel(a[1], b[1]), "B": _norm_rel(a[2], b[2]),
+                       "F": _norm_rel(a[3], b[3]), "x_cells": float(np.abs(a[0] - b[0]).max() / sp.dx),
+                       "p_drift_fp32": float(np.abs(m32[0] - p0[32][0]).max() / sv),
+                       "p_drift_fp64": float(np.abs(m64[0] - p0[64][0]).max() / sv),
+                       "l_drift_fp32": float(np.abs(m32[1] - p0[32][1]).max() / sv),
+                       "l_drift_fp64": float(np.abs(m64[1] - p0[64][1]).max() / sv)})
+    for s in sims.values():
+        s.close()
+    out = {"metric": "drift of the FP32 path", "a": {"workload": f"cube{res}", "particles": sc.n, "steps": 200,
+                                                     "oracle_seconds": secs_a, "rows": rows_a},
+           "b": {"workload": f"spheres{res3}", "particles": sp.n, "steps": 2000, "rows": rows_b}}
+    print(json.dumps(out), flush=True)
+    lines = ["# Drift of the FP32 path over many steps", "",
+             "Written by `python bench.py --workload drift` (one GB300).  Every figure is the largest",
+             "error over all particles, normwise relative (||a - b||_inf / ||b||_inf) unless stated.", "",
+             f"## (a) FP32 GPU against the FP64 oracle: cube {res}^3, side 0.4, 8 ppc ({sc.n} particles),",
+             "fixed-corotated E = 1e4, nu = 0.3, rho = 1, gravity, sticky walls, dt = 2e-5, rotating and",
+             "deformed (F = I + 0.02 U(-1, 1)); both from the same state, 200 steps.", "",
+             "| step | v | B | F | x (cells) | p: GPU - oracle | l: GPU - oracle |", "|---:|---:|---:|---:|---:|---:|---:|"]
+    for r in rows_a:
+        lines.append(f"| {r['step']} | {r['v']:.2e} | {r['B']:.2e} | {r['F']:.2e} | {r['x_cells']:.2e} | "
+                     f"{r['p_gpu_minus_oracle']:.2e} | {r['l_gpu_minus_oracle']:.2e} |")
+    lines += ["", "p and l differences are relative to sum m |v| and sum m |x| |v|.", "",
+              f"## (b) FP32 GPU against FP64 GPU: two cubic-spline spheres at {res3}^3, r = 0.15, 8 ppc",
+              f"({sp.n} particles), +-1, fixed-corotated E = 5e4, nu = 0.4, dt = 5e-6, sticky walls, 2000 steps;",
+              "the FP64 run starts from the FP32 run's state.", "",
+              "| step | v | B | F | x (cells) | p drift FP32 | p drift FP64 | l drift FP32 | l drift FP64 |",
+              "|---:|---:|---:|---:|---:|---:|---:|---:|---:|"]
+    for r in rows_b:
+        lines.append(f"| {r['step']} | {r['v']:.2e} | {r['B']:.2e} | {r['F']:.2e} | {r['x_cells']:.2e} | "
+                     f"{r['p_drift_fp32']:.2e} | {r['p_drift_fp64']:.2e} | {r['l_drift_fp32']:.2e} | {r['l_drift_fp64']:.2e} |")
+    lines += ["", "Drift columns: |p(step) - p(0)| and |l(step) - l(0)| relative to sum m |v| of the FP64 state.",
+              "No wall is reached and there is no gravity, so both runs should keep p and l up to rounding;",
+              "the spheres meet near step 1000.", ""]
+    os.makedirs(os.path.join(ROOT, "profiles"), exist_ok=True)
+    with open(os.path.join(ROOT, "profiles", "drift_fp32.md"), "w") as f:
+        f.write("\n".join(lines))
+    return 0
+
+
 def aggregate(local_ms: float, local_units: float, dist=None, device=None):
     """Whole-job timing over replicas: the slowest rank's time and the sum of all ranks'
     particle-steps (no collective touches the simulation data)."""
@@ -609,7 +727,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="cube128", choices=sorted(WORKLOADS) + ["batched", "serving"])
+    ap.add_argument("--workload", default="cube128", choices=sorted(WORKLOADS) + ["batched", "serving", "drift"])
     ap.add_argument("--sims", type=int, default=512)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=200.0)
@@ -636,6 +754,8 @@ def main():
         return run_batched(args) if rank == 0 else 0
     if args.workload == "serving":
         return run_serving(args) if rank == 0 else 0
+    if args.workload == "drift":
+        return run_drift(args) if rank == 0 else 0
 
     import torch
 

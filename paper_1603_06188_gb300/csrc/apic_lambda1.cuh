@@ -5,7 +5,7 @@
 //   x~_i = x_i + dt v_i, so F_p^{n+1} = (I + dt sum_i v_i (grad w_ip)^T) F_p^n,
 //   f_i = -sum_p V_p P(F_p^{n+1}) (F_p^n)^T grad w_ip                        k_force_lambda1
 //   v~_i = v_i + dt f_i / m_i (+ dt g, walls)                                 k_grid_update_lambda1
-//   the general transfer to particles of Sec. 3.4 at lambda = 1               k_g2p_lambda1
+//   the general transfer to particles of Sec. 3.4 at lambda = 1               k_g2p_general
 // The velocity grid before the update (v_i) lives in its own array (vel1), the updated one
 // (v~_i) in the usual velocity grid, so G2P gathers both.  The force matrix
 // A_p = V_p P(F^{n+1}) (F^n)^T is not symmetric; it is formed and scattered in the same
@@ -118,17 +118,19 @@ __global__ void __launch_bounds__(TPB) k_grid_velocity(R* __restrict__ acc, R* _
     }
 }
 
-// The force at F^{n+1}, tile by tile (a tile = sorted particles of one node block): each
-// particle gathers grad v = sum_i v_i (grad w_ip)^T from vel1, forms F^ = (I + dt grad v) F^n,
-// P(F^) and A = V_p P(F^) (F^n)^T, and adds -dt A grad w_ip into a shared-memory tile of the
-// (4 + ORDER)^D nodes its block's particles reach; the tile is added to the accumulation grid
-// once.  Persistent CTAs take tiles from ctr.
+// The force of Sec. 3.3 at a displaced grid x~_i = x_i + dt u_i, tile by tile (a tile = sorted
+// particles of one node block): each particle gathers grad u = sum_i u_i (grad w_ip)^T from
+// ugrid, forms F^ = (I + dt grad u) F^n, P(F^) and A = V_p P(F^) (F^n)^T, and adds
+// -dt A grad w_ip into a shared-memory tile of the (4 + ORDER)^D nodes its block's particles
+// reach; the tile is added to the accumulation grid once.  u = v_i gives the member
+// lambda = 1 (F^ = F^{n+1}); u = v_i / 2 + dv_i / 4 the implicit midpoint rule's force at
+// F^{n+1/2}.  Persistent CTAs take tiles from ctr.
 template <int D, int ORDER, typename R>
 __global__ void __launch_bounds__(128) k_force_lambda1(PState<R> st, const uint32_t* __restrict__ perm,
                                                        const uint32_t* __restrict__ skeys,
                                                        const uint32_t* __restrict__ tiles,
                                                        const uint32_t* __restrict__ ntiles_p, uint32_t* __restrict__ ctr,
-                                                       const R* __restrict__ vel1, R* __restrict__ acc, DevCfg<R> c,
+                                                       const R* __restrict__ ugrid, R* __restrict__ acc, DevCfg<R> c,
                                                        uint32_t* err, uint32_t* fallbacks)
 {
     constexpr int K = ORDER + 1;
@@ -175,7 +177,7 @@ __global__ void __launch_bounds__(128) k_force_lambda1(PState<R> st, const uint3
             for (int j = 0; j < ((D == 3) ? K * K * K : K * K); ++j) {
                 const int ia = j % K, ib = (j / K) % K, ic = (D == 3) ? j / (K * K) : 0;
                 const int g[3] = {base[0] + ia, base[1] + ib, (D == 3) ? base[D - 1] + ic : 0};
-                const V4<R> vv = ld4(reinterpret_cast<const V4<R>*>(vel1) + node_index<D>(g, c.nb));
+                const V4<R> vv = ld4(reinterpret_cast<const V4<R>*>(ugrid) + node_index<D>(g, c.nb));
                 const R vi[3] = {vv.x, vv.y, vv.z};
                 R gw[3];
                 if (D == 3) {
@@ -288,17 +290,19 @@ __global__ void __launch_bounds__(TPB) k_grid_update_lambda1(R* __restrict__ acc
     }
 }
 
-// The general transfer to particles of Sec. 3.4 at lambda = 1, x~_i = x_i + dt v_i:
-//   v_p = sum_i w v~_i,  x_p^{n+1} = sum_i w x~_i = x_p + dt vbar_p,  vbar_p = sum_i w v_i,
-//   F_p^{n+1} = (I + dt sum_i v_i (grad w)^T) F_p^n,
+// The general transfer to particles of Sec. 3.4, with the nodes moved to x~_i = x_i + dt u_i,
+// u_i = lambda v_i + (1 - lambda) v~_i (ugrid: v_i for lambda = 1, (v_i + v~_i) / 2 for the
+// midpoint rule):
+//   v_p = sum_i w v~_i,  x_p^{n+1} = sum_i w x~_i = x_p + dt ubar_p,  ubar_p = sum_i w u_i,
+//   F_p^{n+1} = (I + dt sum_i u_i (grad w)^T) F_p^n,
 //   B_p = 1/2 sum_i w (v~_i (x_i - x_p + x~_i - x_p^{n+1})^T + (x_i - x_p - x~_i + x_p^{n+1}) v~_i^T)
-//       = sum_i w v~_i (x_i - x_p)^T + dt/2 (sum_i w (v~_i v_i^T - v_i v~_i^T) - (v_p vbar_p^T - vbar_p v_p^T))
-// (the last line is the same sum with x~_i - x_p^{n+1} = x_i - x_p + dt (v_i - vbar_p) put in),
+//       = sum_i w v~_i (x_i - x_p)^T + dt/2 (sum_i w (v~_i u_i^T - u_i v~_i^T) - (v_p ubar_p^T - ubar_p v_p^T))
+// (the last line is the same sum with x~_i - x_p^{n+1} = x_i - x_p + dt (u_i - ubar_p) put in),
 // B_p = 0 for PIC.  Particle k of the sorted order is read through the permutation and written
 // at k, with its next cell key.
 template <int D, int ORDER, typename R>
-__global__ void __launch_bounds__(128) k_g2p_lambda1(PState<R> in, PState<R> out, const uint32_t* __restrict__ perm,
-                                                     const R* __restrict__ vel, const R* __restrict__ vel1,
+__global__ void __launch_bounds__(128) k_g2p_general(PState<R> in, PState<R> out, const uint32_t* __restrict__ perm,
+                                                     const R* __restrict__ vel, const R* __restrict__ ugrid,
                                                      uint32_t* __restrict__ knext, DevCfg<R> c, uint32_t* err)
 {
     constexpr int K = ORDER + 1;
@@ -322,7 +326,7 @@ __global__ void __launch_bounds__(128) k_g2p_lambda1(PState<R> in, PState<R> out
             const int g[3] = {base[0] + ia, base[1] + ib, (D == 3) ? base[D - 1] + ic : 0};
             const uint32_t ni = node_index<D>(g, c.nb);
             const V4<R> t4 = ld4(reinterpret_cast<const V4<R>*>(vel) + ni);
-            const V4<R> v4 = ld4(reinterpret_cast<const V4<R>*>(vel1) + ni);
+            const V4<R> v4 = ld4(reinterpret_cast<const V4<R>*>(ugrid) + ni);
             const R vt[3] = {t4.x, t4.y, t4.z}, v1[3] = {v4.x, v4.y, v4.z};
             const R wt = (D == 3) ? w[0][ia] * w[1][ib] * w[D - 1][ic] : w[0][ia] * w[1][ib];
             R gw[3], rh[3];
@@ -349,7 +353,7 @@ __global__ void __launch_bounds__(128) k_g2p_lambda1(PState<R> in, PState<R> out
                 }
             }
         }
-        // F <- (I + dt grad v) F with the velocities before the update
+        // F <- (I + dt grad u) F with the displacement velocities
         R Fn[D * D];
 #pragma unroll
         for (int a = 0; a < D; ++a)
