@@ -100,14 +100,24 @@ typedef struct {
                                 per cell, else 4) -- that apic_p2g reads the tile count back
                                 and so synchronises once.  Results agree to rounding. */
     int integrator;          /* member of the Sec. 3.3 family: APIC_INTEGRATOR_LAMBDA0 (0, the
-                                explicit symplectic Euler step) or APIC_INTEGRATOR_LAMBDA1 (1:
+                                explicit symplectic Euler step), APIC_INTEGRATOR_LAMBDA1 (1:
                                 the force at F^{n+1} = (I + dt sum_i v_i grad w^T) F^n from the
                                 grid velocities before the update, particles moved with them,
-                                the general transfer of Sec. 3.4); lambda = 1 is for single
-                                APIC / PIC simulations (not FLIP, batches or adaptive steps) */
+                                the general transfer of Sec. 3.4) or APIC_INTEGRATOR_MIDPOINT
+                                (2: the implicit midpoint rule lambda = 1/2, solved on the grid
+                                by Newton iterations with mass-inner-product conjugate gradients,
+                                Sec. 4.1-4.2 and Algorithm 1; neither gravity nor walls, which
+                                the paper's solve does not have).  lambda = 1 and the midpoint
+                                rule are for single APIC / PIC simulations (not FLIP, batches or
+                                adaptive steps) */
+    int newton_max;          /* midpoint rule: Newton iterations per step at most (0 = 20) */
+    int cg_max;              /* midpoint rule: CG iterations per Newton system at most (0 = 200) */
+    double solve_tol;        /* midpoint rule: a Newton loop ends when |dt M^-1 f - dv|_M <=
+                                solve_tol |v|_M, a CG solve when its residual has dropped by
+                                solve_tol (0 = 1e-6 in FP32, 1e-12 in FP64) */
 } apic_config;
 
-enum { APIC_INTEGRATOR_LAMBDA0 = 0, APIC_INTEGRATOR_LAMBDA1 = 1 };
+enum { APIC_INTEGRATOR_LAMBDA0 = 0, APIC_INTEGRATOR_LAMBDA1 = 1, APIC_INTEGRATOR_MIDPOINT = 2 };
 
 /* Bytes of device workspace a simulation with this config and capacity needs.
  * Errors: APIC_ERR_ARG (NULL pointer, bad config), APIC_ERR_UNSUPPORTED. */
@@ -370,6 +380,12 @@ apic_status apic_sort_keys_noalloc(const uint32_t* keys, int64_t n, int key_bits
  * particle state of that step is not valid; the device stays usable.  Host-only
  * bookkeeping.  Errors: APIC_ERR_ARG (NULL, or the simulation is in a batch). */
 apic_status apic_set_wait_limit(apic_sim* sim, unsigned polls);
+
+/* The last grid solve of the implicit midpoint rule: out[0] Newton iterations (systems
+ * solved), out[1] conjugate-gradient iterations over them, out[2] the final Newton residual
+ * |dt M^-1 f - dv|_M / |v|_M.  Zeros for the explicit members.  Host-only, no
+ * synchronisation (apic_grid_update already read the scalars back).  Errors: APIC_ERR_ARG. */
+apic_status apic_solve_stats(apic_sim* sim, double out[3]);
 
 /* Reason for the last failing call on this simulation ("" if none). */
 const char* apic_last_error(apic_sim* sim);

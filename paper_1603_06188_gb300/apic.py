@@ -41,17 +41,20 @@ class Config(C.Structure):
         ("E", C.c_double), ("nu", C.c_double),
         ("particle_mass", C.c_double), ("particle_volume", C.c_double),
         ("tile_particles", C.c_int), ("p2g_kernel", C.c_int), ("flip_alpha", C.c_double),
-        ("p2g_group", C.c_int), ("integrator", C.c_int),
+        ("p2g_group", C.c_int), ("integrator", C.c_int), ("newton_max", C.c_int), ("cg_max", C.c_int),
+        ("solve_tol", C.c_double),
     ]
 
 
 def make_config(dim=3, order=2, precision=32, transfer="apic", res=(64, 64, 64), dx=1 / 64, origin=(0, 0, 0),
                 dt=0.0, gravity=(0, 0, 0), boundary="none", wall=0, model="none", E=0.0, nu=0.0,
                 particle_mass=1.0, particle_volume=1.0, tile_particles=0, p2g_kernel=0, flip_alpha=1.0,
-                p2g_group=0, integrator=0) -> Config:
-    """integrator: 0 = lambda = 0 (symplectic Euler), 1 = the explicit member lambda = 1."""
+                p2g_group=0, integrator=0, newton_max=0, cg_max=0, solve_tol=0.0) -> Config:
+    """integrator: 0 = lambda = 0 (symplectic Euler), 1 = the explicit member lambda = 1,
+    2 = the implicit midpoint rule (newton_max, cg_max, solve_tol: 0 = the library's defaults)."""
     c = Config()
     c.integrator = integrator
+    c.newton_max, c.cg_max, c.solve_tol = newton_max, cg_max, solve_tol
     c.p2g_group = p2g_group
     c.flip_alpha = flip_alpha
     c.dim, c.order, c.precision = dim, order, precision
@@ -121,6 +124,7 @@ SIGNATURES = {
     "apic_batch_run": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_int),
                                  C.POINTER(C.c_int)]),
     "apic_batch_resident_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "apic_solve_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
 }
 PHASES = ["keys", "sort", "tiles", "p2g", "grid_update", "g2p"]
 
@@ -247,6 +251,12 @@ def apic_grid_occupancy(sim, out, n_blocks: int):
 def apic_stats(sim):
     out = np.zeros(5, dtype=np.int64)
     _check(load().apic_stats(sim, _ptr(out)), sim)
+    return out
+
+
+def apic_solve_stats(sim):
+    out = np.zeros(3)
+    _check(load().apic_solve_stats(sim, _ptr(out)), sim)
     return out
 
 
@@ -467,6 +477,10 @@ class Sim:
         s = apic_stats(self.handle)
         return {"particles": int(s[0]), "blocks": int(s[1]), "tiles": int(s[2]), "polar_fp64_fallbacks": int(s[3]),
                 "kernel_launches": int(s[4])}
+
+    def solve_stats(self) -> dict:
+        s = apic_solve_stats(self.handle)
+        return {"newton": int(s[0]), "cg": int(s[1]), "residual": float(s[2])}
 
     def profile(self, enable: bool = True):
         apic_profile(self.handle, 1 if enable else 0)

@@ -39,6 +39,7 @@ struct apic_sim {
     int64_t max_tiles;
     std::string err;
     int64_t launches;      // kernels launched since creation
+    double solve_stats[3]; // the last midpoint solve: Newton and CG iterations, final residual
     // per-phase timing
     bool prof_on;
     std::vector<cudaEvent_t> ev_pool;
@@ -120,15 +121,29 @@ apic_status fill_cfg(const apic_config* in, int64_t max_particles, HostCfg* c, s
     if (c->key_bits > 32) { *why = "grid too large for 32-bit cell keys"; return APIC_ERR_UNSUPPORTED; }
     c->capacity = max_particles;
     c->wait_limit = APIC_DEFAULT_WAIT_LIMIT;
-    if (in->integrator != APIC_INTEGRATOR_LAMBDA0 && in->integrator != APIC_INTEGRATOR_LAMBDA1) {
-        *why = "integrator must be APIC_INTEGRATOR_LAMBDA0 or APIC_INTEGRATOR_LAMBDA1";
+    if (in->integrator < APIC_INTEGRATOR_LAMBDA0 || in->integrator > APIC_INTEGRATOR_MIDPOINT) {
+        *why = "integrator must be APIC_INTEGRATOR_LAMBDA0, _LAMBDA1 or _MIDPOINT";
         return APIC_ERR_ARG;
     }
-    if (in->integrator == APIC_INTEGRATOR_LAMBDA1 && in->transfer == APIC_TRANSFER_FLIP) {
-        *why = "the lambda = 1 member is built for the APIC and PIC transfers";
+    if (in->integrator != APIC_INTEGRATOR_LAMBDA0 && in->transfer == APIC_TRANSFER_FLIP) {
+        *why = "the lambda = 1 and midpoint members are built for the APIC and PIC transfers";
         return APIC_ERR_UNSUPPORTED;
     }
+    if (in->integrator == APIC_INTEGRATOR_MIDPOINT) {
+        if (in->boundary != APIC_BOUNDARY_NONE || in->gravity[0] != 0.0 || in->gravity[1] != 0.0 ||
+            (in->dim == 3 && in->gravity[2] != 0.0)) {
+            *why = "the midpoint solve has neither gravity nor walls (the paper's solve has none)";
+            return APIC_ERR_UNSUPPORTED;
+        }
+        if (in->newton_max < 0 || in->cg_max < 0 || in->solve_tol < 0.0) {
+            *why = "newton_max, cg_max and solve_tol must be >= 0";
+            return APIC_ERR_ARG;
+        }
+    }
     c->integrator = in->integrator;
+    c->newton_max = in->newton_max > 0 ? in->newton_max : 20;
+    c->cg_max = in->cg_max > 0 ? in->cg_max : 200;
+    c->solve_tol = in->solve_tol > 0.0 ? in->solve_tol : (in->precision == 32 ? 1e-6 : 1e-12);
     return APIC_OK;
 }
 
@@ -145,7 +160,7 @@ struct Carve {
 // offsets of every buffer inside the workspace (relative to its base)
 struct Layout {
     size_t st[2][APIC_STATE_LANES];
-    size_t mk[2], mv[2], midx, choff, mcnt, mctl, lbs, step_words, acc2, vdel, vel1;
+    size_t mk[2], mv[2], midx, choff, mcnt, mctl, lbs, step_words, acc2, vdel, vel1, solve[6];
     size_t knext, kA, kB, vA, vB, radix_counts, scan_part, tiles, chunk_cnt, ntiles, tile_ctr;
     size_t acc, vel, flags, mom_part, mom_out, err, fallbacks, staging;
     size_t staging_doubles;
@@ -195,8 +210,11 @@ Layout layout_of(const HostCfg& c)
     const size_t flip_bytes = c.transfer == APIC_TRANSFER_FLIP ? (size_t)c.nblocks * bn * 4 * R : 0;
     L.acc2 = cv.take(flip_bytes);
     L.vdel = cv.take(flip_bytes);
-    // lambda = 1: the grid velocity before the update (4 lanes per node)
-    L.vel1 = cv.take(c.integrator == APIC_INTEGRATOR_LAMBDA1 ? (size_t)c.nblocks * bn * 4 * R : 0);
+    // lambda = 1 and the midpoint rule: the grid velocity before the update (4 lanes per node);
+    // the midpoint solve: its six grid vectors
+    const size_t gv_bytes = (size_t)c.nblocks * bn * 4 * R;
+    L.vel1 = cv.take(c.integrator != APIC_INTEGRATOR_LAMBDA0 ? gv_bytes : 0);
+    for (int i = 0; i < 6; ++i) L.solve[i] = cv.take(c.integrator == APIC_INTEGRATOR_MIDPOINT ? gv_bytes : 0);
     L.flags = cv.take((size_t)c.nblocks * 4);
     L.mom_part = cv.take((size_t)kMomParts * 6 * 8);
     L.mom_out = cv.take(6 * 8);
@@ -364,7 +382,13 @@ apic_status apic_create(const apic_config* cfg, int64_t max_particles, void* wor
     s->b.vel = base + L.vel;
     s->b.acc2 = c.transfer == APIC_TRANSFER_FLIP ? base + L.acc2 : nullptr;
     s->b.vdel = c.transfer == APIC_TRANSFER_FLIP ? base + L.vdel : nullptr;
-    s->b.vel1 = c.integrator == APIC_INTEGRATOR_LAMBDA1 ? base + L.vel1 : nullptr;
+    s->b.vel1 = c.integrator != APIC_INTEGRATOR_LAMBDA0 ? base + L.vel1 : nullptr;
+    {
+        const bool mid = c.integrator == APIC_INTEGRATOR_MIDPOINT;
+        void** sv[6] = {&s->b.sdv, &s->b.su, &s->b.sr, &s->b.sp, &s->b.ss, &s->b.sdu};
+        for (int i = 0; i < 6; ++i) *sv[i] = mid ? base + L.solve[i] : nullptr;
+    }
+    s->solve_stats[0] = s->solve_stats[1] = s->solve_stats[2] = 0.0;
     s->b.flags = (uint32_t*)(base + L.flags);
     s->b.mom_part = (double*)(base + L.mom_part);
     s->b.mom_out = (double*)(base + L.mom_out);
@@ -396,6 +420,10 @@ apic_status apic_create(const apic_config* cfg, int64_t max_particles, void* wor
     if (e == cudaSuccess && s->b.acc2) e = cudaMemsetAsync(s->b.acc2, 0, gbytes, s->stream);
     if (e == cudaSuccess && s->b.vdel) e = cudaMemsetAsync(s->b.vdel, 0, gbytes, s->stream);
     if (e == cudaSuccess && s->b.vel1) e = cudaMemsetAsync(s->b.vel1, 0, gbytes, s->stream);
+    if (c.integrator == APIC_INTEGRATOR_MIDPOINT) {
+        void* sv[6] = {s->b.sdv, s->b.su, s->b.sr, s->b.sp, s->b.ss, s->b.sdu};
+        for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaMemsetAsync(sv[i], 0, gbytes, s->stream);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(s->b.flags, 0, (size_t)c.nblocks * 4, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->b.err, 0, 4, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->b.dt_word, 0, 32, s->stream);
@@ -598,7 +626,13 @@ apic_status apic_grid_update(apic_sim* s)
     IN_BATCH_GUARD(s);
     if (s->phase != 1) return fail(s, APIC_ERR_ARG, "apic_grid_update must follow apic_p2g");
     CK(cudaSetDevice(s->device), "cudaSetDevice");
-    if (s->c.integrator == APIC_INTEGRATOR_LAMBDA1) {
+    if (s->c.integrator == APIC_INTEGRATOR_MIDPOINT) {
+        int64_t kernels = 0;
+        cudaError_t e = DISPATCH(s, grid_update_midpoint, s->c, s->b, s->cur, s->skeys, s->perm, s->n, s->L, s->stream,
+                                 s->solve_stats, &kernels);
+        PhaseScope ps(s, APIC_PHASE_GRID, kernels);
+        CK(e, "midpoint grid solve");
+    } else if (s->c.integrator == APIC_INTEGRATOR_LAMBDA1) {
         PhaseScope ps(s, APIC_PHASE_GRID, (s->c.model != 0 && s->n > 0) ? 3 : 2);
         CK(DISPATCH(s, grid_update_lambda1, s->c, s->b, s->cur, s->skeys, s->perm, s->n, s->L, s->stream),
            "lambda = 1 grid kernels");
@@ -619,8 +653,8 @@ apic_status apic_g2p(apic_sim* s)
     if (s->n > 0) {
         {
             PhaseScope ps(s, APIC_PHASE_G2P, 1);
-            if (s->c.integrator == APIC_INTEGRATOR_LAMBDA1)
-                CK(DISPATCH(s, g2p_lambda1, s->c, s->b, s->cur, s->perm, s->n, s->L, s->stream), "lambda = 1 g2p kernel");
+            if (s->c.integrator != APIC_INTEGRATOR_LAMBDA0)
+                CK(DISPATCH(s, g2p_lambda1, s->c, s->b, s->cur, s->perm, s->n, s->L, s->stream), "general g2p kernel");
             else
                 CK(DISPATCH(s, g2p, s->c, s->b, s->cur, s->skeys, s->perm, s->n, s->L, s->stream), "g2p kernel");
         }
@@ -650,7 +684,7 @@ apic_status apic_step_adaptive(apic_sim* s, int nsteps, double nu, double dt_max
     if (!s || nsteps < 0 || !(nu > 0.0) || !(dt_max > 0.0)) return APIC_ERR_ARG;
     IN_BATCH_GUARD(s);
     if (s->phase != 0) return fail(s, APIC_ERR_ARG, "apic_step_adaptive between apic_p2g and apic_g2p");
-    if (s->c.integrator == APIC_INTEGRATOR_LAMBDA1)
+    if (s->c.integrator != APIC_INTEGRATOR_LAMBDA0)
         return fail(s, APIC_ERR_UNSUPPORTED, "adaptive steps are built for the lambda = 0 integrator");
     CK(cudaSetDevice(s->device), "cudaSetDevice");
     if (elapsed) *elapsed = 0.0;
@@ -818,6 +852,13 @@ apic_status apic_profile_read(apic_sim* s, double ms[APIC_NPHASE], int64_t launc
         ms[r.phase] += t;
         launches[r.phase] += r.kernels;
     }
+    return APIC_OK;
+}
+
+apic_status apic_solve_stats(apic_sim* s, double out[3])
+{
+    if (!s || !out) return APIC_ERR_ARG;
+    for (int i = 0; i < 3; ++i) out[i] = s->solve_stats[i];
     return APIC_OK;
 }
 
@@ -1204,8 +1245,8 @@ apic_status apic_batch_add(apic_batch* b, apic_sim* s)
     if (s->phase != 0) return batch_fail(b, APIC_ERR_ARG, "the simulation is in the middle of a step");
     if (s->c.transfer == APIC_TRANSFER_FLIP)
         return batch_fail(b, APIC_ERR_UNSUPPORTED, "FLIP simulations are stepped on their own, not in batches");
-    if (s->c.integrator == APIC_INTEGRATOR_LAMBDA1)
-        return batch_fail(b, APIC_ERR_UNSUPPORTED, "lambda = 1 simulations are stepped on their own, not in batches");
+    if (s->c.integrator != APIC_INTEGRATOR_LAMBDA0)
+        return batch_fail(b, APIC_ERR_UNSUPPORTED, "lambda = 1 and midpoint simulations are stepped on their own, not in batches");
     if ((int)b->members.size() >= b->max_sims) return batch_fail(b, APIC_ERR_OOM, "batch member capacity reached");
     int64_t parts = 0, blocks = 0;
     for (apic_sim* m : b->members) {

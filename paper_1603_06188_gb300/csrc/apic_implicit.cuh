@@ -311,7 +311,8 @@ __global__ void __launch_bounds__(128) k_force_diff(PState<R> st, const uint32_t
 //   op 3  du += a p,  r -= a s;  <r, r>
 //   op 4  p  = r + a p
 //   op 5  dv += du
-//   op 6  v~ = v + dv into vel (with the mass), u = (v + v~) / 2; flags cleared
+//   op 6  v~ = v + dv into vel (with the mass), u = (v + v~) / 2
+//   op 7  <v, v>_M (acc = vel1 here)
 struct SolveVecs {
     void* vel1; void* dv; void* u; void* r; void* p; void* s; void* du; void* acc; void* vel;
 };
@@ -375,6 +376,7 @@ __global__ void __launch_bounds__(TPB) k_solve_step(SolveVecs sv, uint32_t* __re
                 u[i] = live ? R(0.5) * (v1[i] + vt) : R(0);
                 break;
             }
+            case 7: dot += (double)m * (double)v1[i] * (double)v1[i]; break;
             default: break;
             }
         }
@@ -396,13 +398,14 @@ __global__ void __launch_bounds__(TPB) k_solve_step(SolveVecs sv, uint32_t* __re
     }
 }
 
-// flags cleared after the solve (the next P2G sets them again)
-__global__ void __launch_bounds__(TPB) k_clear_flags(uint32_t* flags, int nblocks)
+// flags cleared after the solve (the next P2G sets them again); one instance per real type
+template <typename R> __global__ void __launch_bounds__(TPB) k_clear_flags(uint32_t* flags, int nblocks)
 {
     for (int b = blockIdx.x * TPB + threadIdx.x; b < nblocks; b += gridDim.x * TPB) flags[b] = 0u;
 }
 
-// sum of np FP64 partials into out[0] (fixed order)
+// sum of np FP64 partials into out[0] (fixed order); one instance per real type
+template <typename R>
 __global__ void __launch_bounds__(TPB) k_sum_partials(const double* __restrict__ part, int np, double* __restrict__ out)
 {
     __shared__ double s[TPB];

@@ -43,7 +43,8 @@ struct Buffers {
     void* vel;                   // velocity grid (4 lanes per node)
     void* acc2;                  // FLIP only: PIC momentum without the force (4 lanes per node)
     void* vdel;                  // FLIP only: the grid change (v~ - v, m) (4 lanes per node)
-    void* vel1;                  // lambda = 1 only: the grid velocity before the update (v, m)
+    void* vel1;                  // lambda = 1 / midpoint: the grid velocity before the update (v, m)
+    void* sdv; void* su; void* sr; void* sp; void* ss; void* sdu;   // midpoint solve vectors (4 lanes per node)
     uint32_t* flags;             // active node blocks
     double* mom_part;            // per-CTA momentum partials
     double* mom_out;             // 6 doubles
@@ -74,7 +75,9 @@ struct HostCfg {
     int nblocks;
     int64_t capacity;
     unsigned wait_limit;         // polls of G2P's first bounded wait (APIC_DEFAULT_WAIT_LIMIT)
-    int integrator;              // 0: lambda = 0 (symplectic Euler), 1: the explicit member lambda = 1
+    int integrator;              // 0: lambda = 0 (symplectic Euler), 1: explicit lambda = 1, 2: implicit midpoint
+    int newton_max, cg_max;      // midpoint: iteration caps
+    double solve_tol;            // midpoint: Newton and CG tolerance
 };
 
 // per-simulation view of the sort buffers, for the batched sort (apic_sort.cu)
@@ -164,7 +167,10 @@ struct Launch {
     cudaError_t grid_update_lambda1_##SFX(const HostCfg& c, const Buffers& b, int cur, const uint32_t* skeys,   \
                                           const uint32_t* perm, int64_t n, const Launch& L, cudaStream_t s);    \
     cudaError_t g2p_lambda1_##SFX(const HostCfg& c, const Buffers& b, int cur, const uint32_t* perm, int64_t n,  \
-                                  const Launch& L, cudaStream_t s);
+                                  const Launch& L, cudaStream_t s);                                              \
+    cudaError_t grid_update_midpoint_##SFX(const HostCfg& c, const Buffers& b, int cur, const uint32_t* skeys,  \
+                                           const uint32_t* perm, int64_t n, const Launch& L, cudaStream_t s,     \
+                                           double* stats, int64_t* kernels);
 
 #define APIC_DECLARE_BATCH(SFX)                                                                              \
     size_t batch_desc_bytes_##SFX();                                                                          \

@@ -1772,6 +1772,7 @@ __global__ void __launch_bounds__(TPB) k_grid_dense(const R* __restrict__ grid, 
 }  // namespace apic
 
 #include "apic_lambda1.cuh"
+#include "apic_implicit.cuh"
 
 namespace apic {
 
@@ -1884,9 +1885,113 @@ template <typename R> struct Impl {
         DevCfg<R> c = HostToDev<R>::make(h, b, n);
         PState<R> in = state_of<R>(b, cur), out = state_of<R>(b, cur ^ 1);
         const unsigned grid = (unsigned)std::min<int64_t>((n + 127) / 128, (int64_t)L.sms * 16);
-        APIC_DISPATCH(h, (k_g2p_general<D, O, R><<<grid, 128, 0, s>>>(in, out, perm, (const R*)b.vel, (const R*)b.vel1,
+        const R* ugrid = (const R*)(h.integrator == 2 ? b.su : b.vel1);   // midpoint: u = (v + v~) / 2
+        APIC_DISPATCH(h, (k_g2p_general<D, O, R><<<grid, 128, 0, s>>>(in, out, perm, (const R*)b.vel, ugrid,
                                                                        b.knext, c, b.err)));
         return cudaGetLastError();
+    }
+    // <., .>_M partials of one solve step (per CTA) summed into mom_out[0] and read back
+    static cudaError_t read_dot(const Buffers& b, int parts, cudaStream_t s, double* out)
+    {
+        k_sum_partials<R><<<1, TPB, 0, s>>>(b.mom_part, parts, b.mom_out);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, b.mom_out, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        return e;
+    }
+    // The grid phase of the implicit midpoint rule: v_i = (m v)_i / m_i, Newton on dv with CG in
+    // the mass inner product for each system (Algorithm 1), then v~ = v + dv and the displacement
+    // velocity u = (v + v~) / 2 for G2P.  The scalars of each iteration are read back to the host,
+    // which takes the decisions of the algorithm.  stats: [0] Newton iterations, [1] CG
+    // iterations, [2] the last Newton residual relative to |v|_M (as doubles).
+    static cudaError_t grid_update_midpoint(const HostCfg& h, const Buffers& b, int cur, const uint32_t* sk,
+                                            const uint32_t* perm, int64_t n, const Launch& L, cudaStream_t s,
+                                            double* stats, int64_t* kernels)
+    {
+        DevCfg<R> c = HostToDev<R>::make(h, b, n);
+        const int ggrid = L.sms * 8;
+        const int parts = L.mom_parts;
+        const double dt = h.dt;
+        SolveVecs sv{b.vel1, b.sdv, b.su, b.sr, b.sp, b.ss, b.sdu, b.acc, b.vel};
+        stats[0] = stats[1] = stats[2] = 0.0;
+        cudaError_t e = cudaSuccess;
+        auto step = [&](int op, double a) {
+            if (e != cudaSuccess) return;
+            if (h.dim == 3) k_solve_step<3, R><<<parts, TPB, 0, s>>>(sv, b.flags, c, op, a, b.mom_part);
+            else k_solve_step<2, R><<<parts, TPB, 0, s>>>(sv, b.flags, c, op, a, b.mom_part);
+            e = cudaGetLastError();
+            *kernels += 1;
+        };
+        auto force = [&](bool diff) {
+            if (e != cudaSuccess || h.model == 0 || n == 0) return;
+            e = cudaMemsetAsync(b.tile_ctr + 3, 0, sizeof(uint32_t), s);
+            PState<R> st = state_of<R>(b, cur);
+            if (e != cudaSuccess) return;
+            if (diff)
+                APIC_DISPATCH(h, (k_force_diff<D, O, R><<<L.sms * 4, 128, 0, s>>>(st, perm, sk, b.tiles, b.ntiles,
+                                     b.tile_ctr + 3, (const R*)b.su, (const R*)b.sp, (R*)b.acc, R(1), c, b.err,
+                                     b.fallbacks)));
+            else
+                APIC_DISPATCH(h, (k_force_lambda1<D, O, R><<<L.sms * 4, 128, 0, s>>>(st, perm, sk, b.tiles, b.ntiles,
+                                     b.tile_ctr + 3, (const R*)b.su, (R*)b.acc, c, b.err, b.fallbacks)));
+            e = cudaGetLastError();
+            *kernels += 1;
+        };
+        if (h.dim == 3) k_grid_velocity<3, R><<<ggrid, TPB, 0, s>>>((R*)b.acc, (R*)b.vel1, b.flags, c);
+        else k_grid_velocity<2, R><<<ggrid, TPB, 0, s>>>((R*)b.acc, (R*)b.vel1, b.flags, c);
+        e = cudaGetLastError();
+        *kernels += 1;
+        // dv = 0 and |v|_M (from u = v / 2 + dv / 4 with dv = 0: |v|_M^2 = 4 <u, u>_M, taken with
+        // op 1 on a zero force: r = -dv = 0 is not it, so use the velocity itself)
+        const size_t gbytes = (size_t)h.nblocks * (h.dim == 3 ? 64 : 16) * 4 * sizeof(R);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b.sdv, 0, gbytes, s);
+        double vnorm2 = 0.0;
+        if (e == cudaSuccess) {
+            if (h.dim == 3) k_solve_step<3, R><<<parts, TPB, 0, s>>>(SolveVecs{b.vel1, b.sdv, b.su, b.sr, b.sp, b.ss, b.sdu, b.vel1, b.vel},
+                                                                       b.flags, c, 7, 0.0, b.mom_part);
+            else k_solve_step<2, R><<<parts, TPB, 0, s>>>(SolveVecs{b.vel1, b.sdv, b.su, b.sr, b.sp, b.ss, b.sdu, b.vel1, b.vel},
+                                                            b.flags, c, 7, 0.0, b.mom_part);
+            e = cudaGetLastError();
+            *kernels += 1;
+        }
+        if (e == cudaSuccess) e = read_dot(b, parts, s, &vnorm2);
+        const double vnorm = sqrt(vnorm2) > 1e-300 ? sqrt(vnorm2) : 1e-300;
+        for (int it = 0; it < h.newton_max && e == cudaSuccess; ++it) {
+            step(0, 0.0);                       // u = v / 2 + dv / 4
+            force(false);                       // acc = dt f at x + dt u
+            double rr = 0.0;
+            step(1, 0.0);                       // r = dt f / m - dv, p = r, du = 0
+            if (e == cudaSuccess) e = read_dot(b, parts, s, &rr);
+            const double rn0 = sqrt(rr);
+            stats[2] = rn0 / vnorm;
+            if (e != cudaSuccess || rn0 <= h.solve_tol * vnorm) break;
+            stats[0] += 1.0;
+            double gamma = rr;
+            for (int k = 0; k < h.cg_max && gamma > 0.0 && e == cudaSuccess; ++k) {
+                force(true);                    // acc = df/dx~ p
+                double ps = 0.0;
+                step(2, 0.0);                   // s = p - dt^2/4 acc / m
+                if (e == cudaSuccess) e = read_dot(b, parts, s, &ps);
+                if (e != cudaSuccess || !(ps > 0.0)) break;
+                const double alpha = gamma / ps;
+                double kappa = 0.0;
+                step(3, alpha);                 // du += alpha p, r -= alpha s
+                if (e == cudaSuccess) e = read_dot(b, parts, s, &kappa);
+                stats[1] += 1.0;
+                if (e != cudaSuccess || sqrt(kappa) <= h.solve_tol * rn0) break;
+                step(4, kappa / gamma);         // p = r + beta p
+                gamma = kappa;
+            }
+            step(5, 0.0);                       // dv += du
+        }
+        step(6, 0.0);                           // v~ = v + dv, u = (v + v~) / 2
+        if (e == cudaSuccess) {
+            k_clear_flags<R><<<ggrid, TPB, 0, s>>>(b.flags, h.nblocks);
+            e = cudaGetLastError();
+            *kernels += 1;
+        }
+        (void)dt;
+        return e;
     }
     static cudaError_t adapt_dt(const HostCfg& h, const Buffers& b, double nu, double dt_max, int first, cudaStream_t s)
     {
@@ -2032,6 +2137,12 @@ template <typename R> struct Impl {
                                   const Launch& L, cudaStream_t s)                                              \
     {                                                                                                           \
         return Impl<R>::g2p_lambda1(c, b, cur, perm, n, L, s);                                                  \
+    }                                                                                                           \
+    cudaError_t grid_update_midpoint_##SFX(const HostCfg& c, const Buffers& b, int cur, const uint32_t* skeys, \
+                                           const uint32_t* perm, int64_t n, const Launch& L, cudaStream_t s,    \
+                                           double* stats, int64_t* kernels)                                     \
+    {                                                                                                           \
+        return Impl<R>::grid_update_midpoint(c, b, cur, skeys, perm, n, L, s, stats, kernels);                  \
     }                                                                                                           \
     cudaError_t set_materials_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const double* E,   \
                                     const double* nu, cudaStream_t s)                                          \
