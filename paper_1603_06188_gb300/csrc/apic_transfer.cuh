@@ -712,85 +712,20 @@ __device__ __forceinline__ void stage_part(R* slot, const PState<R>& s, uint32_t
     }
 }
 
-// Pairs of reals (x, y) = a lane's two sums, or one value duplicated, with fused pair
-// arithmetic: FP32 pairs are the packed fma.rn.f32x2 / mul / add (each component rounded as
-// its scalar counterpart), FP64 pairs two scalar operations.
-template <typename R> struct PairOf;
-template <> struct PairOf<float> { using T = float2; };
-template <> struct PairOf<double> { using T = double2; };
-template <typename R> using pair_t = typename PairOf<R>::T;
-__device__ __forceinline__ float2 pmake(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ double2 pmake(double a, double b) { return make_double2(a, b); }
-__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c)
-{
-    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
-}
-__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ double2 pmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
-__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ double2 padd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-
-// One axis of the B-spline stencil as duplicated pairs: w_i, the derivative dw_i (grid units)
-// and (i - fx) w_i, i = 0 .. ORDER, from the offset o in cell `cell` (Sec. 3.5; the same
-// polynomials as axis_weights)
-template <int ORDER, typename R>
-__device__ __forceinline__ void axis_weights_pair(R o, int cell, int& base, R& fx, pair_t<R>* w, pair_t<R>* dw,
-                                                  pair_t<R>* rw)
-{
-    using P = pair_t<R>;
-    if (ORDER == 2) {
-        const bool hi = o >= R(0.5);
-        base = hi ? cell : cell - 1;
-        fx = hi ? o : o + R(1);
-        const P f = pmake(fx, fx);
-        const P t0 = padd(pmake(R(1.5), R(1.5)), pmake(-fx, -fx));
-        const P t1 = padd(f, pmake(R(-1), R(-1)));
-        const P t2 = padd(f, pmake(R(-0.5), R(-0.5)));
-        const P half = pmake(R(0.5), R(0.5));
-        w[0] = pmul(half, pmul(t0, t0));
-        w[1] = pfma(pmake(-t1.x, -t1.y), t1, pmake(R(0.75), R(0.75)));
-        w[2] = pmul(half, pmul(t2, t2));
-        dw[0] = pmake(-t0.x, -t0.y);
-        dw[1] = pmul(pmake(R(-2), R(-2)), t1);
-        dw[2] = t2;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) rw[i] = pmul(padd(pmake(R(i), R(i)), pmake(-fx, -fx)), w[i]);
-    } else {
-        base = cell - 1;
-        fx = o + R(1);
-        const R a0 = R(2) - fx, a1 = fx - R(1);   // |t| of nodes 0 and 2 is a0, of nodes 1 and 3 (2 - |t|) a1
-        const P A0 = pmake(a0, a0), A1 = pmake(a1, a1);
-        const P A0s = pmul(A0, A0), A1s = pmul(A1, A1);
-        const P sixth = pmake(R(1) / R(6), R(1) / R(6)), half = pmake(R(0.5), R(0.5));
-        const P twothirds = pmake(R(2) / R(3), R(2) / R(3));
-        w[0] = pmul(sixth, pmul(A0s, A0));
-        w[1] = padd(pfma(half, pmul(A1s, A1), pmake(-A1s.x, -A1s.y)), twothirds);
-        w[2] = padd(pfma(half, pmul(A0s, A0), pmake(-A0s.x, -A0s.y)), twothirds);
-        w[3] = pmul(sixth, pmul(A1s, A1));
-        const P m2 = pmake(R(-2), R(-2)), p15 = pmake(R(1.5), R(1.5));
-        dw[0] = pmul(pmake(R(-0.5), R(-0.5)), A0s);
-        dw[1] = pfma(p15, A1s, pmul(m2, A1));
-        const P d2 = pfma(p15, A0s, pmul(m2, A0));
-        dw[2] = pmake(-d2.x, -d2.y);
-        dw[3] = pmul(half, A1s);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) rw[i] = pmul(padd(pmake(R(i), R(i)), pmake(-fx, -fx)), w[i]);
-    }
-}
-
-// One particle's two sums per node of the lane's stencil part added into acc (pairs).
+// One particle's two sums per node of the lane's stencil part added into accA / accB.
 // h: 0 = momentum components (0, 1), 1 = (component 2, mass); zs: the lane's z-half.
 template <int ORDER, typename R>
 __device__ __forceinline__ void p2g_split_particle(const R* slot, bool live, int h, int zs, const int* lb, const int* bo,
                                                    const DevCfg<R>& c, uint32_t* err, R m, R sC, R dt_dx,
-                                                   bool with_tau, pair_t<R>* acc)
+                                                   bool with_tau, R* accA, R* accB)
 {
     using S = SplitShape<ORDER>;
-    using P = pair_t<R>;
     constexpr int K = S::K;
     constexpr int KZ = S::KZ;
     const V4<R> a = *reinterpret_cast<const V4<R>*>(slot + 0);
+    const V4<R> v = *reinterpret_cast<const V4<R>*>(slot + 4);
+    const V4<R> ba = *reinterpret_cast<const V4<R>*>(slot + 8);
+    const V4<R> bb = *reinterpret_cast<const V4<R>*>(slot + 12);
     R o[3] = {a.x, a.y, a.z};
     int cell[3];
     unpack_cell<3>(r2u(a.w), cell);
@@ -801,90 +736,73 @@ __device__ __forceinline__ void p2g_split_particle(const R* slot, bool live, int
             cell[d] = bo[d] + lb[d] + (ORDER == 3 ? 1 : 0);
         }
     }
-    // a particle outside the tile's reach is reported and adds nothing
-    bool ok = true;
+    int base[3];
+    R w[3][K], dw[3][K], fx[3];
+    bool ok = particle_stencil<3, ORDER, R>(o, cell, c, base, fx, w, dw);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const int b = (ORDER == 2) ? (o[d] >= R(0.5) ? cell[d] : cell[d] - 1) : cell[d] - 1;
-        if (b - bo[d] != lb[d] || b < 0 || b + ORDER > c.res[d] - 1) ok = false;
-    }
+    for (int d = 0; d < 3; ++d)
+        if (base[d] - bo[d] != lb[d]) ok = false;
     if (live && !ok) {
         set_err(err, APIC_ERRBIT_RANGE);
         live = false;
     }
-    if (!ok) {
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            o[d] = R(0.5);
-            cell[d] = bo[d] + lb[d] + (ORDER == 3 ? 1 : 0);
-        }
-    }
-    // the lane's two rows as pairs: velocity (times m), B row (times m / (kappa dx)), tau row
-    // (times -dt/dx); the mass row is (1, 0, 0).  A neutral lane's slot may hold anything (even
-    // NaN), so its rows are selected to zero rather than scaled by zero.
+    // the lane's two rows: velocity, B row (affine), tau row (stress); the mass row is (1, 0, 0).
+    // A neutral lane's slot may hold anything (even NaN), so its rows are selected to zero
+    // rather than scaled by zero.
     const bool hi = h != 0;
     const bool tau_on = live && with_tau;
-    P mv, C[3], nT[3];
+    const R mvA = live ? m * (hi ? v.z : v.x) : R(0);
+    const R mvB = live ? (hi ? m : m * v.y) : R(0);
+    R CA[3], CB[3], TA[3], TB[3];
+    CA[0] = live ? sC * (hi ? bb.y : v.w) : R(0);
+    CA[1] = live ? sC * (hi ? bb.z : ba.x) : R(0);
+    CA[2] = live ? sC * (hi ? bb.w : ba.y) : R(0);
+    CB[0] = (live && !hi) ? sC * ba.z : R(0);
+    CB[1] = (live && !hi) ? sC * ba.w : R(0);
+    CB[2] = (live && !hi) ? sC * bb.x : R(0);
     {
-        const V4<R> v = *reinterpret_cast<const V4<R>*>(slot + 4);
-        const V4<R> ba = *reinterpret_cast<const V4<R>*>(slot + 8);
-        const V4<R> bb = *reinterpret_cast<const V4<R>*>(slot + 12);
         const V4<R> ta = *reinterpret_cast<const V4<R>*>(slot + 16);   // t00 t11 t22 t01
         const V2<R> tb = *reinterpret_cast<const V2<R>*>(slot + 20);   // t02 t12
-        const P z = pmake(R(0), R(0));
-        mv = live ? pmake(m * (hi ? v.z : v.x), hi ? m : m * v.y) : z;
-        C[0] = live ? pmake(sC * (hi ? bb.y : v.w), hi ? R(0) : sC * ba.z) : z;
-        C[1] = live ? pmake(sC * (hi ? bb.z : ba.x), hi ? R(0) : sC * ba.w) : z;
-        C[2] = live ? pmake(sC * (hi ? bb.w : ba.y), hi ? R(0) : sC * bb.x) : z;
-        const R nt = -dt_dx;
-        nT[0] = tau_on ? pmake(nt * (hi ? tb.x : ta.x), hi ? R(0) : nt * ta.w) : z;
-        nT[1] = tau_on ? pmake(nt * (hi ? tb.y : ta.w), hi ? R(0) : nt * ta.y) : z;
-        nT[2] = tau_on ? pmake(nt * (hi ? ta.z : tb.x), hi ? R(0) : nt * tb.y) : z;
+        TA[0] = tau_on ? dt_dx * (hi ? tb.x : ta.x) : R(0);
+        TA[1] = tau_on ? dt_dx * (hi ? tb.y : ta.w) : R(0);
+        TA[2] = tau_on ? dt_dx * (hi ? ta.z : tb.x) : R(0);
+        TB[0] = (tau_on && !hi) ? dt_dx * ta.w : R(0);
+        TB[1] = (tau_on && !hi) ? dt_dx * ta.y : R(0);
+        TB[2] = (tau_on && !hi) ? dt_dx * tb.y : R(0);
     }
-    // separable sums as in the cell-parallel kernel, for the lane's two rows and z-half:
+    // separable sums as in the cell-parallel kernel, for the lane's two rows and z-half
     //   sum_c(i,j,k) = w0_i P_c(j,k) + E_c(i) S(j,k),  S = w1_j w2_k
     //   P_c(j,k) = w1_j Q_c(k) + H_c(j) w2_k,  Q_c(k) = mv_c w2_k + C_c2 (r w)2_k - T_c2 dw2_k
     //   H_c(j) = C_c1 (r w)1_j - T_c1 dw1_j,    E_c(i) = C_c0 (r w)0_i - T_c0 dw0_i
-    // The stencil is formed axis by axis, so each axis's derivative and (i - fx) w terms die as
-    // soon as its factor (E, H, or Q of the lane's z nodes) is formed.
-    int base[3];
-    R fx[3];
-    P w0[K], w1[K], E[K], H[K], wz[KZ], Q[KZ];
-    {
-        P w[K], dw[K], rw[K];
-        axis_weights_pair<ORDER, R>(o[2], cell[2], base[2], fx[2], w, dw, rw);
-        const bool up = ORDER == 3 && zs;   // upper z-half: a select, so the weights stay in registers
+    R EA[K], EB[K], HA[K], HB[K];
 #pragma unroll
-        for (int icl = 0; icl < KZ; ++icl) {
-            wz[icl] = up ? w[(KZ + icl) % K] : w[icl];
-            const P dwz = up ? dw[(KZ + icl) % K] : dw[icl];
-            const P rwz = up ? rw[(KZ + icl) % K] : rw[icl];
-            Q[icl] = pfma(mv, wz[icl], pfma(C[2], rwz, pmul(nT[2], dwz)));
-        }
-    }
-    {
-        P dw[K], rw[K];
-        axis_weights_pair<ORDER, R>(o[0], cell[0], base[0], fx[0], w0, dw, rw);
-#pragma unroll
-        for (int i = 0; i < K; ++i) E[i] = pfma(C[0], rw[i], pmul(nT[0], dw[i]));
-    }
-    {
-        P dw[K], rw[K];
-        axis_weights_pair<ORDER, R>(o[1], cell[1], base[1], fx[1], w1, dw, rw);
-#pragma unroll
-        for (int i = 0; i < K; ++i) H[i] = pfma(C[1], rw[i], pmul(nT[1], dw[i]));
+    for (int i = 0; i < K; ++i) {
+        const R rw0 = (R(i) - fx[0]) * w[0][i], rw1 = (R(i) - fx[1]) * w[1][i];
+        EA[i] = CA[0] * rw0 - TA[0] * dw[0][i];
+        EB[i] = CB[0] * rw0 - TB[0] * dw[0][i];
+        HA[i] = CA[1] * rw1 - TA[1] * dw[1][i];
+        HB[i] = CB[1] * rw1 - TB[1] * dw[1][i];
     }
 #pragma unroll
     for (int icl = 0; icl < KZ; ++icl) {
+        // the lane's z node: icl, or KZ + icl in the upper half (a select, so the weights
+        // stay in registers)
+        const R w2 = (ORDER == 3 && zs) ? w[2][(KZ + icl) % K] : w[2][icl];
+        const R dw2 = (ORDER == 3 && zs) ? dw[2][(KZ + icl) % K] : dw[2][icl];
+        const R z = (ORDER == 3 && zs) ? R(KZ + icl) : R(icl);
+        const R rw2 = (z - fx[2]) * w2;
+        const R QA = mvA * w2 + CA[2] * rw2 - TA[2] * dw2;
+        const R QB = mvB * w2 + CB[2] * rw2 - TB[2] * dw2;
 #pragma unroll
         for (int ib = 0; ib < K; ++ib) {
-            const P Sp = pmul(w1[ib], wz[icl]);
-            const P Pp = pfma(w1[ib], Q[icl], pmul(H[ib], wz[icl]));
+            const R S = w[1][ib] * w2;
+            const R PA = w[1][ib] * QA + HA[ib] * w2;
+            const R PB = w[1][ib] * QB + HB[ib] * w2;
 #pragma unroll
             for (int ia = 0; ia < K; ++ia) {
                 const int j = ia + K * ib + K * K * icl;
-                acc[j] = pfma(w0[ia], Pp, acc[j]);
-                acc[j] = pfma(E[ia], Sp, acc[j]);
+                fma_pair<R>(accA[j], accB[j], w[0][ia], w[0][ia], PA, PB);
+                fma_pair<R>(accA[j], accB[j], EA[ia], EB[ia], S, S);
             }
         }
     }
@@ -928,9 +846,9 @@ __device__ __forceinline__ void p2g_split_tile(const PState<R>& st, const uint32
     // instruction stream; lanes past their run carry a neutral particle that adds zeros
     const uint32_t iters = __reduce_max_sync(FULLMASK, run);
     if (iters > 0u) {
-        pair_t<R> acc2[K * K * KZ];
+        R accA[K * K * KZ], accB[K * K * KZ];
 #pragma unroll
-        for (int i = 0; i < K * K * KZ; ++i) acc2[i] = pmake(R(0), R(0));
+        for (int i = 0; i < K * K * KZ; ++i) { accA[i] = R(0); accB[i] = R(0); }
         R* gslots = pslots + (size_t)grp * NSL * SW;
         // particles 0 .. NSL-2 of the run first; particle it + NSL - 1 goes into the slot read
         // in the previous iteration (every lane of the warp has passed this iteration's
@@ -952,7 +870,7 @@ __device__ __forceinline__ void p2g_split_tile(const PState<R>& st, const uint32
                 if (nx + 1 < run) qn = perm[kb + nx + 1];
             }
             p2g_split_particle<ORDER, R>(gslots + (it % NSL) * SW, it < run, h, zs, lb, bo, c, err, m, sC, dt_dx,
-                                         with_tau, acc2);
+                                         with_tau, accA, accB);
         }
         cp_async_wait<0>();
         if (run > 0u) {
@@ -965,7 +883,7 @@ __device__ __forceinline__ void p2g_split_tile(const PState<R>& st, const uint32
                     for (int ia = 0; ia < K; ++ia) {
                         const int jl = ia + K * ib + K * K * icl;
                         const int j = ia + K * ib + K * K * (zs * KZ + icl);
-                        *reinterpret_cast<V2<R>*>(dst + 4 * j) = V2<R>{acc2[jl].x, acc2[jl].y};
+                        *reinterpret_cast<V2<R>*>(dst + 4 * j) = V2<R>{accA[jl], accB[jl]};
                     }
         }
     }

@@ -33,6 +33,7 @@ CASES = [
     (3, 3, 64, 24, 8, "fcr"),
     (2, 2, 64, 64, 4, "fcr"),
     (2, 3, 64, 64, 4, "fcr"),
+    (2, 3, 64, 64, 4, "nh"),
 ]
 
 
