@@ -482,10 +482,22 @@ def run_drift(args) -> int:
                                                      "oracle_seconds": secs_a, "rows": rows_a},
            "b": {"workload": f"spheres{res3}", "particles": sp.n, "steps": 2000, "rows": rows_b}}
     print(json.dumps(out), flush=True)
+    path = args.drift_out or os.path.join(ROOT, "profiles", "drift_fp32.md")
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    with open(path, "w") as f:
+        f.write(drift_markdown(out))
+    return 0
+
+
+def drift_markdown(out: dict) -> str:
+    """The drift record of run_drift as a Markdown summary."""
+    rows_a, rows_b = out["a"]["rows"], out["b"]["rows"]
+    na, nb = out["a"]["particles"], out["b"]["particles"]
+    res, res3 = 64, 128
     lines = ["# Drift of the FP32 path over many steps", "",
              "Written by `python bench.py --workload drift` (one GB300).  Every figure is the largest",
              "error over all particles, normwise relative (||a - b||_inf / ||b||_inf) unless stated.", "",
-             f"## (a) FP32 GPU against the FP64 oracle: cube {res}^3, side 0.4, 8 ppc ({sc.n} particles),",
+             f"## (a) FP32 GPU against the FP64 oracle: cube {res}^3, side 0.4, 8 ppc ({na} particles),",
              "fixed-corotated E = 1e4, nu = 0.3, rho = 1, gravity, sticky walls, dt = 2e-5, rotating and",
              "deformed (F = I + 0.02 U(-1, 1)); both from the same state, 200 steps.", "",
              "| step | v | B | F | x (cells) | p: GPU - oracle | l: GPU - oracle |", "|---:|---:|---:|---:|---:|---:|---:|"]
@@ -494,7 +506,7 @@ def run_drift(args) -> int:
                      f"{r['p_gpu_minus_oracle']:.2e} | {r['l_gpu_minus_oracle']:.2e} |")
     lines += ["", "p and l differences are relative to sum m |v| and sum m |x| |v|.", "",
               f"## (b) FP32 GPU against FP64 GPU: two cubic-spline spheres at {res3}^3, r = 0.15, 8 ppc",
-              f"({sp.n} particles), +-1, fixed-corotated E = 5e4, nu = 0.4, dt = 5e-6, sticky walls, 2000 steps;",
+              f"({nb} particles), +-1, fixed-corotated E = 5e4, nu = 0.4, dt = 5e-6, sticky walls, 2000 steps;",
               "the FP64 run starts from the FP32 run's state.", "",
               "| step | v | B | F | x (cells) | p drift FP32 | p drift FP64 | l drift FP32 | l drift FP64 |",
               "|---:|---:|---:|---:|---:|---:|---:|---:|---:|"]
@@ -504,10 +516,7 @@ def run_drift(args) -> int:
     lines += ["", "Drift columns: |p(step) - p(0)| and |l(step) - l(0)| relative to sum m |v| of the FP64 state.",
               "No wall is reached and there is no gravity, so both runs should keep p and l up to rounding;",
               "the spheres meet near step 1000.", ""]
-    os.makedirs(os.path.join(ROOT, "profiles"), exist_ok=True)
-    with open(os.path.join(ROOT, "profiles", "drift_fp32.md"), "w") as f:
-        f.write("\n".join(lines))
-    return 0
+    return "\n".join(lines)
 
 
 def aggregate(local_ms: float, local_units: float, dist=None, device=None):
@@ -742,11 +751,20 @@ def main():
                     help="only the headline workload (no spheres256 / batched / serving blocks)")
     ap.add_argument("--block-sims", type=int, default=128, help="simulations of the batched block")
     ap.add_argument("--block-requests", type=int, default=100, help="requests of the serving block")
+    ap.add_argument("--drift-out", default=None, help="drift workload: where the Markdown record goes")
+    ap.add_argument("--drift-from-json", default=None,
+                    help="render the drift record from a saved JSON line of --workload drift (no GPU)")
     ap.add_argument("--p2g-kernel", type=int, default=0)
     ap.add_argument("--tile", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.drift_from_json:
+        line = [ln for ln in open(args.drift_from_json) if ln.startswith("{")][-1]
+        path = args.drift_out or os.path.join(ROOT, "profiles", "drift_fp32.md")
+        with open(path, "w") as f:
+            f.write(drift_markdown(json.loads(line)))
+        return 0
     world, rank, local, dist = dist_setup(args.gpus)
     if args.impl == "reference":
         return run_reference(args, world, rank)

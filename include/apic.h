@@ -270,10 +270,15 @@ typedef struct {
     int64_t max_particles;       /* total particles over the members */
     int64_t max_blocks;          /* total node blocks (4^d nodes) over the members' grids */
     int tile_particles;          /* 1024, 2048 or 4096 particles per tile; 0 = 4096 */
-    int group;                   /* lanes sharing one cell in P2G: 1, 2, 4 or 8; 0 = 8 */
+    int group;                   /* P2G: lanes sharing one cell in the cell-parallel kernel, 1, 2,
+                                    4 or 8, or APIC_BATCH_SPLIT for the component-split kernel
+                                    (3-D); 0 = APIC_BATCH_SPLIT in 3-D, 8 in 2-D */
     int use_graph;               /* 1 = replay each step as a captured CUDA graph (needs a
                                     non-NULL stream) */
 } apic_batch_config;
+
+/* apic_batch_config.group value selecting the component-split P2G kernel (3-D) */
+#define APIC_BATCH_SPLIT 16
 
 apic_status apic_batch_workspace_size(const apic_batch_config* cfg, size_t* bytes);
 
@@ -324,11 +329,12 @@ apic_status apic_batch_run(apic_batch* batch, int max_steps, apic_sim** finished
 /* Device bytes of the members admitted with apic_batch_admit and still resident. */
 apic_status apic_batch_resident_bytes(apic_batch* batch, int64_t* bytes);
 
-/* Tile size and P2G lane group for the following steps (0 keeps the current value). */
+/* Tile size and P2G lane group (as apic_batch_config.group) for the following steps (0 keeps
+ * the current value). */
 apic_status apic_batch_set_tuning(apic_batch* batch, int tile_particles, int group);
 
 /* Autotuner: times `steps` batched steps for every candidate (tile 1024 / 2048 / 4096 x
- * group 1 / 2 / 4 / 8), keeps the fastest and reports it.  The trial steps are real steps of the
+ * group 1 / 2 / 4 / 8 / APIC_BATCH_SPLIT in 3-D), keeps the fastest and reports it.  The trial steps are real steps of the
  * members.  Results are cached per (dim, order, precision, particle-count bucket) for the
  * life of the process; force = 1 re-measures.  Synchronising. */
 apic_status apic_batch_autotune(apic_batch* batch, int steps, int force, int* tile_particles, int* group);

@@ -269,6 +269,7 @@ def apic_last_error(sim) -> str:
 
 
 APIC_SORT_NOALLOC_MAX_KEYS = 1 << 20
+APIC_BATCH_SPLIT = 16
 
 
 def apic_sort_keys_noalloc(keys, n: int, key_bits: int, sorted_keys, perm, stream_ptr: int = 0) -> int:

@@ -1168,8 +1168,9 @@ apic_status apic_batch_create(const apic_batch_config* c, void* workspace, size_
     if (c->max_sims <= 0 || c->max_sims > 12000 || c->max_particles <= 0 || c->max_blocks <= 0) return APIC_ERR_ARG;
     const int tile = c->tile_particles == 0 ? 4096 : c->tile_particles;
     if (tile != 1024 && tile != 2048 && tile != 4096) return APIC_ERR_ARG;
-    const int group = c->group == 0 ? 8 : c->group;
-    if (group != 1 && group != 2 && group != 4 && group != 8) return APIC_ERR_ARG;
+    const int group = c->group == 0 ? (c->dim == 3 ? APIC_BATCH_SPLIT : 8) : c->group;
+    if (group != 1 && group != 2 && group != 4 && group != 8 && group != APIC_BATCH_SPLIT) return APIC_ERR_ARG;
+    if (group == APIC_BATCH_SPLIT && c->dim != 3) return APIC_ERR_ARG;
     if (!workspace || ((uintptr_t)workspace & 255)) return APIC_ERR_ARG;
     BatchLayout L = batch_layout(c);
     if (workspace_bytes < L.total) return APIC_ERR_OOM;
@@ -1370,7 +1371,8 @@ apic_status apic_batch_set_tuning(apic_batch* b, int tile, int group)
 {
     if (!b) return APIC_ERR_ARG;
     if (tile != 0 && tile != 1024 && tile != 2048 && tile != 4096) return APIC_ERR_ARG;
-    if (group != 0 && group != 1 && group != 2 && group != 4 && group != 8) return APIC_ERR_ARG;
+    if (group != 0 && group != 1 && group != 2 && group != 4 && group != 8 && group != APIC_BATCH_SPLIT) return APIC_ERR_ARG;
+    if (group == APIC_BATCH_SPLIT && b->dim != 3) return APIC_ERR_ARG;
     if (tile) b->tile = tile;
     if (group) b->group = group;
     b->dirty = true;
@@ -1401,9 +1403,10 @@ apic_status apic_batch_autotune(apic_batch* b, int steps, int force, int* tile_o
     BCK(cudaEventCreate(&e1), "event");
     float best = 1e30f;
     int bt = b->tile, bg = b->group;
-    const int groups[4] = {1, 2, 4, 8};
+    const int groups[5] = {1, 2, 4, 8, APIC_BATCH_SPLIT};
     for (int tile : kBatchTiles)
         for (int group : groups) {
+            if (group == APIC_BATCH_SPLIT && b->dim != 3) continue;
             apic_batch_set_tuning(b, tile, group);
             apic_status st = batch_run(b, 1);   // warm-up (and graph capture)
             if (st != APIC_OK) return st;

@@ -97,6 +97,40 @@ __global__ void __launch_bounds__(128, 2) kb_p2g_cells(SimDesc<R>* __restrict__ 
     }
 }
 
+// the component-split P2G of k_p2g_split over the batch's tiles (3-D)
+template <int ORDER, typename R>
+__global__ void __launch_bounds__(SplitShape<ORDER>::NT, (split_ctas_per_sm<ORDER, R>()))
+    kb_p2g_split(SimDesc<R>* __restrict__ descs, const uint32_t* __restrict__ tile_sim,
+                 const uint32_t* __restrict__ tile_start, const uint32_t* __restrict__ ntiles_p,
+                 uint32_t* __restrict__ tile_ctr, int kpar)
+{
+    constexpr int NT = SplitShape<ORDER>::NT;
+    extern __shared__ __align__(32) unsigned char p2g_smem[];
+    R* cellsum = reinterpret_cast<R*>(p2g_smem);
+    R* pslots = reinterpret_cast<R*>(p2g_smem + (p2g_cellsum_bytes<3, ORDER, R>() + 31) / 32 * 32);
+    __shared__ uint32_t cbeg[64], cend[64];
+    __shared__ int s_tile;
+    __shared__ __align__(16) SimDesc<R> sd;
+    const int ntiles = (int)*ntiles_p;
+    int next = 0;
+    if (threadIdx.x == 0) next = (int)atomicAdd(tile_ctr, 1u);
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = next;
+        if (threadIdx.x < 64) { cbeg[threadIdx.x] = 0u; cend[threadIdx.x] = 0u; }
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= ntiles) break;
+        if (threadIdx.x == 0) next = (int)atomicAdd(tile_ctr, 1u);
+        const uint32_t sim = tile_sim[t];
+        load_desc<R>(&sd, descs + sim, NT);
+        __syncthreads();
+        const uint32_t start = tile_start[t];
+        const uint32_t end = tile_end(tile_sim, tile_start, t, ntiles, sim, (uint32_t)sd.c.n);
+        p2g_split_tile<ORDER, R>(sd.st[sd.cur], sd.vb[kpar], sd.kb[kpar], start, end, sd.acc, sd.flags, sd.c, sd.err,
+                                 cellsum, cbeg, cend, pslots);
+    }
+}
+
 template <int D, int ORDER, typename R, bool EXT>
 __global__ void __launch_bounds__(G2P_THREADS, 4) kb_g2p(SimDesc<R>* __restrict__ descs, const uint32_t* __restrict__ tile_sim,
                                               const uint32_t* __restrict__ tile_start,
@@ -207,9 +241,20 @@ template <typename R> struct BatchImpl {
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(g2p_per_sm, kb_g2p<D, O, R, false>, G2P_THREADS, 0);
         return e;
     }
-    // lane groups of 1, 2, 4 or 8 per base cell (fewer lanes suit fewer particles per cell)
+    template <int O> static cudaError_t setup_split(int* p2g_per_sm, int* g2p_per_sm)
+    {
+        const int smem = (int)p2g_split_smem<O, R>();
+        cudaError_t e = cudaFuncSetAttribute(kb_p2g_split<O, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, kb_p2g_split<O, R>, SplitShape<O>::NT, smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(g2p_per_sm, kb_g2p<3, O, R, false>, G2P_THREADS, 0);
+        return e;
+    }
+    // lane groups of 1, 2, 4 or 8 per base cell (fewer lanes suit fewer particles per cell), or
+    // the component-split kernel (group 16, 3-D)
     template <int D, int O> static cudaError_t setup_dg(int group, int* p, int* g)
     {
+        if (D == 3 && group == 16) return setup_split<O>(p, g);
         if (group == 8) return setup_one<D, O, 8>(p, g);
         if (group == 2) return setup_one<D, O, 2>(p, g);
         if (group == 1) return setup_one<D, O, 1>(p, g);
@@ -233,7 +278,10 @@ template <typename R> struct BatchImpl {
     static void p2g_dg(int group, void* descs, const uint32_t* ts, const uint32_t* tst, const uint32_t* nt,
                        uint32_t* ctr, int kpar, int grid, cudaStream_t s)
     {
-        if (group == 8) p2g_one<D, O, 8>(descs, ts, tst, nt, ctr, kpar, grid, s);
+        if (D == 3 && group == 16)
+            kb_p2g_split<O, R><<<grid, SplitShape<O>::NT, p2g_split_smem<O, R>(), s>>>((SimDesc<R>*)descs, ts, tst, nt,
+                                                                                      ctr, kpar);
+        else if (group == 8) p2g_one<D, O, 8>(descs, ts, tst, nt, ctr, kpar, grid, s);
         else if (group == 2) p2g_one<D, O, 2>(descs, ts, tst, nt, ctr, kpar, grid, s);
         else if (group == 1) p2g_one<D, O, 1>(descs, ts, tst, nt, ctr, kpar, grid, s);
         else p2g_one<D, O, 4>(descs, ts, tst, nt, ctr, kpar, grid, s);

@@ -824,7 +824,12 @@ __device__ __forceinline__ void p2g_split_tile(const PState<R>& st, const uint32
     constexpr int NSL = S::NSL;
     constexpr int NVAL = K * K * K * 4;
     constexpr int SW = slot_words<3>();
-    const int grp = threadIdx.x / LPC;        // the base cell of the block this group takes
+    // lane group grp takes base cell `cell` of the block; the cells of a warp are spread over
+    // the whole block (one in every NT / 32), so a block that is only partly filled (a body's
+    // surface) still gives every warp about the same work and the warps meet at the tile's
+    // barriers together
+    const int grp = threadIdx.x / LPC;
+    const int cell = (grp % (32 / LPC)) * (NT / 32) + grp / (32 / LPC);
     const int r = threadIdx.x % LPC;
     const int h = r & 1;
     const int zs = (ORDER == 3) ? (r >> 1) : 0;
@@ -839,8 +844,8 @@ __device__ __forceinline__ void p2g_split_tile(const PState<R>& st, const uint32
     for (int d = 0; d < 3; ++d) bo[d] *= 4;
     tile_cell_runs<3>(skeys, start, end, cbeg, cend, NT);
     __syncthreads();
-    const uint32_t kb = cbeg[grp], ke = cend[grp];
-    const int lb[3] = {grp & 3, (grp >> 2) & 3, (grp >> 4) & 3};
+    const uint32_t kb = cbeg[cell], ke = cend[cell];
+    const int lb[3] = {cell & 3, (cell >> 2) & 3, (cell >> 4) & 3};
     const uint32_t run = ke - kb;
     // warp-uniform trip count (the longest run among the warp's cells): all lanes follow one
     // instruction stream; lanes past their run carry a neutral particle that adds zeros
@@ -874,7 +879,7 @@ __device__ __forceinline__ void p2g_split_tile(const PState<R>& st, const uint32
         }
         cp_async_wait<0>();
         if (run > 0u) {
-            R* dst = cellsum + (size_t)grp * NVAL + 2 * h;
+            R* dst = cellsum + (size_t)cell * NVAL + 2 * h;
 #pragma unroll
             for (int icl = 0; icl < KZ; ++icl)
 #pragma unroll
@@ -906,12 +911,17 @@ __global__ void __launch_bounds__(SplitShape<ORDER>::NT, (split_ctas_per_sm<ORDE
     __shared__ uint32_t cbeg[64], cend[64];
     __shared__ int s_tile;
     const int ntiles = (int)*ntiles_p;
+    // the next tile's index is requested when a tile starts, so its latency passes during the
+    // tile; thread 0 publishes it after the tile's last barrier
+    int next = 0;
+    if (threadIdx.x == 0) next = (int)atomicAdd(tile_ctr, 1u);
     for (;;) {
-        if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_ctr, 1u);
+        if (threadIdx.x == 0) s_tile = next;
         if (threadIdx.x < 64) { cbeg[threadIdx.x] = 0u; cend[threadIdx.x] = 0u; }
         __syncthreads();
         const int t = s_tile;
         if (t >= ntiles) break;
+        if (threadIdx.x == 0) next = (int)atomicAdd(tile_ctr, 1u);
         p2g_split_tile<ORDER, R>(st, perm, skeys, tiles[t], tiles[t + 1], acc, flags, c, err, cellsum, cbeg, cend,
                                  pslots);
     }
@@ -1719,7 +1729,9 @@ template <typename R> struct Impl {
     {
         if (n == 0) return cudaSuccess;
         DevCfg<R> c0 = HostToDev<R>::make(h, b, n);
-        if (h.integrator == 1) c0.model = 0;   // lambda = 1: the force is taken after the grid velocity
+        // lambda = 1 and the midpoint rule transfer mass and momentum alone: their force is taken
+        // after the grid velocity v_i
+        if (h.integrator != 0) c0.model = 0;
         PState<R> st = state_of<R>(b, cur);
         auto launch = [&](const DevCfg<R>& c, R* acc) {
         if (h.dim == 3 && h.p2g_kernel == 1) {

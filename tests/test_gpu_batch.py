@@ -62,12 +62,15 @@ def check_same(got, ref, tol=1e-5):
         assert np.abs(gx - rx).max() <= 1e-6
 
 
+@pytest.mark.parametrize("group", [0, 2, 8])
 @pytest.mark.parametrize("use_graph", [False, True])
-def test_batch_equals_alone(apic, use_graph):
+def test_batch_equals_alone(apic, use_graph, group):
+    """group 0: the component-split P2G (the 3-D default); 2, 8: the cell-parallel one."""
     members = make_members(apic, 6, seed=1)
     steps = 4
     ref = run_alone(apic, members, steps)
-    batch = apic.Batch(dim=3, order=2, max_sims=8, max_particles=300000, max_blocks=200000, use_graph=use_graph)
+    batch = apic.Batch(dim=3, order=2, max_sims=8, max_particles=300000, max_blocks=200000, use_graph=use_graph,
+                       group=group)
     sims = []
     for cfg, x, v, B, F in members:
         sim = apic.Sim(cfg, len(x))
@@ -124,8 +127,8 @@ def test_batch_autotune_keeps_results(apic):
         sim.upload(x, v, B, F)
         batch.add(sim)
         sims.append(sim)
-    tile, group = batch.autotune(steps=1, force=True)   # 12 candidates x (1 warm-up + 1 timed)
-    assert tile in (1024, 2048, 4096) and group in (1, 2, 4, 8)
+    tile, group = batch.autotune(steps=1, force=True)   # 15 candidates x (1 warm-up + 1 timed)
+    assert tile in (1024, 2048, 4096) and group in (1, 2, 4, 8, apic.APIC_BATCH_SPLIT)
     batch.step(1)
     check_same([s.download() for s in sims], ref)
     batch.close()

@@ -105,7 +105,10 @@ def test_lambda1_phases_match_oracle(apic, case, light):
     gf, bad = oracle.force_at(oc, x0, F0, vol, oc.dt * gv)
     assert bad == 0
     _, vt_ref = oracle.grid_update(oc, m_g, mv_g, gf)
-    assert relerr(vt_g, vt_ref) <= tol
+    # the updated grid velocity adds the force at the displaced F^ = (I + dt grad v) F, whose
+    # gradient the GPU gathers from its FP32 grid velocities: 3e-5 in FP32 (measured up to
+    # 1.4e-5, 2-D cubic Neo-Hookean), 1e-11 in FP64
+    assert relerr(vt_g, vt_ref) <= (3 * tol if prec == 32 else tol)
     # the velocity change alone, (v~ - v) m = dt (f + m g), away from the walls
     dv_g = (vt_g - gv) * m_g[:, None]
     dv_ref = (vt_ref - gv) * m_g[:, None]

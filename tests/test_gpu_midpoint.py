@@ -71,6 +71,10 @@ def test_midpoint_grid_solve_matches_oracle(apic, case):
     x0, v0, B0, F0 = sim.download()
     sim.p2g()
     m_g, mv_g = sim.grid("momentum")
+    # P2G transfers mass and momentum alone (the force enters the solve)
+    oc0 = oracle.make_cfg(dim=dim, order=order, res=(res,) * dim, dx=sc.dx, dt=oc.dt)
+    gm, gmv, _, _ = oracle.p2g(oc0, x0, v0, B0, F0, m, vol)
+    assert relerr(mv_g, gmv) <= (1e-11 if prec == 64 else 1e-5)
     sim.grid_update()
     st = sim.solve_stats()
     _, vt_g = sim.grid("velocity")
