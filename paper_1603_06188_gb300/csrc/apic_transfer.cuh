@@ -824,12 +824,12 @@ __device__ __forceinline__ void p2g_split_tile(const PState<R>& st, const uint32
     constexpr int NSL = S::NSL;
     constexpr int NVAL = K * K * K * 4;
     constexpr int SW = slot_words<3>();
-    // lane group grp takes base cell `cell` of the block; the cells of a warp are spread over
-    // the whole block (one in every NT / 32), so a block that is only partly filled (a body's
-    // surface) still gives every warp about the same work and the warps meet at the tile's
-    // barriers together
+    // lane group grp takes base cell grp of the block, so a warp's cells are neighbours in the
+    // sorted order (its staging reads stay close together; spreading a warp's cells over the
+    // whole block balanced the warps of partly filled blocks but cost more lane-iterations
+    // than it saved in barrier waits)
     const int grp = threadIdx.x / LPC;
-    const int cell = (grp % (32 / LPC)) * (NT / 32) + grp / (32 / LPC);
+    const int cell = grp;
     const int r = threadIdx.x % LPC;
     const int h = r & 1;
     const int zs = (ORDER == 3) ? (r >> 1) : 0;

@@ -119,7 +119,7 @@ def test_batch_membership_changes(apic):
 
 def test_batch_autotune_keeps_results(apic):
     members = make_members(apic, 4, seed=3)
-    ref = run_alone(apic, members, 1 + 12 * 2)
+    ref = run_alone(apic, members, 1 + 15 * 2)     # 15 candidates x (1 warm-up + 1 timed) + 1
     batch = apic.Batch(dim=3, order=2, max_sims=4, max_particles=200000, max_blocks=200000)
     sims = []
     for cfg, x, v, B, F in members:
@@ -127,7 +127,7 @@ def test_batch_autotune_keeps_results(apic):
         sim.upload(x, v, B, F)
         batch.add(sim)
         sims.append(sim)
-    tile, group = batch.autotune(steps=1, force=True)   # 15 candidates x (1 warm-up + 1 timed)
+    tile, group = batch.autotune(steps=1, force=True)
     assert tile in (1024, 2048, 4096) and group in (1, 2, 4, 8, apic.APIC_BATCH_SPLIT)
     batch.step(1)
     check_same([s.download() for s in sims], ref)
