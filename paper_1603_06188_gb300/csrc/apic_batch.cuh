@@ -64,7 +64,7 @@ __device__ __forceinline__ uint32_t tile_end(const uint32_t* tile_sim, const uin
 }
 
 template <int D, int ORDER, typename R, int G>
-__global__ void __launch_bounds__(128, 2) kb_p2g_cells(SimDesc<R>* __restrict__ descs,
+__global__ void __launch_bounds__(128, (cells_ctas_per_sm<D, ORDER>())) kb_p2g_cells(SimDesc<R>* __restrict__ descs,
                                                        const uint32_t* __restrict__ tile_sim,
                                                        const uint32_t* __restrict__ tile_start,
                                                        const uint32_t* __restrict__ ntiles_p,

@@ -634,8 +634,12 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
     __syncthreads();
 }
 
+// CTAs per SM of the cell-parallel P2G: three for 3-D quadratic (a 168-register cap that its
+// 108 accumulators fit without spilling), else two
+template <int D, int ORDER> __host__ __device__ constexpr int cells_ctas_per_sm() { return (D == 3 && ORDER == 2) ? 3 : 2; }
+
 template <int D, int ORDER, typename R, int G>
-__global__ void __launch_bounds__(128, 2) k_p2g_cells(PState<R> st, const uint32_t* __restrict__ perm,
+__global__ void __launch_bounds__(128, (cells_ctas_per_sm<D, ORDER>())) k_p2g_cells(PState<R> st, const uint32_t* __restrict__ perm,
                                                       const uint32_t* __restrict__ skeys,
                                                       const uint32_t* __restrict__ tiles,
                                                       const uint32_t* __restrict__ ntiles_p,

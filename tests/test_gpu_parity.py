@@ -162,12 +162,14 @@ def test_transfer_modes_and_transfer_only(apic, transfer):
 
 
 @pytest.mark.parametrize("tile", [256, 1024, 4096])
-@pytest.mark.parametrize("p2g_kernel", [0, 2])
+@pytest.mark.parametrize("p2g_kernel", [0, 1, 2])
 @pytest.mark.parametrize("dim,order,prec", [(3, 2, 32), (2, 2, 32), (2, 3, 32), (3, 2, 64), (2, 3, 64), (3, 3, 32),
                                             (3, 3, 64)])
 def test_p2g_kernels_and_tile_sizes_agree(apic, tile, p2g_kernel, dim, order, prec):
-    """Both P2G kernels (0: the default, component-split in 3-D; 2: cell-parallel) at every
-    tile size, against the oracle's grid."""
+    """Both P2G kernels (1: component-split, 3-D only; 2: cell-parallel; 0: the default) at
+    every tile size, against the oracle's grid."""
+    if p2g_kernel == 1 and dim == 2:
+        pytest.skip("the component-split kernel is 3-D only")
     r = run_one_step(apic, dim, order, prec, 32 if dim == 3 else 64, 8 if dim == 3 else 4, tile=tile,
                      p2g_kernel=p2g_kernel)
     x0, v0, B0, F0 = r["in"]
