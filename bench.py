@@ -77,6 +77,14 @@ STATE_BYTES_PER_PARTICLE = 6 * 16 + 8 + 16 + 8
 KERNEL_OF_PHASE = {"p2g": "k_p2g_cells", "grid_update": "k_grid_update", "g2p": "k_g2p"}
 
 
+def p2g_kernel_name(order: int, p2g_kernel: int) -> str:
+    """The P2G kernel the library runs for a 3-D simulation: the component-split one for cubic
+    B-splines by default (or when asked for), else the cell-parallel one."""
+    if p2g_kernel == 1 or (p2g_kernel == 0 and order == 3):
+        return "k_p2g_split"
+    return "k_p2g_cells"
+
+
 def make_scene(w: dict, seed: int = 0):
     from paper_1603_06188_gb300 import scenes
 
@@ -256,19 +264,22 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernels."""
+def recorded_traffic(kernel: str, workload: str, ppc: int):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernels
+    and the workload's standard density, with how it was taken (a capture of a smaller
+    case scaled to the full launch says so)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(p):
-        return None
+    if not os.path.exists(p) or ppc != WORKLOADS[workload]["ppc"]:
+        return None, None
     try:
         d = json.load(open(p))
         e = d.get(workload, {}).get(kernel)
         if e and e.get("source_hash") == kernel_source_hash():
-            return float(e["dram_bytes_per_launch"])
+            note = e["scaled_from"]["note"] if "scaled_from" in e else "one ncu capture of this launch"
+            return float(e["dram_bytes_per_launch"]), note
     except (ValueError, KeyError, TypeError):
-        return None
-    return None
+        return None, None
+    return None, None
 
 
 def batched_members(apic, count: int, seed: int, ppc: int = 8):
@@ -704,9 +715,10 @@ def single_block(args, wname: str, rank: int, world: int, local: int, dist, with
         algo = bp * sc.n + bn * active_nodes
         per_phase[name] = {"ms_per_launch": 1e3 * t_launch, "algorithmic_bytes": algo, "gbs": algo / t_launch / 1e9}
     dom = max(per_phase, key=lambda k: per_phase[k]["ms_per_launch"])
-    traffic = recorded_traffic(KERNEL_OF_PHASE[dom], wname)
-    roof = {"bound": "hbm", "kernel": KERNEL_OF_PHASE[dom], "achieved": per_phase[dom]["gbs"], "peak": peak,
-            "unit": "GB/s", "frac": per_phase[dom]["gbs"] / peak, "traffic": traffic,
+    kernel_of = dict(KERNEL_OF_PHASE, p2g=p2g_kernel_name(w["order"], args.p2g_kernel))
+    traffic, traffic_note = recorded_traffic(kernel_of[dom], wname, w["ppc"])
+    roof = {"bound": "hbm", "kernel": kernel_of[dom], "achieved": per_phase[dom]["gbs"], "peak": peak,
+            "unit": "GB/s", "frac": per_phase[dom]["gbs"] / peak, "traffic": traffic, "traffic_source": traffic_note,
             "peak_source": f"{peak_kind} hbm_gbs",
             "algorithmic_bytes_per_launch": per_phase[dom]["algorithmic_bytes"]}
     step_bytes = STEP_BYTES[0] * sc.n + STEP_BYTES[1] * active_nodes
@@ -716,7 +728,7 @@ def single_block(args, wname: str, rank: int, world: int, local: int, dist, with
     p2g_t = per_phase["p2g"]["ms_per_launch"] * 1e-3
     flops = P2G_FLOPS[w["order"]] * sc.n
     alu_peak = fp32_peak_flops(clk["sm_mhz"] if clk else None)
-    alu_roof = {"bound": "alu", "kernel": KERNEL_OF_PHASE["p2g"], "achieved": flops / p2g_t / 1e12,
+    alu_roof = {"bound": "alu", "kernel": kernel_of["p2g"], "achieved": flops / p2g_t / 1e12,
                 "peak": alu_peak / 1e12, "unit": "TFLOP/s", "frac": flops / p2g_t / alu_peak,
                 "flops_per_particle": P2G_FLOPS[w["order"]],
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x sampled SM clock"}
