@@ -101,14 +101,14 @@ def initial_state(sc, order):
     return sc.x, sc.v, B, F
 
 
-def lib_config(w, sc, precision=32, p2g_kernel=0, tile=0):
+def lib_config(w, sc, precision=32, p2g_kernel=0, tile=0, p2g_group=0):
     from paper_1603_06188_gb300 import apic
 
     vol = sc.dx ** 3 / w["ppc"]
     return apic.make_config(dim=3, order=w["order"], precision=precision, res=(w["res"],) * 3, dx=sc.dx,
                             dt=w["dt"], gravity=w["gravity"], boundary=w["boundary"], wall=w["order"] + 1,
                             model=w.get("model", "fcr"), E=w["E"], nu=w["nu"], particle_mass=w["rho"] * vol, particle_volume=vol,
-                            p2g_kernel=p2g_kernel, tile_particles=tile)
+                            p2g_kernel=p2g_kernel, tile_particles=tile, p2g_group=p2g_group)
 
 
 def oracle_config(w, sc):
@@ -657,7 +657,7 @@ def single_block(args, wname: str, rank: int, world: int, local: int, dist, with
         w["ppc"] = args.ppc
     sc = make_scene(w, seed=rank)
     x, v, B, F = initial_state(sc, w["order"])
-    cfg = lib_config(w, sc, p2g_kernel=args.p2g_kernel, tile=args.tile)
+    cfg = lib_config(w, sc, p2g_kernel=args.p2g_kernel, tile=args.tile, p2g_group=args.p2g_group)
     sim = apic.Sim(cfg, sc.n)
     sim.upload(x, v, B, F)
     stream = sim.stream
@@ -825,6 +825,8 @@ def main():
                     help="render the drift record from a saved JSON line of --workload drift (no GPU)")
     ap.add_argument("--p2g-kernel", type=int, default=0)
     ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--p2g-group", type=int, default=0,
+                    help="lanes per cell of the cell-parallel P2G (0: from the particle density)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

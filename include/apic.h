@@ -158,6 +158,22 @@ apic_status apic_upload(apic_sim* sim, int64_t n, const double* x, const double*
  * on_device = 0.  Errors: APIC_ERR_ARG, APIC_ERR_CUDA. */
 apic_status apic_upload_materials(apic_sim* sim, int64_t n, const double* E, const double* nu, int on_device);
 
+/* A mass and a volume per particle: mass[i] = m_p and vol[i] = V_p of the particle uploaded at
+ * index i (n = the count of the last apic_upload), each finite and > 0, in place of the
+ * configuration's `mass` and `vol`.  Sec. 3.2 gives every particle its own constant mass m_p
+ * (in m_i = sum_p m_p w_ip and the affine momentum sum), and Sec. 3.3 its own volume V_p (in
+ * the potential sum_p V_p Psi_p and the force sum_p V_p P_p F_p^T grad w_ip); the momentum
+ * diagnostics use m_p too.  The values are stored in the state's precision (FP32 in an FP32
+ * simulation) and the current stress is recomputed with V_p.  This call and
+ * apic_upload_materials set parts of the same per-particle parameters: what one of them
+ * does not give keeps its earlier per-particle value, or the configuration's if none was
+ * set.  Valid until the next apic_upload, which returns to the configuration's values.
+ * `on_device` as in apic_upload; host values are checked, device values are not.  Not
+ * allowed between apic_p2g and apic_g2p, nor while the simulation is in a batch (a member
+ * keeps its values in the batch).  Synchronising when on_device = 0.
+ * Errors: APIC_ERR_ARG, APIC_ERR_CUDA. */
+apic_status apic_upload_mass_volume(apic_sim* sim, int64_t n, const double* mass, const double* vol, int on_device);
+
 /* Copy the particle state back in upload order (any pointer may be NULL to skip that
  * field).  Synchronising.  Errors: APIC_ERR_ARG, APIC_ERR_CUDA, and a latched device error. */
 apic_status apic_download(apic_sim* sim, double* x, double* v, double* B, double* F, int on_device);

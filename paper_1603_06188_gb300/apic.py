@@ -92,6 +92,7 @@ SIGNATURES = {
     "apic_destroy": (C.c_int, [C.c_void_p]),
     "apic_upload": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "apic_upload_materials": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int]),
+    "apic_upload_mass_volume": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int]),
     "apic_download": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "apic_download_positions": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "apic_p2g": (C.c_int, [C.c_void_p]),
@@ -191,6 +192,10 @@ def apic_upload(sim, n, x, v=None, B=None, F=None, on_device=0):
 
 def apic_upload_materials(sim, n, E, nu, on_device=0):
     _check(load().apic_upload_materials(sim, n, _ptr(E), _ptr(nu), on_device), sim)
+
+
+def apic_upload_mass_volume(sim, n, mass, vol, on_device=0):
+    _check(load().apic_upload_mass_volume(sim, n, _ptr(mass), _ptr(vol), on_device), sim)
 
 
 def apic_download(sim, x=None, v=None, B=None, F=None, on_device=0):
@@ -404,6 +409,12 @@ class Sim:
         E = np.ascontiguousarray(np.broadcast_to(np.asarray(E, dtype=np.float64), (self.n,)))
         nu = np.ascontiguousarray(np.broadcast_to(np.asarray(nu, dtype=np.float64), (self.n,)))
         apic_upload_materials(self.handle, self.n, E, nu, on_device=0)
+
+    def upload_mass_volume(self, mass, vol):
+        """Mass m_p and volume V_p per particle (upload order); scalars broadcast."""
+        mass = np.ascontiguousarray(np.broadcast_to(np.asarray(mass, dtype=np.float64), (self.n,)))
+        vol = np.ascontiguousarray(np.broadcast_to(np.asarray(vol, dtype=np.float64), (self.n,)))
+        apic_upload_mass_volume(self.handle, self.n, mass, vol, on_device=0)
 
     def upload(self, x, v=None, B=None, F=None):
         """Host numpy arrays (float64) or CUDA float64 tensors."""

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <chrono>
+#include <cmath>
 #include <map>
 #include <mutex>
 #include <new>
@@ -176,8 +177,9 @@ Layout layout_of(const HostCfg& c)
     const int64_t n = c.capacity > 0 ? c.capacity : 1;
     const size_t R = c.precision == 32 ? 4 : 8;
     for (int s = 0; s < 2; ++s) {
-        // lanes A V Ba Bb Fa Fb (4 reals), Fc (2), Ta (4), Tb (2), M (2); 2-D keeps A V Ba Fa Tb M
-        static const int width[APIC_STATE_LANES] = {4, 4, 4, 4, 4, 4, 2, 4, 2, 2};
+        // lanes A V Ba Bb Fa Fb (4 reals), Fc (2), Ta (4), Tb (2), M (4: mu, lambda, m_p, V_p);
+        // 2-D keeps A V Ba Fa Tb M
+        static const int width[APIC_STATE_LANES] = {4, 4, 4, 4, 4, 4, 2, 4, 2, 4};
         static const bool used2d[APIC_STATE_LANES] = {true, true, true, false, true, false, false, false, true, true};
         for (int i = 0; i < APIC_STATE_LANES; ++i)
             L.st[s][i] = cv.take((c.dim == 3 || used2d[i]) ? (size_t)n * width[i] * R : 0);
@@ -500,6 +502,7 @@ apic_status apic_upload_materials(apic_sim* s, int64_t n, const double* E, const
     if (n != s->n) return fail(s, APIC_ERR_ARG, "n must equal the particle count of the last apic_upload");
     if (n > 0 && (!E || !nu)) return fail(s, APIC_ERR_ARG, "E and nu are required");
     CK(cudaSetDevice(s->device), "cudaSetDevice");
+    const int keep = s->c.mat;
     if (n == 0) {
         s->c.mat = 1;
         return APIC_OK;
@@ -517,7 +520,39 @@ apic_status apic_upload_materials(apic_sim* s, int64_t n, const double* E, const
         dnu = snu;
     }
     s->c.mat = 1;
-    CK(DISPATCH(s, set_materials, s->c, s->b, s->cur, n, dE, dnu, s->stream), "materials kernel");
+    CK(DISPATCH(s, set_params, s->c, s->b, s->cur, n, dE, dnu, nullptr, nullptr, keep, s->stream), "materials kernel");
+    s->launches += 1;
+    if (!on_device) return check_device(s);
+    return APIC_OK;
+}
+
+apic_status apic_upload_mass_volume(apic_sim* s, int64_t n, const double* mass, const double* vol, int on_device)
+{
+    if (!s) return APIC_ERR_ARG;
+    IN_BATCH_GUARD(s);
+    if (s->phase != 0) return fail(s, APIC_ERR_ARG, "apic_upload_mass_volume between apic_p2g and apic_g2p");
+    if (n != s->n) return fail(s, APIC_ERR_ARG, "n must equal the particle count of the last apic_upload");
+    if (n > 0 && (!mass || !vol)) return fail(s, APIC_ERR_ARG, "mass and vol are required");
+    CK(cudaSetDevice(s->device), "cudaSetDevice");
+    const int keep = s->c.mat;
+    if (n == 0) {
+        s->c.mat = 1;
+        return APIC_OK;
+    }
+    const double *dm = mass, *dv = vol;
+    if (!on_device) {
+        for (int64_t i = 0; i < n; ++i)
+            if (!(mass[i] > 0.0) || !(vol[i] > 0.0) || !std::isfinite(mass[i]) || !std::isfinite(vol[i]))
+                return fail(s, APIC_ERR_ARG, "each mass and each volume must be finite and > 0");
+        double* sm = s->b.staging;
+        double* sv = sm + n;
+        CK(cudaMemcpyAsync(sm, mass, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream), "upload mass");
+        CK(cudaMemcpyAsync(sv, vol, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream), "upload vol");
+        dm = sm;
+        dv = sv;
+    }
+    s->c.mat = 1;
+    CK(DISPATCH(s, set_params, s->c, s->b, s->cur, n, nullptr, nullptr, dm, dv, keep, s->stream), "mass kernel");
     s->launches += 1;
     if (!on_device) return check_device(s);
     return APIC_OK;

@@ -29,7 +29,7 @@ template <typename R> struct alignas(4 * sizeof(R)) V4 { R x, y, z, w; };
 template <typename R> struct alignas(2 * sizeof(R)) V2 { R x, y; };
 
 template <typename R> struct PState {
-    V4<R>* A; V4<R>* V; V4<R>* Ba; V4<R>* Bb; V4<R>* Fa; V4<R>* Fb; V2<R>* Fc; V4<R>* Ta; V2<R>* Tb; V2<R>* M;
+    V4<R>* A; V4<R>* V; V4<R>* Ba; V4<R>* Bb; V4<R>* Fa; V4<R>* Fb; V2<R>* Fc; V4<R>* Ta; V2<R>* Tb; V4<R>* M;
 };
 
 __device__ __forceinline__ V4<float> ld4(const V4<float>* p)
@@ -92,7 +92,8 @@ template <int D, typename R> struct Particle {
     R B[D * D];
     R F[D * D];
     R tau[(D == 3) ? 6 : 3];   // 3-D: t00 t11 t22 t01 t02 t12; 2-D: t00 t11 t01
-    R mu, lam;                 // Lame parameters, when a material per particle is set
+    R mu, lam;                 // Lame parameters, when parameters per particle are set
+    R pm, pv;                  // mass m_p and volume V_p, likewise
 };
 
 // full D x D matrix (row-major) of a symmetric stress held as its independent entries
@@ -191,9 +192,11 @@ __device__ __forceinline__ void load_v(const PState<R>& s, uint32_t k, Particle<
 template <int D, typename R>
 __device__ __forceinline__ void load_mat(const PState<R>& s, uint32_t k, Particle<D, R>& p)
 {
-    const V2<R> m = ld2(s.M + k);
+    const V4<R> m = ld4(s.M + k);
     p.mu = m.x;
     p.lam = m.y;
+    p.pm = m.z;
+    p.pv = m.w;
 }
 
 // every lane of the particle; the stress lanes only when `with_tau` (a model is set), the
@@ -203,7 +206,7 @@ __device__ __forceinline__ void store_all(const PState<R>& s, uint32_t k, const 
                                           bool with_mat = false)
 {
     const R z = R(0);
-    if (with_mat) st2(s.M + k, V2<R>{p.mu, p.lam});
+    if (with_mat) st4(s.M + k, V4<R>{p.mu, p.lam, p.pm, p.pv});
     if (D == 3) {
         st4(s.A + k, V4<R>{p.o[0], p.o[1], p.o[2], u2r(pack_cell<D>(p.cell), z)});
         st4(s.V + k, V4<R>{p.v[0], p.v[1], p.v[2], p.B[0]});
@@ -234,7 +237,7 @@ template <typename R> struct DevCfg {
     R dt;
     R gravity[3];
     int boundary, wall, model, transfer;
-    int mat;             // 1: per-particle Lame parameters in lane M
+    int mat;             // 1: per-particle parameters in lane M (mu, lam, m_p, V_p)
     R mu, lam;
     R mass, vol;
     R inv_kdx;           // 1 / (kappa dx): B_p D_p^{-1} (x_i - x_p) = (B_p / (kappa dx)) r^, r^ = (x_i - x_p)/dx

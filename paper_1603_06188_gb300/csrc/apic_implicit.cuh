@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(128) k_force_diff(PState<R> st, const uint32_t
                     R s = R(0);
 #pragma unroll
                     for (int kk = 0; kk < D; ++kk) s += dP[a * D + kk] * p.F[b2 * D + kk];
-                    A[a * D + b2] = c.vol * s;
+                    A[a * D + b2] = (c.mat ? p.pv : c.vol) * s;
                 }
             // scale * (-A grad w), grad w = grad^ w / dx
             const R sc = -scale * c.inv_dx;

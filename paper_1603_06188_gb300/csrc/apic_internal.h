@@ -63,7 +63,7 @@ struct HostCfg {
     int nb[3];
     double dx, origin[3], dt, gravity[3];
     int boundary, wall, model;
-    int mat;                     // 1: per-particle Lame parameters (lane M), else mu, lam
+    int mat;                     // 1: per-particle parameters (lane M: mu, lam, m_p, V_p), else the config's
     int adaptive;                // 1: kernels read the time step from Buffers::dt_word
     double flip_alpha;           // transfer 2: weight of the FLIP update
     double mu, lam, mass, vol;
@@ -160,8 +160,9 @@ struct Launch {
                                  cudaStream_t s);                                                               \
     cudaError_t occupancy_##SFX(const HostCfg& c, int* p2g_per_sm, int* g2p_per_sm);                         \
     cudaError_t cfl_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const Launch& L, cudaStream_t s); \
-    cudaError_t set_materials_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const double* E,     \
-                                    const double* nu, cudaStream_t s);                                             \
+    cudaError_t set_params_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const double* E,        \
+                                 const double* nu, const double* mass, const double* vol, int keep,             \
+                                 cudaStream_t s);                                                                 \
     cudaError_t adapt_dt_##SFX(const HostCfg& c, const Buffers& b, double nu, double dt_max, int first,         \
                                cudaStream_t s);                                                                 \
     cudaError_t grid_update_lambda1_##SFX(const HostCfg& c, const Buffers& b, int cur, const uint32_t* skeys,   \

@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(128) k_force_lambda1(PState<R> st, const uint3
                     R s = R(0);
 #pragma unroll
                     for (int kk = 0; kk < D; ++kk) s += P[a * D + kk] * p.F[b2 * D + kk];
-                    A[a * D + b2] = c.vol * s;
+                    A[a * D + b2] = (c.mat ? p.pv : c.vol) * s;
                 }
             // dt f_i = -dt A grad w / dx into the tile
 #pragma unroll

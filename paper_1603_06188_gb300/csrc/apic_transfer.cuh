@@ -76,7 +76,7 @@ template <typename R> PState<R> state_of(const Buffers& b, int which)
     s.Fc = (V2<R>*)b.st[which][6];
     s.Ta = (V4<R>*)b.st[which][7];
     s.Tb = (V2<R>*)b.st[which][8];
-    s.M = (V2<R>*)b.st[which][9];
+    s.M = (V4<R>*)b.st[which][9];
     return s;
 }
 
@@ -160,8 +160,17 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// slot of packed state, in units of R: 3-D A V Ba Bb Ta Tb (+2 pad) = 24, 2-D A V Ba Tb (+2) = 16
+// slot of packed state, in units of R: 3-D A V Ba Bb Ta Tb (m_p V_p) = 24, 2-D A V Ba Tb (m_p V_p)
+// = 16; the last two words hold the particle's mass and volume when parameters per particle
+// are set
 template <int D> __host__ __device__ constexpr int slot_words() { return D == 3 ? 24 : 16; }
+template <int D> __host__ __device__ constexpr int slot_mass_word() { return D == 3 ? 22 : 14; }
+
+// the (m_p, V_p) half of a particle's parameter lane
+template <typename R> __device__ __forceinline__ const V2<R>* mass_half(const PState<R>& s, uint32_t q)
+{
+    return reinterpret_cast<const V2<R>*>(s.M + q) + 1;
+}
 
 template <typename R> __device__ __forceinline__ void cp_group4(R* dst, const V4<R>* src)
 {
@@ -178,10 +187,12 @@ template <typename R> __device__ __forceinline__ void cp_group2(R* dst, const V2
     else cp_async16(dst, src);
 }
 
-// what P2G reads of particle q: position, v, B and (with a stress model) tau
+// what P2G reads of particle q: position, v, B, (with a stress model) tau and (with
+// parameters per particle) its mass
 template <int D, typename R>
-__device__ __forceinline__ void stage_particle(R* slot, const PState<R>& s, uint32_t q, bool with_tau)
+__device__ __forceinline__ void stage_particle(R* slot, const PState<R>& s, uint32_t q, bool with_tau, bool mat)
 {
+    if (mat) cp_group2<R>(slot + slot_mass_word<D>(), mass_half(s, q));
     cp_group4<R>(slot + 0, s.A + q);
     cp_group4<R>(slot + 4, s.V + q);
     cp_group4<R>(slot + 8, s.Ba + q);
@@ -197,8 +208,9 @@ __device__ __forceinline__ void stage_particle(R* slot, const PState<R>& s, uint
 }
 
 template <int D, typename R>
-__device__ __forceinline__ void read_staged(const R* slot, Particle<D, R>& p, bool with_tau)
+__device__ __forceinline__ void read_staged(const R* slot, Particle<D, R>& p, bool with_tau, bool mat)
 {
+    if (mat) p.pm = slot[slot_mass_word<D>()];
     const V4<R> a = *reinterpret_cast<const V4<R>*>(slot + 0);
     const V4<R> v = *reinterpret_cast<const V4<R>*>(slot + 4);
     const V4<R> ba = *reinterpret_cast<const V4<R>*>(slot + 8);
@@ -299,10 +311,30 @@ __device__ __forceinline__ void tile_cell_runs(const uint32_t* __restrict__ skey
                                                uint32_t* cbeg, uint32_t* cend, int nt)
 {
     constexpr int NC = (D == 3) ? 64 : 16;
-    for (uint32_t k = start + threadIdx.x; k < end; k += nt) {
-        const uint32_t cl = skeys[k] & (NC - 1);
-        if (k == start || (skeys[k - 1] & (NC - 1)) != cl) cbeg[cl] = k;
-        if (k + 1 == end || (skeys[k + 1] & (NC - 1)) != cl) cend[cl] = k + 1;
+    // U keys per thread and their neighbours are requested before any is used, so a tile
+    // waits for one load latency instead of one per key
+    constexpr int U = 8;
+    for (uint32_t k0 = start; k0 < end; k0 += (uint32_t)nt * U) {
+        uint32_t kc[U], kp[U], kn[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t k = k0 + threadIdx.x + (uint32_t)(u * nt);
+            kc[u] = kp[u] = kn[u] = 0u;
+            if (k < end) {
+                kc[u] = skeys[k];
+                if (k > start) kp[u] = skeys[k - 1];
+                if (k + 1 < end) kn[u] = skeys[k + 1];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t k = k0 + threadIdx.x + (uint32_t)(u * nt);
+            if (k < end) {
+                const uint32_t cl = kc[u] & (NC - 1);
+                if (k == start || (kp[u] & (NC - 1)) != cl) cbeg[cl] = k;
+                if (k + 1 == end || (kn[u] & (NC - 1)) != cl) cend[cl] = k + 1;
+            }
+        }
     }
 }
 
@@ -335,19 +367,56 @@ __device__ __forceinline__ void tile_flush_nodes(const R* cellsum, uint64_t occ,
     constexpr int NS = (D == 3) ? K * K * K : K * K;
     constexpr int NV = D + 1;
     constexpr int NVAL = NS * NV;
+    // Cell n - (a, b, c) is linear index L - dj with L = n0 + 4 n1 + 16 n2 and dj = a + 4 b +
+    // 16 c.  Per node the occupancy word is shifted so that the cell of stencil offset j sits
+    // at the fixed bit DM - dj, and masked with the offsets whose cell lies in the block
+    // (built from per-axis masks: bit K-1-a set when 0 <= n - a <= 3), so each of the NS
+    // candidates costs one constant bit test.
+    constexpr int DM = (K - 1) * ((D == 3) ? 21 : 5);
+    constexpr unsigned KM = (1u << K) - 1u;
+    // reversed valid-offset masks of the TE node positions of an axis, K bits each
+    constexpr unsigned long long RA = [] {
+        unsigned long long r = 0;
+        for (int n = 0; n < TE; ++n) {
+            unsigned m = 0;
+            for (int a = 0; a < K; ++a)
+                if (n - a >= 0 && n - a <= 3) m |= 1u << (K - 1 - a);
+            r |= (unsigned long long)m << (K * n);
+        }
+        return r;
+    }();
     for (int i = threadIdx.x; i < TN; i += nt) {
         const int n0 = i % TE, n1 = (i / TE) % TE, n2 = (D == 3) ? i / (TE * TE) : 0;
+        const int L = n0 + 4 * n1 + 16 * n2;
+        uint64_t t = (L >= DM) ? (occ >> (L - DM)) : (occ << (DM - L));
+        {
+            const uint64_t ra = (RA >> (K * n0)) & KM;
+            const unsigned rb = (unsigned)(RA >> (K * n1)) & KM;
+            uint64_t y = 0;
+#pragma unroll
+            for (int b = 0; b < K; ++b)
+                if ((rb >> b) & 1u) y |= ra << (4 * b);
+            if (D == 3) {
+                const unsigned rc = (unsigned)(RA >> (K * n2)) & KM;
+                uint64_t z = 0;
+#pragma unroll
+                for (int c3 = 0; c3 < K; ++c3)
+                    if ((rc >> c3) & 1u) z |= y << (16 * c3);
+                t &= z;
+            } else {
+                t &= y;
+            }
+        }
+        const int cl0 = L;
         R sum[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) sum[v] = R(0);
 #pragma unroll
         for (int j = 0; j < NS; ++j) {
             const int ia = j % K, ib = (j / K) % K, ic = j / (K * K);
-            const int c0 = n0 - ia, c1 = n1 - ib, c2 = (D == 3) ? n2 - ic : 0;
-            if (c0 < 0 || c0 > 3 || c1 < 0 || c1 > 3 || c2 < 0 || c2 > 3) continue;
-            const int cl = c0 | (c1 << 2) | (c2 << 4);
-            if (!((occ >> cl) & 1ull)) continue;
-            const R* src = cellsum + (size_t)cl * NVAL + j * NV;
+            const int dj = ia + 4 * ib + 16 * ic;
+            if (!((t >> (DM - dj)) & 1ull)) continue;
+            const R* src = cellsum + (size_t)(cl0 - dj) * NVAL + j * NV;
 #pragma unroll
             for (int v = 0; v < NV; ++v) sum[v] += src[v];
         }
@@ -407,6 +476,21 @@ template <> __device__ __forceinline__ void fma_pair<float>(float& c0, float& c1
         : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
 }
 
+// two FP32 products in one packed instruction (d0 = a0 b0, d1 = a1 b1), each rounded as a
+// scalar multiply; the FP64 form is two scalar products
+template <typename R> __device__ __forceinline__ void mul_pair(R& d0, R& d1, R a0, R a1, R b0, R b1)
+{
+    d0 = a0 * b0;
+    d1 = a1 * b1;
+}
+template <> __device__ __forceinline__ void mul_pair<float>(float& d0, float& d1, float a0, float a1, float b0, float b1)
+{
+    asm("{\n\t.reg .b64 pa, pb, pd;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "mul.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(d0), "=f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
 // One particle's stencil sums added to a lane's registers cur (the z-slab SLAB of the
 // stencil for 3-D cubic).  A lane past its cell's run (live false) carries a neutral
 // particle: an in-cell position and zero state, so its weights are finite and it adds
@@ -441,7 +525,7 @@ __device__ __forceinline__ void p2g_cells_particle(Particle<D, R>& p, bool live,
         live = false;
     }
     const R ml = live ? m : R(0);
-    R mv[D], mC[D * D], T[D * D];
+    R mv[D], mC[D * D], T[D * D];   // T = -dt/dx tau
 #pragma unroll
     for (int a = 0; a < D; ++a) mv[a] = ml * p.v[a];
 #pragma unroll
@@ -450,18 +534,20 @@ __device__ __forceinline__ void p2g_cells_particle(Particle<D, R>& p, bool live,
         R tau[D * D];
         tau_full<D, R>(p.tau, tau);
 #pragma unroll
-        for (int i = 0; i < D * D; ++i) T[i] = (live ? dt_dx : R(0)) * tau[i];
+        for (int i = 0; i < D * D; ++i) T[i] = (live ? -dt_dx : R(0)) * tau[i];
     } else {
 #pragma unroll
         for (int i = 0; i < D * D; ++i) T[i] = R(0);
     }
     // The weights are tensor products, so the contributions separate axis by axis
-    // (r = node - fx in grid units, T = dt/dx tau, mC = m B D^{-1} dx):
+    // (r = node - fx in grid units, T = -dt/dx tau, mC = m B D^{-1} dx):
     //   dp_c(i,j,k) = w0_i P_c(j,k) + E_c(i) S(j,k),       mass = w0_i m S(j,k)
     //   P_c(j,k) = w1_j Q_c(k) + H_c(j) w2_k,              S(j,k) = w1_j w2_k
-    //   Q_c(k) = m v_c w2_k + mC_c2 (r w)2_k - T_c2 dw2_k
-    //   H_c(j) = mC_c1 (r w)1_j - T_c1 dw1_j,  E_c(i) = mC_c0 (r w)0_i - T_c0 dw0_i
-    // which is w m (v + C (x_i - x_p)) - dt tau grad w summed in fewer operations.
+    //   Q_c(k) = m v_c w2_k + mC_c2 (r w)2_k + T_c2 dw2_k
+    //   H_c(j) = mC_c1 (r w)1_j + T_c1 dw1_j,  E_c(i) = mC_c0 (r w)0_i + T_c0 dw0_i
+    // which is w m (v + C (x_i - x_p)) - dt tau grad w summed in fewer operations; the
+    // factors are formed two at a time in packed pairs (components 0 and 1 together, and
+    // component 2 of E with that of H)
     if (D == 3) {
         R E[3][K], H[3][K], mw0[K];
 #pragma unroll
@@ -469,25 +555,30 @@ __device__ __forceinline__ void p2g_cells_particle(Particle<D, R>& p, bool live,
 #pragma unroll
         for (int i = 0; i < K; ++i) {
             const R rw0 = (R(i) - fx[0]) * w[0][i], rw1 = (R(i) - fx[1]) * w[1][i];
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc) {
-                E[cc][i] = mC[cc * 3 + 0] * rw0 - T[cc * 3 + 0] * dw[0][i];
-                H[cc][i] = mC[cc * 3 + 1] * rw1 - T[cc * 3 + 1] * dw[1][i];
-            }
+            mul_pair<R>(E[0][i], E[1][i], mC[0], mC[3], rw0, rw0);
+            fma_pair<R>(E[0][i], E[1][i], T[0], T[3], dw[0][i], dw[0][i]);
+            mul_pair<R>(H[0][i], H[1][i], mC[1], mC[4], rw1, rw1);
+            fma_pair<R>(H[0][i], H[1][i], T[1], T[4], dw[1][i], dw[1][i]);
+            mul_pair<R>(E[2][i], H[2][i], mC[6], mC[7], rw0, rw1);
+            fma_pair<R>(E[2][i], H[2][i], T[6], T[7], dw[0][i], dw[1][i]);
         }
 #pragma unroll
         for (int icl = 0; icl < KZ; ++icl) {
             const int ic = SLAB * KZ + icl;
             const R w2 = w[2][ic], dw2 = dw[2][ic], rw2 = (R(ic) - fx[2]) * w2;
             R Q[3];
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc) Q[cc] = mv[cc] * w2 + mC[cc * 3 + 2] * rw2 - T[cc * 3 + 2] * dw2;
+            mul_pair<R>(Q[0], Q[1], mv[0], mv[1], w2, w2);
+            fma_pair<R>(Q[0], Q[1], mC[2], mC[5], rw2, rw2);
+            fma_pair<R>(Q[0], Q[1], T[2], T[5], dw2, dw2);
+            Q[2] = fma(T[8], dw2, fma(mC[8], rw2, mv[2] * w2));
 #pragma unroll
             for (int ib = 0; ib < K; ++ib) {
-                const R S = w[1][ib] * w2;
-                R P[3];
-#pragma unroll
-                for (int cc = 0; cc < 3; ++cc) P[cc] = w[1][ib] * Q[cc] + H[cc][ib] * w2;
+                const R w1 = w[1][ib];
+                R P[3], S;
+                mul_pair<R>(P[0], P[1], w1, w1, Q[0], Q[1]);
+                fma_pair<R>(P[0], P[1], H[0][ib], H[1][ib], w2, w2);
+                mul_pair<R>(P[2], S, w1, w1, Q[2], w2);
+                P[2] = fma(H[2][ib], w2, P[2]);
 #pragma unroll
                 for (int ia = 0; ia < K; ++ia) {
                     const int j = ia + K * ib + K * K * icl;
@@ -505,14 +596,14 @@ __device__ __forceinline__ void p2g_cells_particle(Particle<D, R>& p, bool live,
         for (int i = 0; i < K; ++i) {
             const R rw0 = (R(i) - fx[0]) * w[0][i];
 #pragma unroll
-            for (int cc = 0; cc < 2; ++cc) E[cc][i] = mC[cc * 2 + 0] * rw0 - T[cc * 2 + 0] * dw[0][i];
+            for (int cc = 0; cc < 2; ++cc) E[cc][i] = mC[cc * 2 + 0] * rw0 + T[cc * 2 + 0] * dw[0][i];
         }
 #pragma unroll
         for (int ib = 0; ib < K; ++ib) {
             const R w1 = w[1][ib], rw1 = (R(ib) - fx[1]) * w1, mw1 = ml * w1;
             R Q[2];
 #pragma unroll
-            for (int cc = 0; cc < 2; ++cc) Q[cc] = mv[cc] * w1 + mC[cc * 2 + 1] * rw1 - T[cc * 2 + 1] * dw[1][ib];
+            for (int cc = 0; cc < 2; ++cc) Q[cc] = mv[cc] * w1 + mC[cc * 2 + 1] * rw1 + T[cc * 2 + 1] * dw[1][ib];
 #pragma unroll
             for (int ia = 0; ia < K; ++ia) {
                 const int j = ia + K * ib;
@@ -550,6 +641,7 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
     const R m = c.mass;
     const R sC = (c.transfer == 0) ? m * c.inv_kdx : R(0);
     const bool with_tau = c.model != 0;
+    const bool mat = c.mat != 0;
     const uint32_t blk = skeys[start] >> (2 * D);
     int bo[3] = {0, 0, 0};
     block_coords<D, R>(blk, c, bo);
@@ -587,7 +679,7 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
 #pragma unroll
             for (int i = 0; i < NSL; ++i) {
                 const uint32_t kk = kb + lig + (uint32_t)(i * G);
-                if (kk < ke) stage_particle<D, R>(pslots + (size_t)(i * NT + threadIdx.x) * SW, st, perm[kk], with_tau);
+                if (kk < ke) stage_particle<D, R>(pslots + (size_t)(i * NT + threadIdx.x) * SW, st, perm[kk], with_tau, mat);
                 cp_async_commit();
             }
             // the permutation entry of the particle staged next is read one iteration early,
@@ -604,18 +696,21 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
                 cp_async_wait<NSL - 1>();
                 R* slot = pslots + (size_t)((it % NSL) * NT + threadIdx.x) * SW;
                 Particle<D, R> p;
-                read_staged<D, R>(slot, p, with_tau);
+                read_staged<D, R>(slot, p, with_tau, mat);
                 {
                     const uint32_t kn = k + (uint32_t)(NSL * G);
-                    if (kn < ke) stage_particle<D, R>(slot, st, qn, with_tau);
+                    if (kn < ke) stage_particle<D, R>(slot, st, qn, with_tau, mat);
                     cp_async_commit();
                     const uint32_t kq = kn + (uint32_t)G;
                     if (kq < ke) qn = perm[kq];
                 }
+                // the particle's own mass when parameters per particle are set
+                const R mp = mat ? p.pm : m;
+                const R sCp = mat ? ((c.transfer == 0) ? mp * c.inv_kdx : R(0)) : sC;
                 if (ZS == 1 || slab == 0)
-                    p2g_cells_particle<D, ORDER, R, KZ, 0>(p, live, lb, bo, c, err, m, sC, dt_dx, with_tau, cur);
+                    p2g_cells_particle<D, ORDER, R, KZ, 0>(p, live, lb, bo, c, err, mp, sCp, dt_dx, with_tau, cur);
                 else
-                    p2g_cells_particle<D, ORDER, R, KZ, ZS - 1>(p, live, lb, bo, c, err, m, sC, dt_dx, with_tau, cur);
+                    p2g_cells_particle<D, ORDER, R, KZ, ZS - 1>(p, live, lb, bo, c, err, mp, sCp, dt_dx, with_tau, cur);
             }
             cp_async_wait<0>();
             int off = 0, cnt = NVS;
@@ -699,14 +794,16 @@ template <int ORDER, typename R> __host__ __device__ constexpr size_t p2g_split_
            (size_t)64 * SplitShape<ORDER>::NSL * slot_words<3>() * sizeof(R);
 }
 
-// lane r of a group copies the 16-byte groups g = r, r + LPC, ... of particle q's packed
-// state (A V Ba Bb Ta Tb) into the group's slot
+// lane r of a group copies the groups g = r, r + LPC, ... of particle q's packed state (A V Ba
+// Bb Ta Tb, then the (m_p, V_p) half of M when parameters per particle are set) into the
+// group's slot
 template <int LPC, typename R>
-__device__ __forceinline__ void stage_part(R* slot, const PState<R>& s, uint32_t q, int r)
+__device__ __forceinline__ void stage_part(R* slot, const PState<R>& s, uint32_t q, int r, bool mat)
 {
 #pragma unroll
-    for (int g = 0; g < 6; ++g) {
+    for (int g = 0; g < 7; ++g) {
         if (g % LPC != r) continue;
+        if (g == 6 && mat) cp_group2<R>(slot + slot_mass_word<3>(), mass_half(s, q));
         if (g == 0) cp_group4<R>(slot + 0, s.A + q);
         if (g == 1) cp_group4<R>(slot + 4, s.V + q);
         if (g == 2) cp_group4<R>(slot + 8, s.Ba + q);
@@ -841,6 +938,7 @@ __device__ __forceinline__ void p2g_split_tile(const PState<R>& st, const uint32
     const R m = c.mass;
     const R sC = (c.transfer == 0) ? m * c.inv_kdx : R(0);
     const bool with_tau = c.model != 0;
+    const bool mat = c.mat != 0;
     const uint32_t blk = skeys[start] >> 6;
     int bo[3] = {0, 0, 0};
     block_coords<3, R>(blk, c, bo);
@@ -864,7 +962,7 @@ __device__ __forceinline__ void p2g_split_tile(const PState<R>& st, const uint32
         // barrier after reading it)
 #pragma unroll
         for (int i = 0; i < NSL - 1; ++i) {
-            if ((uint32_t)i < run) stage_part<LPC, R>(gslots + i * SW, st, perm[kb + i], r);
+            if ((uint32_t)i < run) stage_part<LPC, R>(gslots + i * SW, st, perm[kb + i], r, mat);
             cp_async_commit();
         }
         uint32_t qn = ((uint32_t)(NSL - 1) < run) ? perm[kb + NSL - 1] : 0u;
@@ -874,12 +972,15 @@ __device__ __forceinline__ void p2g_split_tile(const PState<R>& st, const uint32
             __syncwarp();
             {
                 const uint32_t nx = it + NSL - 1;
-                if (nx < run) stage_part<LPC, R>(gslots + (nx % NSL) * SW, st, qn, r);
+                if (nx < run) stage_part<LPC, R>(gslots + (nx % NSL) * SW, st, qn, r, mat);
                 cp_async_commit();
                 if (nx + 1 < run) qn = perm[kb + nx + 1];
             }
-            p2g_split_particle<ORDER, R>(gslots + (it % NSL) * SW, it < run, h, zs, lb, bo, c, err, m, sC, dt_dx,
-                                         with_tau, accA, accB);
+            // the particle's own mass when parameters per particle are set
+            const R* sl = gslots + (it % NSL) * SW;
+            const R mp = mat ? sl[slot_mass_word<3>()] : m;
+            const R sCp = mat ? ((c.transfer == 0) ? mp * c.inv_kdx : R(0)) : sC;
+            p2g_split_particle<ORDER, R>(sl, it < run, h, zs, lb, bo, c, err, mp, sCp, dt_dx, with_tau, accA, accB);
         }
         cp_async_wait<0>();
         if (run > 0u) {
@@ -1333,8 +1434,8 @@ __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>
         }
         // the stress of the new F_p, for the next P2G
         if (c.model != 0)
-            stress_sym<D, R>(c.model, p.F, (EXT && c.mat) ? p.mu : c.mu, (EXT && c.mat) ? p.lam : c.lam, c.vol,
-                             p.tau, fallbacks);
+            stress_sym<D, R>(c.model, p.F, (EXT && c.mat) ? p.mu : c.mu, (EXT && c.mat) ? p.lam : c.lam,
+                             (EXT && c.mat) ? p.pv : c.vol, p.tau, fallbacks);
         store_all<D, R>(out, k, p, c.model != 0, EXT && c.mat != 0);
         knext[k] = key_of<D, ORDER, R>(p.o, p.cell, c, err);
     }
@@ -1426,7 +1527,7 @@ __device__ __forceinline__ void block_sum6(double* a, double* part)
 }
 
 template <int D, typename R>
-__global__ void __launch_bounds__(TPB) k_mom_particles(PState<R> st, DevCfg<R> c, double mass, double dx,
+__global__ void __launch_bounds__(TPB) k_mom_particles(PState<R> st, DevCfg<R> c, double mass_cfg, double dx,
                                                        double o0, double o1, double o2, double* part)
 {
     // every particle's terms in FP64 from its state widened exactly (the position as
@@ -1437,6 +1538,7 @@ __global__ void __launch_bounds__(TPB) k_mom_particles(PState<R> st, DevCfg<R> c
         Particle<D, R> p;
         load_x<D, R>(st, k, p);
         load_vB<D, R>(st, k, p);
+        const double mass = c.mat ? (double)ld4(st.M + k).z : mass_cfg;
         double x[3] = {0.0, 0.0, 0.0}, v[3] = {0.0, 0.0, 0.0};
 #pragma unroll
         for (int d = 0; d < D; ++d) {
@@ -1617,9 +1719,10 @@ __global__ void __launch_bounds__(TPB) k_upload(PState<R> st, DevCfg<R> c, doubl
 // a material per particle: Lame parameters from (E, nu) given in upload order (index = id),
 // stored in lane M of the particle wherever it now sits, and its stress recomputed
 template <int D, typename R>
-__global__ void __launch_bounds__(TPB) k_set_materials(PState<R> st, DevCfg<R> c, const double* __restrict__ E,
-                                                       const double* __restrict__ nu, uint32_t* fallbacks,
-                                                       uint32_t* err)
+__global__ void __launch_bounds__(TPB) k_set_params(PState<R> st, DevCfg<R> c, const double* __restrict__ E,
+                                                    const double* __restrict__ nu, const double* __restrict__ mass,
+                                                    const double* __restrict__ vol, int keep, uint32_t* fallbacks,
+                                                    uint32_t* err)
 {
     const int k = blockIdx.x * TPB + threadIdx.x;
     if (k >= c.n) return;
@@ -1630,10 +1733,25 @@ __global__ void __launch_bounds__(TPB) k_set_materials(PState<R> st, DevCfg<R> c
         set_err(err, APIC_ERRBIT_RANGE);
         return;
     }
-    const double e = E[p.id], v = nu[p.id];
-    p.mu = (R)(e / (2.0 * (1.0 + v)));
-    p.lam = (R)(e * v / ((1.0 + v) * (1.0 - 2.0 * v)));
-    if (c.model != 0) stress_sym<D, R>(c.model, p.F, p.mu, p.lam, c.vol, p.tau, fallbacks);
+    // what is not given keeps the particle's earlier value (keep) or the configuration's
+    if (keep) {
+        load_mat<D, R>(st, k, p);
+    } else {
+        p.mu = c.mu;
+        p.lam = c.lam;
+        p.pm = c.mass;
+        p.pv = c.vol;
+    }
+    if (E) {
+        const double e = E[p.id], v = nu[p.id];
+        p.mu = (R)(e / (2.0 * (1.0 + v)));
+        p.lam = (R)(e * v / ((1.0 + v) * (1.0 - 2.0 * v)));
+    }
+    if (mass) {
+        p.pm = (R)mass[p.id];
+        p.pv = (R)vol[p.id];
+    }
+    if (c.model != 0) stress_sym<D, R>(c.model, p.F, p.mu, p.lam, p.pv, p.tau, fallbacks);
     store_all<D, R>(st, k, p, c.model != 0, true);
 }
 
@@ -1932,14 +2050,14 @@ template <typename R> struct Impl {
         k_adapt_dt<R><<<1, 1, 0, s>>>((R*)b.dt_word, b.smax_word, b.mom_out, b.elapsed, h.dx, nu, dt_max, first);
         return cudaGetLastError();
     }
-    static cudaError_t set_materials(const HostCfg& h, const Buffers& b, int cur, int64_t n, const double* E,
-                                     const double* nu, cudaStream_t s)
+    static cudaError_t set_params(const HostCfg& h, const Buffers& b, int cur, int64_t n, const double* E,
+                                  const double* nu, const double* mass, const double* vol, int keep, cudaStream_t s)
     {
         if (n == 0) return cudaSuccess;
         DevCfg<R> c = HostToDev<R>::make(h, n);
         PState<R> st = state_of<R>(b, cur);
-        if (h.dim == 3) k_set_materials<3, R><<<blocks_for(n), TPB, 0, s>>>(st, c, E, nu, b.fallbacks, b.err);
-        else k_set_materials<2, R><<<blocks_for(n), TPB, 0, s>>>(st, c, E, nu, b.fallbacks, b.err);
+        if (h.dim == 3) k_set_params<3, R><<<blocks_for(n), TPB, 0, s>>>(st, c, E, nu, mass, vol, keep, b.fallbacks, b.err);
+        else k_set_params<2, R><<<blocks_for(n), TPB, 0, s>>>(st, c, E, nu, mass, vol, keep, b.fallbacks, b.err);
         return cudaGetLastError();
     }
     static cudaError_t upload(const HostCfg& h, const Buffers& b, int cur, int64_t n, const double* x,
@@ -2078,10 +2196,11 @@ template <typename R> struct Impl {
     {                                                                                                           \
         return Impl<R>::grid_update_midpoint(c, b, cur, skeys, perm, n, L, s, stats, kernels);                  \
     }                                                                                                           \
-    cudaError_t set_materials_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const double* E,   \
-                                    const double* nu, cudaStream_t s)                                          \
+    cudaError_t set_params_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const double* E,      \
+                                 const double* nu, const double* mass, const double* vol, int keep,           \
+                                 cudaStream_t s)                                                               \
     {                                                                                                           \
-        return Impl<R>::set_materials(c, b, cur, n, E, nu, s);                                                  \
+        return Impl<R>::set_params(c, b, cur, n, E, nu, mass, vol, keep, s);                                    \
     }                                                                                                           \
     cudaError_t upload_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const double* x,          \
                              const double* v, const double* B, const double* F, cudaStream_t s)                 \
