@@ -78,11 +78,9 @@ KERNEL_OF_PHASE = {"p2g": "k_p2g_cells", "grid_update": "k_grid_update", "g2p": 
 
 
 def p2g_kernel_name(order: int, p2g_kernel: int) -> str:
-    """The P2G kernel the library runs for a 3-D simulation: the component-split one for cubic
-    B-splines by default (or when asked for), else the cell-parallel one."""
-    if p2g_kernel == 1 or (p2g_kernel == 0 and order == 3):
-        return "k_p2g_split"
-    return "k_p2g_cells"
+    """The P2G kernel the library runs for a 3-D simulation: the component-split one when asked
+    for, else (the default) the cell-parallel one."""
+    return "k_p2g_split" if p2g_kernel == 1 else "k_p2g_cells"
 
 
 def make_scene(w: dict, seed: int = 0):

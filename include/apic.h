@@ -85,7 +85,7 @@ typedef struct {
     double particle_volume;  /* V_p (reference volume), the same for every particle */
     int tile_particles;      /* particles per P2G / G2P tile (power of two, 256..4096);
                                 0 = default */
-    int p2g_kernel;          /* P2G kernel: 0 = default (1 for 3-D cubic, else 2); 1 = component-
+    int p2g_kernel;          /* P2G kernel: 0 = default (2); 1 = component-
                                 split (3-D only: the lanes of a group per base cell each sum two
                                 of the four node sums); 2 = cell-parallel (lanes of a group
                                 share a cell's particles and reduce their full sums); results

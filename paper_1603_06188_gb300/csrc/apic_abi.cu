@@ -113,9 +113,9 @@ apic_status fill_cfg(const apic_config* in, int64_t max_particles, HostCfg* c, s
     c->tile = tile;
     if (in->p2g_kernel < 0 || in->p2g_kernel > 2) { *why = "p2g_kernel must be 0, 1 or 2"; return APIC_ERR_ARG; }
     if (in->p2g_kernel == 1 && in->dim != 3) { *why = "the component-split P2G kernel is 3-D only"; return APIC_ERR_ARG; }
-    // default: the component-split kernel for 3-D cubic, the cell-parallel one otherwise (the
-    // faster of the two on the 128^3 cube and the 256^3 spheres)
-    c->p2g_kernel = in->p2g_kernel != 0 ? in->p2g_kernel : ((in->dim == 3 && in->order == 3) ? 1 : 2);
+    // default: the cell-parallel kernel (the faster of the two on the 128^3 quadratic cube and
+    // the 256^3 cubic spheres)
+    c->p2g_kernel = in->p2g_kernel != 0 ? in->p2g_kernel : 2;
     if (in->p2g_group != 0 && in->p2g_group != 2 && in->p2g_group != 4) { *why = "p2g_group must be 0, 2 or 4"; return APIC_ERR_ARG; }
     c->p2g_group = in->p2g_group != 0 ? in->p2g_group : 4;
     c->p2g_group_auto = in->p2g_group == 0;

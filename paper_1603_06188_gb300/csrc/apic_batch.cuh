@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(128, (cells_ctas_per_sm<D, ORDER>())) kb_p2g_c
         __syncthreads();
         const uint32_t start = tile_start[t];
         const uint32_t end = tile_end(tile_sim, tile_start, t, ntiles, sim, (uint32_t)sd.c.n);
-        p2g_cells_tile<D, ORDER, R, G>(sd.st[sd.cur], sd.vb[kpar], sd.kb[kpar], start, end, sd.acc, sd.flags, sd.c,
+        p2g_cells_tile<D, ORDER, R, G>(sd.st[sd.cur], sd.vb[kpar], sd.kb[kpar] + start, start, end, sd.acc, sd.flags, sd.c,
                                        sd.err, sd.fallbacks, cellsum, cbeg, cend, &s_cell, pslots);
     }
 }

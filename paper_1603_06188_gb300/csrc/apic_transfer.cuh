@@ -157,6 +157,10 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
@@ -253,6 +257,12 @@ template <int D, int ORDER, typename R> __host__ __device__ constexpr size_t p2g
 {
     return (p2g_cellsum_bytes<D, ORDER, R>() + 31) / 32 * 32 + (size_t)p2g_slots<R>() * 128 * slot_words<D>() * sizeof(R);
 }
+// FP32 single-simulation P2G copies the next tile's keys (up to 4096) into shared memory
+template <typename R> __host__ __device__ constexpr bool p2g_key_prefetch() { return sizeof(R) == 4; }
+template <int D, int ORDER, typename R> __host__ __device__ constexpr size_t p2g_cells_launch_smem()
+{
+    return p2g_cells_smem<D, ORDER, R>() + (p2g_key_prefetch<R>() ? (size_t)4096 * 4 : 0);
+}
 
 // ---------------------------------------------------------------- P2G, cell-parallel
 // Butterfly reduce-scatter of N register values over a group of lanes: at distance H the
@@ -307,7 +317,7 @@ template <typename R, int N> struct ReduceScatter<R, N, 1> {
 // runs of equal base cell inside a tile (sorted keys of one node block): cbeg / cend per
 // in-block cell (whole CTA of nt threads; the caller synchronises afterwards)
 template <int D>
-__device__ __forceinline__ void tile_cell_runs(const uint32_t* __restrict__ skeys, uint32_t start, uint32_t end,
+__device__ __forceinline__ void tile_cell_runs(const uint32_t* __restrict__ tk, uint32_t start, uint32_t end,
                                                uint32_t* cbeg, uint32_t* cend, int nt)
 {
     constexpr int NC = (D == 3) ? 64 : 16;
@@ -321,9 +331,9 @@ __device__ __forceinline__ void tile_cell_runs(const uint32_t* __restrict__ skey
             const uint32_t k = k0 + threadIdx.x + (uint32_t)(u * nt);
             kc[u] = kp[u] = kn[u] = 0u;
             if (k < end) {
-                kc[u] = skeys[k];
-                if (k > start) kp[u] = skeys[k - 1];
-                if (k + 1 < end) kn[u] = skeys[k + 1];
+                kc[u] = tk[k - start];
+                if (k > start) kp[u] = tk[k - start - 1];
+                if (k + 1 < end) kn[u] = tk[k - start + 1];
             }
         }
 #pragma unroll
@@ -620,10 +630,12 @@ __device__ __forceinline__ void p2g_cells_particle(Particle<D, R>& p, bool live,
 // barrier).  Leaves the smem free for the next tile after its final barrier.
 template <int D, int ORDER, typename R, int G>
 __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32_t* __restrict__ perm,
-                                               const uint32_t* __restrict__ skeys, uint32_t start, uint32_t end,
+                                               const uint32_t* tk, uint32_t start, uint32_t end,
                                                R* __restrict__ acc, uint32_t* __restrict__ flags, const DevCfg<R>& c,
                                                uint32_t* err, uint32_t* fallbacks, R* cellsum, uint32_t* cbeg,
-                                               uint32_t* cend, int* s_cell, R* pslots)
+                                               uint32_t* cend, int* s_cell, R* pslots,
+                                               const uint32_t* pf_src = nullptr, uint32_t pf_n = 0u,
+                                               uint32_t* pf_dst = nullptr)
 {
     constexpr int NT = 128;
     constexpr int K = ORDER + 1;
@@ -642,13 +654,18 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
     const R sC = (c.transfer == 0) ? m * c.inv_kdx : R(0);
     const bool with_tau = c.model != 0;
     const bool mat = c.mat != 0;
-    const uint32_t blk = skeys[start] >> (2 * D);
+    const uint32_t blk = tk[0] >> (2 * D);
     int bo[3] = {0, 0, 0};
     block_coords<D, R>(blk, c, bo);
 #pragma unroll
     for (int a = 0; a < D; ++a) bo[a] *= 4;
-        tile_cell_runs<D>(skeys, start, end, cbeg, cend, NT);
+        tile_cell_runs<D>(tk, start, end, cbeg, cend, NT);
         __syncthreads();
+        // the tile's keys are read: the next tile's may be copied over them while it runs
+        if (pf_n > 0u) {
+            for (uint32_t i = threadIdx.x; i < pf_n; i += NT) cp_async4(pf_dst + i, pf_src + i);
+            cp_async_commit();
+        }
         // A warp takes GPW cells at once (one per lane group) and runs a warp-uniform number
         // of iterations -- the longest run among them -- so all lanes follow one instruction
         // stream; lanes past their run carry a neutral particle that adds zeros.  (Groups
@@ -747,19 +764,55 @@ __global__ void __launch_bounds__(128, (cells_ctas_per_sm<D, ORDER>())) k_p2g_ce
     R* cellsum = reinterpret_cast<R*>(p2g_smem);   // [NC][NVAL]
     R* pslots = reinterpret_cast<R*>(p2g_smem + (p2g_cellsum_bytes<D, ORDER, R>() + 31) / 32 * 32);
     __shared__ uint32_t cbeg[NC], cend[NC];
-    __shared__ int s_tile, s_cell;
+    __shared__ int s_tile, s_cell, s_next;
     const int ntiles = (int)*ntiles_p;
-    for (;;) {
+    if constexpr (p2g_key_prefetch<R>()) {
+        // The keys of the next tile are copied into shared memory while the current tile
+        // runs (its index is taken one tile ahead), so a tile starts without waiting for its
+        // key loads.
+        uint32_t* kbuf = reinterpret_cast<uint32_t*>(p2g_smem + p2g_cells_smem<D, ORDER, R>());
         if (threadIdx.x == 0) {
             s_tile = (int)atomicAdd(tile_ctr, 1u);
-            s_cell = 0;
+            s_next = (int)atomicAdd(tile_ctr, 1u);
         }
-        for (int i = threadIdx.x; i < NC; i += 128) { cbeg[i] = 0u; cend[i] = 0u; }
         __syncthreads();
-        const int t = s_tile;
-        if (t >= ntiles) break;
-        p2g_cells_tile<D, ORDER, R, G>(st, perm, skeys, tiles[t], tiles[t + 1], acc, flags, c, err, fallbacks, cellsum,
-                                       cbeg, cend, &s_cell, pslots);
+        int t = s_tile;
+        if (t < ntiles) {
+            const uint32_t b0 = tiles[t], b1 = tiles[t + 1];
+            for (uint32_t k = b0 + threadIdx.x; k < b1; k += 128u) cp_async4(kbuf + (k - b0), skeys + k);
+            cp_async_commit();
+        }
+        while (t < ntiles) {
+            const uint32_t b0 = tiles[t], b1 = tiles[t + 1];
+            const int tn = s_next;
+            uint32_t nb0 = 0u, nb1 = 0u;
+            if (tn < ntiles) {
+                nb0 = tiles[tn];
+                nb1 = tiles[tn + 1];
+            }
+            for (int i = threadIdx.x; i < NC; i += 128) { cbeg[i] = 0u; cend[i] = 0u; }
+            if (threadIdx.x == 0) s_cell = 0;
+            cp_async_wait<0>();
+            __syncthreads();   // this tile's keys have landed; s_next has been read by all
+            if (threadIdx.x == 0) s_next = (int)atomicAdd(tile_ctr, 1u);   // read after the tile's barriers
+            p2g_cells_tile<D, ORDER, R, G>(st, perm, kbuf, b0, b1, acc, flags, c, err, fallbacks, cellsum, cbeg,
+                                           cend, &s_cell, pslots, skeys + nb0, nb1 - nb0, kbuf);
+            t = tn;
+        }
+        cp_async_wait<0>();
+    } else {
+        for (;;) {
+            if (threadIdx.x == 0) {
+                s_tile = (int)atomicAdd(tile_ctr, 1u);
+                s_cell = 0;
+            }
+            for (int i = threadIdx.x; i < NC; i += 128) { cbeg[i] = 0u; cend[i] = 0u; }
+            __syncthreads();
+            const int t = s_tile;
+            if (t >= ntiles) break;
+            p2g_cells_tile<D, ORDER, R, G>(st, perm, skeys + tiles[t], tiles[t], tiles[t + 1], acc, flags, c, err,
+                                           fallbacks, cellsum, cbeg, cend, &s_cell, pslots);
+        }
     }
 }
 
@@ -944,7 +997,7 @@ __device__ __forceinline__ void p2g_split_tile(const PState<R>& st, const uint32
     block_coords<3, R>(blk, c, bo);
 #pragma unroll
     for (int d = 0; d < 3; ++d) bo[d] *= 4;
-    tile_cell_runs<3>(skeys, start, end, cbeg, cend, NT);
+    tile_cell_runs<3>(skeys + start, start, end, cbeg, cend, NT);
     __syncthreads();
     const uint32_t kb = cbeg[cell], ke = cend[cell];
     const int lb[3] = {cell & 3, (cell >> 2) & 3, (cell >> 4) & 3};
@@ -1864,10 +1917,10 @@ template <typename R> struct Impl {
                 k_p2g_split<3, R><<<L.p2g_grid, SplitShape<3>::NT, p2g_split_smem<3, R>(), s>>>(
                     st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc, b.flags, c, b.err);
         } else if (h.p2g_group == 2)
-            APIC_DISPATCH(h, (k_p2g_cells<D, O, R, 2><<<L.p2g_grid, 128, p2g_cells_smem<D, O, R>(), s>>>(
+            APIC_DISPATCH(h, (k_p2g_cells<D, O, R, 2><<<L.p2g_grid, 128, p2g_cells_launch_smem<D, O, R>(), s>>>(
                                  st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc, b.flags, c, b.err, b.fallbacks)));
         else
-            APIC_DISPATCH(h, (k_p2g_cells<D, O, R, 4><<<L.p2g_grid, 128, p2g_cells_smem<D, O, R>(), s>>>(
+            APIC_DISPATCH(h, (k_p2g_cells<D, O, R, 4><<<L.p2g_grid, 128, p2g_cells_launch_smem<D, O, R>(), s>>>(
                                  st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc, b.flags, c, b.err, b.fallbacks)));
         return cudaGetLastError();
         };
@@ -2137,17 +2190,17 @@ template <typename R> struct Impl {
             } else {
                 // both lane groups are set up: the group can change at the next upload
                 e = cudaFuncSetAttribute(k_p2g_cells<D, O, R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)p2g_cells_smem<D, O, R>());
+                                         (int)p2g_cells_launch_smem<D, O, R>());
                 if (e == cudaSuccess)
                     e = cudaFuncSetAttribute(k_p2g_cells<D, O, R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)p2g_cells_smem<D, O, R>());
+                                             (int)p2g_cells_launch_smem<D, O, R>());
                 int per2 = 0;
                 if (e == cudaSuccess)
                     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_p2g_cells<D, O, R, 2>, 128,
-                                                                      p2g_cells_smem<D, O, R>());
+                                                                      p2g_cells_launch_smem<D, O, R>());
                 if (e == cudaSuccess)
                     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2g_per_sm, k_p2g_cells<D, O, R, 4>, 128,
-                                                                      p2g_cells_smem<D, O, R>());
+                                                                      p2g_cells_launch_smem<D, O, R>());
                 if (e == cudaSuccess && per2 < *p2g_per_sm) *p2g_per_sm = per2;
             }
             if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(g2p_per_sm, k_g2p<D, O, R, false>, G2P_THREADS, 0);
