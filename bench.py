@@ -455,6 +455,48 @@ def _norm_rel(a, b) -> float:
     return float(np.abs(a - b).max() / den) if den > 0 else float(np.abs(a).max())
 
 
+def run_sort_scaling(args) -> int:
+    """How the step's sort and tile list scale with the share of keys that change per step.
+    The cube128 particles (4.29M, 32 per cell) move rigidly with v = 0 except a chosen share f,
+    which moves exactly one cell along x per step (v_x = dx / dt), so a share f of the keys
+    changes every step; no stress model, no gravity, no walls.  For each f: the phase times of
+    `--steps` profiled steps after 2 warm-up steps (the library's CUDA events)."""
+    import torch
+
+    from paper_1603_06188_gb300 import apic, build
+
+    build.build()
+    apic.load()
+    w = dict(WORKLOADS["cube128"])
+    sc = make_scene(w, seed=0)
+    n = sc.n
+    dt = w["dt"]
+    rng = np.random.default_rng(11)
+    steps = max(2, min(args.steps, 20))   # movers advance a cell per step and stay inside the grid
+    rows = []
+    for frac in (0.0, 0.001, 0.01, 0.1, 0.5, 1.0):
+        v = np.zeros((n, 3))
+        movers = rng.random(n) < frac
+        v[movers, 0] = sc.dx / dt
+        x = sc.x.copy()
+        cfg = apic.make_config(dim=3, order=2, precision=32, res=(w["res"],) * 3, dx=sc.dx, dt=dt, model="none",
+                               particle_mass=w["rho"] * sc.dx ** 3 / w["ppc"], particle_volume=sc.dx ** 3 / w["ppc"])
+        sim = apic.Sim(cfg, n)
+        sim.upload(x, v)
+        sim.step(2)
+        torch.cuda.synchronize()
+        sim.profile(True)
+        sim.step(steps)
+        torch.cuda.synchronize()
+        sim.profile(False)
+        ph = sim.profile_read()
+        sim.close()
+        rows.append({"moved_share": frac, "sort_ms": ph["sort"]["ms"] / steps, "tiles_ms": ph["tiles"]["ms"] / steps,
+                     "sort_launches_per_step": ph["sort"]["launches"] / steps})
+    print(json.dumps({"workload": "sortscale", "particles": n, "steps": steps, "rows": rows}))
+    return 0
+
+
 def run_drift(args) -> int:
     """Drift of the FP32 path over many steps, written to profiles/drift_fp32.md and printed
     as one JSON line:
@@ -803,7 +845,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="cube128", choices=sorted(WORKLOADS) + ["batched", "serving", "drift"])
+    ap.add_argument("--workload", default="cube128", choices=sorted(WORKLOADS) + ["batched", "serving", "drift", "sortscale"])
     ap.add_argument("--sims", type=int, default=512)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=200.0)
@@ -843,6 +885,8 @@ def main():
         return run_serving(args) if rank == 0 else 0
     if args.workload == "drift":
         return run_drift(args) if rank == 0 else 0
+    if args.workload == "sortscale":
+        return run_sort_scaling(args) if rank == 0 else 0
 
     import torch
 

@@ -147,18 +147,29 @@ __global__ void __launch_bounds__(G2P_THREADS, 4) kb_g2p(SimDesc<R>* __restrict_
     __shared__ __align__(16) SimDesc<R> sd;
     unsigned phase[2] = {0u, 0u};
     const int ntiles = (int)*ntiles_p;
-    // thread 0 starts the grid-block copies of tile t (its simulation read from global)
+    // the grid-block copies of tile t (its simulation read from global): thread 0 in the
+    // block layout, warp 0 in the dense one
+    constexpr bool DENSE = g2p_dense<ORDER>();
+    const int lane = threadIdx.x & 31;
     auto issue = [&](int t, int b) {
         const SimDesc<R>& d = descs[tile_sim[t]];
         const uint32_t blk = d.kb[kpar][tile_start[t]] >> (2 * D);
-        g2p_issue<D, R>(d.vel, blk, d.c.nb, sv[b], &mbar[b]);
+        if (DENSE) g2p_issue_dense<D, R>(d.vel, blk, d.c.nb, sv[b], &mbar[b], lane);
+        else g2p_issue<D, R>(d.vel, blk, d.c.nb, sv[b], &mbar[b]);
     };
-    if (threadIdx.x == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
-        const int t0 = (int)atomicAdd(tile_ctr + 1, 1u);
-        s_t[0] = t0;
-        if (t0 < ntiles) issue(t0, 0);
+    if (threadIdx.x < 32) {
+        int t0 = 0;
+        if (lane == 0) {
+            mbar_init(&mbar[0], 1);
+            mbar_init(&mbar[1], 1);
+            t0 = (int)atomicAdd(tile_ctr + 1, 1u);
+            s_t[0] = t0;
+            if (!DENSE && t0 < ntiles) issue(t0, 0);
+        }
+        if (DENSE) {
+            t0 = __shfl_sync(FULLMASK, t0, 0);
+            if (t0 < ntiles) issue(t0, 0);
+        }
     }
     __syncthreads();
     for (int buf = 0;; buf ^= 1) {
@@ -166,13 +177,22 @@ __global__ void __launch_bounds__(G2P_THREADS, 4) kb_g2p(SimDesc<R>* __restrict_
         if (t >= ntiles) break;
         const uint32_t sim = tile_sim[t];
         load_desc<R>(&sd, descs + sim, G2P_THREADS);
-        if (threadIdx.x == 0) {
-            const int t1 = (int)atomicAdd(tile_ctr + 1, 1u);
-            s_t[buf ^ 1] = t1;
-            if (t1 < ntiles) issue(t1, buf ^ 1);
-            const bool ok = g2p_wait(&mbar[buf], phase[buf], descs[sim].err, descs[sim].c.wait_limit);   // sd is not complete before the barrier
-            if (!ok && t1 < ntiles) mbar_wait_bounded(&mbar[buf ^ 1], phase[buf ^ 1], 1u << 22);   // drain before leaving
-            s_ok = ok ? 1 : 0;
+        if (threadIdx.x < 32) {
+            int t1 = 0;
+            if (lane == 0) {
+                t1 = (int)atomicAdd(tile_ctr + 1, 1u);
+                s_t[buf ^ 1] = t1;
+                if (!DENSE && t1 < ntiles) issue(t1, buf ^ 1);
+            }
+            if (DENSE) {
+                t1 = __shfl_sync(FULLMASK, t1, 0);
+                if (t1 < ntiles) issue(t1, buf ^ 1);
+            }
+            if (lane == 0) {
+                const bool ok = g2p_wait(&mbar[buf], phase[buf], descs[sim].err, descs[sim].c.wait_limit);   // sd is not complete before the barrier
+                if (!ok && t1 < ntiles) mbar_wait_bounded(&mbar[buf ^ 1], phase[buf ^ 1], 1u << 22);   // drain before leaving
+                s_ok = ok ? 1 : 0;
+            }
         }
         __syncthreads();
         if (!s_ok) return;

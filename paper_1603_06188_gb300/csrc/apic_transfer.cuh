@@ -1239,6 +1239,55 @@ __device__ __forceinline__ void g2p_issue(const R* __restrict__ vel, uint32_t bl
     }
 }
 
+// 3-D cubic G2P stages the dense 8^3 node array around the tile (node (x, y, z) at x + 8 y +
+// 64 z), so a stencil node's offset is a per-particle base plus a constant; the 2^D blocks'
+// rows of 4 nodes (contiguous in both layouts) are copied by the lanes of warp 0, after lane
+// 0 has set the byte count the buffer's mbarrier expects.  (Quadratic G2P keeps the block
+// layout: there the dense one raised its registers past the cap.)
+template <int ORDER> __host__ __device__ constexpr bool g2p_dense() { return ORDER == 3; }
+
+template <int D, typename R>
+__device__ __noinline__ void g2p_issue_dense(const R* __restrict__ vel, uint32_t blk, const int* nb,
+                                             R (*sv)[(D == 3) ? 64 : 16][4], uint64_t* mbar, int lane)
+{
+    constexpr int BN = (D == 3) ? 64 : 16;
+    constexpr int NB = 1 << D;
+    constexpr int ROWS = BN / 4;
+    int bc[3];
+    bc[0] = (int)(blk % (uint32_t)nb[0]);
+    if (D == 3) {
+        bc[1] = (int)((blk / (uint32_t)nb[0]) % (uint32_t)nb[1]);
+        bc[2] = (int)(blk / ((uint32_t)nb[0] * (uint32_t)nb[1]));
+    } else {
+        bc[1] = (int)(blk / (uint32_t)nb[0]);
+        bc[2] = 0;
+    }
+    unsigned nblk = 0;
+    bool inb[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        inb[q] = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            if (bc[a] + ((q >> a) & 1) >= nb[a]) inb[q] = false;
+        nblk += inb[q] ? 1u : 0u;
+    }
+    if (lane == 0) mbar_expect_tx(mbar, nblk * (unsigned)(BN * 4 * sizeof(R)));
+    __syncwarp();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    R* dense = &sv[0][0][0];
+    const unsigned row_bytes = (unsigned)(4 * 4 * sizeof(R));
+    for (int rr = lane; rr < NB * ROWS; rr += 32) {
+        const int q = rr / ROWS, r = rr % ROWS;
+        if (!inb[q]) continue;
+        const int bb[3] = {bc[0] + (q & 1), bc[1] + ((q >> 1) & 1), (D == 3) ? bc[2] + ((q >> 2) & 1) : 0};
+        const uint32_t b2 = (D == 3) ? ((uint32_t)bb[2] * nb[1] + bb[1]) * nb[0] + bb[0] : (uint32_t)bb[1] * nb[0] + bb[0];
+        const int q0 = 4 * (q & 1) + 32 * ((q >> 1) & 1) + ((D == 3) ? 256 * ((q >> 2) & 1) : 0);
+        const int y = r & 3, z = r >> 2;
+        bulk_copy_g2s(dense + 4 * (q0 + 8 * y + 64 * z), vel + ((size_t)b2 * BN + 4 * r) * 4, row_bytes, mbar);
+    }
+}
+
 // thread 0: wait (at most `limit` polls) for a buffer's copies; false on timeout, after a
 // second bounded wait that lets the copies in flight land before the CTA leaves
 __device__ __forceinline__ bool g2p_wait(uint64_t* mbar, unsigned parity, uint32_t* err, unsigned limit)
@@ -1357,15 +1406,17 @@ __device__ __forceinline__ void g2p_compute(const PState<R>& in, const PState<R>
         // at in-block index (L0&3) | (L1&3)<<2 | (L2&3)<<4 (L = lb + stencil index); its offset
         // in the staging buffer is a sum of per-axis terms, taken once per particle
         constexpr int BNN = (D == 3) ? 64 : 16;
+        constexpr bool DENSE = g2p_dense<ORDER>();
         int ox[D][K];
 #pragma unroll
         for (int a = 0; a < D; ++a)
 #pragma unroll
             for (int i = 0; i < K; ++i) {
                 const int L = lb[a] + i;
-                ox[a][i] = 4 * ((L >> 2) * (BNN << a) + (L & 3) * (1 << (2 * a)));
+                // dense 8^D layout: node lb + (i, j, k) at a per-particle base plus a constant
+                ox[a][i] = DENSE ? 4 * i * (1 << (3 * a)) : 4 * ((L >> 2) * (BNN << a) + (L & 3) * (1 << (2 * a)));
             }
-        const R* svf = &sv[0][0][0];
+        const R* svf = &sv[0][0][0] + (DENSE ? 4 * (lb[0] + 8 * lb[1] + ((D == 3) ? 64 * lb[2] : 0)) : 0);
         R rw[D][K];   // (node - fx) * w per axis
 #pragma unroll
         for (int a = 0; a < D; ++a)
@@ -1519,24 +1570,44 @@ __global__ void __launch_bounds__(G2P_THREADS, 4) k_g2p(PState<R> in, PState<R> 
     unsigned phase[2] = {0u, 0u};
     float smax_l = 0.0f;
     const int ntiles = (int)*ntiles_p;
-    if (threadIdx.x == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
-        const int t0 = (int)atomicAdd(tile_ctr + 1, 1u);
-        s_t[0] = t0;
-        if (t0 < ntiles) g2p_issue<D, R>(vel, skeys[tiles[t0]] >> (2 * D), c.nb, sv[0], &mbar[0]);
+    constexpr bool DENSE = g2p_dense<ORDER>();
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        int t0 = 0;
+        if (lane == 0) {
+            mbar_init(&mbar[0], 1);
+            mbar_init(&mbar[1], 1);
+            t0 = (int)atomicAdd(tile_ctr + 1, 1u);
+            s_t[0] = t0;
+            if (!DENSE && t0 < ntiles) g2p_issue<D, R>(vel, skeys[tiles[t0]] >> (2 * D), c.nb, sv[0], &mbar[0]);
+        }
+        if (DENSE) {
+            t0 = __shfl_sync(FULLMASK, t0, 0);
+            if (t0 < ntiles) g2p_issue_dense<D, R>(vel, skeys[tiles[t0]] >> (2 * D), c.nb, sv[0], &mbar[0], lane);
+        }
     }
     __syncthreads();
     for (int buf = 0;; buf ^= 1) {
         const int t = s_t[buf];
         if (t >= ntiles) break;
-        if (threadIdx.x == 0) {
-            const int t1 = (int)atomicAdd(tile_ctr + 1, 1u);
-            s_t[buf ^ 1] = t1;
-            if (t1 < ntiles) g2p_issue<D, R>(vel, skeys[tiles[t1]] >> (2 * D), c.nb, sv[buf ^ 1], &mbar[buf ^ 1]);
-            const bool ok = g2p_wait(&mbar[buf], phase[buf], err, c.wait_limit);
-            if (!ok && t1 < ntiles) mbar_wait_bounded(&mbar[buf ^ 1], phase[buf ^ 1], 1u << 22);   // drain before leaving
-            s_ok = ok ? 1 : 0;
+        if (threadIdx.x < 32) {
+            int t1 = 0;
+            if (lane == 0) {
+                t1 = (int)atomicAdd(tile_ctr + 1, 1u);
+                s_t[buf ^ 1] = t1;
+                if (!DENSE && t1 < ntiles)
+                    g2p_issue<D, R>(vel, skeys[tiles[t1]] >> (2 * D), c.nb, sv[buf ^ 1], &mbar[buf ^ 1]);
+            }
+            if (DENSE) {
+                t1 = __shfl_sync(FULLMASK, t1, 0);
+                if (t1 < ntiles)
+                    g2p_issue_dense<D, R>(vel, skeys[tiles[t1]] >> (2 * D), c.nb, sv[buf ^ 1], &mbar[buf ^ 1], lane);
+            }
+            if (lane == 0) {
+                const bool ok = g2p_wait(&mbar[buf], phase[buf], err, c.wait_limit);
+                if (!ok && t1 < ntiles) mbar_wait_bounded(&mbar[buf ^ 1], phase[buf ^ 1], 1u << 22);   // drain before leaving
+                s_ok = ok ? 1 : 0;
+            }
         }
         __syncthreads();
         if (!s_ok) return;
