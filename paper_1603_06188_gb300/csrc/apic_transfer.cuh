@@ -247,10 +247,18 @@ __device__ __forceinline__ void read_staged(const R* slot, Particle<D, R>& p, bo
 // staging depth (particles in flight per lane) of the cell-parallel P2G
 template <typename R> __host__ __device__ constexpr int p2g_slots() { return 2; }
 
+// the per-cell stencil sums of a tile, one row per base cell: rows are padded by 16 bytes
+// when their length in 4-byte words is a multiple of 8, so that the rows read by 8 lanes at
+// once (consecutive cells, the same stencil entry) start in different bank groups
+template <int D, int ORDER, typename R> __host__ __device__ constexpr int p2g_cell_stride()
+{
+    constexpr int nval = ((D == 3) ? (ORDER + 1) * (ORDER + 1) * (ORDER + 1) : (ORDER + 1) * (ORDER + 1)) * (D + 1);
+    constexpr int words = nval * (int)(sizeof(R) / 4);
+    return (words % 8 == 0) ? nval + 16 / (int)sizeof(R) : nval;
+}
 template <int D, int ORDER, typename R> __host__ __device__ constexpr size_t p2g_cellsum_bytes()
 {
-    return (size_t)((D == 3) ? 64 : 16) * ((D == 3) ? (ORDER + 1) * (ORDER + 1) * (ORDER + 1) : (ORDER + 1) * (ORDER + 1)) *
-           (D + 1) * sizeof(R);
+    return (size_t)((D == 3) ? 64 : 16) * p2g_cell_stride<D, ORDER, R>() * sizeof(R);
 }
 // dynamic shared memory of the cell-parallel P2G: per-cell sums, then the staging slots
 template <int D, int ORDER, typename R> __host__ __device__ constexpr size_t p2g_cells_smem()
@@ -426,7 +434,7 @@ __device__ __forceinline__ void tile_flush_nodes(const R* cellsum, uint64_t occ,
             const int ia = j % K, ib = (j / K) % K, ic = j / (K * K);
             const int dj = ia + 4 * ib + 16 * ic;
             if (!((t >> (DM - dj)) & 1ull)) continue;
-            const R* src = cellsum + (size_t)(cl0 - dj) * NVAL + j * NV;
+            const R* src = cellsum + (size_t)(cl0 - dj) * p2g_cell_stride<D, ORDER, R>() + j * NV;
 #pragma unroll
             for (int v = 0; v < NV; ++v) sum[v] += src[v];
         }
@@ -734,7 +742,7 @@ __device__ __forceinline__ void p2g_cells_tile(const PState<R>& st, const uint32
             ReduceScatter<R, NVS, G>::run(cur, FULLMASK, lig, off, cnt);
             constexpr int FIN = ReduceScatter<R, NVS, G>::FINAL;
             if (has) {
-                R* dst = cellsum + (size_t)cell * NVAL + (size_t)slab * NVS + off;
+                R* dst = cellsum + (size_t)cell * p2g_cell_stride<D, ORDER, R>() + (size_t)slab * NVS + off;
 #pragma unroll
                 for (int i = 0; i < FIN; ++i)
                     if (i < cnt) dst[i] = cur[i];
@@ -761,7 +769,7 @@ __global__ void __launch_bounds__(128, (cells_ctas_per_sm<D, ORDER>())) k_p2g_ce
 {
     constexpr int NC = (D == 3) ? 64 : 16;
     extern __shared__ __align__(32) unsigned char p2g_smem[];
-    R* cellsum = reinterpret_cast<R*>(p2g_smem);   // [NC][NVAL]
+    R* cellsum = reinterpret_cast<R*>(p2g_smem);   // [NC][cell stride]
     R* pslots = reinterpret_cast<R*>(p2g_smem + (p2g_cellsum_bytes<D, ORDER, R>() + 31) / 32 * 32);
     __shared__ uint32_t cbeg[NC], cend[NC];
     __shared__ int s_tile, s_cell, s_next;
@@ -1037,7 +1045,7 @@ __device__ __forceinline__ void p2g_split_tile(const PState<R>& st, const uint32
         }
         cp_async_wait<0>();
         if (run > 0u) {
-            R* dst = cellsum + (size_t)cell * NVAL + 2 * h;
+            R* dst = cellsum + (size_t)cell * p2g_cell_stride<3, ORDER, R>() + 2 * h;
 #pragma unroll
             for (int icl = 0; icl < KZ; ++icl)
 #pragma unroll
@@ -1064,7 +1072,7 @@ __global__ void __launch_bounds__(SplitShape<ORDER>::NT, (split_ctas_per_sm<ORDE
 {
     constexpr int NT = SplitShape<ORDER>::NT;
     extern __shared__ __align__(32) unsigned char p2g_smem[];
-    R* cellsum = reinterpret_cast<R*>(p2g_smem);   // [64][NVAL]
+    R* cellsum = reinterpret_cast<R*>(p2g_smem);   // [64][cell stride]
     R* pslots = reinterpret_cast<R*>(p2g_smem + (p2g_cellsum_bytes<3, ORDER, R>() + 31) / 32 * 32);
     __shared__ uint32_t cbeg[64], cend[64];
     __shared__ int s_tile;
@@ -1650,14 +1658,101 @@ __device__ __forceinline__ void block_sum6(double* a, double* part)
     }
 }
 
+// Exact FP32 building blocks of the FP32 momentum sums: a running sum hi + lo that takes an
+// FP32 term with no error beyond the rounding of lo (Knuth's TwoSum puts the rounding error
+// of hi + x into lo), and the product of two FP32 numbers as p + e exactly (e by one fused
+// multiply-add).  With an FP32 state every term of the momentum is such a product or value,
+// so the sums carry about 48 bits, and the FP32 pipe does what FP64 arithmetic per particle
+// would otherwise do at a small fraction of its rate.
+struct SumF {
+    float hi, lo;
+};
+__device__ __forceinline__ void sumf_add(SumF& a, float x)
+{
+    const float s = __fadd_rn(a.hi, x);
+    const float bp = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    a.hi = s;
+    a.lo = __fadd_rn(a.lo, e);
+}
+__device__ __forceinline__ void sumf_add_prod(SumF& a, float x, float y)
+{
+    const float p = __fmul_rn(x, y);
+    const float e = __fmaf_rn(x, y, -p);   // x y = p + e exactly
+    sumf_add(a, p);
+    a.lo = __fadd_rn(a.lo, e);             // |e| <= ulp(p) / 2: lo's own rounding covers it
+}
+__device__ __forceinline__ double sumf_value(const SumF& a) { return (double)a.hi + (double)a.lo; }
+
 template <int D, typename R>
 __global__ void __launch_bounds__(TPB) k_mom_particles(PState<R> st, DevCfg<R> c, double mass_cfg, double dx,
                                                        double o0, double o1, double o2, double* part)
 {
-    // every particle's terms in FP64 from its state widened exactly (the position as
-    // origin + (cell + offset) dx, so the offset keeps its full precision), sums in FP64
     double a[6] = {0, 0, 0, 0, 0, 0};
     const double org[3] = {o0, o1, o2};
+    if (sizeof(R) == 4 && !c.mat) {
+        // FP32 state, one mass: with x = org + dx (cell + o),
+        //   p = m sum v,  l = m (org x sum v + dx sum (cell + o) x v + sum B^T : eps)
+        // every term of the three sums an FP32 value or an exact product of two
+        SumF sv[3] = {}, sx[3] = {}, sb[3] = {};
+        for (int k = blockIdx.x * TPB + threadIdx.x; k < c.n; k += gridDim.x * TPB) {
+            Particle<D, R> p;
+            load_x<D, R>(st, k, p);
+            load_vB<D, R>(st, k, p);
+            float cf[3] = {0.0f, 0.0f, 0.0f}, of[3] = {0.0f, 0.0f, 0.0f}, vf[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                cf[d] = (float)p.cell[d];   // exact: a cell index is far below 2^24
+                of[d] = (float)p.o[d];
+                vf[d] = (float)p.v[d];
+                sumf_add(sv[d], vf[d]);
+            }
+            // (cell + o) x v, component q = (a b): t_a v_b - t_b v_a
+#pragma unroll
+            for (int q = 0; q < ((D == 3) ? 3 : 1); ++q) {
+                const int ia = (D == 3) ? (q + 1) % 3 : 0, ib = (D == 3) ? (q + 2) % 3 : 1;
+                const int out = (D == 3) ? q : 0;
+                sumf_add_prod(sx[out], cf[ia], vf[ib]);
+                sumf_add_prod(sx[out], of[ia], vf[ib]);
+                sumf_add_prod(sx[out], -cf[ib], vf[ia]);
+                sumf_add_prod(sx[out], -of[ib], vf[ia]);
+            }
+            if (c.transfer == 0) {   // (B_p)^T : eps of Sec. 5.3
+                if (D == 3) {
+                    sumf_add(sb[0], (float)p.B[7]);
+                    sumf_add(sb[0], -(float)p.B[5]);
+                    sumf_add(sb[1], (float)p.B[2]);
+                    sumf_add(sb[1], -(float)p.B[6]);
+                    sumf_add(sb[2], (float)p.B[3]);
+                    sumf_add(sb[2], -(float)p.B[1]);
+                } else {
+                    sumf_add(sb[0], (float)p.B[2]);
+                    sumf_add(sb[0], -(float)p.B[1]);
+                }
+            }
+        }
+        double v[3], x[3], b[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            v[d] = sumf_value(sv[d]);
+            x[d] = sumf_value(sx[d]);
+            b[d] = sumf_value(sb[d]);
+        }
+#pragma unroll
+        for (int d = 0; d < D; ++d) a[d] = mass_cfg * v[d];
+        if (D == 3) {
+            a[3] = mass_cfg * (org[1] * v[2] - org[2] * v[1] + dx * x[0] + b[0]);
+            a[4] = mass_cfg * (org[2] * v[0] - org[0] * v[2] + dx * x[1] + b[1]);
+            a[5] = mass_cfg * (org[0] * v[1] - org[1] * v[0] + dx * x[2] + b[2]);
+        } else {
+            a[3] = mass_cfg * (org[0] * v[1] - org[1] * v[0] + dx * x[0] + b[0]);
+        }
+        block_sum6(a, part);
+        return;
+    }
+    // FP64 state or a mass per particle: every particle's terms in FP64 from its state
+    // widened exactly (the position as origin + (cell + offset) dx, so the offset keeps its
+    // full precision), sums in FP64
     for (int k = blockIdx.x * TPB + threadIdx.x; k < c.n; k += gridDim.x * TPB) {
         Particle<D, R> p;
         load_x<D, R>(st, k, p);
