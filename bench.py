@@ -782,19 +782,33 @@ def single_block(args, wname: str, rank: int, world: int, local: int, dist, with
         hx[:], hv[:], hB[:], hF[:] = x, v, B, F
         ox, ov, oB, oF = pin((n, 3)), pin((n, 3)), pin((n, 3, 3)), pin((n, 3, 3))
         e_steps = max(1, min(steps, 100))
+
+        def e2e_pass(k):
+            marks = [time.perf_counter()]
+            apic.apic_upload(sim.handle, n, hx, hv, hB, hF, on_device=0)
+            marks.append(time.perf_counter())
+            for _ in range(k):
+                sim.step(1)
+                sim.momentum("particles")
+            marks.append(time.perf_counter())
+            apic.apic_download(sim.handle, ox, ov, oB, oF, on_device=0)
+            torch.cuda.synchronize()
+            marks.append(time.perf_counter())
+            return marks
+
+        # one untimed pass of two steps first: the first copies through freshly pinned pages
+        # pay a one-time cost that is not the interface's
+        e2e_pass(2)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        apic.apic_upload(sim.handle, n, hx, hv, hB, hF, on_device=0)
-        for _ in range(e_steps):
-            sim.step(1)
-            sim.momentum("particles")
-        apic.apic_download(sim.handle, ox, ov, oB, oF, on_device=0)
-        torch.cuda.synchronize()
-        et = time.perf_counter() - t0
+        marks = e2e_pass(e_steps)
+        et = marks[3] - marks[0]
         state_bytes = n * (3 + 3 + 9 + 9) * 8
         e2e = {"value": n * e_steps / et * world, "unit": UNIT, "steps": e_steps,
-               "note": f"one upload and one download of the whole state around {e_steps} steps, the FP64 "
-                       "momentum read back after every step",
+               "note": f"one upload and one download of the whole state (FP64, pinned host buffers) around "
+                       f"{e_steps} steps, the FP64 momentum read back after every step; after one untimed "
+                       "pass of two steps over the same buffers",
+               "ms": {"upload": (marks[1] - marks[0]) * 1e3, "steps_with_momentum": (marks[2] - marks[1]) * 1e3,
+                      "download": (marks[3] - marks[2]) * 1e3},
                "h2d_bytes_per_step": state_bytes / e_steps, "d2h_bytes_per_step": state_bytes / e_steps + 48}
 
     cpu = None

@@ -925,25 +925,27 @@ __device__ __forceinline__ void p2g_split_particle(const R* slot, bool live, int
     {
         const V4<R> ta = *reinterpret_cast<const V4<R>*>(slot + 16);   // t00 t11 t22 t01
         const V2<R> tb = *reinterpret_cast<const V2<R>*>(slot + 20);   // t02 t12
-        TA[0] = tau_on ? dt_dx * (hi ? tb.x : ta.x) : R(0);
-        TA[1] = tau_on ? dt_dx * (hi ? tb.y : ta.w) : R(0);
-        TA[2] = tau_on ? dt_dx * (hi ? ta.z : tb.x) : R(0);
-        TB[0] = (tau_on && !hi) ? dt_dx * ta.w : R(0);
-        TB[1] = (tau_on && !hi) ? dt_dx * ta.y : R(0);
-        TB[2] = (tau_on && !hi) ? dt_dx * tb.y : R(0);
+        // T = -dt/dx tau (the sign folded in, so every factor below is a sum of products)
+        TA[0] = tau_on ? -dt_dx * (hi ? tb.x : ta.x) : R(0);
+        TA[1] = tau_on ? -dt_dx * (hi ? tb.y : ta.w) : R(0);
+        TA[2] = tau_on ? -dt_dx * (hi ? ta.z : tb.x) : R(0);
+        TB[0] = (tau_on && !hi) ? -dt_dx * ta.w : R(0);
+        TB[1] = (tau_on && !hi) ? -dt_dx * ta.y : R(0);
+        TB[2] = (tau_on && !hi) ? -dt_dx * tb.y : R(0);
     }
     // separable sums as in the cell-parallel kernel, for the lane's two rows and z-half
     //   sum_c(i,j,k) = w0_i P_c(j,k) + E_c(i) S(j,k),  S = w1_j w2_k
-    //   P_c(j,k) = w1_j Q_c(k) + H_c(j) w2_k,  Q_c(k) = mv_c w2_k + C_c2 (r w)2_k - T_c2 dw2_k
-    //   H_c(j) = C_c1 (r w)1_j - T_c1 dw1_j,    E_c(i) = C_c0 (r w)0_i - T_c0 dw0_i
+    //   P_c(j,k) = w1_j Q_c(k) + H_c(j) w2_k,  Q_c(k) = mv_c w2_k + C_c2 (r w)2_k + T_c2 dw2_k
+    //   H_c(j) = C_c1 (r w)1_j + T_c1 dw1_j,    E_c(i) = C_c0 (r w)0_i + T_c0 dw0_i
+    // the two rows' factors formed together in packed pairs
     R EA[K], EB[K], HA[K], HB[K];
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         const R rw0 = (R(i) - fx[0]) * w[0][i], rw1 = (R(i) - fx[1]) * w[1][i];
-        EA[i] = CA[0] * rw0 - TA[0] * dw[0][i];
-        EB[i] = CB[0] * rw0 - TB[0] * dw[0][i];
-        HA[i] = CA[1] * rw1 - TA[1] * dw[1][i];
-        HB[i] = CB[1] * rw1 - TB[1] * dw[1][i];
+        mul_pair<R>(EA[i], EB[i], CA[0], CB[0], rw0, rw0);
+        fma_pair<R>(EA[i], EB[i], TA[0], TB[0], dw[0][i], dw[0][i]);
+        mul_pair<R>(HA[i], HB[i], CA[1], CB[1], rw1, rw1);
+        fma_pair<R>(HA[i], HB[i], TA[1], TB[1], dw[1][i], dw[1][i]);
     }
 #pragma unroll
     for (int icl = 0; icl < KZ; ++icl) {
@@ -953,13 +955,17 @@ __device__ __forceinline__ void p2g_split_particle(const R* slot, bool live, int
         const R dw2 = (ORDER == 3 && zs) ? dw[2][(KZ + icl) % K] : dw[2][icl];
         const R z = (ORDER == 3 && zs) ? R(KZ + icl) : R(icl);
         const R rw2 = (z - fx[2]) * w2;
-        const R QA = mvA * w2 + CA[2] * rw2 - TA[2] * dw2;
-        const R QB = mvB * w2 + CB[2] * rw2 - TB[2] * dw2;
+        R QA, QB;
+        mul_pair<R>(QA, QB, mvA, mvB, w2, w2);
+        fma_pair<R>(QA, QB, CA[2], CB[2], rw2, rw2);
+        fma_pair<R>(QA, QB, TA[2], TB[2], dw2, dw2);
 #pragma unroll
         for (int ib = 0; ib < K; ++ib) {
-            const R S = w[1][ib] * w2;
-            const R PA = w[1][ib] * QA + HA[ib] * w2;
-            const R PB = w[1][ib] * QB + HB[ib] * w2;
+            const R w1 = w[1][ib];
+            const R S = w1 * w2;
+            R PA, PB;
+            mul_pair<R>(PA, PB, w1, w1, QA, QB);
+            fma_pair<R>(PA, PB, HA[ib], HB[ib], w2, w2);
 #pragma unroll
             for (int ia = 0; ia < K; ++ia) {
                 const int j = ia + K * ib + K * K * icl;
