@@ -21,6 +21,8 @@
 
 using namespace apic;
 
+constexpr int kCopyEvents = 18;   // pieces of a host transfer (at most 16) and two more
+
 struct apic_sim {
     apic_batch* batch;     // the batch this simulation belongs to, if any
     HostCfg c;
@@ -41,6 +43,11 @@ struct apic_sim {
     std::string err;
     int64_t launches;      // kernels launched since creation
     double solve_stats[3]; // the last midpoint solve: Newton and CG iterations, final residual
+    // host uploads and downloads in pieces: copies on their own stream, ordered against the
+    // simulation's stream by events, so a piece's copies overlap the kernel of another
+    cudaStream_t cstream;
+    cudaEvent_t cev[kCopyEvents];
+    bool copy_ready;
     // per-phase timing
     bool prof_on;
     std::vector<cudaEvent_t> ev_pool;
@@ -313,6 +320,31 @@ apic_status batch_sync_member(apic_sim* s);
 
 #define DISPATCH(s, fn, ...) ((s)->c.precision == 32 ? fn##_f32(__VA_ARGS__) : fn##_f64(__VA_ARGS__))
 
+// the copy stream and events of a simulation's host transfers, made on first use
+cudaError_t ensure_copy_stream(apic_sim* s)
+{
+    if (s->copy_ready) return cudaSuccess;
+    cudaError_t e = cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking);
+    int made = 0;
+    for (; e == cudaSuccess && made < kCopyEvents; ++made)
+        e = cudaEventCreateWithFlags(&s->cev[made], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        for (int i = 0; i < made; ++i) cudaEventDestroy(s->cev[i]);
+        if (s->cstream) cudaStreamDestroy(s->cstream);
+        s->cstream = nullptr;
+        return e;
+    }
+    s->copy_ready = true;
+    return cudaSuccess;
+}
+
+// pieces of a host transfer of n particles: about half a million particles each, at most 16
+int copy_pieces(int64_t n)
+{
+    const int64_t p = (n + (int64_t)(1 << 19) - 1) >> 19;
+    return (int)(p < 1 ? 1 : (p > 16 ? 16 : p));
+}
+
 }  // namespace
 
 extern "C" {
@@ -446,6 +478,11 @@ apic_status apic_destroy(apic_sim* s)
     if (s->batch) apic_batch_remove(s->batch, s);
     cudaError_t e = cudaStreamSynchronize(s->stream);
     for (cudaEvent_t ev : s->ev_pool) cudaEventDestroy(ev);
+    if (s->copy_ready) {
+        cudaStreamSynchronize(s->cstream);
+        for (cudaEvent_t ev : s->cev) cudaEventDestroy(ev);
+        cudaStreamDestroy(s->cstream);
+    }
     delete s;
     return e == cudaSuccess ? APIC_OK : APIC_ERR_CUDA;
 }
@@ -460,22 +497,6 @@ apic_status apic_upload(apic_sim* s, int64_t n, const double* x, const double* v
     if (n > 0 && !x) return fail(s, APIC_ERR_ARG, "positions are required");
     CK(cudaSetDevice(s->device), "cudaSetDevice");
     const int d = s->c.dim;
-    const double *dx_ = x, *dv = v, *dB = B, *dF = F;
-    if (!on_device && n > 0) {
-        double* st = s->b.staging;
-        double* sx = st;
-        double* sv = sx + n * d;
-        double* sB = sv + n * d;
-        double* sF = sB + n * d * d;
-        CK(cudaMemcpyAsync(sx, x, sizeof(double) * n * d, cudaMemcpyHostToDevice, s->stream), "upload x");
-        if (v) CK(cudaMemcpyAsync(sv, v, sizeof(double) * n * d, cudaMemcpyHostToDevice, s->stream), "upload v");
-        if (B) CK(cudaMemcpyAsync(sB, B, sizeof(double) * n * d * d, cudaMemcpyHostToDevice, s->stream), "upload B");
-        if (F) CK(cudaMemcpyAsync(sF, F, sizeof(double) * n * d * d, cudaMemcpyHostToDevice, s->stream), "upload F");
-        dx_ = sx;
-        dv = v ? sv : nullptr;
-        dB = B ? sB : nullptr;
-        dF = F ? sF : nullptr;
-    }
     s->n = n;
     s->cur = 0;
     s->keys_valid = false;
@@ -484,7 +505,39 @@ apic_status apic_upload(apic_sim* s, int64_t n, const double* x, const double* v
     s->order_sorted = false;
     s->group_pending = s->c.p2g_group_auto != 0;   // the new particle set's density decides
     s->c.mat = 0;   // a new particle set: materials come from the configuration until set again
-    CK(DISPATCH(s, upload, s->c, s->b, s->cur, n, dx_, dv, dB, dF, s->stream), "upload kernel");
+    if (on_device || n == 0) {
+        CK(DISPATCH(s, upload, s->c, s->b, s->cur, n, x, v, B, F, s->stream, (int64_t)0, n), "upload kernel");
+    } else {
+        // host input: in pieces, each piece's copies on the copy stream and its kernel on the
+        // simulation's stream after them, so copies and kernels overlap; the copy stream
+        // first waits for the simulation's earlier work (it may still read the staging buffer)
+        CK(ensure_copy_stream(s), "copy stream");
+        double* sx = s->b.staging;
+        double* sv = sx + n * d;
+        double* sB = sv + n * d;
+        double* sF = sB + n * d * d;
+        const int pieces = copy_pieces(n);
+        CK(cudaEventRecord(s->cev[kCopyEvents - 1], s->stream), "event");
+        CK(cudaStreamWaitEvent(s->cstream, s->cev[kCopyEvents - 1], 0), "stream wait");
+        for (int p = 0; p < pieces; ++p) {
+            const int64_t k0 = n * p / pieces, k1 = n * (p + 1) / pieces, m = k1 - k0;
+            CK(cudaMemcpyAsync(sx + k0 * d, x + k0 * d, sizeof(double) * m * d, cudaMemcpyHostToDevice, s->cstream),
+               "upload x");
+            if (v)
+                CK(cudaMemcpyAsync(sv + k0 * d, v + k0 * d, sizeof(double) * m * d, cudaMemcpyHostToDevice,
+                                   s->cstream), "upload v");
+            if (B)
+                CK(cudaMemcpyAsync(sB + k0 * d * d, B + k0 * d * d, sizeof(double) * m * d * d,
+                                   cudaMemcpyHostToDevice, s->cstream), "upload B");
+            if (F)
+                CK(cudaMemcpyAsync(sF + k0 * d * d, F + k0 * d * d, sizeof(double) * m * d * d,
+                                   cudaMemcpyHostToDevice, s->cstream), "upload F");
+            CK(cudaEventRecord(s->cev[p], s->cstream), "event");
+            CK(cudaStreamWaitEvent(s->stream, s->cev[p], 0), "stream wait");
+            CK(DISPATCH(s, upload, s->c, s->b, s->cur, n, sx, v ? sv : nullptr, B ? sB : nullptr, F ? sF : nullptr,
+                        s->stream, k0, k1), "upload kernel");
+        }
+    }
     if (!on_device) {
         uint32_t bits = 0;
         apic_status st = check_device(s, &bits);
@@ -573,17 +626,40 @@ apic_status apic_download(apic_sim* s, double* x, double* v, double* B, double* 
         CK(DISPATCH(s, download, s->c, s->b, s->cur, n, x, v, B, F, nullptr, nullptr, s->stream), "download kernel");
         return check_device(s);
     }
+    // host output: the particles are gathered in upload order piece by piece (through the
+    // inverse of their id lane, kept in the sort's moved-index scratch, free between steps),
+    // and each piece's copies start on the copy stream as soon as its kernel is done
+    CK(ensure_copy_stream(s), "copy stream");
     double* sx = s->b.staging;
     double* sv = sx + n * d;
     double* sB = sv + n * d;
     double* sF = sB + n * d * d;
-    CK(DISPATCH(s, download, s->c, s->b, s->cur, n, x ? sx : nullptr, v ? sv : nullptr, B ? sB : nullptr,
-                F ? sF : nullptr, nullptr, nullptr, s->stream),
-       "download kernel");
-    if (x) CK(cudaMemcpyAsync(x, sx, sizeof(double) * n * d, cudaMemcpyDeviceToHost, s->stream), "download x");
-    if (v) CK(cudaMemcpyAsync(v, sv, sizeof(double) * n * d, cudaMemcpyDeviceToHost, s->stream), "download v");
-    if (B) CK(cudaMemcpyAsync(B, sB, sizeof(double) * n * d * d, cudaMemcpyDeviceToHost, s->stream), "download B");
-    if (F) CK(cudaMemcpyAsync(F, sF, sizeof(double) * n * d * d, cudaMemcpyDeviceToHost, s->stream), "download F");
+    uint32_t* inv = s->b.midx;
+    CK(DISPATCH(s, inverse_ids, s->c, s->b, s->cur, n, inv, s->stream), "id inverse kernel");
+    const int pieces = copy_pieces(n);
+    for (int p = 0; p < pieces; ++p) {
+        const int64_t k0 = n * p / pieces, k1 = n * (p + 1) / pieces, m = k1 - k0;
+        CK(DISPATCH(s, download_ids, s->c, s->b, s->cur, n, inv, k0, k1, x ? sx : nullptr, v ? sv : nullptr,
+                    B ? sB : nullptr, F ? sF : nullptr, s->stream),
+           "download kernel");
+        CK(cudaEventRecord(s->cev[p], s->stream), "event");
+        CK(cudaStreamWaitEvent(s->cstream, s->cev[p], 0), "stream wait");
+        if (x)
+            CK(cudaMemcpyAsync(x + k0 * d, sx + k0 * d, sizeof(double) * m * d, cudaMemcpyDeviceToHost, s->cstream),
+               "download x");
+        if (v)
+            CK(cudaMemcpyAsync(v + k0 * d, sv + k0 * d, sizeof(double) * m * d, cudaMemcpyDeviceToHost, s->cstream),
+               "download v");
+        if (B)
+            CK(cudaMemcpyAsync(B + k0 * d * d, sB + k0 * d * d, sizeof(double) * m * d * d, cudaMemcpyDeviceToHost,
+                               s->cstream), "download B");
+        if (F)
+            CK(cudaMemcpyAsync(F + k0 * d * d, sF + k0 * d * d, sizeof(double) * m * d * d, cudaMemcpyDeviceToHost,
+                               s->cstream), "download F");
+    }
+    // later work on the simulation's stream (and the synchronisation below) waits for the copies
+    CK(cudaEventRecord(s->cev[kCopyEvents - 2], s->cstream), "event");
+    CK(cudaStreamWaitEvent(s->stream, s->cev[kCopyEvents - 2], 0), "stream wait");
     return check_device(s);
 }
 

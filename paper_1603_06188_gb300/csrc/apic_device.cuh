@@ -290,6 +290,31 @@ __device__ __forceinline__ void axis_weights(R o, int cell, int& base, R& fx, R*
     }
 }
 
+// The 1-D weights and derivatives from the distance fx to the base node alone (as
+// axis_weights, for a caller that knows the base)
+template <int ORDER, typename R> __device__ __forceinline__ void axis_weights_fx(R fx, R* w, R* dw)
+{
+    if (ORDER == 2) {
+        const R t0 = R(1.5) - fx, t1 = fx - R(1), t2 = fx - R(0.5);
+        w[0] = R(0.5) * t0 * t0;
+        w[1] = R(0.75) - t1 * t1;
+        w[2] = R(0.5) * t2 * t2;
+        dw[0] = -t0;
+        dw[1] = R(-2) * t1;
+        dw[2] = t2;
+    } else {
+        const R a0 = R(2) - fx, a1 = fx - R(1), a2 = R(2) - fx, a3 = fx - R(1);
+        w[0] = a0 * a0 * a0 * (R(1) / R(6));
+        w[1] = R(0.5) * a1 * a1 * a1 - a1 * a1 + R(2) / R(3);
+        w[2] = R(0.5) * a2 * a2 * a2 - a2 * a2 + R(2) / R(3);
+        w[3] = a3 * a3 * a3 * (R(1) / R(6));
+        dw[0] = R(-0.5) * a0 * a0;
+        dw[1] = R(1.5) * a1 * a1 - R(2) * a1;
+        dw[2] = -(R(1.5) * a2 * a2 - R(2) * a2);
+        dw[3] = R(0.5) * a3 * a3;
+    }
+}
+
 // ---------------------------------------------------------------- small matrices
 template <typename R> __device__ __forceinline__ R det3(const R* A)
 {

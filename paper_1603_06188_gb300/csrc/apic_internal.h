@@ -151,7 +151,13 @@ struct Launch {
     cudaError_t g2p_##SFX(const HostCfg& c, const Buffers& b, int cur, const uint32_t* skeys,                 \
                           const uint32_t* perm, int64_t n, const Launch& L, cudaStream_t s);                   \
     cudaError_t upload_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const double* x,         \
-                             const double* v, const double* B, const double* F, cudaStream_t s);              \
+                             const double* v, const double* B, const double* F, cudaStream_t s, int64_t k0,   \
+                             int64_t k1);                                                                      \
+    cudaError_t inverse_ids_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, uint32_t* inv,       \
+                                  cudaStream_t s);                                                             \
+    cudaError_t download_ids_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const uint32_t* inv,\
+                                   int64_t id0, int64_t id1, double* x, double* v, double* B, double* F,       \
+                                   cudaStream_t s);                                                            \
     cudaError_t download_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, double* x, double* v,  \
                                double* B, double* F, int32_t* cell, double* off, cudaStream_t s);              \
     cudaError_t momentum_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, int where,             \

@@ -520,24 +520,27 @@ __device__ __forceinline__ void p2g_cells_particle(Particle<D, R>& p, bool live,
 {
     constexpr int K = ORDER + 1;
     constexpr int NV = D + 1;
-    if (!live) {   // neutral: an in-cell position and zero state (finite weights, zero sums)
+    if (!live) {   // neutral: zero state (the weights below are those of an in-cell point)
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-            p.o[a] = R(0.5);
-            p.cell[a] = bo[a] + lb[a] + (ORDER == 3 ? 1 : 0);
-            p.v[a] = R(0);
-        }
+        for (int a = 0; a < D; ++a) p.v[a] = R(0);
 #pragma unroll
         for (int i = 0; i < D * D; ++i) p.B[i] = R(0);
 #pragma unroll
         for (int i = 0; i < ((D == 3) ? 6 : 3); ++i) p.tau[i] = R(0);
     }
-    int base[D];
+    // The stencil base of the lane's cell is known (bo + lb), so only the particle's distance
+    // from it is needed: fx = o + (cell - base), with cell - base = 1 - [o >= 1/2] (quadratic)
+    // or 1 (cubic) exactly when the particle's own base is that node (as axis_weights
+    // decides); a particle outside its run's cell is reported and adds nothing
     R w[D][K], dw[D][K], fx[D];
-    bool ok = particle_stencil<D, ORDER, R>(p.o, p.cell, c, base, fx, w, dw);
+    bool ok = true;
 #pragma unroll
-    for (int a = 0; a < D; ++a)
-        if (base[a] - bo[a] != lb[a]) ok = false;
+    for (int a = 0; a < D; ++a) {
+        const int d = p.cell[a] - (bo[a] + lb[a]);
+        ok = ok && (d == ((ORDER == 2) ? (p.o[a] >= R(0.5) ? 0 : 1) : 1));
+        fx[a] = live ? p.o[a] + R(d) : ((ORDER == 2) ? R(1) : R(1.5));
+        axis_weights_fx<ORDER, R>(fx[a], w[a], dw[a]);
+    }
     if (live && !ok) {
         set_err(err, APIC_ERRBIT_RANGE);
         live = false;
@@ -1890,10 +1893,11 @@ template <int D, typename R>
 __global__ void __launch_bounds__(TPB) k_upload(PState<R> st, DevCfg<R> c, double dx, double o0, double o1, double o2,
                                                 const double* __restrict__ x, const double* __restrict__ v,
                                                 const double* __restrict__ B, const double* __restrict__ F,
-                                                uint32_t* err, uint32_t* fallbacks)
+                                                uint32_t* err, uint32_t* fallbacks, int64_t k0, int64_t k1)
 {
-    const int k = blockIdx.x * TPB + threadIdx.x;
-    if (k >= c.n) return;
+    // particles [k0, k1) of the upload (a host upload runs in pieces, each after its copies)
+    const int64_t k = k0 + (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (k >= k1) return;
     const double org[3] = {o0, o1, o2};
     Particle<D, R> p;
     p.id = (uint32_t)k;
@@ -1992,6 +1996,53 @@ __global__ void k_adapt_dt(R* dtw, const uint32_t* smax, const double* speed64, 
     const double sp = first ? speed64[0] : (double)__uint_as_float(*smax);
     const double dt = sp > 0.0 ? fmin(dt_max, nu * dx / sp) : dt_max;
     *dtw = (R)dt;
+}
+
+// inv[id] = the storage slot of the particle uploaded at index id (inv filled with ~0 first);
+// an id out of range is not valid state and is reported
+template <int D, typename R>
+__global__ void __launch_bounds__(TPB) k_inverse_ids(PState<R> st, DevCfg<R> c, uint32_t* __restrict__ inv,
+                                                     uint32_t* err)
+{
+    const int k = blockIdx.x * TPB + threadIdx.x;
+    if (k >= c.n) return;
+    const uint32_t id = (D == 3) ? r2u(ld2(st.Fc + k).y) : r2u(ld4(st.A + k).w);
+    if (id >= (uint32_t)c.n) {
+        set_err(err, APIC_ERRBIT_RANGE);
+        return;
+    }
+    inv[id] = (uint32_t)k;
+}
+
+// the particles uploaded at indices [id0, id1), read through inv and written in upload order
+// (a host download gathers in pieces so that each piece's copies can start early)
+template <int D, typename R>
+__global__ void __launch_bounds__(TPB) k_download_ids(PState<R> st, DevCfg<R> c, double dx, double o0, double o1,
+                                                      double o2, const uint32_t* __restrict__ inv, int64_t id0,
+                                                      int64_t id1, double* __restrict__ x, double* __restrict__ v,
+                                                      double* __restrict__ B, double* __restrict__ F, uint32_t* err)
+{
+    const int64_t id = id0 + (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (id >= id1) return;
+    const uint32_t k = inv[id];
+    if (k >= (uint32_t)c.n) {   // no particle carries this id: not valid state
+        set_err(err, APIC_ERRBIT_RANGE);
+        return;
+    }
+    const double org[3] = {o0, o1, o2};
+    Particle<D, R> p;
+    load_xF<D, R>(st, k, p);
+    load_vB<D, R>(st, k, p);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        if (x) x[id * D + a] = org[a] + ((double)p.cell[a] + (double)p.o[a]) * dx;
+        if (v) v[id * D + a] = (double)p.v[a];
+    }
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) {
+        if (B) B[id * D * D + i] = (double)p.B[i];
+        if (F) F[id * D * D + i] = (double)p.F[i];
+    }
 }
 
 template <int D, typename R>
@@ -2286,15 +2337,43 @@ template <typename R> struct Impl {
         return cudaGetLastError();
     }
     static cudaError_t upload(const HostCfg& h, const Buffers& b, int cur, int64_t n, const double* x,
-                              const double* v, const double* B, const double* F, cudaStream_t s)
+                              const double* v, const double* B, const double* F, cudaStream_t s, int64_t k0,
+                              int64_t k1)
+    {
+        if (k1 <= k0) return cudaSuccess;
+        DevCfg<R> c = HostToDev<R>::make(h, n);
+        PState<R> st = state_of<R>(b, cur);
+        const int g = blocks_for(k1 - k0);
+        if (h.dim == 3)
+            k_upload<3, R><<<g, TPB, 0, s>>>(st, c, h.dx, h.origin[0], h.origin[1], h.origin[2], x, v, B, F, b.err, b.fallbacks, k0, k1);
+        else
+            k_upload<2, R><<<g, TPB, 0, s>>>(st, c, h.dx, h.origin[0], h.origin[1], h.origin[2], x, v, B, F, b.err, b.fallbacks, k0, k1);
+        return cudaGetLastError();
+    }
+    static cudaError_t inverse_ids(const HostCfg& h, const Buffers& b, int cur, int64_t n, uint32_t* inv,
+                                   cudaStream_t s)
     {
         if (n == 0) return cudaSuccess;
         DevCfg<R> c = HostToDev<R>::make(h, n);
         PState<R> st = state_of<R>(b, cur);
+        cudaError_t e = cudaMemsetAsync(inv, 0xff, sizeof(uint32_t) * (size_t)n, s);
+        if (e != cudaSuccess) return e;
+        if (h.dim == 3) k_inverse_ids<3, R><<<blocks_for(n), TPB, 0, s>>>(st, c, inv, b.err);
+        else k_inverse_ids<2, R><<<blocks_for(n), TPB, 0, s>>>(st, c, inv, b.err);
+        return cudaGetLastError();
+    }
+    static cudaError_t download_ids(const HostCfg& h, const Buffers& b, int cur, int64_t n, const uint32_t* inv,
+                                    int64_t id0, int64_t id1, double* x, double* v, double* B, double* F,
+                                    cudaStream_t s)
+    {
+        if (id1 <= id0) return cudaSuccess;
+        DevCfg<R> c = HostToDev<R>::make(h, n);
+        PState<R> st = state_of<R>(b, cur);
+        const int g = blocks_for(id1 - id0);
         if (h.dim == 3)
-            k_upload<3, R><<<blocks_for(n), TPB, 0, s>>>(st, c, h.dx, h.origin[0], h.origin[1], h.origin[2], x, v, B, F, b.err, b.fallbacks);
+            k_download_ids<3, R><<<g, TPB, 0, s>>>(st, c, h.dx, h.origin[0], h.origin[1], h.origin[2], inv, id0, id1, x, v, B, F, b.err);
         else
-            k_upload<2, R><<<blocks_for(n), TPB, 0, s>>>(st, c, h.dx, h.origin[0], h.origin[1], h.origin[2], x, v, B, F, b.err, b.fallbacks);
+            k_download_ids<2, R><<<g, TPB, 0, s>>>(st, c, h.dx, h.origin[0], h.origin[1], h.origin[2], inv, id0, id1, x, v, B, F, b.err);
         return cudaGetLastError();
     }
     static cudaError_t download(const HostCfg& h, const Buffers& b, int cur, int64_t n, double* x, double* v,
@@ -2428,9 +2507,21 @@ template <typename R> struct Impl {
         return Impl<R>::set_params(c, b, cur, n, E, nu, mass, vol, keep, s);                                    \
     }                                                                                                           \
     cudaError_t upload_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const double* x,          \
-                             const double* v, const double* B, const double* F, cudaStream_t s)                 \
+                             const double* v, const double* B, const double* F, cudaStream_t s, int64_t k0,     \
+                             int64_t k1)                                                                        \
     {                                                                                                           \
-        return Impl<R>::upload(c, b, cur, n, x, v, B, F, s);                                                    \
+        return Impl<R>::upload(c, b, cur, n, x, v, B, F, s, k0, k1);                                            \
+    }                                                                                                           \
+    cudaError_t inverse_ids_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, uint32_t* inv,        \
+                                  cudaStream_t s)                                                               \
+    {                                                                                                           \
+        return Impl<R>::inverse_ids(c, b, cur, n, inv, s);                                                      \
+    }                                                                                                           \
+    cudaError_t download_ids_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, const uint32_t* inv, \
+                                   int64_t id0, int64_t id1, double* x, double* v, double* B, double* F,        \
+                                   cudaStream_t s)                                                              \
+    {                                                                                                           \
+        return Impl<R>::download_ids(c, b, cur, n, inv, id0, id1, x, v, B, F, s);                               \
     }                                                                                                           \
     cudaError_t download_##SFX(const HostCfg& c, const Buffers& b, int cur, int64_t n, double* x, double* v,   \
                                double* B, double* F, int32_t* cell, double* off, cudaStream_t s)                \
