@@ -463,7 +463,9 @@ __device__ __forceinline__ bool polar_newton3(const R* F, R* Rot)
 #pragma unroll
     for (int i = 0; i < 9; ++i) X[i] = F[i];
     const R tol = sizeof(R) == 4 ? R(2e-4) : R(1e-8);
-    bool scale = true;
+    // the scaling factor (det^(-1/3)) speeds up iterates far from orthogonal; near a rotation
+    // (det F within 5 % of 1) the plain iteration already converges quadratically
+    bool scale = fabs(det3<R>(F) - R(1)) > R(0.05);
 #pragma unroll 1
     for (int it = 0; it < 12; ++it) {
         R C[9];
