@@ -384,7 +384,6 @@ __device__ __forceinline__ void tile_flush_nodes(const R* cellsum, uint64_t occ,
     constexpr int TN = (D == 3) ? TE * TE * TE : TE * TE;
     constexpr int NS = (D == 3) ? K * K * K : K * K;
     constexpr int NV = D + 1;
-    constexpr int NVAL = NS * NV;
     // Cell n - (a, b, c) is linear index L - dj with L = n0 + 4 n1 + 16 n2 and dj = a + 4 b +
     // 16 c.  Per node the occupancy word is shifted so that the cell of stencil offset j sits
     // at the fixed bit DM - dj, and masked with the offsets whose cell lies in the block
@@ -993,7 +992,6 @@ __device__ __forceinline__ void p2g_split_tile(const PState<R>& st, const uint32
     constexpr int LPC = S::LPC;
     constexpr int NT = S::NT;
     constexpr int NSL = S::NSL;
-    constexpr int NVAL = K * K * K * 4;
     constexpr int SW = slot_words<3>();
     // lane group grp takes base cell grp of the block, so a warp's cells are neighbours in the
     // sorted order (its staging reads stay close together; spreading a warp's cells over the
@@ -1079,7 +1077,6 @@ __global__ void __launch_bounds__(SplitShape<ORDER>::NT, (split_ctas_per_sm<ORDE
                 uint32_t* __restrict__ tile_ctr, R* __restrict__ acc, uint32_t* __restrict__ flags, DevCfg<R> c,
                 uint32_t* err)
 {
-    constexpr int NT = SplitShape<ORDER>::NT;
     extern __shared__ __align__(32) unsigned char p2g_smem[];
     R* cellsum = reinterpret_cast<R*>(p2g_smem);   // [64][cell stride]
     R* pslots = reinterpret_cast<R*>(p2g_smem + (p2g_cellsum_bytes<3, ORDER, R>() + 31) / 32 * 32);
