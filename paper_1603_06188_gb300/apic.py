@@ -198,11 +198,31 @@ def apic_upload_mass_volume(sim, n, mass, vol, on_device=0):
     _check(load().apic_upload_mass_volume(sim, n, _ptr(mass), _ptr(vol), on_device), sim)
 
 
+# dimension of each simulation handle made through Sim, so that the host-array wrappers can
+# check an output array holds what the library will write into it
+_DIMS: dict = {}
+
+
+def _check_host_outputs(sim, arrays):
+    """Raise APIC_ERR_ARG if a host output array is smaller than the library's particle count
+    times its per-particle entries (the library writes that many)."""
+    d = _DIMS.get(sim if isinstance(sim, int) else getattr(sim, "value", sim))
+    if d is None:
+        return
+    n = int(apic_stats(sim)[0])
+    for a, per in arrays:
+        if isinstance(a, np.ndarray) and a.size < n * per(d):
+            raise ApicError(APIC_ERR_ARG, f"host array of {a.size} entries for {n} particles")
+
+
 def apic_download(sim, x=None, v=None, B=None, F=None, on_device=0):
+    if not on_device:
+        _check_host_outputs(sim, [(x, lambda d: d), (v, lambda d: d), (B, lambda d: d * d), (F, lambda d: d * d)])
     _check(load().apic_download(sim, _ptr(x), _ptr(v), _ptr(B), _ptr(F), on_device), sim)
 
 
 def apic_download_positions(sim, cell, offset):
+    _check_host_outputs(sim, [(cell, lambda d: d), (offset, lambda d: d)])
     _check(load().apic_download_positions(sim, _ptr(cell), _ptr(offset)), sim)
 
 
@@ -390,6 +410,7 @@ class Sim:
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.stream = stream or torch.cuda.current_stream(self.device)
         self.handle = apic_create(cfg, max_particles, self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
+        _DIMS[self.handle.value] = self.dim
         self.n = 0
 
     @property
@@ -433,13 +454,19 @@ class Sim:
             self.n = int(apic_stats(self.handle)[0])
             raise
 
+    def count(self) -> int:
+        """The library's particle count (also after an upload through the plain entry point)."""
+        self.n = int(apic_stats(self.handle)[0])
+        return self.n
+
     def download(self):
-        d, n = self.dim, self.n
+        d, n = self.dim, self.count()
         x = np.zeros((n, d)); v = np.zeros((n, d)); B = np.zeros((n, d, d)); F = np.zeros((n, d, d))
         apic_download(self.handle, x, v, B, F, on_device=0)
         return x, v, B, F
 
     def download_positions(self):
+        self.count()
         cell = np.zeros((self.n, self.dim), dtype=np.int32)
         off = np.zeros((self.n, self.dim))
         apic_download_positions(self.handle, cell, off)
@@ -475,6 +502,7 @@ class Sim:
         return m, mv
 
     def keys(self):
+        self.count()
         k = np.zeros(self.n, dtype=np.uint32)
         p = np.zeros(self.n, dtype=np.uint32)
         apic_keys_download(self.handle, k, p)
@@ -503,6 +531,7 @@ class Sim:
 
     def close(self):
         if getattr(self, "handle", None):
+            _DIMS.pop(self.handle.value, None)
             apic_destroy(self.handle)
             self.handle = None
 
