@@ -1,9 +1,12 @@
-// apic_internal.h -- declarations shared by the library's translation units (host side).
+// apic_internal.h -- declarations shared by the library's translation units (host side),
+// and the launch helper of the step's kernel chain.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
+
+#include <utility>
 
 #define APIC_BLOCK_EDGE 4
 #define APIC_ERRBIT_RANGE 1u     // a particle's stencil left the grid (clamped)
@@ -198,5 +201,34 @@ APIC_DECLARE_PRECISION(f32)
 APIC_DECLARE_PRECISION(f64)
 APIC_DECLARE_BATCH(f32)
 APIC_DECLARE_BATCH(f64)
+
+// Programmatic dependent launch for the kernels of a step, which run back to back on one
+// stream (sort passes, tile list, P2G, grid update, G2P): such a kernel is launched while the
+// one before it drains, so its launch and the ramp of its CTAs overlap the previous kernel's
+// tail.  Every kernel launched this way calls pdl_wait() before its first access to global
+// memory: it returns once the previous kernel has completed and its writes are visible (so
+// each kernel also completes after all earlier ones, and stream order holds for every
+// buffer).  pdl_trigger() lets the next kernel launch once every CTA of this one is running.
+// Without the launch attribute both are no-ops.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+#endif
 
 }  // namespace apic

@@ -155,6 +155,8 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t& excl)
 
 __global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t* __restrict__ in, int64_t n, uint32_t* __restrict__ part)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t base = (int64_t)blockIdx.x * SCH + threadIdx.x * 16;
     uint32_t s = 0;
 #pragma unroll
@@ -167,6 +169,8 @@ __global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t* __restrict_
 
 __global__ void __launch_bounds__(256) k_scan_top(uint32_t* __restrict__ part, int64_t np, uint32_t* __restrict__ total)
 {
+    pdl_wait();
+    pdl_trigger();
     uint32_t carry = 0;
     for (int64_t b = 0; b < np; b += 256) {
         const int64_t i = b + threadIdx.x;
@@ -182,6 +186,8 @@ __global__ void __launch_bounds__(256) k_scan_top(uint32_t* __restrict__ part, i
 __global__ void __launch_bounds__(256) k_scan_down(const uint32_t* in, uint32_t* out, int64_t n,
                                                    const uint32_t* __restrict__ part)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t base = (int64_t)blockIdx.x * SCH + threadIdx.x * 16;
     uint32_t v[16];
     uint32_t s = 0;
@@ -264,6 +270,8 @@ __device__ __forceinline__ void write_heads(const uint32_t* __restrict__ skeys, 
 __global__ void __launch_bounds__(256) k_tile_count(const uint32_t* __restrict__ skeys, int64_t n, int sh, int tile,
                                                     uint32_t* __restrict__ cnt)
 {
+    pdl_wait();
+    pdl_trigger();
     const uint32_t tot = count_heads(skeys, n, sh, tile, (int64_t)blockIdx.x * tile);
     if (threadIdx.x == 0) cnt[blockIdx.x] = tot;
 }
@@ -274,6 +282,8 @@ __global__ void __launch_bounds__(256) k_tile_write(const uint32_t* __restrict__
                                                     uint32_t* __restrict__ err, uint32_t* __restrict__ tile_ctr,
                                                     const uint32_t* __restrict__ cnt)
 {
+    pdl_wait();
+    pdl_trigger();
     // with cnt given, off[] and ntiles are computed here: chunk t's offset is the sum of the
     // counts of chunks 0..t-1 (a block reduction, used while the chunks are few)
     __shared__ uint32_t s_off;
@@ -513,6 +523,8 @@ __global__ void __launch_bounds__(RT) k_moved_count(const uint32_t* __restrict__
                                                     int64_t n, uint32_t* __restrict__ cnt, uint32_t* __restrict__ mhist,
                                                     int passes)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t h[4][256];
     for (int i = threadIdx.x; i < 4 * 256; i += RT) (&h[0][0])[i] = 0u;
     const int64_t base = (int64_t)blockIdx.x * RTILE;
@@ -552,6 +564,8 @@ __global__ void __launch_bounds__(RT) k_moved_compact(const uint32_t* __restrict
                                                       uint32_t* __restrict__ mv,
                                                       uint32_t* __restrict__ choff, uint32_t* __restrict__ err)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t wc[RI][RW];
     const uint32_t t = blockIdx.x;
     uint32_t excl;
@@ -613,6 +627,8 @@ __global__ void __launch_bounds__(RT) k_msort_pass(const uint32_t* __restrict__ 
                                                    uint32_t* __restrict__ ctl, int pass, const uint32_t* __restrict__ hist,
                                                    unsigned long long* lbs, uint32_t epoch, uint32_t* err)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t wc[RW][256];
     __shared__ uint32_t goff[256];
     __shared__ uint32_t dst0[256];
@@ -714,6 +730,8 @@ __global__ void __launch_bounds__(RT) k_merge(const uint32_t* __restrict__ knext
                                               const uint32_t* __restrict__ ctl, int nchunks,
                                               uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, uint32_t* err)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t wc[RI][RW];
     __shared__ uint32_t s_lo, s_nx, s_nm;
     __shared__ uint32_t sk[MERGE_MCAP], sv[MERGE_MCAP];
@@ -1177,10 +1195,10 @@ cudaError_t exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_
         return cudaSuccess;
     }
     const int64_t np = (n + SCH - 1) / SCH;
-    k_scan_reduce<<<(unsigned)np, 256, 0, s>>>(in, n, part);
-    k_scan_top<<<1, 256, 0, s>>>(part, np, total);
-    k_scan_down<<<(unsigned)np, 256, 0, s>>>(in, out, n, part);
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(k_scan_reduce, dim3((unsigned)np), dim3(256), 0, s, in, n, part);
+    if (e == cudaSuccess) e = launch_pdl(k_scan_top, dim3(1), dim3(256), 0, s, part, np, total);
+    if (e == cudaSuccess) e = launch_pdl(k_scan_down, dim3((unsigned)np), dim3(256), 0, s, in, out, n, part);
+    return e;
 }
 
 cudaError_t radix_sort(const Buffers& b, int64_t n, int key_bits, cudaStream_t s, uint32_t** keys_out,
@@ -1230,21 +1248,24 @@ cudaError_t resort(const Buffers& b, int64_t n, int key_bits, const uint32_t* pk
     e = cudaMemsetAsync(b.mctl, 0, kMsortCtlBytes, s);   // counters, m, digit counts
     if (e != cudaSuccess) return e;
     k_moved_count<<<nchunks, RT, 0, s>>>(b.knext, pk, n, b.mcnt, b.mhist, passes);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     const uint32_t* off = nullptr;
     if (nchunks > kReduceChunks) {   // many chunks: offsets by the device scan instead
         e = exclusive_scan(b.mcnt, b.choff, nchunks, b.scan_part, nullptr, s);
         if (e != cudaSuccess) return e;
         off = b.choff;
     }
-    k_moved_compact<<<nchunks, RT, 0, s>>>(b.knext, pk, n, b.mcnt, off, nchunks, b.mctl, b.mk[0], b.mv[0],
-                                           b.choff, b.err);
+    e = launch_pdl(k_moved_compact, dim3(nchunks), dim3(RT), 0, s, b.knext, pk, n, b.mcnt, off, nchunks, b.mctl,
+                   b.mk[0], b.mv[0], b.choff, b.err);
     const int grid = nchunks < sms * 8 ? nchunks : sms * 8;
-    for (int p = 0; p < passes; ++p)
-        k_msort_pass<<<grid, RT, 0, s>>>(b.mk[p & 1], b.mv[p & 1], b.mk[(p + 1) & 1], b.mv[(p + 1) & 1], b.mctl, p,
-                                         b.mhist + 256 * p, b.lbs, (*epoch)++, b.err);
-    k_merge<<<nchunks, RT, 0, s>>>(b.knext, pk, n, b.choff, b.mk[passes & 1], b.mv[passes & 1], b.mctl, nchunks,
-                                    kout, vout, b.err);
-    return cudaGetLastError();
+    for (int p = 0; p < passes && e == cudaSuccess; ++p)
+        e = launch_pdl(k_msort_pass, dim3(grid), dim3(RT), 0, s, b.mk[p & 1], b.mv[p & 1], b.mk[(p + 1) & 1],
+                       b.mv[(p + 1) & 1], b.mctl, p, b.mhist + 256 * p, b.lbs, (*epoch)++, b.err);
+    if (e == cudaSuccess)
+        e = launch_pdl(k_merge, dim3(nchunks), dim3(RT), 0, s, b.knext, pk, n, b.choff, b.mk[passes & 1],
+                       b.mv[passes & 1], b.mctl, nchunks, kout, vout, b.err);
+    return e;
 }
 
 cudaError_t batch_resort(const SortDesc* sd, const uint32_t* rt_sim, uint32_t total_rtiles, int nsims, int passes,
@@ -1281,17 +1302,15 @@ cudaError_t build_tiles(const Buffers& b, const uint32_t* skeys, int64_t n, int 
 {
     const int64_t nchunks = (n + tile - 1) / tile;
     const int sh = 2 * dim;
-    k_tile_count<<<(unsigned)nchunks, 256, 0, s>>>(skeys, n, sh, tile, b.chunk_cnt);
-    if (nchunks <= kReduceChunks) {
-        k_tile_write<<<(unsigned)nchunks, 256, 0, s>>>(skeys, n, sh, tile, nullptr, b.ntiles, max_tiles, b.tiles,
-                                                       (int)nchunks, b.err, b.tile_ctr, b.chunk_cnt);
-        return cudaGetLastError();
-    }
-    cudaError_t e = exclusive_scan(b.chunk_cnt, b.chunk_cnt, nchunks, b.scan_part, b.ntiles, s);
+    cudaError_t e = launch_pdl(k_tile_count, dim3((unsigned)nchunks), dim3(256), 0, s, skeys, n, sh, tile, b.chunk_cnt);
     if (e != cudaSuccess) return e;
-    k_tile_write<<<(unsigned)nchunks, 256, 0, s>>>(skeys, n, sh, tile, b.chunk_cnt, b.ntiles, max_tiles, b.tiles,
-                                                   (int)nchunks, b.err, b.tile_ctr, nullptr);
-    return cudaGetLastError();
+    if (nchunks <= kReduceChunks)
+        return launch_pdl(k_tile_write, dim3((unsigned)nchunks), dim3(256), 0, s, skeys, n, sh, tile, nullptr, b.ntiles,
+                          max_tiles, b.tiles, (int)nchunks, b.err, b.tile_ctr, b.chunk_cnt);
+    e = exclusive_scan(b.chunk_cnt, b.chunk_cnt, nchunks, b.scan_part, b.ntiles, s);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_tile_write, dim3((unsigned)nchunks), dim3(256), 0, s, skeys, n, sh, tile, b.chunk_cnt, b.ntiles,
+                      max_tiles, b.tiles, (int)nchunks, b.err, b.tile_ctr, nullptr);
 }
 
 }  // namespace apic

@@ -769,6 +769,8 @@ __global__ void __launch_bounds__(128, (cells_ctas_per_sm<D, ORDER>())) k_p2g_ce
                                                       uint32_t* __restrict__ flags, DevCfg<R> c, uint32_t* err,
                                                       uint32_t* fallbacks)
 {
+    pdl_wait();
+    pdl_trigger();
     constexpr int NC = (D == 3) ? 64 : 16;
     extern __shared__ __align__(32) unsigned char p2g_smem[];
     R* cellsum = reinterpret_cast<R*>(p2g_smem);   // [NC][cell stride]
@@ -1077,6 +1079,8 @@ __global__ void __launch_bounds__(SplitShape<ORDER>::NT, (split_ctas_per_sm<ORDE
                 uint32_t* __restrict__ tile_ctr, R* __restrict__ acc, uint32_t* __restrict__ flags, DevCfg<R> c,
                 uint32_t* err)
 {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(32) unsigned char p2g_smem[];
     R* cellsum = reinterpret_cast<R*>(p2g_smem);   // [64][cell stride]
     R* pslots = reinterpret_cast<R*>(p2g_smem + (p2g_cellsum_bytes<3, ORDER, R>() + 31) / 32 * 32);
@@ -1162,6 +1166,8 @@ template <int D, typename R>
 __global__ void __launch_bounds__(TPB) k_grid_update(R* __restrict__ acc, R* __restrict__ vel,
                                                      uint32_t* __restrict__ flags, DevCfg<R> c, R* acc2, R* vdel)
 {
+    pdl_wait();
+    pdl_trigger();
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * TPB + threadIdx.x) >> 5;
     const int nw = (gridDim.x * TPB) >> 5;
@@ -1571,6 +1577,8 @@ __global__ void __launch_bounds__(G2P_THREADS, 4) k_g2p(PState<R> in, PState<R> 
                                              const R* __restrict__ vel, uint32_t* __restrict__ knext, DevCfg<R> c,
                                              uint32_t* err, uint32_t* fallbacks, const R* __restrict__ vdel)
 {
+    pdl_wait();
+    pdl_trigger();
     constexpr int BN = (D == 3) ? 64 : 16;
     constexpr int NB = 1 << D;
     __shared__ __align__(128) R sv[2][NB][BN][4];
@@ -2129,20 +2137,23 @@ template <typename R> struct Impl {
         if (h.integrator != 0) c0.model = 0;
         PState<R> st = state_of<R>(b, cur);
         auto launch = [&](const DevCfg<R>& c, R* acc) {
+        cudaError_t e = cudaSuccess;
         if (h.dim == 3 && h.p2g_kernel == 1) {
             if (h.order == 2)
-                k_p2g_split<2, R><<<L.p2g_grid, SplitShape<2>::NT, p2g_split_smem<2, R>(), s>>>(
-                    st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc, b.flags, c, b.err);
+                e = launch_pdl(k_p2g_split<2, R>, dim3(L.p2g_grid), dim3(SplitShape<2>::NT), p2g_split_smem<2, R>(), s,
+                               st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc, b.flags, c, b.err);
             else
-                k_p2g_split<3, R><<<L.p2g_grid, SplitShape<3>::NT, p2g_split_smem<3, R>(), s>>>(
-                    st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc, b.flags, c, b.err);
+                e = launch_pdl(k_p2g_split<3, R>, dim3(L.p2g_grid), dim3(SplitShape<3>::NT), p2g_split_smem<3, R>(), s,
+                               st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc, b.flags, c, b.err);
         } else if (h.p2g_group == 2)
-            APIC_DISPATCH(h, (k_p2g_cells<D, O, R, 2><<<L.p2g_grid, 128, p2g_cells_launch_smem<D, O, R>(), s>>>(
-                                 st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc, b.flags, c, b.err, b.fallbacks)));
+            APIC_DISPATCH(h, (e = launch_pdl(k_p2g_cells<D, O, R, 2>, dim3(L.p2g_grid), dim3(128),
+                                             p2g_cells_launch_smem<D, O, R>(), s, st, perm, sk, b.tiles, b.ntiles,
+                                             b.tile_ctr, acc, b.flags, c, b.err, b.fallbacks)));
         else
-            APIC_DISPATCH(h, (k_p2g_cells<D, O, R, 4><<<L.p2g_grid, 128, p2g_cells_launch_smem<D, O, R>(), s>>>(
-                                 st, perm, sk, b.tiles, b.ntiles, b.tile_ctr, acc, b.flags, c, b.err, b.fallbacks)));
-        return cudaGetLastError();
+            APIC_DISPATCH(h, (e = launch_pdl(k_p2g_cells<D, O, R, 4>, dim3(L.p2g_grid), dim3(128),
+                                             p2g_cells_launch_smem<D, O, R>(), s, st, perm, sk, b.tiles, b.ntiles,
+                                             b.tile_ctr, acc, b.flags, c, b.err, b.fallbacks)));
+        return e;
         };
         cudaError_t e = launch(c0, (R*)b.acc);
         if (e == cudaSuccess && h.transfer == 2) {
@@ -2160,9 +2171,11 @@ template <typename R> struct Impl {
     {
         DevCfg<R> c = HostToDev<R>::make(h, b, 0);
         const int grid = L.sms * 8;
-        if (h.dim == 3) k_grid_update<3, R><<<grid, TPB, 0, s>>>((R*)b.acc, (R*)b.vel, b.flags, c, (R*)b.acc2, (R*)b.vdel);
-        else k_grid_update<2, R><<<grid, TPB, 0, s>>>((R*)b.acc, (R*)b.vel, b.flags, c, (R*)b.acc2, (R*)b.vdel);
-        return cudaGetLastError();
+        if (h.dim == 3)
+            return launch_pdl(k_grid_update<3, R>, dim3(grid), dim3(TPB), 0, s, (R*)b.acc, (R*)b.vel, b.flags, c,
+                              (R*)b.acc2, (R*)b.vdel);
+        return launch_pdl(k_grid_update<2, R>, dim3(grid), dim3(TPB), 0, s, (R*)b.acc, (R*)b.vel, b.flags, c,
+                          (R*)b.acc2, (R*)b.vdel);
     }
     static cudaError_t g2p(const HostCfg& h, const Buffers& b, int cur, const uint32_t* sk, const uint32_t* perm,
                            int64_t n, const Launch& L, cudaStream_t s)
@@ -2170,13 +2183,16 @@ template <typename R> struct Impl {
         if (n == 0) return cudaSuccess;
         DevCfg<R> c = HostToDev<R>::make(h, b, n);
         PState<R> in = state_of<R>(b, cur), out = state_of<R>(b, cur ^ 1);
+        cudaError_t e = cudaSuccess;
         if (h.mat || h.adaptive || h.transfer == 2)
-            APIC_DISPATCH(h, (k_g2p<D, O, R, true><<<L.g2p_grid, G2P_THREADS, 0, s>>>(in, out, perm, sk, b.tiles, b.ntiles,
-                                     b.tile_ctr, (const R*)b.vel, b.knext, c, b.err, b.fallbacks, (const R*)b.vdel)));
+            APIC_DISPATCH(h, (e = launch_pdl(k_g2p<D, O, R, true>, dim3(L.g2p_grid), dim3(G2P_THREADS), 0, s, in, out,
+                                             perm, sk, b.tiles, b.ntiles, b.tile_ctr, (const R*)b.vel, b.knext, c,
+                                             b.err, b.fallbacks, (const R*)b.vdel)));
         else
-            APIC_DISPATCH(h, (k_g2p<D, O, R, false><<<L.g2p_grid, G2P_THREADS, 0, s>>>(in, out, perm, sk, b.tiles, b.ntiles,
-                                     b.tile_ctr, (const R*)b.vel, b.knext, c, b.err, b.fallbacks, nullptr)));
-        return cudaGetLastError();
+            APIC_DISPATCH(h, (e = launch_pdl(k_g2p<D, O, R, false>, dim3(L.g2p_grid), dim3(G2P_THREADS), 0, s, in, out,
+                                             perm, sk, b.tiles, b.ntiles, b.tile_ctr, (const R*)b.vel, b.knext, c,
+                                             b.err, b.fallbacks, nullptr)));
+        return e;
     }
     // the grid phase of the lambda = 1 member: grid velocity, the force at F^{n+1}, the update
     static cudaError_t grid_update_lambda1(const HostCfg& h, const Buffers& b, int cur, const uint32_t* sk,
