@@ -514,6 +514,15 @@ __device__ __forceinline__ uint32_t lookback64(unsigned long long* words, uint32
     return excl;
 }
 
+// zeroes the incremental sort's control words and digit counts (a kernel rather than a memset,
+// so that the step's chain of dependent launches is not broken)
+__global__ void __launch_bounds__(256) k_msort_reset(uint32_t* __restrict__ mctl, int words)
+{
+    pdl_wait();
+    pdl_trigger();
+    for (int i = blockIdx.x * 256 + threadIdx.x; i < words; i += gridDim.x * 256) mctl[i] = 0u;
+}
+
 // moved keys of chunk t (RTILE consecutive indices, thread-major rounds): count per chunk and
 // the digit counts of every pass.  All keys of the thread are loaded before any is counted
 // (the shared-memory atomics would otherwise hold back the later loads), and the digit counts
@@ -1175,7 +1184,7 @@ int radix_sort_kernels(int key_bits) { return 2 + (key_bits + 7) / 8; }
 int resort_kernels(int64_t n, int key_bits)
 {
     if (n <= 0) return 0;
-    return 3 + (key_bits + 7) / 8 + (radix_tiles(n) > kReduceChunks ? 3 : 0);
+    return 4 + (key_bits + 7) / 8 + (radix_tiles(n) > kReduceChunks ? 3 : 0);
 }
 int build_tiles_kernels(int64_t n, int tile) { return (n + tile - 1) / tile <= kReduceChunks ? 2 : 5; }
 int batch_sort_and_tiles_kernels(int passes) { return (5 + passes) + 5; }
@@ -1245,10 +1254,11 @@ cudaError_t resort(const Buffers& b, int64_t n, int key_bits, const uint32_t* pk
         if (e != cudaSuccess) return e;
         *epoch = 1u;
     }
-    e = cudaMemsetAsync(b.mctl, 0, kMsortCtlBytes, s);   // counters, m, digit counts
-    if (e != cudaSuccess) return e;
-    k_moved_count<<<nchunks, RT, 0, s>>>(b.knext, pk, n, b.mcnt, b.mhist, passes);
-    e = cudaGetLastError();
+    // counters, m, digit counts
+    static_assert(kMsortCtlBytes % 4 == 0, "the control block is zeroed as 32-bit words");
+    e = launch_pdl(k_msort_reset, dim3(16), dim3(256), 0, s, b.mctl, (int)(kMsortCtlBytes / 4));
+    if (e == cudaSuccess)
+        e = launch_pdl(k_moved_count, dim3(nchunks), dim3(RT), 0, s, b.knext, pk, n, b.mcnt, b.mhist, passes);
     if (e != cudaSuccess) return e;
     const uint32_t* off = nullptr;
     if (nchunks > kReduceChunks) {   // many chunks: offsets by the device scan instead
