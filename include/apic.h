@@ -229,6 +229,21 @@ apic_status apic_step_adaptive(apic_sim* sim, int nsteps, double nu, double dt_m
  * sum x_i x m_i v~_i.  In 2-D, l[0] is the z component.  Synchronising, host pointers. */
 apic_status apic_momentum(apic_sim* sim, int where, double p[3], double l[3]);
 
+/* The particle momentum of apic_momentum (APIC_WHERE_PARTICLES) of the state as it stands
+ * after the work queued so far, read without synchronising: the reduction runs on a stream
+ * of its own (with its own scratch) once that work is done, overlapping whatever is queued
+ * next, and writes out[0..2] = p, out[3..5] = l (in 2-D out[3] is the z component and
+ * out[2] = out[4] = out[5] = 0).  `out` (6 doubles, host or device memory, caller-owned)
+ * must stay valid until apic_momentum_wait returns; with pinned host or device memory the
+ * call returns at once, with pageable host memory only when the read is done.  A later
+ * call that overwrites the state copy that was read (apic_g2p two steps on, an upload, new
+ * materials or masses) waits for the read on the device first, so the value is that of the
+ * state at the time of the call.  Not for members of a batch (APIC_ERR_ARG). */
+apic_status apic_momentum_async(apic_sim* sim, double* out);
+
+/* Waits until every apic_momentum_async read of this simulation has written its output. */
+apic_status apic_momentum_wait(apic_sim* sim);
+
 /* Sec. 4.3 time-step bound: *max_speed = max_p (|v_p| + (6 sqrt(d) / dx) |B_p|_F), the
  * (kappa / k) dx factor being the same for quadratic and cubic B-splines; a step with
  * dt <= nu dx / *max_speed moves no particle more than nu dx at the grid velocity.

@@ -101,6 +101,8 @@ SIGNATURES = {
     "apic_step": (C.c_int, [C.c_void_p, C.c_int]),
     "apic_step_adaptive": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_double)]),
     "apic_momentum": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "apic_momentum_async": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "apic_momentum_wait": (C.c_int, [C.c_void_p]),
     "apic_cfl": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "apic_grid_download": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "apic_keys_download": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -247,6 +249,26 @@ def apic_momentum(sim, where: int):
     l = np.zeros(3)
     _check(load().apic_momentum(sim, where, _ptr(p), _ptr(l)), sim)
     return p, l
+
+
+def apic_momentum_async(sim, out):
+    """Queue the particle momentum of the current state into out[0:6] = (p, l) without
+    synchronising.  `out` is a C-contiguous float64 numpy array or torch tensor of at least 6
+    entries (pinned host or CUDA memory for the call to return at once); the caller keeps it
+    alive until apic_momentum_wait."""
+    if isinstance(out, np.ndarray):
+        ok = out.dtype == np.float64 and out.flags.c_contiguous and out.size >= 6
+    else:
+        import torch
+
+        ok = out.dtype == torch.float64 and out.is_contiguous() and out.numel() >= 6
+    if not ok:
+        raise ApicError(APIC_ERR_ARG, "momentum output must be 6 contiguous float64 values")
+    _check(load().apic_momentum_async(sim, _ptr(out)), sim)
+
+
+def apic_momentum_wait(sim):
+    _check(load().apic_momentum_wait(sim), sim)
 
 
 def apic_step_adaptive(sim, n: int, nu: float, dt_max: float) -> float:
@@ -490,6 +512,14 @@ class Sim:
 
     def momentum(self, where: str = "particles"):
         return apic_momentum(self.handle, WHERE_PARTICLES if where == "particles" else WHERE_GRID)
+
+    def momentum_async(self, out):
+        """Queue the particle momentum (p, l) of the current state into out[0:6]; see
+        apic_momentum_async.  Read `out` after momentum_wait()."""
+        apic_momentum_async(self.handle, out)
+
+    def momentum_wait(self):
+        apic_momentum_wait(self.handle)
 
     def cfl_speed(self) -> float:
         """max_p(|v_p| + 6 sqrt(d)/dx |B_p|_F); dt <= nu dx / this (Sec. 4.3)."""

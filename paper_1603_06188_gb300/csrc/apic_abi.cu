@@ -48,6 +48,13 @@ struct apic_sim {
     cudaStream_t cstream;
     cudaEvent_t cev[kCopyEvents];
     bool copy_ready;
+    // apic_momentum_async: reads on their own stream, after an event of the simulation's
+    // stream; mdone[c] marks the last read of state copy c, which a later write of that copy
+    // waits for (mpending[c] while such a wait is still owed)
+    cudaStream_t mstream;
+    cudaEvent_t mready, mdone[2];
+    bool mom_ready;
+    bool mpending[2];
     // per-phase timing
     bool prof_on;
     std::vector<cudaEvent_t> ev_pool;
@@ -171,7 +178,7 @@ struct Layout {
     size_t st[2][APIC_STATE_LANES];
     size_t mk[2], mv[2], midx, choff, mcnt, mctl, lbs, step_words, acc2, vdel, vel1, solve[6];
     size_t knext, kA, kB, vA, vB, radix_counts, scan_part, tiles, chunk_cnt, ntiles, tile_ctr;
-    size_t acc, vel, flags, mom_part, mom_out, err, fallbacks, staging;
+    size_t acc, vel, flags, mom_part, mom_out, amom_part, amom_out, err, fallbacks, staging;
     size_t staging_doubles;
     int64_t max_tiles;
     size_t total;
@@ -228,6 +235,8 @@ Layout layout_of(const HostCfg& c)
     L.flags = cv.take((size_t)c.nblocks * 4);
     L.mom_part = cv.take((size_t)kMomParts * 6 * 8);
     L.mom_out = cv.take(6 * 8);
+    L.amom_part = cv.take((size_t)kMomParts * 6 * 8);
+    L.amom_out = cv.take(6 * 8);
     L.err = cv.take(4);
     L.fallbacks = cv.take(4);
     L.step_words = cv.take(32);   // dt word (8), speed maximum (4), elapsed time (8 at +16)
@@ -338,6 +347,37 @@ cudaError_t ensure_copy_stream(apic_sim* s)
     return cudaSuccess;
 }
 
+// the stream and events of apic_momentum_async, made on first use
+cudaError_t ensure_mom_stream(apic_sim* s)
+{
+    if (s->mom_ready) return cudaSuccess;
+    cudaError_t e = cudaStreamCreateWithFlags(&s->mstream, cudaStreamNonBlocking);
+    cudaEvent_t* ev[3] = {&s->mready, &s->mdone[0], &s->mdone[1]};
+    int made = 0;
+    for (; e == cudaSuccess && made < 3; ++made) e = cudaEventCreateWithFlags(ev[made], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        for (int i = 0; i < made; ++i) cudaEventDestroy(*ev[i]);
+        if (s->mstream) cudaStreamDestroy(s->mstream);
+        s->mstream = nullptr;
+        return e;
+    }
+    s->mom_ready = true;
+    return cudaSuccess;
+}
+
+// before work that overwrites state copy `copy` (-1: both): the simulation's stream waits
+// for the asynchronous momentum reads of it that are still owed
+cudaError_t mom_fence(apic_sim* s, int copy)
+{
+    for (int c = 0; c < 2; ++c) {
+        if ((copy >= 0 && copy != c) || !s->mpending[c]) continue;
+        const cudaError_t e = cudaStreamWaitEvent(s->stream, s->mdone[c], 0);
+        if (e != cudaSuccess) return e;
+        s->mpending[c] = false;
+    }
+    return cudaSuccess;
+}
+
 // pieces of a host transfer of n particles: about half a million particles each, at most 16
 int copy_pieces(int64_t n)
 {
@@ -427,6 +467,8 @@ apic_status apic_create(const apic_config* cfg, int64_t max_particles, void* wor
     s->b.flags = (uint32_t*)(base + L.flags);
     s->b.mom_part = (double*)(base + L.mom_part);
     s->b.mom_out = (double*)(base + L.mom_out);
+    s->b.amom_part = (double*)(base + L.amom_part);
+    s->b.amom_out = (double*)(base + L.amom_out);
     s->b.err = (uint32_t*)(base + L.err);
     s->b.fallbacks = (uint32_t*)(base + L.fallbacks);
     s->b.dt_word = base + L.step_words;
@@ -483,6 +525,13 @@ apic_status apic_destroy(apic_sim* s)
         for (cudaEvent_t ev : s->cev) cudaEventDestroy(ev);
         cudaStreamDestroy(s->cstream);
     }
+    if (s->mom_ready) {
+        cudaStreamSynchronize(s->mstream);
+        cudaEventDestroy(s->mready);
+        cudaEventDestroy(s->mdone[0]);
+        cudaEventDestroy(s->mdone[1]);
+        cudaStreamDestroy(s->mstream);
+    }
     delete s;
     return e == cudaSuccess ? APIC_OK : APIC_ERR_CUDA;
 }
@@ -496,6 +545,7 @@ apic_status apic_upload(apic_sim* s, int64_t n, const double* x, const double* v
     if (n > s->c.capacity) return fail(s, APIC_ERR_OOM, "n exceeds the particle capacity given to apic_create");
     if (n > 0 && !x) return fail(s, APIC_ERR_ARG, "positions are required");
     CK(cudaSetDevice(s->device), "cudaSetDevice");
+    CK(mom_fence(s, -1), "wait for momentum reads");
     const int d = s->c.dim;
     s->n = n;
     s->cur = 0;
@@ -555,6 +605,7 @@ apic_status apic_upload_materials(apic_sim* s, int64_t n, const double* E, const
     if (n != s->n) return fail(s, APIC_ERR_ARG, "n must equal the particle count of the last apic_upload");
     if (n > 0 && (!E || !nu)) return fail(s, APIC_ERR_ARG, "E and nu are required");
     CK(cudaSetDevice(s->device), "cudaSetDevice");
+    CK(mom_fence(s, -1), "wait for momentum reads");
     const int keep = s->c.mat;
     if (n == 0) {
         s->c.mat = 1;
@@ -587,6 +638,7 @@ apic_status apic_upload_mass_volume(apic_sim* s, int64_t n, const double* mass, 
     if (n != s->n) return fail(s, APIC_ERR_ARG, "n must equal the particle count of the last apic_upload");
     if (n > 0 && (!mass || !vol)) return fail(s, APIC_ERR_ARG, "mass and vol are required");
     CK(cudaSetDevice(s->device), "cudaSetDevice");
+    CK(mom_fence(s, -1), "wait for momentum reads");
     const int keep = s->c.mat;
     if (n == 0) {
         s->c.mat = 1;
@@ -762,6 +814,7 @@ apic_status apic_g2p(apic_sim* s)
     IN_BATCH_GUARD(s);
     if (s->phase != 2) return fail(s, APIC_ERR_ARG, "apic_g2p must follow apic_grid_update");
     CK(cudaSetDevice(s->device), "cudaSetDevice");
+    CK(mom_fence(s, s->cur ^ 1), "wait for momentum reads");   // G2P writes the other copy
     if (s->n > 0) {
         {
             PhaseScope ps(s, APIC_PHASE_G2P, 1);
@@ -857,6 +910,34 @@ apic_status apic_momentum(apic_sim* s, int where, double p[3], double l[3])
         l[1] = l[2] = 0.0;
     }
     return st;
+}
+
+apic_status apic_momentum_async(apic_sim* s, double* out)
+{
+    if (!s || !out) return APIC_ERR_ARG;
+    if (s->batch) return fail(s, APIC_ERR_ARG, "asynchronous momentum reads are for simulations outside a batch");
+    CK(cudaSetDevice(s->device), "cudaSetDevice");
+    CK(ensure_mom_stream(s), "momentum stream");
+    CK(cudaEventRecord(s->mready, s->stream), "record event");
+    CK(cudaStreamWaitEvent(s->mstream, s->mready, 0), "stream wait");
+    Buffers ab = s->b;   // the reduction's own scratch, so it may overlap the calls that follow
+    ab.mom_part = s->b.amom_part;
+    ab.mom_out = s->b.amom_out;
+    CK(DISPATCH(s, momentum, s->c, ab, s->cur, s->n, (int)APIC_WHERE_PARTICLES, 0, s->L, s->mstream), "momentum kernel");
+    s->launches += 2;
+    CK(cudaMemcpyAsync(out, s->b.amom_out, 6 * sizeof(double), cudaMemcpyDefault, s->mstream), "read momentum");
+    CK(cudaEventRecord(s->mdone[s->cur], s->mstream), "record event");
+    s->mpending[s->cur] = true;
+    return APIC_OK;
+}
+
+apic_status apic_momentum_wait(apic_sim* s)
+{
+    if (!s) return APIC_ERR_ARG;
+    if (!s->mom_ready) return APIC_OK;
+    CK(cudaSetDevice(s->device), "cudaSetDevice");
+    CK(cudaStreamSynchronize(s->mstream), "wait for momentum reads");
+    return APIC_OK;
 }
 
 apic_status apic_cfl(apic_sim* s, double* max_speed)
@@ -1378,6 +1459,7 @@ apic_status apic_batch_add(apic_batch* b, apic_sim* s)
         s->keys_valid = true;
         s->launches += 1;
     }
+    BCK(mom_fence(s, -1), "wait for momentum reads");   // batch kernels will write the state
     // look-back words of the batch's sort epochs start clear
     BCK(cudaMemsetAsync(s->b.lbs, 0, sizeof(unsigned long long) * 256 * ((size_t)radix_tiles(s->c.capacity) + 1),
                         s->stream), "clear look-back words");

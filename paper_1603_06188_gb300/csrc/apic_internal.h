@@ -51,6 +51,8 @@ struct Buffers {
     uint32_t* flags;             // active node blocks
     double* mom_part;            // per-CTA momentum partials
     double* mom_out;             // 6 doubles
+    double* amom_part;           // the same two for apic_momentum_async, which runs on a
+    double* amom_out;            // stream of its own
     uint32_t* err;               // latched error bits
     uint32_t* fallbacks;         // FP64 polar fallbacks
     void* dt_word;               // the current time step (one real) of adaptive stepping
