@@ -176,7 +176,7 @@ struct Carve {
 // offsets of every buffer inside the workspace (relative to its base)
 struct Layout {
     size_t st[2][APIC_STATE_LANES];
-    size_t mk[2], mv[2], midx, choff, mcnt, mctl, lbs, step_words, acc2, vdel, vel1, solve[6];
+    size_t mk[2], mv[2], midx, choff, mcnt, mbits, mctl, lbs, step_words, acc2, vdel, vel1, solve[6];
     size_t knext, kA, kB, vA, vB, radix_counts, scan_part, tiles, chunk_cnt, ntiles, tile_ctr;
     size_t acc, vel, flags, mom_part, mom_out, amom_part, amom_out, err, fallbacks, staging;
     size_t staging_doubles;
@@ -211,6 +211,7 @@ Layout layout_of(const HostCfg& c)
     L.midx = cv.take((size_t)n * 4);
     L.choff = cv.take(((size_t)radix_tiles(n) + 1) * 4);
     L.mcnt = cv.take(((size_t)radix_tiles(n) + 1) * 4);
+    L.mbits = cv.take(moved_bitmap_words(n) * 4);
     L.mctl = cv.take(kMsortCtlBytes);
     L.lbs = cv.take((size_t)256 * ((size_t)radix_tiles(n) + 1) * 8);
     const int64_t nchunks = (n + c.tile - 1) / c.tile;
@@ -445,6 +446,7 @@ apic_status apic_create(const apic_config* cfg, int64_t max_particles, void* wor
     s->b.midx = (uint32_t*)(base + L.midx);
     s->b.choff = (uint32_t*)(base + L.choff);
     s->b.mcnt = (uint32_t*)(base + L.mcnt);
+    s->b.mbits = (uint32_t*)(base + L.mbits);
     s->b.mctl = (uint32_t*)(base + L.mctl);
     s->b.mhist = s->b.mctl + 16;
     s->b.lbs = (unsigned long long*)(base + L.lbs);

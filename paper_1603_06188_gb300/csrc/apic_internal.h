@@ -34,6 +34,7 @@ struct Buffers {
     uint32_t* midx;
     uint32_t* choff;
     uint32_t* mcnt;              // moved count per chunk
+    uint32_t* mbits;             // moved flags of the incremental sort, 1 bit per key
     uint32_t* mctl;              // [1] moved count, [2..5] pass tile counters
     uint32_t* mhist;             // [kMhistCopies][4][256] digit counts of the moved keys (follows mctl)
     unsigned long long* lbs;     // 256 * (radix tiles + 1)
@@ -108,6 +109,8 @@ struct SortDesc {
 
 // sort / tiles (apic_sort.cu)
 int radix_tiles(int64_t n);
+// words of the incremental sort's moved-key bitmap for n keys
+size_t moved_bitmap_words(int64_t n);
 // kernels launched by radix_sort, resort, build_tiles, and by batch_resort plus
 // batch_build_tiles together (for the launch counters)
 int radix_sort_kernels(int key_bits);

@@ -528,9 +528,12 @@ __global__ void __launch_bounds__(256) k_msort_reset(uint32_t* __restrict__ mctl
 // (the shared-memory atomics would otherwise hold back the later loads), and the digit counts
 // go to copy t % kMhistCopies of the histogram: the high digits of the moved keys are nearly
 // all alike, and one global counter per digit would take every chunk's add in turn.
+// The moved flags also go to a bitmap (word blockIdx.x * RTILE / 32 + r * RW + w holds the
+// flags of round r of warp w, bit = lane), so that the compaction and the merge read 1 bit
+// per key instead of both keys.
 __global__ void __launch_bounds__(RT) k_moved_count(const uint32_t* __restrict__ knext, const uint32_t* __restrict__ pk,
                                                     int64_t n, uint32_t* __restrict__ cnt, uint32_t* __restrict__ mhist,
-                                                    int passes)
+                                                    int passes, uint32_t* __restrict__ mbits)
 {
     pdl_wait();
     pdl_trigger();
@@ -545,6 +548,12 @@ __global__ void __launch_bounds__(RT) k_moved_count(const uint32_t* __restrict__
         kp[r] = k < n ? pk[k] : 0u;
     }
     __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int r = 0; r < RI; ++r) {
+        const unsigned bal = __ballot_sync(FULL, kn[r] != kp[r]);
+        if (lane == 0) mbits[(size_t)blockIdx.x * (RTILE / 32) + r * RW + w] = bal;
+    }
     uint32_t c = 0;
 #pragma unroll
     for (int r = 0; r < RI; ++r) {
@@ -571,7 +580,8 @@ __global__ void __launch_bounds__(RT) k_moved_compact(const uint32_t* __restrict
                                                       const uint32_t* __restrict__ off, int nchunks,
                                                       uint32_t* __restrict__ ctl, uint32_t* __restrict__ mk,
                                                       uint32_t* __restrict__ mv,
-                                                      uint32_t* __restrict__ choff, uint32_t* __restrict__ err)
+                                                      uint32_t* __restrict__ choff, uint32_t* __restrict__ err,
+                                                      const uint32_t* __restrict__ mbits)
 {
     pdl_wait();
     pdl_trigger();
@@ -593,9 +603,9 @@ __global__ void __launch_bounds__(RT) k_moved_compact(const uint32_t* __restrict
 #pragma unroll
     for (int r = 0; r < RI; ++r) {
         const int64_t k = base + r * RT + threadIdx.x;
-        const bool moved = k < n && knext[k] != pk[k];
+        bal[r] = mbits[(size_t)t * (RTILE / 32) + r * RW + w];
+        const bool moved = (bal[r] >> lane) & 1u;
         key[r] = moved ? knext[k] : 0u;
-        bal[r] = __ballot_sync(FULL, moved);
         if (lane == 0) wc[r][w] = (uint32_t)__popc(bal[r]);
     }
     __syncthreads();
@@ -737,7 +747,8 @@ __global__ void __launch_bounds__(RT) k_merge(const uint32_t* __restrict__ knext
                                               int64_t n, const uint32_t* __restrict__ choff,
                                               const uint32_t* __restrict__ msk, const uint32_t* __restrict__ msv,
                                               const uint32_t* __restrict__ ctl, int nchunks,
-                                              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, uint32_t* err)
+                                              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, uint32_t* err,
+                                              const uint32_t* __restrict__ mbits)
 {
     pdl_wait();
     pdl_trigger();
@@ -756,9 +767,7 @@ __global__ void __launch_bounds__(RT) k_merge(const uint32_t* __restrict__ knext
     unsigned bal[RI];
 #pragma unroll
     for (int r = 0; r < RI; ++r) {
-        const int64_t k = base + r * RT + threadIdx.x;
-        const bool moved = k < n && knext[k] != pk[k];
-        bal[r] = __ballot_sync(FULL, moved);
+        bal[r] = mbits[(size_t)t * (RTILE / 32) + r * RW + w];
         if (lane == 0) wc[r][w] = (uint32_t)__popc(bal[r]);
     }
     __syncthreads();
@@ -1178,6 +1187,7 @@ __global__ void __launch_bounds__(256) kb_tile_write(const SortDesc* __restrict_
 }  // namespace
 
 int radix_tiles(int64_t n) { return (int)((n + RTILE - 1) / RTILE); }
+size_t moved_bitmap_words(int64_t n) { return (size_t)radix_tiles(n) * (RTILE / 32); }
 
 // kernels the routines below launch (memsets not counted), for the launch counters
 int radix_sort_kernels(int key_bits) { return 2 + (key_bits + 7) / 8; }
@@ -1258,7 +1268,7 @@ cudaError_t resort(const Buffers& b, int64_t n, int key_bits, const uint32_t* pk
     static_assert(kMsortCtlBytes % 4 == 0, "the control block is zeroed as 32-bit words");
     e = launch_pdl(k_msort_reset, dim3(16), dim3(256), 0, s, b.mctl, (int)(kMsortCtlBytes / 4));
     if (e == cudaSuccess)
-        e = launch_pdl(k_moved_count, dim3(nchunks), dim3(RT), 0, s, b.knext, pk, n, b.mcnt, b.mhist, passes);
+        e = launch_pdl(k_moved_count, dim3(nchunks), dim3(RT), 0, s, b.knext, pk, n, b.mcnt, b.mhist, passes, b.mbits);
     if (e != cudaSuccess) return e;
     const uint32_t* off = nullptr;
     if (nchunks > kReduceChunks) {   // many chunks: offsets by the device scan instead
@@ -1267,14 +1277,14 @@ cudaError_t resort(const Buffers& b, int64_t n, int key_bits, const uint32_t* pk
         off = b.choff;
     }
     e = launch_pdl(k_moved_compact, dim3(nchunks), dim3(RT), 0, s, b.knext, pk, n, b.mcnt, off, nchunks, b.mctl,
-                   b.mk[0], b.mv[0], b.choff, b.err);
+                   b.mk[0], b.mv[0], b.choff, b.err, b.mbits);
     const int grid = nchunks < sms * 8 ? nchunks : sms * 8;
     for (int p = 0; p < passes && e == cudaSuccess; ++p)
         e = launch_pdl(k_msort_pass, dim3(grid), dim3(RT), 0, s, b.mk[p & 1], b.mv[p & 1], b.mk[(p + 1) & 1],
                        b.mv[(p + 1) & 1], b.mctl, p, b.mhist + 256 * p, b.lbs, (*epoch)++, b.err);
     if (e == cudaSuccess)
         e = launch_pdl(k_merge, dim3(nchunks), dim3(RT), 0, s, b.knext, pk, n, b.choff, b.mk[passes & 1],
-                       b.mv[passes & 1], b.mctl, nchunks, kout, vout, b.err);
+                       b.mv[passes & 1], b.mctl, nchunks, kout, vout, b.err, b.mbits);
     return e;
 }
 
