@@ -1110,15 +1110,25 @@ __global__ void __launch_bounds__(SplitShape<ORDER>::NT, (split_ctas_per_sm<ORDE
 template <int D, typename R>
 __device__ __forceinline__ void grid_update_block(R* __restrict__ acc, R* __restrict__ vel,
                                                   uint32_t* __restrict__ flags, const DevCfg<R>& c, int b, int lane,
-                                                  R* __restrict__ acc2 = nullptr, R* __restrict__ vdel = nullptr)
+                                                  R* __restrict__ acc2 = nullptr, R* __restrict__ vdel = nullptr,
+                                                  bool known_active = false)
 {
     constexpr int BN = (D == 3) ? 64 : 16;
-    if (flags[b] == 0u) return;
+    if (!known_active && flags[b] == 0u) return;
     int bc[3] = {0, 0, 0};
     block_coords<D, R>((uint32_t)b, c, bc);
-    for (int i = lane; i < BN; i += 32) {
+    // the lane's nodes lane + 32 q, all loaded before any is written
+    constexpr int PER = (BN + 31) / 32;
+    V4<R> av[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q)
+        if (lane + 32 * q < BN) av[q] = *reinterpret_cast<const V4<R>*>(acc + 4 * ((size_t)b * BN + lane + 32 * q));
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int i = lane + 32 * q;
+        if (i >= BN) continue;
         const size_t node = (size_t)b * BN + i;
-        V4<R> a = *reinterpret_cast<const V4<R>*>(acc + 4 * node);
+        const V4<R> a = av[q];
         int g[3];
         g[0] = bc[0] * 4 + (i & 3);
         g[1] = bc[1] * 4 + ((i >> 2) & 3);
@@ -1172,7 +1182,17 @@ __global__ void __launch_bounds__(TPB) k_grid_update(R* __restrict__ acc, R* __r
     const int gw = (blockIdx.x * TPB + threadIdx.x) >> 5;
     const int nw = (gridDim.x * TPB) >> 5;
     if (c.smax && blockIdx.x == 0 && threadIdx.x == 0) *c.smax = 0u;   // G2P, next, max-reduces into it
-    for (int b = gw; b < c.nblocks; b += nw) grid_update_block<D, R>(acc, vel, flags, c, b, lane, acc2, vdel);
+    // the warp's blocks b0 + j nw, 32 at a time: their flags in one load (lane j), then the
+    // active ones one after another
+    for (int b0 = gw; b0 < c.nblocks; b0 += 32 * nw) {
+        const int bj = b0 + lane * nw;
+        unsigned act = __ballot_sync(FULLMASK, bj < c.nblocks && flags[bj] != 0u);
+        while (act) {
+            const int j = __ffs(act) - 1;
+            act &= act - 1u;
+            grid_update_block<D, R>(acc, vel, flags, c, b0 + j * nw, lane, acc2, vdel, true);
+        }
+    }
 }
 
 // ---------------------------------------------------------------- mbarrier + bulk copy
