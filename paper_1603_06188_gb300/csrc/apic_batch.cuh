@@ -236,7 +236,8 @@ __global__ void __launch_bounds__(TPB) kb_grid_update(SimDesc<R>* __restrict__ d
             todo &= todo - 1u;
             const int s2 = __shfl_sync(FULLMASK, sim, src);
             const SimDesc<R>& d = descs[s2];
-            grid_update_block<D, R>(d.acc, d.vel, d.flags, d.c, (int)(g0 + (uint32_t)src - bbase[s2]), lane);
+            grid_update_block<D, R>(d.acc, d.vel, d.flags, d.c, (int)(g0 + (uint32_t)src - bbase[s2]), lane, nullptr,
+                                    nullptr, true);
         }
     }
 }
