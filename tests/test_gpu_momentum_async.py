@@ -110,3 +110,25 @@ def test_async_arguments(apic):
     assert e.value.status == apic.APIC_ERR_ARG
     batch.close()
     sim.close()
+
+
+@pytest.mark.parametrize("integrator", [1, 2])
+def test_async_read_with_the_other_integrators(apic, integrator):
+    """lambda = 1 and the midpoint rule write the next state copy in their own G2P; a read
+    queued before two of their steps still returns the state at the time of the call."""
+    import torch
+
+    sc = scenes.falling_cube_3d(res=32, side=0.3, ppc=8, omega=(2.0, 1.0, -1.0), seed=9)
+    cfg = apic.make_config(dim=3, order=2, res=(32,) * 3, dx=sc.dx, dt=1e-4, model="fcr", E=1e4, nu=0.3,
+                           particle_mass=sc.dx ** 3 / 8, particle_volume=sc.dx ** 3 / 8, integrator=integrator)
+    sim = apic.Sim(cfg, sc.n)
+    sim.upload(sc.x, sc.v, sc.grad_v * (0.25 * sc.dx * sc.dx))
+    sim.step(1)
+    before = _sync6(sim)
+    out = torch.full((6,), float("nan"), dtype=torch.float64).pin_memory()
+    sim.momentum_async(out)
+    sim.step(2)
+    sim.momentum_wait()
+    np.testing.assert_array_equal(out.numpy(), before)
+    assert np.abs(_sync6(sim) - before).max() > 0
+    sim.close()
