@@ -152,9 +152,13 @@ __global__ void __launch_bounds__(128) k_force_lambda1(PState<R> st, const uint3
         block_coords<D, R>(blk, c, bo);
 #pragma unroll
         for (int a = 0; a < D; ++a) bo[a] *= 4;
-        for (uint32_t k = start + threadIdx.x; k < end; k += 128) {
+        // warp-uniform rounds: a lane past the tile's end takes the tile's first particle and
+        // adds nothing, so that every lane takes part in the warp's shuffles below
+        for (uint32_t k0 = start; k0 < end; k0 += 128) {
+            const uint32_t k = k0 + threadIdx.x;
+            const bool live = k < end;
             Particle<D, R> p;
-            const uint32_t q = perm[k];
+            const uint32_t q = perm[live ? k : start];
             load_xF<D, R>(st, q, p);
             if (c.mat) load_mat<D, R>(st, q, p);
             int base[D], lb[3] = {0, 0, 0};
@@ -163,12 +167,13 @@ __global__ void __launch_bounds__(128) k_force_lambda1(PState<R> st, const uint3
 #pragma unroll
             for (int a = 0; a < D; ++a) {
                 lb[a] = base[a] - bo[a];
-                if (lb[a] < 0 || lb[a] > 3) ok = false;
+                if (lb[a] < 0 || lb[a] > 3) {
+                    ok = false;
+                    lb[a] = 0;
+                }
             }
-            if (!ok) {
-                set_err(err, APIC_ERRBIT_RANGE);
-                continue;
-            }
+            if (live && !ok) set_err(err, APIC_ERRBIT_RANGE);
+            const bool add = live && ok;
             // grad v in grid units: G_ab = sum_i v_ia (d w / d x^_b)
             R G[D * D];
 #pragma unroll
@@ -212,9 +217,23 @@ __global__ void __launch_bounds__(128) k_force_lambda1(PState<R> st, const uint3
                     R s = R(0);
 #pragma unroll
                     for (int kk = 0; kk < D; ++kk) s += P[a * D + kk] * p.F[b2 * D + kk];
-                    A[a * D + b2] = (c.mat ? p.pv : c.vol) * s;
+                    A[a * D + b2] = add ? (c.mat ? p.pv : c.vol) * s : R(0);
                 }
-            // dt f_i = -dt A grad w / dx into the tile
+            // dt f_i = -dt A grad w / dx into the tile.  The warp's particles are consecutive in
+            // the sorted order, so lanes with the same base cell form runs of lanes: each value is
+            // summed over its run (a segmented suffix sum by shuffles) and the run's first lane
+            // adds it, one shared-memory add per run instead of one per particle.  Every shuffle
+            // is executed by all 32 lanes (none sits behind a lane-dependent condition).
+            const int ck = add ? (lb[0] | (lb[1] << 2) | (lb[2] << 4)) : -1;
+            const int lane = threadIdx.x & 31;
+            bool same[5];
+#pragma unroll
+            for (int s5 = 0; s5 < 5; ++s5) {
+                const int cn = __shfl_down_sync(FULLMASK, ck, 1 << s5);
+                same[s5] = lane + (1 << s5) < 32 && cn == ck;
+            }
+            const int cprev = __shfl_up_sync(FULLMASK, ck, 1);
+            const bool head = add && (lane == 0 || cprev != ck);
 #pragma unroll
             for (int j = 0; j < ((D == 3) ? K * K * K : K * K); ++j) {
                 const int ia = j % K, ib = (j / K) % K, ic = (D == 3) ? j / (K * K) : 0;
@@ -233,7 +252,13 @@ __global__ void __launch_bounds__(128) k_force_lambda1(PState<R> st, const uint3
                     R s = R(0);
 #pragma unroll
                     for (int b2 = 0; b2 < D; ++b2) s += A[a * D + b2] * gw[b2];
-                    atomicAdd(&sf[a][li], -dt_dx * s);
+                    s *= -dt_dx;
+#pragma unroll
+                    for (int s5 = 0; s5 < 5; ++s5) {
+                        const R u = __shfl_down_sync(FULLMASK, s, 1 << s5);
+                        if (same[s5]) s += u;
+                    }
+                    if (head) atomicAdd(&sf[a][li], s);
                 }
             }
         }
