@@ -34,11 +34,13 @@ CASES = [
     (2, 2, 64, 64, 4, "fcr"),
     (2, 3, 64, 64, 4, "fcr"),
     (2, 3, 64, 64, 4, "nh"),
+    # 32 per cell: a warp's 32 particles are mostly one cell, the force's warp sums one run
+    (3, 2, 32, 24, 32, "fcr"),
 ]
 
 
 def _ids(c):
-    return f"d{c[0]}_o{c[1]}_fp{c[2]}_{c[5]}"
+    return f"d{c[0]}_o{c[1]}_fp{c[2]}_{c[5]}" + ("_ppc32" if c[4] == 32 else "")
 
 
 @pytest.fixture(scope="module")
